@@ -1,0 +1,255 @@
+/*
+ * romap.h -- C ABI of the GB300 per-object NeRF training library.
+ *
+ * The library trains one small neural radiance field per detected object, as
+ * in RO-MAP (Han et al., RA-L 2023): each object instance gets its own model
+ * made of a multiresolution hash encoding and a tiny MLP (Sec. V), receives
+ * rays from keyframes incrementally (Sec. V-A-1), and is trained by volume
+ * rendering (Sec. V-B, Eq. 6) against the losses of Eq. 7-11 with Adam.  Many
+ * objects train side by side on one GPU (Sec. V-A-2): one call of
+ * romap_train_step runs a step of every listed object in one batched launch
+ * sequence.
+ *
+ * Conventions
+ *  - Every function returns a romap_status: ROMAP_OK (0) or a negative error.
+ *    romap_last_error() returns the message of the calling thread's last
+ *    error.  No C++ exception crosses this boundary.
+ *  - The library owns all per-object device state (parameters, Adam moments,
+ *    ray pools).  The caller owns every buffer it passes.  Host buffers are
+ *    consumed before the call returns.  Device buffers (flag
+ *    ROMAP_DEVICE_PTR, or the functional API below) must stay valid until the
+ *    context's stream has passed the call.
+ *  - All GPU work is enqueued on the CUDA stream given to romap_init.  Calls
+ *    that return host data synchronise that stream.
+ *  - A context is not thread-safe: use one per host thread, or lock.
+ *  - Frames: rays are given in the world frame unless ROMAP_OBJECT_FRAME.
+ *    The object frame is x_o = R_z(yaw)^T (x_w - t) (Sec. IV-B: objects have
+ *    a translation and a yaw); its box is [-a, a] with a = half_size (Eq. 4).
+ *    Directions are normalised by the library; depths are distances along
+ *    the unit direction.
+ */
+#ifndef ROMAP_H
+#define ROMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ROMAP_API __attribute__((visibility("default")))
+#else
+#define ROMAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t romap_status;
+#define ROMAP_OK 0
+#define ROMAP_ERR_INVALID_ARG (-1) /* null pointer, bad size or flag */
+#define ROMAP_ERR_NOT_FOUND (-2)   /* unknown object id */
+#define ROMAP_ERR_OOM (-3)         /* device or host allocation failed */
+#define ROMAP_ERR_CAPACITY (-4)    /* more objects or rays than configured */
+#define ROMAP_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define ROMAP_ERR_NONFINITE (-6)   /* NaN/Inf in inputs or in the loss */
+#define ROMAP_ERR_TIMEOUT (-7)     /* a bounded device wait gave up */
+#define ROMAP_ERR_BAD_STATE (-8)   /* call not valid in the object's state */
+#define ROMAP_ERR_UNSUPPORTED (-9) /* configuration not built */
+
+/* flags */
+#define ROMAP_DEVICE_PTR 0x1u   /* pointers are device pointers */
+#define ROMAP_OBJECT_FRAME 0x2u /* rays are already in the object frame */
+#define ROMAP_REPLACE 0x4u      /* romap_add_rays: replace the pool instead of appending */
+#define ROMAP_JITTER 0x8u       /* functional forward: stratified jitter instead of midpoints */
+
+/* ray classes from the instance mask (Sec. V-B) */
+#define ROMAP_CLS_OBJECT 0     /* R_o: photometric loss, Eq. 7 */
+#define ROMAP_CLS_BACKGROUND 1 /* R_b: random-colour loss and density loss, Eq. 9-10 */
+#define ROMAP_CLS_OCCLUDER 2   /* no loss */
+
+/* precision of the training step */
+#define ROMAP_PREC_FP32 0       /* FP32 tables, FP32 SIMT MLP */
+#define ROMAP_PREC_MIXED_BF16 1 /* FP16 table copy + FP32 masters, BF16 tensor-core MLP, FP32 accumulation */
+
+typedef struct romap_ctx romap_ctx;
+
+/* Model, loss and optimiser configuration (fixed per context).
+ * Hash grid (Mueller et al. 2022, cited in Sec. II): n_levels levels of
+ * n_features features; level l has resolution
+ *   N_l = floor(base_resolution * b^l + 1e-6),
+ * b = growth, or exp((ln max_resolution - ln base_resolution)/(n_levels-1))
+ * when growth <= 0.  Level l is a dense grid of (N_l+1)^3 entries when that
+ * is <= 2^log2_table_size, else a spatial hash of 2^log2_table_size entries.
+ * MLP (Sec. V, "single-layer MLP", hidden 64): density net (L*F)->64->16
+ * with ReLU, sigma = exp(clamp(out_0, -15, 15)); colour net
+ * (15 geometry features + dir_dims)->64->64->3 with ReLU and sigmoid; no
+ * biases.  Loss weights lambda1, lambda2 of Eq. 11. */
+typedef struct romap_config {
+  int32_t n_levels;        /* L, 1..16 */
+  int32_t n_features;      /* F, must be 2 */
+  int32_t log2_table_size; /* log2 T, 8..24 */
+  int32_t base_resolution; /* N_min >= 1 */
+  double growth;           /* b; <= 0 to derive it from max_resolution */
+  int32_t max_resolution;  /* N_max (used when growth <= 0) */
+  int32_t hidden;          /* must be 64 */
+  int32_t dir_dims;        /* 0 or 3 */
+  int32_t n_samples;       /* N samples per ray, 1..1024 (Sec. V-B) */
+  int32_t rays_per_step;   /* rays drawn per object per step (default) */
+  float lambda1;           /* depth loss weight (Eq. 11) */
+  float lambda2;           /* density loss weight (Eq. 11) */
+  float lr, beta1, beta2, eps; /* Adam */
+  int32_t bg_random;       /* 1: each ray composites over a random colour redrawn every step (Eq. 9) */
+  float bg_const[3];       /* background colour when bg_random == 0 */
+  int32_t precision;       /* ROMAP_PREC_* */
+  int32_t max_objects;     /* capacity of live objects */
+  int64_t max_rays_per_object; /* ray-pool capacity of one object */
+  /* Optional device allocator (both or neither).  alloc returns NULL on
+   * failure, which the library reports as ROMAP_ERR_OOM. */
+  void* (*alloc)(void* user, size_t bytes);
+  void (*dealloc)(void* user, void* ptr);
+  void* alloc_user;
+} romap_config;
+
+/* An object landmark: cuboid pose and size (Sec. IV-B, Eq. 1 and 4). */
+typedef struct romap_object_desc {
+  float t[3];            /* translation (world) */
+  double yaw;            /* rotation about world z, radians */
+  float half_size[3];    /* half extents a of the box */
+  uint64_t seed;         /* random stream of this object (Philox4x32-10 key) */
+  int32_t rays_per_step; /* rays per step for this object; 0 = config default */
+} romap_object_desc;
+
+/* Training rays, structure of arrays, n entries each (Sec. V-A-1: RGB,
+ * instance mask class, sparse depth). */
+typedef struct romap_rays {
+  const float* origin;  /* [3n] */
+  const float* dir;     /* [3n], any non-zero length */
+  const float* rgb;     /* [3n] target colour in [0,1] */
+  const float* depth;   /* [n] target depth, NaN = none; NULL = no depth */
+  const uint8_t* cls;   /* [n] ROMAP_CLS_*; NULL = all object rays */
+} romap_rays;
+
+/* Parameter layout of one object (host-side description). */
+typedef struct romap_layout {
+  int64_t n_params;          /* hash entries * F + MLP weights */
+  int64_t n_hash_params;
+  int32_t n_levels;
+  int32_t resolution[16];    /* N_l */
+  int32_t dense[16];         /* 1 if level l is dense */
+  int64_t level_offset[16];  /* first entry of level l */
+  int64_t mlp_offset[5];     /* parameter offset of MLP layers: density 1, density 2, colour 1, colour 2, colour 3 */
+  int32_t mlp_rows[5], mlp_cols[5]; /* row-major [out][in] */
+} romap_layout;
+
+/* Checkpoint of one object: caller-owned arrays of n_params floats each
+ * (host, or device with ROMAP_DEVICE_PTR in flags). */
+typedef struct romap_state {
+  float* params;
+  float* adam_m;
+  float* adam_v;
+  int64_t n_params;
+  int64_t step;       /* Adam steps taken so far */
+  uint32_t flags;
+} romap_state;
+
+/* Counters accumulated by the context since romap_reset_stats. */
+typedef struct romap_stats {
+  int64_t steps;          /* object-steps run */
+  int64_t rays;           /* rays drawn */
+  int64_t live_samples;   /* samples that went through forward, backward and Adam */
+  int64_t kernel_launches;/* kernels enqueued by the library */
+} romap_stats;
+
+/* ---- lifetime ---------------------------------------------------------- */
+/* Validates cfg, selects the current CUDA device and binds the context to
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream). */
+ROMAP_API romap_status romap_init(const romap_config* cfg, void* cuda_stream, romap_ctx** out);
+ROMAP_API romap_status romap_destroy(romap_ctx* ctx);
+ROMAP_API const char* romap_status_string(romap_status s);
+/* Copies the calling thread's last error message (NUL-terminated). */
+ROMAP_API romap_status romap_last_error(char* buf, size_t n);
+/* Host-only: parameter layout implied by cfg (no GPU needed). */
+ROMAP_API romap_status romap_param_layout(const romap_config* cfg, romap_layout* out);
+
+/* ---- objects (Sec. V: one model per detected instance) ----------------- */
+/* Allocates the object's parameters, Adam moments and ray pool, and
+ * initialises the parameters: hash table U(-1e-4, 1e-4), MLP weights
+ * Glorot-uniform, both from Philox4x32-10 keyed by desc->seed. */
+ROMAP_API romap_status romap_create_object(romap_ctx* ctx, const romap_object_desc* desc, int32_t* out_id);
+ROMAP_API romap_status romap_destroy_object(romap_ctx* ctx, int32_t id);
+/* Occupancy bitgrid of 64^3 cells over the object's box, bit index
+ * x + 64 y + 4096 z in 4096 uint64 words; samples in empty cells are
+ * skipped (density 0).  bits == NULL removes the grid. */
+ROMAP_API romap_status romap_set_occupancy(romap_ctx* ctx, int32_t id, const uint64_t* bits, uint32_t flags);
+/* Appends n rays to the object's pool (incremental data, Sec. V-A-1), or
+ * replaces the pool with ROMAP_REPLACE.  Rays are moved to the object frame
+ * and their directions normalised on the device. */
+ROMAP_API romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* rays, int64_t n, uint32_t flags);
+ROMAP_API romap_status romap_pool_size(romap_ctx* ctx, int32_t id, int64_t* out_n);
+
+/* ---- training (Sec. V-A, V-B; Eq. 6-11; Adam) -------------------------- */
+/* Runs n_steps training steps of every listed object.  Each step of an
+ * object draws B = min(rays_per_step, pool size) rays (uniformly with
+ * replacement, or the whole pool in order when B equals the pool size),
+ * samples N stratified points in the box per ray, encodes and evaluates
+ * them, composites (Eq. 6), evaluates L = L_rgb + L_rr + lambda1 L_depth +
+ * lambda2 L_density (Eq. 11, every term divided by B), backpropagates and
+ * applies Adam.  out_loss (host, nullable) receives n_ids losses of the
+ * last step.  Listed ids must be distinct. */
+ROMAP_API romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps, float* out_loss);
+/* The forward/backward half of a step without Adam: gradients are left in
+ * the objects' gradient buffers (read them with romap_get_grad).
+ * out_loss (host, nullable): 5 floats per object: L, then the rgb, rr,
+ * depth and density sums divided by B. */
+ROMAP_API romap_status romap_forward_backward(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, float* out_loss);
+/* Adam on the listed objects' gradients; zeroes the gradients. */
+ROMAP_API romap_status romap_adam_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids);
+/* Copies the object's gradient buffer (n_params floats). */
+ROMAP_API romap_status romap_get_grad(romap_ctx* ctx, int32_t id, float* out, uint32_t flags);
+/* Copies the last step's ray draw of an object: pool index (int64) and
+ * background colour (3 floats) per ray.  Either pointer may be NULL. */
+ROMAP_API romap_status romap_last_batch(romap_ctx* ctx, int32_t id, int64_t* pool_idx, float* bg, int64_t* out_n);
+
+/* ---- inference --------------------------------------------------------- */
+/* Renders n rays (world frame unless ROMAP_OBJECT_FRAME) with midpoint
+ * samples over bg (3 floats, host).  Outputs per ray (nullable each):
+ * out_rgb [3n], out_depth [n], out_opacity [n]; host unless
+ * ROMAP_DEVICE_PTR, in which case every pointer is a device pointer. */
+ROMAP_API romap_status romap_render(romap_ctx* ctx, int32_t id, const float* origin, const float* dir, int64_t n,
+                          const float bg[3], float* out_rgb, float* out_depth, float* out_opacity, uint32_t flags);
+
+/* ---- checkpoint -------------------------------------------------------- */
+ROMAP_API romap_status romap_get_state(romap_ctx* ctx, int32_t id, romap_state* out);
+ROMAP_API romap_status romap_set_state(romap_ctx* ctx, int32_t id, const romap_state* in);
+
+/* ---- functional, differentiable API (device buffers only) ------------- */
+/* These run the same kernels as training on caller-owned device buffers so
+ * that a differentiable wrapper can call forward and backward separately.
+ * rays: n object-frame rays (origin [3n], dir [3n], unit length), bg [3n].
+ * The RNG of ray r uses key seed and counter (step, r, purpose, .).
+ * Outputs per ray: out_ray [6n] = (C_hat rgb, D_hat, opacity A = 1 -
+ * T_{N+1}, sum_i sigma_i over live samples).  workspace holds the samples
+ * between forward and backward; its size comes from
+ * romap_fn_workspace_size.  Flags: ROMAP_JITTER. */
+ROMAP_API romap_status romap_fn_workspace_size(romap_ctx* ctx, int64_t n, size_t* bytes);
+ROMAP_API romap_status romap_fn_forward(romap_ctx* ctx, const float* params, const float half_size[3], uint64_t seed,
+                              uint32_t step, const uint64_t* occupancy, const float* origin, const float* dir,
+                              const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
+                              float* out_ray, float* out_samples);
+/* Backward of romap_fn_forward given dL/d(out_ray) grad_ray [6n]; adds
+ * dL/dparams into grad_params (n_params floats, device).  out_dsigma
+ * (nullable, [n*N]) receives dL/dsigma per sample slot (0 for missed or
+ * culled slots).  flags: ROMAP_JITTER as in the forward. */
+ROMAP_API romap_status romap_fn_backward(romap_ctx* ctx, const float* params, const float half_size[3], uint64_t seed,
+                               uint32_t step, const uint64_t* occupancy, const float* origin, const float* dir,
+                               const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
+                               const float* grad_ray, float* grad_params, float* out_dsigma);
+
+/* ---- counters ---------------------------------------------------------- */
+ROMAP_API romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out);
+ROMAP_API romap_status romap_reset_stats(romap_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROMAP_H */

@@ -1,0 +1,254 @@
+// Volume rendering (Sec. V-B, Eq. 6), the losses of Eq. 7-11, the
+// compositing adjoint, and the fused Adam update.
+//
+// Compositing: one warp per ray; the samples of a ray are contiguous.  The
+// transmittance T_i = exp(-sum_{j<i} sigma_j delta_j) comes from a warp
+// shuffle prefix scan of sigma*delta carried across 32-sample chunks; the
+// occupancy o_i = 1 - exp(-sigma_i delta_i) is formed with expm1f to avoid
+// cancellation.  The adjoint walks the chunks backwards with a suffix scan:
+//   dC/dsigma_i = delta_i [T_{i+1} c_i - sum_{j>i} w_j c_j - T_{N+1} bg]
+//   dD/dsigma_i = delta_i [T_{i+1} t_i - sum_{j>i} w_j t_j]
+//   dA/dsigma_i = delta_i T_{N+1},  dC/dc_i = w_i.
+// Every ray composites over its own background colour (zero density then
+// renders that colour, which is what the random-colour loss of Eq. 9 asks
+// background rays to learn).
+#include <cuda_fp16.h>
+
+#include "romap_internal.cuh"
+
+namespace romap {
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline float warp_incl_prefix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+__device__ inline float warp_incl_suffix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float n = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v += n;
+  }
+  return v;
+}
+
+// MODE 0: render outputs only.  1: training loss (Eq. 7-11) + adjoint.
+// 2: adjoint of an upstream gradient of the per-ray outputs.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_composite(GridParams g, BatchDesc b, RayBuf R, SampleBuf S, BatchDyn* dyn,
+                                                   int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= b.n_rays) return;
+  const uint32_t cnt = R.count[r], off = R.off[r];
+  const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
+
+  // ---- forward: Eq. 6 -----------------------------------------------------
+  float carry = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dh = 0.f, ssum = 0.f;
+  for (uint32_t base = 0; base < cnt; base += 32) {
+    const uint32_t j = base + lane;
+    const bool in = j < cnt;
+    const float sg = in ? S.sigma[off + j] : 0.f;
+    const float dt = in ? S.dt[off + j] : 0.f;
+    const float tt = in ? S.t[off + j] : 0.f;
+    const float sd = sg * dt;
+    const float incl = warp_incl_prefix(sd, lane);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.f;
+    const float P = carry + excl;
+    const float w = expf(-P) * (-expm1f(-sd));
+    if (in) {
+      C0 = fmaf(w, S.rgb[3 * (off + j)], C0);
+      C1 = fmaf(w, S.rgb[3 * (off + j) + 1], C1);
+      C2 = fmaf(w, S.rgb[3 * (off + j) + 2], C2);
+      Dh = fmaf(w, tt, Dh);
+      ssum += sg;
+      if (MODE != 0) S.dsigma[off + j] = P;  // exclusive prefix, consumed by the adjoint below
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  C0 = warp_sum(C0); C1 = warp_sum(C1); C2 = warp_sum(C2); Dh = warp_sum(Dh); ssum = warp_sum(ssum);
+  const float Tend = expf(-carry);
+  const float A = -expm1f(-carry);
+  const float Ch0 = fmaf(Tend, bg0, C0), Ch1 = fmaf(Tend, bg1, C1), Ch2 = fmaf(Tend, bg2, C2);
+  if (lane == 0) {
+    float* o = R.out + 6 * r;
+    o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = A; o[5] = ssum;
+  }
+  if (MODE == 0) return;
+
+  // ---- loss (Eq. 7-11) or upstream gradient --------------------------------
+  float gC0, gC1, gC2, gD, gA = 0.f, gdir = 0.f;
+  if (MODE == 1) {
+    const int bi = R.obj[r];
+    const float invB = 1.0f / (float)(b.ray_base[bi + 1] - b.ray_base[bi]);
+    const int cls = R.cls[r];
+    float loss = 0.f, l_rgb = 0.f, l_rr = 0.f, l_dep = 0.f, l_den = 0.f;
+    gC0 = gC1 = gC2 = gD = 0.f;
+    if (cls != kClsOccluder) {
+      const float t0 = cls == kClsObject ? R.rgb[3 * r] : bg0;
+      const float t1 = cls == kClsObject ? R.rgb[3 * r + 1] : bg1;
+      const float t2 = cls == kClsObject ? R.rgb[3 * r + 2] : bg2;
+      const float e0 = Ch0 - t0, e1 = Ch1 - t1, e2 = Ch2 - t2;
+      const float sq = e0 * e0 + e1 * e1 + e2 * e2;
+      loss += sq;
+      if (cls == kClsObject) l_rgb = sq; else l_rr = sq;
+      gC0 = 2.f * e0 * invB; gC1 = 2.f * e1 * invB; gC2 = 2.f * e2 * invB;
+      const float dep = R.depth[r];
+      if (isfinite(dep)) {
+        const float e = Dh - dep;
+        loss += g.lambda1 * fabsf(e);
+        l_dep = fabsf(e);
+        gD = g.lambda1 * (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) * invB;
+      }
+      if (cls == kClsBackground) {
+        loss += g.lambda2 * ssum;
+        l_den = ssum;
+        gdir = g.lambda2 * invB;
+      }
+    }
+    if (lane == 0) {
+      float* L = dyn[bi].loss;
+      atomicAdd(L + 0, loss);
+      if (l_rgb != 0.f) atomicAdd(L + 1, l_rgb);
+      if (l_rr != 0.f) atomicAdd(L + 2, l_rr);
+      if (l_dep != 0.f) atomicAdd(L + 3, l_dep);
+      if (l_den != 0.f) atomicAdd(L + 4, l_den);
+      if (!isfinite(loss) && status) atomicOr(status, 1);
+    }
+  } else {
+    const float* u = R.gout + 6 * r;
+    gC0 = u[0]; gC1 = u[1]; gC2 = u[2]; gD = u[3]; gA = u[4]; gdir = u[5];
+  }
+
+  // ---- adjoint, chunks in reverse order -----------------------------------
+  float SC0 = 0.f, SC1 = 0.f, SC2 = 0.f, SD = 0.f;  // sum_{j > chunk} w_j c_j, w_j t_j
+  const float bgterm = Tend * (gC0 * bg0 + gC1 * bg1 + gC2 * bg2);
+  if (cnt == 0) return;
+  for (int base = (int)((cnt - 1) / 32) * 32; base >= 0; base -= 32) {
+    const uint32_t j = (uint32_t)base + lane;
+    const bool in = j < cnt;
+    const float sg = in ? S.sigma[off + j] : 0.f;
+    const float dt = in ? S.dt[off + j] : 0.f;
+    const float tt = in ? S.t[off + j] : 0.f;
+    const float P = in ? S.dsigma[off + j] : 0.f;
+    const float c0 = in ? S.rgb[3 * (off + j)] : 0.f;
+    const float c1 = in ? S.rgb[3 * (off + j) + 1] : 0.f;
+    const float c2 = in ? S.rgb[3 * (off + j) + 2] : 0.f;
+    const float sd = sg * dt;
+    const float Ti = expf(-P);
+    const float Tn = expf(-(P + sd));
+    const float w = in ? Ti * (-expm1f(-sd)) : 0.f;
+    const float wc0 = w * c0, wc1 = w * c1, wc2 = w * c2, wt = w * tt;
+    float s0 = warp_incl_suffix(wc0, lane), s1 = warp_incl_suffix(wc1, lane);
+    float s2 = warp_incl_suffix(wc2, lane), s3 = warp_incl_suffix(wt, lane);
+    float e0 = __shfl_down_sync(0xffffffffu, s0, 1), e1 = __shfl_down_sync(0xffffffffu, s1, 1);
+    float e2 = __shfl_down_sync(0xffffffffu, s2, 1), e3 = __shfl_down_sync(0xffffffffu, s3, 1);
+    if (lane == 31) e0 = e1 = e2 = e3 = 0.f;
+    const float suf0 = SC0 + e0, suf1 = SC1 + e1, suf2 = SC2 + e2, sufD = SD + e3;
+    float gs = gC0 * (Tn * c0 - suf0) + gC1 * (Tn * c1 - suf1) + gC2 * (Tn * c2 - suf2) - bgterm;
+    gs += gD * (Tn * tt - sufD) + gA * Tend;
+    gs = dt * gs + gdir;
+    if (in) {
+      S.dsigma[off + j] = gs;
+      S.drgb[3 * (off + j)] = gC0 * w;
+      S.drgb[3 * (off + j) + 1] = gC1 * w;
+      S.drgb[3 * (off + j) + 2] = gC2 * w;
+    }
+    SC0 += __shfl_sync(0xffffffffu, s0, 0);
+    SC1 += __shfl_sync(0xffffffffu, s1, 0);
+    SC2 += __shfl_sync(0xffffffffu, s2, 0);
+    SD += __shfl_sync(0xffffffffu, s3, 0);
+  }
+}
+
+void launch_composite(int mode, const GridParams& g, const BatchDesc& b, RayBuf r, SampleBuf s, BatchDyn* dyn,
+                      int32_t* status, cudaStream_t stream) {
+  if (b.n_rays <= 0) return;
+  unsigned blocks = (unsigned)(((int64_t)b.n_rays * 32 + 255) / 256);
+  if (mode == 0) k_composite<0><<<blocks, 256, 0, stream>>>(g, b, r, s, dyn, status);
+  else if (mode == 1) k_composite<1><<<blocks, 256, 0, stream>>>(g, b, r, s, dyn, status);
+  else k_composite<2><<<blocks, 256, 0, stream>>>(g, b, r, s, dyn, status);
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba) with bias correction over every parameter of every
+// batch object; zeroes the gradient; optionally refreshes the FP16 copy of
+// the hash table.  float4 streaming, grid (chunks, objects).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int write_half) {
+  const ObjectDev& ob = b.objs[b.slot[blockIdx.y]];
+  const double t = (double)ob.step;
+  const float c1 = (float)(1.0 / (1.0 - pow((double)g.beta1, t)));
+  const float c2 = (float)(1.0 / (1.0 - pow((double)g.beta2, t)));
+  const float b1 = g.beta1, b2 = g.beta2, lr = g.lr, eps = g.eps;
+  const float ob1 = 1.0f - b1, ob2 = 1.0f - b2;
+  float4* P = reinterpret_cast<float4*>(ob.params);
+  float4* G = reinterpret_cast<float4*>(ob.grad);
+  float4* M = reinterpret_cast<float4*>(ob.m);
+  float4* V = reinterpret_cast<float4*>(ob.v);
+  const int64_t n4 = g.n_params_pad / 4;
+  const int64_t nh4 = g.n_hash / 4;  // n_hash is even; the FP16 copy covers whole float4s below n_hash
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 gr = G[i], m = M[i], v = V[i], p = P[i];
+    float gv[4] = {gr.x, gr.y, gr.z, gr.w}, mv[4] = {m.x, m.y, m.z, m.w}, vv[4] = {v.x, v.y, v.z, v.w};
+    float pv[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      mv[k] = b1 * mv[k] + ob1 * gv[k];
+      vv[k] = b2 * vv[k] + ob2 * gv[k] * gv[k];
+      pv[k] -= lr * (mv[k] * c1) / (sqrtf(vv[k] * c2) + eps);
+    }
+    P[i] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    M[i] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+    V[i] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+    G[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (write_half && ob.table_h && i < nh4) {
+      __half2 h0 = __floats2half2_rn(pv[0], pv[1]), h1 = __floats2half2_rn(pv[2], pv[3]);
+      reinterpret_cast<__half2*>(ob.table_h)[2 * i] = h0;
+      reinterpret_cast<__half2*>(ob.table_h)[2 * i + 1] = h1;
+    }
+  }
+}
+
+__global__ void k_advance_step(BatchDesc b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < b.n) b.objs[b.slot[i]].step += 1u;
+}
+
+void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream) {
+  if (b.n <= 0) return;
+  int64_t n4 = g.n_params_pad / 4;
+  int chunks = (int)((n4 + 255) / 256);
+  int max_chunks = 2048 / (b.n < 1 ? 1 : b.n) + 1;
+  if (max_chunks < 8) max_chunks = 8;
+  if (chunks > max_chunks) chunks = max_chunks;
+  k_adam<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, write_half);
+  k_advance_step<<<(b.n + 127) / 128, 128, 0, stream>>>(b);
+}
+
+__global__ void k_split_outputs(const float* __restrict__ ray_out, int64_t n, float* rgb, float* depth,
+                                float* opacity) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const float* o = ray_out + 6 * r;
+  rgb[3 * r] = o[0]; rgb[3 * r + 1] = o[1]; rgb[3 * r + 2] = o[2];
+  depth[r] = o[3];
+  opacity[r] = o[4];
+}
+
+void launch_split_outputs(const float* ray_out, int64_t n, float* rgb, float* depth, float* opacity,
+                          cudaStream_t stream) {
+  if (n <= 0) return;
+  k_split_outputs<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(ray_out, n, rgb, depth, opacity);
+}
+
+}  // namespace romap

@@ -1,0 +1,443 @@
+// Ray sampling stage of the training step (Sec. V-B): ray draw, world ->
+// object frame, ray/box slab test, stratified samples, occupancy culling and
+// compaction; plus parameter initialisation.
+//
+// The FP32 arithmetic of this stage is written operation by operation with
+// round-to-nearest intrinsics (no contraction into FMA) in one fixed order,
+// so that sample positions and hash indices are reproducible bit for bit.
+#include "romap_internal.cuh"
+
+namespace romap {
+
+__device__ inline uint32_t philox_word(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                                       int w) {
+  return u4_word(philox(c0, c1, c2, c3, k0, k1), w);
+}
+
+// ---------------------------------------------------------------------------
+// Parameter initialisation: hash entries U(-1e-4, 1e-4) (counter (k>>2, 0,
+// INIT_HASH, 0), word k&3); MLP layer l Glorot-uniform with limit
+// sqrt(6/(fan_in+fan_out)) (counter (k>>2, l, INIT_MLP, 0), word k&3).
+// ---------------------------------------------------------------------------
+__global__ void k_init_params(GridParams g, float* params, uint32_t key0, uint32_t key1, float lim0, float lim1,
+                              float lim2, float lim3, float lim4) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < g.n_params_pad; i += stride) {
+    if (i >= g.n_params) { params[i] = 0.0f; continue; }
+    uint32_t ctr1 = 0, purpose = kPurposeInitHash;
+    int64_t k = i;
+    float lim = 1e-4f;
+    if (i >= g.n_hash) {
+      int layer = 0;
+#pragma unroll
+      for (int l = 1; l < 5; ++l)
+        if (i >= g.mlp_off[l]) layer = l;
+      k = i - g.mlp_off[layer];
+      ctr1 = (uint32_t)layer;
+      purpose = kPurposeInitMlp;
+      lim = layer == 0 ? lim0 : layer == 1 ? lim1 : layer == 2 ? lim2 : layer == 3 ? lim3 : lim4;
+    }
+    uint32_t x = philox_word((uint32_t)(k >> 2), ctr1, purpose, 0u, key0, key1, (int)(k & 3));
+    float u = u01(x);
+    params[i] = __fmul_rn(__fsub_rn(__fmul_rn(2.0f, u), 1.0f), lim);
+  }
+}
+
+void launch_init_params(const GridParams& g, float* params, uint32_t key0, uint32_t key1, cudaStream_t stream) {
+  int dims[5][2] = {{kH, g.LF}, {kDOut, kH}, {kH, g.cin}, {kH, kH}, {3, kH}};
+  float lim[5];
+  for (int l = 0; l < 5; ++l) lim[l] = (float)sqrt(6.0 / (double)(dims[l][0] + dims[l][1]));
+  int blocks = (int)((g.n_params_pad + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_init_params<<<blocks, 256, 0, stream>>>(g, params, key0, key1, lim[0], lim[1], lim[2], lim[3], lim[4]);
+}
+
+// ---------------------------------------------------------------------------
+// World -> object frame (Sec. IV-B pose: translation t, yaw about z):
+// x_o = R_z^T (x_w - t), d_o = R_z^T d_w / |R_z^T d_w|.
+// ---------------------------------------------------------------------------
+__global__ void k_transform_rays(const float* __restrict__ o_in, const float* __restrict__ d_in,
+                                 const float* __restrict__ rgb_in, const float* __restrict__ depth_in,
+                                 const uint8_t* __restrict__ cls_in, int64_t n, int object_frame, float tx, float ty,
+                                 float tz, float cz, float sz, float* o_out, float* d_out, float* rgb_out,
+                                 float* depth_out, uint8_t* cls_out) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  float ox = o_in[3 * r], oy = o_in[3 * r + 1], oz = o_in[3 * r + 2];
+  float dx = d_in[3 * r], dy = d_in[3 * r + 1], dz = d_in[3 * r + 2];
+  float rx = dx, ry = dy, rz = dz;
+  if (!object_frame) {
+    float px = __fsub_rn(ox, tx), py = __fsub_rn(oy, ty), pz = __fsub_rn(oz, tz);
+    ox = __fadd_rn(__fmul_rn(cz, px), __fmul_rn(sz, py));
+    oy = __fsub_rn(__fmul_rn(cz, py), __fmul_rn(sz, px));
+    oz = pz;
+    rx = __fadd_rn(__fmul_rn(cz, dx), __fmul_rn(sz, dy));
+    ry = __fsub_rn(__fmul_rn(cz, dy), __fmul_rn(sz, dx));
+    rz = dz;
+  }
+  float len = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)), __fmul_rn(rz, rz)));
+  o_out[3 * r] = ox; o_out[3 * r + 1] = oy; o_out[3 * r + 2] = oz;
+  d_out[3 * r] = __fdiv_rn(rx, len);
+  d_out[3 * r + 1] = __fdiv_rn(ry, len);
+  d_out[3 * r + 2] = __fdiv_rn(rz, len);
+  rgb_out[3 * r] = rgb_in ? rgb_in[3 * r] : 0.0f;
+  rgb_out[3 * r + 1] = rgb_in ? rgb_in[3 * r + 1] : 0.0f;
+  rgb_out[3 * r + 2] = rgb_in ? rgb_in[3 * r + 2] : 0.0f;
+  depth_out[r] = depth_in ? depth_in[r] : __int_as_float(0x7fc00000);
+  cls_out[r] = cls_in ? cls_in[r] : (uint8_t)kClsObject;
+}
+
+void launch_transform_rays(const float* o_in, const float* d_in, const float* rgb_in, const float* depth_in,
+                           const uint8_t* cls_in, int64_t n, int object_frame, float tx, float ty, float tz, float cz,
+                           float sz, float* o_out, float* d_out, float* rgb_out, float* depth_out, uint8_t* cls_out,
+                           cudaStream_t stream) {
+  if (n <= 0) return;
+  int64_t blocks = (n + 255) / 256;
+  k_transform_rays<<<(unsigned)blocks, 256, 0, stream>>>(o_in, d_in, rgb_in, depth_in, cls_in, n, object_frame, tx,
+                                                         ty, tz, cz, sz, o_out, d_out, rgb_out, depth_out, cls_out);
+}
+
+// ---------------------------------------------------------------------------
+// Ray/box slab test (box [-half, half]); returns hit.
+// ---------------------------------------------------------------------------
+__device__ inline bool slab(const float o[3], const float d[3], const float half[3], float& tn, float& tf) {
+  float t0 = 0.0f, t1 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float lo = -half[a], hi = half[a];
+    float inv = __fdiv_rn(1.0f, d[a]);
+    float ta = __fmul_rn(__fsub_rn(lo, o[a]), inv);
+    float tb = __fmul_rn(__fsub_rn(hi, o[a]), inv);
+    float mn = fminf(ta, tb), mx = fmaxf(ta, tb);
+    t0 = (a == 0) ? mn : fmaxf(t0, mn);
+    t1 = (a == 0) ? mx : fminf(t1, mx);
+  }
+  tn = fmaxf(t0, 0.0f);
+  tf = t1;
+  return t1 > tn;
+}
+
+__device__ inline bool occupied(const uint64_t* occ, float x, float y, float z, const float half[3],
+                                const float inv_ext[3]) {
+  if (!occ) return true;
+  float p[3] = {x, y, z};
+  uint32_t c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u = fminf(fmaxf(__fmul_rn(__fsub_rn(p[a], -half[a]), inv_ext[a]), 0.0f), 1.0f);
+    int ci = (int)__fmul_rn(u, 64.0f);
+    c[a] = (uint32_t)(ci > 63 ? 63 : ci);
+  }
+  uint32_t bit = c[0] + 64u * c[1] + 4096u * c[2];
+  return (__ldg(occ + (bit >> 6)) >> (bit & 63u)) & 1ull;
+}
+
+// Stratified candidates t_i = t_near + (i + u_i) dt_N, delta_i = t_{i+1} - t_i
+// (last: t_far - t_{N-1}), x_i = o + t_i d; f(i, t, delta, x, y, z, live).
+template <class Fn>
+__device__ inline void for_candidates(const float o[3], const float d[3], float tn, float tf, int N, uint32_t k0,
+                                      uint32_t k1, uint32_t step, uint32_t slot, int jitter, const uint64_t* occ,
+                                      const float half[3], const float inv_ext[3], Fn f) {
+  float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
+  U4 rnd = {0, 0, 0, 0};
+  auto t_of = [&](int i) -> float {
+    float u = 0.5f;
+    if (jitter) {
+      if ((i & 3) == 0) rnd = philox(step, slot, kPurposeJitter, (uint32_t)i >> 2, k0, k1);
+      u = u01(u4_word(rnd, i & 3));
+    }
+    return __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, u), step_len));
+  };
+  float t_cur = t_of(0);
+  for (int i = 0; i < N; ++i) {
+    float t_next = (i + 1 < N) ? t_of(i + 1) : tf;
+    float dt = __fsub_rn(t_next, t_cur);
+    float x = __fadd_rn(o[0], __fmul_rn(t_cur, d[0]));
+    float y = __fadd_rn(o[1], __fmul_rn(t_cur, d[1]));
+    float z = __fadd_rn(o[2], __fmul_rn(t_cur, d[2]));
+    f(i, t_cur, dt, x, y, z, occupied(occ, x, y, z, half, inv_ext));
+    t_cur = t_next;
+  }
+}
+
+// Block-wide exclusive scan of 256 values.
+__device__ inline uint32_t block_excl_scan256(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[8];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  uint32_t base = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i < w) base += warp_tot[i];
+    tot += warp_tot[i];
+  }
+  *total = tot;
+  __syncthreads();
+  return base + incl - v;
+}
+
+struct RayCtx {
+  int bi, rl, r;
+  bool valid;
+};
+
+__device__ inline RayCtx ray_of_thread(const BatchDesc& b) {
+  RayCtx c;
+  c.bi = b.block_obj[blockIdx.x];
+  int local_block = blockIdx.x - b.block_base[c.bi];
+  c.rl = local_block * 256 + threadIdx.x;
+  int n = b.ray_base[c.bi + 1] - b.ray_base[c.bi];
+  c.valid = c.rl < n;
+  c.r = b.ray_base[c.bi] + c.rl;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Ray draw + slab + live-sample count.  One block of 256 ray slots of one
+// batch object.  Draw: slot s of an object takes pool index s when the whole
+// pool is used, else mulhi32(Philox(step, s, RAY, 0).x, pool size); its
+// background is u01 of Philox(step, s, BG, 0) words 0..2 when random.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, RayBuf R, uint32_t* block_sums) {
+  RayCtx c = ray_of_thread(b);
+  const ObjectDev& ob = b.objs[b.slot[c.bi]];
+  uint32_t count = 0;
+  if (c.valid) {
+    float o[3], d[3], bg[3];
+    uint32_t step = b.explicit_rays ? b.explicit_step : ob.step;
+    if (b.explicit_rays) {
+      for (int a = 0; a < 3; ++a) {
+        o[a] = b.ex_o[3 * c.r + a];
+        d[a] = b.ex_d[3 * c.r + a];
+        bg[a] = b.ex_bg[3 * c.r + a];
+      }
+      R.rgb[3 * c.r] = R.rgb[3 * c.r + 1] = R.rgb[3 * c.r + 2] = 0.0f;
+      R.depth[c.r] = __int_as_float(0x7fc00000);
+      R.cls[c.r] = kClsObject;
+      R.pool_idx[c.r] = c.rl;
+    } else {
+      int64_t p;
+      if (ob.whole_pool) {
+        p = c.rl;
+      } else {
+        uint32_t x = philox(step, (uint32_t)c.rl, kPurposeRay, 0u, ob.key0, ob.key1).x;
+        p = (int64_t)(((uint64_t)x * (uint64_t)ob.pool_n) >> 32);
+      }
+      for (int a = 0; a < 3; ++a) {
+        o[a] = ob.pool_o[3 * p + a];
+        d[a] = ob.pool_d[3 * p + a];
+        R.rgb[3 * c.r + a] = ob.pool_rgb[3 * p + a];
+      }
+      R.depth[c.r] = ob.pool_depth[p];
+      R.cls[c.r] = ob.pool_cls[p];
+      R.pool_idx[c.r] = p;
+      if (g.bg_random) {
+        U4 w = philox(step, (uint32_t)c.rl, kPurposeBg, 0u, ob.key0, ob.key1);
+        bg[0] = u01(w.x); bg[1] = u01(w.y); bg[2] = u01(w.z);
+      } else {
+        bg[0] = g.bg_const[0]; bg[1] = g.bg_const[1]; bg[2] = g.bg_const[2];
+      }
+    }
+    float tn, tf;
+    bool hit = slab(o, d, ob.half, tn, tf);
+    if (hit) {
+      if (!ob.occ) {
+        count = (uint32_t)g.n_samples;
+      } else {
+        for_candidates(o, d, tn, tf, g.n_samples, ob.key0, ob.key1, step, (uint32_t)c.rl, b.jitter, ob.occ, ob.half,
+                       ob.inv_ext, [&](int, float, float, float, float, float, bool live) { count += live ? 1u : 0u; });
+      }
+    }
+    for (int a = 0; a < 3; ++a) {
+      R.o[3 * c.r + a] = o[a];
+      R.d[3 * c.r + a] = d[a];
+      R.bg[3 * c.r + a] = bg[a];
+    }
+    R.tn[c.r] = tn;
+    R.tf[c.r] = hit ? tf : tn;
+    R.count[c.r] = count;
+    R.obj[c.r] = c.bi;
+  }
+  uint32_t total;
+  uint32_t excl = block_excl_scan256(count, &total);
+  if (c.valid) R.off[c.r] = excl;
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+void launch_ray_setup(const GridParams& g, const BatchDesc& b, RayBuf r, uint32_t* block_sums, cudaStream_t stream) {
+  if (b.n_blocks <= 0) return;
+  k_ray_setup<<<b.n_blocks, 256, 0, stream>>>(g, b, r, block_sums);
+}
+
+// ---------------------------------------------------------------------------
+// Per-object offsets: each warp scans the block totals of its objects; one
+// block-wide scan over tile counts places every object on a tile boundary.
+// Padding samples up to the tile boundary get ray = kNoRay.
+// ---------------------------------------------------------------------------
+constexpr int kMaxBatch = 1024;
+
+__global__ void __launch_bounds__(1024) k_scan(BatchDesc b, uint32_t* block_sums, BatchDyn* dyn, int32_t* totals,
+                                               SampleBuf S, unsigned long long* live_counter) {
+  __shared__ uint32_t s_count[kMaxBatch];
+  __shared__ uint32_t s_tiles[kMaxBatch];
+  __shared__ uint32_t s_wsum[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = w; i < b.n; i += 32) {
+    int bb = b.block_base[i], nb = b.block_base[i + 1] - bb;
+    uint32_t carry = 0;
+    for (int c = 0; c < nb; c += 32) {
+      uint32_t v = (c + lane < nb) ? block_sums[bb + c + lane] : 0u;
+      uint32_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+      }
+      if (c + lane < nb) block_sums[bb + c + lane] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+      s_count[i] = carry;
+      s_tiles[i] = (carry + kTile - 1) / kTile;
+    }
+  }
+  __syncthreads();
+  // exclusive scan of s_tiles over batch entries (n <= 1024)
+  uint32_t v = threadIdx.x < (unsigned)b.n ? s_tiles[threadIdx.x] : 0u;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) s_wsum[w] = incl;
+  __syncthreads();
+  uint32_t base = 0, all = 0;
+  for (int i = 0; i < 32; ++i) {
+    if (i < w) base += s_wsum[i];
+    all += s_wsum[i];
+  }
+  uint32_t tile_base = base + incl - v;
+  if (threadIdx.x < (unsigned)b.n) {
+    int i = threadIdx.x;
+    BatchDyn dd;
+    dd.tile_base = (int32_t)tile_base;
+    dd.n_tiles = (int32_t)v;
+    dd.sample_base = (int64_t)tile_base * kTile;
+    dd.n_samples = (int32_t)s_count[i];
+    dd.pad_ = 0;
+    for (int k = 0; k < 5; ++k) dd.loss[k] = 0.0f;
+    dd.pad2_[0] = dd.pad2_[1] = dd.pad2_[2] = 0.0f;
+    dyn[i] = dd;
+  }
+  if (threadIdx.x < (unsigned)b.n) s_tiles[threadIdx.x] = tile_base;  // now the first tile of entry i
+  __syncthreads();
+  // padding samples of every entry up to its tile boundary
+  for (int i = w; i < b.n; i += 32) {
+    uint32_t cnt = s_count[i];
+    uint32_t n_tiles = (cnt + kTile - 1) / kTile;
+    uint32_t pad = n_tiles * kTile - cnt;
+    int64_t start = (int64_t)s_tiles[i] * kTile + cnt;
+    for (uint32_t j = lane; j < pad; j += 32) S.ray[start + j] = kNoRay;
+  }
+  if (threadIdx.x == 0) {
+    totals[0] = (int32_t)all;
+    uint64_t tot = 0;
+    for (int i = 0; i < b.n; ++i) tot += s_count[i];
+    totals[1] = (int32_t)tot;
+    if (live_counter) atomicAdd(live_counter, (unsigned long long)tot);
+  }
+}
+
+void launch_scan(const GridParams&, const BatchDesc& b, uint32_t* block_sums, BatchDyn* dyn, int32_t* totals,
+                 SampleBuf s, unsigned long long* live_counter, cudaStream_t stream) {
+  k_scan<<<1, 1024, 0, stream>>>(b, block_sums, dyn, totals, s, live_counter);
+}
+
+// ---------------------------------------------------------------------------
+// Write the live samples of every ray at its compacted offset.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_write_samples(GridParams g, BatchDesc b, RayBuf R, const uint32_t* block_sums,
+                                                       const BatchDyn* dyn, SampleBuf S) {
+  RayCtx c = ray_of_thread(b);
+  if (!c.valid) return;
+  const ObjectDev& ob = b.objs[b.slot[c.bi]];
+  uint32_t off = (uint32_t)(dyn[c.bi].sample_base + block_sums[blockIdx.x] + R.off[c.r]);
+  R.off[c.r] = off;
+  uint32_t count = R.count[c.r];
+  if (count == 0) return;
+  float o[3] = {R.o[3 * c.r], R.o[3 * c.r + 1], R.o[3 * c.r + 2]};
+  float d[3] = {R.d[3 * c.r], R.d[3 * c.r + 1], R.d[3 * c.r + 2]};
+  uint32_t step = b.explicit_rays ? b.explicit_step : ob.step;
+  uint32_t j = off;
+  for_candidates(o, d, R.tn[c.r], R.tf[c.r], g.n_samples, ob.key0, ob.key1, step, (uint32_t)c.rl, b.jitter, ob.occ,
+                 ob.half, ob.inv_ext, [&](int i, float t, float dt, float x, float y, float z, bool live) {
+                   if (!live) return;
+                   S.x[3 * (size_t)j] = x;
+                   S.x[3 * (size_t)j + 1] = y;
+                   S.x[3 * (size_t)j + 2] = z;
+                   S.t[j] = t;
+                   S.dt[j] = dt;
+                   S.ray[j] = (uint32_t)c.r;
+                   S.cand[j] = (uint32_t)i;
+                   ++j;
+                 });
+}
+
+void launch_write_samples(const GridParams& g, const BatchDesc& b, RayBuf r, const uint32_t* block_sums,
+                          const BatchDyn* dyn, SampleBuf s, cudaStream_t stream) {
+  if (b.n_blocks <= 0) return;
+  k_write_samples<<<b.n_blocks, 256, 0, stream>>>(g, b, r, block_sums, dyn, s);
+}
+
+// ---------------------------------------------------------------------------
+// Scatter per-sample values into per-slot arrays [ray * N + candidate].
+// ---------------------------------------------------------------------------
+__global__ void k_scatter_slots(int n_samples_per_ray, int64_t n_rays, RayBuf R, SampleBuf S, const float* src,
+                                int src_stride, float* dst, int dst_stride) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  uint32_t cnt = R.count[r], off = R.off[r];
+  for (uint32_t j = 0; j < cnt; ++j) {
+    uint32_t s = off + j;
+    int64_t slot = r * n_samples_per_ray + S.cand[s];
+    for (int k = 0; k < dst_stride; ++k) dst[slot * dst_stride + k] = src[(int64_t)s * src_stride + k];
+  }
+}
+
+void launch_scatter_slots(const GridParams& g, int64_t n_rays, const RayBuf r, const SampleBuf s, const float* src,
+                          int src_stride, float* dst, int dst_stride, cudaStream_t stream) {
+  if (n_rays <= 0) return;
+  k_scatter_slots<<<(unsigned)((n_rays + 255) / 256), 256, 0, stream>>>(g.n_samples, n_rays, r, s, src, src_stride,
+                                                                        dst, dst_stride);
+}
+
+// Per slot [ray * N + candidate] x 6: t, delta, x, y, z, sigma.
+__global__ void k_sample_slots(int n_samples_per_ray, int64_t n_rays, RayBuf R, SampleBuf S, float* dst) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  uint32_t cnt = R.count[r], off = R.off[r];
+  for (uint32_t j = 0; j < cnt; ++j) {
+    uint32_t s = off + j;
+    float* o = dst + (r * n_samples_per_ray + S.cand[s]) * 6;
+    o[0] = S.t[s]; o[1] = S.dt[s];
+    o[2] = S.x[3 * (size_t)s]; o[3] = S.x[3 * (size_t)s + 1]; o[4] = S.x[3 * (size_t)s + 2];
+    o[5] = S.sigma[s];
+  }
+}
+
+void launch_sample_slots(const GridParams& g, int64_t n_rays, const RayBuf r, const SampleBuf s, float* dst,
+                         cudaStream_t stream) {
+  if (n_rays <= 0) return;
+  k_sample_slots<<<(unsigned)((n_rays + 255) / 256), 256, 0, stream>>>(g.n_samples, n_rays, r, s, dst);
+}
+
+}  // namespace romap

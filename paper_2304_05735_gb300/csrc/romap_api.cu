@@ -1,0 +1,1097 @@
+// Host runtime of libromap: the C ABI declared in include/romap.h.
+//
+// It owns contexts, objects (parameters, Adam moments, ray pools, occupancy
+// grids), the per-step workspace, and the launch sequence of a training
+// step on the context's stream:
+//   ray setup -> scan -> sample write -> tile forward -> composite/loss/adjoint
+//   -> tile backward -> Adam (+ step counter advance)
+// Every object's step counter (the Philox counter of its ray draw and the
+// Adam bias-correction exponent) lives on the device and is advanced by the
+// Adam launch, so a step's launch sequence does not depend on host state
+// that changes from step to step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "romap.h"
+#include "romap_internal.cuh"
+
+using namespace romap;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+romap_status fail(romap_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                                  \
+  do {                                                                                                  \
+    cudaError_t e_ = (expr);                                                                            \
+    if (e_ != cudaSuccess) return fail(ROMAP_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                             \
+  } while (0)
+
+#define ROMAP_TRY(expr)            \
+  do {                             \
+    romap_status s_ = (expr);      \
+    if (s_ != ROMAP_OK) return s_; \
+  } while (0)
+
+struct Object {
+  bool alive = false;
+  romap_object_desc desc{};
+  float* params = nullptr;
+  float* grad = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  uint16_t* table_h = nullptr;
+  float* pool_o = nullptr;
+  float* pool_d = nullptr;
+  float* pool_rgb = nullptr;
+  float* pool_depth = nullptr;
+  uint8_t* pool_cls = nullptr;
+  int64_t pool_n = 0, pool_cap = 0;
+  uint64_t* occ = nullptr;
+  int64_t steps_done = 0;
+  int32_t rays_per_step = 0;
+};
+
+// A device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct romap_ctx {
+  romap_config cfg{};
+  GridParams g{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_sms = 0;
+  std::vector<Object> objs;
+  std::vector<ObjectDev> objs_host;  // mirror of objs_dev
+  ObjectDev* objs_dev = nullptr;
+  ObjectDev* fn_obj_dev = nullptr;   // object record of functional calls
+  // step workspace
+  DevBuf ws_rays, ws_samples, ws_blocks, ws_batch, ws_dyn, ws_stage;
+  int64_t cap_rays = 0, cap_samples = 0, cap_blocks = 0, cap_batch = 0;
+  RayBuf R{};
+  SampleBuf S{};
+  uint32_t* block_sums = nullptr;
+  BatchDyn* dyn = nullptr;
+  int32_t* totals = nullptr;
+  int32_t* status = nullptr;
+  unsigned long long* live_counter = nullptr;
+  int32_t* batch_arrays = nullptr;
+  std::vector<int32_t> batch_key;  // host copy of the uploaded batch arrays
+  int batch_n = 0;                 // entries of the uploaded batch
+  BatchDyn* dyn_host = nullptr;    // pinned
+  romap_stats stats{};
+  int64_t launches = 0;
+};
+
+namespace {
+
+romap_status dev_alloc(romap_ctx* ctx, size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (ctx->cfg.alloc) {
+    *out = ctx->cfg.alloc(ctx->cfg.alloc_user, bytes);
+    if (!*out) return fail(ROMAP_ERR_OOM, "device allocation of %zu bytes failed (caller allocator)", bytes);
+    return ROMAP_OK;
+  }
+  cudaError_t e = cudaMallocAsync(out, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return fail(ROMAP_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return ROMAP_OK;
+}
+
+void dev_free(romap_ctx* ctx, void* p) {
+  if (!p) return;
+  if (ctx->cfg.alloc) ctx->cfg.dealloc(ctx->cfg.alloc_user, p);
+  else cudaFreeAsync(p, ctx->stream);
+}
+
+template <class T>
+romap_status dev_alloc_t(romap_ctx* ctx, size_t count, T** out) {
+  void* p = nullptr;
+  romap_status s = dev_alloc(ctx, count * sizeof(T), &p);
+  *out = static_cast<T*>(p);
+  return s;
+}
+
+romap_status grow(romap_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return ROMAP_OK;
+  size_t nb = bytes + bytes / 4;
+  void* p = nullptr;
+  ROMAP_TRY(dev_alloc(ctx, nb, &p));
+  dev_free(ctx, b.p);
+  b.p = p;
+  b.bytes = nb;
+  return ROMAP_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves a RayBuf of capacity nr from base; returns bytes used.
+size_t carve_rays(char* base, int64_t nr, RayBuf* R) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + o : nullptr;
+    o = align_up(o + bytes, 256);
+    return p;
+  };
+  R->o = (float*)take(sizeof(float) * 3 * nr);
+  R->d = (float*)take(sizeof(float) * 3 * nr);
+  R->tn = (float*)take(sizeof(float) * nr);
+  R->tf = (float*)take(sizeof(float) * nr);
+  R->bg = (float*)take(sizeof(float) * 3 * nr);
+  R->rgb = (float*)take(sizeof(float) * 3 * nr);
+  R->depth = (float*)take(sizeof(float) * nr);
+  R->cls = (uint8_t*)take(nr);
+  R->pool_idx = (int64_t*)take(sizeof(int64_t) * nr);
+  R->count = (uint32_t*)take(sizeof(uint32_t) * nr);
+  R->off = (uint32_t*)take(sizeof(uint32_t) * nr);
+  R->obj = (int32_t*)take(sizeof(int32_t) * nr);
+  R->out = (float*)take(sizeof(float) * 6 * nr);
+  R->gout = nullptr;
+  return o;
+}
+
+size_t carve_samples(char* base, int64_t ns, SampleBuf* S) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + o : nullptr;
+    o = align_up(o + bytes, 256);
+    return p;
+  };
+  S->x = (float*)take(sizeof(float) * 3 * ns);
+  S->t = (float*)take(sizeof(float) * ns);
+  S->dt = (float*)take(sizeof(float) * ns);
+  S->ray = (uint32_t*)take(sizeof(uint32_t) * ns);
+  S->cand = (uint32_t*)take(sizeof(uint32_t) * ns);
+  S->sigma = (float*)take(sizeof(float) * ns);
+  S->rgb = (float*)take(sizeof(float) * 3 * ns);
+  S->dsigma = (float*)take(sizeof(float) * ns);
+  S->drgb = (float*)take(sizeof(float) * 3 * ns);
+  return o;
+}
+
+romap_status ensure_workspace(romap_ctx* ctx, int64_t nr, int64_t ns, int64_t nblocks, int64_t nbatch) {
+  if (nr > ctx->cap_rays) {
+    int64_t cap = nr + nr / 4 + 256;
+    ROMAP_TRY(grow(ctx, ctx->ws_rays, carve_rays(nullptr, cap, &ctx->R)));
+    carve_rays((char*)ctx->ws_rays.p, cap, &ctx->R);
+    ctx->cap_rays = cap;
+  }
+  if (ns > ctx->cap_samples) {
+    int64_t cap = ns + ns / 4 + 1024;
+    ROMAP_TRY(grow(ctx, ctx->ws_samples, carve_samples(nullptr, cap, &ctx->S)));
+    carve_samples((char*)ctx->ws_samples.p, cap, &ctx->S);
+    ctx->cap_samples = cap;
+  }
+  if (nblocks > ctx->cap_blocks) {
+    int64_t cap = nblocks + 64;
+    ROMAP_TRY(grow(ctx, ctx->ws_blocks, sizeof(uint32_t) * cap));
+    ctx->block_sums = (uint32_t*)ctx->ws_blocks.p;
+    ctx->cap_blocks = cap;
+  }
+  if (nbatch > ctx->cap_batch) {
+    int64_t cap = nbatch < 64 ? 64 : nbatch;
+    ROMAP_TRY(grow(ctx, ctx->ws_dyn, sizeof(BatchDyn) * cap));
+    ctx->dyn = (BatchDyn*)ctx->ws_dyn.p;
+    if (ctx->dyn_host) cudaFreeHost(ctx->dyn_host);
+    CUDA_TRY(cudaMallocHost((void**)&ctx->dyn_host, sizeof(BatchDyn) * cap));
+    ctx->cap_batch = cap;
+  }
+  return ROMAP_OK;
+}
+
+// Batch arrays: slot[n], ray_base[n+1], block_base[n+1], block_obj[n_blocks].
+struct HostBatch {
+  std::vector<int32_t> arr;
+  int n = 0, n_blocks = 0, n_rays = 0;
+};
+
+void build_batch(const std::vector<int32_t>& slots, const std::vector<int32_t>& rays, HostBatch* hb) {
+  int n = (int)slots.size();
+  hb->n = n;
+  std::vector<int32_t> ray_base(n + 1, 0), block_base(n + 1, 0), block_obj;
+  for (int i = 0; i < n; ++i) {
+    ray_base[i + 1] = ray_base[i] + rays[i];
+    int nb = (rays[i] + 255) / 256;
+    block_base[i + 1] = block_base[i] + nb;
+    for (int k = 0; k < nb; ++k) block_obj.push_back(i);
+  }
+  hb->n_rays = ray_base[n];
+  hb->n_blocks = block_base[n];
+  hb->arr.clear();
+  hb->arr.insert(hb->arr.end(), slots.begin(), slots.end());
+  hb->arr.insert(hb->arr.end(), ray_base.begin(), ray_base.end());
+  hb->arr.insert(hb->arr.end(), block_base.begin(), block_base.end());
+  hb->arr.insert(hb->arr.end(), block_obj.begin(), block_obj.end());
+}
+
+BatchDesc desc_from(const HostBatch& hb, const int32_t* dev, ObjectDev* objs) {
+  BatchDesc b{};
+  b.n = hb.n;
+  b.n_blocks = hb.n_blocks;
+  b.n_rays = hb.n_rays;
+  b.slot = dev;
+  b.ray_base = dev + hb.n;
+  b.block_base = dev + 2 * hb.n + 1;
+  b.block_obj = dev + 3 * hb.n + 2;
+  b.objs = objs;
+  b.jitter = 1;
+  return b;
+}
+
+romap_status upload_batch(romap_ctx* ctx, const HostBatch& hb, BatchDesc* out) {
+  size_t bytes = sizeof(int32_t) * hb.arr.size();
+  if (ctx->batch_key != hb.arr) {
+    ROMAP_TRY(grow(ctx, ctx->ws_batch, bytes));
+    CUDA_TRY(cudaMemcpyAsync(ctx->ws_batch.p, hb.arr.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->batch_key = hb.arr;
+    ctx->batch_n = hb.n;
+  }
+  *out = desc_from(hb, (const int32_t*)ctx->ws_batch.p, ctx->objs_dev);
+  return ROMAP_OK;
+}
+
+romap_status sync_object(romap_ctx* ctx, int slot) {
+  const Object& o = ctx->objs[slot];
+  ObjectDev& d = ctx->objs_host[slot];
+  d.params = o.params;
+  d.grad = o.grad;
+  d.m = o.m;
+  d.v = o.v;
+  d.table_h = o.table_h;
+  d.pool_o = o.pool_o;
+  d.pool_d = o.pool_d;
+  d.pool_rgb = o.pool_rgb;
+  d.pool_depth = o.pool_depth;
+  d.pool_cls = o.pool_cls;
+  d.pool_n = o.pool_n;
+  d.occ = o.occ;
+  for (int a = 0; a < 3; ++a) {
+    d.half[a] = o.desc.half_size[a];
+    d.inv_ext[a] = 1.0f / (o.desc.half_size[a] - (-o.desc.half_size[a]));
+  }
+  d.key0 = (uint32_t)o.desc.seed;
+  d.key1 = (uint32_t)(o.desc.seed >> 32);
+  int64_t B = o.rays_per_step < o.pool_n ? o.rays_per_step : o.pool_n;
+  d.n_rays = (int32_t)B;
+  d.whole_pool = o.rays_per_step >= o.pool_n ? 1 : 0;
+  d.step = (uint32_t)(o.steps_done + 1);
+  d.pad_ = 0;
+  CUDA_TRY(cudaMemcpyAsync(ctx->objs_dev + slot, &d, sizeof(ObjectDev), cudaMemcpyHostToDevice, ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status check_ctx(romap_ctx* ctx) {
+  if (!ctx) return fail(ROMAP_ERR_INVALID_ARG, "ctx is NULL");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ROMAP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  return ROMAP_OK;
+}
+
+romap_status check_id(romap_ctx* ctx, int32_t id) {
+  if (id < 0 || id >= (int32_t)ctx->objs.size() || !ctx->objs[id].alive)
+    return fail(ROMAP_ERR_NOT_FOUND, "object id %d does not exist", id);
+  return ROMAP_OK;
+}
+
+romap_status make_grid(const romap_config* c, GridParams* g) {
+  if (!c) return fail(ROMAP_ERR_INVALID_ARG, "config is NULL");
+  if (c->n_levels < 1 || c->n_levels > kMaxL) return fail(ROMAP_ERR_INVALID_ARG, "n_levels must be in 1..16");
+  if (c->n_features != 2) return fail(ROMAP_ERR_UNSUPPORTED, "n_features must be 2");
+  if (c->log2_table_size < 8 || c->log2_table_size > 24)
+    return fail(ROMAP_ERR_INVALID_ARG, "log2_table_size must be in 8..24");
+  if (c->base_resolution < 1) return fail(ROMAP_ERR_INVALID_ARG, "base_resolution must be >= 1");
+  if (!(c->growth > 0.0) && (c->max_resolution < c->base_resolution || c->n_levels < 2) && c->n_levels > 1)
+    return fail(ROMAP_ERR_INVALID_ARG, "growth <= 0 needs max_resolution >= base_resolution");
+  if (c->hidden != kH) return fail(ROMAP_ERR_UNSUPPORTED, "hidden must be 64");
+  if (c->dir_dims != 0 && c->dir_dims != 3) return fail(ROMAP_ERR_INVALID_ARG, "dir_dims must be 0 or 3");
+  if (c->n_samples < 1 || c->n_samples > 1024) return fail(ROMAP_ERR_INVALID_ARG, "n_samples must be in 1..1024");
+  if (c->rays_per_step < 1) return fail(ROMAP_ERR_INVALID_ARG, "rays_per_step must be >= 1");
+  if (!(c->lambda1 >= 0.f) || !(c->lambda2 >= 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "loss weights must be >= 0");
+  if (!(c->lr > 0.f) || !(c->beta1 >= 0.f && c->beta1 < 1.f) || !(c->beta2 >= 0.f && c->beta2 < 1.f) ||
+      !(c->eps >= 0.f))
+    return fail(ROMAP_ERR_INVALID_ARG, "invalid Adam hyperparameters");
+  if (c->precision != ROMAP_PREC_FP32 && c->precision != ROMAP_PREC_MIXED_BF16)
+    return fail(ROMAP_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+  if (c->max_objects < 1 || c->max_objects > 1024) return fail(ROMAP_ERR_INVALID_ARG, "max_objects must be in 1..1024");
+  if (c->max_rays_per_object < 1 || c->max_rays_per_object > (int64_t)1 << 31)
+    return fail(ROMAP_ERR_INVALID_ARG, "max_rays_per_object must be in 1..2^31");
+  if ((c->alloc == nullptr) != (c->dealloc == nullptr))
+    return fail(ROMAP_ERR_INVALID_ARG, "alloc and dealloc must be given together");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(c->bg_const[k])) return fail(ROMAP_ERR_INVALID_ARG, "bg_const must be finite");
+  GridParams G{};
+  G.L = c->n_levels;
+  G.F = 2;
+  G.LF = 2 * G.L;
+  G.T = 1u << c->log2_table_size;
+  double b = c->growth;
+  if (!(b > 0.0)) b = G.L > 1 ? std::exp((std::log((double)c->max_resolution) - std::log((double)c->base_resolution)) /
+                                         (double)(G.L - 1))
+                              : 1.0;
+  uint64_t off = 0;
+  for (int l = 0; l < G.L; ++l) {
+    double r = std::floor((double)c->base_resolution * std::pow(b, (double)l) + 1e-6);
+    if (r < 1.0 || r > (double)(1 << 20)) return fail(ROMAP_ERR_INVALID_ARG, "level %d resolution out of range", l);
+    G.res[l] = (int)r;
+    uint64_t n1 = (uint64_t)G.res[l] + 1;
+    uint64_t dense = n1 * n1 * n1;
+    G.dense[l] = dense <= (uint64_t)G.T ? 1 : 0;
+    G.off[l] = (uint32_t)off;
+    off += G.dense[l] ? dense : (uint64_t)G.T;
+    if (off >= ((uint64_t)1 << 31)) return fail(ROMAP_ERR_INVALID_ARG, "hash table too large");
+  }
+  G.n_hash = (int64_t)off * 2;
+  G.dir_dims = c->dir_dims;
+  G.cin = kGeo + c->dir_dims;
+  G.mlp_off[0] = G.n_hash;
+  G.mlp_off[1] = G.mlp_off[0] + (int64_t)kH * G.LF;
+  G.mlp_off[2] = G.mlp_off[1] + (int64_t)kDOut * kH;
+  G.mlp_off[3] = G.mlp_off[2] + (int64_t)kH * G.cin;
+  G.mlp_off[4] = G.mlp_off[3] + (int64_t)kH * kH;
+  G.n_params = G.mlp_off[4] + 3 * kH;
+  G.n_params_pad = (G.n_params + 3) / 4 * 4;
+  G.n_samples = c->n_samples;
+  G.lambda1 = c->lambda1;
+  G.lambda2 = c->lambda2;
+  G.lr = c->lr;
+  G.beta1 = c->beta1;
+  G.beta2 = c->beta2;
+  G.eps = c->eps;
+  G.bg_random = c->bg_random ? 1 : 0;
+  for (int k = 0; k < 3; ++k) G.bg_const[k] = c->bg_const[k];
+  *g = G;
+  return ROMAP_OK;
+}
+
+void free_object(romap_ctx* ctx, Object& o) {
+  dev_free(ctx, o.params);
+  dev_free(ctx, o.grad);
+  dev_free(ctx, o.m);
+  dev_free(ctx, o.v);
+  dev_free(ctx, o.table_h);
+  dev_free(ctx, o.pool_o);
+  dev_free(ctx, o.pool_d);
+  dev_free(ctx, o.pool_rgb);
+  dev_free(ctx, o.pool_depth);
+  dev_free(ctx, o.pool_cls);
+  dev_free(ctx, o.occ);
+  o = Object{};
+}
+
+// Runs the sampling stage for a batch: ray setup, scan, sample write.
+romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBuf S, uint32_t* block_sums,
+                          BatchDyn* dyn, int32_t* totals, bool count_live) {
+  launch_ray_setup(ctx->g, b, R, block_sums, ctx->stream);
+  launch_scan(ctx->g, b, block_sums, dyn, totals, S, count_live ? ctx->live_counter : nullptr, ctx->stream);
+  launch_write_samples(ctx->g, b, R, block_sums, dyn, S, ctx->stream);
+  ctx->launches += 3;
+  CUDA_TRY(cudaGetLastError());
+  return ROMAP_OK;
+}
+
+int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
+
+// forward + loss + backward of a batch (no Adam)
+romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchDesc* out_b) {
+  std::vector<int32_t> slots(ids.begin(), ids.end()), rays(ids.size());
+  for (size_t i = 0; i < ids.size(); ++i) {
+    rays[i] = ctx->objs_host[ids[i]].n_rays;
+    if (rays[i] < 1) return fail(ROMAP_ERR_BAD_STATE, "object %d has no training rays", ids[i]);
+  }
+  HostBatch hb;
+  build_batch(slots, rays, &hb);
+  int64_t ns = (int64_t)hb.n_rays * ctx->g.n_samples + (int64_t)hb.n * kTile;
+  ROMAP_TRY(ensure_workspace(ctx, hb.n_rays, ns, hb.n_blocks, hb.n));
+  BatchDesc b;
+  ROMAP_TRY(upload_batch(ctx, hb, &b));
+  ROMAP_TRY(run_sampling(ctx, b, ctx->R, ctx->S, ctx->block_sums, ctx->dyn, ctx->totals, true));
+  launch_tile_mlp(0, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+  launch_composite(1, ctx->g, b, ctx->R, ctx->S, ctx->dyn, ctx->status, ctx->stream);
+  launch_tile_mlp(1, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+  ctx->launches += 3;
+  CUDA_TRY(cudaGetLastError());
+  ctx->stats.steps += hb.n;
+  ctx->stats.rays += hb.n_rays;
+  *out_b = b;
+  return ROMAP_OK;
+}
+
+romap_status validate_ids(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, std::vector<int32_t>* out) {
+  if (!ids || n_ids < 1) return fail(ROMAP_ERR_INVALID_ARG, "ids must be a non-empty array");
+  if (n_ids > ctx->cfg.max_objects) return fail(ROMAP_ERR_CAPACITY, "more ids than max_objects");
+  std::vector<char> seen(ctx->objs.size(), 0);
+  out->clear();
+  for (int i = 0; i < n_ids; ++i) {
+    ROMAP_TRY(check_id(ctx, ids[i]));
+    if (seen[ids[i]]) return fail(ROMAP_ERR_INVALID_ARG, "object id %d listed twice", ids[i]);
+    seen[ids[i]] = 1;
+    out->push_back(ids[i]);
+  }
+  return ROMAP_OK;
+}
+
+romap_status read_losses(romap_ctx* ctx, int n, float* out_loss, int per_obj, const std::vector<int32_t>& ids) {
+  CUDA_TRY(cudaMemcpyAsync(ctx->dyn_host, ctx->dyn, sizeof(BatchDyn) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  int32_t st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  bool bad = st != 0;
+  for (int i = 0; i < n; ++i) {
+    float B = (float)ctx->objs_host[ids[i]].n_rays;
+    float inv = B > 0 ? 1.0f / B : 0.0f;
+    for (int k = 0; k < per_obj; ++k) {
+      float v = ctx->dyn_host[i].loss[k] * inv;
+      out_loss[per_obj * i + k] = v;
+      if (!std::isfinite(v)) bad = true;
+    }
+  }
+  if (bad) {
+    CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
+    return fail(ROMAP_ERR_NONFINITE, "non-finite loss");
+  }
+  return ROMAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* romap_status_string(romap_status s) {
+  switch (s) {
+    case ROMAP_OK: return "ok";
+    case ROMAP_ERR_INVALID_ARG: return "invalid argument";
+    case ROMAP_ERR_NOT_FOUND: return "object not found";
+    case ROMAP_ERR_OOM: return "out of memory";
+    case ROMAP_ERR_CAPACITY: return "capacity exceeded";
+    case ROMAP_ERR_CUDA: return "CUDA error";
+    case ROMAP_ERR_NONFINITE: return "non-finite value";
+    case ROMAP_ERR_TIMEOUT: return "device wait timed out";
+    case ROMAP_ERR_BAD_STATE: return "bad state";
+    case ROMAP_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+romap_status romap_last_error(char* buf, size_t n) {
+  if (!buf || n == 0) return ROMAP_ERR_INVALID_ARG;
+  snprintf(buf, n, "%s", g_last_error.c_str());
+  return ROMAP_OK;
+}
+
+romap_status romap_param_layout(const romap_config* cfg, romap_layout* out) {
+  if (!out) return fail(ROMAP_ERR_INVALID_ARG, "out is NULL");
+  GridParams g;
+  ROMAP_TRY(make_grid(cfg, &g));
+  memset(out, 0, sizeof(*out));
+  out->n_params = g.n_params;
+  out->n_hash_params = g.n_hash;
+  out->n_levels = g.L;
+  for (int l = 0; l < g.L; ++l) {
+    out->resolution[l] = g.res[l];
+    out->dense[l] = g.dense[l];
+    out->level_offset[l] = g.off[l];
+  }
+  int rows[5] = {kH, kDOut, kH, kH, 3}, cols[5] = {g.LF, kH, g.cin, kH, kH};
+  for (int i = 0; i < 5; ++i) {
+    out->mlp_offset[i] = g.mlp_off[i];
+    out->mlp_rows[i] = rows[i];
+    out->mlp_cols[i] = cols[i];
+  }
+  return ROMAP_OK;
+}
+
+romap_status romap_init(const romap_config* cfg, void* cuda_stream, romap_ctx** out) {
+  if (!out) return fail(ROMAP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  GridParams g;
+  ROMAP_TRY(make_grid(cfg, &g));
+  if (cfg->precision == ROMAP_PREC_MIXED_BF16) return fail(ROMAP_ERR_UNSUPPORTED, "mixed precision is not built");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+  romap_ctx* ctx = new romap_ctx();
+  ctx->cfg = *cfg;
+  ctx->g = g;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->device = dev;
+  ctx->n_sms = prop.multiProcessorCount;
+  ctx->objs.resize(cfg->max_objects);
+  ctx->objs_host.resize(cfg->max_objects);
+  memset(ctx->objs_host.data(), 0, sizeof(ObjectDev) * ctx->objs_host.size());
+  romap_status s = dev_alloc_t(ctx, cfg->max_objects, &ctx->objs_dev);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, 1, &ctx->fn_obj_dev);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, 4, &ctx->totals);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, 1, &ctx->status);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, 1, &ctx->live_counter);
+  if (s == ROMAP_OK) {
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->live_counter, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->objs_dev, 0, sizeof(ObjectDev) * cfg->max_objects, ctx->stream);
+    if (e != cudaSuccess) s = fail(ROMAP_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  if (s == ROMAP_OK) s = ensure_workspace(ctx, 1024, 1024 * 8, 8, 8);
+  if (s != ROMAP_OK) {
+    romap_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return ROMAP_OK;
+}
+
+romap_status romap_destroy(romap_ctx* ctx) {
+  if (!ctx) return fail(ROMAP_ERR_INVALID_ARG, "ctx is NULL");
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& o : ctx->objs)
+    if (o.alive) free_object(ctx, o);
+  dev_free(ctx, ctx->objs_dev);
+  dev_free(ctx, ctx->fn_obj_dev);
+  dev_free(ctx, ctx->totals);
+  dev_free(ctx, ctx->status);
+  dev_free(ctx, ctx->live_counter);
+  for (DevBuf* b : {&ctx->ws_rays, &ctx->ws_samples, &ctx->ws_blocks, &ctx->ws_batch, &ctx->ws_dyn, &ctx->ws_stage})
+    dev_free(ctx, b->p);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->dyn_host) cudaFreeHost(ctx->dyn_host);
+  delete ctx;
+  return ROMAP_OK;
+}
+
+romap_status romap_create_object(romap_ctx* ctx, const romap_object_desc* d, int32_t* out_id) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (!d || !out_id) return fail(ROMAP_ERR_INVALID_ARG, "desc and out_id must not be NULL");
+  for (int a = 0; a < 3; ++a) {
+    if (!(d->half_size[a] > 0.f) || !std::isfinite(d->half_size[a]))
+      return fail(ROMAP_ERR_INVALID_ARG, "half_size must be positive and finite");
+    if (!std::isfinite(d->t[a])) return fail(ROMAP_ERR_INVALID_ARG, "t must be finite");
+  }
+  if (!std::isfinite(d->yaw)) return fail(ROMAP_ERR_INVALID_ARG, "yaw must be finite");
+  if (d->rays_per_step < 0) return fail(ROMAP_ERR_INVALID_ARG, "rays_per_step must be >= 0");
+  int slot = -1;
+  for (int i = 0; i < (int)ctx->objs.size(); ++i)
+    if (!ctx->objs[i].alive) { slot = i; break; }
+  if (slot < 0) return fail(ROMAP_ERR_CAPACITY, "all %d object slots are in use", ctx->cfg.max_objects);
+  Object o;
+  o.desc = *d;
+  o.rays_per_step = d->rays_per_step > 0 ? d->rays_per_step : ctx->cfg.rays_per_step;
+  size_t np = (size_t)ctx->g.n_params_pad;
+  romap_status s = dev_alloc_t(ctx, np, &o.params);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, np, &o.grad);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, np, &o.m);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, np, &o.v);
+  if (s == ROMAP_OK && ctx->cfg.precision == ROMAP_PREC_MIXED_BF16)
+    s = dev_alloc_t(ctx, (size_t)ctx->g.n_hash + 8, &o.table_h);
+  if (s != ROMAP_OK) {
+    o.alive = true;
+    free_object(ctx, o);
+    return s;
+  }
+  cudaMemsetAsync(o.grad, 0, np * sizeof(float), ctx->stream);
+  cudaMemsetAsync(o.m, 0, np * sizeof(float), ctx->stream);
+  cudaMemsetAsync(o.v, 0, np * sizeof(float), ctx->stream);
+  launch_init_params(ctx->g, o.params, (uint32_t)d->seed, (uint32_t)(d->seed >> 32), ctx->stream);
+  ctx->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  o.alive = true;
+  ctx->objs[slot] = o;
+  ROMAP_TRY(sync_object(ctx, slot));
+  *out_id = slot;
+  return ROMAP_OK;
+}
+
+romap_status romap_destroy_object(romap_ctx* ctx, int32_t id) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  free_object(ctx, ctx->objs[id]);
+  memset(&ctx->objs_host[id], 0, sizeof(ObjectDev));
+  CUDA_TRY(cudaMemsetAsync(ctx->objs_dev + id, 0, sizeof(ObjectDev), ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status romap_set_occupancy(romap_ctx* ctx, int32_t id, const uint64_t* bits, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  Object& o = ctx->objs[id];
+  if (!bits) {
+    dev_free(ctx, o.occ);
+    o.occ = nullptr;
+    return sync_object(ctx, id);
+  }
+  if (!o.occ) ROMAP_TRY(dev_alloc_t(ctx, 4096, &o.occ));
+  CUDA_TRY(cudaMemcpyAsync(o.occ, bits, 4096 * sizeof(uint64_t),
+                           (flags & ROMAP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           ctx->stream));
+  return sync_object(ctx, id);
+}
+
+romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* r, int64_t n, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!r || n < 0) return fail(ROMAP_ERR_INVALID_ARG, "rays must not be NULL and n >= 0");
+  if (n > 0 && (!r->origin || !r->dir || !r->rgb)) return fail(ROMAP_ERR_INVALID_ARG, "origin, dir and rgb are required");
+  if (flags & ~(ROMAP_DEVICE_PTR | ROMAP_OBJECT_FRAME | ROMAP_REPLACE)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  Object& o = ctx->objs[id];
+  bool dev = (flags & ROMAP_DEVICE_PTR) != 0;
+  int64_t start = (flags & ROMAP_REPLACE) ? 0 : o.pool_n;
+  int64_t need = start + n;
+  if (need > ctx->cfg.max_rays_per_object)
+    return fail(ROMAP_ERR_CAPACITY, "pool of object %d would hold %lld rays (max %lld)", id, (long long)need,
+                (long long)ctx->cfg.max_rays_per_object);
+  if (!dev) {  // host inputs: every value must be finite (depth may be NaN = none)
+    for (int64_t i = 0; i < 3 * n; ++i)
+      if (!std::isfinite(r->origin[i]) || !std::isfinite(r->dir[i]) || !std::isfinite(r->rgb[i]))
+        return fail(ROMAP_ERR_NONFINITE, "non-finite origin, dir or rgb at ray %lld", (long long)(i / 3));
+    for (int64_t i = 0; i < n; ++i) {
+      if (r->depth && std::isinf(r->depth[i])) return fail(ROMAP_ERR_NONFINITE, "infinite depth at ray %lld", (long long)i);
+      if (r->cls && r->cls[i] > 2) return fail(ROMAP_ERR_INVALID_ARG, "class %d at ray %lld", r->cls[i], (long long)i);
+      float dd = r->dir[3 * i] * r->dir[3 * i] + r->dir[3 * i + 1] * r->dir[3 * i + 1] + r->dir[3 * i + 2] * r->dir[3 * i + 2];
+      if (!(dd > 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "zero direction at ray %lld", (long long)i);
+    }
+  }
+  if (n == 0) {
+    if (flags & ROMAP_REPLACE) {
+      o.pool_n = 0;
+      return sync_object(ctx, id);
+    }
+    return ROMAP_OK;
+  }
+  if (need > o.pool_cap) {  // grow the pool
+    int64_t cap = need > 2 * o.pool_cap ? need : 2 * o.pool_cap;
+    if (cap > ctx->cfg.max_rays_per_object) cap = ctx->cfg.max_rays_per_object;
+    float *po, *pd, *prgb, *pdep;
+    uint8_t* pcls;
+    ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &po));
+    ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &pd));
+    ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &prgb));
+    ROMAP_TRY(dev_alloc_t(ctx, cap, &pdep));
+    ROMAP_TRY(dev_alloc_t(ctx, cap, &pcls));
+    if (start > 0) {
+      CUDA_TRY(cudaMemcpyAsync(po, o.pool_o, 12 * start, cudaMemcpyDeviceToDevice, ctx->stream));
+      CUDA_TRY(cudaMemcpyAsync(pd, o.pool_d, 12 * start, cudaMemcpyDeviceToDevice, ctx->stream));
+      CUDA_TRY(cudaMemcpyAsync(prgb, o.pool_rgb, 12 * start, cudaMemcpyDeviceToDevice, ctx->stream));
+      CUDA_TRY(cudaMemcpyAsync(pdep, o.pool_depth, 4 * start, cudaMemcpyDeviceToDevice, ctx->stream));
+      CUDA_TRY(cudaMemcpyAsync(pcls, o.pool_cls, start, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    dev_free(ctx, o.pool_o); dev_free(ctx, o.pool_d); dev_free(ctx, o.pool_rgb);
+    dev_free(ctx, o.pool_depth); dev_free(ctx, o.pool_cls);
+    o.pool_o = po; o.pool_d = pd; o.pool_rgb = prgb; o.pool_depth = pdep; o.pool_cls = pcls;
+    o.pool_cap = cap;
+  }
+  const float *so = r->origin, *sd = r->dir, *srgb = r->rgb, *sdep = r->depth;
+  const uint8_t* scls = r->cls;
+  bool pinned = false;
+  if (!dev) {  // stage host arrays on the device
+    size_t b3 = align_up(12 * (size_t)n, 256), b1 = align_up(4 * (size_t)n, 256), bc = align_up((size_t)n, 256);
+    ROMAP_TRY(grow(ctx, ctx->ws_stage, 3 * b3 + b1 + bc));
+    char* st = (char*)ctx->ws_stage.p;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, r->origin) == cudaSuccess && attr.type == cudaMemoryTypeHost) pinned = true;
+    cudaGetLastError();
+    CUDA_TRY(cudaMemcpyAsync(st, r->origin, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(st + b3, r->dir, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(st + 2 * b3, r->rgb, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+    so = (const float*)st;
+    sd = (const float*)(st + b3);
+    srgb = (const float*)(st + 2 * b3);
+    if (r->depth) {
+      CUDA_TRY(cudaMemcpyAsync(st + 3 * b3, r->depth, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+      sdep = (const float*)(st + 3 * b3);
+    }
+    if (r->cls) {
+      CUDA_TRY(cudaMemcpyAsync(st + 3 * b3 + b1, r->cls, n, cudaMemcpyHostToDevice, ctx->stream));
+      scls = (const uint8_t*)(st + 3 * b3 + b1);
+    }
+  }
+  float cz = (float)std::cos(o.desc.yaw), sz = (float)std::sin(o.desc.yaw);
+  launch_transform_rays(so, sd, srgb, sdep, scls, n, (flags & ROMAP_OBJECT_FRAME) ? 1 : 0, o.desc.t[0], o.desc.t[1],
+                        o.desc.t[2], cz, sz, o.pool_o + 3 * start, o.pool_d + 3 * start, o.pool_rgb + 3 * start,
+                        o.pool_depth + start, o.pool_cls + start, ctx->stream);
+  ctx->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  if (pinned) CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // pinned host buffers are read asynchronously
+  o.pool_n = need;
+  return sync_object(ctx, id);
+}
+
+romap_status romap_pool_size(romap_ctx* ctx, int32_t id, int64_t* out_n) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!out_n) return fail(ROMAP_ERR_INVALID_ARG, "out_n is NULL");
+  *out_n = ctx->objs[id].pool_n;
+  return ROMAP_OK;
+}
+
+romap_status romap_forward_backward(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, float* out_loss) {
+  ROMAP_TRY(check_ctx(ctx));
+  std::vector<int32_t> v;
+  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+  BatchDesc b;
+  ROMAP_TRY(run_fwd_bwd(ctx, v, &b));
+  if (out_loss) ROMAP_TRY(read_losses(ctx, n_ids, out_loss, 5, v));
+  return ROMAP_OK;
+}
+
+romap_status romap_adam_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids) {
+  ROMAP_TRY(check_ctx(ctx));
+  std::vector<int32_t> v;
+  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+  std::vector<int32_t> rays(v.size(), 0);
+  HostBatch hb;
+  build_batch(v, rays, &hb);
+  BatchDesc b;
+  ROMAP_TRY(upload_batch(ctx, hb, &b));
+  launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+  ctx->launches += 2;
+  CUDA_TRY(cudaGetLastError());
+  for (int32_t id : v) {
+    ctx->objs[id].steps_done += 1;
+    ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
+  }
+  return ROMAP_OK;
+}
+
+romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps, float* out_loss) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (n_steps < 1) return fail(ROMAP_ERR_INVALID_ARG, "n_steps must be >= 1");
+  std::vector<int32_t> v;
+  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+  for (int s = 0; s < n_steps; ++s) {
+    BatchDesc b;
+    ROMAP_TRY(run_fwd_bwd(ctx, v, &b));
+    launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+    ctx->launches += 2;
+    CUDA_TRY(cudaGetLastError());
+    for (int32_t id : v) {
+      ctx->objs[id].steps_done += 1;
+      ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
+    }
+  }
+  if (out_loss) {
+    std::vector<float> tmp(5 * (size_t)n_ids);
+    ROMAP_TRY(read_losses(ctx, n_ids, tmp.data(), 5, v));
+    for (int i = 0; i < n_ids; ++i) out_loss[i] = tmp[5 * i];
+  }
+  return ROMAP_OK;
+}
+
+romap_status romap_get_grad(romap_ctx* ctx, int32_t id, float* out, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!out) return fail(ROMAP_ERR_INVALID_ARG, "out is NULL");
+  bool dev = flags & ROMAP_DEVICE_PTR;
+  CUDA_TRY(cudaMemcpyAsync(out, ctx->objs[id].grad, sizeof(float) * ctx->g.n_params,
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dev) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status romap_last_batch(romap_ctx* ctx, int32_t id, int64_t* pool_idx, float* bg, int64_t* out_n) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  const std::vector<int32_t>& k = ctx->batch_key;
+  if (k.empty()) return fail(ROMAP_ERR_BAD_STATE, "no step has run");
+  const int n = ctx->batch_n;
+  int pos = -1;
+  for (int i = 0; i < n; ++i)
+    if (k[i] == id) pos = i;
+  if (pos < 0) return fail(ROMAP_ERR_BAD_STATE, "object %d was not in the last step", id);
+  int64_t r0 = k[n + pos], r1 = k[n + pos + 1];
+  if (out_n) *out_n = r1 - r0;
+  if (pool_idx)
+    CUDA_TRY(cudaMemcpyAsync(pool_idx, ctx->R.pool_idx + r0, sizeof(int64_t) * (r1 - r0), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  if (bg) CUDA_TRY(cudaMemcpyAsync(bg, ctx->R.bg + 3 * r0, sizeof(float) * 3 * (r1 - r0), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status romap_get_state(romap_ctx* ctx, int32_t id, romap_state* out) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!out || !out->params || !out->adam_m || !out->adam_v)
+    return fail(ROMAP_ERR_INVALID_ARG, "state buffers must not be NULL");
+  if (out->n_params != ctx->g.n_params)
+    return fail(ROMAP_ERR_INVALID_ARG, "n_params is %lld, expected %lld", (long long)out->n_params,
+                (long long)ctx->g.n_params);
+  const Object& o = ctx->objs[id];
+  cudaMemcpyKind k = (out->flags & ROMAP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  size_t bytes = sizeof(float) * ctx->g.n_params;
+  CUDA_TRY(cudaMemcpyAsync(out->params, o.params, bytes, k, ctx->stream));
+  CUDA_TRY(cudaMemcpyAsync(out->adam_m, o.m, bytes, k, ctx->stream));
+  CUDA_TRY(cudaMemcpyAsync(out->adam_v, o.v, bytes, k, ctx->stream));
+  out->step = o.steps_done;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status romap_set_state(romap_ctx* ctx, int32_t id, const romap_state* in) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!in || !in->params || !in->adam_m || !in->adam_v)
+    return fail(ROMAP_ERR_INVALID_ARG, "state buffers must not be NULL");
+  if (in->n_params != ctx->g.n_params) return fail(ROMAP_ERR_INVALID_ARG, "n_params mismatch");
+  if (in->step < 0 || in->step > 0x7fffffff) return fail(ROMAP_ERR_INVALID_ARG, "step out of range");
+  Object& o = ctx->objs[id];
+  cudaMemcpyKind k = (in->flags & ROMAP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  size_t bytes = sizeof(float) * ctx->g.n_params;
+  CUDA_TRY(cudaMemcpyAsync(o.params, in->params, bytes, k, ctx->stream));
+  CUDA_TRY(cudaMemcpyAsync(o.m, in->adam_m, bytes, k, ctx->stream));
+  CUDA_TRY(cudaMemcpyAsync(o.v, in->adam_v, bytes, k, ctx->stream));
+  CUDA_TRY(cudaMemsetAsync(o.grad, 0, sizeof(float) * ctx->g.n_params_pad, ctx->stream));
+  o.steps_done = in->step;
+  ROMAP_TRY(sync_object(ctx, id));
+  if (!(in->flags & ROMAP_DEVICE_PTR)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (!out) return fail(ROMAP_ERR_INVALID_ARG, "out is NULL");
+  unsigned long long live = 0;
+  CUDA_TRY(cudaMemcpyAsync(&live, ctx->live_counter, sizeof(live), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  *out = ctx->stats;
+  out->live_samples = (int64_t)live;
+  out->kernel_launches = ctx->launches;
+  return ROMAP_OK;
+}
+
+romap_status romap_reset_stats(romap_ctx* ctx) {
+  ROMAP_TRY(check_ctx(ctx));
+  ctx->stats = romap_stats{};
+  ctx->launches = 0;
+  CUDA_TRY(cudaMemsetAsync(ctx->live_counter, 0, sizeof(unsigned long long), ctx->stream));
+  return ROMAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Functional API and rendering: one object record (params given), explicit
+// rays, workspace carved from a caller buffer or the context.
+// ---------------------------------------------------------------------------
+struct FnLayout {
+  size_t rays, samples, blocks, batch, dyn, totals, total;
+  int64_t nr, ns, nb;
+};
+
+static FnLayout fn_layout(const GridParams& g, int64_t n) {
+  FnLayout L{};
+  L.nr = n;
+  L.ns = n * g.n_samples + kTile;
+  L.nb = (n + 255) / 256;
+  RayBuf R;
+  SampleBuf S;
+  L.rays = carve_rays(nullptr, n, &R);
+  L.samples = carve_samples(nullptr, L.ns, &S);
+  L.blocks = align_up(sizeof(uint32_t) * (L.nb + 1), 256);
+  L.batch = align_up(sizeof(int32_t) * (4 + L.nb + 8), 256);
+  L.dyn = align_up(sizeof(BatchDyn), 256);
+  L.totals = 256;
+  L.total = L.rays + L.samples + L.blocks + L.batch + L.dyn + L.totals + 256;
+  return L;
+}
+
+struct FnView {
+  RayBuf R;
+  SampleBuf S;
+  uint32_t* blocks;
+  int32_t* batch;
+  BatchDyn* dyn;
+  int32_t* totals;
+};
+
+static FnView fn_view(char* base, const FnLayout& L) {
+  FnView v;
+  base = (char*)align_up((size_t)base, 256);
+  size_t o = 0;
+  carve_rays(base + o, L.nr, &v.R); o += L.rays;
+  carve_samples(base + o, L.ns, &v.S); o += L.samples;
+  v.blocks = (uint32_t*)(base + o); o += L.blocks;
+  v.batch = (int32_t*)(base + o); o += L.batch;
+  v.dyn = (BatchDyn*)(base + o); o += L.dyn;
+  v.totals = (int32_t*)(base + o);
+  return v;
+}
+
+static romap_status fn_setup(romap_ctx* ctx, const float* params, float* grad, const float half[3], uint64_t seed,
+                             uint32_t step, const uint64_t* occ, const float* origin, const float* dir,
+                             const float* bg, int64_t n, uint32_t flags, char* ws, size_t ws_bytes, FnView* out_v,
+                             BatchDesc* out_b, bool upload) {
+  if (!params || !half || !origin || !dir || !bg || !ws) return fail(ROMAP_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || n > (int64_t)1 << 24) return fail(ROMAP_ERR_INVALID_ARG, "n must be in 1..2^24");
+  if (flags & ~(ROMAP_JITTER)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  for (int a = 0; a < 3; ++a)
+    if (!(half[a] > 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "half_size must be positive");
+  FnLayout L = fn_layout(ctx->g, n);
+  if (ws_bytes < L.total) return fail(ROMAP_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes, L.total);
+  FnView v = fn_view(ws, L);
+  HostBatch hb;
+  build_batch(std::vector<int32_t>{0}, std::vector<int32_t>{(int32_t)n}, &hb);
+  if (upload)
+    CUDA_TRY(cudaMemcpyAsync(v.batch, hb.arr.data(), sizeof(int32_t) * hb.arr.size(), cudaMemcpyHostToDevice,
+                             ctx->stream));
+  ObjectDev d{};
+  d.params = const_cast<float*>(params);
+  d.grad = grad;
+  d.occ = occ;
+  for (int a = 0; a < 3; ++a) {
+    d.half[a] = half[a];
+    d.inv_ext[a] = 1.0f / (half[a] - (-half[a]));
+  }
+  d.key0 = (uint32_t)seed;
+  d.key1 = (uint32_t)(seed >> 32);
+  d.n_rays = (int32_t)n;
+  d.step = step;
+  ObjectDev* od = ctx->fn_obj_dev;
+  CUDA_TRY(cudaMemcpyAsync(od, &d, sizeof(d), cudaMemcpyHostToDevice, ctx->stream));
+  BatchDesc b = desc_from(hb, v.batch, od);
+  b.explicit_rays = 1;
+  b.explicit_step = step;
+  b.jitter = (flags & ROMAP_JITTER) ? 1 : 0;
+  b.ex_o = origin;
+  b.ex_d = dir;
+  b.ex_bg = bg;
+  *out_v = v;
+  *out_b = b;
+  return ROMAP_OK;
+}
+
+romap_status romap_fn_workspace_size(romap_ctx* ctx, int64_t n, size_t* bytes) {
+  if (!ctx || !bytes) return fail(ROMAP_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(ROMAP_ERR_INVALID_ARG, "n must be >= 1");
+  *bytes = fn_layout(ctx->g, n).total;
+  return ROMAP_OK;
+}
+
+romap_status romap_fn_forward(romap_ctx* ctx, const float* params, const float half_size[3], uint64_t seed,
+                              uint32_t step, const uint64_t* occupancy, const float* origin, const float* dir,
+                              const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
+                              float* out_ray, float* out_samples) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (!out_ray) return fail(ROMAP_ERR_INVALID_ARG, "out_ray is NULL");
+  FnView v;
+  BatchDesc b;
+  ROMAP_TRY(fn_setup(ctx, params, nullptr, half_size, seed, step, occupancy, origin, dir, bg, n, flags,
+                     (char*)workspace, ws_bytes, &v, &b, true));
+  ROMAP_TRY(run_sampling(ctx, b, v.R, v.S, v.blocks, v.dyn, v.totals, false));
+  launch_tile_mlp(0, ctx->g, b, v.dyn, v.totals, v.R, v.S, tile_ctas(ctx), ctx->stream);
+  launch_composite(0, ctx->g, b, v.R, v.S, v.dyn, nullptr, ctx->stream);
+  ctx->launches += 2;
+  CUDA_TRY(cudaMemcpyAsync(out_ray, v.R.out, sizeof(float) * 6 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (out_samples) {  // per slot: t, delta, x, y, z, sigma (zeros for missed or culled slots)
+    CUDA_TRY(cudaMemsetAsync(out_samples, 0, sizeof(float) * 6 * n * ctx->g.n_samples, ctx->stream));
+    launch_sample_slots(ctx->g, n, v.R, v.S, out_samples, ctx->stream);
+    ctx->launches += 1;
+  }
+  CUDA_TRY(cudaGetLastError());
+  return ROMAP_OK;
+}
+
+romap_status romap_fn_backward(romap_ctx* ctx, const float* params, const float half_size[3], uint64_t seed,
+                               uint32_t step, const uint64_t* occupancy, const float* origin, const float* dir,
+                               const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
+                               const float* grad_ray, float* grad_params, float* out_dsigma) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (!grad_ray || !grad_params) return fail(ROMAP_ERR_INVALID_ARG, "grad_ray and grad_params are required");
+  FnView v;
+  BatchDesc b;
+  ROMAP_TRY(fn_setup(ctx, params, grad_params, half_size, seed, step, occupancy, origin, dir, bg, n, flags,
+                     (char*)workspace, ws_bytes, &v, &b, false));
+  v.R.gout = grad_ray;
+  launch_composite(2, ctx->g, b, v.R, v.S, v.dyn, nullptr, ctx->stream);
+  launch_tile_mlp(1, ctx->g, b, v.dyn, v.totals, v.R, v.S, tile_ctas(ctx), ctx->stream);
+  ctx->launches += 2;
+  if (out_dsigma) {
+    CUDA_TRY(cudaMemsetAsync(out_dsigma, 0, sizeof(float) * n * ctx->g.n_samples, ctx->stream));
+    launch_scatter_slots(ctx->g, n, v.R, v.S, v.S.dsigma, 1, out_dsigma, 1, ctx->stream);
+    ctx->launches += 1;
+  }
+  CUDA_TRY(cudaGetLastError());
+  return ROMAP_OK;
+}
+
+romap_status romap_render(romap_ctx* ctx, int32_t id, const float* origin, const float* dir, int64_t n,
+                          const float bg[3], float* out_rgb, float* out_depth, float* out_opacity, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!origin || !dir || !bg || n < 1) return fail(ROMAP_ERR_INVALID_ARG, "origin, dir, bg required and n >= 1");
+  if (flags & ~(ROMAP_DEVICE_PTR | ROMAP_OBJECT_FRAME)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  bool dev = flags & ROMAP_DEVICE_PTR;
+  Object& o = ctx->objs[id];
+  FnLayout L = fn_layout(ctx->g, n);
+  size_t extra = align_up(sizeof(float) * 9 * n, 256) + align_up(sizeof(float) * 6 * (size_t)n, 256) +
+                 align_up(sizeof(float) * 6 * (size_t)n, 256) + 1024;
+  ROMAP_TRY(grow(ctx, ctx->ws_stage, L.total + extra));
+  char* base = (char*)ctx->ws_stage.p;
+  char* xb = base + align_up(L.total, 256);
+  float* o_obj = (float*)xb;
+  float* d_obj = o_obj + 3 * n;
+  float* bgs = d_obj + 3 * n;
+  float* scratch_rgb = (float*)(xb + align_up(sizeof(float) * 9 * n, 256));
+  float* scratch_dep = scratch_rgb + 3 * n;
+  uint8_t* scratch_cls = (uint8_t*)(scratch_dep + n);
+  const float* so = origin;
+  const float* sd = dir;
+  float* st = (float*)(xb + align_up(sizeof(float) * 9 * n, 256) + align_up(sizeof(float) * 6 * (size_t)n, 256));
+  if (!dev) {
+    CUDA_TRY(cudaMemcpyAsync(st, origin, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(st + 3 * n, dir, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+    so = st;
+    sd = st + 3 * n;
+  }
+  std::vector<float> hbg(3 * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    hbg[3 * i] = bg[0]; hbg[3 * i + 1] = bg[1]; hbg[3 * i + 2] = bg[2];
+  }
+  CUDA_TRY(cudaMemcpyAsync(bgs, hbg.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+  float cz = (float)std::cos(o.desc.yaw), sz = (float)std::sin(o.desc.yaw);
+  launch_transform_rays(so, sd, nullptr, nullptr, nullptr, n, (flags & ROMAP_OBJECT_FRAME) ? 1 : 0, o.desc.t[0],
+                        o.desc.t[1], o.desc.t[2], cz, sz, o_obj, d_obj, scratch_rgb, scratch_dep, scratch_cls,
+                        ctx->stream);
+  FnView v;
+  BatchDesc b;
+  ROMAP_TRY(fn_setup(ctx, o.params, nullptr, o.desc.half_size, o.desc.seed, 0, o.occ, o_obj, d_obj, bgs, n, 0, base,
+                     L.total, &v, &b, true));
+  ROMAP_TRY(run_sampling(ctx, b, v.R, v.S, v.blocks, v.dyn, v.totals, false));
+  launch_tile_mlp(0, ctx->g, b, v.dyn, v.totals, v.R, v.S, tile_ctas(ctx), ctx->stream);
+  launch_composite(0, ctx->g, b, v.R, v.S, v.dyn, nullptr, ctx->stream);
+  ctx->launches += 3;
+  CUDA_TRY(cudaGetLastError());
+  float* outs = st;  // staging area is free again: rgb [3n], depth [n], opacity [n]
+  launch_split_outputs(v.R.out, n, outs, outs + 3 * n, outs + 4 * n, ctx->stream);
+  ctx->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (out_rgb) CUDA_TRY(cudaMemcpyAsync(out_rgb, outs, sizeof(float) * 3 * n, k, ctx->stream));
+  if (out_depth) CUDA_TRY(cudaMemcpyAsync(out_depth, outs + 3 * n, sizeof(float) * n, k, ctx->stream));
+  if (out_opacity) CUDA_TRY(cudaMemcpyAsync(out_opacity, outs + 4 * n, sizeof(float) * n, k, ctx->stream));
+  if (!dev) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+}  // extern "C"

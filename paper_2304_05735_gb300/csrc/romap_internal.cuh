@@ -1,0 +1,188 @@
+// Internal declarations shared by the CUDA translation units of libromap.
+//
+// Data layout in HBM (one context):
+//  * per object (slot k of max_objects): parameters, gradient, Adam m and v as
+//    FP32 arrays of n_params_pad floats (hash table first, level-major, entry
+//    x F; then the five MLP layers row-major [out][in]); an FP16 copy of the
+//    hash table for the mixed-precision path; the ray pool as structure of
+//    arrays (object-frame origin and unit direction, target rgb, depth,
+//    class); an optional 64^3 occupancy bitgrid.
+//  * per step (workspace): ray records and compacted sample records, both
+//    structure of arrays; every object's samples start on a 128-sample tile
+//    boundary so that a tile belongs to one object.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace romap {
+
+constexpr int kH = 64;          // MLP hidden width (Sec. VI: hidden size 64)
+constexpr int kGeo = 15;        // geometry features passed from the density to the colour net
+constexpr int kDOut = 16;       // density-net outputs: log-density + 15 geometry features
+constexpr int kMaxL = 16;       // maximum levels
+constexpr int kTile = 128;      // samples per tile of the MLP kernels
+constexpr int kOC = 20;         // rows of the density-output/colour-input buffer (1 + 15 + 3 + pad)
+constexpr int kCinPad = 20;     // colour-net first-layer input width as stored (cin <= 18, zero padded)
+constexpr int kC3Rows = 4;      // colour-net last layer rows as stored (3, zero padded)
+constexpr int kAS = 132;        // row stride (floats) of the per-tile activation buffers in shared memory
+constexpr int kThreads = 256;   // threads of the tile kernel
+constexpr uint32_t kNoRay = 0xffffffffu;
+
+enum : uint32_t { kPurposeRay = 1, kPurposeBg = 2, kPurposeJitter = 3, kPurposeInitHash = 4, kPurposeInitMlp = 5 };
+enum : int { kClsObject = 0, kClsBackground = 1, kClsOccluder = 2 };
+
+// Grid and network shape, passed by value to kernels.
+struct GridParams {
+  int L, F, LF;
+  uint32_t T;
+  int res[kMaxL];
+  uint32_t off[kMaxL];     // first entry of level l
+  int dense[kMaxL];
+  int64_t n_hash;          // hash parameters (entries * F)
+  int64_t mlp_off[5];      // absolute parameter offsets of the MLP layers
+  int64_t n_params;
+  int64_t n_params_pad;    // n_params rounded up to a multiple of 4
+  int dir_dims, cin;       // cin = 15 + dir_dims
+  int n_samples;           // N
+  float lambda1, lambda2;
+  float lr, beta1, beta2, eps;
+  int bg_random;
+  float bg_const[3];
+};
+
+// One live object as the kernels see it (device-resident, indexed by slot).
+struct ObjectDev {
+  float* params;
+  float* grad;
+  float* m;
+  float* v;
+  uint16_t* table_h;       // FP16 copy of the hash table (mixed precision)
+  const float* pool_o;     // [3n] object frame
+  const float* pool_d;     // [3n] unit
+  const float* pool_rgb;   // [3n]
+  const float* pool_depth; // [n]
+  const uint8_t* pool_cls; // [n]
+  int64_t pool_n;
+  const uint64_t* occ;     // 4096 words or null
+  float half[3];
+  float inv_ext[3];        // 1 / (2 half), FP32
+  uint32_t key0, key1;     // Philox key
+  int32_t n_rays;          // rays per step B = min(rays_per_step, pool_n)
+  int32_t whole_pool;      // 1 if the whole pool is used in order
+  uint32_t step;           // Adam step about to run (1-based); advanced by the Adam kernel
+  int32_t pad_;
+};
+
+// Per-batch-object values written on the device during a step.
+struct BatchDyn {
+  int64_t sample_base;     // first sample (tile aligned)
+  int32_t n_samples;       // live samples
+  int32_t tile_base;
+  int32_t n_tiles;
+  int32_t pad_;
+  float loss[5];           // B*L, then rgb, rr, depth, density sums (unscaled)
+  float pad2_[3];
+};
+
+// Batch description (device): object slots and the ray/block prefix sums.
+struct BatchDesc {
+  const int32_t* slot;       // [n] object slot of batch entry i
+  const int32_t* ray_base;   // [n+1]
+  const int32_t* block_base; // [n+1] blocks of 256 rays
+  const int32_t* block_obj;  // [n_blocks] batch entry of each ray block
+  int32_t n;
+  int32_t n_blocks;
+  int32_t n_rays;
+  int32_t explicit_rays;     // functional API: rays given, slot r = ray r, no pool draw
+  uint32_t explicit_step;    // RNG step of the functional API
+  int32_t jitter;            // stratified jitter (training) vs midpoints (render)
+  const float* ex_o;         // explicit rays, object frame [3n]
+  const float* ex_d;
+  const float* ex_bg;        // [3n]
+  ObjectDev* objs;           // device array indexed by slot
+};
+
+// Per-step ray records (structure of arrays, capacity R).
+struct RayBuf {
+  float* o;        // [3R] object frame
+  float* d;        // [3R]
+  float* tn;       // [R]
+  float* tf;       // [R]
+  float* bg;       // [3R]
+  float* rgb;      // [3R] target
+  float* depth;    // [R]
+  uint8_t* cls;    // [R]
+  int64_t* pool_idx; // [R]
+  uint32_t* count; // [R] live samples
+  uint32_t* off;   // [R] local offset in its block, then global sample offset
+  int32_t* obj;    // [R] batch entry
+  float* out;      // [6R] C_hat(3), D_hat, A, sum sigma
+  const float* gout; // [6R] upstream gradient (functional API), or null
+};
+
+// Per-step compacted samples (structure of arrays, capacity S).
+struct SampleBuf {
+  float* x;        // [3S] (x, y, z interleaved)
+  float* t;        // [S]
+  float* dt;       // [S]
+  uint32_t* ray;   // [S] ray index or kNoRay
+  uint32_t* cand;  // [S] candidate index within the ray
+  float* sigma;    // [S]
+  float* rgb;      // [3S]
+  float* dsigma;   // [S] dL/dsigma including the direct density term
+  float* drgb;     // [3S]
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the Philox S-box with
+// multipliers 0xD2511F53, 0xCD9E8D57 and Weyl key increments 0x9E3779B9,
+// 0xBB67AE85.  u01(x) = (x >> 8) * 2^-24.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+__host__ __device__ inline uint32_t u4_word(const U4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ inline float u01(uint32_t x) { return __fmul_rn((float)(x >> 8), 5.9604644775390625e-08f); }
+
+// Launchers (defined in the .cu files), all on `stream`.
+void launch_init_params(const GridParams& g, float* params, uint32_t key0, uint32_t key1, cudaStream_t stream);
+void launch_transform_rays(const float* o_in, const float* d_in, const float* rgb_in, const float* depth_in,
+                           const uint8_t* cls_in, int64_t n, int object_frame, float tx, float ty, float tz, float cz,
+                           float sz, float* o_out, float* d_out, float* rgb_out, float* depth_out, uint8_t* cls_out,
+                           cudaStream_t stream);
+void launch_ray_setup(const GridParams& g, const BatchDesc& b, RayBuf r, uint32_t* block_sums, cudaStream_t stream);
+void launch_scan(const GridParams& g, const BatchDesc& b, uint32_t* block_sums, BatchDyn* dyn, int32_t* totals,
+                 SampleBuf s, unsigned long long* live_counter, cudaStream_t stream);
+void launch_write_samples(const GridParams& g, const BatchDesc& b, RayBuf r, const uint32_t* block_sums,
+                          const BatchDyn* dyn, SampleBuf s, cudaStream_t stream);
+// mode: 0 forward (sigma, rgb out), 1 backward (recompute + adjoint + gradients)
+void launch_tile_mlp(int mode, const GridParams& g, const BatchDesc& b, const BatchDyn* dyn, const int32_t* totals,
+                     RayBuf r, SampleBuf s, int n_ctas, cudaStream_t stream);
+// mode: 0 render (outputs only), 1 training loss + adjoint, 2 upstream gradient + adjoint
+void launch_composite(int mode, const GridParams& g, const BatchDesc& b, RayBuf r, SampleBuf s, BatchDyn* dyn,
+                      int32_t* status, cudaStream_t stream);
+void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream);
+void launch_scatter_slots(const GridParams& g, int64_t n_rays, const RayBuf r, const SampleBuf s, const float* src,
+                          int src_stride, float* dst, int dst_stride, cudaStream_t stream);
+void launch_sample_slots(const GridParams& g, int64_t n_rays, const RayBuf r, const SampleBuf s, float* dst,
+                         cudaStream_t stream);
+void launch_split_outputs(const float* ray_out, int64_t n, float* rgb, float* depth, float* opacity,
+                          cudaStream_t stream);
+int tile_kernel_smem_bytes(int LF);
+
+}  // namespace romap

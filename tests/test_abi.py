@@ -1,0 +1,98 @@
+"""The C ABI library loads and exports every function include/romap.h declares; host-side argument checks and
+the parameter layout work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import romap_oracle as O
+from paper_2304_05735_gb300 import romap as R
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "romap.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return re.findall(r"^ROMAP_API\s+[\w\s\*]+?\b(romap_\w+)\s*\(", src, flags=re.M)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("romap_create_object", "romap_add_rays", "romap_train_step", "romap_render", "romap_init",
+                     "romap_fn_forward", "romap_fn_backward", "romap_get_state", "romap_set_state"):
+        assert required in names
+    assert set(names) == set(R.SIGNATURES), set(names) ^ set(R.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol():
+    L = R.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_null_arguments():
+    assert R.status_string(R.ROMAP_OK) == "ok"
+    assert R.status_string(R.ROMAP_ERR_NONFINITE) == "non-finite value"
+    out = C.c_void_p()
+    assert R.romap_init(None, None, C.byref(out)) == R.ROMAP_ERR_INVALID_ARG
+    assert R.romap_destroy(None) == R.ROMAP_ERR_INVALID_ARG
+    assert R.romap_create_object(None, None, None) == R.ROMAP_ERR_INVALID_ARG
+    assert R.romap_train_step(None, None, 0, 1, None) == R.ROMAP_ERR_INVALID_ARG
+    assert "ctx is NULL" in R.last_error()
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("n_levels", 0, R.ROMAP_ERR_INVALID_ARG), ("n_levels", 17, R.ROMAP_ERR_INVALID_ARG),
+    ("n_features", 4, R.ROMAP_ERR_UNSUPPORTED), ("log2_table_size", 30, R.ROMAP_ERR_INVALID_ARG),
+    ("hidden", 32, R.ROMAP_ERR_UNSUPPORTED), ("dir_dims", 2, R.ROMAP_ERR_INVALID_ARG),
+    ("n_samples", 0, R.ROMAP_ERR_INVALID_ARG), ("n_samples", 2000, R.ROMAP_ERR_INVALID_ARG),
+    ("lr", 0.0, R.ROMAP_ERR_INVALID_ARG), ("beta1", 1.0, R.ROMAP_ERR_INVALID_ARG),
+    ("precision", 7, R.ROMAP_ERR_INVALID_ARG), ("max_objects", 0, R.ROMAP_ERR_INVALID_ARG),
+])
+def test_config_validation_is_host_side(field, value, status):
+    cfg = R.make_config()
+    setattr(cfg, field, value)
+    lay = R.romap_layout()
+    assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == status
+    out = C.c_void_p()
+    assert R.romap_init(C.byref(cfg), None, C.byref(out)) == status
+
+
+def test_allocator_hooks_must_come_in_pairs():
+    cfg = R.make_config()
+    cfg.alloc = R.ALLOC_FN(lambda u, n: None)
+    lay = R.romap_layout()
+    assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == R.ROMAP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kw,okw", [
+    (dict(n_levels=8, log2_table_size=12, base_resolution=16, growth=1.5), dict(L=8, T=2 ** 12, growth=1.5)),
+    (dict(n_levels=16, log2_table_size=16, base_resolution=16, growth=0.0, max_resolution=512),
+     dict(L=16, T=2 ** 16, growth=0.0, n_max=512)),
+    (dict(n_levels=4, log2_table_size=10, base_resolution=16, growth=2.0), dict(L=4, T=2 ** 10, growth=2.0)),
+    (dict(n_levels=16, log2_table_size=19, base_resolution=16, growth=0.0, max_resolution=512, dir_dims=0),
+     dict(L=16, T=2 ** 19, growth=0.0, n_max=512, dir_dims=0)),
+])
+def test_param_layout_matches_oracle(kw, okw):
+    lay = R.param_layout(R.make_config(**kw))
+    oc = O.make_config(**okw)
+    assert lay.n_params == O.param_count(oc)
+    assert lay.n_hash_params == O.hash_param_count(oc)
+    for l in range(lay.n_levels):
+        assert lay.resolution[l] == oc.res[l]
+        assert lay.level_offset[l] == O.level_offset(oc, l)
+        assert bool(lay.dense[l]) == O.level_is_dense(oc, l)
+    for i in range(5):
+        assert lay.mlp_offset[i] == O.hash_param_count(oc) + O.mlp_layer_offset(oc, i)
+
+
+def test_init_without_gpu_reports_cuda_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    out = C.c_void_p()
+    cfg = R.make_config()
+    assert R.romap_init(C.byref(cfg), None, C.byref(out)) == R.ROMAP_ERR_CUDA
+    assert not out.value
