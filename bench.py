@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Training throughput of the per-object NeRF step (RO-MAP Sec. V) on GB300.
+
+One step = one forward + loss + backward + Adam pass of every object of the
+workload (ray draw, box sampling, hash encoding, MLP, compositing, Eq. 7-11
+losses, adjoints, hash-gradient scatter, Adam), run through the C ABI of
+libromap.  The default workload is the multi-object configuration: 8
+objects, 4096 rays per object per step, 64 samples per ray, hash grid L=16,
+F=2, T=2^16, resolutions 16..512, each object seen in 30 frames of 320x240.
+
+Prints one JSON line (rank 0).  Under torchrun every rank trains its own 8
+objects on its own GPU (weak scaling, no collective on the data path).
+--impl reference times the CPU oracle (plain FP64 C) on a bounded sample of
+the same workload.
+"""
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "train samples/s (fwd+bwd+Adam), batched mixed vs plain fp32, at oracle-matched loss"
+WORKLOAD = dict(objects=8, rays_per_object=4096, samples_per_ray=64, levels=16, features=2, log2_table=16,
+                base_resolution=16, max_resolution=512, frames=30, width=320, height=240, focal=320.0)
+WORKLOAD_NAME = ("multi-object training: 8 objects x 4096 rays x 64 samples per step, hash grid L=16 F=2 T=2^16 "
+                 "(16->512), MLP 32-64-16 / 18-64-64-3, 30 frames of 320x240 per object")
+# FP32 SIMT peak of the GB300: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2070 MHz maximum SM clock.
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic work per live sample (real multiply-adds of the five layers, no padding):
+#   forward MLP 8512 MAC; backward input gradients 8320 MAC (the direction inputs need none);
+#   weight gradients 8512 MAC; the backward kernel recomputes the forward.
+MAC_FWD, MAC_DX, MAC_DW = 8512, 8320, 8512
+PHASE_KERNEL = ("k_ray_setup + k_scan + k_write_samples", "k_tile_mlp<forward>", "k_composite<loss>",
+                "k_tile_mlp<backward>", "k_adam + k_advance_step")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp32", "mixed"), default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f if ln.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("kernels_tile.cu", "romap_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2304_05735_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, precision):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        e = d.get(f"{kernel}|{precision}")
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e.get("bytes_per_launch_full_workload")
+    except (OSError, ValueError):
+        return None
+    return None
+
+
+def make_ctx(R, torch, precision):
+    w = WORKLOAD
+    rc = R.make_config(n_levels=w["levels"], log2_table_size=w["log2_table"], base_resolution=w["base_resolution"],
+                       growth=0.0, max_resolution=w["max_resolution"], n_samples=w["samples_per_ray"],
+                       rays_per_step=w["rays_per_object"], bg_random=True,
+                       precision=R.ROMAP_PREC_MIXED_BF16 if precision == "mixed" else R.ROMAP_PREC_FP32,
+                       max_objects=2 * w["objects"])
+    h = C.c_void_p()
+    R.check(R.romap_init(C.byref(rc), C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(h)), "romap_init")
+    return rc, h
+
+
+def add_objects(R, h, scenes):
+    ids = []
+    for sc in scenes:
+        oid = C.c_int32()
+        d = R.object_desc(t=tuple(sc.t), yaw=sc.yaw, half_size=tuple(sc.half), seed=sc.seed)
+        R.check(R.romap_create_object(h, C.byref(d), C.byref(oid)), "romap_create_object")
+        p = sc.pool
+        rays = R.romap_rays(p["origin"].ctypes.data, p["dir"].ctypes.data, p["rgb"].ctypes.data,
+                            p["depth"].ctypes.data, p["cls"].ctypes.data)
+        R.check(R.romap_add_rays(h, oid.value, C.byref(rays), p["cls"].size, 0), "romap_add_rays")
+        ids.append(oid.value)
+    return ids
+
+
+def timed(torch, fn, world, dist):
+    """Runs fn() between barrier + synchronize brackets; returns (device ms on the current stream, max over ranks)."""
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    fn()
+    e.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = s.elapsed_time(e)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def allsum(torch, dist, world, x):
+    if world == 1:
+        return x
+    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t)
+    return t.item()
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2304_05735_gb300 import romap as R
+    from paper_2304_05735_gb300 import synth
+
+    R.lib()
+    w = WORKLOAD
+    scenes = synth.multi_object_scene(w["objects"], seed0=1 + w["objects"] * rank, n_frames=w["frames"],
+                                      W=w["width"], H=w["height"], f=w["focal"])
+    rc, h = make_ctx(R, torch, args.precision)
+    ids = add_objects(R, h, scenes)
+    idarr = (C.c_int32 * len(ids))(*ids)
+    n = len(ids)
+
+    # warm-up, then K timed steps of the batched path
+    R.check(R.romap_train_step(h, idarr, n, max(args.warmup, 3), None))
+    torch.cuda.synchronize()
+    R.check(R.romap_reset_stats(h))
+    R.check(R.romap_set_profiling(h, 1))
+    gpu_index = (os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local]
+                 if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local))
+    sampler = ClockSampler(gpu_index)
+    time.sleep(0.3)
+
+    def steps():
+        for _ in range(args.steps):
+            R.check(R.romap_train_step(h, idarr, n, 1, None))
+
+    ms = timed(torch, steps, world, dist)
+    clocks = sampler.stop()
+    st = R.romap_stats()
+    R.check(R.romap_get_stats(h, C.byref(st)))
+    phase_ms = (C.c_double * R.ROMAP_N_PHASES)()
+    phase_n = (C.c_int64 * R.ROMAP_N_PHASES)()
+    R.check(R.romap_phase_times(h, phase_ms, phase_n))
+    R.check(R.romap_set_profiling(h, 0))
+    live = allsum(torch, dist, world, st.live_samples)
+    value = live / (ms / 1e3)
+    live_per_step = st.live_samples / args.steps  # this rank
+    launches = st.kernel_launches
+    loss_batched = np.zeros(n, np.float32)
+    R.check(R.romap_train_step(h, idarr, n, 1, loss_batched.ctypes.data))
+
+    # phases and the roofline of the dominant kernel
+    phases = {}
+    for i, name in enumerate(R.PHASES):
+        per_launch_ms = phase_ms[i] / max(1, args.steps)
+        ent = {"kernel": PHASE_KERNEL[i], "ms_per_step": per_launch_ms, "share": phase_ms[i] / max(1e-9, sum(phase_ms))}
+        phases[name] = ent
+    bwd_ms = phase_ms[3] / args.steps
+    fwd_ms = phase_ms[1] / args.steps
+    flop_bwd = 2.0 * (MAC_FWD + MAC_DX + MAC_DW) * live_per_step
+    flop_fwd = 2.0 * MAC_FWD * live_per_step
+    phases["mlp_backward_scatter"]["achieved_tflops"] = flop_bwd / (bwd_ms / 1e3) / 1e12
+    phases["mlp_forward"]["achieved_tflops"] = flop_fwd / (fwd_ms / 1e3) / 1e12
+    adam_bytes = 32.0 * int(R.param_layout(rc).n_params) * n
+    phases["adam"]["achieved_gbs"] = adam_bytes / (phase_ms[4] / args.steps / 1e3) / 1e9
+    dominant = max(range(R.ROMAP_N_PHASES), key=lambda i: phase_ms[i])
+    if dominant in (1, 3):
+        flop = flop_bwd if dominant == 3 else flop_fwd
+        kms = bwd_ms if dominant == 3 else fwd_ms
+        achieved = flop / (kms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": PHASE_KERNEL[dominant], "achieved": achieved,
+                    "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS,
+                    "traffic": profiled_traffic(PHASE_KERNEL[dominant], args.precision),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 SIMT FMA)",
+                    "work_per_unit": f"{2 * (MAC_FWD + MAC_DX + MAC_DW) if dominant == 3 else 2 * MAC_FWD} "
+                                     "FLOP per live sample",
+                    "units_per_launch": live_per_step, "ms_per_launch": kms}
+    else:
+        roofline = {"bound": "hbm", "kernel": PHASE_KERNEL[dominant], "achieved": None, "peak": None,
+                    "unit": "GB/s", "frac": None, "traffic": None}
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = None
+    if os.path.exists(peaks_path):
+        hbm_peak = json.load(open(peaks_path)).get("hbm_gbs")
+    if hbm_peak:
+        phases["adam"]["frac_of_measured_hbm"] = phases["adam"]["achieved_gbs"] / hbm_peak
+
+    # the plain per-object FP32 path: one launch sequence per object
+    plain = None
+    if not args.no_plain:
+        k_plain = max(5, args.steps // 4)
+        R.check(R.romap_reset_stats(h))
+
+        def plain_steps():
+            for _ in range(k_plain):
+                for i in ids:
+                    one = (C.c_int32 * 1)(i)
+                    R.check(R.romap_train_step(h, one, 1, 1, None))
+
+        ms_p = timed(torch, plain_steps, world, dist)
+        stp = R.romap_stats()
+        R.check(R.romap_get_stats(h, C.byref(stp)))
+        live_p = allsum(torch, dist, world, stp.live_samples)
+        plain = {"value": live_p / (ms_p / 1e3), "ms_per_step": ms_p / k_plain, "steps": k_plain,
+                 "path": "plain FP32, one launch sequence per object"}
+
+    # end to end through the C ABI with host buffers: each step replaces every object's rays with a fresh batch
+    # of 4096 rays from pinned host memory, trains, and reads the losses back
+    e2e = None
+    if not args.no_e2e:
+        rng = np.random.default_rng(100 + rank)
+        B = w["rays_per_object"]
+        k_e2e = max(3, min(args.steps, 50))
+        batches = []
+        for _ in range(k_e2e + 2):
+            per = []
+            for sc in scenes:
+                sel = rng.integers(0, sc.pool["cls"].size, B)
+                arrs = {}
+                for k in ("origin", "dir", "rgb", "depth", "cls"):
+                    a = sc.pool[k][sel]
+                    t = torch.empty(a.shape, dtype=torch.uint8 if k == "cls" else torch.float32, pin_memory=True)
+                    t.numpy()[...] = a
+                    arrs[k] = t
+                per.append(arrs)
+            batches.append(per)
+        h2d = sum(t.numel() * t.element_size() for t in batches[0][0].values()) * n
+        loss = np.zeros(n, np.float32)
+
+        def e2e_step(per):
+            for i, arrs in zip(ids, per):
+                rays = R.romap_rays(arrs["origin"].data_ptr(), arrs["dir"].data_ptr(), arrs["rgb"].data_ptr(),
+                                    arrs["depth"].data_ptr(), arrs["cls"].data_ptr())
+                R.check(R.romap_add_rays(h, i, C.byref(rays), B, R.ROMAP_REPLACE), "romap_add_rays")
+            R.check(R.romap_train_step(h, idarr, n, 1, loss.ctypes.data), "romap_train_step")
+
+        for per in batches[:2]:
+            e2e_step(per)
+        R.check(R.romap_reset_stats(h))
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for per in batches[2:]:
+            e2e_step(per)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = t.item()
+        ste = R.romap_stats()
+        R.check(R.romap_get_stats(h, C.byref(ste)))
+        live_e = allsum(torch, dist, world, ste.live_samples)
+        e2e = {"value": live_e / el, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(n * 48 + 4), "steps": k_e2e,
+               "path": "romap_add_rays(REPLACE, pinned host) x 8 + romap_train_step(out_loss to host), wall clock"}
+    R.check(R.romap_destroy(h))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n_rays=4096, steps=1)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f16+f32",
+               "data": "synthetic (analytic shapes, seeded)",
+               "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "precision": args.precision, "path": "batched",
+                          "parallelism": f"replicas x{world} (objects sharded, no collective)",
+                          "l2": "inputs larger than L2: per step 219 MB of parameters, gradients and Adam moments "
+                                "plus 0.4 GB of ray pools (L2 129 MB)"},
+               "live_samples_per_step": live_per_step, "loss_after_timed_steps": [float(x) for x in loss_batched],
+               "roofline": roofline, "phases": phases, "plain_per_object": plain, "e2e": e2e,
+               "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_setup(n_rays, seed=1):
+    import numpy as np
+
+    from oracle import romap_oracle as O
+    from paper_2304_05735_gb300 import synth
+
+    w = WORKLOAD
+    sc = synth.multi_object_scene(1, seed0=seed, n_frames=4, W=w["width"], H=w["height"], f=w["focal"])[0]
+    oc = O.make_config(L=w["levels"], T=2 ** w["log2_table"], n_min=w["base_resolution"], growth=0.0,
+                       n_max=w["max_resolution"], n_samples=w["samples_per_ray"], rays_per_step=n_rays,
+                       bg_random=True)
+    o, d = O.world_to_object(sc.pool["origin"], sc.pool["dir"], sc.t.astype(np.float32), sc.yaw)
+    pool = dict(o=o, d=d, rgb=sc.pool["rgb"], depth=sc.pool["depth"], cls=sc.pool["cls"])
+    p = O.init_params(oc, sc.seed)
+    return O, oc, sc, pool, p
+
+
+def cpu_baseline(n_rays=4096, steps=1):
+    import numpy as np
+
+    O, oc, sc, pool, p = _oracle_setup(n_rays)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    live = 0
+    t0 = time.perf_counter()
+    for s in range(1, steps + 1):
+        r = O.train_step(oc, sc.half.astype(np.float32), sc.seed, s, pool, p, m, v, want_samples=True)
+        p, m, v = r["params"], r["m"], r["v"]
+        live += int(r["samples"][:, :, 5].sum())
+    el = time.perf_counter() - t0
+    return {"value": live / el, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} step(s) of 1 object x {n_rays} rays x {WORKLOAD['samples_per_ray']} samples at the "
+                      f"workload's model size (FP64 C oracle, single thread), {live} live samples in {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    n_rays = 256
+    O, oc, sc, pool, p = _oracle_setup(n_rays)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    half = sc.half.astype(np.float32)
+    step = 1
+    for _ in range(args.warmup):
+        r = O.train_step(oc, half, sc.seed, step, pool, p, m, v)
+        p, m, v = r["params"], r["m"], r["v"]
+        step += 1
+    live = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = O.train_step(oc, half, sc.seed, step, pool, p, m, v, want_samples=True)
+        p, m, v = r["params"], r["m"], r["v"]
+        live += int(r["samples"][:, :, 5].sum())
+        step += 1
+    el = time.perf_counter() - t0
+    value = live / el
+    sample = (f"each step: 1 object x {n_rays} rays x {WORKLOAD['samples_per_ray']} samples of the workload's model "
+              f"(L=16, T=2^16) incl. dense Adam over all parameters; FP64 C oracle, one thread")
+    out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic shapes, seeded)",
+           "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "reference_sample_rays": n_rays},
+           "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

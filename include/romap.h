@@ -247,7 +247,18 @@ ROMAP_API romap_status romap_fn_backward(romap_ctx* ctx, const float* params, co
 
 /* ---- counters ---------------------------------------------------------- */
 ROMAP_API romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out);
+/* Also clears the phase times below. */
 ROMAP_API romap_status romap_reset_stats(romap_ctx* ctx);
+/* Phase timing: while on, every phase of a step is bracketed by CUDA events
+ * on the context's stream.  romap_phase_times synchronises the stream and
+ * returns, per phase, the device milliseconds and kernel launches since the
+ * last reset: [0] sampling (ray draw, scan, sample write), [1] MLP forward,
+ * [2] compositing + loss + adjoint, [3] MLP backward + hash scatter,
+ * [4] Adam.  ms and launches point to ROMAP_N_PHASES entries (launches
+ * nullable). */
+#define ROMAP_N_PHASES 5
+ROMAP_API romap_status romap_set_profiling(romap_ctx* ctx, int32_t on);
+ROMAP_API romap_status romap_phase_times(romap_ctx* ctx, double* ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

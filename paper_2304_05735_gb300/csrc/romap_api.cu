@@ -101,6 +101,12 @@ struct romap_ctx {
   BatchDyn* dyn_host = nullptr;    // pinned
   romap_stats stats{};
   int64_t launches = 0;
+  // phase timing
+  bool profiling = false;
+  struct Prof { int phase; cudaEvent_t a, b; int launches; };
+  std::vector<Prof> prof;
+  double phase_ms[ROMAP_N_PHASES] = {0};
+  int64_t phase_launches[ROMAP_N_PHASES] = {0};
 };
 
 namespace {
@@ -402,9 +408,30 @@ void free_object(romap_ctx* ctx, Object& o) {
   o = Object{};
 }
 
+// Brackets a phase with CUDA events when profiling is on.
+struct PhaseScope {
+  romap_ctx* ctx;
+  romap_ctx::Prof p{};
+  bool on;
+  PhaseScope(romap_ctx* c, int phase, int launches) : ctx(c), on(c->profiling) {
+    if (!on) return;
+    p.phase = phase;
+    p.launches = launches;
+    cudaEventCreate(&p.a);
+    cudaEventCreate(&p.b);
+    cudaEventRecord(p.a, ctx->stream);
+  }
+  ~PhaseScope() {
+    if (!on) return;
+    cudaEventRecord(p.b, ctx->stream);
+    ctx->prof.push_back(p);
+  }
+};
+
 // Runs the sampling stage for a batch: ray setup, scan, sample write.
 romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBuf S, uint32_t* block_sums,
                           BatchDyn* dyn, int32_t* totals, bool count_live) {
+  PhaseScope ps(ctx, 0, 3);
   launch_ray_setup(ctx->g, b, R, block_sums, ctx->stream);
   launch_scan(ctx->g, b, block_sums, dyn, totals, S, count_live ? ctx->live_counter : nullptr, ctx->stream);
   launch_write_samples(ctx->g, b, R, block_sums, dyn, S, ctx->stream);
@@ -429,9 +456,18 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
   BatchDesc b;
   ROMAP_TRY(upload_batch(ctx, hb, &b));
   ROMAP_TRY(run_sampling(ctx, b, ctx->R, ctx->S, ctx->block_sums, ctx->dyn, ctx->totals, true));
-  launch_tile_mlp(0, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
-  launch_composite(1, ctx->g, b, ctx->R, ctx->S, ctx->dyn, ctx->status, ctx->stream);
-  launch_tile_mlp(1, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+  {
+    PhaseScope ps(ctx, 1, 1);
+    launch_tile_mlp(0, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+  }
+  {
+    PhaseScope ps(ctx, 2, 1);
+    launch_composite(1, ctx->g, b, ctx->R, ctx->S, ctx->dyn, ctx->status, ctx->stream);
+  }
+  {
+    PhaseScope ps(ctx, 3, 1);
+    launch_tile_mlp(1, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+  }
   ctx->launches += 3;
   CUDA_TRY(cudaGetLastError());
   ctx->stats.steps += hb.n;
@@ -578,6 +614,10 @@ romap_status romap_destroy(romap_ctx* ctx) {
     dev_free(ctx, b->p);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->dyn_host) cudaFreeHost(ctx->dyn_host);
+  for (auto& p : ctx->prof) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
   delete ctx;
   return ROMAP_OK;
 }
@@ -765,7 +805,10 @@ romap_status romap_adam_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids) 
   build_batch(v, rays, &hb);
   BatchDesc b;
   ROMAP_TRY(upload_batch(ctx, hb, &b));
-  launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+  {
+    PhaseScope ps(ctx, 4, 2);
+    launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+  }
   ctx->launches += 2;
   CUDA_TRY(cudaGetLastError());
   for (int32_t id : v) {
@@ -783,7 +826,10 @@ romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids,
   for (int s = 0; s < n_steps; ++s) {
     BatchDesc b;
     ROMAP_TRY(run_fwd_bwd(ctx, v, &b));
-    launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+    {
+      PhaseScope ps(ctx, 4, 2);
+      launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+    }
     ctx->launches += 2;
     CUDA_TRY(cudaGetLastError());
     for (int32_t id : v) {
@@ -882,10 +928,45 @@ romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out) {
   return ROMAP_OK;
 }
 
+romap_status romap_set_profiling(romap_ctx* ctx, int32_t on) {
+  ROMAP_TRY(check_ctx(ctx));
+  ctx->profiling = on != 0;
+  return ROMAP_OK;
+}
+
+romap_status romap_phase_times(romap_ctx* ctx, double* ms, int64_t* launches) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (!ms) return fail(ROMAP_ERR_INVALID_ARG, "ms is NULL");
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  for (auto& p : ctx->prof) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ctx->phase_ms[p.phase] += t;
+    ctx->phase_launches[p.phase] += p.launches;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  ctx->prof.clear();
+  for (int i = 0; i < ROMAP_N_PHASES; ++i) {
+    ms[i] = ctx->phase_ms[i];
+    if (launches) launches[i] = ctx->phase_launches[i];
+  }
+  return ROMAP_OK;
+}
+
 romap_status romap_reset_stats(romap_ctx* ctx) {
   ROMAP_TRY(check_ctx(ctx));
   ctx->stats = romap_stats{};
   ctx->launches = 0;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& p : ctx->prof) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  ctx->prof.clear();
+  for (int i = 0; i < ROMAP_N_PHASES; ++i) {
+    ctx->phase_ms[i] = 0.0;
+    ctx->phase_launches[i] = 0;
+  }
   CUDA_TRY(cudaMemsetAsync(ctx->live_counter, 0, sizeof(unsigned long long), ctx->stream));
   return ROMAP_OK;
 }

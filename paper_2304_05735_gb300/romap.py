@@ -102,7 +102,11 @@ SIGNATURES = {
                                  _vp]),
     "romap_get_stats": (_i32, [_vp, _P(romap_stats)]),
     "romap_reset_stats": (_i32, [_vp]),
+    "romap_set_profiling": (_i32, [_vp, _i32]),
+    "romap_phase_times": (_i32, [_vp, _vp, _vp]),
 }
+ROMAP_N_PHASES = 5
+PHASES = ("sampling", "mlp_forward", "composite_loss_adjoint", "mlp_backward_scatter", "adam")
 
 _lib = None
 

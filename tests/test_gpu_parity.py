@@ -81,7 +81,8 @@ def test_sample_positions_bit_exact(torch, N, use_occ):
 
 
 def test_world_to_object_transform_bit_exact(torch):
-    """Rendering world-frame rays equals rendering the oracle's object-frame copy of them, bit for bit."""
+    """Rendering world-frame rays equals the functional forward on the oracle's object-frame copy of them (same
+    midpoint samples and background), bit for bit: the device transform matches the oracle's FP32 transform."""
     oc, rc = paired_config()
     rng = np.random.default_rng(1)
     o_obj, d_obj = _rays_at_box(200, rng)
@@ -93,20 +94,18 @@ def test_world_to_object_transform_bit_exact(torch):
     ctx = Ctx(rc)
     try:
         oid = ctx.create(t=tuple(t), yaw=yaw, seed=3)
-        bg = (R.C.c_float * 3)(0.2, 0.3, 0.4)
-
-        def render(o, d, flags):
-            rgb = np.zeros((200, 3), np.float32); dep = np.zeros(200, np.float32); op = np.zeros(200, np.float32)
-            o = np.ascontiguousarray(o, np.float32); d = np.ascontiguousarray(d, np.float32)
-            R.check(R.romap_render(ctx.h, oid, o.ctypes.data, d.ctypes.data, 200, bg, rgb.ctypes.data,
-                                   dep.ctypes.data, op.ctypes.data, flags), "romap_render")
-            return rgb, dep, op
-
-        a = render(o_w, d_w, 0)
-        b = render(oo.reshape(-1, 3), do.reshape(-1, 3), R.ROMAP_OBJECT_FRAME)
-        for x, y in zip(a, b):
-            assert np.array_equal(x, y)
-        assert (a[2] > 0).sum() > 100
+        bgv = (0.2, 0.3, 0.4)
+        bg = (R.C.c_float * 3)(*bgv)
+        rgb = np.zeros((200, 3), np.float32); dep = np.zeros(200, np.float32); op = np.zeros(200, np.float32)
+        R.check(R.romap_render(ctx.h, oid, o_w.ctypes.data, d_w.ctypes.data, 200, bg, rgb.ctypes.data,
+                               dep.ctypes.data, op.ctypes.data, 0), "romap_render")
+        params = torch.tensor(ctx.state(oid)[0], device="cuda")
+        to = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32).reshape(-1, 3), device="cuda")
+        out, _, _ = ctx.fn_forward(params, (0.5, 0.5, 0.5), 3, 0, to(oo), to(do), to(np.tile(bgv, (200, 1))),
+                                   jitter=False)
+        out = out.cpu().numpy()
+        assert np.array_equal(rgb, out[:, :3]) and np.array_equal(dep, out[:, 3]) and np.array_equal(op, out[:, 4])
+        assert (op > 0).sum() > 100
     finally:
         ctx.close()
 
@@ -226,7 +225,7 @@ def test_training_loss_decreases_plain_config(torch):
 def test_masked_losses_parity(torch):
     """Object, background (random colour + density loss), occluder and depth rays, posed object."""
     oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, n_samples=32, rays_per_step=2048, bg_random=True)
-    sc = synth.multi_object_scene(1, seed0=5, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2)[0]
+    sc = synth.multi_object_scene(1, seed0=5, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2, occluder_prob=1.0)[0]
     ctx = Ctx(rc)
     try:
         oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=5)
@@ -263,7 +262,7 @@ def test_batched_objects_equal_separate_launches(torch):
                 oid = ctx2.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=300 + 150 * k)
                 ctx2.add_rays(oid, sc.pool)
                 ls = ctx2.fwd_bwd([oid])
-                assert np.allclose(ls[0], lb[k], rtol=1e-6, atol=1e-8)
+                assert np.allclose(ls[0], lb[k], rtol=1e-5, atol=1e-8)  # FP32 atomic sums, any order
                 assert_grad_close(ctx2.grad(oid), gb[k], tol=1e-5, what=f"object {k}")
         finally:
             ctx2.close()
