@@ -245,6 +245,30 @@ ROMAP_API romap_status romap_fn_backward(romap_ctx* ctx, const float* params, co
                                const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
                                const float* grad_ray, float* grad_params, float* out_dsigma);
 
+/* Same as romap_fn_forward, without a context and without any device
+ * allocation by the library or the caller: for callers that cannot allocate
+ * device memory where they render (a plugin whose host framework owns all
+ * device memory and offers no allocator; a real-time loop that must not call
+ * cudaMalloc/cudaFree because they can synchronise the device).  The paper
+ * has no counterpart; this is a deployment convenience.
+ *  - Scratch lives in one static 32 MiB device array inside the library,
+ *    held by every GPU that loads it until process exit.  Calls whose
+ *    scratch would not fit (about n * (105 + 60 * n_samples) bytes) return
+ *    ROMAP_ERR_CAPACITY with the largest n that fits.
+ *  - The first call on each device resolves the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make it before any
+ *    stream capture.
+ *  - All calls on a device share the array: calls that overlap on the GPU
+ *    race and must be serialised by the caller.
+ * cfg as for romap_init (validated, nothing allocated); cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream); every pointer is a device
+ * pointer except cfg and half_size (host); out_ray [6n] as for
+ * romap_fn_forward. */
+ROMAP_API romap_status romap_fn_forward_noalloc(const romap_config* cfg, void* cuda_stream, const float* params,
+                                                const float half_size[3], uint64_t seed, uint32_t step,
+                                                const uint64_t* occupancy, const float* origin, const float* dir,
+                                                const float* bg, int64_t n, uint32_t flags, float* out_ray);
+
 /* ---- counters ---------------------------------------------------------- */
 ROMAP_API romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out);
 /* Also clears the phase times below. */

@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1176,3 +1177,112 @@ romap_status romap_render(romap_ctx* ctx, int32_t id, const float* origin, const
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Functional forward that allocates nothing.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// render: a plugin inside a host framework that owns every byte of device
+// memory and hands out no allocator, or a real-time mapping loop that must
+// not call cudaMalloc/cudaFree (which may synchronise the whole device and
+// stall the frame).  romap_fn_forward needs a caller workspace, which such a
+// caller cannot provide.  This variant keeps its scratch (ray records,
+// compacted samples, scan totals, the object record) in one file-scope device
+// array of kNoAllocScratchBytes, loaded with the library: every GPU that
+// loads libromap holds those bytes until the process exits.
+//
+// Set-up: the first call on each device, with that device current, looks up
+// the array's device address with cudaGetSymbolAddress (host code cannot use
+// the array's name as a device address) and caches it; make that first call
+// before any stream capture.  All calls on a device share the one array and
+// it keeps the last call's contents: every scratch word the kernels read is
+// written earlier in the same call, so nothing needs clearing, but calls that
+// overlap on the GPU (two streams, two threads) race on the array and must be
+// serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+romap_status noalloc_scratch(int dev, char** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ROMAP_ERR_UNSUPPORTED, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(ROMAP_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (char*)g_noalloc_ptr[dev];
+  return ROMAP_OK;
+}
+}  // namespace
+
+extern "C" romap_status romap_fn_forward_noalloc(const romap_config* cfg, void* cuda_stream, const float* params,
+                                                 const float half_size[3], uint64_t seed, uint32_t step,
+                                                 const uint64_t* occupancy, const float* origin, const float* dir,
+                                                 const float* bg, int64_t n, uint32_t flags, float* out_ray) {
+  GridParams g;
+  ROMAP_TRY(make_grid(cfg, &g));
+  if (!params || !half_size || !origin || !dir || !bg || !out_ray) return fail(ROMAP_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(ROMAP_ERR_INVALID_ARG, "n must be >= 1");
+  if (flags & ~(ROMAP_JITTER)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  for (int a = 0; a < 3; ++a)
+    if (!(half_size[a] > 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "half_size must be positive");
+  const size_t rec = align_up(sizeof(ObjectDev), 256);
+  FnLayout L = fn_layout(g, n);
+  if (rec + L.total > kNoAllocScratchBytes) {
+    int64_t max_n = 0;
+    for (int64_t lo = 1, hi = n; lo <= hi;) {  // largest n that fits, for the message
+      int64_t mid = lo + (hi - lo) / 2;
+      if (rec + fn_layout(g, mid).total <= kNoAllocScratchBytes) { max_n = mid; lo = mid + 1; } else hi = mid - 1;
+    }
+    return fail(ROMAP_ERR_CAPACITY,
+                "romap_fn_forward_noalloc: %lld rays of %d samples need %zu bytes of scratch, more than the %zu-byte "
+                "static scratch; at most %lld rays fit",
+                (long long)n, g.n_samples, rec + L.total, kNoAllocScratchBytes, (long long)max_n);
+  }
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  char* base = nullptr;
+  ROMAP_TRY(noalloc_scratch(dev, &base));
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  ObjectDev* od = (ObjectDev*)base;
+  FnView v = fn_view(base + rec, L);
+  HostBatch hb;
+  build_batch(std::vector<int32_t>{0}, std::vector<int32_t>{(int32_t)n}, &hb);
+  CUDA_TRY(cudaMemcpyAsync(v.batch, hb.arr.data(), sizeof(int32_t) * hb.arr.size(), cudaMemcpyHostToDevice, stream));
+  ObjectDev d{};
+  d.params = const_cast<float*>(params);
+  d.occ = occupancy;
+  for (int a = 0; a < 3; ++a) {
+    d.half[a] = half_size[a];
+    d.inv_ext[a] = 1.0f / (half_size[a] - (-half_size[a]));
+  }
+  d.key0 = (uint32_t)seed;
+  d.key1 = (uint32_t)(seed >> 32);
+  d.n_rays = (int32_t)n;
+  d.step = step;
+  CUDA_TRY(cudaMemcpyAsync(od, &d, sizeof(d), cudaMemcpyHostToDevice, stream));
+  BatchDesc b = desc_from(hb, v.batch, od);
+  b.explicit_rays = 1;
+  b.explicit_step = step;
+  b.jitter = (flags & ROMAP_JITTER) ? 1 : 0;
+  b.ex_o = origin;
+  b.ex_d = dir;
+  b.ex_bg = bg;
+  launch_ray_setup(g, b, v.R, v.blocks, stream);
+  launch_scan(g, b, v.blocks, v.dyn, v.totals, v.S, nullptr, stream);
+  launch_write_samples(g, b, v.R, v.blocks, v.dyn, v.S, stream);
+  launch_tile_mlp(0, g, b, v.dyn, v.totals, v.R, v.S, sms > 0 ? sms : 1, stream);
+  launch_composite(0, g, b, v.R, v.S, v.dyn, nullptr, stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(out_ray, v.R.out, sizeof(float) * 6 * n, cudaMemcpyDeviceToDevice, stream));
+  return ROMAP_OK;
+}
