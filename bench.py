@@ -247,14 +247,36 @@ def run_ours(args):
         phases[name] = ent
     bwd_ms = phase_ms[3] / args.steps
     fwd_ms = phase_ms[1] / args.steps
-    flop_bwd = 2.0 * (MAC_FWD + MAC_DX + MAC_DW) * live_per_step
+    mixed = args.precision == "mixed"
+    peaks = {}
+    peaks_path0 = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path0):
+        peaks = json.load(open(peaks_path0))
+    if mixed:
+        # the fused kernel does forward (8512 MAC), input gradients (8320) and weight gradients (8512) per sample
+        phases["mlp_backward_scatter"]["kernel"] = "k_tile_tc (fused: samples, gather, MLP fwd, Eq. 6-11, bwd, scatter)"
+        flop_bwd = 2.0 * (MAC_FWD + MAC_DX + MAC_DW) * live_per_step
+    else:
+        flop_bwd = 2.0 * (MAC_FWD + MAC_DX + MAC_DW) * live_per_step
     flop_fwd = 2.0 * MAC_FWD * live_per_step
-    phases["mlp_backward_scatter"]["achieved_tflops"] = flop_bwd / (bwd_ms / 1e3) / 1e12
-    phases["mlp_forward"]["achieved_tflops"] = flop_fwd / (fwd_ms / 1e3) / 1e12
-    adam_bytes = 32.0 * int(R.param_layout(rc).n_params) * n
-    phases["adam"]["achieved_gbs"] = adam_bytes / (phase_ms[4] / args.steps / 1e3) / 1e9
+    if bwd_ms > 0:
+        phases["mlp_backward_scatter"]["achieved_tflops"] = flop_bwd / (bwd_ms / 1e3) / 1e12
+    if fwd_ms > 0:
+        phases["mlp_forward"]["achieved_tflops"] = flop_fwd / (fwd_ms / 1e3) / 1e12
+    adam_bytes = (32.0 + (2.0 if mixed else 0.0)) * int(R.param_layout(rc).n_params) * n
+    if phase_ms[4] > 0:
+        phases["adam"]["achieved_gbs"] = adam_bytes / (phase_ms[4] / args.steps / 1e3) / 1e9
     dominant = max(range(R.ROMAP_N_PHASES), key=lambda i: phase_ms[i])
-    if dominant in (1, 3):
+    if dominant == 3 and mixed:
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        achieved = flop_bwd / (bwd_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "kernel": phases["mlp_backward_scatter"]["kernel"], "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": profiled_traffic("k_tile_tc", args.precision),
+                    "peak_source": "measured bf16 dense, sustained (MEASURED_PEAKS.json)" if peaks else "fallback",
+                    "work_per_unit": f"{2 * (MAC_FWD + MAC_DX + MAC_DW)} FLOP per live sample (BF16 MMA)",
+                    "units_per_launch": live_per_step, "ms_per_launch": bwd_ms}
+    elif dominant in (1, 3):
         flop = flop_bwd if dominant == 3 else flop_fwd
         kms = bwd_ms if dominant == 3 else fwd_ms
         achieved = flop / (kms / 1e3) / 1e12
@@ -266,8 +288,10 @@ def run_ours(args):
                                      "FLOP per live sample",
                     "units_per_launch": live_per_step, "ms_per_launch": kms}
     else:
-        roofline = {"bound": "hbm", "kernel": PHASE_KERNEL[dominant], "achieved": None, "peak": None,
-                    "unit": "GB/s", "frac": None, "traffic": None}
+        hbm = peaks.get("hbm_gbs") or 6800.0
+        ach = phases["adam"].get("achieved_gbs") if dominant == 4 else None
+        roofline = {"bound": "hbm", "kernel": PHASE_KERNEL[dominant], "achieved": ach, "peak": hbm,
+                    "unit": "GB/s", "frac": (ach / hbm) if ach else None, "traffic": None}
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = None
     if os.path.exists(peaks_path):

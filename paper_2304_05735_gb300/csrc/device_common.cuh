@@ -1,0 +1,121 @@
+// Device helpers shared by the sampling, FP32 tile and tensor-core tile kernels: the ray/box slab test, the
+// occupancy lookup, stratified sample positions and hash-grid corners.  The FP32 arithmetic of the slab test, the
+// sample positions and the corner selection is written with round-to-nearest intrinsics in one fixed order (no
+// contraction into FMA), so that every kernel and the oracle produce the same bits.
+#pragma once
+#include "romap_internal.cuh"
+
+namespace romap {
+
+// ---------------------------------------------------------------------------
+// Ray/box slab test (box [-half, half]); returns hit.
+// ---------------------------------------------------------------------------
+__device__ inline bool slab(const float o[3], const float d[3], const float half[3], float& tn, float& tf) {
+  float t0 = 0.0f, t1 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float lo = -half[a], hi = half[a];
+    float inv = __fdiv_rn(1.0f, d[a]);
+    float ta = __fmul_rn(__fsub_rn(lo, o[a]), inv);
+    float tb = __fmul_rn(__fsub_rn(hi, o[a]), inv);
+    float mn = fminf(ta, tb), mx = fmaxf(ta, tb);
+    t0 = (a == 0) ? mn : fmaxf(t0, mn);
+    t1 = (a == 0) ? mx : fminf(t1, mx);
+  }
+  tn = fmaxf(t0, 0.0f);
+  tf = t1;
+  return t1 > tn;
+}
+
+__device__ inline bool occupied(const uint64_t* occ, float x, float y, float z, const float half[3],
+                                const float inv_ext[3]) {
+  if (!occ) return true;
+  float p[3] = {x, y, z};
+  uint32_t c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u = fminf(fmaxf(__fmul_rn(__fsub_rn(p[a], -half[a]), inv_ext[a]), 0.0f), 1.0f);
+    int ci = (int)__fmul_rn(u, 64.0f);
+    c[a] = (uint32_t)(ci > 63 ? 63 : ci);
+  }
+  uint32_t bit = c[0] + 64u * c[1] + 4096u * c[2];
+  return (__ldg(occ + (bit >> 6)) >> (bit & 63u)) & 1ull;
+}
+
+// Stratified candidates t_i = t_near + (i + u_i) dt_N, delta_i = t_{i+1} - t_i
+// (last: t_far - t_{N-1}), x_i = o + t_i d; f(i, t, delta, x, y, z, live).
+template <class Fn>
+__device__ inline void for_candidates(const float o[3], const float d[3], float tn, float tf, int N, uint32_t k0,
+                                      uint32_t k1, uint32_t step, uint32_t slot, int jitter, const uint64_t* occ,
+                                      const float half[3], const float inv_ext[3], Fn f) {
+  float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
+  U4 rnd = {0, 0, 0, 0};
+  auto t_of = [&](int i) -> float {
+    float u = 0.5f;
+    if (jitter) {
+      if ((i & 3) == 0) rnd = philox(step, slot, kPurposeJitter, (uint32_t)i >> 2, k0, k1);
+      u = u01(u4_word(rnd, i & 3));
+    }
+    return __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, u), step_len));
+  };
+  float t_cur = t_of(0);
+  for (int i = 0; i < N; ++i) {
+    float t_next = (i + 1 < N) ? t_of(i + 1) : tf;
+    float dt = __fsub_rn(t_next, t_cur);
+    float x = __fadd_rn(o[0], __fmul_rn(t_cur, d[0]));
+    float y = __fadd_rn(o[1], __fmul_rn(t_cur, d[1]));
+    float z = __fadd_rn(o[2], __fmul_rn(t_cur, d[2]));
+    f(i, t_cur, dt, x, y, z, occupied(occ, x, y, z, half, inv_ext));
+    t_cur = t_next;
+  }
+}
+
+// Position of candidate i of a ray (same operations as for_candidates).
+__device__ inline float candidate_t(float tn, float step_len, int i, uint32_t k0, uint32_t k1, uint32_t step,
+                                    uint32_t slot, int jitter) {
+  float u = 0.5f;
+  if (jitter) u = u01(u4_word(philox(step, slot, kPurposeJitter, (uint32_t)i >> 2, k0, k1), i & 3));
+  return __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, u), step_len));
+}
+
+// ---------------------------------------------------------------------------
+// Hash-grid corners of one level for an object-frame point (FP32, fixed
+// order): u = clamp((x + half) inv_ext, 0, 1), pos = u N_l, i0 =
+// min(floor(pos), N_l - 1), f = pos - i0; dense index x + y(N+1) + z(N+1)^2
+// or spatial hash (x * 1 ^ y * 2654435761 ^ z * 805459861) mod T.
+// ---------------------------------------------------------------------------
+struct Corners {
+  uint32_t idx[8];
+  float w[8];
+};
+
+__device__ inline void level_corners(const GridParams& g, int l, const float p[3], const float half[3],
+                                     const float inv_ext[3], Corners& c) {
+  int i0[3];
+  float f[3];
+  const int N = g.res[l];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u = fminf(fmaxf(__fmul_rn(__fsub_rn(p[a], -half[a]), inv_ext[a]), 0.0f), 1.0f);
+    float pos = __fmul_rn(u, (float)N);
+    int i = (int)floorf(pos);
+    i = i > N - 1 ? N - 1 : i;
+    i0[a] = i;
+    f[a] = __fsub_rn(pos, (float)i);
+  }
+  const uint32_t n1 = (uint32_t)N + 1u;
+  const bool dense = g.dense[l];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    uint32_t cx = (uint32_t)(i0[0] + (k & 1));
+    uint32_t cy = (uint32_t)(i0[1] + ((k >> 1) & 1));
+    uint32_t cz = (uint32_t)(i0[2] + ((k >> 2) & 1));
+    c.idx[k] = dense ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) % g.T);
+    float wx = (k & 1) ? f[0] : 1.0f - f[0];
+    float wy = ((k >> 1) & 1) ? f[1] : 1.0f - f[1];
+    float wz = ((k >> 2) & 1) ? f[2] : 1.0f - f[2];
+    c.w[k] = wx * wy * wz;
+  }
+}
+
+}  // namespace romap

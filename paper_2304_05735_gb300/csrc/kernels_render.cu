@@ -186,9 +186,14 @@ void launch_composite(int mode, const GridParams& g, const BatchDesc& b, RayBuf 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int write_half) {
   const ObjectDev& ob = b.objs[b.slot[blockIdx.y]];
-  const double t = (double)ob.step;
-  const float c1 = (float)(1.0 / (1.0 - pow((double)g.beta1, t)));
-  const float c2 = (float)(1.0 / (1.0 - pow((double)g.beta2, t)));
+  __shared__ float s_c[2];
+  if (threadIdx.x == 0) {  // bias corrections 1/(1 - beta^t), once per block
+    const double t = (double)ob.step;
+    s_c[0] = (float)(1.0 / (1.0 - pow((double)g.beta1, t)));
+    s_c[1] = (float)(1.0 / (1.0 - pow((double)g.beta2, t)));
+  }
+  __syncthreads();
+  const float c1 = s_c[0], c2 = s_c[1];
   const float b1 = g.beta1, b2 = g.beta2, lr = g.lr, eps = g.eps;
   const float ob1 = 1.0f - b1, ob2 = 1.0f - b2;
   float4* P = reinterpret_cast<float4*>(ob.params);
@@ -228,8 +233,8 @@ void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaSt
   if (b.n <= 0) return;
   int64_t n4 = g.n_params_pad / 4;
   int chunks = (int)((n4 + 255) / 256);
-  int max_chunks = 2048 / (b.n < 1 ? 1 : b.n) + 1;
-  if (max_chunks < 8) max_chunks = 8;
+  int max_chunks = 8192 / (b.n < 1 ? 1 : b.n) + 1;  // about 8k blocks in all: enough loads in flight for HBM
+  if (max_chunks < 16) max_chunks = 16;
   if (chunks > max_chunks) chunks = max_chunks;
   k_adam<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, write_half);
   k_advance_step<<<(b.n + 127) / 128, 128, 0, stream>>>(b);

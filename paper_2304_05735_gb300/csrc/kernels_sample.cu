@@ -5,6 +5,7 @@
 // The FP32 arithmetic of this stage is written operation by operation with
 // round-to-nearest intrinsics (no contraction into FMA) in one fixed order,
 // so that sample positions and hash indices are reproducible bit for bit.
+#include "device_common.cuh"
 #include "romap_internal.cuh"
 
 namespace romap {
@@ -96,69 +97,6 @@ void launch_transform_rays(const float* o_in, const float* d_in, const float* rg
   int64_t blocks = (n + 255) / 256;
   k_transform_rays<<<(unsigned)blocks, 256, 0, stream>>>(o_in, d_in, rgb_in, depth_in, cls_in, n, object_frame, tx,
                                                          ty, tz, cz, sz, o_out, d_out, rgb_out, depth_out, cls_out);
-}
-
-// ---------------------------------------------------------------------------
-// Ray/box slab test (box [-half, half]); returns hit.
-// ---------------------------------------------------------------------------
-__device__ inline bool slab(const float o[3], const float d[3], const float half[3], float& tn, float& tf) {
-  float t0 = 0.0f, t1 = 0.0f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float lo = -half[a], hi = half[a];
-    float inv = __fdiv_rn(1.0f, d[a]);
-    float ta = __fmul_rn(__fsub_rn(lo, o[a]), inv);
-    float tb = __fmul_rn(__fsub_rn(hi, o[a]), inv);
-    float mn = fminf(ta, tb), mx = fmaxf(ta, tb);
-    t0 = (a == 0) ? mn : fmaxf(t0, mn);
-    t1 = (a == 0) ? mx : fminf(t1, mx);
-  }
-  tn = fmaxf(t0, 0.0f);
-  tf = t1;
-  return t1 > tn;
-}
-
-__device__ inline bool occupied(const uint64_t* occ, float x, float y, float z, const float half[3],
-                                const float inv_ext[3]) {
-  if (!occ) return true;
-  float p[3] = {x, y, z};
-  uint32_t c[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float u = fminf(fmaxf(__fmul_rn(__fsub_rn(p[a], -half[a]), inv_ext[a]), 0.0f), 1.0f);
-    int ci = (int)__fmul_rn(u, 64.0f);
-    c[a] = (uint32_t)(ci > 63 ? 63 : ci);
-  }
-  uint32_t bit = c[0] + 64u * c[1] + 4096u * c[2];
-  return (__ldg(occ + (bit >> 6)) >> (bit & 63u)) & 1ull;
-}
-
-// Stratified candidates t_i = t_near + (i + u_i) dt_N, delta_i = t_{i+1} - t_i
-// (last: t_far - t_{N-1}), x_i = o + t_i d; f(i, t, delta, x, y, z, live).
-template <class Fn>
-__device__ inline void for_candidates(const float o[3], const float d[3], float tn, float tf, int N, uint32_t k0,
-                                      uint32_t k1, uint32_t step, uint32_t slot, int jitter, const uint64_t* occ,
-                                      const float half[3], const float inv_ext[3], Fn f) {
-  float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
-  U4 rnd = {0, 0, 0, 0};
-  auto t_of = [&](int i) -> float {
-    float u = 0.5f;
-    if (jitter) {
-      if ((i & 3) == 0) rnd = philox(step, slot, kPurposeJitter, (uint32_t)i >> 2, k0, k1);
-      u = u01(u4_word(rnd, i & 3));
-    }
-    return __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, u), step_len));
-  };
-  float t_cur = t_of(0);
-  for (int i = 0; i < N; ++i) {
-    float t_next = (i + 1 < N) ? t_of(i + 1) : tf;
-    float dt = __fsub_rn(t_next, t_cur);
-    float x = __fadd_rn(o[0], __fmul_rn(t_cur, d[0]));
-    float y = __fadd_rn(o[1], __fmul_rn(t_cur, d[1]));
-    float z = __fadd_rn(o[2], __fmul_rn(t_cur, d[2]));
-    f(i, t_cur, dt, x, y, z, occupied(occ, x, y, z, half, inv_ext));
-    t_cur = t_next;
-  }
 }
 
 // Block-wide exclusive scan of 256 values.
@@ -346,7 +284,8 @@ __global__ void __launch_bounds__(1024) k_scan(BatchDesc b, uint32_t* block_sums
     uint32_t n_tiles = (cnt + kTile - 1) / kTile;
     uint32_t pad = n_tiles * kTile - cnt;
     int64_t start = (int64_t)s_tiles[i] * kTile + cnt;
-    for (uint32_t j = lane; j < pad; j += 32) S.ray[start + j] = kNoRay;
+    if (S.ray)
+      for (uint32_t j = lane; j < pad; j += 32) S.ray[start + j] = kNoRay;
   }
   if (threadIdx.x == 0) {
     totals[0] = (int32_t)all;

@@ -1,0 +1,778 @@
+// Mixed-precision training step on the 5th-generation tensor cores: one fused kernel per tile of 128 sample
+// slots that holds whole rays (slots per ray P = next power of two >= N, P <= 128).
+//
+// Per tile, in one CTA of 128 threads (thread s <-> sample slot s <-> TMEM lane s):
+//   1. sample positions of the slot (same FP32 operations as the sampling kernels: bit-identical),
+//   2. multiresolution hash encoding gathered from the FP16 copy of the table, interpolated in FP32,
+//      stored as BF16 (the A operand of the first layer),
+//   3. the five MLP layers (Sec. V; hidden 64) as tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM),
+//      each followed by an epilogue that reads its row from TMEM, applies the activation and writes the
+//      next BF16 operand row to shared memory,
+//   4. volume rendering (Eq. 6), the losses of Eq. 7-11 and the compositing adjoint, one warp per ray,
+//   5. the backward: per layer one GEMM for the input gradient (dX = dY W: A = dY K-major, B = W read
+//      MN-major from the forward copy) and one for the weight gradient (dW^T = X^T dY over the 128 samples:
+//      both operands read MN-major from the activation buffers, M padded to 128), the latter accumulated in
+//      TMEM across all tiles of the same object and added to the FP32 gradient once per object change,
+//   6. the hash-gradient scatter (FP32 vector atomics into the FP32 gradient of the table).
+// The transmittance scan, the losses and every accumulation stay in FP32; Adam keeps FP32 masters and
+// refreshes the FP16 table copy.
+//
+// Shared-memory operands use the canonical no-swizzle core-matrix layout (8 rows x 16 bytes per core
+// matrix): for a K-major [R rows][K] buffer, element (r, k) sits at (r/8)*(K/8)*128 + (k/8)*128 +
+// (r%8)*16 + (k%8)*2 bytes; the descriptor strides are LBO = 128 (between 8-column groups along K) and
+// SBO = (K/8)*128 (between 8-row groups).  The same buffer read as an MN-major operand (MN = its columns,
+// K = its rows) has LBO = (K/8)*128 and SBO = 128.
+//
+// Every wait on an mbarrier is bounded; on time-out the kernel records ROMAP_ERR_TIMEOUT in the status
+// word, waits (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "device_common.cuh"
+#include "romap_internal.cuh"
+
+namespace romap {
+namespace {
+
+constexpr int kT = 128;           // samples per tile (MMA M)
+constexpr int kTcThreads = 128;   // one warpgroup
+constexpr int kTmemCols = 512;
+// TMEM columns: weight-gradient accumulators, then the per-layer temporary
+constexpr uint32_t kColDW1 = 0, kColDW2 = 64, kColDW3 = 80, kColDW4 = 144, kColDW5 = 208, kColTmp = 256;
+constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// K-major operand: [rows][K] buffer; K-step kk covers columns 16 kk .. 16 kk + 15
+__device__ __forceinline__ uint64_t desc_k(const void* buf, int K, int kk) {
+  return make_desc(smem_u32(buf) + (uint32_t)kk * 256u, 128u, (uint32_t)(K / 8) * 128u);
+}
+// MN-major view of a K-major [rows][F] buffer: MN = its F columns, K = its rows; K-step kk covers rows 16 kk ..
+__device__ __forceinline__ uint64_t desc_mn(const void* buf, int F, int kk) {
+  return make_desc(smem_u32(buf) + (uint32_t)kk * 2u * (uint32_t)(F / 8) * 128u, (uint32_t)(F / 8) * 128u, 128u);
+}
+// instruction descriptor, kind::f16: BF16 A and B, FP32 D
+__host__ __device__ constexpr uint32_t idesc(int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  }
+  return done != 0;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32 w .. 32 w + 31)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of element (r, k) in a K-major [rows][K] BF16 buffer
+__device__ __forceinline__ uint32_t kmaj(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+// row r, 8 columns starting at 8c, packed as BF16
+__device__ __forceinline__ void store8(unsigned char* buf, int r, int c, int K, const float* v) {
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+  uint4 q;
+  q.x = *reinterpret_cast<uint32_t*>(&p0); q.y = *reinterpret_cast<uint32_t*>(&p1);
+  q.z = *reinterpret_cast<uint32_t*>(&p2); q.w = *reinterpret_cast<uint32_t*>(&p3);
+  *reinterpret_cast<uint4*>(buf + kmaj(r, 8 * c, K)) = q;
+}
+__device__ __forceinline__ void load8(const unsigned char* buf, int r, int c, int K, float* v) {
+  uint4 q = *reinterpret_cast<const uint4*>(buf + kmaj(r, 8 * c, K));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float2 f = __bfloat1622float2(h[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+template <int LFP>
+struct TcSmem {
+  // weights (B operands of the forward), K-major BF16 [out][in]
+  __align__(128) unsigned char w1[kH * LFP * 2];
+  __align__(128) unsigned char w2[16 * kH * 2];
+  __align__(128) unsigned char w3[kH * 32 * 2];
+  __align__(128) unsigned char w4[kH * kH * 2];
+  __align__(128) unsigned char w5[16 * kH * 2];
+  // activations (A operands), K-major BF16 [128 samples][features]; kept contiguous and in this order: the
+  // MN-major views of the weight-gradient GEMMs read up to 2 KB past a buffer (rows >= its feature count of
+  // the padded M = 128), which lands in the next buffer and only feeds TMEM rows that are never read.
+  __align__(128) unsigned char E[kT * LFP * 2];
+  __align__(128) unsigned char H1[kT * kH * 2];
+  __align__(128) unsigned char CIN[kT * 32 * 2];
+  __align__(128) unsigned char H2[kT * kH * 2];
+  __align__(128) unsigned char H3[kT * kH * 2];
+  __align__(128) unsigned char DL[kT * 16 * 2];  // dL/dlogit, then dL/d(density outputs)
+  float px[3][kT];
+  float t[kT];
+  float dt[kT];
+  float sig[kT];
+  float o0[kT];
+  float rgb[3][kT];
+  float dsig[kT];
+  float drgb[3][kT];
+  int valid[kT];
+  __align__(8) uint64_t mbar;
+  uint32_t tmem_base;
+  int fail;
+};
+
+template <int LFP>
+__device__ void load_weights(TcSmem<LFP>& sm, const GridParams& g, const float* __restrict__ P) {
+  const int t = threadIdx.x;
+  for (int i = t; i < kH * LFP; i += kTcThreads) {
+    int o = i / LFP, k = i % LFP;
+    float v = k < g.LF ? P[g.mlp_off[0] + o * g.LF + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w1 + kmaj(o, k, LFP)) = __float2bfloat16_rn(v);
+  }
+  for (int i = t; i < 16 * kH; i += kTcThreads) {
+    int o = i / kH, k = i % kH;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w2 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[1] + i]);
+  }
+  for (int i = t; i < kH * 32; i += kTcThreads) {
+    int o = i / 32, k = i % 32;
+    float v = k < g.cin ? P[g.mlp_off[2] + o * g.cin + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w3 + kmaj(o, k, 32)) = __float2bfloat16_rn(v);
+  }
+  for (int i = t; i < kH * kH; i += kTcThreads) {
+    int o = i / kH, k = i % kH;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w4 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[3] + i]);
+  }
+  for (int i = t; i < 16 * kH; i += kTcThreads) {
+    int o = i / kH, k = i % kH;
+    float v = o < 3 ? P[g.mlp_off[4] + o * kH + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w5 + kmaj(o, k, kH)) = __float2bfloat16_rn(v);
+  }
+}
+
+// Adds the TMEM weight-gradient accumulators of one object to its FP32 gradient (rows = input features).
+template <int LFP>
+__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad) {
+  const int t = threadIdx.x, w = t >> 5;
+  if (w >= 2) return;  // rows 0..63 live in the lanes of warps 0 and 1
+  const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);
+  const int row = t;
+  float v[16];
+  // dW1^T: rows = encoding features (LF), 64 columns (hidden units)
+  for (int c = 0; c < kH; c += 16) {
+    tmem_ld16(lane_base + kColDW1 + c, v);
+    tmem_wait_ld();
+    if (row < g.LF)
+      for (int j = 0; j < 16; ++j)
+        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[0] + (c + j) * g.LF + row, v[j]);
+  }
+  tmem_ld16(lane_base + kColDW2, v);  // dW2^T: rows = hidden (64), 16 columns (density outputs)
+  tmem_wait_ld();
+  for (int j = 0; j < 16; ++j)
+    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[1] + j * kH + row, v[j]);
+  for (int c = 0; c < kH; c += 16) {  // dW3^T: rows = colour inputs (cin), 64 columns
+    tmem_ld16(lane_base + kColDW3 + c, v);
+    tmem_wait_ld();
+    if (row < g.cin)
+      for (int j = 0; j < 16; ++j)
+        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[2] + (c + j) * g.cin + row, v[j]);
+  }
+  for (int c = 0; c < kH; c += 16) {  // dW4^T: rows = hidden (64), 64 columns
+    tmem_ld16(lane_base + kColDW4 + c, v);
+    tmem_wait_ld();
+    for (int j = 0; j < 16; ++j)
+      if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[3] + (c + j) * kH + row, v[j]);
+  }
+  tmem_ld16(lane_base + kColDW5, v);  // dW5^T: rows = hidden (64), columns 0..2 real
+  tmem_wait_ld();
+  for (int j = 0; j < 3; ++j)
+    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[4] + j * kH + row, v[j]);
+}
+
+__device__ __forceinline__ float warp_incl_prefix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+__device__ __forceinline__ float warp_incl_suffix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float n = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v += n;
+  }
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Eq. 6 + Eq. 7-11 + adjoint for one ray whose samples occupy slots [base, base + P) of the tile.
+template <int LFP>
+__device__ void composite_ray(TcSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
+                              int bi, int64_t r, int base, int P, float invB, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
+  float carry = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dh = 0.f, ssum = 0.f;
+  for (int c = 0; c < P; c += 32) {
+    const int j = c + lane;
+    const bool in = j < P && sm.valid[base + j];
+    const int s = base + (j < P ? j : 0);
+    const float sg = in ? sm.sig[s] : 0.f, dt = in ? sm.dt[s] : 0.f, tt = in ? sm.t[s] : 0.f;
+    const float sd = sg * dt;
+    const float incl = warp_incl_prefix(sd, lane);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.f;
+    const float Pf = carry + excl;
+    const float w = expf(-Pf) * (-expm1f(-sd));
+    if (in) {
+      C0 = fmaf(w, sm.rgb[0][s], C0);
+      C1 = fmaf(w, sm.rgb[1][s], C1);
+      C2 = fmaf(w, sm.rgb[2][s], C2);
+      Dh = fmaf(w, tt, Dh);
+      ssum += sg;
+    }
+    if (j < P) sm.dsig[s] = Pf;  // exclusive prefix, consumed by the adjoint below
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  C0 = warp_sum(C0); C1 = warp_sum(C1); C2 = warp_sum(C2); Dh = warp_sum(Dh); ssum = warp_sum(ssum);
+  const float Tend = expf(-carry);
+  const float Ch0 = fmaf(Tend, bg0, C0), Ch1 = fmaf(Tend, bg1, C1), Ch2 = fmaf(Tend, bg2, C2);
+  if (lane == 0) {
+    float* o = R.out + 6 * r;
+    o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = -expm1f(-carry); o[5] = ssum;
+  }
+  // losses of Eq. 7-11 (every term divided by the batch size B)
+  const int cls = R.cls[r];
+  float loss = 0.f, l_rgb = 0.f, l_rr = 0.f, l_dep = 0.f, l_den = 0.f;
+  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gdir = 0.f;
+  if (cls != kClsOccluder) {
+    const float t0 = cls == kClsObject ? R.rgb[3 * r] : bg0;
+    const float t1 = cls == kClsObject ? R.rgb[3 * r + 1] : bg1;
+    const float t2 = cls == kClsObject ? R.rgb[3 * r + 2] : bg2;
+    const float e0 = Ch0 - t0, e1 = Ch1 - t1, e2 = Ch2 - t2;
+    const float sq = e0 * e0 + e1 * e1 + e2 * e2;
+    loss += sq;
+    if (cls == kClsObject) l_rgb = sq; else l_rr = sq;
+    gC0 = 2.f * e0 * invB; gC1 = 2.f * e1 * invB; gC2 = 2.f * e2 * invB;
+    const float dep = R.depth[r];
+    if (isfinite(dep)) {
+      const float e = Dh - dep;
+      loss += g.lambda1 * fabsf(e);
+      l_dep = fabsf(e);
+      gD = g.lambda1 * (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) * invB;
+    }
+    if (cls == kClsBackground) {
+      loss += g.lambda2 * ssum;
+      l_den = ssum;
+      gdir = g.lambda2 * invB;
+    }
+  }
+  if (lane == 0) {
+    float* L = dyn[bi].loss;
+    atomicAdd(L + 0, loss);
+    if (l_rgb != 0.f) atomicAdd(L + 1, l_rgb);
+    if (l_rr != 0.f) atomicAdd(L + 2, l_rr);
+    if (l_dep != 0.f) atomicAdd(L + 3, l_dep);
+    if (l_den != 0.f) atomicAdd(L + 4, l_den);
+    if (!isfinite(loss) && status) atomicOr(status, 1);
+  }
+  // adjoint, chunks in reverse order
+  float SC0 = 0.f, SC1 = 0.f, SC2 = 0.f, SD = 0.f;
+  const float bgterm = Tend * (gC0 * bg0 + gC1 * bg1 + gC2 * bg2);
+  for (int c = ((P - 1) / 32) * 32; c >= 0; c -= 32) {
+    const int j = c + lane;
+    const bool in = j < P && sm.valid[base + j];
+    const int s = base + (j < P ? j : 0);
+    const float sg = in ? sm.sig[s] : 0.f, dt = in ? sm.dt[s] : 0.f, tt = in ? sm.t[s] : 0.f;
+    const float Pf = (j < P) ? sm.dsig[s] : 0.f;
+    const float c0 = in ? sm.rgb[0][s] : 0.f, c1 = in ? sm.rgb[1][s] : 0.f, c2 = in ? sm.rgb[2][s] : 0.f;
+    const float sd = sg * dt;
+    const float Tn = expf(-(Pf + sd));
+    const float w = in ? expf(-Pf) * (-expm1f(-sd)) : 0.f;
+    float s0 = warp_incl_suffix(w * c0, lane), s1 = warp_incl_suffix(w * c1, lane);
+    float s2 = warp_incl_suffix(w * c2, lane), s3 = warp_incl_suffix(w * tt, lane);
+    float e0 = __shfl_down_sync(0xffffffffu, s0, 1), e1 = __shfl_down_sync(0xffffffffu, s1, 1);
+    float e2 = __shfl_down_sync(0xffffffffu, s2, 1), e3 = __shfl_down_sync(0xffffffffu, s3, 1);
+    if (lane == 31) e0 = e1 = e2 = e3 = 0.f;
+    float gs = gC0 * (Tn * c0 - (SC0 + e0)) + gC1 * (Tn * c1 - (SC1 + e1)) + gC2 * (Tn * c2 - (SC2 + e2)) - bgterm;
+    gs += gD * (Tn * tt - (SD + e3));
+    gs = dt * gs + gdir;
+    if (j < P) {
+      sm.dsig[s] = in ? gs : 0.f;
+      sm.drgb[0][s] = in ? gC0 * w : 0.f;
+      sm.drgb[1][s] = in ? gC1 * w : 0.f;
+      sm.drgb[2][s] = in ? gC2 * w : 0.f;
+    }
+    SC0 += __shfl_sync(0xffffffffu, s0, 0);
+    SC1 += __shfl_sync(0xffffffffu, s1, 0);
+    SC2 += __shfl_sync(0xffffffffu, s2, 0);
+    SD += __shfl_sync(0xffffffffu, s3, 0);
+  }
+}
+
+template <int LFP>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int P, int total_tiles) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TcSmem<LFP>& sm = *reinterpret_cast<TcSmem<LFP>*>(smem_raw);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int tile_lo = (int)((int64_t)total_tiles * blockIdx.x / gridDim.x);
+  const int tile_hi = (int)((int64_t)total_tiles * (blockIdx.x + 1) / gridDim.x);
+  if (tile_lo >= tile_hi) return;
+
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sm.fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&sm.tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tm = sm.tmem_base;
+  const uint32_t my_lane = tm + ((uint32_t)(32 * warp) << 16);
+  const uint32_t tmp = my_lane + kColTmp;
+  uint32_t phase = 0;
+  bool ok = true;
+  const int rays_per_tile = kT / P;
+  const int N = g.n_samples;
+
+  // issue helpers (thread 0) ---------------------------------------------------------------------------
+  auto sync_then_issue = [&]() {  // make every thread's shared writes and TMEM reads visible to the MMAs
+    fence_async_smem();
+    tc_before();
+    __syncthreads();
+    tc_after();
+  };
+  auto wait_mma = [&]() -> bool {  // all threads: wait for the last commit
+    bool d = mbar_wait(&sm.mbar, phase);
+    phase ^= 1u;
+    if (!d) atomicExch(&sm.fail, 1);
+    __syncthreads();
+    tc_after();
+    return sm.fail == 0;
+  };
+
+  int bi = -1;
+  const ObjectDev* ob = nullptr;
+  uint32_t acc_dw = 0;  // 0 for the first weight-gradient GEMM of an object
+  for (int tile = tile_lo; tile < tile_hi && ok; ++tile) {
+    int nbi = bi < 0 ? 0 : bi;
+    while (nbi + 1 < b.n && tile >= b.tile_base[nbi + 1]) ++nbi;
+    if (nbi != bi) {
+      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
+      bi = nbi;
+      ob = &b.objs[b.slot[bi]];
+      load_weights<LFP>(sm, g, ob->params);
+      acc_dw = 0;
+    }
+    const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
+    const float invB = 1.0f / (float)n_rays_obj;
+    const int tile_local = tile - b.tile_base[bi];
+    // ---- 1. sample of this thread's slot ----------------------------------------------------------------
+    {
+      const int rl = tile_local * rays_per_tile + t / P;
+      const int i = t % P;
+      bool valid = rl < n_rays_obj && i < N;
+      float x = 0.f, y = 0.f, z = 0.f, ti = 0.f, dti = 0.f;
+      if (valid) {
+        const int64_t r = b.ray_base[bi] + rl;
+        const float tn = R.tn[r], tf = R.tf[r];
+        valid = tf > tn;
+        if (valid) {
+          const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
+          const uint32_t step = ob->step;
+          ti = candidate_t(tn, step_len, i, ob->key0, ob->key1, step, (uint32_t)rl, 1);
+          const float tnext = (i + 1 < N) ? candidate_t(tn, step_len, i + 1, ob->key0, ob->key1, step, (uint32_t)rl, 1) : tf;
+          dti = __fsub_rn(tnext, ti);
+          x = __fadd_rn(R.o[3 * r], __fmul_rn(ti, R.d[3 * r]));
+          y = __fadd_rn(R.o[3 * r + 1], __fmul_rn(ti, R.d[3 * r + 1]));
+          z = __fadd_rn(R.o[3 * r + 2], __fmul_rn(ti, R.d[3 * r + 2]));
+          valid = occupied(ob->occ, x, y, z, ob->half, ob->inv_ext);
+        }
+      }
+      sm.valid[t] = valid ? 1 : 0;
+      sm.px[0][t] = x; sm.px[1][t] = y; sm.px[2][t] = z;
+      sm.t[t] = ti;
+      sm.dt[t] = dti;
+      // ---- 2. hash encoding from the FP16 table -> E row (BF16) -------------------------------------------
+      const float p[3] = {x, y, z};
+      const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
+      float e[LFP];
+#pragma unroll
+      for (int k = 0; k < LFP; ++k) e[k] = 0.f;
+      if (valid) {
+#pragma unroll
+        for (int l = 0; l < LFP / 2; ++l) {
+          if (l < g.L) {
+            Corners c;
+            level_corners(g, l, p, ob->half, ob->inv_ext, c);
+            float2 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __half22float2(__ldg(tab + g.off[l] + c.idx[k]));
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              a0 = fmaf(c.w[k], v[k].x, a0);
+              a1 = fmaf(c.w[k], v[k].y, a1);
+            }
+            e[2 * l] = a0;
+            e[2 * l + 1] = a1;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < LFP / 8; ++c) store8(sm.E, t, c, LFP, e + 8 * c);
+    }
+    sync_then_issue();
+    // ---- 3. forward layers -------------------------------------------------------------------------------
+    // L1: H1 = relu(E W1^T)
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < LFP / 16; ++kk)
+        mma(kColTmp + tm, desc_k(sm.E, LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0), kk > 0);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(tmp + 16 * c, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+        store8(sm.H1, t, 2 * c, kH, v);
+        store8(sm.H1, t, 2 * c + 1, kH, v + 8);
+      }
+    }
+    sync_then_issue();
+    // L2: OUT = H1 W2^T (16 outputs)
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H1, kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0), kk > 0);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {
+      float v[16];
+      tmem_ld16(tmp, v);
+      tmem_wait_ld();
+      const float o0 = v[0];
+      sm.o0[t] = o0;
+      sm.sig[t] = expf(fminf(fmaxf(o0, -15.f), 15.f));
+      // colour input: 15 geometry features, the view direction, zero padding to 32
+      float cin[32];
+#pragma unroll
+      for (int j = 0; j < 15; ++j) cin[j] = v[1 + j];
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+      if (g.dir_dims == 3 && sm.valid[t]) {
+        const int64_t r = b.ray_base[bi] + tile_local * rays_per_tile + t / P;
+        d0 = R.d[3 * r]; d1 = R.d[3 * r + 1]; d2 = R.d[3 * r + 2];
+      }
+      cin[15] = d0; cin[16] = d1; cin[17] = d2;
+#pragma unroll
+      for (int j = 18; j < 32; ++j) cin[j] = 0.f;
+      if (g.dir_dims == 0) cin[15] = cin[16] = cin[17] = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) store8(sm.CIN, t, c, 32, cin + 8 * c);
+    }
+    sync_then_issue();
+    // L3: H2 = relu(CIN W3^T)
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) mma(kColTmp + tm, desc_k(sm.CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0), kk > 0);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(tmp + 16 * c, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+        store8(sm.H2, t, 2 * c, kH, v);
+        store8(sm.H2, t, 2 * c + 1, kH, v + 8);
+      }
+    }
+    sync_then_issue();
+    // L4: H3 = relu(H2 W4^T)
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(tmp + 16 * c, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+        store8(sm.H3, t, 2 * c, kH, v);
+        store8(sm.H3, t, 2 * c + 1, kH, v + 8);
+      }
+    }
+    sync_then_issue();
+    // L5: logits = H3 W5^T (3 of 16 outputs)
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0), kk > 0);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {
+      float v[16];
+      tmem_ld16(tmp, v);
+      tmem_wait_ld();
+      sm.rgb[0][t] = 1.0f / (1.0f + expf(-v[0]));
+      sm.rgb[1][t] = 1.0f / (1.0f + expf(-v[1]));
+      sm.rgb[2][t] = 1.0f / (1.0f + expf(-v[2]));
+    }
+    __syncthreads();
+    // ---- 4. compositing, losses, adjoint (one warp per ray) ------------------------------------------------
+    for (int j = warp; j < rays_per_tile; j += kTcThreads / 32) {
+      const int rl = tile_local * rays_per_tile + j;
+      if (rl < n_rays_obj) composite_ray<LFP>(sm, g, b, R, dyn, bi, b.ray_base[bi] + rl, j * P, P, invB, status);
+    }
+    __syncthreads();
+    // ---- 5. backward ----------------------------------------------------------------------------------------
+    float dpre;
+    {
+      const bool valid = sm.valid[t];
+      float dl[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) dl[k] = 0.f;
+      if (valid) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float c = sm.rgb[k][t];
+          dl[k] = sm.drgb[k][t] * c * (1.f - c);
+        }
+      }
+      const float o0 = sm.o0[t];
+      dpre = (valid && o0 >= -15.f && o0 <= 15.f) ? sm.dsig[t] * sm.sig[t] : 0.f;
+      store8(sm.DL, t, 0, 16, dl);
+      store8(sm.DL, t, 1, 16, dl + 8);
+    }
+    sync_then_issue();
+    // dH3 = DL W5 ; dW5^T += H3^T DL
+    if (t == 0) {
+      mma(kColTmp + tm, desc_k(sm.DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1), 0);
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk)
+        mma(kColDW5 + tm, desc_mn(sm.H3, kH, kk), desc_mn(sm.DL, 16, kk), idesc(16, 1, 1), kk > 0 ? 1u : acc_dw);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {  // dH3 masked by relu'(H3), in place of H3
+      float v[16], h[16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(tmp + 16 * c, v);
+        tmem_wait_ld();
+        load8(sm.H3, t, 2 * c, kH, h);
+        load8(sm.H3, t, 2 * c + 1, kH, h + 8);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
+        store8(sm.H3, t, 2 * c, kH, v);
+        store8(sm.H3, t, 2 * c + 1, kH, v + 8);
+      }
+    }
+    sync_then_issue();
+    // dH2 = dH3 W4 ; dW4^T += H2^T dH3
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1), kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk)
+        mma(kColDW4 + tm, desc_mn(sm.H2, kH, kk), desc_mn(sm.H3, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {
+      float v[16], h[16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(tmp + 16 * c, v);
+        tmem_wait_ld();
+        load8(sm.H2, t, 2 * c, kH, h);
+        load8(sm.H2, t, 2 * c + 1, kH, h + 8);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
+        store8(sm.H2, t, 2 * c, kH, v);
+        store8(sm.H2, t, 2 * c + 1, kH, v + 8);
+      }
+    }
+    sync_then_issue();
+    // dCIN = dH2 W3 (32 columns) ; dW3^T += CIN^T dH2
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1), kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk)
+        mma(kColDW3 + tm, desc_mn(sm.CIN, 32, kk), desc_mn(sm.H2, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {  // dOUT = [dsigma * sigma, dCIN[0..14]] into DL
+      float v[16], d[16];
+      tmem_ld16(tmp, v);
+      tmem_wait_ld();
+      d[0] = dpre;
+#pragma unroll
+      for (int j = 0; j < 15; ++j) d[1 + j] = v[j];
+      store8(sm.DL, t, 0, 16, d);
+      store8(sm.DL, t, 1, 16, d + 8);
+    }
+    sync_then_issue();
+    // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
+    if (t == 0) {
+      mma(kColTmp + tm, desc_k(sm.DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1), 0);
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk)
+        mma(kColDW2 + tm, desc_mn(sm.H1, kH, kk), desc_mn(sm.DL, 16, kk), idesc(16, 1, 1), kk > 0 ? 1u : acc_dw);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    {
+      float v[16], h[16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16(tmp + 16 * c, v);
+        tmem_wait_ld();
+        load8(sm.H1, t, 2 * c, kH, h);
+        load8(sm.H1, t, 2 * c + 1, kH, h + 8);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
+        store8(sm.H1, t, 2 * c, kH, v);
+        store8(sm.H1, t, 2 * c + 1, kH, v + 8);
+      }
+    }
+    sync_then_issue();
+    // dE = dH1 W1 (LFP columns) ; dW1^T += E^T dH1
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1), kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk)
+        mma(kColDW1 + tm, desc_mn(sm.E, LFP, kk), desc_mn(sm.H1, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = wait_mma())) break;
+    acc_dw = 1;
+    {  // ---- 6. scatter dL/dencoding into the FP32 table gradient ----
+      float de[LFP];
+#pragma unroll
+      for (int c = 0; c < LFP / 16; ++c) tmem_ld16(tmp + 16 * c, de + 16 * c);
+      tmem_wait_ld();
+      if (sm.valid[t]) {
+        const float p[3] = {sm.px[0][t], sm.px[1][t], sm.px[2][t]};
+        float2* gt = reinterpret_cast<float2*>(ob->grad);
+#pragma unroll
+        for (int l = 0; l < LFP / 2; ++l) {
+          const float d0 = de[2 * l], d1 = de[2 * l + 1];
+          if (l >= g.L || (d0 == 0.f && d1 == 0.f)) continue;
+          Corners c;
+          level_corners(g, l, p, ob->half, ob->inv_ext, c);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) atomicAdd(gt + g.off[l] + c.idx[k], make_float2(c.w[k] * d0, c.w[k] * d1));
+        }
+      }
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+  }
+  if (ok && bi >= 0) {
+    flush_dw<LFP>(tm, g, ob->grad);
+  } else if (!ok) {
+    if (t == 0 && status) atomicOr(status, 2);
+    mbar_wait(&sm.mbar, phase ^ 1u);  // bounded: let the MMAs still in flight finish before the columns are freed
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(kTmemCols));
+}
+
+template <int LFP>
+void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
+                 int total_tiles, int n_ctas, cudaStream_t stream) {
+  // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
+  // CTA never waits on another
+  int bytes = (int)sizeof(TcSmem<LFP>);
+  if (bytes < 116 * 1024) bytes = 116 * 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_tile_tc<LFP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr_set = true;
+  }
+  int grid = n_ctas < total_tiles ? n_ctas : total_tiles;
+  if (grid < 1) return;
+  k_tile_tc<LFP><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status, P, total_tiles);
+}
+
+}  // namespace
+
+void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
+                    int total_tiles, int n_ctas, cudaStream_t stream) {
+  if (g.LF <= 16) launch_tc_t<16>(g, b, dyn, r, status, P, total_tiles, n_ctas, stream);
+  else launch_tc_t<32>(g, b, dyn, r, status, P, total_tiles, n_ctas, stream);
+}
+
+// FP16 copy of the hash table (n_hash is even)
+__global__ void k_to_half(const float* __restrict__ src, __half2* __restrict__ dst, int64_t n2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __floats2half2_rn(src[2 * i], src[2 * i + 1]);
+}
+
+void launch_to_half(const float* params, uint16_t* table_h, int64_t n_hash, cudaStream_t stream) {
+  int64_t n2 = n_hash / 2;
+  int blocks = (int)((n2 + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) return;
+  k_to_half<<<blocks, 256, 0, stream>>>(params, reinterpret_cast<__half2*>(table_h), n2);
+}
+
+}  // namespace romap

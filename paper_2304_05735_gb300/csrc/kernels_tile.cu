@@ -13,6 +13,7 @@
 // object in registers and flushes them with one atomic add per weight per
 // object change, and scatters the encoding gradient into the hash-table
 // gradient with vector atomics (red.global.add.v2.f32).
+#include "device_common.cuh"
 #include "romap_internal.cuh"
 
 namespace romap {
@@ -154,46 +155,6 @@ __device__ inline void zero2(float (&g)[TO][TK]) {
   for (int i = 0; i < TO; ++i)
 #pragma unroll
     for (int j = 0; j < TK; ++j) g[i][j] = 0.0f;
-}
-
-// ---------------------------------------------------------------------------
-// Hash-grid corners of one level for an object-frame point (FP32, fixed
-// order): u = clamp((x + half) inv_ext, 0, 1), pos = u N_l, i0 =
-// min(floor(pos), N_l - 1), f = pos - i0; dense index x + y(N+1) + z(N+1)^2
-// or spatial hash (x * 1 ^ y * 2654435761 ^ z * 805459861) mod T.
-// ---------------------------------------------------------------------------
-struct Corners {
-  uint32_t idx[8];
-  float w[8];
-};
-
-__device__ inline void level_corners(const GridParams& g, int l, const float p[3], const float half[3],
-                                     const float inv_ext[3], Corners& c) {
-  int i0[3];
-  float f[3];
-  const int N = g.res[l];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float u = fminf(fmaxf(__fmul_rn(__fsub_rn(p[a], -half[a]), inv_ext[a]), 0.0f), 1.0f);
-    float pos = __fmul_rn(u, (float)N);
-    int i = (int)floorf(pos);
-    i = i > N - 1 ? N - 1 : i;
-    i0[a] = i;
-    f[a] = __fsub_rn(pos, (float)i);
-  }
-  const uint32_t n1 = (uint32_t)N + 1u;
-  const bool dense = g.dense[l];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    uint32_t cx = (uint32_t)(i0[0] + (k & 1));
-    uint32_t cy = (uint32_t)(i0[1] + ((k >> 1) & 1));
-    uint32_t cz = (uint32_t)(i0[2] + ((k >> 2) & 1));
-    c.idx[k] = dense ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) % g.T);
-    float wx = (k & 1) ? f[0] : 1.0f - f[0];
-    float wy = ((k >> 1) & 1) ? f[1] : 1.0f - f[1];
-    float wz = ((k >> 2) & 1) ? f[2] : 1.0f - f[2];
-    c.w[k] = wx * wy * wz;
-  }
 }
 
 // ---------------------------------------------------------------------------

@@ -230,28 +230,39 @@ romap_status ensure_workspace(romap_ctx* ctx, int64_t nr, int64_t ns, int64_t nb
   return ROMAP_OK;
 }
 
-// Batch arrays: slot[n], ray_base[n+1], block_base[n+1], block_obj[n_blocks].
+// Batch arrays: slot[n], ray_base[n+1], block_base[n+1], tile_base[n+1], block_obj[n_blocks].
 struct HostBatch {
   std::vector<int32_t> arr;
-  int n = 0, n_blocks = 0, n_rays = 0;
+  int n = 0, n_blocks = 0, n_rays = 0, n_tiles = 0;
 };
 
-void build_batch(const std::vector<int32_t>& slots, const std::vector<int32_t>& rays, HostBatch* hb) {
+// Slots per ray of the fused mixed-precision kernel: the next power of two >= N (so rays never straddle tiles).
+int slots_per_ray(int N) {
+  int P = 1;
+  while (P < N) P <<= 1;
+  return P;
+}
+
+void build_batch(const std::vector<int32_t>& slots, const std::vector<int32_t>& rays, HostBatch* hb, int P = 0) {
   int n = (int)slots.size();
   hb->n = n;
-  std::vector<int32_t> ray_base(n + 1, 0), block_base(n + 1, 0), block_obj;
+  std::vector<int32_t> ray_base(n + 1, 0), block_base(n + 1, 0), tile_base(n + 1, 0), block_obj;
   for (int i = 0; i < n; ++i) {
     ray_base[i + 1] = ray_base[i] + rays[i];
     int nb = (rays[i] + 255) / 256;
     block_base[i + 1] = block_base[i] + nb;
     for (int k = 0; k < nb; ++k) block_obj.push_back(i);
+    int tiles = P > 0 ? (int)(((int64_t)rays[i] * P + kTile - 1) / kTile) : 0;
+    tile_base[i + 1] = tile_base[i] + tiles;
   }
   hb->n_rays = ray_base[n];
   hb->n_blocks = block_base[n];
+  hb->n_tiles = tile_base[n];
   hb->arr.clear();
   hb->arr.insert(hb->arr.end(), slots.begin(), slots.end());
   hb->arr.insert(hb->arr.end(), ray_base.begin(), ray_base.end());
   hb->arr.insert(hb->arr.end(), block_base.begin(), block_base.end());
+  hb->arr.insert(hb->arr.end(), tile_base.begin(), tile_base.end());
   hb->arr.insert(hb->arr.end(), block_obj.begin(), block_obj.end());
 }
 
@@ -263,7 +274,8 @@ BatchDesc desc_from(const HostBatch& hb, const int32_t* dev, ObjectDev* objs) {
   b.slot = dev;
   b.ray_base = dev + hb.n;
   b.block_base = dev + 2 * hb.n + 1;
-  b.block_obj = dev + 3 * hb.n + 2;
+  b.tile_base = dev + 3 * hb.n + 2;
+  b.block_obj = dev + 4 * hb.n + 3;
   b.objs = objs;
   b.jitter = 1;
   return b;
@@ -443,6 +455,18 @@ romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBu
 
 int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
 
+// Sampling stage of the mixed path: ray draw + slab + live counts, and the per-object scan (live-sample counter,
+// loss reset).  Samples are formed inside the fused kernel, so nothing is compacted.
+romap_status run_sampling_mixed(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBuf S, uint32_t* block_sums,
+                                BatchDyn* dyn, int32_t* totals) {
+  PhaseScope ps(ctx, 0, 2);
+  launch_ray_setup(ctx->g, b, R, block_sums, ctx->stream);
+  launch_scan(ctx->g, b, block_sums, dyn, totals, S, ctx->live_counter, ctx->stream);
+  ctx->launches += 2;
+  CUDA_TRY(cudaGetLastError());
+  return ROMAP_OK;
+}
+
 // forward + loss + backward of a batch (no Adam)
 romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchDesc* out_b) {
   std::vector<int32_t> slots(ids.begin(), ids.end()), rays(ids.size());
@@ -450,26 +474,36 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
     rays[i] = ctx->objs_host[ids[i]].n_rays;
     if (rays[i] < 1) return fail(ROMAP_ERR_BAD_STATE, "object %d has no training rays", ids[i]);
   }
+  const bool mixed = ctx->cfg.precision == ROMAP_PREC_MIXED_BF16;
+  const int P = slots_per_ray(ctx->g.n_samples);
   HostBatch hb;
-  build_batch(slots, rays, &hb);
-  int64_t ns = (int64_t)hb.n_rays * ctx->g.n_samples + (int64_t)hb.n * kTile;
+  build_batch(slots, rays, &hb, mixed ? P : 0);
+  int64_t ns = mixed ? 0 : (int64_t)hb.n_rays * ctx->g.n_samples + (int64_t)hb.n * kTile;
   ROMAP_TRY(ensure_workspace(ctx, hb.n_rays, ns, hb.n_blocks, hb.n));
   BatchDesc b;
   ROMAP_TRY(upload_batch(ctx, hb, &b));
-  ROMAP_TRY(run_sampling(ctx, b, ctx->R, ctx->S, ctx->block_sums, ctx->dyn, ctx->totals, true));
-  {
-    PhaseScope ps(ctx, 1, 1);
-    launch_tile_mlp(0, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
-  }
-  {
-    PhaseScope ps(ctx, 2, 1);
-    launch_composite(1, ctx->g, b, ctx->R, ctx->S, ctx->dyn, ctx->status, ctx->stream);
-  }
-  {
+  if (mixed) {
+    SampleBuf none{};
+    ROMAP_TRY(run_sampling_mixed(ctx, b, ctx->R, none, ctx->block_sums, ctx->dyn, ctx->totals));
     PhaseScope ps(ctx, 3, 1);
-    launch_tile_mlp(1, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+    launch_tile_tc(ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, hb.n_tiles, tile_ctas(ctx), ctx->stream);
+    ctx->launches += 1;
+  } else {
+    ROMAP_TRY(run_sampling(ctx, b, ctx->R, ctx->S, ctx->block_sums, ctx->dyn, ctx->totals, true));
+    {
+      PhaseScope ps(ctx, 1, 1);
+      launch_tile_mlp(0, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+    }
+    {
+      PhaseScope ps(ctx, 2, 1);
+      launch_composite(1, ctx->g, b, ctx->R, ctx->S, ctx->dyn, ctx->status, ctx->stream);
+    }
+    {
+      PhaseScope ps(ctx, 3, 1);
+      launch_tile_mlp(1, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+    }
+    ctx->launches += 3;
   }
-  ctx->launches += 3;
   CUDA_TRY(cudaGetLastError());
   ctx->stats.steps += hb.n;
   ctx->stats.rays += hb.n_rays;
@@ -566,7 +600,8 @@ romap_status romap_init(const romap_config* cfg, void* cuda_stream, romap_ctx** 
   *out = nullptr;
   GridParams g;
   ROMAP_TRY(make_grid(cfg, &g));
-  if (cfg->precision == ROMAP_PREC_MIXED_BF16) return fail(ROMAP_ERR_UNSUPPORTED, "mixed precision is not built");
+  if (cfg->precision == ROMAP_PREC_MIXED_BF16 && cfg->n_samples > kTile)
+    return fail(ROMAP_ERR_UNSUPPORTED, "mixed precision needs n_samples <= %d", kTile);
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   cudaDeviceProp prop;
@@ -657,6 +692,10 @@ romap_status romap_create_object(romap_ctx* ctx, const romap_object_desc* d, int
   cudaMemsetAsync(o.v, 0, np * sizeof(float), ctx->stream);
   launch_init_params(ctx->g, o.params, (uint32_t)d->seed, (uint32_t)(d->seed >> 32), ctx->stream);
   ctx->launches += 1;
+  if (o.table_h) {
+    launch_to_half(o.params, o.table_h, ctx->g.n_hash, ctx->stream);
+    ctx->launches += 1;
+  }
   CUDA_TRY(cudaGetLastError());
   o.alive = true;
   ctx->objs[slot] = o;
@@ -911,6 +950,7 @@ romap_status romap_set_state(romap_ctx* ctx, int32_t id, const romap_state* in) 
   CUDA_TRY(cudaMemcpyAsync(o.m, in->adam_m, bytes, k, ctx->stream));
   CUDA_TRY(cudaMemcpyAsync(o.v, in->adam_v, bytes, k, ctx->stream));
   CUDA_TRY(cudaMemsetAsync(o.grad, 0, sizeof(float) * ctx->g.n_params_pad, ctx->stream));
+  if (o.table_h) launch_to_half(o.params, o.table_h, ctx->g.n_hash, ctx->stream);
   o.steps_done = in->step;
   ROMAP_TRY(sync_object(ctx, id));
   if (!(in->flags & ROMAP_DEVICE_PTR)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));

@@ -90,6 +90,7 @@ struct BatchDesc {
   const int32_t* ray_base;   // [n+1]
   const int32_t* block_base; // [n+1] blocks of 256 rays
   const int32_t* block_obj;  // [n_blocks] batch entry of each ray block
+  const int32_t* tile_base;  // [n+1] first fused-kernel tile of each entry (slots of P per ray, 128 per tile)
   int32_t n;
   int32_t n_blocks;
   int32_t n_rays;
@@ -184,5 +185,9 @@ void launch_sample_slots(const GridParams& g, int64_t n_rays, const RayBuf r, co
 void launch_split_outputs(const float* ray_out, int64_t n, float* rgb, float* depth, float* opacity,
                           cudaStream_t stream);
 int tile_kernel_smem_bytes(int LF);
+// Mixed precision: fused forward + compositing + backward on tensor cores; P slots per ray (power of two <= 128).
+void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
+                    int total_tiles, int n_ctas, cudaStream_t stream);
+void launch_to_half(const float* params, uint16_t* table_h, int64_t n_hash, cudaStream_t stream);
 
 }  // namespace romap

@@ -1,0 +1,112 @@
+"""Mixed-precision training step (FP16 table copy + FP32 masters, BF16 tcgen05 MLP, FP32 accumulation) against the
+FP64 oracle and against the FP32 path.  Tolerances: loss within 1e-3 relative of the oracle; gradients compared by
+relative L2 error and cosine; the measured errors are printed."""
+import numpy as np
+import pytest
+
+from oracle import romap_oracle as O
+from paper_2304_05735_gb300 import romap as R
+from paper_2304_05735_gb300 import synth
+
+from _harness import Ctx, object_frame_pool, paired_config
+
+pytestmark = pytest.mark.gpu
+MIXED = R.ROMAP_PREC_MIXED_BF16
+
+
+@pytest.fixture
+def torch():
+    import torch
+    return torch
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _cos(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("scene", ["plain", "masked"])
+def test_mixed_step_vs_oracle(torch, scene):
+    if scene == "plain":
+        oc, rc = paired_config(precision=MIXED)
+        sc = synth.config0_scene()
+    else:
+        oc, rc = paired_config(L=16, T=2 ** 16, growth=0.0, n_max=512, n_samples=64, rays_per_step=2048,
+                               bg_random=True, precision=MIXED)
+        sc = synth.multi_object_scene(1, seed0=5, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2, occluder_prob=1.0)[0]
+    ctx = Ctx(rc)
+    try:
+        oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed)
+        ctx.add_rays(oid, sc.pool)
+        pool = object_frame_pool(sc)
+        p0 = O.init_params(oc, sc.seed)
+        loss = ctx.fwd_bwd([oid])[0]
+        ref = O.train_step(oc, sc.half.astype(np.float32), sc.seed, 1, pool, p0, p0 * 0, p0 * 0, do_adam=False)
+        g = ctx.grad(oid)
+        nh = O.hash_param_count(oc)
+        rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
+        rel_h, rel_m = _rel(g[:nh], ref["grad"][:nh]), _rel(g[nh:], ref["grad"][nh:])
+        print(f"\n[{scene}] mixed vs oracle: loss rel {rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
+              f"(cos {_cos(g[:nh], ref['grad'][:nh]):.6f}), mlp-grad rel L2 {rel_m:.2e}")
+        assert rel_loss < 1e-3
+        assert rel_h < 5e-2 and rel_m < 5e-2
+        assert _cos(g, ref["grad"]) > 0.998
+    finally:
+        ctx.close()
+
+
+def test_mixed_batched_equals_separate(torch):
+    oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, n_samples=32, rays_per_step=700, bg_random=True,
+                           precision=MIXED)
+    scenes = synth.multi_object_scene(3, seed0=21, n_frames=2, W=64, H=48, f=64.0)
+    ctx = Ctx(rc)
+    try:
+        ids = []
+        for k, sc in enumerate(scenes):
+            oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=333 + 100 * k)
+            ctx.add_rays(oid, sc.pool)
+            ids.append(oid)
+        lb = ctx.fwd_bwd(ids)
+        gb = [ctx.grad(i) for i in ids]
+        ctx2 = Ctx(rc)
+        try:
+            for k, sc in enumerate(scenes):
+                oid = ctx2.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=333 + 100 * k)
+                ctx2.add_rays(oid, sc.pool)
+                ls = ctx2.fwd_bwd([oid])
+                assert np.allclose(ls[0], lb[k], rtol=1e-5, atol=1e-8)
+                assert _rel(ctx2.grad(oid), gb[k]) < 1e-5
+        finally:
+            ctx2.close()
+    finally:
+        ctx.close()
+
+
+def test_mixed_training_tracks_fp32_training(torch):
+    """Same seeds, 60 steps on the plain-method scene.  The first-step losses agree to 1e-3; after 60 steps the
+    mixed loss is compared with the spread of two FP32 runs (FP32 atomics make runs differ, and Adam's normalised
+    steps amplify small gradient differences), and must stay within 10% of the FP32 loss."""
+    runs = []
+    for prec in (R.ROMAP_PREC_FP32, R.ROMAP_PREC_FP32, MIXED):
+        oc, rc = paired_config(precision=prec)
+        ctx = Ctx(rc)
+        try:
+            sc = synth.config0_scene()
+            oid = ctx.create(seed=0)
+            ctx.add_rays(oid, sc.pool)
+            runs.append(np.array([ctx.train([oid])[0] for _ in range(60)]))
+        finally:
+            ctx.close()
+    a, a2, b = runs
+    spread = abs(a[-1] - a2[-1]) / a[-1]
+    gap = abs(a[-1] - b[-1]) / a[-1]
+    print(f"\nloss after 60 steps: fp32 {a[-1]:.6e} / {a2[-1]:.6e} (run-to-run {spread:.2e}), mixed {b[-1]:.6e} "
+          f"(gap {gap:.2e}); first step gap {abs(a[0] - b[0]) / a[0]:.2e}")
+    assert b[-1] < 0.3 * b[0]
+    assert abs(a[0] - b[0]) / a[0] < 1e-3
+    assert gap < 0.1
