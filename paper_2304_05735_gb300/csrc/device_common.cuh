@@ -70,6 +70,11 @@ __device__ inline void for_candidates(const float o[3], const float d[3], float 
   }
 }
 
+// Non-returning vector atomic add of two floats (red.global.add.v2.f32): the scatter never reads the old value.
+__device__ __forceinline__ void red_add2(float2* addr, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
 // Position of candidate i of a ray (same operations as for_candidates).
 __device__ inline float candidate_t(float tn, float step_len, int i, uint32_t k0, uint32_t k1, uint32_t step,
                                     uint32_t slot, int jitter) {

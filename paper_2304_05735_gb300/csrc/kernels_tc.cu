@@ -35,9 +35,10 @@ namespace romap {
 namespace {
 
 constexpr int kT = 128;           // samples per tile (MMA M)
-constexpr int kTcThreads = 128;   // one warpgroup
+constexpr int kTilesPerCta = 2;   // tiles processed in lockstep: warpgroup g works on tile g of the pair
+constexpr int kTcThreads = 128 * kTilesPerCta;
 constexpr int kTmemCols = 512;
-// TMEM columns: weight-gradient accumulators, then the per-layer temporary
+// TMEM columns: weight-gradient accumulators (shared by the tiles of a pair), then one 64-column temporary per tile
 constexpr uint32_t kColDW1 = 0, kColDW2 = 64, kColDW3 = 80, kColDW4 = 144, kColDW5 = 208, kColTmp = 256;
 constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before giving up
 
@@ -119,17 +120,12 @@ __device__ __forceinline__ void load8(const unsigned char* buf, int r, int c, in
   }
 }
 
+// Buffers of one tile.  The activation buffers are contiguous and in this order: the MN-major views of the
+// weight-gradient GEMMs read up to 2 KB past a buffer (the rows >= its feature count of the padded M = 128), which
+// lands in the next buffer of the same tile and only feeds TMEM rows that are never read; DL is read without
+// overrun.
 template <int LFP>
-struct TcSmem {
-  // weights (B operands of the forward), K-major BF16 [out][in]
-  __align__(128) unsigned char w1[kH * LFP * 2];
-  __align__(128) unsigned char w2[16 * kH * 2];
-  __align__(128) unsigned char w3[kH * 32 * 2];
-  __align__(128) unsigned char w4[kH * kH * 2];
-  __align__(128) unsigned char w5[16 * kH * 2];
-  // activations (A operands), K-major BF16 [128 samples][features]; kept contiguous and in this order: the
-  // MN-major views of the weight-gradient GEMMs read up to 2 KB past a buffer (rows >= its feature count of
-  // the padded M = 128), which lands in the next buffer and only feeds TMEM rows that are never read.
+struct TileBufs {
   __align__(128) unsigned char E[kT * LFP * 2];
   __align__(128) unsigned char H1[kT * kH * 2];
   __align__(128) unsigned char CIN[kT * 32 * 2];
@@ -145,6 +141,17 @@ struct TcSmem {
   float dsig[kT];
   float drgb[3][kT];
   int valid[kT];
+};
+
+template <int LFP>
+struct TcSmem {
+  // weights (B operands of the forward), K-major BF16 [out][in]
+  __align__(128) unsigned char w1[kH * LFP * 2];
+  __align__(128) unsigned char w2[16 * kH * 2];
+  __align__(128) unsigned char w3[kH * 32 * 2];
+  __align__(128) unsigned char w4[kH * kH * 2];
+  __align__(128) unsigned char w5[16 * kH * 2];
+  TileBufs<LFP> tb[kTilesPerCta];
   __align__(8) uint64_t mbar;
   uint32_t tmem_base;
   int fail;
@@ -182,7 +189,7 @@ __device__ void load_weights(TcSmem<LFP>& sm, const GridParams& g, const float* 
 template <int LFP>
 __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad) {
   const int t = threadIdx.x, w = t >> 5;
-  if (w >= 2) return;  // rows 0..63 live in the lanes of warps 0 and 1
+  if (w >= 2) return;  // rows 0..63 live in the lanes read by warps 0 and 1
   const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);
   const int row = t;
   float v[16];
@@ -241,7 +248,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Eq. 6 + Eq. 7-11 + adjoint for one ray whose samples occupy slots [base, base + P) of the tile.
 template <int LFP>
-__device__ void composite_ray(TcSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
+__device__ void composite_ray(TileBufs<LFP>& sm, const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
                               int bi, int64_t r, int base, int P, float invB, int32_t* status) {
   const int lane = threadIdx.x & 31;
   const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
@@ -343,15 +350,73 @@ __device__ void composite_ray(TcSmem<LFP>& sm, const GridParams& g, const BatchD
   }
 }
 
+// Hash encoding of one sample from the FP16 table, two levels per round so that 16 gathers are in flight.
+template <int LFP>
+__device__ __forceinline__ void encode_fp16(const GridParams& g, const ObjectDev* ob, const float p[3], float* e) {
+  const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
+#pragma unroll
+  for (int l = 0; l < LFP / 2; l += 2) {
+    const bool has0 = l < g.L, has1 = l + 1 < g.L;
+    Corners c0, c1;
+    if (has0) level_corners(g, l, p, ob->half, ob->inv_ext, c0);
+    if (has1) level_corners(g, l + 1, p, ob->half, ob->inv_ext, c1);
+    __half2 v0[8], v1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v0[k] = has0 ? __ldg(tab + g.off[l] + c0.idx[k]) : __half2{};
+      v1[k] = has1 ? __ldg(tab + g.off[l + 1] + c1.idx[k]) : __half2{};
+    }
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 f0 = __half22float2(v0[k]), f1 = __half22float2(v1[k]);
+      if (has0) { a0 = fmaf(c0.w[k], f0.x, a0); a1 = fmaf(c0.w[k], f0.y, a1); }
+      if (has1) { b0 = fmaf(c1.w[k], f1.x, b0); b1 = fmaf(c1.w[k], f1.y, b1); }
+    }
+    e[2 * l] = a0; e[2 * l + 1] = a1;
+    e[2 * l + 2] = b0; e[2 * l + 3] = b1;
+  }
+}
+
+// relu(TMEM row) -> BF16 row of an activation buffer (64 columns); the four TMEM loads share one wait
+__device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, int row) {
+  float v[64];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j], 0.f);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c);
+}
+// TMEM row masked by relu'(the forward activation stored in buf) -> written back into buf (64 columns)
+__device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, int row) {
+  float v[64];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
+  tmem_wait_ld();
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float h[8];
+    load8(buf, row, c, kH, h);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = h[j] > 0.f ? v[8 * c + j] : 0.f;
+    store8(buf, row, c, kH, h);
+  }
+}
+
 template <int LFP>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int P, int total_tiles) {
+    k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int P, int total_pairs) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem<LFP>& sm = *reinterpret_cast<TcSmem<LFP>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
-  const int tile_lo = (int)((int64_t)total_tiles * blockIdx.x / gridDim.x);
-  const int tile_hi = (int)((int64_t)total_tiles * (blockIdx.x + 1) / gridDim.x);
-  if (tile_lo >= tile_hi) return;
+  const int wg = t >> 7;          // tile of the pair
+  const int s = t & (kT - 1);     // slot within the tile = TMEM lane
+  TileBufs<LFP>& tb = sm.tb[wg];
+  const int pair_lo = (int)((int64_t)total_pairs * blockIdx.x / gridDim.x);
+  const int pair_hi = (int)((int64_t)total_pairs * (blockIdx.x + 1) / gridDim.x);
+  if (pair_lo >= pair_hi) return;
 
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar)));
@@ -367,21 +432,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_after();
   const uint32_t tm = sm.tmem_base;
-  const uint32_t my_lane = tm + ((uint32_t)(32 * warp) << 16);
-  const uint32_t tmp = my_lane + kColTmp;
+  const uint32_t tmp = tm + ((uint32_t)(32 * (warp & 3)) << 16) + kColTmp + 64u * (uint32_t)wg;  // this thread's row
   uint32_t phase = 0;
   bool ok = true;
   const int rays_per_tile = kT / P;
   const int N = g.n_samples;
 
-  // issue helpers (thread 0) ---------------------------------------------------------------------------
-  auto sync_then_issue = [&]() {  // make every thread's shared writes and TMEM reads visible to the MMAs
+  auto sync_then_issue = [&]() {  // every thread's shared writes and TMEM reads become visible to the MMAs
     fence_async_smem();
     tc_before();
     __syncthreads();
     tc_after();
   };
-  auto wait_mma = [&]() -> bool {  // all threads: wait for the last commit
+  auto wait_mma = [&]() -> bool {
     bool d = mbar_wait(&sm.mbar, phase);
     phase ^= 1u;
     if (!d) atomicExch(&sm.fail, 1);
@@ -389,13 +452,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_after();
     return sm.fail == 0;
   };
+  // thread 0 issues for both tiles; tile u's temporary starts at column kColTmp + 64 u
+  auto tmp_d = [&](int u) { return tm + kColTmp + 64u * (uint32_t)u; };
 
   int bi = -1;
   const ObjectDev* ob = nullptr;
-  uint32_t acc_dw = 0;  // 0 for the first weight-gradient GEMM of an object
-  for (int tile = tile_lo; tile < tile_hi && ok; ++tile) {
+  uint32_t acc_dw = 0;  // 0 until the first weight-gradient GEMM of an object has run
+  for (int pair = pair_lo; pair < pair_hi && ok; ++pair) {
+    const int tile0 = pair * kTilesPerCta;
     int nbi = bi < 0 ? 0 : bi;
-    while (nbi + 1 < b.n && tile >= b.tile_base[nbi + 1]) ++nbi;
+    while (nbi + 1 < b.n && tile0 >= b.tile_base[nbi + 1]) ++nbi;
     if (nbi != bi) {
       if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
       bi = nbi;
@@ -405,11 +471,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
-    const int tile_local = tile - b.tile_base[bi];
-    // ---- 1. sample of this thread's slot ----------------------------------------------------------------
+    const int tile_local = tile0 + wg - b.tile_base[bi];
+    // ---- 1-2. sample of this slot and its encoding -----------------------------------------------------------
     {
-      const int rl = tile_local * rays_per_tile + t / P;
-      const int i = t % P;
+      const int rl = tile_local * rays_per_tile + s / P;
+      const int i = s % P;
       bool valid = rl < n_rays_obj && i < N;
       float x = 0.f, y = 0.f, z = 0.f, ti = 0.f, dti = 0.f;
       if (valid) {
@@ -420,7 +486,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
           const uint32_t step = ob->step;
           ti = candidate_t(tn, step_len, i, ob->key0, ob->key1, step, (uint32_t)rl, 1);
-          const float tnext = (i + 1 < N) ? candidate_t(tn, step_len, i + 1, ob->key0, ob->key1, step, (uint32_t)rl, 1) : tf;
+          const float tnext =
+              (i + 1 < N) ? candidate_t(tn, step_len, i + 1, ob->key0, ob->key1, step, (uint32_t)rl, 1) : tf;
           dti = __fsub_rn(tnext, ti);
           x = __fadd_rn(R.o[3 * r], __fmul_rn(ti, R.d[3 * r]));
           y = __fadd_rn(R.o[3 * r + 1], __fmul_rn(ti, R.d[3 * r + 1]));
@@ -428,66 +495,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           valid = occupied(ob->occ, x, y, z, ob->half, ob->inv_ext);
         }
       }
-      sm.valid[t] = valid ? 1 : 0;
-      sm.px[0][t] = x; sm.px[1][t] = y; sm.px[2][t] = z;
-      sm.t[t] = ti;
-      sm.dt[t] = dti;
-      // ---- 2. hash encoding from the FP16 table -> E row (BF16) -------------------------------------------
-      const float p[3] = {x, y, z};
-      const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
+      tb.valid[s] = valid ? 1 : 0;
+      tb.px[0][s] = x; tb.px[1][s] = y; tb.px[2][s] = z;
+      tb.t[s] = ti;
+      tb.dt[s] = dti;
       float e[LFP];
 #pragma unroll
       for (int k = 0; k < LFP; ++k) e[k] = 0.f;
       if (valid) {
-#pragma unroll
-        for (int l = 0; l < LFP / 2; ++l) {
-          if (l < g.L) {
-            Corners c;
-            level_corners(g, l, p, ob->half, ob->inv_ext, c);
-            float2 v[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = __half22float2(__ldg(tab + g.off[l] + c.idx[k]));
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              a0 = fmaf(c.w[k], v[k].x, a0);
-              a1 = fmaf(c.w[k], v[k].y, a1);
-            }
-            e[2 * l] = a0;
-            e[2 * l + 1] = a1;
-          }
-        }
+        const float p[3] = {x, y, z};
+        encode_fp16<LFP>(g, ob, p, e);
       }
 #pragma unroll
-      for (int c = 0; c < LFP / 8; ++c) store8(sm.E, t, c, LFP, e + 8 * c);
+      for (int c = 0; c < LFP / 8; ++c) store8(tb.E, s, c, LFP, e + 8 * c);
     }
     sync_then_issue();
-    // ---- 3. forward layers -------------------------------------------------------------------------------
-    // L1: H1 = relu(E W1^T)
-    if (t == 0) {
+    // ---- 3. forward ----------------------------------------------------------------------------------------------
+    if (t == 0) {  // L1: E W1^T
+      for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
-      for (int kk = 0; kk < LFP / 16; ++kk)
-        mma(kColTmp + tm, desc_k(sm.E, LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0), kk > 0);
+        for (int kk = 0; kk < LFP / 16; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].E, LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    {
-      float v[16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tmem_ld16(tmp + 16 * c, v);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-        store8(sm.H1, t, 2 * c, kH, v);
-        store8(sm.H1, t, 2 * c + 1, kH, v + 8);
-      }
-    }
+    epi_relu64(tmp, tb.H1, s);
     sync_then_issue();
-    // L2: OUT = H1 W2^T (16 outputs)
-    if (t == 0) {
+    if (t == 0) {  // L2: H1 W2^T (16 outputs)
+      for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H1, kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0), kk > 0);
+        for (int kk = 0; kk < 4; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
@@ -496,69 +534,48 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tmem_ld16(tmp, v);
       tmem_wait_ld();
       const float o0 = v[0];
-      sm.o0[t] = o0;
-      sm.sig[t] = expf(fminf(fmaxf(o0, -15.f), 15.f));
-      // colour input: 15 geometry features, the view direction, zero padding to 32
+      tb.o0[s] = o0;
+      tb.sig[s] = expf(fminf(fmaxf(o0, -15.f), 15.f));
       float cin[32];
 #pragma unroll
       for (int j = 0; j < 15; ++j) cin[j] = v[1 + j];
       float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-      if (g.dir_dims == 3 && sm.valid[t]) {
-        const int64_t r = b.ray_base[bi] + tile_local * rays_per_tile + t / P;
+      if (g.dir_dims == 3 && tb.valid[s]) {
+        const int64_t r = b.ray_base[bi] + tile_local * rays_per_tile + s / P;
         d0 = R.d[3 * r]; d1 = R.d[3 * r + 1]; d2 = R.d[3 * r + 2];
       }
       cin[15] = d0; cin[16] = d1; cin[17] = d2;
 #pragma unroll
       for (int j = 18; j < 32; ++j) cin[j] = 0.f;
-      if (g.dir_dims == 0) cin[15] = cin[16] = cin[17] = 0.f;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) store8(sm.CIN, t, c, 32, cin + 8 * c);
+      for (int c = 0; c < 4; ++c) store8(tb.CIN, s, c, 32, cin + 8 * c);
     }
     sync_then_issue();
-    // L3: H2 = relu(CIN W3^T)
-    if (t == 0) {
+    if (t == 0) {  // L3: CIN W3^T
+      for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) mma(kColTmp + tm, desc_k(sm.CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0), kk > 0);
+        for (int kk = 0; kk < 2; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    {
-      float v[16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tmem_ld16(tmp + 16 * c, v);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-        store8(sm.H2, t, 2 * c, kH, v);
-        store8(sm.H2, t, 2 * c + 1, kH, v + 8);
-      }
-    }
+    epi_relu64(tmp, tb.H2, s);
     sync_then_issue();
-    // L4: H3 = relu(H2 W4^T)
-    if (t == 0) {
+    if (t == 0) {  // L4: H2 W4^T
+      for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+        for (int kk = 0; kk < 4; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    {
-      float v[16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tmem_ld16(tmp + 16 * c, v);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-        store8(sm.H3, t, 2 * c, kH, v);
-        store8(sm.H3, t, 2 * c + 1, kH, v + 8);
-      }
-    }
+    epi_relu64(tmp, tb.H3, s);
     sync_then_issue();
-    // L5: logits = H3 W5^T (3 of 16 outputs)
-    if (t == 0) {
+    if (t == 0) {  // L5: H3 W5^T (3 of 16 outputs)
+      for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0), kk > 0);
+        for (int kk = 0; kk < 4; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
@@ -566,93 +583,77 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       float v[16];
       tmem_ld16(tmp, v);
       tmem_wait_ld();
-      sm.rgb[0][t] = 1.0f / (1.0f + expf(-v[0]));
-      sm.rgb[1][t] = 1.0f / (1.0f + expf(-v[1]));
-      sm.rgb[2][t] = 1.0f / (1.0f + expf(-v[2]));
+      tb.rgb[0][s] = 1.0f / (1.0f + expf(-v[0]));
+      tb.rgb[1][s] = 1.0f / (1.0f + expf(-v[1]));
+      tb.rgb[2][s] = 1.0f / (1.0f + expf(-v[2]));
     }
     __syncthreads();
-    // ---- 4. compositing, losses, adjoint (one warp per ray) ------------------------------------------------
-    for (int j = warp; j < rays_per_tile; j += kTcThreads / 32) {
-      const int rl = tile_local * rays_per_tile + j;
-      if (rl < n_rays_obj) composite_ray<LFP>(sm, g, b, R, dyn, bi, b.ray_base[bi] + rl, j * P, P, invB, status);
+    // ---- 4. compositing, losses, adjoint: one warp per ray of the pair -----------------------------------------
+    for (int j = warp; j < kTilesPerCta * rays_per_tile; j += kTcThreads / 32) {
+      const int u = j / rays_per_tile, jr = j % rays_per_tile;
+      const int rl = (tile0 + u - b.tile_base[bi]) * rays_per_tile + jr;
+      if (rl < n_rays_obj)
+        composite_ray<LFP>(sm.tb[u], g, b, R, dyn, bi, b.ray_base[bi] + rl, jr * P, P, invB, status);
     }
     __syncthreads();
-    // ---- 5. backward ----------------------------------------------------------------------------------------
+    // ---- 5. backward -----------------------------------------------------------------------------------------------
     float dpre;
     {
-      const bool valid = sm.valid[t];
+      const bool valid = tb.valid[s];
       float dl[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) dl[k] = 0.f;
       if (valid) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const float c = sm.rgb[k][t];
-          dl[k] = sm.drgb[k][t] * c * (1.f - c);
+          const float c = tb.rgb[k][s];
+          dl[k] = tb.drgb[k][s] * c * (1.f - c);
         }
       }
-      const float o0 = sm.o0[t];
-      dpre = (valid && o0 >= -15.f && o0 <= 15.f) ? sm.dsig[t] * sm.sig[t] : 0.f;
-      store8(sm.DL, t, 0, 16, dl);
-      store8(sm.DL, t, 1, 16, dl + 8);
+      const float o0 = tb.o0[s];
+      dpre = (valid && o0 >= -15.f && o0 <= 15.f) ? tb.dsig[s] * tb.sig[s] : 0.f;
+      store8(tb.DL, s, 0, 16, dl);
+      store8(tb.DL, s, 1, 16, dl + 8);
     }
     sync_then_issue();
-    // dH3 = DL W5 ; dW5^T += H3^T DL
-    if (t == 0) {
-      mma(kColTmp + tm, desc_k(sm.DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1), 0);
+    if (t == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
+      for (int u = 0; u < kTilesPerCta; ++u) {
+        mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1), 0);
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW5 + tm, desc_mn(sm.H3, kH, kk), desc_mn(sm.DL, 16, kk), idesc(16, 1, 1), kk > 0 ? 1u : acc_dw);
+        for (int kk = 0; kk < 8; ++kk)
+          mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
+              (u > 0 || kk > 0) ? 1u : acc_dw);
+      }
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    {  // dH3 masked by relu'(H3), in place of H3
-      float v[16], h[16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tmem_ld16(tmp + 16 * c, v);
-        tmem_wait_ld();
-        load8(sm.H3, t, 2 * c, kH, h);
-        load8(sm.H3, t, 2 * c + 1, kH, h + 8);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
-        store8(sm.H3, t, 2 * c, kH, v);
-        store8(sm.H3, t, 2 * c + 1, kH, v + 8);
-      }
-    }
+    epi_mask64(tmp, tb.H3, s);
     sync_then_issue();
-    // dH2 = dH3 W4 ; dW4^T += H2^T dH3
-    if (t == 0) {
+    if (t == 0) {  // dH2 = dH3 W4 ; dW4^T += H2^T dH3
+      for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1), kk > 0);
+        for (int kk = 0; kk < 4; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1), kk > 0);
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW4 + tm, desc_mn(sm.H2, kH, kk), desc_mn(sm.H3, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+        for (int kk = 0; kk < 8; ++kk)
+          mma(kColDW4 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1),
+              (u > 0 || kk > 0) ? 1u : acc_dw);
+      }
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    {
-      float v[16], h[16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tmem_ld16(tmp + 16 * c, v);
-        tmem_wait_ld();
-        load8(sm.H2, t, 2 * c, kH, h);
-        load8(sm.H2, t, 2 * c + 1, kH, h + 8);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
-        store8(sm.H2, t, 2 * c, kH, v);
-        store8(sm.H2, t, 2 * c + 1, kH, v + 8);
-      }
-    }
+    epi_mask64(tmp, tb.H2, s);
     sync_then_issue();
-    // dCIN = dH2 W3 (32 columns) ; dW3^T += CIN^T dH2
-    if (t == 0) {
+    if (t == 0) {  // dCIN = dH2 W3 (32 columns) ; dW3^T += CIN^T dH2
+      for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1), kk > 0);
+        for (int kk = 0; kk < 4; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1), kk > 0);
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW3 + tm, desc_mn(sm.CIN, 32, kk), desc_mn(sm.H2, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+        for (int kk = 0; kk < 8; ++kk)
+          mma(kColDW3 + tm, desc_mn(sm.tb[u].CIN, 32, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1),
+              (u > 0 || kk > 0) ? 1u : acc_dw);
+      }
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
@@ -663,41 +664,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       d[0] = dpre;
 #pragma unroll
       for (int j = 0; j < 15; ++j) d[1 + j] = v[j];
-      store8(sm.DL, t, 0, 16, d);
-      store8(sm.DL, t, 1, 16, d + 8);
+      store8(tb.DL, s, 0, 16, d);
+      store8(tb.DL, s, 1, 16, d + 8);
     }
     sync_then_issue();
-    // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
-    if (t == 0) {
-      mma(kColTmp + tm, desc_k(sm.DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1), 0);
+    if (t == 0) {  // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
+      for (int u = 0; u < kTilesPerCta; ++u) {
+        mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1), 0);
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW2 + tm, desc_mn(sm.H1, kH, kk), desc_mn(sm.DL, 16, kk), idesc(16, 1, 1), kk > 0 ? 1u : acc_dw);
+        for (int kk = 0; kk < 8; ++kk)
+          mma(kColDW2 + tm, desc_mn(sm.tb[u].H1, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
+              (u > 0 || kk > 0) ? 1u : acc_dw);
+      }
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    {
-      float v[16], h[16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tmem_ld16(tmp + 16 * c, v);
-        tmem_wait_ld();
-        load8(sm.H1, t, 2 * c, kH, h);
-        load8(sm.H1, t, 2 * c + 1, kH, h + 8);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
-        store8(sm.H1, t, 2 * c, kH, v);
-        store8(sm.H1, t, 2 * c + 1, kH, v + 8);
-      }
-    }
+    epi_mask64(tmp, tb.H1, s);
     sync_then_issue();
-    // dE = dH1 W1 (LFP columns) ; dW1^T += E^T dH1
-    if (t == 0) {
+    if (t == 0) {  // dE = dH1 W1 (LFP columns) ; dW1^T += E^T dH1
+      for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(kColTmp + tm, desc_k(sm.H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1), kk > 0);
+        for (int kk = 0; kk < 4; ++kk)
+          mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1), kk > 0);
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW1 + tm, desc_mn(sm.E, LFP, kk), desc_mn(sm.H1, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+        for (int kk = 0; kk < 8; ++kk)
+          mma(kColDW1 + tm, desc_mn(sm.tb[u].E, LFP, kk), desc_mn(sm.tb[u].H1, kH, kk), idesc(64, 1, 1),
+              (u > 0 || kk > 0) ? 1u : acc_dw);
+      }
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
@@ -707,8 +700,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
       for (int c = 0; c < LFP / 16; ++c) tmem_ld16(tmp + 16 * c, de + 16 * c);
       tmem_wait_ld();
-      if (sm.valid[t]) {
-        const float p[3] = {sm.px[0][t], sm.px[1][t], sm.px[2][t]};
+      if (tb.valid[s]) {
+        const float p[3] = {tb.px[0][s], tb.px[1][s], tb.px[2][s]};
         float2* gt = reinterpret_cast<float2*>(ob->grad);
 #pragma unroll
         for (int l = 0; l < LFP / 2; ++l) {
@@ -717,7 +710,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           Corners c;
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) atomicAdd(gt + g.off[l] + c.idx[k], make_float2(c.w[k] * d0, c.w[k] * d1));
+          for (int k = 0; k < 8; ++k) red_add2(gt + g.off[l] + c.idx[k], c.w[k] * d0, c.w[k] * d1);
         }
       }
     }
@@ -748,12 +741,15 @@ void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
     cudaFuncSetAttribute(k_tile_tc<LFP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr_set = true;
   }
-  int grid = n_ctas < total_tiles ? n_ctas : total_tiles;
+  const int total_pairs = total_tiles / kTilesPerCta;
+  int grid = n_ctas < total_pairs ? n_ctas : total_pairs;
   if (grid < 1) return;
-  k_tile_tc<LFP><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status, P, total_tiles);
+  k_tile_tc<LFP><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status, P, total_pairs);
 }
 
 }  // namespace
+
+int tc_tiles_per_cta() { return kTilesPerCta; }
 
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
                     int total_tiles, int n_ctas, cudaStream_t stream) {

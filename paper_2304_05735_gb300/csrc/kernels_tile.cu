@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
           float2* gt = reinterpret_cast<float2*>(ob->grad) + g.off[l];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) atomicAdd(gt + c.idx[k], make_float2(c.w[k] * d0, c.w[k] * d1));
+          for (int k = 0; k < 8; ++k) red_add2(gt + c.idx[k], c.w[k] * d0, c.w[k] * d1);
         }
       }
     }

@@ -253,6 +253,8 @@ void build_batch(const std::vector<int32_t>& slots, const std::vector<int32_t>& 
     block_base[i + 1] = block_base[i] + nb;
     for (int k = 0; k < nb; ++k) block_obj.push_back(i);
     int tiles = P > 0 ? (int)(((int64_t)rays[i] * P + kTile - 1) / kTile) : 0;
+    const int per = tc_tiles_per_cta();
+    tiles = (tiles + per - 1) / per * per;  // tiles of one object are processed in groups that never straddle objects
     tile_base[i + 1] = tile_base[i] + tiles;
   }
   hb->n_rays = ray_base[n];
