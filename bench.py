@@ -40,15 +40,17 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 MAC_FWD, MAC_DX, MAC_DW = 8512, 8320, 8512
 PHASE_KERNEL = ("k_ray_setup + k_scan + k_write_samples", "k_tile_mlp<forward>", "k_composite<loss>",
                 "k_tile_mlp<backward>", "k_adam + k_advance_step")
+TC_KERNEL = "k_tile_tc (fused: samples, FP16 gather, BF16 tcgen05 MLP fwd+bwd, Eq. 6-11, scatter)"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32", "mixed"), default="fp32")
+    ap.add_argument("--precision", choices=("fp32", "mixed"), default="mixed")
+    ap.add_argument("--loss-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -205,22 +207,35 @@ def run_ours(args):
     w = WORKLOAD
     scenes = synth.multi_object_scene(w["objects"], seed0=1 + w["objects"] * rank, n_frames=w["frames"],
                                       W=w["width"], H=w["height"], f=w["focal"])
-    rc, h = make_ctx(R, torch, args.precision)
+    n = len(scenes)
+    main_prec = args.precision
+
+    # ---- loss comparison: same seeds, batched mixed vs batched FP32, per-step losses (untimed) -------------------
+    curves = {}
+    if not args.no_plain:
+        for prec in ("fp32", "mixed"):
+            rc, h = make_ctx(R, torch, prec)
+            ids = add_objects(R, h, scenes)
+            idarr = (C.c_int32 * n)(*ids)
+            ls = np.zeros((args.loss_steps, n), np.float32)
+            for k in range(args.loss_steps):
+                R.check(R.romap_train_step(h, idarr, n, 1, ls[k].ctypes.data))
+            curves[prec] = ls.mean(axis=1)
+            R.check(R.romap_destroy(h))
+
+    # ---- the timed batched step -------------------------------------------------------------------------------------
+    rc, h = make_ctx(R, torch, main_prec)
     ids = add_objects(R, h, scenes)
     idarr = (C.c_int32 * len(ids))(*ids)
-    n = len(ids)
-
-    # warm-up, then K timed steps of the batched path
     R.check(R.romap_train_step(h, idarr, n, max(args.warmup, 3), None))
     torch.cuda.synchronize()
     R.check(R.romap_reset_stats(h))
-    R.check(R.romap_set_profiling(h, 1))
     gpu_index = (os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local]
                  if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local))
     sampler = ClockSampler(gpu_index)
     time.sleep(0.3)
 
-    def steps():
+    def steps():  # one call per step: after its first step the library replays a captured CUDA graph
         for _ in range(args.steps):
             R.check(R.romap_train_step(h, idarr, n, 1, None))
 
@@ -228,51 +243,54 @@ def run_ours(args):
     clocks = sampler.stop()
     st = R.romap_stats()
     R.check(R.romap_get_stats(h, C.byref(st)))
-    phase_ms = (C.c_double * R.ROMAP_N_PHASES)()
-    phase_n = (C.c_int64 * R.ROMAP_N_PHASES)()
-    R.check(R.romap_phase_times(h, phase_ms, phase_n))
-    R.check(R.romap_set_profiling(h, 0))
     live = allsum(torch, dist, world, st.live_samples)
     value = live / (ms / 1e3)
     live_per_step = st.live_samples / args.steps  # this rank
     launches = st.kernel_launches
-    loss_batched = np.zeros(n, np.float32)
-    R.check(R.romap_train_step(h, idarr, n, 1, loss_batched.ctypes.data))
+    # per-phase device time: the same steps again with CUDA events around every phase (eager launches)
+    k_prof = max(3, min(args.steps, 100))
+    R.check(R.romap_reset_stats(h))
+    R.check(R.romap_set_profiling(h, 1))
+    R.check(R.romap_train_step(h, idarr, n, k_prof, None))
+    phase_ms = (C.c_double * R.ROMAP_N_PHASES)()
+    phase_n = (C.c_int64 * R.ROMAP_N_PHASES)()
+    R.check(R.romap_phase_times(h, phase_ms, phase_n))
+    R.check(R.romap_set_profiling(h, 0))
+    for i in range(R.ROMAP_N_PHASES):
+        phase_ms[i] *= args.steps / k_prof  # per-step averages below divide by args.steps
 
     # phases and the roofline of the dominant kernel
     phases = {}
     for i, name in enumerate(R.PHASES):
-        per_launch_ms = phase_ms[i] / max(1, args.steps)
-        ent = {"kernel": PHASE_KERNEL[i], "ms_per_step": per_launch_ms, "share": phase_ms[i] / max(1e-9, sum(phase_ms))}
-        phases[name] = ent
+        phases[name] = {"kernel": PHASE_KERNEL[i], "ms_per_step": phase_ms[i] / max(1, args.steps),
+                        "share": phase_ms[i] / max(1e-9, sum(phase_ms))}
     bwd_ms = phase_ms[3] / args.steps
     fwd_ms = phase_ms[1] / args.steps
-    mixed = args.precision == "mixed"
+    mixed = main_prec == "mixed"
     peaks = {}
-    peaks_path0 = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(peaks_path0):
-        peaks = json.load(open(peaks_path0))
-    if mixed:
-        # the fused kernel does forward (8512 MAC), input gradients (8320) and weight gradients (8512) per sample
-        phases["mlp_backward_scatter"]["kernel"] = "k_tile_tc (fused: samples, gather, MLP fwd, Eq. 6-11, bwd, scatter)"
-        flop_bwd = 2.0 * (MAC_FWD + MAC_DX + MAC_DW) * live_per_step
-    else:
-        flop_bwd = 2.0 * (MAC_FWD + MAC_DX + MAC_DW) * live_per_step
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peaks = json.load(open(peaks_path))
+    flop_bwd = 2.0 * (MAC_FWD + MAC_DX + MAC_DW) * live_per_step
     flop_fwd = 2.0 * MAC_FWD * live_per_step
+    if mixed:
+        phases["mlp_backward_scatter"]["kernel"] = TC_KERNEL
     if bwd_ms > 0:
         phases["mlp_backward_scatter"]["achieved_tflops"] = flop_bwd / (bwd_ms / 1e3) / 1e12
     if fwd_ms > 0:
         phases["mlp_forward"]["achieved_tflops"] = flop_fwd / (fwd_ms / 1e3) / 1e12
-    adam_bytes = (32.0 + (2.0 if mixed else 0.0)) * int(R.param_layout(rc).n_params) * n
+    n_params = int(R.param_layout(rc).n_params)
+    adam_bytes = (32.0 + (2.0 if mixed else 0.0)) * n_params * n
+    hbm = peaks.get("hbm_gbs") or 6800.0
     if phase_ms[4] > 0:
         phases["adam"]["achieved_gbs"] = adam_bytes / (phase_ms[4] / args.steps / 1e3) / 1e9
+        phases["adam"]["frac_of_hbm"] = phases["adam"]["achieved_gbs"] / hbm
     dominant = max(range(R.ROMAP_N_PHASES), key=lambda i: phase_ms[i])
     if dominant == 3 and mixed:
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         achieved = flop_bwd / (bwd_ms / 1e3) / 1e12
-        roofline = {"bound": "tensor", "kernel": phases["mlp_backward_scatter"]["kernel"], "achieved": achieved,
-                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": profiled_traffic("k_tile_tc", args.precision),
+        roofline = {"bound": "tensor", "kernel": TC_KERNEL, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": profiled_traffic("k_tile_tc", main_prec),
                     "peak_source": "measured bf16 dense, sustained (MEASURED_PEAKS.json)" if peaks else "fallback",
                     "work_per_unit": f"{2 * (MAC_FWD + MAC_DX + MAC_DW)} FLOP per live sample (BF16 MMA)",
                     "units_per_launch": live_per_step, "ms_per_launch": bwd_ms}
@@ -282,44 +300,19 @@ def run_ours(args):
         achieved = flop / (kms / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": PHASE_KERNEL[dominant], "achieved": achieved,
                     "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS,
-                    "traffic": profiled_traffic(PHASE_KERNEL[dominant], args.precision),
+                    "traffic": profiled_traffic(PHASE_KERNEL[dominant], main_prec),
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 SIMT FMA)",
                     "work_per_unit": f"{2 * (MAC_FWD + MAC_DX + MAC_DW) if dominant == 3 else 2 * MAC_FWD} "
                                      "FLOP per live sample",
                     "units_per_launch": live_per_step, "ms_per_launch": kms}
     else:
-        hbm = peaks.get("hbm_gbs") or 6800.0
         ach = phases["adam"].get("achieved_gbs") if dominant == 4 else None
         roofline = {"bound": "hbm", "kernel": PHASE_KERNEL[dominant], "achieved": ach, "peak": hbm,
                     "unit": "GB/s", "frac": (ach / hbm) if ach else None, "traffic": None}
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    hbm_peak = None
-    if os.path.exists(peaks_path):
-        hbm_peak = json.load(open(peaks_path)).get("hbm_gbs")
-    if hbm_peak:
-        phases["adam"]["frac_of_measured_hbm"] = phases["adam"]["achieved_gbs"] / hbm_peak
 
-    # the plain per-object FP32 path: one launch sequence per object
-    plain = None
-    if not args.no_plain:
-        k_plain = max(5, args.steps // 4)
-        R.check(R.romap_reset_stats(h))
-
-        def plain_steps():
-            for _ in range(k_plain):
-                for i in ids:
-                    one = (C.c_int32 * 1)(i)
-                    R.check(R.romap_train_step(h, one, 1, 1, None))
-
-        ms_p = timed(torch, plain_steps, world, dist)
-        stp = R.romap_stats()
-        R.check(R.romap_get_stats(h, C.byref(stp)))
-        live_p = allsum(torch, dist, world, stp.live_samples)
-        plain = {"value": live_p / (ms_p / 1e3), "ms_per_step": ms_p / k_plain, "steps": k_plain,
-                 "path": "plain FP32, one launch sequence per object"}
-
-    # end to end through the C ABI with host buffers: each step replaces every object's rays with a fresh batch
-    # of 4096 rays from pinned host memory, trains, and reads the losses back
+    # ---- end to end through the C ABI with host buffers ---------------------------------------------------------------
+    # each step replaces every object's rays with a fresh batch of 4096 rays from pinned host memory, trains, and
+    # reads the losses back
     e2e = None
     if not args.no_e2e:
         rng = np.random.default_rng(100 + rank)
@@ -371,6 +364,47 @@ def run_ours(args):
                "path": "romap_add_rays(REPLACE, pinned host) x 8 + romap_train_step(out_loss to host), wall clock"}
     R.check(R.romap_destroy(h))
 
+    # ---- the comparison paths: batched FP32 and the plain per-object FP32 path ---------------------------------------
+    others = {}
+    if not args.no_plain:
+        k_cmp = max(5, min(args.steps, 100))
+        rc2, h2 = make_ctx(R, torch, "fp32")
+        ids2 = add_objects(R, h2, scenes)
+        arr2 = (C.c_int32 * n)(*ids2)
+        R.check(R.romap_train_step(h2, arr2, n, 3, None))
+        for label, per_object in (("batched_fp32", False), ("plain_fp32_per_object", True)):
+            R.check(R.romap_reset_stats(h2))
+
+            def run_cmp():
+                for _ in range(k_cmp):
+                    if per_object:
+                        for i in ids2:
+                            R.check(R.romap_train_step(h2, (C.c_int32 * 1)(i), 1, 1, None))
+                    else:
+                        R.check(R.romap_train_step(h2, arr2, n, 1, None))
+
+            ms_c = timed(torch, run_cmp, world, dist)
+            stc = R.romap_stats()
+            R.check(R.romap_get_stats(h2, C.byref(stc)))
+            live_c = allsum(torch, dist, world, stc.live_samples)
+            others[label] = {"value": live_c / (ms_c / 1e3), "ms_per_step": ms_c / k_cmp, "steps": k_cmp}
+        R.check(R.romap_destroy(h2))
+
+    loss_cmp = None
+    if curves:
+        tail = max(1, args.loss_steps // 10)
+        lf, lm = float(curves["fp32"][-tail:].mean()), float(curves["mixed"][-tail:].mean())
+        target = lf
+        reach = np.nonzero(curves["mixed"] <= target)[0]
+        loss_cmp = {"steps": args.loss_steps, "mean_loss_last_steps": tail, "fp32": lf, "mixed": lm,
+                    "rel_diff": abs(lm - lf) / lf, "first_step_rel_diff":
+                    float(abs(curves["mixed"][0] - curves["fp32"][0]) / curves["fp32"][0]),
+                    "mixed_steps_to_fp32_final_loss": int(reach[0] + 1) if reach.size else None}
+        if mixed and others.get("plain_fp32_per_object") and reach.size:
+            t_mixed = (reach[0] + 1) * ms / args.steps
+            t_plain = args.loss_steps * others["plain_fp32_per_object"]["ms_per_step"]
+            loss_cmp["time_to_fp32_final_loss_ms"] = {"mixed_batched": t_mixed, "plain_fp32_per_object": t_plain}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n_rays=4096, steps=1)
@@ -378,15 +412,19 @@ def run_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f16+f32",
+               "vs_baseline": None,
+               "dtype": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)" if mixed
+               else "f32",
                "data": "synthetic (analytic shapes, seeded)",
-               "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "precision": args.precision, "path": "batched",
+               "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "precision": main_prec, "path": "batched",
                           "parallelism": f"replicas x{world} (objects sharded, no collective)",
                           "l2": "inputs larger than L2: per step 219 MB of parameters, gradients and Adam moments "
                                 "plus 0.4 GB of ray pools (L2 129 MB)"},
-               "live_samples_per_step": live_per_step, "loss_after_timed_steps": [float(x) for x in loss_batched],
-               "roofline": roofline, "phases": phases, "plain_per_object": plain, "e2e": e2e,
-               "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks}
+               "live_samples_per_step": live_per_step, "roofline": roofline, "phases": phases,
+               "comparison": others, "loss_check": loss_cmp, "e2e": e2e, "cpu_baseline": cpu,
+               "gpu_launches": int(launches), "clocks": clocks}
+        if others.get("plain_fp32_per_object"):
+            out["speedup_vs_plain_fp32_per_object"] = value / others["plain_fp32_per_object"]["value"]
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()

@@ -102,6 +102,14 @@ struct romap_ctx {
   BatchDyn* dyn_host = nullptr;    // pinned
   romap_stats stats{};
   int64_t launches = 0;
+  // CUDA graph of one training step of the last batch composition (captured on cap_stream, replayed on stream)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  std::vector<int32_t> graph_key;
+  std::vector<int32_t> graph_batch;  // batch arrays the graph's kernels read from ws_batch
+  uint64_t ws_generation = 0;   // bumped whenever a workspace buffer moves
+  uint64_t graph_ws_generation = 0;
+  bool graphs_enabled = true;
   // phase timing
   bool profiling = false;
   struct Prof { int phase; cudaEvent_t a, b; int launches; };
@@ -151,6 +159,7 @@ romap_status grow(romap_ctx* ctx, DevBuf& b, size_t bytes) {
   dev_free(ctx, b.p);
   b.p = p;
   b.bytes = nb;
+  ctx->ws_generation += 1;
   return ROMAP_OK;
 }
 
@@ -637,10 +646,14 @@ romap_status romap_init(const romap_config* cfg, void* cuda_stream, romap_ctx** 
   return ROMAP_OK;
 }
 
+static void drop_graph(romap_ctx* ctx);
+
 romap_status romap_destroy(romap_ctx* ctx) {
   if (!ctx) return fail(ROMAP_ERR_INVALID_ARG, "ctx is NULL");
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto& o : ctx->objs)
     if (o.alive) free_object(ctx, o);
   dev_free(ctx, ctx->objs_dev);
@@ -860,24 +873,105 @@ romap_status romap_adam_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids) 
   return ROMAP_OK;
 }
 
+// One training step (forward, loss, backward, Adam) of a batch on ctx->stream.
+static romap_status enqueue_step(romap_ctx* ctx, const std::vector<int32_t>& v) {
+  BatchDesc b;
+  ROMAP_TRY(run_fwd_bwd(ctx, v, &b));
+  {
+    PhaseScope ps(ctx, 4, 2);
+    launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+  }
+  ctx->launches += 2;
+  CUDA_TRY(cudaGetLastError());
+  for (int32_t id : v) {
+    ctx->objs[id].steps_done += 1;
+    ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
+  }
+  return ROMAP_OK;
+}
+
+static void drop_graph(romap_ctx* ctx) {
+  if (ctx->step_graph) cudaGraphExecDestroy(ctx->step_graph);
+  ctx->step_graph = nullptr;
+  ctx->graph_key.clear();
+}
+
+// Captures one step of batch v into ctx->step_graph (nothing executes during capture).
+static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, const std::vector<int32_t>& key) {
+  drop_graph(ctx);
+  if (!ctx->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  // the capture records launches only; host-side counters are restored afterwards and advanced per replay
+  std::vector<int64_t> done(v.size());
+  for (size_t i = 0; i < v.size(); ++i) done[i] = ctx->objs[v[i]].steps_done;
+  romap_stats saved = ctx->stats;
+  int64_t saved_launches = ctx->launches;
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  romap_status st = ROMAP_OK;
+  if (e == cudaSuccess) {
+    st = enqueue_step(ctx, v);
+    e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  }
+  ctx->stream = user;
+  for (size_t i = 0; i < v.size(); ++i) {
+    ctx->objs[v[i]].steps_done = done[i];
+    ctx->objs_host[v[i]].step = (uint32_t)(done[i] + 1);
+  }
+  ctx->stats = saved;
+  ctx->launches = saved_launches;
+  if (e == cudaSuccess && st == ROMAP_OK && graph) {
+    e = cudaGraphInstantiate(&ctx->step_graph, graph, 0);
+    if (e != cudaSuccess) ctx->step_graph = nullptr;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || st != ROMAP_OK || !ctx->step_graph) {
+    cudaGetLastError();
+    ctx->step_graph = nullptr;
+    ctx->graphs_enabled = false;  // fall back to eager launches for the rest of the context
+    return ROMAP_OK;
+  }
+  ctx->graph_key = key;
+  ctx->graph_batch = ctx->batch_key;
+  ctx->graph_ws_generation = ctx->ws_generation;
+  return ROMAP_OK;
+}
+
 romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps, float* out_loss) {
   ROMAP_TRY(check_ctx(ctx));
   if (n_steps < 1) return fail(ROMAP_ERR_INVALID_ARG, "n_steps must be >= 1");
   std::vector<int32_t> v;
   ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+  // the graph key: the batch composition (object slots and their rays per step) and the precision
+  std::vector<int32_t> key(v.begin(), v.end());
+  for (int32_t id : v) key.push_back(ctx->objs_host[id].n_rays);
+  key.push_back(ctx->cfg.precision);
   for (int s = 0; s < n_steps; ++s) {
-    BatchDesc b;
-    ROMAP_TRY(run_fwd_bwd(ctx, v, &b));
-    {
-      PhaseScope ps(ctx, 4, 2);
-      launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+    const bool use_graph = ctx->graphs_enabled && !ctx->profiling;
+    if (use_graph && ctx->step_graph && ctx->graph_key == key && ctx->graph_ws_generation == ctx->ws_generation) {
+      if (ctx->batch_key != ctx->graph_batch) {  // another call reused the batch buffer: restore the graph's arrays
+        CUDA_TRY(cudaMemcpyAsync(ctx->ws_batch.p, ctx->graph_batch.data(), sizeof(int32_t) * ctx->graph_batch.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+        ctx->batch_key = ctx->graph_batch;
+        ctx->batch_n = (int)v.size();
+      }
+      CUDA_TRY(cudaGraphLaunch(ctx->step_graph, ctx->stream));
+      // what enqueue_step does on the host for each step
+      int64_t rays = 0;
+      for (int32_t id : v) {
+        rays += ctx->objs_host[id].n_rays;
+        ctx->objs[id].steps_done += 1;
+        ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
+      }
+      ctx->stats.steps += (int64_t)v.size();
+      ctx->stats.rays += rays;
+      ctx->launches += ctx->cfg.precision == ROMAP_PREC_MIXED_BF16 ? 5 : 8;
+      continue;
     }
-    ctx->launches += 2;
-    CUDA_TRY(cudaGetLastError());
-    for (int32_t id : v) {
-      ctx->objs[id].steps_done += 1;
-      ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
-    }
+    ROMAP_TRY(enqueue_step(ctx, v));
+    if (use_graph && (ctx->graph_key != key || !ctx->step_graph || ctx->graph_ws_generation != ctx->ws_generation))
+      ROMAP_TRY(capture_step(ctx, v, key));
   }
   if (out_loss) {
     std::vector<float> tmp(5 * (size_t)n_ids);
