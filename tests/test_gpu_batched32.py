@@ -1,0 +1,108 @@
+"""Uneven batches with occupancy culling: 32 objects whose rays per step are log-uniform in 256..16384, 128
+candidate samples per ray culled by a 64^3 occupancy grid (the object's shape dilated by 2 cells plus random cells),
+hash grid L=16, F=2, T=2^19 (levels 0-6 dense), mixed precision.  The batched launch equals separate launches, and
+the smallest objects match the FP64 oracle; the FP32 path with culling matches the oracle too."""
+import numpy as np
+import pytest
+
+from oracle import romap_oracle as O
+from paper_2304_05735_gb300 import romap as R
+from paper_2304_05735_gb300 import synth
+
+from _harness import Ctx, assert_grad_close, object_frame_pool, paired_config
+
+pytestmark = pytest.mark.gpu
+
+
+def _scene(n_objects, seed0=40):
+    scenes = synth.multi_object_scene(n_objects, seed0=seed0, n_frames=2, W=160, H=120, f=160.0, depth_frac=0.02)
+    rng = np.random.default_rng(7)
+    rays = np.exp(rng.uniform(np.log(256), np.log(16384), n_objects)).astype(int)
+    occ = [synth.occupancy_bits(sc.shape, sc.half, dilate=2, p=0.05, seed=sc.seed) for sc in scenes]
+    return scenes, rays, occ
+
+
+def _setup(ctx, scenes, rays, occ):
+    ids = []
+    for sc, rp, bits in zip(scenes, rays, occ):
+        oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=int(rp))
+        ctx.add_rays(oid, sc.pool)
+        R.check(R.romap_set_occupancy(ctx.h, oid, np.ascontiguousarray(bits).ctypes.data, 0))
+        ids.append(oid)
+    return ids
+
+
+def test_uneven_batch_with_occupancy_mixed():
+    import torch  # noqa: F401
+
+    oc, rc = paired_config(L=16, T=2 ** 19, growth=0.0, n_max=512, n_samples=128, bg_random=True,
+                           precision=R.ROMAP_PREC_MIXED_BF16)
+    scenes, rays, occ = _scene(32)
+    ctx = Ctx(rc)
+    try:
+        ids = _setup(ctx, scenes, rays, occ)
+        st0 = R.romap_stats()
+        R.check(R.romap_reset_stats(ctx.h))
+        lb = ctx.fwd_bwd(ids)
+        R.check(R.romap_get_stats(ctx.h, R.C.byref(st0)))
+        pools = [min(int(r), sc.pool["cls"].size) for r, sc in zip(rays, scenes)]
+        live_per_ray = st0.live_samples / sum(pools)
+        print(f"\n32 objects, {sum(pools)} rays, {st0.live_samples} live samples ({live_per_ray:.1f} per ray of 128)")
+        assert 8 < live_per_ray < 128
+        g_small = {}
+        order = np.argsort(pools)
+        for k in order[:2]:
+            g_small[k] = ctx.grad(ids[k])
+        # separate launches of the two smallest objects give the same loss and gradient
+        ctx2 = Ctx(rc)
+        try:
+            for k in order[:2]:
+                oid = ctx2.create(t=tuple(scenes[k].t), yaw=scenes[k].yaw, seed=scenes[k].seed,
+                                  rays_per_step=int(rays[k]))
+                ctx2.add_rays(oid, scenes[k].pool)
+                R.check(R.romap_set_occupancy(ctx2.h, oid, np.ascontiguousarray(occ[k]).ctypes.data, 0))
+                ls = ctx2.fwd_bwd([oid])
+                assert np.allclose(ls[0], lb[k], rtol=1e-5, atol=1e-8)
+                gs = ctx2.grad(oid)
+                assert np.linalg.norm(gs - g_small[k]) <= 1e-5 * np.linalg.norm(g_small[k])
+        finally:
+            ctx2.close()
+        # the smallest object against the FP64 oracle (mixed precision: loss within 1e-3 relative)
+        k = order[0]
+        oc.rays_per_step = int(rays[k])
+        pool = object_frame_pool(scenes[k])
+        p0 = O.init_params(oc, scenes[k].seed)
+        ref = O.train_step(oc, scenes[k].half.astype(np.float32), scenes[k].seed, 1, pool, p0, p0 * 0, p0 * 0,
+                           occ=occ[k], do_adam=False)
+        rel = abs(lb[k][0] - ref["loss"][0]) / abs(ref["loss"][0])
+        g = g_small[k].astype(np.float64)
+        cos = g @ ref["grad"] / (np.linalg.norm(g) * np.linalg.norm(ref["grad"]))
+        print(f"object {k} ({pools[k]} rays): loss rel {rel:.2e}, gradient cosine {cos:.6f}")
+        assert rel < 1e-3 and cos > 0.995
+    finally:
+        ctx.close()
+
+
+def test_fp32_step_with_occupancy_matches_oracle():
+    import torch  # noqa: F401
+
+    oc, rc = paired_config(L=16, T=2 ** 19, growth=0.0, n_max=512, n_samples=128, rays_per_step=300, bg_random=True)
+    scenes, _, occ = _scene(1, seed0=44)
+    sc = scenes[0]
+    ctx = Ctx(rc)
+    try:
+        oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed)
+        ctx.add_rays(oid, sc.pool)
+        R.check(R.romap_set_occupancy(ctx.h, oid, np.ascontiguousarray(occ[0]).ctypes.data, 0))
+        loss = ctx.fwd_bwd([oid])[0]
+        pool = object_frame_pool(sc)
+        p0 = O.init_params(oc, sc.seed)
+        ref = O.train_step(oc, sc.half.astype(np.float32), sc.seed, 1, pool, p0, p0 * 0, p0 * 0, occ=occ[0],
+                           do_adam=False)
+        assert np.allclose(loss, ref["loss"], rtol=1e-5, atol=1e-8), (loss, ref["loss"])
+        g = ctx.grad(oid)
+        nh = O.hash_param_count(oc)
+        assert_grad_close(g[:nh], ref["grad"][:nh], what="hash gradient")
+        assert_grad_close(g[nh:], ref["grad"][nh:], what="MLP gradient")
+    finally:
+        ctx.close()
