@@ -350,13 +350,14 @@ __device__ void composite_ray(TileBufs<LFP>& sm, const GridParams& g, const Batc
   }
 }
 
-// Hash encoding of one sample from the FP16 table, two levels per round so that 16 gathers are in flight.
-template <int LFP>
-__device__ __forceinline__ void encode_fp16(const GridParams& g, const ObjectDev* ob, const float p[3], float* e) {
+// Hash encoding of levels [L0, L1) of one sample from the FP16 table, two levels per round so that 16 gathers are
+// in flight; e holds the LFP features (levels outside [L0, L1) are left untouched).
+template <int LFP, int L0, int L1>
+__device__ __forceinline__ void gather_levels(const GridParams& g, const ObjectDev* ob, const float p[3], float* e) {
   const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
 #pragma unroll
-  for (int l = 0; l < LFP / 2; l += 2) {
-    const bool has0 = l < g.L, has1 = l + 1 < g.L;
+  for (int l = L0; l < L1; l += 2) {
+    const bool has0 = l < g.L, has1 = (l + 1 < L1) && (l + 1 < g.L);
     Corners c0, c1;
     if (has0) level_corners(g, l, p, ob->half, ob->inv_ext, c0);
     if (has1) level_corners(g, l + 1, p, ob->half, ob->inv_ext, c1);
@@ -374,8 +375,43 @@ __device__ __forceinline__ void encode_fp16(const GridParams& g, const ObjectDev
       if (has1) { b0 = fmaf(c1.w[k], f1.x, b0); b1 = fmaf(c1.w[k], f1.y, b1); }
     }
     e[2 * l] = a0; e[2 * l + 1] = a1;
-    e[2 * l + 2] = b0; e[2 * l + 3] = b1;
+    if (l + 1 < L1) { e[2 * l + 2] = b0; e[2 * l + 3] = b1; }
   }
+}
+
+// The sample of one slot: candidate i of ray rl of the object (same FP32 operations as the sampling kernels).
+struct SlotSample {
+  float x, y, z, t, dt;
+  int valid;
+};
+
+__device__ __forceinline__ SlotSample make_sample(const GridParams& g, const BatchDesc& b, const RayBuf& R,
+                                                  const ObjectDev* ob, int bi, int tile_local, int s, int P) {
+  SlotSample q{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+  const int N = g.n_samples;
+  const int rl = tile_local * (kT / P) + s / P;
+  const int i = s % P;
+  const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
+  if (rl >= n_rays_obj || i >= N) return q;
+  const int64_t r = b.ray_base[bi] + rl;
+  const float tn = R.tn[r], tf = R.tf[r];
+  if (!(tf > tn)) return q;
+  const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
+  const uint32_t step = ob->step;
+  q.t = candidate_t(tn, step_len, i, ob->key0, ob->key1, step, (uint32_t)rl, 1);
+  const float tnext = (i + 1 < N) ? candidate_t(tn, step_len, i + 1, ob->key0, ob->key1, step, (uint32_t)rl, 1) : tf;
+  q.dt = __fsub_rn(tnext, q.t);
+  q.x = __fadd_rn(R.o[3 * r], __fmul_rn(q.t, R.d[3 * r]));
+  q.y = __fadd_rn(R.o[3 * r + 1], __fmul_rn(q.t, R.d[3 * r + 1]));
+  q.z = __fadd_rn(R.o[3 * r + 2], __fmul_rn(q.t, R.d[3 * r + 2]));
+  q.valid = occupied(ob->occ, q.x, q.y, q.z, ob->half, ob->inv_ext) ? 1 : 0;
+  return q;
+}
+
+__device__ __forceinline__ int locate_object(const BatchDesc& b, int tile, int start) {
+  int i = start < 0 ? 0 : start;
+  while (i + 1 < b.n && tile >= b.tile_base[i + 1]) ++i;
+  return i;
 }
 
 // relu(TMEM row) -> BF16 row of an activation buffer (64 columns); the four TMEM loads share one wait
@@ -444,10 +480,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc_after();
   };
-  auto wait_mma = [&]() -> bool {
-    bool d = mbar_wait(&sm.mbar, phase);
+  auto wait_mma = [&]() -> bool {  // one thread polls the mbarrier; the others wait at the CTA barrier
+    if (t == 0) {
+      if (!mbar_wait(&sm.mbar, phase)) sm.fail = 1;
+    }
     phase ^= 1u;
-    if (!d) atomicExch(&sm.fail, 1);
     __syncthreads();
     tc_after();
     return sm.fail == 0;
@@ -458,56 +495,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   int bi = -1;
   const ObjectDev* ob = nullptr;
   uint32_t acc_dw = 0;  // 0 until the first weight-gradient GEMM of an object has run
+  constexpr int LMAX = LFP / 2;
+  // the sample and encoding of the next pair are computed ahead, mostly while the backward GEMMs of the current
+  // pair run, and kept in registers until the current pair no longer reads the tile buffers
+  int nx_bi = locate_object(b, pair_lo * kTilesPerCta, 0);
+  const ObjectDev* nx_ob = &b.objs[b.slot[nx_bi]];
+  SlotSample nx = make_sample(g, b, R, nx_ob, nx_bi, pair_lo * kTilesPerCta + wg - b.tile_base[nx_bi], s, P);
+  float ne[LFP];
+#pragma unroll
+  for (int k = 0; k < LFP; ++k) ne[k] = 0.f;
+  if (nx.valid) {
+    const float p[3] = {nx.x, nx.y, nx.z};
+    gather_levels<LFP, 0, LMAX>(g, nx_ob, p, ne);
+  }
   for (int pair = pair_lo; pair < pair_hi && ok; ++pair) {
     const int tile0 = pair * kTilesPerCta;
-    int nbi = bi < 0 ? 0 : bi;
-    while (nbi + 1 < b.n && tile0 >= b.tile_base[nbi + 1]) ++nbi;
-    if (nbi != bi) {
+    // ---- 1-2. the prepared sample and encoding of this pair -> tile buffers ---------------------------------------
+    tb.valid[s] = nx.valid;
+    tb.px[0][s] = nx.x; tb.px[1][s] = nx.y; tb.px[2][s] = nx.z;
+    tb.t[s] = nx.t;
+    tb.dt[s] = nx.dt;
+#pragma unroll
+    for (int c = 0; c < LFP / 8; ++c) store8(tb.E, s, c, LFP, ne + 8 * c);
+    if (nx_bi != bi) {
       if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
-      bi = nbi;
-      ob = &b.objs[b.slot[bi]];
+      bi = nx_bi;
+      ob = nx_ob;
       load_weights<LFP>(sm, g, ob->params);
       acc_dw = 0;
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
     const int tile_local = tile0 + wg - b.tile_base[bi];
-    // ---- 1-2. sample of this slot and its encoding -----------------------------------------------------------
-    {
-      const int rl = tile_local * rays_per_tile + s / P;
-      const int i = s % P;
-      bool valid = rl < n_rays_obj && i < N;
-      float x = 0.f, y = 0.f, z = 0.f, ti = 0.f, dti = 0.f;
-      if (valid) {
-        const int64_t r = b.ray_base[bi] + rl;
-        const float tn = R.tn[r], tf = R.tf[r];
-        valid = tf > tn;
-        if (valid) {
-          const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
-          const uint32_t step = ob->step;
-          ti = candidate_t(tn, step_len, i, ob->key0, ob->key1, step, (uint32_t)rl, 1);
-          const float tnext =
-              (i + 1 < N) ? candidate_t(tn, step_len, i + 1, ob->key0, ob->key1, step, (uint32_t)rl, 1) : tf;
-          dti = __fsub_rn(tnext, ti);
-          x = __fadd_rn(R.o[3 * r], __fmul_rn(ti, R.d[3 * r]));
-          y = __fadd_rn(R.o[3 * r + 1], __fmul_rn(ti, R.d[3 * r + 1]));
-          z = __fadd_rn(R.o[3 * r + 2], __fmul_rn(ti, R.d[3 * r + 2]));
-          valid = occupied(ob->occ, x, y, z, ob->half, ob->inv_ext);
-        }
-      }
-      tb.valid[s] = valid ? 1 : 0;
-      tb.px[0][s] = x; tb.px[1][s] = y; tb.px[2][s] = z;
-      tb.t[s] = ti;
-      tb.dt[s] = dti;
-      float e[LFP];
-#pragma unroll
-      for (int k = 0; k < LFP; ++k) e[k] = 0.f;
-      if (valid) {
-        const float p[3] = {x, y, z};
-        encode_fp16<LFP>(g, ob, p, e);
-      }
-#pragma unroll
-      for (int c = 0; c < LFP / 8; ++c) store8(tb.E, s, c, LFP, e + 8 * c);
+    const bool has_next = pair + 1 < pair_hi;
+    if (has_next) {
+      nx_bi = locate_object(b, (pair + 1) * kTilesPerCta, bi);
+      nx_ob = &b.objs[b.slot[nx_bi]];
     }
     sync_then_issue();
     // ---- 3. forward ----------------------------------------------------------------------------------------------
@@ -626,6 +649,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
+    {  // while the MMAs run: part 0 of the next pair's sample and encoding
+      if (has_next) {
+        nx = make_sample(g, b, R, nx_ob, nx_bi, (pair + 1) * kTilesPerCta + wg - b.tile_base[nx_bi], s, P);
+#pragma unroll
+        for (int q = 0; q < LFP; ++q) ne[q] = 0.f;
+      }
+      if (has_next && nx.valid) {
+        constexpr int S0 = 0 * LMAX / 5, S1 = 1 * LMAX / 5;
+        const float p[3] = {nx.x, nx.y, nx.z};
+        gather_levels<LFP, S0, S1>(g, nx_ob, p, ne);
+      }
+    }
     if (!(ok = wait_mma())) break;
     epi_mask64(tmp, tb.H3, s);
     sync_then_issue();
@@ -641,6 +676,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
+    {  // while the MMAs run: part 1 of the next pair's sample and encoding
+      if (has_next && nx.valid) {
+        constexpr int S1 = 1 * LMAX / 5, S2 = 2 * LMAX / 5;
+        const float p[3] = {nx.x, nx.y, nx.z};
+        gather_levels<LFP, S1, S2>(g, nx_ob, p, ne);
+      }
+    }
     if (!(ok = wait_mma())) break;
     epi_mask64(tmp, tb.H2, s);
     sync_then_issue();
@@ -655,6 +697,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
+    }
+    {  // while the MMAs run: part 2 of the next pair's sample and encoding
+      if (has_next && nx.valid) {
+        constexpr int S2 = 2 * LMAX / 5, S3 = 3 * LMAX / 5;
+        const float p[3] = {nx.x, nx.y, nx.z};
+        gather_levels<LFP, S2, S3>(g, nx_ob, p, ne);
+      }
     }
     if (!(ok = wait_mma())) break;
     {  // dOUT = [dsigma * sigma, dCIN[0..14]] into DL
@@ -678,6 +727,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
+    {  // while the MMAs run: part 3 of the next pair's sample and encoding
+      if (has_next && nx.valid) {
+        constexpr int S3 = 3 * LMAX / 5, S4 = 4 * LMAX / 5;
+        const float p[3] = {nx.x, nx.y, nx.z};
+        gather_levels<LFP, S3, S4>(g, nx_ob, p, ne);
+      }
+    }
     if (!(ok = wait_mma())) break;
     epi_mask64(tmp, tb.H1, s);
     sync_then_issue();
@@ -692,6 +748,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
+    }
+    {  // while the MMAs run: part 4 of the next pair's sample and encoding
+      if (has_next && nx.valid) {
+        constexpr int S4 = 4 * LMAX / 5, S5 = LMAX;
+        const float p[3] = {nx.x, nx.y, nx.z};
+        gather_levels<LFP, S4, S5>(g, nx_ob, p, ne);
+      }
     }
     if (!(ok = wait_mma())) break;
     acc_dw = 1;
@@ -721,8 +784,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (ok && bi >= 0) {
     flush_dw<LFP>(tm, g, ob->grad);
   } else if (!ok) {
-    if (t == 0 && status) atomicOr(status, 2);
-    mbar_wait(&sm.mbar, phase ^ 1u);  // bounded: let the MMAs still in flight finish before the columns are freed
+    if (t == 0) {
+      if (status) atomicOr(status, 2);
+      mbar_wait(&sm.mbar, phase ^ 1u);  // bounded: let the MMAs still in flight finish before the columns are freed
+    }
   }
   tc_before();
   __syncthreads();
