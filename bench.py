@@ -247,6 +247,15 @@ def run_ours(args):
     value = live / (ms / 1e3)
     live_per_step = st.live_samples / args.steps  # this rank
     launches = st.kernel_launches
+    autotune = None
+    if main_prec == "mixed":
+        chosen = C.c_int32()
+        tms = (C.c_float * 4)()
+        names = C.create_string_buffer(256)
+        R.check(R.romap_autotune_report(h, C.byref(chosen), tms, 4, names, 256))
+        cands = names.value.decode().split(";")
+        autotune = {"chosen": cands[chosen.value] if chosen.value >= 0 else None,
+                    "ms_per_launch": {c: float(tms[i]) for i, c in enumerate(cands)}}
     # per-phase device time: the same steps again with CUDA events around every phase (eager launches)
     k_prof = max(3, min(args.steps, 100))
     R.check(R.romap_reset_stats(h))
@@ -421,7 +430,7 @@ def run_ours(args):
                           "l2": "inputs larger than L2: per step 219 MB of parameters, gradients and Adam moments "
                                 "plus 0.4 GB of ray pools (L2 129 MB)"},
                "live_samples_per_step": live_per_step, "roofline": roofline, "phases": phases,
-               "comparison": others, "loss_check": loss_cmp, "e2e": e2e, "cpu_baseline": cpu,
+               "comparison": others, "loss_check": loss_cmp, "autotune": autotune, "e2e": e2e, "cpu_baseline": cpu,
                "gpu_launches": int(launches), "clocks": clocks}
         if others.get("plain_fp32_per_object"):
             out["speedup_vs_plain_fp32_per_object"] = value / others["plain_fp32_per_object"]["value"]

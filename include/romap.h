@@ -281,6 +281,16 @@ ROMAP_API romap_status romap_reset_stats(romap_ctx* ctx);
  * [4] Adam.  ms and launches point to ROMAP_N_PHASES entries (launches
  * nullable). */
 #define ROMAP_N_PHASES 5
+/* Autotuner of the mixed-precision step: the first mixed step of a context
+ * times each candidate fused tile kernel on that batch and keeps the
+ * fastest.  chosen receives its index (-1 before the first mixed step), ms
+ * (n entries) the measured milliseconds per launch, names (nullable) the
+ * candidates' names separated by ';'. */
+/* Forces candidate `index` (0 = lockstep tile pairs, 1 = warp-specialized),
+ * or -1 to autotune again at the next mixed step. */
+ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);
+ROMAP_API romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, int32_t n, char* names,
+                                             size_t names_len);
 ROMAP_API romap_status romap_set_profiling(romap_ctx* ctx, int32_t on);
 ROMAP_API romap_status romap_phase_times(romap_ctx* ctx, double* ms, int64_t* launches);
 

@@ -102,6 +102,9 @@ struct romap_ctx {
   BatchDyn* dyn_host = nullptr;    // pinned
   romap_stats stats{};
   int64_t launches = 0;
+  // autotuned choice of the mixed-precision tile kernel: -1 until tuned, then an index of kTileKernels
+  int tile_kernel = -1;
+  float tile_kernel_ms[4] = {0, 0, 0, 0};
   // CUDA graph of one training step of the last batch composition (captured on cap_stream, replayed on stream)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t step_graph = nullptr;
@@ -466,6 +469,13 @@ romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBu
 
 int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
 
+// Candidate fused tile kernels of the mixed path (same results, different schedules).
+typedef void (*TileKernelFn)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int, int,
+                             cudaStream_t);
+const TileKernelFn kTileKernels[] = {launch_tile_tc, launch_tile_ws};
+const char* const kTileKernelNames[] = {"lockstep tile pairs", "warp-specialized"};
+constexpr int kNumTileKernels = 2;
+
 // Sampling stage of the mixed path: ray draw + slab + live counts, and the per-object scan (live-sample counter,
 // loss reset).  Samples are formed inside the fused kernel, so nothing is compacted.
 romap_status run_sampling_mixed(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBuf S, uint32_t* block_sums,
@@ -475,6 +485,42 @@ romap_status run_sampling_mixed(romap_ctx* ctx, const BatchDesc& b, RayBuf R, Sa
   launch_scan(ctx->g, b, block_sums, dyn, totals, S, ctx->live_counter, ctx->stream);
   ctx->launches += 2;
   CUDA_TRY(cudaGetLastError());
+  return ROMAP_OK;
+}
+
+const std::vector<int32_t>& v_ids_for_tuning(const std::vector<int32_t>& ids) { return ids; }
+
+// Times every candidate tile kernel on this batch (two launches each, CUDA events on the context's stream), keeps
+// the fastest, and undoes the candidates' side effects: their gradients are zeroed here, and the caller's sampling
+// stage that follows rewrites the ray records and resets the losses.
+romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& ids, const BatchDesc& b, int n_tiles,
+                                  int P) {
+  SampleBuf none{};
+  ROMAP_TRY(run_sampling_mixed(ctx, b, ctx->R, none, ctx->block_sums, ctx->dyn, ctx->totals));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int best = 0;
+  for (int k = 0; k < kNumTileKernels; ++k) {
+    kTileKernels[k](ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, n_tiles, tile_ctas(ctx), ctx->stream);  // warm
+    CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+    for (int rep = 0; rep < 2; ++rep)
+      kTileKernels[k](ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, n_tiles, tile_ctas(ctx), ctx->stream);
+    CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    ctx->tile_kernel_ms[k] = ms / 2.f;
+    if (ctx->tile_kernel_ms[k] < ctx->tile_kernel_ms[best]) best = k;
+    ctx->launches += 3;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CUDA_TRY(cudaGetLastError());
+  for (int32_t id : ids)
+    CUDA_TRY(cudaMemsetAsync(ctx->objs[id].grad, 0, sizeof(float) * ctx->g.n_params_pad, ctx->stream));
+  CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
+  ctx->tile_kernel = best;
   return ROMAP_OK;
 }
 
@@ -495,9 +541,11 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
   ROMAP_TRY(upload_batch(ctx, hb, &b));
   if (mixed) {
     SampleBuf none{};
+    if (ctx->tile_kernel < 0) ROMAP_TRY(autotune_tile_kernel(ctx, v_ids_for_tuning(ids), b, hb.n_tiles, P));
     ROMAP_TRY(run_sampling_mixed(ctx, b, ctx->R, none, ctx->block_sums, ctx->dyn, ctx->totals));
     PhaseScope ps(ctx, 3, 1);
-    launch_tile_tc(ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, hb.n_tiles, tile_ctas(ctx), ctx->stream);
+    kTileKernels[ctx->tile_kernel](ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, hb.n_tiles, tile_ctas(ctx),
+                                   ctx->stream);
     ctx->launches += 1;
   } else {
     ROMAP_TRY(run_sampling(ctx, b, ctx->R, ctx->S, ctx->block_sums, ctx->dyn, ctx->totals, true));
@@ -1062,6 +1110,27 @@ romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out) {
   *out = ctx->stats;
   out->live_samples = (int64_t)live;
   out->kernel_launches = ctx->launches;
+  return ROMAP_OK;
+}
+
+romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (index < -1 || index >= kNumTileKernels) return fail(ROMAP_ERR_INVALID_ARG, "tile kernel %d out of range", index);
+  ctx->tile_kernel = index;
+  drop_graph(ctx);
+  return ROMAP_OK;
+}
+
+romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, int32_t n, char* names,
+                                   size_t names_len) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (chosen) *chosen = ctx->tile_kernel;
+  for (int i = 0; ms && i < n && i < kNumTileKernels; ++i) ms[i] = ctx->tile_kernel_ms[i];
+  if (names && names_len) {
+    std::string all;
+    for (int i = 0; i < kNumTileKernels; ++i) all += std::string(i ? ";" : "") + kTileKernelNames[i];
+    snprintf(names, names_len, "%s", all.c_str());
+  }
   return ROMAP_OK;
 }
 

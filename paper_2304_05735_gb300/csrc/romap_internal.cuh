@@ -189,6 +189,10 @@ int tile_kernel_smem_bytes(int LF);
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
                     int total_tiles, int n_ctas, cudaStream_t stream);
 void launch_to_half(const float* params, uint16_t* table_h, int64_t n_hash, cudaStream_t stream);
+// Warp-specialized variant of launch_tile_tc (same results): compute warps run the MMA chain of one tile while
+// memory warps gather the next tile and scatter the previous one.
+void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
+                    int total_tiles, int n_ctas, cudaStream_t stream);
 // tiles the fused kernel processes together; every object's tile count is padded to a multiple of it
 int tc_tiles_per_cta();
 

@@ -1,0 +1,358 @@
+// tcgen05 helpers shared by the tensor-core tile kernels (instruction and shared-memory descriptors, TMEM loads,
+// BF16 operand rows, weight staging, weight-gradient flush, compositing of one ray, hash gathers, slot samples).
+// See kernels_tc.cu for the operand layouts.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "device_common.cuh"
+#include "romap_internal.cuh"
+
+namespace romap {
+namespace tc {
+
+
+constexpr int kT = 128;           // samples per tile (MMA M)
+constexpr int kTmemCols = 512;
+// TMEM columns: weight-gradient accumulators (shared by the tiles of a pair), then one 64-column temporary per tile
+constexpr uint32_t kColDW1 = 0, kColDW2 = 64, kColDW3 = 80, kColDW4 = 144, kColDW5 = 208, kColTmp = 256;
+constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// K-major operand: [rows][K] buffer; K-step kk covers columns 16 kk .. 16 kk + 15
+__device__ __forceinline__ uint64_t desc_k(const void* buf, int K, int kk) {
+  return make_desc(smem_u32(buf) + (uint32_t)kk * 256u, 128u, (uint32_t)(K / 8) * 128u);
+}
+// MN-major view of a K-major [rows][F] buffer: MN = its F columns, K = its rows; K-step kk covers rows 16 kk ..
+__device__ __forceinline__ uint64_t desc_mn(const void* buf, int F, int kk) {
+  return make_desc(smem_u32(buf) + (uint32_t)kk * 2u * (uint32_t)(F / 8) * 128u, (uint32_t)(F / 8) * 128u, 128u);
+}
+// instruction descriptor, kind::f16: BF16 A and B, FP32 D
+__host__ __device__ constexpr uint32_t idesc(int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  }
+  return done != 0;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32 w .. 32 w + 31)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of element (r, k) in a K-major [rows][K] BF16 buffer
+__device__ __forceinline__ uint32_t kmaj(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+// row r, 8 columns starting at 8c, packed as BF16
+__device__ __forceinline__ void store8(unsigned char* buf, int r, int c, int K, const float* v) {
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+  uint4 q;
+  q.x = *reinterpret_cast<uint32_t*>(&p0); q.y = *reinterpret_cast<uint32_t*>(&p1);
+  q.z = *reinterpret_cast<uint32_t*>(&p2); q.w = *reinterpret_cast<uint32_t*>(&p3);
+  *reinterpret_cast<uint4*>(buf + kmaj(r, 8 * c, K)) = q;
+}
+__device__ __forceinline__ void load8(const unsigned char* buf, int r, int c, int K, float* v) {
+  uint4 q = *reinterpret_cast<const uint4*>(buf + kmaj(r, 8 * c, K));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float2 f = __bfloat1622float2(h[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+template <int LFP, class Smem>
+__device__ void load_weights(Smem& sm, const GridParams& g, const float* __restrict__ P, int nthreads) {
+  const int t = threadIdx.x % nthreads;
+  for (int i = t; i < kH * LFP; i += nthreads) {
+    int o = i / LFP, k = i % LFP;
+    float v = k < g.LF ? P[g.mlp_off[0] + o * g.LF + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w1 + kmaj(o, k, LFP)) = __float2bfloat16_rn(v);
+  }
+  for (int i = t; i < 16 * kH; i += nthreads) {
+    int o = i / kH, k = i % kH;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w2 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[1] + i]);
+  }
+  for (int i = t; i < kH * 32; i += nthreads) {
+    int o = i / 32, k = i % 32;
+    float v = k < g.cin ? P[g.mlp_off[2] + o * g.cin + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w3 + kmaj(o, k, 32)) = __float2bfloat16_rn(v);
+  }
+  for (int i = t; i < kH * kH; i += nthreads) {
+    int o = i / kH, k = i % kH;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w4 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[3] + i]);
+  }
+  for (int i = t; i < 16 * kH; i += nthreads) {
+    int o = i / kH, k = i % kH;
+    float v = o < 3 ? P[g.mlp_off[4] + o * kH + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w5 + kmaj(o, k, kH)) = __float2bfloat16_rn(v);
+  }
+}
+
+// Adds the TMEM weight-gradient accumulators of one object to its FP32 gradient (rows = input features).
+template <int LFP>
+__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad) {
+  const int t = threadIdx.x, w = t >> 5;
+  if (w >= 2) return;  // rows 0..63 live in the lanes read by warps 0 and 1
+  const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);
+  const int row = t;
+  float v[16];
+  // dW1^T: rows = encoding features (LF), 64 columns (hidden units)
+  for (int c = 0; c < kH; c += 16) {
+    tmem_ld16(lane_base + kColDW1 + c, v);
+    tmem_wait_ld();
+    if (row < g.LF)
+      for (int j = 0; j < 16; ++j)
+        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[0] + (c + j) * g.LF + row, v[j]);
+  }
+  tmem_ld16(lane_base + kColDW2, v);  // dW2^T: rows = hidden (64), 16 columns (density outputs)
+  tmem_wait_ld();
+  for (int j = 0; j < 16; ++j)
+    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[1] + j * kH + row, v[j]);
+  for (int c = 0; c < kH; c += 16) {  // dW3^T: rows = colour inputs (cin), 64 columns
+    tmem_ld16(lane_base + kColDW3 + c, v);
+    tmem_wait_ld();
+    if (row < g.cin)
+      for (int j = 0; j < 16; ++j)
+        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[2] + (c + j) * g.cin + row, v[j]);
+  }
+  for (int c = 0; c < kH; c += 16) {  // dW4^T: rows = hidden (64), 64 columns
+    tmem_ld16(lane_base + kColDW4 + c, v);
+    tmem_wait_ld();
+    for (int j = 0; j < 16; ++j)
+      if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[3] + (c + j) * kH + row, v[j]);
+  }
+  tmem_ld16(lane_base + kColDW5, v);  // dW5^T: rows = hidden (64), columns 0..2 real
+  tmem_wait_ld();
+  for (int j = 0; j < 3; ++j)
+    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[4] + j * kH + row, v[j]);
+}
+
+__device__ __forceinline__ float warp_incl_prefix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+__device__ __forceinline__ float warp_incl_suffix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float n = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v += n;
+  }
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Eq. 6 + Eq. 7-11 + adjoint for one ray whose samples occupy slots [base, base + P) of the tile.
+template <class Bufs>
+__device__ void composite_ray(Bufs& sm, const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
+                              int bi, int64_t r, int base, int P, float invB, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
+  float carry = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dh = 0.f, ssum = 0.f;
+  for (int c = 0; c < P; c += 32) {
+    const int j = c + lane;
+    const bool in = j < P && sm.valid[base + j];
+    const int s = base + (j < P ? j : 0);
+    const float sg = in ? sm.sig[s] : 0.f, dt = in ? sm.dt[s] : 0.f, tt = in ? sm.t[s] : 0.f;
+    const float sd = sg * dt;
+    const float incl = warp_incl_prefix(sd, lane);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.f;
+    const float Pf = carry + excl;
+    const float w = expf(-Pf) * (-expm1f(-sd));
+    if (in) {
+      C0 = fmaf(w, sm.rgb[0][s], C0);
+      C1 = fmaf(w, sm.rgb[1][s], C1);
+      C2 = fmaf(w, sm.rgb[2][s], C2);
+      Dh = fmaf(w, tt, Dh);
+      ssum += sg;
+    }
+    if (j < P) sm.dsig[s] = Pf;  // exclusive prefix, consumed by the adjoint below
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  C0 = warp_sum(C0); C1 = warp_sum(C1); C2 = warp_sum(C2); Dh = warp_sum(Dh); ssum = warp_sum(ssum);
+  const float Tend = expf(-carry);
+  const float Ch0 = fmaf(Tend, bg0, C0), Ch1 = fmaf(Tend, bg1, C1), Ch2 = fmaf(Tend, bg2, C2);
+  if (lane == 0) {
+    float* o = R.out + 6 * r;
+    o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = -expm1f(-carry); o[5] = ssum;
+  }
+  // losses of Eq. 7-11 (every term divided by the batch size B)
+  const int cls = R.cls[r];
+  float loss = 0.f, l_rgb = 0.f, l_rr = 0.f, l_dep = 0.f, l_den = 0.f;
+  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gdir = 0.f;
+  if (cls != kClsOccluder) {
+    const float t0 = cls == kClsObject ? R.rgb[3 * r] : bg0;
+    const float t1 = cls == kClsObject ? R.rgb[3 * r + 1] : bg1;
+    const float t2 = cls == kClsObject ? R.rgb[3 * r + 2] : bg2;
+    const float e0 = Ch0 - t0, e1 = Ch1 - t1, e2 = Ch2 - t2;
+    const float sq = e0 * e0 + e1 * e1 + e2 * e2;
+    loss += sq;
+    if (cls == kClsObject) l_rgb = sq; else l_rr = sq;
+    gC0 = 2.f * e0 * invB; gC1 = 2.f * e1 * invB; gC2 = 2.f * e2 * invB;
+    const float dep = R.depth[r];
+    if (isfinite(dep)) {
+      const float e = Dh - dep;
+      loss += g.lambda1 * fabsf(e);
+      l_dep = fabsf(e);
+      gD = g.lambda1 * (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) * invB;
+    }
+    if (cls == kClsBackground) {
+      loss += g.lambda2 * ssum;
+      l_den = ssum;
+      gdir = g.lambda2 * invB;
+    }
+  }
+  if (lane == 0) {
+    float* L = dyn[bi].loss;
+    atomicAdd(L + 0, loss);
+    if (l_rgb != 0.f) atomicAdd(L + 1, l_rgb);
+    if (l_rr != 0.f) atomicAdd(L + 2, l_rr);
+    if (l_dep != 0.f) atomicAdd(L + 3, l_dep);
+    if (l_den != 0.f) atomicAdd(L + 4, l_den);
+    if (!isfinite(loss) && status) atomicOr(status, 1);
+  }
+  // adjoint, chunks in reverse order
+  float SC0 = 0.f, SC1 = 0.f, SC2 = 0.f, SD = 0.f;
+  const float bgterm = Tend * (gC0 * bg0 + gC1 * bg1 + gC2 * bg2);
+  for (int c = ((P - 1) / 32) * 32; c >= 0; c -= 32) {
+    const int j = c + lane;
+    const bool in = j < P && sm.valid[base + j];
+    const int s = base + (j < P ? j : 0);
+    const float sg = in ? sm.sig[s] : 0.f, dt = in ? sm.dt[s] : 0.f, tt = in ? sm.t[s] : 0.f;
+    const float Pf = (j < P) ? sm.dsig[s] : 0.f;
+    const float c0 = in ? sm.rgb[0][s] : 0.f, c1 = in ? sm.rgb[1][s] : 0.f, c2 = in ? sm.rgb[2][s] : 0.f;
+    const float sd = sg * dt;
+    const float Tn = expf(-(Pf + sd));
+    const float w = in ? expf(-Pf) * (-expm1f(-sd)) : 0.f;
+    float s0 = warp_incl_suffix(w * c0, lane), s1 = warp_incl_suffix(w * c1, lane);
+    float s2 = warp_incl_suffix(w * c2, lane), s3 = warp_incl_suffix(w * tt, lane);
+    float e0 = __shfl_down_sync(0xffffffffu, s0, 1), e1 = __shfl_down_sync(0xffffffffu, s1, 1);
+    float e2 = __shfl_down_sync(0xffffffffu, s2, 1), e3 = __shfl_down_sync(0xffffffffu, s3, 1);
+    if (lane == 31) e0 = e1 = e2 = e3 = 0.f;
+    float gs = gC0 * (Tn * c0 - (SC0 + e0)) + gC1 * (Tn * c1 - (SC1 + e1)) + gC2 * (Tn * c2 - (SC2 + e2)) - bgterm;
+    gs += gD * (Tn * tt - (SD + e3));
+    gs = dt * gs + gdir;
+    if (j < P) {
+      sm.dsig[s] = in ? gs : 0.f;
+      sm.drgb[0][s] = in ? gC0 * w : 0.f;
+      sm.drgb[1][s] = in ? gC1 * w : 0.f;
+      sm.drgb[2][s] = in ? gC2 * w : 0.f;
+    }
+    SC0 += __shfl_sync(0xffffffffu, s0, 0);
+    SC1 += __shfl_sync(0xffffffffu, s1, 0);
+    SC2 += __shfl_sync(0xffffffffu, s2, 0);
+    SD += __shfl_sync(0xffffffffu, s3, 0);
+  }
+}
+
+// Hash encoding of levels [L0, L1) of one sample from the FP16 table, two levels per round so that 16 gathers are
+// in flight; e holds the LFP features (levels outside [L0, L1) are left untouched).
+template <int LFP, int L0, int L1>
+__device__ __forceinline__ void gather_levels(const GridParams& g, const ObjectDev* ob, const float p[3], float* e) {
+  const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
+#pragma unroll
+  for (int l = L0; l < L1; l += 2) {
+    const bool has0 = l < g.L, has1 = (l + 1 < L1) && (l + 1 < g.L);
+    Corners c0, c1;
+    if (has0) level_corners(g, l, p, ob->half, ob->inv_ext, c0);
+    if (has1) level_corners(g, l + 1, p, ob->half, ob->inv_ext, c1);
+    __half2 v0[8], v1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v0[k] = has0 ? __ldg(tab + g.off[l] + c0.idx[k]) : __half2{};
+      v1[k] = has1 ? __ldg(tab + g.off[l + 1] + c1.idx[k]) : __half2{};
+    }
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 f0 = __half22float2(v0[k]), f1 = __half22float2(v1[k]);
+      if (has0) { a0 = fmaf(c0.w[k], f0.x, a0); a1 = fmaf(c0.w[k], f0.y, a1); }
+      if (has1) { b0 = fmaf(c1.w[k], f1.x, b0); b1 = fmaf(c1.w[k], f1.y, b1); }
+    }
+    e[2 * l] = a0; e[2 * l + 1] = a1;
+    if (l + 1 < L1) { e[2 * l + 2] = b0; e[2 * l + 3] = b1; }
+  }
+}
+
+// The sample of one slot: candidate i of ray rl of the object (same FP32 operations as the sampling kernels).
+struct SlotSample {
+  float x, y, z, t, dt;
+  int valid;
+};
+
+__device__ __forceinline__ SlotSample make_sample(const GridParams& g, const BatchDesc& b, const RayBuf& R,
+                                                  const ObjectDev* ob, int bi, int tile_local, int s, int P) {
+  SlotSample q{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+  const int N = g.n_samples;
+  const int rl = tile_local * (kT / P) + s / P;
+  const int i = s % P;
+  const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
+  if (rl >= n_rays_obj || i >= N) return q;
+  const int64_t r = b.ray_base[bi] + rl;
+  const float tn = R.tn[r], tf = R.tf[r];
+  if (!(tf > tn)) return q;
+  const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
+  const uint32_t step = ob->step;
+  q.t = candidate_t(tn, step_len, i, ob->key0, ob->key1, step, (uint32_t)rl, 1);
+  const float tnext = (i + 1 < N) ? candidate_t(tn, step_len, i + 1, ob->key0, ob->key1, step, (uint32_t)rl, 1) : tf;
+  q.dt = __fsub_rn(tnext, q.t);
+  q.x = __fadd_rn(R.o[3 * r], __fmul_rn(q.t, R.d[3 * r]));
+  q.y = __fadd_rn(R.o[3 * r + 1], __fmul_rn(q.t, R.d[3 * r + 1]));
+  q.z = __fadd_rn(R.o[3 * r + 2], __fmul_rn(q.t, R.d[3 * r + 2]));
+  q.valid = occupied(ob->occ, q.x, q.y, q.z, ob->half, ob->inv_ext) ? 1 : 0;
+  return q;
+}
+
+__device__ __forceinline__ int locate_object(const BatchDesc& b, int tile, int start) {
+  int i = start < 0 ? 0 : start;
+  while (i + 1 < b.n && tile >= b.tile_base[i + 1]) ++i;
+  return i;
+}
+
+
+}  // namespace tc
+}  // namespace romap

@@ -30,8 +30,9 @@ def _cos(a, b):
     return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("scene", ["plain", "masked"])
-def test_mixed_step_vs_oracle(torch, scene):
+def test_mixed_step_vs_oracle(torch, scene, kernel):
     if scene == "plain":
         oc, rc = paired_config(precision=MIXED)
         sc = synth.config0_scene()
@@ -41,6 +42,7 @@ def test_mixed_step_vs_oracle(torch, scene):
         sc = synth.multi_object_scene(1, seed0=5, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2, occluder_prob=1.0)[0]
     ctx = Ctx(rc)
     try:
+        R.check(R.romap_set_tile_kernel(ctx.h, kernel))
         oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed)
         ctx.add_rays(oid, sc.pool)
         pool = object_frame_pool(sc)
@@ -51,7 +53,7 @@ def test_mixed_step_vs_oracle(torch, scene):
         nh = O.hash_param_count(oc)
         rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
         rel_h, rel_m = _rel(g[:nh], ref["grad"][:nh]), _rel(g[nh:], ref["grad"][nh:])
-        print(f"\n[{scene}] mixed vs oracle: loss rel {rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
+        print(f"\n[{scene}, kernel {kernel}] mixed vs oracle: loss rel {rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
               f"(cos {_cos(g[:nh], ref['grad'][:nh]):.6f}), mlp-grad rel L2 {rel_m:.2e}")
         assert rel_loss < 1e-3
         assert rel_h < 5e-2 and rel_m < 5e-2
@@ -60,12 +62,14 @@ def test_mixed_step_vs_oracle(torch, scene):
         ctx.close()
 
 
-def test_mixed_batched_equals_separate(torch):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_mixed_batched_equals_separate(torch, kernel):
     oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, n_samples=32, rays_per_step=700, bg_random=True,
                            precision=MIXED)
     scenes = synth.multi_object_scene(3, seed0=21, n_frames=2, W=64, H=48, f=64.0)
     ctx = Ctx(rc)
     try:
+        R.check(R.romap_set_tile_kernel(ctx.h, kernel))
         ids = []
         for k, sc in enumerate(scenes):
             oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=333 + 100 * k)
@@ -75,6 +79,7 @@ def test_mixed_batched_equals_separate(torch):
         gb = [ctx.grad(i) for i in ids]
         ctx2 = Ctx(rc)
         try:
+            R.check(R.romap_set_tile_kernel(ctx2.h, 1 - kernel))  # the other kernel, one object at a time
             for k, sc in enumerate(scenes):
                 oid = ctx2.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=333 + 100 * k)
                 ctx2.add_rays(oid, sc.pool)
@@ -110,3 +115,25 @@ def test_mixed_training_tracks_fp32_training(torch):
     assert b[-1] < 0.3 * b[0]
     assert abs(a[0] - b[0]) / a[0] < 1e-3
     assert gap < 0.1
+
+
+def test_autotuner_picks_a_measured_candidate(torch):
+    oc, rc = paired_config(precision=MIXED)
+    ctx = Ctx(rc)
+    try:
+        sc = synth.config0_scene()
+        oid = ctx.create(seed=0)
+        ctx.add_rays(oid, sc.pool)
+        chosen = R.C.c_int32()
+        ms = (R.C.c_float * 4)()
+        names = R.C.create_string_buffer(256)
+        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 4, names, 256))
+        assert chosen.value == -1
+        ctx.train([oid], n_steps=2)
+        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 4, names, 256))
+        cands = names.value.decode().split(";")
+        print(f"\nautotuner: {dict(zip(cands, list(ms)[:len(cands)]))} -> {cands[chosen.value]}")
+        assert len(cands) == 2 and 0 <= chosen.value < 2
+        assert all(ms[i] > 0 for i in range(2)) and ms[chosen.value] == min(ms[0], ms[1])
+    finally:
+        ctx.close()
