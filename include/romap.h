@@ -286,6 +286,12 @@ ROMAP_API romap_status romap_reset_stats(romap_ctx* ctx);
  * fastest.  chosen receives its index (-1 before the first mixed step), ms
  * (n entries) the measured milliseconds per launch, names (nullable) the
  * candidates' names separated by ';'. */
+/* Failure-detection self-test: runs a kernel whose bounded wait on an
+ * mbarrier that nothing signals gives up after poll_limit polls, records
+ * the time-out in the device status word, frees its tensor memory and
+ * returns.  Returns ROMAP_ERR_TIMEOUT when the device reported the time-out
+ * (the expected outcome); the context stays usable. */
+ROMAP_API romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_limit);
 /* Forces candidate `index` (0 = lockstep tile pairs, 1 = warp-specialized),
  * or -1 to autotune again at the next mixed step. */
 ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);

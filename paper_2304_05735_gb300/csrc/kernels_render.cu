@@ -184,6 +184,18 @@ void launch_composite(int mode, const GridParams& g, const BatchDesc& b, RayBuf 
 // batch object; zeroes the gradient; optionally refreshes the FP16 copy of
 // the hash table.  float4 streaming, grid (chunks, objects).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void adam4(float4& p, float4& m, float4& v, const float4 gr, float b1, float b2, float ob1,
+                                      float ob2, float lr, float eps, float c1, float c2) {
+  float* pp = &p.x; float* mm = &m.x; float* vv = &v.x;
+  const float* gg = &gr.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    mm[k] = b1 * mm[k] + ob1 * gg[k];
+    vv[k] = b2 * vv[k] + ob2 * gg[k] * gg[k];
+    pp[k] -= lr * (mm[k] * c1) / (sqrtf(vv[k] * c2) + eps);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int write_half) {
   const ObjectDev& ob = b.objs[b.slot[blockIdx.y]];
   __shared__ float s_c[2];
@@ -200,27 +212,39 @@ __global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int wri
   float4* G = reinterpret_cast<float4*>(ob.grad);
   float4* M = reinterpret_cast<float4*>(ob.m);
   float4* V = reinterpret_cast<float4*>(ob.v);
+  __half2* H = reinterpret_cast<__half2*>(ob.table_h);
+  const bool half = write_half && ob.table_h;
   const int64_t n4 = g.n_params_pad / 4;
   const int64_t nh4 = g.n_hash / 4;  // n_hash is even; the FP16 copy covers whole float4s below n_hash
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 gr = G[i], m = M[i], v = V[i], p = P[i];
-    float gv[4] = {gr.x, gr.y, gr.z, gr.w}, mv[4] = {m.x, m.y, m.z, m.w}, vv[4] = {v.x, v.y, v.z, v.w};
-    float pv[4] = {p.x, p.y, p.z, p.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      mv[k] = b1 * mv[k] + ob1 * gv[k];
-      vv[k] = b2 * vv[k] + ob2 * gv[k] * gv[k];
-      pv[k] -= lr * (mv[k] * c1) / (sqrtf(vv[k] * c2) + eps);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // two float4 groups per thread in flight; the moments are streamed (only this kernel touches them)
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < n4; i += 2 * stride) {
+    const int64_t j = i + stride;
+    float4 g0 = G[i], g1 = G[j];
+    float4 m0 = __ldcs(M + i), m1 = __ldcs(M + j);
+    float4 v0 = __ldcs(V + i), v1 = __ldcs(V + j);
+    float4 p0 = P[i], p1 = P[j];
+    adam4(p0, m0, v0, g0, b1, b2, ob1, ob2, lr, eps, c1, c2);
+    adam4(p1, m1, v1, g1, b1, b2, ob1, ob2, lr, eps, c1, c2);
+    P[i] = p0; P[j] = p1;
+    __stcs(M + i, m0); __stcs(M + j, m1);
+    __stcs(V + i, v0); __stcs(V + j, v1);
+    G[i] = zero; G[j] = zero;
+    if (half) {
+      if (i < nh4) { H[2 * i] = __floats2half2_rn(p0.x, p0.y); H[2 * i + 1] = __floats2half2_rn(p0.z, p0.w); }
+      if (j < nh4) { H[2 * j] = __floats2half2_rn(p1.x, p1.y); H[2 * j + 1] = __floats2half2_rn(p1.z, p1.w); }
     }
-    P[i] = make_float4(pv[0], pv[1], pv[2], pv[3]);
-    M[i] = make_float4(mv[0], mv[1], mv[2], mv[3]);
-    V[i] = make_float4(vv[0], vv[1], vv[2], vv[3]);
-    G[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (write_half && ob.table_h && i < nh4) {
-      __half2 h0 = __floats2half2_rn(pv[0], pv[1]), h1 = __floats2half2_rn(pv[2], pv[3]);
-      reinterpret_cast<__half2*>(ob.table_h)[2 * i] = h0;
-      reinterpret_cast<__half2*>(ob.table_h)[2 * i + 1] = h1;
-    }
+  }
+  for (; i < n4; i += stride) {
+    float4 g0 = G[i], m0 = __ldcs(M + i), v0 = __ldcs(V + i), p0 = P[i];
+    adam4(p0, m0, v0, g0, b1, b2, ob1, ob2, lr, eps, c1, c2);
+    P[i] = p0;
+    __stcs(M + i, m0);
+    __stcs(V + i, v0);
+    G[i] = zero;
+    if (half && i < nh4) { H[2 * i] = __floats2half2_rn(p0.x, p0.y); H[2 * i + 1] = __floats2half2_rn(p0.z, p0.w); }
   }
 }
 
@@ -233,7 +257,7 @@ void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaSt
   if (b.n <= 0) return;
   int64_t n4 = g.n_params_pad / 4;
   int chunks = (int)((n4 + 255) / 256);
-  int max_chunks = 8192 / (b.n < 1 ? 1 : b.n) + 1;  // about 8k blocks in all: enough loads in flight for HBM
+  int max_chunks = 4096 / (b.n < 1 ? 1 : b.n) + 1;  // about 4k blocks of 256 threads, two float4 groups each
   if (max_chunks < 16) max_chunks = 16;
   if (chunks > max_chunks) chunks = max_chunks;
   k_adam<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, write_half);

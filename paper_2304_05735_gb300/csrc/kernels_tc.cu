@@ -482,6 +482,33 @@ void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayB
   else launch_tc_t<32>(g, b, dyn, r, status, P, total_tiles, n_ctas, stream);
 }
 
+// Failure-detection self-test: a bounded wait on an mbarrier that nothing signals must give up, record the
+// time-out in the status word (bit 1), free the tensor memory it holds and return.
+__global__ void k_selftest_wait(int32_t* status, int limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tslot)),
+                 "r"(32));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc::tc_before();
+  __syncthreads();
+  tc::tc_after();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, limit)) atomicOr(status, 2);
+  tc::tc_before();
+  __syncthreads();
+  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tslot), "r"(32));
+}
+
+void launch_selftest_wait(int32_t* status, int limit, cudaStream_t stream) {
+  k_selftest_wait<<<1, 64, 0, stream>>>(status, limit);
+}
+
 // FP16 copy of the hash table (n_hash is even)
 __global__ void k_to_half(const float* __restrict__ src, __half2* __restrict__ dst, int64_t n2) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)

@@ -601,6 +601,7 @@ romap_status read_losses(romap_ctx* ctx, int n, float* out_loss, int per_obj, co
   }
   if (bad) {
     CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
+    if (st & kStatusTimeout) return fail(ROMAP_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
     return fail(ROMAP_ERR_NONFINITE, "non-finite loss");
   }
   return ROMAP_OK;
@@ -1110,6 +1111,21 @@ romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out) {
   *out = ctx->stats;
   out->live_samples = (int64_t)live;
   out->kernel_launches = ctx->launches;
+  return ROMAP_OK;
+}
+
+romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_limit) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (poll_limit < 1) return fail(ROMAP_ERR_INVALID_ARG, "poll_limit must be >= 1");
+  CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
+  launch_selftest_wait(ctx->status, poll_limit, ctx->stream);
+  ctx->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  int32_t st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
+  if (st & kStatusTimeout) return fail(ROMAP_ERR_TIMEOUT, "self-test: the bounded wait gave up as expected");
   return ROMAP_OK;
 }
 

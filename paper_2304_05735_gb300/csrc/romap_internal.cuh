@@ -195,5 +195,8 @@ void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayB
                     int total_tiles, int n_ctas, cudaStream_t stream);
 // tiles the fused kernel processes together; every object's tile count is padded to a multiple of it
 int tc_tiles_per_cta();
+// status word bits written by the kernels
+constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2;
+void launch_selftest_wait(int32_t* status, int limit, cudaStream_t stream);
 
 }  // namespace romap

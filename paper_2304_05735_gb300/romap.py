@@ -104,6 +104,7 @@ SIGNATURES = {
     "romap_reset_stats": (_i32, [_vp]),
     "romap_fn_forward_noalloc": (_i32, [_P(romap_config), _vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _i64, _u32,
                                         _vp]),
+    "romap_selftest_wait_timeout": (_i32, [_vp, _i32]),
     "romap_set_tile_kernel": (_i32, [_vp, _i32]),
     "romap_autotune_report": (_i32, [_vp, _P(_i32), _vp, _i32, C.c_char_p, _sz]),
     "romap_set_profiling": (_i32, [_vp, _i32]),

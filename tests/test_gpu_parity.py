@@ -386,3 +386,42 @@ def test_graph_replay_matches_eager_launches(torch, precision):
     for x, y in zip(pa, pb):
         assert np.linalg.norm(x - y) <= 1e-2 * np.linalg.norm(y)
         assert np.mean(np.isclose(x, y, rtol=1e-3, atol=1e-5)) > 0.995
+
+
+def test_device_wait_timeout_is_reported_and_context_survives(torch):
+    """A bounded device wait that nothing signals gives up and reports ROMAP_ERR_TIMEOUT; training continues."""
+    oc, rc = paired_config(precision=R.ROMAP_PREC_MIXED_BF16)
+    ctx = Ctx(rc)
+    try:
+        assert R.romap_selftest_wait_timeout(ctx.h, 1 << 14) == R.ROMAP_ERR_TIMEOUT
+        assert "gave up" in R.last_error()
+        sc = synth.config0_scene()
+        oid = ctx.create(seed=0)
+        ctx.add_rays(oid, sc.pool)
+        assert np.isfinite(ctx.train([oid], n_steps=2)).all()
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, R.ROMAP_PREC_MIXED_BF16])
+def test_nonfinite_device_rays_reported_through_status_word(torch, precision):
+    """Device-pointer rays skip the host-side finiteness check; a NaN target reaches the loss and the device status
+    word turns it into ROMAP_ERR_NONFINITE; the context stays usable."""
+    oc, rc = paired_config(precision=precision)
+    ctx = Ctx(rc)
+    try:
+        sc = synth.config0_scene()
+        oid = ctx.create(seed=0)
+        dev = {k: torch.tensor(v, device="cuda") for k, v in sc.pool.items()}
+        dev["rgb"][::7, 0] = float("nan")
+        rays = R.romap_rays(dev["origin"].data_ptr(), dev["dir"].data_ptr(), dev["rgb"].data_ptr(),
+                            dev["depth"].data_ptr(), dev["cls"].data_ptr())
+        R.check(R.romap_add_rays(ctx.h, oid, R.C.byref(rays), sc.pool["cls"].size, R.ROMAP_DEVICE_PTR))
+        with pytest.raises(R.RomapError) as e:
+            ctx.train([oid])
+        assert e.value.status == R.ROMAP_ERR_NONFINITE
+        ctx.add_rays(oid, sc.pool, flags=R.ROMAP_REPLACE)
+        ctx.set_state(oid, O.init_params(oc, 0))
+        assert np.isfinite(ctx.train([oid])).all()
+    finally:
+        ctx.close()
