@@ -111,9 +111,16 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "fp32": ("kernels_tile.cu", "device_common.cuh", "romap_internal.cuh"),
+    "mixed": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
+}
+
+
+def kernel_source_hash(precision):
+    """Hash of the sources the dominant kernel of `precision` is built from (profiles/dram_traffic.json keys)."""
     h = hashlib.sha256()
-    for name in ("kernels_tile.cu", "romap_internal.cuh"):
+    for name in KERNEL_SOURCES[precision]:
         with open(os.path.join(ROOT, "paper_2304_05735_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -127,7 +134,7 @@ def profiled_traffic(kernel, precision):
     try:
         d = json.load(open(path))
         e = d.get(f"{kernel}|{precision}")
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash(precision):
             return e.get("bytes_per_launch_full_workload")
     except (OSError, ValueError):
         return None

@@ -104,7 +104,9 @@ typedef struct romap_config {
   int32_t max_objects;     /* capacity of live objects */
   int64_t max_rays_per_object; /* ray-pool capacity of one object */
   /* Optional device allocator (both or neither).  alloc returns NULL on
-   * failure, which the library reports as ROMAP_ERR_OOM. */
+   * failure, which the library reports as ROMAP_ERR_OOM; a pointer that is
+   * not 256-byte aligned is handed back to dealloc and reported as
+   * ROMAP_ERR_INVALID_ARG. */
   void* (*alloc)(void* user, size_t bytes);
   void (*dealloc)(void* user, void* ptr);
   void* alloc_user;
@@ -136,7 +138,8 @@ typedef struct romap_layout {
   int32_t n_levels;
   int32_t resolution[16];    /* N_l */
   int32_t dense[16];         /* 1 if level l is dense */
-  int64_t level_offset[16];  /* first entry of level l */
+  int64_t level_offset[16];  /* first entry of level l: a multiple of 8; entries
+                                between (N_l+1)^3 and the next level are unused */
   int64_t mlp_offset[5];     /* parameter offset of MLP layers: density 1, density 2, colour 1, colour 2, colour 3 */
   int32_t mlp_rows[5], mlp_cols[5]; /* row-major [out][in] */
 } romap_layout;
@@ -237,7 +240,8 @@ ROMAP_API romap_status romap_fn_forward(romap_ctx* ctx, const float* params, con
                               const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
                               float* out_ray, float* out_samples);
 /* Backward of romap_fn_forward given dL/d(out_ray) grad_ray [6n]; adds
- * dL/dparams into grad_params (n_params floats, device).  out_dsigma
+ * dL/dparams into grad_params (n_params floats, device, 16-byte aligned,
+ * else ROMAP_ERR_INVALID_ARG).  out_dsigma
  * (nullable, [n*N]) receives dL/dsigma per sample slot (0 for missed or
  * culled slots).  flags: ROMAP_JITTER as in the forward. */
 ROMAP_API romap_status romap_fn_backward(romap_ctx* ctx, const float* params, const float half_size[3], uint64_t seed,

@@ -130,9 +130,11 @@ int oc_level_is_dense(const oc_config* c, int l) { return level_dense_count(c, l
 uint64_t oc_level_size(const oc_config* c, int l) {
   return oc_level_is_dense(c, l) ? level_dense_count(c, l) : (uint64_t)c->T;
 }
+/* Storage layout (not part of the method): each level's entries start at a multiple of 8 entries, so a level of
+ * (N+1)^3 dense entries is followed by up to 7 unused entries. */
 uint64_t oc_level_offset(const oc_config* c, int l) {
   uint64_t off = 0;
-  for (int i = 0; i < l; ++i) off += oc_level_size(c, i);
+  for (int i = 0; i < l; ++i) off += (oc_level_size(c, i) + 7u) / 8u * 8u;
   return off;
 }
 uint64_t oc_hash_param_count(const oc_config* c) {

@@ -74,6 +74,29 @@ __device__ inline void for_candidates(const float o[3], const float d[3], float 
 __device__ __forceinline__ void red_add2(float2* addr, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
 }
+// 16-byte aligned addr
+__device__ __forceinline__ void red_add4(float2* addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+// Scatter of one level: the 8 corner gradients (w_k d0, w_k d1) added into the FP32 gradient of the level (gt points
+// at the level's first entry, 16-byte aligned since levels start at multiples of 8 entries).  Corners k and k+1
+// differ by one step in x; when their entries form an aligned pair {2m, 2m+1} (x even on a hashed level, an even
+// index on a dense one) one 16-byte vector add covers both, which saves one L1->L2 request.
+__device__ __forceinline__ void scatter_corners(float2* gt, const uint32_t idx[8], const float w[8], float d0,
+                                                float d1) {
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) {
+    const uint32_t i0 = idx[k], i1 = idx[k + 1];
+    const float a0 = w[k] * d0, a1 = w[k] * d1, b0 = w[k + 1] * d0, b1 = w[k + 1] * d1;
+    if ((i0 ^ i1) == 1u) {
+      if (i0 < i1) red_add4(gt + i0, a0, a1, b0, b1);
+      else red_add4(gt + i1, b0, b1, a0, a1);
+    } else {
+      red_add2(gt + i0, a0, a1);
+      red_add2(gt + i1, b0, b1);
+    }
+  }
+}
 
 // Position of candidate i of a ray (same operations as for_candidates).
 __device__ inline float candidate_t(float tn, float step_len, int i, uint32_t k0, uint32_t k1, uint32_t step,
@@ -115,7 +138,8 @@ __device__ inline void level_corners(const GridParams& g, int l, const float p[3
     uint32_t cx = (uint32_t)(i0[0] + (k & 1));
     uint32_t cy = (uint32_t)(i0[1] + ((k >> 1) & 1));
     uint32_t cz = (uint32_t)(i0[2] + ((k >> 2) & 1));
-    c.idx[k] = dense ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) % g.T);
+    // T = 2^log2_table_size, so the modulo is a mask
+    c.idx[k] = dense ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) & (g.T - 1u));
     float wx = (k & 1) ? f[0] : 1.0f - f[0];
     float wy = ((k >> 1) & 1) ? f[1] : 1.0f - f[1];
     float wz = ((k >> 2) & 1) ? f[2] : 1.0f - f[2];

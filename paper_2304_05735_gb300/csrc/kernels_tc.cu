@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           Corners c;
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) red_add2(gt + g.off[l] + c.idx[k], c.w[k] * d0, c.w[k] * d1);
+          scatter_corners(gt + g.off[l], c.idx, c.w, d0, d1);
         }
       }
     }

@@ -396,8 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           Corners c;
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
           float2* gt = reinterpret_cast<float2*>(ob->grad) + g.off[l];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) red_add2(gt + c.idx[k], c.w[k] * d0, c.w[k] * d1);
+          scatter_corners(gt, c.idx, c.w, d0, d1);
         }
       }
     }

@@ -125,7 +125,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
           Corners c;
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) red_add2(gt + g.off[l] + c.idx[q], c.w[q] * d0, c.w[q] * d1);
+          scatter_corners(gt + g.off[l], c.idx, c.w, d0, d1);
         }
       }
     }

@@ -129,6 +129,11 @@ romap_status dev_alloc(romap_ctx* ctx, size_t bytes, void** out) {
   if (ctx->cfg.alloc) {
     *out = ctx->cfg.alloc(ctx->cfg.alloc_user, bytes);
     if (!*out) return fail(ROMAP_ERR_OOM, "device allocation of %zu bytes failed (caller allocator)", bytes);
+    if (reinterpret_cast<uintptr_t>(*out) % 256 != 0) {  // vector loads and reductions assume aligned bases
+      ctx->cfg.dealloc(ctx->cfg.alloc_user, *out);
+      *out = nullptr;
+      return fail(ROMAP_ERR_INVALID_ARG, "the caller allocator returned a pointer that is not 256-byte aligned");
+    }
     return ROMAP_OK;
   }
   cudaError_t e = cudaMallocAsync(out, bytes, ctx->stream);
@@ -394,7 +399,7 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
     uint64_t dense = n1 * n1 * n1;
     G.dense[l] = dense <= (uint64_t)G.T ? 1 : 0;
     G.off[l] = (uint32_t)off;
-    off += G.dense[l] ? dense : (uint64_t)G.T;
+    off += ((G.dense[l] ? dense : (uint64_t)G.T) + 7u) / 8u * 8u;  // levels start at multiples of 8 entries
     if (off >= ((uint64_t)1 << 31)) return fail(ROMAP_ERR_INVALID_ARG, "hash table too large");
   }
   G.n_hash = (int64_t)off * 2;
@@ -1321,6 +1326,8 @@ romap_status romap_fn_backward(romap_ctx* ctx, const float* params, const float 
                                const float* grad_ray, float* grad_params, float* out_dsigma) {
   ROMAP_TRY(check_ctx(ctx));
   if (!grad_ray || !grad_params) return fail(ROMAP_ERR_INVALID_ARG, "grad_ray and grad_params are required");
+  if (reinterpret_cast<uintptr_t>(grad_params) % 16 != 0)
+    return fail(ROMAP_ERR_INVALID_ARG, "grad_params must be 16-byte aligned");
   FnView v;
   BatchDesc b;
   ROMAP_TRY(fn_setup(ctx, params, grad_params, half_size, seed, step, occupancy, origin, dir, bg, n, flags,
