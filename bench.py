@@ -27,11 +27,31 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2304_05735_gb300.sharding import max_over_ranks, sum_over_ranks  # noqa: E402
+
 METRIC = "train samples/s (fwd+bwd+Adam), batched mixed vs plain fp32, at oracle-matched loss"
-WORKLOAD = dict(objects=8, rays_per_object=4096, samples_per_ray=64, levels=16, features=2, log2_table=16,
-                base_resolution=16, max_resolution=512, frames=30, width=320, height=240, focal=320.0)
-WORKLOAD_NAME = ("multi-object training: 8 objects x 4096 rays x 64 samples per step, hash grid L=16 F=2 T=2^16 "
-                 "(16->512), MLP 32-64-16 / 18-64-64-3, 30 frames of 320x240 per object")
+WORKLOADS = {
+    # the default: 8 objects of equal batch size (weak scaling under torchrun: every rank trains 8 objects)
+    "multi8": dict(
+        name="multi-object training: 8 objects x 4096 rays x 64 samples per step, hash grid L=16 F=2 T=2^16 "
+             "(16->512), MLP 32-64-16 / 18-64-64-3, 30 frames of 320x240 per object",
+        objects=8, rays_per_object=4096, samples_per_ray=64, levels=16, features=2, log2_table=16,
+        base_resolution=16, max_resolution=512, frames=30, width=320, height=240, focal=320.0, occupancy=None,
+        seed0=1, scaling="weak",
+        l2="inputs larger than L2: per step 219 MB of parameters, gradients and Adam moments plus 0.4 GB of ray "
+           "pools (L2 129 MB)"),
+    # uneven batches with occupancy culling (the objects are placed on ranks by LPT bin-packing: strong scaling)
+    "uneven32": dict(
+        name="uneven batched training: 32 objects, rays per object per step log-uniform in 256..16384 (seeded, "
+             "fixed per object), 128 candidate samples per ray culled by a 64^3 occupancy bitgrid (shape dilated "
+             "by 2 cells plus 5% random cells), hash grid L=16 F=2 T=2^19 (16->512), 3 frames of 640x480 per object",
+        objects=32, rays_per_object=(256, 16384), samples_per_ray=128, levels=16, features=2, log2_table=19,
+        base_resolution=16, max_resolution=512, frames=3, width=640, height=480, focal=640.0,
+        occupancy=dict(dilate=2, p=0.05), seed0=40, scaling="strong",
+        l2="inputs larger than L2: per step 6.1 GB of parameters, gradients, Adam moments and FP16 tables "
+           "(L2 129 MB)"),
+}
+WORKLOAD = WORKLOADS["multi8"]
 # FP32 SIMT peak of the GB300: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2070 MHz maximum SM clock.
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithmic work per live sample (real multiply-adds of the five layers, no padding):
@@ -50,11 +70,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "mixed"), default="mixed")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="multi8")
     ap.add_argument("--loss-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     return ap.parse_args()
+
+
+def config_keys(w):
+    return {k: v for k, v in w.items() if k not in ("name", "scaling", "seed0")}
 
 
 def dist_env():
@@ -141,11 +166,53 @@ def profiled_traffic(kernel, precision):
     return None
 
 
+class Item:
+    """One object of the workload on this rank: its scene, rays per step and occupancy bitgrid (or None)."""
+
+    def __init__(self, scene, rays, occ):
+        self.scene, self.rays, self.occ = scene, rays, occ
+
+
+def workload_rays(w):
+    if isinstance(w["rays_per_object"], int):
+        return [w["rays_per_object"]] * w["objects"]
+    import numpy as np
+
+    lo, hi = w["rays_per_object"]
+    rng = np.random.default_rng(7)
+    return [int(r) for r in np.exp(rng.uniform(np.log(lo), np.log(hi), w["objects"]))]
+
+
+def build_items(w, rank, world):
+    """This rank's objects.  Equal batches: every rank trains its own w["objects"] objects (seeds shifted by rank).
+    Uneven batches: the w["objects"] objects are placed on the ranks by LPT bin-packing on rays x samples."""
+    from paper_2304_05735_gb300 import synth
+    from paper_2304_05735_gb300.sharding import lpt_partition
+
+    rays = workload_rays(w)
+    if w["scaling"] == "weak":
+        seeds = [w["seed0"] + w["objects"] * rank + k for k in range(w["objects"])]
+        mine = list(range(w["objects"]))
+    else:
+        mine = lpt_partition([r * w["samples_per_ray"] for r in rays], world)[rank]
+        seeds = [w["seed0"] + k for k in mine]
+    items = []
+    for k, seed in zip(mine, seeds):
+        sc = synth.multi_object_scene(1, seed0=seed, n_frames=w["frames"], W=w["width"], H=w["height"],
+                                      f=w["focal"])[0]
+        occ = None
+        if w["occupancy"]:
+            occ = synth.occupancy_bits(sc.shape, sc.half, dilate=w["occupancy"]["dilate"], p=w["occupancy"]["p"],
+                                       seed=sc.seed)
+        items.append(Item(sc, rays[k], occ))
+    return items
+
+
 def make_ctx(R, torch, precision):
     w = WORKLOAD
     rc = R.make_config(n_levels=w["levels"], log2_table_size=w["log2_table"], base_resolution=w["base_resolution"],
                        growth=0.0, max_resolution=w["max_resolution"], n_samples=w["samples_per_ray"],
-                       rays_per_step=w["rays_per_object"], bg_random=True,
+                       rays_per_step=4096, bg_random=True,
                        precision=R.ROMAP_PREC_MIXED_BF16 if precision == "mixed" else R.ROMAP_PREC_FP32,
                        max_objects=2 * w["objects"])
     h = C.c_void_p()
@@ -153,12 +220,18 @@ def make_ctx(R, torch, precision):
     return rc, h
 
 
-def add_objects(R, h, scenes):
+def add_objects(R, h, items):
+    import numpy as np
+
     ids = []
-    for sc in scenes:
+    for it in items:
+        sc = it.scene
         oid = C.c_int32()
-        d = R.object_desc(t=tuple(sc.t), yaw=sc.yaw, half_size=tuple(sc.half), seed=sc.seed)
+        d = R.object_desc(t=tuple(sc.t), yaw=sc.yaw, half_size=tuple(sc.half), seed=sc.seed, rays_per_step=it.rays)
         R.check(R.romap_create_object(h, C.byref(d), C.byref(oid)), "romap_create_object")
+        if it.occ is not None:
+            bits = np.ascontiguousarray(it.occ)
+            R.check(R.romap_set_occupancy(h, oid.value, bits.ctypes.data, 0), "romap_set_occupancy")
         p = sc.pool
         rays = R.romap_rays(p["origin"].ctypes.data, p["dir"].ctypes.data, p["rgb"].ctypes.data,
                             p["depth"].ctypes.data, p["cls"].ctypes.data)
@@ -180,19 +253,11 @@ def timed(torch, fn, world, dist):
     if world > 1:
         dist.barrier()
     ms = s.elapsed_time(e)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    return max_over_ranks(ms, dist if world > 1 else None, "cuda")
 
 
 def allsum(torch, dist, world, x):
-    if world == 1:
-        return x
-    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t)
-    return t.item()
+    return sum_over_ranks(x, dist if world > 1 else None, "cuda") if world > 1 else x
 
 
 def run_ours(args):
@@ -212,9 +277,8 @@ def run_ours(args):
 
     R.lib()
     w = WORKLOAD
-    scenes = synth.multi_object_scene(w["objects"], seed0=1 + w["objects"] * rank, n_frames=w["frames"],
-                                      W=w["width"], H=w["height"], f=w["focal"])
-    n = len(scenes)
+    items = build_items(w, rank, world)
+    n = len(items)
     main_prec = args.precision
 
     # ---- loss comparison: same seeds, batched mixed vs batched FP32, per-step losses (untimed) -------------------
@@ -222,7 +286,7 @@ def run_ours(args):
     if not args.no_plain:
         for prec in ("fp32", "mixed"):
             rc, h = make_ctx(R, torch, prec)
-            ids = add_objects(R, h, scenes)
+            ids = add_objects(R, h, items)
             idarr = (C.c_int32 * n)(*ids)
             ls = np.zeros((args.loss_steps, n), np.float32)
             for k in range(args.loss_steps):
@@ -232,7 +296,7 @@ def run_ours(args):
 
     # ---- the timed batched step -------------------------------------------------------------------------------------
     rc, h = make_ctx(R, torch, main_prec)
-    ids = add_objects(R, h, scenes)
+    ids = add_objects(R, h, items)
     idarr = (C.c_int32 * len(ids))(*ids)
     R.check(R.romap_train_step(h, idarr, n, max(args.warmup, 3), None))
     torch.cuda.synchronize()
@@ -327,18 +391,18 @@ def run_ours(args):
                     "unit": "GB/s", "frac": (ach / hbm) if ach else None, "traffic": None}
 
     # ---- end to end through the C ABI with host buffers ---------------------------------------------------------------
-    # each step replaces every object's rays with a fresh batch of 4096 rays from pinned host memory, trains, and
-    # reads the losses back
+    # each step replaces every object's rays with a fresh batch of its rays per step from pinned host memory, trains,
+    # and reads the losses back
     e2e = None
     if not args.no_e2e:
         rng = np.random.default_rng(100 + rank)
-        B = w["rays_per_object"]
         k_e2e = max(3, min(args.steps, 50))
         batches = []
         for _ in range(k_e2e + 2):
             per = []
-            for sc in scenes:
-                sel = rng.integers(0, sc.pool["cls"].size, B)
+            for it in items:
+                sc = it.scene
+                sel = rng.integers(0, sc.pool["cls"].size, it.rays)
                 arrs = {}
                 for k in ("origin", "dir", "rgb", "depth", "cls"):
                     a = sc.pool[k][sel]
@@ -347,14 +411,14 @@ def run_ours(args):
                     arrs[k] = t
                 per.append(arrs)
             batches.append(per)
-        h2d = sum(t.numel() * t.element_size() for t in batches[0][0].values()) * n
+        h2d = sum(t.numel() * t.element_size() for per in batches[:1] for arrs in per for t in arrs.values())
         loss = np.zeros(n, np.float32)
 
         def e2e_step(per):
-            for i, arrs in zip(ids, per):
+            for i, it, arrs in zip(ids, items, per):
                 rays = R.romap_rays(arrs["origin"].data_ptr(), arrs["dir"].data_ptr(), arrs["rgb"].data_ptr(),
                                     arrs["depth"].data_ptr(), arrs["cls"].data_ptr())
-                R.check(R.romap_add_rays(h, i, C.byref(rays), B, R.ROMAP_REPLACE), "romap_add_rays")
+                R.check(R.romap_add_rays(h, i, C.byref(rays), it.rays, R.ROMAP_REPLACE), "romap_add_rays")
             R.check(R.romap_train_step(h, idarr, n, 1, loss.ctypes.data), "romap_train_step")
 
         for per in batches[:2]:
@@ -368,16 +432,13 @@ def run_ours(args):
             e2e_step(per)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = t.item()
+        el = max_over_ranks(el, dist if world > 1 else None, "cuda")
         ste = R.romap_stats()
         R.check(R.romap_get_stats(h, C.byref(ste)))
         live_e = allsum(torch, dist, world, ste.live_samples)
         e2e = {"value": live_e / el, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(n * 48 + 4), "steps": k_e2e,
-               "path": "romap_add_rays(REPLACE, pinned host) x 8 + romap_train_step(out_loss to host), wall clock"}
+               "path": f"romap_add_rays(REPLACE, pinned host) x {n} + romap_train_step(out_loss to host), wall clock"}
     R.check(R.romap_destroy(h))
 
     # ---- the comparison paths: batched FP32 and the plain per-object FP32 path ---------------------------------------
@@ -385,7 +446,7 @@ def run_ours(args):
     if not args.no_plain:
         k_cmp = max(5, min(args.steps, 100))
         rc2, h2 = make_ctx(R, torch, "fp32")
-        ids2 = add_objects(R, h2, scenes)
+        ids2 = add_objects(R, h2, items)
         arr2 = (C.c_int32 * n)(*ids2)
         R.check(R.romap_train_step(h2, arr2, n, 3, None))
         for label, per_object in (("batched_fp32", False), ("plain_fp32_per_object", True)):
@@ -427,15 +488,14 @@ def run_ours(args):
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": w["scaling"], "vs_baseline": None,
                "dtype": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)" if mixed
                else "f32",
                "data": "synthetic (analytic shapes, seeded)",
-               "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "precision": main_prec, "path": "batched",
-                          "parallelism": f"replicas x{world} (objects sharded, no collective)",
-                          "l2": "inputs larger than L2: per step 219 MB of parameters, gradients and Adam moments "
-                                "plus 0.4 GB of ray pools (L2 129 MB)"},
+               "config": {"workload": w["name"], **config_keys(w), "precision": main_prec, "path": "batched",
+                          "objects_this_rank": n, "rays_per_step_this_rank": int(sum(it.rays for it in items)),
+                          "parallelism": f"{world} rank(s), objects sharded, no collective"},
                "live_samples_per_step": live_per_step, "roofline": roofline, "phases": phases,
                "comparison": others, "loss_check": loss_cmp, "autotune": autotune, "e2e": e2e, "cpu_baseline": cpu,
                "gpu_launches": int(launches), "clocks": clocks}
@@ -450,32 +510,38 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # the CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def _oracle_setup(n_rays, seed=1):
+def _oracle_setup(n_rays):
+    """One object of the workload (its first seed, up to 4 frames, its occupancy bitgrid if the workload culls)."""
     import numpy as np
 
     from oracle import romap_oracle as O
     from paper_2304_05735_gb300 import synth
 
     w = WORKLOAD
-    sc = synth.multi_object_scene(1, seed0=seed, n_frames=4, W=w["width"], H=w["height"], f=w["focal"])[0]
+    sc = synth.multi_object_scene(1, seed0=w["seed0"], n_frames=min(4, w["frames"]), W=w["width"], H=w["height"],
+                                  f=w["focal"])[0]
+    occ = None
+    if w["occupancy"]:
+        occ = synth.occupancy_bits(sc.shape, sc.half, dilate=w["occupancy"]["dilate"], p=w["occupancy"]["p"],
+                                   seed=sc.seed)
     oc = O.make_config(L=w["levels"], T=2 ** w["log2_table"], n_min=w["base_resolution"], growth=0.0,
                        n_max=w["max_resolution"], n_samples=w["samples_per_ray"], rays_per_step=n_rays,
                        bg_random=True)
     o, d = O.world_to_object(sc.pool["origin"], sc.pool["dir"], sc.t.astype(np.float32), sc.yaw)
     pool = dict(o=o, d=d, rgb=sc.pool["rgb"], depth=sc.pool["depth"], cls=sc.pool["cls"])
     p = O.init_params(oc, sc.seed)
-    return O, oc, sc, pool, p
+    return O, oc, sc, pool, p, occ
 
 
 def cpu_baseline(n_rays=4096, steps=1):
     import numpy as np
 
-    O, oc, sc, pool, p = _oracle_setup(n_rays)
+    O, oc, sc, pool, p, occ = _oracle_setup(n_rays)
     m, v = np.zeros_like(p), np.zeros_like(p)
     live = 0
     t0 = time.perf_counter()
     for s in range(1, steps + 1):
-        r = O.train_step(oc, sc.half.astype(np.float32), sc.seed, s, pool, p, m, v, want_samples=True)
+        r = O.train_step(oc, sc.half.astype(np.float32), sc.seed, s, pool, p, m, v, occ=occ, want_samples=True)
         p, m, v = r["params"], r["m"], r["v"]
         live += int(r["samples"][:, :, 5].sum())
     el = time.perf_counter() - t0
@@ -491,29 +557,31 @@ def run_reference(args):
     import numpy as np
 
     n_rays = 256
-    O, oc, sc, pool, p = _oracle_setup(n_rays)
+    O, oc, sc, pool, p, occ = _oracle_setup(n_rays)
     m, v = np.zeros_like(p), np.zeros_like(p)
     half = sc.half.astype(np.float32)
     step = 1
     for _ in range(args.warmup):
-        r = O.train_step(oc, half, sc.seed, step, pool, p, m, v)
+        r = O.train_step(oc, half, sc.seed, step, pool, p, m, v, occ=occ)
         p, m, v = r["params"], r["m"], r["v"]
         step += 1
     live = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r = O.train_step(oc, half, sc.seed, step, pool, p, m, v, want_samples=True)
+        r = O.train_step(oc, half, sc.seed, step, pool, p, m, v, occ=occ, want_samples=True)
         p, m, v = r["params"], r["m"], r["v"]
         live += int(r["samples"][:, :, 5].sum())
         step += 1
     el = time.perf_counter() - t0
     value = live / el
-    sample = (f"each step: 1 object x {n_rays} rays x {WORKLOAD['samples_per_ray']} samples of the workload's model "
-              f"(L=16, T=2^16) incl. dense Adam over all parameters; FP64 C oracle, one thread")
+    w = WORKLOAD
+    sample = (f"each step: 1 object x {n_rays} rays x {w['samples_per_ray']} samples of the workload's model "
+              f"(L={w['levels']}, T=2^{w['log2_table']}{', occupancy-culled' if occ is not None else ''}) incl. "
+              f"dense Adam over all parameters; FP64 C oracle, one thread")
     out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic shapes, seeded)",
-           "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "reference_sample_rays": n_rays},
+           "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": w["scaling"], "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic shapes, seeded)",
+           "config": {"workload": w["name"], **config_keys(w), "reference_sample_rays": n_rays},
            "impl": "reference",
            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -521,7 +589,9 @@ def run_reference(args):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -145,9 +145,12 @@ __device__ inline RayCtx ray_of_thread(const BatchDesc& b) {
 // background is u01 of Philox(step, s, BG, 0) words 0..2 when random.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, RayBuf R, uint32_t* block_sums) {
+  __shared__ uint32_t s_cls[kPlanClasses];
+  if (b.plan && threadIdx.x < kPlanClasses) s_cls[threadIdx.x] = 0u;
   RayCtx c = ray_of_thread(b);
   const ObjectDev& ob = b.objs[b.slot[c.bi]];
   uint32_t count = 0;
+  uint32_t m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;  // live candidates (tile plan of the mixed-precision path, N <= 128)
   if (c.valid) {
     float o[3], d[3], bg[3];
     uint32_t step = b.explicit_rays ? b.explicit_step : ob.step;
@@ -189,9 +192,25 @@ __global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, Ra
     if (hit) {
       if (!ob.occ) {
         count = (uint32_t)g.n_samples;
+        if (b.plan) {
+          auto first = [&](int lo) {
+            return g.n_samples >= lo + 32 ? 0xffffffffu : (g.n_samples > lo ? (1u << (g.n_samples - lo)) - 1u : 0u);
+          };
+          m0 = first(0); m1 = first(32); m2 = first(64); m3 = first(96);
+        }
       } else {
         for_candidates(o, d, tn, tf, g.n_samples, ob.key0, ob.key1, step, (uint32_t)c.rl, b.jitter, ob.occ, ob.half,
-                       ob.inv_ext, [&](int, float, float, float, float, float, bool live) { count += live ? 1u : 0u; });
+                       ob.inv_ext, [&](int i, float, float, float, float, float, bool live) {
+                         if (live) {
+                           ++count;
+                           if (b.plan) {
+                             const uint32_t bit = 1u << (i & 31);
+                             const int wd = i >> 5;
+                             m0 |= wd == 0 ? bit : 0u; m1 |= wd == 1 ? bit : 0u;
+                             m2 |= wd == 2 ? bit : 0u; m3 |= wd == 3 ? bit : 0u;
+                           }
+                         }
+                       });
       }
     }
     for (int a = 0; a < 3; ++a) {
@@ -203,6 +222,13 @@ __global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, Ra
     R.tf[c.r] = hit ? tf : tn;
     R.count[c.r] = count;
     R.obj[c.r] = c.bi;
+    if (b.plan) *reinterpret_cast<uint4*>(R.mask + 4 * c.r) = make_uint4(m0, m1, m2, m3);
+  }
+  if (b.plan) {  // rays of each plan class in this block
+    __syncthreads();
+    if (c.valid) atomicAdd(&s_cls[plan_class(count)], 1u);
+    __syncthreads();
+    if (threadIdx.x < kPlanClasses) b.plan_bcls[blockIdx.x * kPlanClasses + threadIdx.x] = s_cls[threadIdx.x];
   }
   uint32_t total;
   uint32_t excl = block_excl_scan256(count, &total);
@@ -221,6 +247,85 @@ void launch_ray_setup(const GridParams& g, const BatchDesc& b, RayBuf r, uint32_
 // Padding samples up to the tile boundary get ray = kNoRay.
 // ---------------------------------------------------------------------------
 constexpr int kMaxBatch = 1024;
+
+// Tile plan (mixed-precision path), run by the single block of k_scan: per batch entry (one warp each), the class
+// counts of its ray blocks become block offsets within the entry's class, the classes get consecutive ranges of
+// plan_perm (class 1 first) and consecutive tiles; entries get consecutive, even tile ranges; then every tile record
+// {entry, P, rays, first perm index} is written and the pair count stored.  s_tiles and s_wsum are scratch.
+__device__ void plan_tiles_of_batch(const BatchDesc& b, uint32_t* s_tiles, uint32_t* s_wsum) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  for (int i = w; i < b.n; i += 32) {
+    const int bb = b.block_base[i], nb = b.block_base[i + 1] - bb;
+    int32_t* po = b.plan_obj + i * 3 * kPlanClasses;
+    int perm_base = 0, tile_base = 0;
+    for (int k = 0; k < kPlanClasses; ++k) {
+      uint32_t carry = 0;
+      for (int c = 0; c < nb; c += 32) {
+        uint32_t* p = b.plan_bcls + (size_t)(bb + c + lane) * kPlanClasses + k;
+        const uint32_t v = (c + lane < nb) ? *p : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += n;
+        }
+        if (c + lane < nb) *p = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      const int rays_k = (int)carry;
+      const int per = plan_rays_per_tile(k);
+      const int tiles_k = k == 0 ? 0 : (rays_k + per - 1) / per;
+      if (lane == 0) {
+        po[k] = k == 0 ? 0 : perm_base;
+        po[kPlanClasses + k] = tile_base;
+        po[2 * kPlanClasses + k] = rays_k;
+      }
+      if (k > 0) {
+        perm_base += rays_k;
+        tile_base += tiles_k;
+      }
+    }
+    if (lane == 0) s_tiles[i] = (uint32_t)((tile_base + 1) & ~1);  // even: a pair never mixes entries
+  }
+  __syncthreads();
+  // exclusive scan of the entries' tile counts
+  const uint32_t v = threadIdx.x < (unsigned)b.n ? s_tiles[threadIdx.x] : 0u;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) s_wsum[w] = incl;
+  __syncthreads();
+  uint32_t base = 0, all = 0;
+  for (int k = 0; k < 32; ++k) {
+    if (k < w) base += s_wsum[k];
+    all += s_wsum[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < (unsigned)b.n) s_tiles[threadIdx.x] = base + incl - v;  // first tile of entry i
+  if (threadIdx.x == 0) b.plan_npairs[0] = (int32_t)(all / 2);
+  __syncthreads();
+  for (int i = w; i < b.n; i += 32) {
+    const int32_t* po = b.plan_obj + i * 3 * kPlanClasses;
+    const int t0 = (int)s_tiles[i];
+    const int nt = (int)((i + 1 < b.n ? s_tiles[i + 1] : all) - s_tiles[i]);
+    for (int t = lane; t < nt; t += 32) {
+      // the class whose tiles cover t: the highest one that starts at or before t (a class that starts at t with no
+      // tiles is never followed by one that starts at t too, except past the last class: the padding tile)
+      int k = kPlanClasses - 1;
+      while (k > 1 && po[kPlanClasses + k] > t) --k;
+      int4 rec = make_int4(i, kTile, 0, b.ray_base[i]);  // padding tile: no rays
+      const int per = plan_rays_per_tile(k);
+      const int q = t - po[kPlanClasses + k];
+      const int left = po[2 * kPlanClasses + k] - q * per;
+      if (q >= 0 && left > 0) rec = make_int4(i, plan_slots(k), left < per ? left : per, b.ray_base[i] + po[k] + q * per);
+      b.plan_tiles[t0 + t] = rec;
+    }
+  }
+}
 
 __global__ void __launch_bounds__(1024) k_scan(BatchDesc b, uint32_t* block_sums, BatchDyn* dyn, int32_t* totals,
                                                SampleBuf S, unsigned long long* live_counter) {
@@ -294,6 +399,7 @@ __global__ void __launch_bounds__(1024) k_scan(BatchDesc b, uint32_t* block_sums
     totals[1] = (int32_t)tot;
     if (live_counter) atomicAdd(live_counter, (unsigned long long)tot);
   }
+  if (b.plan) plan_tiles_of_batch(b, s_tiles, s_wsum);
 }
 
 void launch_scan(const GridParams&, const BatchDesc& b, uint32_t* block_sums, BatchDyn* dyn, int32_t* totals,

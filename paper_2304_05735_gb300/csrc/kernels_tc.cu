@@ -1,5 +1,6 @@
-// Mixed-precision training step on the 5th-generation tensor cores: one fused kernel per tile of 128 sample
-// slots that holds whole rays (slots per ray P = next power of two >= N, P <= 128).
+// Mixed-precision training step on the 5th-generation tensor cores: one fused kernel over tiles of 128 sample
+// slots that hold whole rays.  The tile plan packs the rays of each object by their number of live samples (rays of
+// one class share a slot count P = 128 / k for k rays per tile), so culled candidates and missed rays take no slots.
 //
 // Per tile, in one CTA of 128 threads (thread s <-> sample slot s <-> TMEM lane s):
 //   1. sample positions of the slot (same FP32 operations as the sampling kernels: bit-identical),
@@ -58,6 +59,8 @@ struct TileBufs {
   float dsig[kT];
   float drgb[3][kT];
   int valid[kT];
+  int ray[kT];  // global ray index of the slot (-1 outside the tile's rays)
+  int P, nrays; // slots per ray and rays of the tile
 };
 
 template <int LFP>
@@ -103,13 +106,14 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 
 template <int LFP>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int P, int total_pairs) {
+    k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem<LFP>& sm = *reinterpret_cast<TcSmem<LFP>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int wg = t >> 7;          // tile of the pair
   const int s = t & (kT - 1);     // slot within the tile = TMEM lane
   TileBufs<LFP>& tb = sm.tb[wg];
+  const int total_pairs = *b.plan_npairs;
   const int pair_lo = (int)((int64_t)total_pairs * blockIdx.x / gridDim.x);
   const int pair_hi = (int)((int64_t)total_pairs * (blockIdx.x + 1) / gridDim.x);
   if (pair_lo >= pair_hi) return;
@@ -131,8 +135,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmp = tm + ((uint32_t)(32 * (warp & 3)) << 16) + kColTmp + 64u * (uint32_t)wg;  // this thread's row
   uint32_t phase = 0;
   bool ok = true;
-  const int rays_per_tile = kT / P;
-  const int N = g.n_samples;
 
   auto sync_then_issue = [&]() {  // every thread's shared writes and TMEM reads become visible to the MMAs
     fence_async_smem();
@@ -158,9 +160,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr int LMAX = LFP / 2;
   // the sample and encoding of the next pair are computed ahead, mostly while the backward GEMMs of the current
   // pair run, and kept in registers until the current pair no longer reads the tile buffers
-  int nx_bi = locate_object(b, pair_lo * kTilesPerCta, 0);
+  int4 nx_ti = b.plan_tiles[pair_lo * kTilesPerCta + wg];  // both tiles of a pair belong to the same object
+  int nx_bi = nx_ti.x;
   const ObjectDev* nx_ob = &b.objs[b.slot[nx_bi]];
-  SlotSample nx = make_sample(g, b, R, nx_ob, nx_bi, pair_lo * kTilesPerCta + wg - b.tile_base[nx_bi], s, P);
+  SlotSample nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
   float ne[LFP];
 #pragma unroll
   for (int k = 0; k < LFP; ++k) ne[k] = 0.f;
@@ -169,9 +172,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     gather_levels<LFP, 0, LMAX>(g, nx_ob, p, ne);
   }
   for (int pair = pair_lo; pair < pair_hi && ok; ++pair) {
-    const int tile0 = pair * kTilesPerCta;
     // ---- 1-2. the prepared sample and encoding of this pair -> tile buffers ---------------------------------------
     tb.valid[s] = nx.valid;
+    tb.ray[s] = nx.ray;
+    if (s == 0) {
+      tb.P = nx_ti.y;
+      tb.nrays = nx_ti.z;
+    }
     tb.px[0][s] = nx.x; tb.px[1][s] = nx.y; tb.px[2][s] = nx.z;
     tb.t[s] = nx.t;
     tb.dt[s] = nx.dt;
@@ -186,10 +193,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
-    const int tile_local = tile0 + wg - b.tile_base[bi];
     const bool has_next = pair + 1 < pair_hi;
     if (has_next) {
-      nx_bi = locate_object(b, (pair + 1) * kTilesPerCta, bi);
+      nx_ti = b.plan_tiles[(pair + 1) * kTilesPerCta + wg];
+      nx_bi = nx_ti.x;
       nx_ob = &b.objs[b.slot[nx_bi]];
     }
     sync_then_issue();
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int j = 0; j < 15; ++j) cin[j] = v[1 + j];
       float d0 = 0.f, d1 = 0.f, d2 = 0.f;
       if (g.dir_dims == 3 && tb.valid[s]) {
-        const int64_t r = b.ray_base[bi] + tile_local * rays_per_tile + s / P;
+        const int64_t r = tb.ray[s];
         d0 = R.d[3 * r]; d1 = R.d[3 * r + 1]; d2 = R.d[3 * r + 2];
       }
       cin[15] = d0; cin[16] = d1; cin[17] = d2;
@@ -272,11 +279,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     __syncthreads();
     // ---- 4. compositing, losses, adjoint: one warp per ray of the pair -----------------------------------------
-    for (int j = warp; j < kTilesPerCta * rays_per_tile; j += kTcThreads / 32) {
-      const int u = j / rays_per_tile, jr = j % rays_per_tile;
-      const int rl = (tile0 + u - b.tile_base[bi]) * rays_per_tile + jr;
-      if (rl < n_rays_obj)
-        composite_ray(sm.tb[u], g, b, R, dyn, bi, b.ray_base[bi] + rl, jr * P, P, invB, status);
+    {
+      const int nr0 = sm.tb[0].nrays, nr_all = nr0 + sm.tb[1].nrays;
+      for (int j = warp; j < nr_all; j += kTcThreads / 32) {
+        const int u = j < nr0 ? 0 : 1, jr = j < nr0 ? j : j - nr0;
+        const int Pu = sm.tb[u].P;
+        composite_ray(sm.tb[u], g, b, R, dyn, bi, (int64_t)sm.tb[u].ray[jr * Pu], jr * Pu, Pu, invB, status);
+      }
     }
     __syncthreads();
     // ---- 5. backward -----------------------------------------------------------------------------------------------
@@ -311,7 +320,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     {  // while the MMAs run: part 0 of the next pair's sample and encoding
       if (has_next) {
-        nx = make_sample(g, b, R, nx_ob, nx_bi, (pair + 1) * kTilesPerCta + wg - b.tile_base[nx_bi], s, P);
+        nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
 #pragma unroll
         for (int q = 0; q < LFP; ++q) ne[q] = 0.f;
       }
@@ -455,8 +464,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 template <int LFP>
-void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
-                 int total_tiles, int n_ctas, cudaStream_t stream) {
+void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
+                 int max_tiles, int n_ctas, cudaStream_t stream) {
   // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
   // CTA never waits on another
   int bytes = (int)sizeof(TcSmem<LFP>);
@@ -466,20 +475,60 @@ void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
     cudaFuncSetAttribute(k_tile_tc<LFP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr_set = true;
   }
-  const int total_pairs = total_tiles / kTilesPerCta;
-  int grid = n_ctas < total_pairs ? n_ctas : total_pairs;
+  // the plan's pair count is read on the device; max_tiles only bounds the grid
+  const int max_pairs = (max_tiles + kTilesPerCta - 1) / kTilesPerCta;
+  int grid = n_ctas < max_pairs ? n_ctas : max_pairs;
   if (grid < 1) return;
-  k_tile_tc<LFP><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status, P, total_pairs);
+  k_tile_tc<LFP><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status);
+}
+
+// Places every ray of the batch in the tile plan: rays with live samples go to their class's position in
+// plan_perm (stable: class base of the entry + offset of the ray block within the entry + rank in the block); rays
+// without live samples add their loss here (C_hat = background, D_hat = 0) and write their outputs.
+__global__ void __launch_bounds__(256) k_plan_rays(GridParams g, BatchDesc b, RayBuf R, BatchDyn* dyn) {
+  __shared__ uint32_t s_wcnt[8][kPlanClasses];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bi = b.block_obj[blockIdx.x];
+  const int rl = (blockIdx.x - b.block_base[bi]) * 256 + threadIdx.x;
+  const int n_obj = b.ray_base[bi + 1] - b.ray_base[bi];
+  const bool valid = rl < n_obj;
+  const int64_t r = b.ray_base[bi] + rl;
+  const int cls = valid ? plan_class(R.count[r]) : -1;
+  uint32_t rank = 0;
+#pragma unroll
+  for (int k = 0; k < kPlanClasses; ++k) {
+    const uint32_t m = __ballot_sync(0xffffffffu, cls == k);
+    if (cls == k) rank = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) s_wcnt[warp][k] = __popc(m);
+  }
+  __syncthreads();
+  if (cls > 0) {
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += s_wcnt[w][cls];
+    const int pos = b.plan_obj[bi * 3 * kPlanClasses + cls] + (int)b.plan_bcls[blockIdx.x * kPlanClasses + cls] +
+                    (int)(before + rank);
+    b.plan_perm[b.ray_base[bi] + pos] = (int32_t)r;
+  } else if (cls == 0) {
+    const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
+    float* o = R.out + 6 * r;
+    o[0] = bg0; o[1] = bg1; o[2] = bg2; o[3] = 0.f; o[4] = 0.f; o[5] = 0.f;
+    const RayLoss q = ray_loss(g, R, r, bg0, bg1, bg2, 0.f, 0.f, bg0, bg1, bg2, 1.0f / (float)n_obj);
+    add_ray_loss(dyn, bi, q, nullptr);
+  }
 }
 
 }  // namespace
 
-int tc_tiles_per_cta() { return kTilesPerCta; }
 
-void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
-                    int total_tiles, int n_ctas, cudaStream_t stream) {
-  if (g.LF <= 16) launch_tc_t<16>(g, b, dyn, r, status, P, total_tiles, n_ctas, stream);
-  else launch_tc_t<32>(g, b, dyn, r, status, P, total_tiles, n_ctas, stream);
+void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
+                    int max_tiles, int n_ctas, cudaStream_t stream) {
+  if (g.LF <= 16) launch_tc_t<16>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+  else launch_tc_t<32>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+}
+
+void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream) {
+  if (b.n_blocks <= 0) return;
+  k_plan_rays<<<b.n_blocks, 256, 0, stream>>>(g, b, r, dyn);
 }
 
 // Failure-detection self-test: a bounded wait on an mbarrier that nothing signals must give up, record the

@@ -11,6 +11,8 @@
 // request throughput, overlaps the latency-bound chain of MMA round trips of the compute warps.
 // Every wait is bounded; on time-out the kernel records ROMAP_ERR_TIMEOUT, lets its MMAs drain (bounded), frees its
 // tensor memory and returns.
+#include <cstddef>
+
 #include "tc_common.cuh"
 
 namespace romap {
@@ -39,7 +41,9 @@ struct WsSlot {
   float dsig[kT];
   float drgb[3][kT];
   int valid[kT];
-  float dE[kT][LFP + 4];  // dL/dencoding staged for the scatter (padded rows: conflict-free float4 access)
+  int ray[kT];            // global ray index of the slot (-1 outside the tile's rays)
+  __align__(16) float dE[kT][LFP + 4];  // dL/dencoding staged for the scatter (padded rows: float4 access)
+  int P, nrays, bi;       // slots per ray, rays and batch entry of the tile
 };
 
 template <int LFP>
@@ -92,11 +96,10 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 // memory warps: scatter the tile that left a slot, then gather the next tile into it
 // ---------------------------------------------------------------------------------------------------------------
 template <int LFP>
-__device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, const RayBuf& R, int P,
-                            int tile_lo, int n) {
+__device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, const RayBuf& R, int tile_lo,
+                            int n) {
   const int s = threadIdx.x - kCompute;
   constexpr int LMAX = LFP / 2;
-  int bi_prep = 0, bi_scat = 0;
   for (int k = 0; k < n + 2; ++k) {
     if (sm.fail) break;
     const int slot = k & 1;
@@ -106,10 +109,8 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
         sm.fail = 1;
         break;
       }
-      const int tile = tile_lo + k - 2;
-      bi_scat = locate_object(b, tile, bi_scat);
       if (sl.valid[s]) {
-        const ObjectDev* ob = &b.objs[b.slot[bi_scat]];
+        const ObjectDev* ob = &b.objs[b.slot[b.plan_tiles[tile_lo + k - 2].x]];
         const float p[3] = {sl.px[0][s], sl.px[1][s], sl.px[2][s]};
         float2* gt = reinterpret_cast<float2*>(ob->grad);
         float de[LFP];
@@ -130,10 +131,15 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
       }
     }
     if (k < n) {
-      const int tile = tile_lo + k;
-      bi_prep = locate_object(b, tile, bi_prep);
-      const ObjectDev* ob = &b.objs[b.slot[bi_prep]];
-      const SlotSample q = make_sample(g, b, R, ob, bi_prep, tile - b.tile_base[bi_prep], s, P);
+      const int4 ti = b.plan_tiles[tile_lo + k];
+      const ObjectDev* ob = &b.objs[b.slot[ti.x]];
+      const SlotSample q = plan_sample(g, b, R, ob, ti.x, ti, s);
+      if (s == 0) {
+        sl.P = ti.y;
+        sl.nrays = ti.z;
+        sl.bi = ti.x;
+      }
+      sl.ray[s] = q.ray;
       sl.valid[s] = q.valid;
       sl.px[0][s] = q.x; sl.px[1][s] = q.y; sl.px[2][s] = q.z;
       sl.t[s] = q.t;
@@ -158,12 +164,11 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
 // ---------------------------------------------------------------------------------------------------------------
 template <int LFP>
 __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf R,
-                             int32_t* status, int P, int tile_lo, int n, uint32_t& phase, bool& pending) {
+                             int32_t* status, int tile_lo, int n, uint32_t& phase, bool& pending) {
   const int s = threadIdx.x, warp = s >> 5;
   const uint32_t tm = sm.tmem_base;
   const uint32_t tmp = tm + ((uint32_t)(32 * warp) << 16) + kColTmp;
   const uint32_t dtmp = tm + kColTmp;
-  const int rays_per_tile = kT / P;
   auto sync_then_issue = [&]() {
     fence_async_smem();
     tc_before();
@@ -195,8 +200,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     }
     bar_compute();
     if (sm.c_stop) break;
-    const int tile = tile_lo + k;
-    const int nbi = locate_object(b, tile, bi < 0 ? 0 : bi);
+    const int nbi = sl.bi;
     if (nbi != bi) {
       if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
       bi = nbi;
@@ -206,7 +210,6 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
-    const int tile_local = tile - b.tile_base[bi];
     sync_then_issue();
     // ---- forward ----
     if (s == 0) {
@@ -237,7 +240,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       for (int j = 0; j < 15; ++j) cin[j] = v[1 + j];
       float d0 = 0.f, d1 = 0.f, d2 = 0.f;
       if (g.dir_dims == 3 && sl.valid[s]) {
-        const int64_t r = b.ray_base[bi] + tile_local * rays_per_tile + s / P;
+        const int64_t r = sl.ray[s];
         d0 = R.d[3 * r]; d1 = R.d[3 * r + 1]; d2 = R.d[3 * r + 2];
       }
       cin[15] = d0; cin[16] = d1; cin[17] = d2;
@@ -279,9 +282,10 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     }
     bar_compute();
     // ---- compositing, losses, adjoint: one warp per ray ----
-    for (int j = warp; j < rays_per_tile; j += kCompute / 32) {
-      const int rl = tile_local * rays_per_tile + j;
-      if (rl < n_rays_obj) composite_ray(sl, g, b, R, dyn, bi, b.ray_base[bi] + rl, j * P, P, invB, status);
+    {
+      const int P = sl.P, nr = sl.nrays;
+      for (int j = warp; j < nr; j += kCompute / 32)
+        composite_ray(sl, g, b, R, dyn, bi, (int64_t)sl.ray[j * P], j * P, P, invB, status);
     }
     bar_compute();
     // ---- backward ----
@@ -383,10 +387,11 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
 
 template <int LFP>
 __global__ void __launch_bounds__(kWsThreads, 1)
-    k_tile_ws(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int P, int total_tiles) {
+    k_tile_ws(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   WsSmem<LFP>& sm = *reinterpret_cast<WsSmem<LFP>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
+  const int total_tiles = 2 * *b.plan_npairs;
   const int tile_lo = (int)((int64_t)total_tiles * blockIdx.x / gridDim.x);
   const int tile_hi = (int)((int64_t)total_tiles * (blockIdx.x + 1) / gridDim.x);
   const int n = tile_hi - tile_lo;
@@ -411,8 +416,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   tc_after();
   uint32_t phase = 0;
   bool pending = false;
-  if (warp < 4) compute_role<LFP>(sm, g, b, dyn, R, status, P, tile_lo, n, phase, pending);
-  else memory_role<LFP>(sm, g, b, R, P, tile_lo, n);
+  if (warp < 4) compute_role<LFP>(sm, g, b, dyn, R, status, tile_lo, n, phase, pending);
+  else memory_role<LFP>(sm, g, b, R, tile_lo, n);
   if (t == 0 && sm.fail) {
     if (status) atomicOr(status, 2);
     if (pending) mbar_wait(&sm.mma_bar, phase ^ 1u);  // bounded: let MMAs in flight finish before freeing TMEM
@@ -422,9 +427,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base), "r"(kTmemCols));
 }
 
+static_assert(offsetof(WsSlot<16>, dE) % 16 == 0 && offsetof(WsSlot<32>, dE) % 16 == 0, "float4 rows of dE");
+
 template <int LFP>
-void launch_ws_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
-                 int total_tiles, int n_ctas, cudaStream_t stream) {
+void launch_ws_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int max_tiles,
+                 int n_ctas, cudaStream_t stream) {
   int bytes = (int)sizeof(WsSmem<LFP>);
   if (bytes < 116 * 1024) bytes = 116 * 1024;  // one CTA per SM: the 512-column TMEM allocation never waits
   static bool attr_set = false;
@@ -432,17 +439,18 @@ void launch_ws_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
     cudaFuncSetAttribute(k_tile_ws<LFP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr_set = true;
   }
-  int grid = n_ctas < total_tiles ? n_ctas : total_tiles;
+  // the plan's tile count is read on the device; max_tiles only bounds the grid
+  int grid = n_ctas < max_tiles ? n_ctas : max_tiles;
   if (grid < 1) return;
-  k_tile_ws<LFP><<<grid, kWsThreads, bytes, stream>>>(g, b, dyn, r, status, P, total_tiles);
+  k_tile_ws<LFP><<<grid, kWsThreads, bytes, stream>>>(g, b, dyn, r, status);
 }
 
 }  // namespace
 
-void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
-                    int total_tiles, int n_ctas, cudaStream_t stream) {
-  if (g.LF <= 16) launch_ws_t<16>(g, b, dyn, r, status, P, total_tiles, n_ctas, stream);
-  else launch_ws_t<32>(g, b, dyn, r, status, P, total_tiles, n_ctas, stream);
+void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
+                    int max_tiles, int n_ctas, cudaStream_t stream) {
+  if (g.LF <= 16) launch_ws_t<16>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+  else launch_ws_t<32>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
 }
 
 }  // namespace romap

@@ -87,8 +87,17 @@ struct romap_ctx {
   ObjectDev* objs_dev = nullptr;
   ObjectDev* fn_obj_dev = nullptr;   // object record of functional calls
   // step workspace
-  DevBuf ws_rays, ws_samples, ws_blocks, ws_batch, ws_dyn, ws_stage;
+  DevBuf ws_rays, ws_samples, ws_blocks, ws_batch, ws_dyn, ws_stage, ws_plan;
   int64_t cap_rays = 0, cap_samples = 0, cap_blocks = 0, cap_batch = 0;
+  // tile plan of the mixed-precision path (capacities: rays, ray blocks, batch entries, tiles)
+  int64_t cap_plan[4] = {0, 0, 0, 0};
+  struct PlanView {
+    uint32_t* bcls = nullptr;
+    int32_t* obj = nullptr;
+    int32_t* perm = nullptr;
+    int4* tiles = nullptr;
+    int32_t* npairs = nullptr;
+  } plan;
   RayBuf R{};
   SampleBuf S{};
   uint32_t* block_sums = nullptr;
@@ -173,8 +182,9 @@ romap_status grow(romap_ctx* ctx, DevBuf& b, size_t bytes) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Carves a RayBuf of capacity nr from base; returns bytes used.
-size_t carve_rays(char* base, int64_t nr, RayBuf* R) {
+// Carves a RayBuf of capacity nr from base; returns bytes used.  with_mask: the live-candidate masks of the tile
+// plan (mixed-precision training).
+size_t carve_rays(char* base, int64_t nr, RayBuf* R, bool with_mask = false) {
   size_t o = 0;
   auto take = [&](size_t bytes) {
     char* p = base ? base + o : nullptr;
@@ -194,8 +204,43 @@ size_t carve_rays(char* base, int64_t nr, RayBuf* R) {
   R->off = (uint32_t*)take(sizeof(uint32_t) * nr);
   R->obj = (int32_t*)take(sizeof(int32_t) * nr);
   R->out = (float*)take(sizeof(float) * 6 * nr);
+  R->mask = with_mask ? (uint32_t*)take(sizeof(uint32_t) * 4 * nr) : nullptr;
   R->gout = nullptr;
   return o;
+}
+
+// Carves the tile-plan arrays for capacities cap = {rays, ray blocks, batch entries, tiles}; returns bytes used.
+size_t carve_plan(char* base, const int64_t cap[4], romap_ctx::PlanView* P) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + o : nullptr;
+    o = align_up(o + bytes, 256);
+    return p;
+  };
+  P->bcls = (uint32_t*)take(sizeof(uint32_t) * kPlanClasses * cap[1]);
+  P->obj = (int32_t*)take(sizeof(int32_t) * 3 * kPlanClasses * cap[2]);
+  P->perm = (int32_t*)take(sizeof(int32_t) * cap[0]);
+  P->tiles = (int4*)take(sizeof(int4) * cap[3]);
+  P->npairs = (int32_t*)take(sizeof(int32_t));
+  return o;
+}
+
+romap_status ensure_plan(romap_ctx* ctx, int64_t nr, int64_t nblocks, int64_t nbatch, int64_t ntiles) {
+  const int64_t need[4] = {nr, nblocks, nbatch, ntiles};
+  bool fits = true;
+  for (int k = 0; k < 4; ++k) fits = fits && need[k] <= ctx->cap_plan[k];
+  if (fits) return ROMAP_OK;
+  int64_t cap[4];
+  for (int k = 0; k < 4; ++k) {
+    cap[k] = ctx->cap_plan[k];
+    if (need[k] > cap[k]) cap[k] = need[k] + need[k] / 4 + 64;
+  }
+  romap_ctx::PlanView pv;
+  ROMAP_TRY(grow(ctx, ctx->ws_plan, carve_plan(nullptr, cap, &pv)));
+  carve_plan((char*)ctx->ws_plan.p, cap, &ctx->plan);
+  for (int k = 0; k < 4; ++k) ctx->cap_plan[k] = cap[k];
+  ctx->ws_generation += 1;
+  return ROMAP_OK;
 }
 
 size_t carve_samples(char* base, int64_t ns, SampleBuf* S) {
@@ -220,8 +265,8 @@ size_t carve_samples(char* base, int64_t ns, SampleBuf* S) {
 romap_status ensure_workspace(romap_ctx* ctx, int64_t nr, int64_t ns, int64_t nblocks, int64_t nbatch) {
   if (nr > ctx->cap_rays) {
     int64_t cap = nr + nr / 4 + 256;
-    ROMAP_TRY(grow(ctx, ctx->ws_rays, carve_rays(nullptr, cap, &ctx->R)));
-    carve_rays((char*)ctx->ws_rays.p, cap, &ctx->R);
+    ROMAP_TRY(grow(ctx, ctx->ws_rays, carve_rays(nullptr, cap, &ctx->R, true)));
+    carve_rays((char*)ctx->ws_rays.p, cap, &ctx->R, true);
     ctx->cap_rays = cap;
   }
   if (ns > ctx->cap_samples) {
@@ -253,14 +298,7 @@ struct HostBatch {
   int n = 0, n_blocks = 0, n_rays = 0, n_tiles = 0;
 };
 
-// Slots per ray of the fused mixed-precision kernel: the next power of two >= N (so rays never straddle tiles).
-int slots_per_ray(int N) {
-  int P = 1;
-  while (P < N) P <<= 1;
-  return P;
-}
-
-void build_batch(const std::vector<int32_t>& slots, const std::vector<int32_t>& rays, HostBatch* hb, int P = 0) {
+void build_batch(const std::vector<int32_t>& slots, const std::vector<int32_t>& rays, HostBatch* hb) {
   int n = (int)slots.size();
   hb->n = n;
   std::vector<int32_t> ray_base(n + 1, 0), block_base(n + 1, 0), tile_base(n + 1, 0), block_obj;
@@ -269,10 +307,7 @@ void build_batch(const std::vector<int32_t>& slots, const std::vector<int32_t>& 
     int nb = (rays[i] + 255) / 256;
     block_base[i + 1] = block_base[i] + nb;
     for (int k = 0; k < nb; ++k) block_obj.push_back(i);
-    int tiles = P > 0 ? (int)(((int64_t)rays[i] * P + kTile - 1) / kTile) : 0;
-    const int per = tc_tiles_per_cta();
-    tiles = (tiles + per - 1) / per * per;  // tiles of one object are processed in groups that never straddle objects
-    tile_base[i + 1] = tile_base[i] + tiles;
+    tile_base[i + 1] = tile_base[i];  // (tiles of the FP32 path are placed on the device)
   }
   hb->n_rays = ray_base[n];
   hb->n_blocks = block_base[n];
@@ -475,20 +510,22 @@ romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBu
 int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
 
 // Candidate fused tile kernels of the mixed path (same results, different schedules).
-typedef void (*TileKernelFn)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int, int,
+typedef void (*TileKernelFn)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int,
                              cudaStream_t);
 const TileKernelFn kTileKernels[] = {launch_tile_tc, launch_tile_ws};
 const char* const kTileKernelNames[] = {"lockstep tile pairs", "warp-specialized"};
 constexpr int kNumTileKernels = 2;
 
-// Sampling stage of the mixed path: ray draw + slab + live counts, and the per-object scan (live-sample counter,
-// loss reset).  Samples are formed inside the fused kernel, so nothing is compacted.
+// Sampling stage of the mixed path: ray draw + slab + live counts and masks, the per-object scan (live-sample
+// counter, loss reset) with the tile plan, and the placement of every ray in the plan.  Samples are formed inside the
+// fused kernel from the masks, so no sample records are written.
 romap_status run_sampling_mixed(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBuf S, uint32_t* block_sums,
                                 BatchDyn* dyn, int32_t* totals) {
-  PhaseScope ps(ctx, 0, 2);
+  PhaseScope ps(ctx, 0, 3);
   launch_ray_setup(ctx->g, b, R, block_sums, ctx->stream);
   launch_scan(ctx->g, b, block_sums, dyn, totals, S, ctx->live_counter, ctx->stream);
-  ctx->launches += 2;
+  launch_plan_rays(ctx->g, b, R, dyn, ctx->stream);
+  ctx->launches += 3;
   CUDA_TRY(cudaGetLastError());
   return ROMAP_OK;
 }
@@ -498,8 +535,8 @@ const std::vector<int32_t>& v_ids_for_tuning(const std::vector<int32_t>& ids) { 
 // Times every candidate tile kernel on this batch (two launches each, CUDA events on the context's stream), keeps
 // the fastest, and undoes the candidates' side effects: their gradients are zeroed here, and the caller's sampling
 // stage that follows rewrites the ray records and resets the losses.
-romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& ids, const BatchDesc& b, int n_tiles,
-                                  int P) {
+romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& ids, const BatchDesc& b,
+                                  int max_tiles) {
   SampleBuf none{};
   ROMAP_TRY(run_sampling_mixed(ctx, b, ctx->R, none, ctx->block_sums, ctx->dyn, ctx->totals));
   cudaEvent_t e0, e1;
@@ -507,10 +544,10 @@ romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& id
   CUDA_TRY(cudaEventCreate(&e1));
   int best = 0;
   for (int k = 0; k < kNumTileKernels; ++k) {
-    kTileKernels[k](ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, n_tiles, tile_ctas(ctx), ctx->stream);  // warm
+    kTileKernels[k](ctx->g, b, ctx->dyn, ctx->R, ctx->status, max_tiles, tile_ctas(ctx), ctx->stream);  // warm
     CUDA_TRY(cudaEventRecord(e0, ctx->stream));
     for (int rep = 0; rep < 2; ++rep)
-      kTileKernels[k](ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, n_tiles, tile_ctas(ctx), ctx->stream);
+      kTileKernels[k](ctx->g, b, ctx->dyn, ctx->R, ctx->status, max_tiles, tile_ctas(ctx), ctx->stream);
     CUDA_TRY(cudaEventRecord(e1, ctx->stream));
     CUDA_TRY(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -537,19 +574,27 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
     if (rays[i] < 1) return fail(ROMAP_ERR_BAD_STATE, "object %d has no training rays", ids[i]);
   }
   const bool mixed = ctx->cfg.precision == ROMAP_PREC_MIXED_BF16;
-  const int P = slots_per_ray(ctx->g.n_samples);
   HostBatch hb;
-  build_batch(slots, rays, &hb, mixed ? P : 0);
+  build_batch(slots, rays, &hb);
   int64_t ns = mixed ? 0 : (int64_t)hb.n_rays * ctx->g.n_samples + (int64_t)hb.n * kTile;
   ROMAP_TRY(ensure_workspace(ctx, hb.n_rays, ns, hb.n_blocks, hb.n));
+  // tile plan bound: per entry at most one partly filled tile per class plus the even padding
+  const int64_t max_tiles = (int64_t)hb.n_rays + (int64_t)(kPlanClasses + 1) * hb.n;
+  if (mixed) ROMAP_TRY(ensure_plan(ctx, hb.n_rays, hb.n_blocks, hb.n, max_tiles));
   BatchDesc b;
   ROMAP_TRY(upload_batch(ctx, hb, &b));
   if (mixed) {
+    b.plan = 1;
+    b.plan_bcls = ctx->plan.bcls;
+    b.plan_obj = ctx->plan.obj;
+    b.plan_perm = ctx->plan.perm;
+    b.plan_tiles = ctx->plan.tiles;
+    b.plan_npairs = ctx->plan.npairs;
     SampleBuf none{};
-    if (ctx->tile_kernel < 0) ROMAP_TRY(autotune_tile_kernel(ctx, v_ids_for_tuning(ids), b, hb.n_tiles, P));
+    if (ctx->tile_kernel < 0) ROMAP_TRY(autotune_tile_kernel(ctx, v_ids_for_tuning(ids), b, (int)max_tiles));
     ROMAP_TRY(run_sampling_mixed(ctx, b, ctx->R, none, ctx->block_sums, ctx->dyn, ctx->totals));
     PhaseScope ps(ctx, 3, 1);
-    kTileKernels[ctx->tile_kernel](ctx->g, b, ctx->dyn, ctx->R, ctx->status, P, hb.n_tiles, tile_ctas(ctx),
+    kTileKernels[ctx->tile_kernel](ctx->g, b, ctx->dyn, ctx->R, ctx->status, (int)max_tiles, tile_ctas(ctx),
                                    ctx->stream);
     ctx->launches += 1;
   } else {
@@ -1020,7 +1065,7 @@ romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids,
       }
       ctx->stats.steps += (int64_t)v.size();
       ctx->stats.rays += rays;
-      ctx->launches += ctx->cfg.precision == ROMAP_PREC_MIXED_BF16 ? 5 : 8;
+      ctx->launches += ctx->cfg.precision == ROMAP_PREC_MIXED_BF16 ? 6 : 8;
       continue;
     }
     ROMAP_TRY(enqueue_step(ctx, v));

@@ -9,7 +9,9 @@
 //    class); an optional 64^3 occupancy bitgrid.
 //  * per step (workspace): ray records and compacted sample records, both
 //    structure of arrays; every object's samples start on a 128-sample tile
-//    boundary so that a tile belongs to one object.
+//    boundary so that a tile belongs to one object.  The mixed-precision path
+//    keeps no sample records: it packs whole rays into tiles by their number
+//    of live samples (the tile plan below) and forms the samples in-kernel.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -84,6 +86,23 @@ struct BatchDyn {
   float pad2_[3];
 };
 
+// Tile plan of the mixed-precision path.  A ray with c > 0 live samples belongs to class k (1..kPlanClasses-1), the
+// largest one whose slot count P_k = 128 / kPlanRays[k] (floor) is >= c; a tile holds up to kPlanRays[k] rays of one
+// class and one object, P_k slots each, and the ray's live samples fill the first c slots of its range.  Class 0
+// holds the rays without live samples, which only add their loss (Eq. 7-11 with C_hat = background).  Every object's
+// tile count is rounded up to even so that a pair of tiles never mixes objects.
+constexpr int kPlanClasses = 10;
+__host__ __device__ constexpr int plan_rays_per_tile(int k) {
+  return k <= 0 ? 0 : (k <= 8 ? k : 16);
+}
+__host__ __device__ constexpr int plan_slots(int k) { return k <= 0 ? 0 : kTile / plan_rays_per_tile(k); }
+__host__ __device__ inline int plan_class(uint32_t live) {
+  if (live == 0) return 0;
+  int k = kPlanClasses - 1;
+  while (k > 1 && (uint32_t)plan_slots(k) < live) --k;
+  return k;
+}
+
 // Batch description (device): object slots and the ray/block prefix sums.
 struct BatchDesc {
   const int32_t* slot;       // [n] object slot of batch entry i
@@ -101,6 +120,13 @@ struct BatchDesc {
   const float* ex_d;
   const float* ex_bg;        // [3n]
   ObjectDev* objs;           // device array indexed by slot
+  // tile plan (mixed-precision path only; plan == 0 elsewhere)
+  int32_t plan;
+  uint32_t* plan_bcls;       // [n_blocks * kPlanClasses] rays of each class per ray block, then offsets in the entry
+  int32_t* plan_obj;         // [n * 3 * kPlanClasses] per entry and class: first perm index, first tile, rays
+  int32_t* plan_perm;        // [n_rays] ray indices in tile order (rays with live samples only)
+  int4* plan_tiles;          // [max tiles] {batch entry, slots per ray P, rays in the tile, first perm index}
+  int32_t* plan_npairs;      // [1] number of tile pairs
 };
 
 // Per-step ray records (structure of arrays, capacity R).
@@ -115,6 +141,7 @@ struct RayBuf {
   uint8_t* cls;    // [R]
   int64_t* pool_idx; // [R]
   uint32_t* count; // [R] live samples
+  uint32_t* mask;  // [4R] live candidates of the ray (bit i of word i / 32), mixed-precision path
   uint32_t* off;   // [R] local offset in its block, then global sample offset
   int32_t* obj;    // [R] batch entry
   float* out;      // [6R] C_hat(3), D_hat, A, sum sigma
@@ -186,15 +213,14 @@ void launch_split_outputs(const float* ray_out, int64_t n, float* rgb, float* de
                           cudaStream_t stream);
 int tile_kernel_smem_bytes(int LF);
 // Mixed precision: fused forward + compositing + backward on tensor cores; P slots per ray (power of two <= 128).
-void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
+void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream);
+void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int total_tiles, int n_ctas, cudaStream_t stream);
 void launch_to_half(const float* params, uint16_t* table_h, int64_t n_hash, cudaStream_t stream);
 // Warp-specialized variant of launch_tile_tc (same results): compute warps run the MMA chain of one tile while
 // memory warps gather the next tile and scatter the previous one.
-void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int P,
+void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int total_tiles, int n_ctas, cudaStream_t stream);
-// tiles the fused kernel processes together; every object's tile count is padded to a multiple of it
-int tc_tiles_per_cta();
 // status word bits written by the kernels
 constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2;
 void launch_selftest_wait(int32_t* status, int limit, cudaStream_t stream);

@@ -185,6 +185,51 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Losses of Eq. 7-11 of one ray from its rendered colour and depth (every term divided by the batch size B through
+// invB in the gradients; the sums are accumulated unscaled).
+struct RayLoss {
+  float loss, l_rgb, l_rr, l_dep, l_den;
+  float gC0, gC1, gC2, gD, gdir;
+};
+__device__ __forceinline__ RayLoss ray_loss(const GridParams& g, const RayBuf& R, int64_t r, float Ch0, float Ch1,
+                                            float Ch2, float Dh, float ssum, float bg0, float bg1, float bg2,
+                                            float invB) {
+  RayLoss q{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int cls = R.cls[r];
+  if (cls != kClsOccluder) {
+    const float t0 = cls == kClsObject ? R.rgb[3 * r] : bg0;
+    const float t1 = cls == kClsObject ? R.rgb[3 * r + 1] : bg1;
+    const float t2 = cls == kClsObject ? R.rgb[3 * r + 2] : bg2;
+    const float e0 = Ch0 - t0, e1 = Ch1 - t1, e2 = Ch2 - t2;
+    const float sq = e0 * e0 + e1 * e1 + e2 * e2;
+    q.loss += sq;
+    if (cls == kClsObject) q.l_rgb = sq; else q.l_rr = sq;
+    q.gC0 = 2.f * e0 * invB; q.gC1 = 2.f * e1 * invB; q.gC2 = 2.f * e2 * invB;
+    const float dep = R.depth[r];
+    if (isfinite(dep)) {
+      const float e = Dh - dep;
+      q.loss += g.lambda1 * fabsf(e);
+      q.l_dep = fabsf(e);
+      q.gD = g.lambda1 * (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) * invB;
+    }
+    if (cls == kClsBackground) {
+      q.loss += g.lambda2 * ssum;
+      q.l_den = ssum;
+      q.gdir = g.lambda2 * invB;
+    }
+  }
+  return q;
+}
+__device__ __forceinline__ void add_ray_loss(BatchDyn* dyn, int bi, const RayLoss& q, int32_t* status) {
+  float* L = dyn[bi].loss;
+  atomicAdd(L + 0, q.loss);
+  if (q.l_rgb != 0.f) atomicAdd(L + 1, q.l_rgb);
+  if (q.l_rr != 0.f) atomicAdd(L + 2, q.l_rr);
+  if (q.l_dep != 0.f) atomicAdd(L + 3, q.l_dep);
+  if (q.l_den != 0.f) atomicAdd(L + 4, q.l_den);
+  if (!isfinite(q.loss) && status) atomicOr(status, 1);
+}
+
 // Eq. 6 + Eq. 7-11 + adjoint for one ray whose samples occupy slots [base, base + P) of the tile.
 template <class Bufs>
 __device__ void composite_ray(Bufs& sm, const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
@@ -221,40 +266,9 @@ __device__ void composite_ray(Bufs& sm, const GridParams& g, const BatchDesc& b,
     o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = -expm1f(-carry); o[5] = ssum;
   }
   // losses of Eq. 7-11 (every term divided by the batch size B)
-  const int cls = R.cls[r];
-  float loss = 0.f, l_rgb = 0.f, l_rr = 0.f, l_dep = 0.f, l_den = 0.f;
-  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gdir = 0.f;
-  if (cls != kClsOccluder) {
-    const float t0 = cls == kClsObject ? R.rgb[3 * r] : bg0;
-    const float t1 = cls == kClsObject ? R.rgb[3 * r + 1] : bg1;
-    const float t2 = cls == kClsObject ? R.rgb[3 * r + 2] : bg2;
-    const float e0 = Ch0 - t0, e1 = Ch1 - t1, e2 = Ch2 - t2;
-    const float sq = e0 * e0 + e1 * e1 + e2 * e2;
-    loss += sq;
-    if (cls == kClsObject) l_rgb = sq; else l_rr = sq;
-    gC0 = 2.f * e0 * invB; gC1 = 2.f * e1 * invB; gC2 = 2.f * e2 * invB;
-    const float dep = R.depth[r];
-    if (isfinite(dep)) {
-      const float e = Dh - dep;
-      loss += g.lambda1 * fabsf(e);
-      l_dep = fabsf(e);
-      gD = g.lambda1 * (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) * invB;
-    }
-    if (cls == kClsBackground) {
-      loss += g.lambda2 * ssum;
-      l_den = ssum;
-      gdir = g.lambda2 * invB;
-    }
-  }
-  if (lane == 0) {
-    float* L = dyn[bi].loss;
-    atomicAdd(L + 0, loss);
-    if (l_rgb != 0.f) atomicAdd(L + 1, l_rgb);
-    if (l_rr != 0.f) atomicAdd(L + 2, l_rr);
-    if (l_dep != 0.f) atomicAdd(L + 3, l_dep);
-    if (l_den != 0.f) atomicAdd(L + 4, l_den);
-    if (!isfinite(loss) && status) atomicOr(status, 1);
-  }
+  const RayLoss q = ray_loss(g, R, r, Ch0, Ch1, Ch2, Dh, ssum, bg0, bg1, bg2, invB);
+  if (lane == 0) add_ray_loss(dyn, bi, q, status);
+  const float gC0 = q.gC0, gC1 = q.gC1, gC2 = q.gC2, gD = q.gD, gdir = q.gdir;
   // adjoint, chunks in reverse order
   float SC0 = 0.f, SC1 = 0.f, SC2 = 0.f, SD = 0.f;
   const float bgterm = Tend * (gC0 * bg0 + gC1 * bg1 + gC2 * bg2);
@@ -322,19 +336,50 @@ __device__ __forceinline__ void gather_levels(const GridParams& g, const ObjectD
 struct SlotSample {
   float x, y, z, t, dt;
   int valid;
+  int ray;  // global ray index of the slot, or -1 for a slot outside the tile's rays
 };
 
-__device__ __forceinline__ SlotSample make_sample(const GridParams& g, const BatchDesc& b, const RayBuf& R,
-                                                  const ObjectDev* ob, int bi, int tile_local, int s, int P) {
-  SlotSample q{0.f, 0.f, 0.f, 0.f, 0.f, 0};
+// Position of the (j+1)-th set bit of x (j < popc(x)), by halving popcounts.
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int j) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const int c = __popc(x & ((1u << w) - 1u));
+    if (j >= c) {
+      j -= c;
+      x >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+// The sample of slot s of a planned tile (see kPlanClasses): ray jr = s / P of the tile, its (s % P)-th live
+// candidate i, found in the ray's live-candidate mask; same FP32 operations as the sampling kernels.
+__device__ __forceinline__ SlotSample plan_sample(const GridParams& g, const BatchDesc& b, const RayBuf& R,
+                                                  const ObjectDev* ob, int bi, int4 tile, int s) {
+  SlotSample q{0.f, 0.f, 0.f, 0.f, 0.f, 0, -1};
+  const int P = tile.y;
+  const int jr = s / P;
+  if (jr >= tile.z) return q;
+  const int r = b.plan_perm[tile.w + jr];
+  q.ray = r;
+  int j = s - jr * P;
+  if ((uint32_t)j >= R.count[r]) return q;
+  int i = 0;
+#pragma unroll 1
+  for (int wd = 0; wd < 4; ++wd) {
+    const uint32_t m = R.mask[4 * (int64_t)r + wd];
+    const int c = __popc(m);
+    if (j < c) {
+      i = 32 * wd + nth_set_bit(m, j);
+      break;
+    }
+    j -= c;
+  }
   const int N = g.n_samples;
-  const int rl = tile_local * (kT / P) + s / P;
-  const int i = s % P;
-  const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
-  if (rl >= n_rays_obj || i >= N) return q;
-  const int64_t r = b.ray_base[bi] + rl;
+  const int rl = r - b.ray_base[bi];
   const float tn = R.tn[r], tf = R.tf[r];
-  if (!(tf > tn)) return q;
   const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
   const uint32_t step = ob->step;
   q.t = candidate_t(tn, step_len, i, ob->key0, ob->key1, step, (uint32_t)rl, 1);
@@ -343,16 +388,9 @@ __device__ __forceinline__ SlotSample make_sample(const GridParams& g, const Bat
   q.x = __fadd_rn(R.o[3 * r], __fmul_rn(q.t, R.d[3 * r]));
   q.y = __fadd_rn(R.o[3 * r + 1], __fmul_rn(q.t, R.d[3 * r + 1]));
   q.z = __fadd_rn(R.o[3 * r + 2], __fmul_rn(q.t, R.d[3 * r + 2]));
-  q.valid = occupied(ob->occ, q.x, q.y, q.z, ob->half, ob->inv_ext) ? 1 : 0;
+  q.valid = 1;
   return q;
 }
-
-__device__ __forceinline__ int locate_object(const BatchDesc& b, int tile, int start) {
-  int i = start < 0 ? 0 : start;
-  while (i + 1 < b.n && tile >= b.tile_base[i + 1]) ++i;
-  return i;
-}
-
 
 }  // namespace tc
 }  // namespace romap
