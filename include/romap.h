@@ -212,6 +212,10 @@ ROMAP_API romap_status romap_get_grad(romap_ctx* ctx, int32_t id, float* out, ui
 /* Copies the last step's ray draw of an object: pool index (int64) and
  * background colour (3 floats) per ray.  Either pointer may be NULL. */
 ROMAP_API romap_status romap_last_batch(romap_ctx* ctx, int32_t id, int64_t* pool_idx, float* bg, int64_t* out_n);
+/* Copies the per-ray outputs of the object's rays in the last step, in ray
+ * slot order: [C_hat rgb (3), D_hat, opacity A, sum of sigma] (Eq. 6), 6
+ * floats per ray, computed in the step's precision.  out may be NULL. */
+ROMAP_API romap_status romap_last_outputs(romap_ctx* ctx, int32_t id, float* out, int64_t* out_n);
 
 /* ---- inference --------------------------------------------------------- */
 /* Renders n rays (world frame unless ROMAP_OBJECT_FRAME) with midpoint

@@ -198,14 +198,7 @@ __device__ __forceinline__ void adam4(float4& p, float4& m, float4& v, const flo
 
 __global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int write_half) {
   const ObjectDev& ob = b.objs[b.slot[blockIdx.y]];
-  __shared__ float s_c[2];
-  if (threadIdx.x == 0) {  // bias corrections 1/(1 - beta^t), once per block
-    const double t = (double)ob.step;
-    s_c[0] = (float)(1.0 / (1.0 - pow((double)g.beta1, t)));
-    s_c[1] = (float)(1.0 / (1.0 - pow((double)g.beta2, t)));
-  }
-  __syncthreads();
-  const float c1 = s_c[0], c2 = s_c[1];
+  const float c1 = ob.bc1, c2 = ob.bc2;  // bias corrections of this step, set with the step counter
   const float b1 = g.beta1, b2 = g.beta2, lr = g.lr, eps = g.eps;
   const float ob1 = 1.0f - b1, ob2 = 1.0f - b2;
   float4* P = reinterpret_cast<float4*>(ob.params);
@@ -248,9 +241,12 @@ __global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int wri
   }
 }
 
-__global__ void k_advance_step(BatchDesc b) {
+__global__ void k_advance_step(GridParams g, BatchDesc b) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < b.n) b.objs[b.slot[i]].step += 1u;
+  if (i < b.n) {
+    ObjectDev& ob = b.objs[b.slot[i]];
+    set_object_step(ob, ob.step + 1u, g.beta1, g.beta2);
+  }
 }
 
 void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream) {
@@ -261,7 +257,7 @@ void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaSt
   if (max_chunks < 16) max_chunks = 16;
   if (chunks > max_chunks) chunks = max_chunks;
   k_adam<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, write_half);
-  k_advance_step<<<(b.n + 127) / 128, 128, 0, stream>>>(b);
+  k_advance_step<<<(b.n + 127) / 128, 128, 0, stream>>>(g, b);
 }
 
 __global__ void k_split_outputs(const float* __restrict__ ray_out, int64_t n, float* rgb, float* depth,

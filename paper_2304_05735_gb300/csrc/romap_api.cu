@@ -371,7 +371,7 @@ romap_status sync_object(romap_ctx* ctx, int slot) {
   int64_t B = o.rays_per_step < o.pool_n ? o.rays_per_step : o.pool_n;
   d.n_rays = (int32_t)B;
   d.whole_pool = o.rays_per_step >= o.pool_n ? 1 : 0;
-  d.step = (uint32_t)(o.steps_done + 1);
+  set_object_step(d, (uint32_t)(o.steps_done + 1), ctx->cfg.beta1, ctx->cfg.beta2);
   d.pad_ = 0;
   CUDA_TRY(cudaMemcpyAsync(ctx->objs_dev + slot, &d, sizeof(ObjectDev), cudaMemcpyHostToDevice, ctx->stream));
   return ROMAP_OK;
@@ -967,7 +967,7 @@ romap_status romap_adam_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids) 
   CUDA_TRY(cudaGetLastError());
   for (int32_t id : v) {
     ctx->objs[id].steps_done += 1;
-    ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
+    set_object_step(ctx->objs_host[id], (uint32_t)(ctx->objs[id].steps_done + 1), ctx->cfg.beta1, ctx->cfg.beta2);
   }
   return ROMAP_OK;
 }
@@ -984,7 +984,7 @@ static romap_status enqueue_step(romap_ctx* ctx, const std::vector<int32_t>& v) 
   CUDA_TRY(cudaGetLastError());
   for (int32_t id : v) {
     ctx->objs[id].steps_done += 1;
-    ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
+    set_object_step(ctx->objs_host[id], (uint32_t)(ctx->objs[id].steps_done + 1), ctx->cfg.beta1, ctx->cfg.beta2);
   }
   return ROMAP_OK;
 }
@@ -1016,7 +1016,7 @@ static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, 
   ctx->stream = user;
   for (size_t i = 0; i < v.size(); ++i) {
     ctx->objs[v[i]].steps_done = done[i];
-    ctx->objs_host[v[i]].step = (uint32_t)(done[i] + 1);
+    set_object_step(ctx->objs_host[v[i]], (uint32_t)(done[i] + 1), ctx->cfg.beta1, ctx->cfg.beta2);
   }
   ctx->stats = saved;
   ctx->launches = saved_launches;
@@ -1061,7 +1061,7 @@ romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids,
       for (int32_t id : v) {
         rays += ctx->objs_host[id].n_rays;
         ctx->objs[id].steps_done += 1;
-        ctx->objs_host[id].step = (uint32_t)(ctx->objs[id].steps_done + 1);
+        set_object_step(ctx->objs_host[id], (uint32_t)(ctx->objs[id].steps_done + 1), ctx->cfg.beta1, ctx->cfg.beta2);
       }
       ctx->stats.steps += (int64_t)v.size();
       ctx->stats.rays += rays;
@@ -1108,6 +1108,25 @@ romap_status romap_last_batch(romap_ctx* ctx, int32_t id, int64_t* pool_idx, flo
                              ctx->stream));
   if (bg) CUDA_TRY(cudaMemcpyAsync(bg, ctx->R.bg + 3 * r0, sizeof(float) * 3 * (r1 - r0), cudaMemcpyDeviceToHost,
                                    ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status romap_last_outputs(romap_ctx* ctx, int32_t id, float* out, int64_t* out_n) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  const std::vector<int32_t>& k = ctx->batch_key;
+  if (k.empty()) return fail(ROMAP_ERR_BAD_STATE, "no step has run");
+  const int n = ctx->batch_n;
+  int pos = -1;
+  for (int i = 0; i < n; ++i)
+    if (k[i] == id) pos = i;
+  if (pos < 0) return fail(ROMAP_ERR_BAD_STATE, "object %d was not in the last step", id);
+  int64_t r0 = k[n + pos], r1 = k[n + pos + 1];
+  if (out_n) *out_n = r1 - r0;
+  if (out)
+    CUDA_TRY(cudaMemcpyAsync(out, ctx->R.out + 6 * r0, sizeof(float) * 6 * (r1 - r0), cudaMemcpyDeviceToHost,
+                             ctx->stream));
   CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return ROMAP_OK;
 }
@@ -1319,7 +1338,7 @@ static romap_status fn_setup(romap_ctx* ctx, const float* params, float* grad, c
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
   d.n_rays = (int32_t)n;
-  d.step = step;
+  set_object_step(d, step, ctx->cfg.beta1, ctx->cfg.beta2);
   ObjectDev* od = ctx->fn_obj_dev;
   CUDA_TRY(cudaMemcpyAsync(od, &d, sizeof(d), cudaMemcpyHostToDevice, ctx->stream));
   BatchDesc b = desc_from(hb, v.batch, od);
@@ -1541,7 +1560,7 @@ extern "C" romap_status romap_fn_forward_noalloc(const romap_config* cfg, void* 
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
   d.n_rays = (int32_t)n;
-  d.step = step;
+  d.step = step;  // the forward reads the step as the RNG counter only
   CUDA_TRY(cudaMemcpyAsync(od, &d, sizeof(d), cudaMemcpyHostToDevice, stream));
   BatchDesc b = desc_from(hb, v.batch, od);
   b.explicit_rays = 1;

@@ -13,6 +13,7 @@
 //    keeps no sample records: it packs whole rays into tiles by their number
 //    of live samples (the tile plan below) and forms the samples in-kernel.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -71,9 +72,20 @@ struct ObjectDev {
   uint32_t key0, key1;     // Philox key
   int32_t n_rays;          // rays per step B = min(rays_per_step, pool_n)
   int32_t whole_pool;      // 1 if the whole pool is used in order
-  uint32_t step;           // Adam step about to run (1-based); advanced by the Adam kernel
+  uint32_t step;           // Adam step about to run (1-based); advanced after the Adam kernel
+  float bc1, bc2;          // Adam bias corrections of that step: 1 / (1 - beta1^step), 1 / (1 - beta2^step)
   int32_t pad_;
 };
+
+// Adam bias corrections of step t (Kingma & Ba, Algorithm 1), evaluated in FP64 and rounded once to FP32.
+__host__ __device__ inline void adam_bias_corrections(float beta1, float beta2, uint32_t t, float* c1, float* c2) {
+  *c1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)t)));
+  *c2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)t)));
+}
+__host__ __device__ inline void set_object_step(ObjectDev& d, uint32_t t, float beta1, float beta2) {
+  d.step = t;
+  adam_bias_corrections(beta1, beta2, t, &d.bc1, &d.bc2);
+}
 
 // Per-batch-object values written on the device during a step.
 struct BatchDyn {

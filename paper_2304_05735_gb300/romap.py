@@ -93,6 +93,7 @@ SIGNATURES = {
     "romap_adam_step": (_i32, [_vp, _vp, _i32]),
     "romap_get_grad": (_i32, [_vp, _i32, _vp, _u32]),
     "romap_last_batch": (_i32, [_vp, _i32, _vp, _vp, _P(_i64)]),
+    "romap_last_outputs": (_i32, [_vp, _i32, _vp, _P(_i64)]),
     "romap_render": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _u32]),
     "romap_get_state": (_i32, [_vp, _i32, _P(romap_state)]),
     "romap_set_state": (_i32, [_vp, _i32, _P(romap_state)]),

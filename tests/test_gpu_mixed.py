@@ -137,3 +137,36 @@ def test_autotuner_picks_a_measured_candidate(torch):
         assert all(ms[i] > 0 for i in range(2)) and ms[chosen.value] == min(ms[0], ms[1])
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, MIXED])
+def test_rendered_rgb_vs_oracle_after_training(torch, precision):
+    """After 30 training steps, the next step's per-ray rendered colour (Eq. 6) and loss against the FP64 oracle
+    evaluated on the same FP32 master parameters: the mixed path within 2e-3 absolute RGB and 1e-3 relative loss,
+    the FP32 path within its forward tolerance."""
+    oc, rc = paired_config(L=16, T=2 ** 16, growth=0.0, n_max=512, n_samples=64, rays_per_step=2048, bg_random=True,
+                           precision=precision)
+    sc = synth.multi_object_scene(1, seed0=6, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2)[0]
+    ctx = Ctx(rc)
+    try:
+        oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed)
+        ctx.add_rays(oid, sc.pool)
+        ctx.train([oid], n_steps=30)
+        p, m, v, step = ctx.state(oid)
+        loss = ctx.fwd_bwd([oid])[0]
+        n = R.C.c_int64()
+        out = np.zeros((2048, 6), np.float32)
+        R.check(R.romap_last_outputs(ctx.h, oid, out.ctypes.data, R.C.byref(n)))
+        assert n.value == 2048
+        ref = O.train_step(oc, sc.half.astype(np.float32), sc.seed, step + 1, object_frame_pool(sc), p, m, v,
+                           do_adam=False, want_rays=True)
+        err = np.abs(out[:, :3] - ref["rays"][:, :3]).max()
+        rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
+        print(f"\n[{'mixed' if precision == MIXED else 'fp32'}] after 30 steps: max |RGB - oracle| {err:.2e}, "
+              f"loss rel {rel_loss:.2e}, mean |RGB| {np.abs(ref['rays'][:, :3]).mean():.3f}")
+        if precision == MIXED:
+            assert err < 2e-3 and rel_loss < 1e-3
+        else:
+            assert np.allclose(out[:, :3], ref["rays"][:, :3], rtol=1e-5, atol=1e-5) and rel_loss < 1e-5
+    finally:
+        ctx.close()
