@@ -39,6 +39,9 @@
  *       sigmoid; no biases.
  *  R-13 sigma = exp(clamp(o_0, -15, 15)); zero gradient outside the clamp.
  *  R-14 Adam (Kingma & Ba) with bias correction, step counter from 1.
+ *  R-17 Occupancy update (not in the paper): density at the 64^3 cell
+ *       centres, d = max(decay d, sigma), bit = d > threshold.
+ * Storage (not the method): each level's entries start at a multiple of 8.
  */
 #include <math.h>
 #include <stdint.h>
@@ -733,4 +736,67 @@ int64_t oc_train_step(const oc_config* c, const float half[3], uint64_t seed, ui
   if (bg_out) memcpy(bg_out, bg, sizeof(double) * 3 * (size_t)B);
   free(pidx); free(bg); free(bo); free(bd); free(brgb); free(bdep); free(bcls); free(g);
   return B;
+}
+
+/* ------------------------------------------------------------------ */
+/* Occupancy grid from the learned density.  Not in the paper (which   */
+/* samples the whole box); the build's scope table defines it as an    */
+/* exponential moving maximum of the density at the 64^3 cell centres, */
+/* thresholded into the bitgrid that culls samples (R-8).              */
+/* ------------------------------------------------------------------ */
+/* Centre of cell (ix, iy, iz) of the object box, FP32 in a fixed order:
+ * x_a = -a + (i + 0.5) * ((a - (-a)) / 64). */
+void oc_cell_centre(const float half[3], int ix, int iy, int iz, float x[3]) {
+  const int idx[3] = {ix, iy, iz};
+  for (int a = 0; a < 3; ++a) {
+    float lo = -half[a];
+    float w = (half[a] - lo) / 64.0f;
+    x[a] = lo + ((float)idx[a] + 0.5f) * w;
+  }
+}
+
+/* sigma = exp(clamp(o_0, -15, 15)) of the density net (R-11, R-13) at one
+ * object-frame point: encoding, first layer with ReLU, output 0 of the
+ * second layer. */
+double oc_density(const oc_config* c, const double* params, const float x[3], const float half[3]) {
+  double enc[OC_MAX_LF], h[OC_MAX_H];
+  int H = c->hidden, LF = c->L * c->F;
+  const double* mlp = params + oc_hash_param_count(c);
+  const double* W0 = mlp + oc_mlp_layer_offset(c, 0);
+  const double* W1 = mlp + oc_mlp_layer_offset(c, 1);
+  oc_encode(c, params, x, half, enc);
+  for (int i = 0; i < H; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < LF; ++j) s += W0[(size_t)i * LF + j] * enc[j];
+    h[i] = relu(s);
+  }
+  double o0 = 0.0;
+  for (int i = 0; i < H; ++i) o0 += W1[i] * h[i];
+  if (o0 < -15.0) o0 = -15.0;
+  if (o0 > 15.0) o0 = 15.0;
+  return exp(o0);
+}
+
+/* sigma at all 64^3 cell centres; cell index x + 64 y + 4096 z. */
+void oc_density_grid(const oc_config* c, const double* params, const float half[3], double* sigma) {
+  for (int z = 0; z < 64; ++z)
+    for (int y = 0; y < 64; ++y)
+      for (int x = 0; x < 64; ++x) {
+        float p[3];
+        oc_cell_centre(half, x, y, z, p);
+        sigma[x + 64 * y + 4096 * z] = oc_density(c, params, p, half);
+      }
+}
+
+/* One update of n cells: density = max(decay * density, sigma); bit i of
+ * bits (word i / 64, bit i % 64) = density_i > threshold. */
+void oc_occupancy_update(int64_t n, const double* sigma, double decay, double threshold, double* density,
+                         uint64_t* bits) {
+  memset(bits, 0, sizeof(uint64_t) * (size_t)((n + 63) / 64));
+  for (int64_t i = 0; i < n; ++i) {
+    double d = decay * density[i];
+    if (sigma[i] > d) d = sigma[i];
+    density[i] = d;
+    if (d > threshold) bits[i >> 6] |= (uint64_t)1 << (i & 63);
+  }
 }

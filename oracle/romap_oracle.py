@@ -73,6 +73,10 @@ def lib():
                                       vp, vp, vp, vp]),
             "oc_train_step": (i64, [vp, vp, u64, u32, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int, vp, vp, vp,
                                     vp, vp, vp]),
+            "oc_cell_centre": (None, [vp, C.c_int, C.c_int, C.c_int, vp]),
+            "oc_density": (d, [vp, vp, vp, vp]),
+            "oc_density_grid": (None, [vp, vp, vp, vp]),
+            "oc_occupancy_update": (None, [i64, vp, d, d, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -342,3 +346,31 @@ def train_step(cfg, half, seed, step, pool, params, m, v, occ=None, do_adam=True
     assert got == B
     return dict(params=params, m=m, v=v, grad=grad, loss=loss, pool_idx=pidx, bg=bg, rays=ray_out,
                 samples=sample_out)
+
+
+def cell_centre(half, ix, iy, iz):
+    """Centre of occupancy cell (ix, iy, iz) of the box [-half, half] (FP32, fixed order)."""
+    x = np.zeros(3, np.float32)
+    lib().oc_cell_centre(_p(_f32(half)), int(ix), int(iy), int(iz), _p(x))
+    return x
+
+
+def density(cfg, params, x, half):
+    """sigma of the density net at one object-frame point."""
+    return float(lib().oc_density(_cp(cfg), _p(_f64(params)), _p(_f32(x)), _p(_f32(half))))
+
+
+def density_grid(cfg, params, half):
+    """sigma at all 64^3 cell centres, index x + 64 y + 4096 z."""
+    out = np.zeros(64 ** 3, np.float64)
+    lib().oc_density_grid(_cp(cfg), _p(_f64(params)), _p(_f32(half)), _p(out))
+    return out
+
+
+def occupancy_update(sigma, decay, threshold, density_in):
+    """density = max(decay * density, sigma); returns (density, 64-bit words of density > threshold)."""
+    sigma = _f64(sigma)
+    dens = _f64(density_in).copy()
+    bits = np.zeros((sigma.size + 63) // 64, np.uint64)
+    lib().oc_occupancy_update(sigma.size, _p(sigma), float(decay), float(threshold), _p(dens), _p(bits))
+    return dens, bits
