@@ -184,6 +184,21 @@ ROMAP_API romap_status romap_destroy_object(romap_ctx* ctx, int32_t id);
  * x + 64 y + 4096 z in 4096 uint64 words; samples in empty cells are
  * skipped (density 0).  bits == NULL removes the grid. */
 ROMAP_API romap_status romap_set_occupancy(romap_ctx* ctx, int32_t id, const uint64_t* bits, uint32_t flags);
+/* Occupancy from the learned density (empty-space skipping; not in the
+ * paper).  Evaluates the object's density net (FP32 master parameters) at
+ * the centre of each of the 64^3 cells of its box, x_a = -a + (i + 0.5)
+ * (2a / 64) in FP32, keeps per cell d = max(decay * d, sigma) (d starts at
+ * sigma on the first call and with flags ROMAP_REPLACE), and replaces the
+ * object's bitgrid with d > threshold; later steps cull samples in cells
+ * whose bit is 0.  decay in [0, 1], threshold finite and >= 0, else
+ * ROMAP_ERR_INVALID_ARG.  Enqueued on the context's stream. */
+ROMAP_API romap_status romap_update_occupancy(romap_ctx* ctx, int32_t id, float decay, float threshold,
+                                              uint32_t flags);
+/* Copies the object's bitgrid (4096 uint64 words) and/or the per-cell
+ * densities of romap_update_occupancy (64^3 floats, x fastest) to host
+ * memory; either pointer may be NULL.  ROMAP_ERR_BAD_STATE if a requested
+ * array does not exist yet. */
+ROMAP_API romap_status romap_get_occupancy(romap_ctx* ctx, int32_t id, uint64_t* bits, float* density);
 /* Appends n rays to the object's pool (incremental data, Sec. V-A-1), or
  * replaces the pool with ROMAP_REPLACE.  Rays are moved to the object frame
  * and their directions normalised on the device. */

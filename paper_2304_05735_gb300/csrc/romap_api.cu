@@ -64,6 +64,7 @@ struct Object {
   uint8_t* pool_cls = nullptr;
   int64_t pool_n = 0, pool_cap = 0;
   uint64_t* occ = nullptr;
+  float* occ_density = nullptr;  // per-cell moving maximum of the learned density (romap_update_occupancy)
   int64_t steps_done = 0;
   int32_t rays_per_step = 0;
 };
@@ -472,6 +473,7 @@ void free_object(romap_ctx* ctx, Object& o) {
   dev_free(ctx, o.pool_depth);
   dev_free(ctx, o.pool_cls);
   dev_free(ctx, o.occ);
+  dev_free(ctx, o.occ_density);
   o = Object{};
 }
 
@@ -841,6 +843,42 @@ romap_status romap_set_occupancy(romap_ctx* ctx, int32_t id, const uint64_t* bit
                            (flags & ROMAP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            ctx->stream));
   return sync_object(ctx, id);
+}
+
+romap_status romap_update_occupancy(romap_ctx* ctx, int32_t id, float decay, float threshold, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!(decay >= 0.f && decay <= 1.f)) return fail(ROMAP_ERR_INVALID_ARG, "decay must be in [0, 1]");
+  if (!(threshold >= 0.f) || !std::isfinite(threshold))
+    return fail(ROMAP_ERR_INVALID_ARG, "threshold must be finite and >= 0");
+  if (flags & ~ROMAP_REPLACE) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  Object& o = ctx->objs[id];
+  bool fresh = false;
+  if (!o.occ_density) {
+    ROMAP_TRY(dev_alloc_t(ctx, (size_t)64 * 64 * 64, &o.occ_density));
+    fresh = true;
+  }
+  if (!o.occ) ROMAP_TRY(dev_alloc_t(ctx, 4096, &o.occ));
+  ROMAP_TRY(sync_object(ctx, id));
+  launch_occ_update(ctx->g, ctx->objs_dev, id, decay, threshold, (fresh || (flags & ROMAP_REPLACE)) ? 1 : 0,
+                    o.occ_density, o.occ, ctx->stream);
+  ctx->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  return ROMAP_OK;
+}
+
+romap_status romap_get_occupancy(romap_ctx* ctx, int32_t id, uint64_t* bits, float* density) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  const Object& o = ctx->objs[id];
+  if (bits && !o.occ) return fail(ROMAP_ERR_BAD_STATE, "object %d has no occupancy grid", id);
+  if (density && !o.occ_density) return fail(ROMAP_ERR_BAD_STATE, "object %d has no occupancy densities", id);
+  if (bits) CUDA_TRY(cudaMemcpyAsync(bits, o.occ, 4096 * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  if (density)
+    CUDA_TRY(cudaMemcpyAsync(density, o.occ_density, sizeof(float) * 64 * 64 * 64, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
 }
 
 romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* r, int64_t n, uint32_t flags) {

@@ -225,6 +225,8 @@ void launch_split_outputs(const float* ray_out, int64_t n, float* rgb, float* de
                           cudaStream_t stream);
 int tile_kernel_smem_bytes(int LF);
 // Mixed precision: fused forward + compositing + backward on tensor cores; P slots per ray (power of two <= 128).
+void launch_occ_update(const GridParams& g, const ObjectDev* objs, int slot, float decay, float threshold, int reset,
+                       float* dens, uint64_t* bits, cudaStream_t stream);
 void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream);
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int total_tiles, int n_ctas, cudaStream_t stream);

@@ -86,6 +86,8 @@ SIGNATURES = {
     "romap_create_object": (_i32, [_vp, _P(romap_object_desc), _P(_i32)]),
     "romap_destroy_object": (_i32, [_vp, _i32]),
     "romap_set_occupancy": (_i32, [_vp, _i32, _vp, _u32]),
+    "romap_update_occupancy": (_i32, [_vp, _i32, C.c_float, C.c_float, _u32]),
+    "romap_get_occupancy": (_i32, [_vp, _i32, _vp, _vp]),
     "romap_add_rays": (_i32, [_vp, _i32, _P(romap_rays), _i64, _u32]),
     "romap_pool_size": (_i32, [_vp, _i32, _P(_i64)]),
     "romap_train_step": (_i32, [_vp, _vp, _i32, _i32, _vp]),
