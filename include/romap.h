@@ -232,6 +232,37 @@ ROMAP_API romap_status romap_last_batch(romap_ctx* ctx, int32_t id, int64_t* poo
  * floats per ray, computed in the step's precision.  out may be NULL. */
 ROMAP_API romap_status romap_last_outputs(romap_ctx* ctx, int32_t id, float* out, int64_t* out_n);
 
+/* ---- incremental training data and budgeted training ------------------- */
+/* Eq. 5 (Sec. V-A-1): the angle, in degrees, between the vectors from the
+ * object centre to the camera centre of the last image used for training
+ * (cam_last) and to the current camera centre (cam_now); world frame, FP64.
+ * A camera at the object centre gives 180.  Host-only, needs no context. */
+ROMAP_API romap_status romap_view_angle(const double cam_last[3], const double cam_now[3], const double center[3],
+                                        double* out_deg);
+/* The incremental data rule: if the object has no image yet, or the Eq. 5
+ * angle between its last used camera centre and cam_center (world) around
+ * the object's centre (desc t) exceeds threshold_deg (Sec. VI: 25), appends
+ * the rays (as romap_add_rays with flags) , records cam_center as the last
+ * used image and grants `iterations` more training steps (Sec. VI: 300);
+ * otherwise the rays are ignored.  *out_updated (nullable) = 1 / 0. */
+ROMAP_API romap_status romap_observe(romap_ctx* ctx, int32_t id, const double cam_center[3], float threshold_deg,
+                                     const romap_rays* rays, int64_t n, uint32_t flags, int32_t iterations,
+                                     int32_t* out_updated);
+/* Training steps still owed to the object (granted by romap_observe,
+ * consumed by romap_train_budget). */
+ROMAP_API romap_status romap_pending(romap_ctx* ctx, int32_t id, int64_t* out);
+ROMAP_API romap_status romap_set_pending(romap_ctx* ctx, int32_t id, int64_t pending);
+/* Budgeted training of the listed objects that still owe steps: batched
+ * steps (CUDA-graph replays) of all of them, in chunks of at most max_chunk
+ * (<= 0: 64), while the measured device time of the steps so far plus the
+ * step time measured for the current batch composition fits in budget_ms
+ * (an unseen composition first runs one step to measure it).  An object
+ * leaves the batch when its owed steps reach 0.  Blocks until the steps
+ * finish.  out_steps: steps run; out_ms: their device time; out_loss
+ * (n_ids, nullable): each object's last loss, NaN if it did not train. */
+ROMAP_API romap_status romap_train_budget(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, float budget_ms,
+                                          int32_t max_chunk, int32_t* out_steps, float* out_ms, float* out_loss);
+
 /* ---- inference --------------------------------------------------------- */
 /* Renders n rays (world frame unless ROMAP_OBJECT_FRAME) with midpoint
  * samples over bg (3 floats, host).  Outputs per ray (nullable each):

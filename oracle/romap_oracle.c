@@ -41,6 +41,9 @@
  *  R-14 Adam (Kingma & Ba) with bias correction, step counter from 1.
  *  R-17 Occupancy update (not in the paper): density at the 64^3 cell
  *       centres, d = max(decay d, sigma), bit = d > threshold.
+ *  R-18 Data-update rule (Eq. 5): the angle between the object-to-camera
+ *       vectors of the last used and the current image; update when it
+ *       exceeds the threshold, and always for the first image.
  * Storage (not the method): each level's entries start at a multiple of 8.
  */
 #include <math.h>
@@ -799,4 +802,36 @@ void oc_occupancy_update(int64_t n, const double* sigma, double decay, double th
     density[i] = d;
     if (d > threshold) bits[i >> 6] |= (uint64_t)1 << (i & 63);
   }
+}
+
+/* ------------------------------------------------------------------ */
+/* Incremental training-data rule (Sec. V-A-1, Eq. 5).                 */
+/* ------------------------------------------------------------------ */
+/* Rotation angle, in degrees, between the last updated image I_m and the
+ * current image I_n as seen from the object: the angle between the vectors
+ * from the object centre t_O to the two camera centres (FP64).  The cosine
+ * is clamped to [-1, 1] against rounding.  Degenerate vectors (a camera at
+ * the object centre) give 180 degrees, i.e. always update. */
+double oc_view_angle_deg(const double t_m[3], const double t_n[3], const double t_o[3]) {
+  double a[3], b[3], ab = 0.0, aa = 0.0, bb = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    a[k] = t_m[k] - t_o[k];
+    b[k] = t_n[k] - t_o[k];
+    ab += a[k] * b[k];
+    aa += a[k] * a[k];
+    bb += b[k] * b[k];
+  }
+  if (aa == 0.0 || bb == 0.0) return 180.0;
+  double c = ab / (sqrt(aa) * sqrt(bb));
+  if (c > 1.0) c = 1.0;
+  if (c < -1.0) c = -1.0;
+  return acos(c) * (180.0 / 3.14159265358979323846);
+}
+
+/* The rule: update when no image has been used yet, or when the angle is
+ * larger than the threshold (Sec. VI: 25 degrees). */
+int oc_should_update(int have_last, const double t_m[3], const double t_n[3], const double t_o[3],
+                     double threshold_deg) {
+  if (!have_last) return 1;
+  return oc_view_angle_deg(t_m, t_n, t_o) > threshold_deg;
 }

@@ -77,6 +77,8 @@ def lib():
             "oc_density": (d, [vp, vp, vp, vp]),
             "oc_density_grid": (None, [vp, vp, vp, vp]),
             "oc_occupancy_update": (None, [i64, vp, d, d, vp, vp]),
+            "oc_view_angle_deg": (d, [vp, vp, vp]),
+            "oc_should_update": (C.c_int, [C.c_int, vp, vp, vp, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -374,3 +376,15 @@ def occupancy_update(sigma, decay, threshold, density_in):
     bits = np.zeros((sigma.size + 63) // 64, np.uint64)
     lib().oc_occupancy_update(sigma.size, _p(sigma), float(decay), float(threshold), _p(dens), _p(bits))
     return dens, bits
+
+
+def view_angle_deg(t_m, t_n, t_o):
+    """Eq. 5: angle between the object-to-camera vectors of the last updated and the current image, degrees."""
+    return float(lib().oc_view_angle_deg(_p(_f64(t_m)), _p(_f64(t_n)), _p(_f64(t_o))))
+
+
+def should_update(t_m, t_n, t_o, threshold_deg):
+    """The data-update rule: True when t_m is None (no image yet) or the Eq. 5 angle exceeds the threshold."""
+    if t_m is None:
+        return bool(lib().oc_should_update(0, None, _p(_f64(t_n)), _p(_f64(t_o)), float(threshold_deg)))
+    return bool(lib().oc_should_update(1, _p(_f64(t_m)), _p(_f64(t_n)), _p(_f64(t_o)), float(threshold_deg)))

@@ -9,12 +9,16 @@
 // Adam bias-correction exponent) lives on the device and is advanced by the
 // Adam launch, so a step's launch sequence does not depend on host state
 // that changes from step to step.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <limits>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "romap.h"
@@ -65,6 +69,10 @@ struct Object {
   int64_t pool_n = 0, pool_cap = 0;
   uint64_t* occ = nullptr;
   float* occ_density = nullptr;  // per-cell moving maximum of the learned density (romap_update_occupancy)
+  // incremental training data (Eq. 5): camera centre of the last image used, training iterations still owed
+  bool have_view = false;
+  double last_view[3] = {0, 0, 0};
+  int64_t pending = 0;
   int64_t steps_done = 0;
   int32_t rays_per_step = 0;
 };
@@ -123,6 +131,8 @@ struct romap_ctx {
   uint64_t ws_generation = 0;   // bumped whenever a workspace buffer moves
   uint64_t graph_ws_generation = 0;
   bool graphs_enabled = true;
+  // budgeted training: measured step time of each batch composition (ms, moving average)
+  std::map<std::vector<int32_t>, double> step_ms_est;
   // phase timing
   bool profiling = false;
   struct Prof { int phase; cudaEvent_t a, b; int launches; };
@@ -1116,6 +1126,136 @@ romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids,
     for (int i = 0; i < n_ids; ++i) out_loss[i] = tmp[5 * i];
   }
   return ROMAP_OK;
+}
+
+// ---- incremental training data and budgeted training (Sec. V-A-1, Eq. 5; Sec. VI) ---------------------------------
+romap_status romap_view_angle(const double cam_last[3], const double cam_now[3], const double center[3],
+                              double* out_deg) {
+  if (!cam_last || !cam_now || !center || !out_deg) return fail(ROMAP_ERR_INVALID_ARG, "NULL argument");
+  double dot = 0.0, n_last = 0.0, n_now = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double u = cam_last[a] - center[a], w = cam_now[a] - center[a];
+    dot += u * w;
+    n_last += u * u;
+    n_now += w * w;
+  }
+  if (!(n_last > 0.0) || !(n_now > 0.0)) {  // a camera at the object centre: no direction, always new data
+    *out_deg = 180.0;
+    return std::isfinite(n_last) && std::isfinite(n_now) ? ROMAP_OK : fail(ROMAP_ERR_NONFINITE, "non-finite input");
+  }
+  const double c = std::min(1.0, std::max(-1.0, dot / std::sqrt(n_last * n_now)));
+  if (!std::isfinite(c)) return fail(ROMAP_ERR_NONFINITE, "non-finite input");
+  *out_deg = std::acos(c) * (180.0 / 3.14159265358979323846);
+  return ROMAP_OK;
+}
+
+romap_status romap_observe(romap_ctx* ctx, int32_t id, const double cam_center[3], float threshold_deg,
+                           const romap_rays* rays, int64_t n, uint32_t flags, int32_t iterations, int32_t* out_updated) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!cam_center) return fail(ROMAP_ERR_INVALID_ARG, "cam_center is required");
+  if (!(threshold_deg >= 0.f && threshold_deg <= 180.f)) return fail(ROMAP_ERR_INVALID_ARG, "threshold_deg in [0, 180]");
+  if (iterations < 0) return fail(ROMAP_ERR_INVALID_ARG, "iterations must be >= 0");
+  Object& o = ctx->objs[id];
+  const double center[3] = {o.desc.t[0], o.desc.t[1], o.desc.t[2]};
+  bool update = !o.have_view;
+  if (!update) {
+    double deg = 0.0;
+    ROMAP_TRY(romap_view_angle(o.last_view, cam_center, center, &deg));
+    update = deg > (double)threshold_deg;
+  } else {
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(cam_center[a])) return fail(ROMAP_ERR_NONFINITE, "non-finite camera centre");
+  }
+  if (update) {
+    if (rays && n > 0) ROMAP_TRY(romap_add_rays(ctx, id, rays, n, flags));
+    o.have_view = true;
+    for (int a = 0; a < 3; ++a) o.last_view[a] = cam_center[a];
+    o.pending += iterations;
+  }
+  if (out_updated) *out_updated = update ? 1 : 0;
+  return ROMAP_OK;
+}
+
+romap_status romap_pending(romap_ctx* ctx, int32_t id, int64_t* out) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!out) return fail(ROMAP_ERR_INVALID_ARG, "out is required");
+  *out = ctx->objs[id].pending;
+  return ROMAP_OK;
+}
+
+romap_status romap_set_pending(romap_ctx* ctx, int32_t id, int64_t pending) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (pending < 0) return fail(ROMAP_ERR_INVALID_ARG, "pending must be >= 0");
+  ctx->objs[id].pending = pending;
+  return ROMAP_OK;
+}
+
+romap_status romap_train_budget(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, float budget_ms,
+                                int32_t max_chunk, int32_t* out_steps, float* out_ms, float* out_loss) {
+  ROMAP_TRY(check_ctx(ctx));
+  std::vector<int32_t> all;
+  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &all));
+  if (!(budget_ms >= 0.f) || !std::isfinite(budget_ms)) return fail(ROMAP_ERR_INVALID_ARG, "budget_ms must be >= 0");
+  if (max_chunk < 1) max_chunk = 64;
+  if (out_loss)
+    for (int i = 0; i < n_ids; ++i) out_loss[i] = std::numeric_limits<float>::quiet_NaN();
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  double elapsed = 0.0;
+  int32_t steps = 0;
+  romap_status st = ROMAP_OK;
+  std::vector<float> loss;
+  while (st == ROMAP_OK) {
+    std::vector<int32_t> act;
+    int64_t min_pending = INT64_MAX;
+    for (int32_t id : all)
+      if (ctx->objs[id].pending > 0) {
+        act.push_back(id);
+        min_pending = std::min(min_pending, ctx->objs[id].pending);
+      }
+    if (act.empty()) break;
+    std::vector<int32_t> key(act);
+    for (int32_t id : act) key.push_back(ctx->objs_host[id].n_rays);
+    auto it = ctx->step_ms_est.find(key);
+    // steps of this composition that fit in what is left of the budget; an unknown composition runs one step to
+    // learn its time
+    int64_t k = 1;
+    if (it != ctx->step_ms_est.end()) {
+      const double left = (double)budget_ms - elapsed;
+      k = it->second > 0.0 ? (int64_t)(left / it->second) : max_chunk;
+      if (k < 1) break;
+    } else if (elapsed > 0.0 && elapsed >= (double)budget_ms) {
+      break;
+    }
+    k = std::min<int64_t>(std::min<int64_t>(k, max_chunk), min_pending);
+    loss.assign(act.size(), 0.f);
+    CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+    st = romap_train_step(ctx, act.data(), (int32_t)act.size(), (int32_t)k, loss.data());
+    CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    elapsed += ms;
+    const double per = ms / (double)k;
+    // a composition's first step includes its graph capture: keep the estimate from the later, replayed steps
+    if (it == ctx->step_ms_est.end()) ctx->step_ms_est[key] = per;
+    else it->second = 0.5 * it->second + 0.5 * per;
+    steps += (int32_t)k;
+    for (int32_t id : act) ctx->objs[id].pending -= k;
+    if (out_loss)
+      for (size_t j = 0; j < act.size(); ++j)
+        for (int i = 0; i < n_ids; ++i)
+          if (ids[i] == act[j]) out_loss[i] = loss[j];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out_steps) *out_steps = steps;
+  if (out_ms) *out_ms = (float)elapsed;
+  return st;
 }
 
 romap_status romap_get_grad(romap_ctx* ctx, int32_t id, float* out, uint32_t flags) {

@@ -96,3 +96,25 @@ def test_init_without_gpu_reports_cuda_error():
     cfg = R.make_config()
     assert R.romap_init(C.byref(cfg), None, C.byref(out)) == R.ROMAP_ERR_CUDA
     assert not out.value
+
+
+def test_view_angle_matches_oracle():
+    """Eq. 5 in the library (host code) against the oracle's FP64 restatement on random camera pairs."""
+    import ctypes as C
+
+    import numpy as np
+
+    from oracle import romap_oracle as O
+
+    rng = np.random.default_rng(11)
+    out = C.c_double()
+    for _ in range(500):
+        o = rng.normal(size=3)
+        a, b = o + rng.normal(size=3) * 2, o + rng.normal(size=3) * 2
+        arr = [np.ascontiguousarray(x, np.float64) for x in (a, b, o)]
+        assert R.romap_view_angle(*(x.ctypes.data for x in arr), C.byref(out)) == R.ROMAP_OK
+        assert out.value == pytest.approx(O.view_angle_deg(a, b, o), abs=1e-6)
+    z = np.zeros(3)
+    assert R.romap_view_angle(z.ctypes.data, np.ones(3).ctypes.data, z.ctypes.data, C.byref(out)) == R.ROMAP_OK
+    assert out.value == 180.0
+    assert R.romap_view_angle(None, z.ctypes.data, z.ctypes.data, C.byref(out)) == R.ROMAP_ERR_INVALID_ARG

@@ -1,6 +1,6 @@
-"""Pins of the oracle's occupancy update (density at the 64^3 cell centres, moving maximum, threshold): cell centres
-in closed form and against the occupancy lookup, the density chain against a closed-form model, the moving maximum
-and the bit layout by brute force."""
+"""Pins of the oracle's mapping-side functions: the occupancy update (density at the 64^3 cell centres, moving
+maximum, threshold) by closed forms, the full forward and brute-force bit layout; the Eq. 5 data-update angle by
+closed forms."""
 import numpy as np
 import pytest
 
@@ -107,3 +107,25 @@ def test_moving_maximum_and_bits_brute_force():
     assert np.array_equal(d2, s)
     d3, b3 = O.occupancy_update(s, 0.0, thr, d2)
     assert np.array_equal(d3, d2) and np.array_equal(b3, b2)
+
+
+def test_view_angle_closed_forms():
+    """Eq. 5 against closed forms: orthogonal, coincident and opposite directions, a 25-degree rotation about an
+    arbitrary object centre (scale-free in the distances), and the first image always updating."""
+    o = np.array([0.3, -1.2, 0.8])
+    assert O.view_angle_deg(o + [1, 0, 0], o + [0, 3, 0], o) == pytest.approx(90.0, abs=1e-12)
+    assert O.view_angle_deg(o + [1, 2, 3], o + [2, 4, 6], o) == pytest.approx(0.0, abs=1e-6)
+    assert O.view_angle_deg(o + [1, 2, 3], o - [2, 4, 6], o) == pytest.approx(180.0, abs=1e-6)
+    rng = np.random.default_rng(4)
+    for deg in (5.0, 24.9, 25.1, 60.0, 133.0):
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        v = np.cross(axis, rng.normal(size=3))
+        v /= np.linalg.norm(v)
+        th = np.deg2rad(deg)
+        w = v * np.cos(th) + np.cross(axis, v) * np.sin(th)  # v rotated about axis (axis _|_ v)
+        got = O.view_angle_deg(o + 2.5 * v, o + 0.7 * w, o)
+        assert got == pytest.approx(deg, abs=1e-9)
+        assert O.should_update(o + 2.5 * v, o + 0.7 * w, o, 25.0) == (deg > 25.0)
+    assert O.should_update(None, o + [1, 0, 0], o, 25.0)
+    assert O.view_angle_deg(o, o + [1, 0, 0], o) == 180.0  # degenerate: a camera at the object centre
