@@ -254,12 +254,15 @@ ROMAP_API romap_status romap_pending(romap_ctx* ctx, int32_t id, int64_t* out);
 ROMAP_API romap_status romap_set_pending(romap_ctx* ctx, int32_t id, int64_t pending);
 /* Budgeted training of the listed objects that still owe steps: batched
  * steps (CUDA-graph replays) of all of them, in chunks of at most max_chunk
- * (<= 0: 64), while the measured device time of the steps so far plus the
- * step time measured for the current batch composition fits in budget_ms
- * (an unseen composition first runs one step to measure it).  An object
- * leaves the batch when its owed steps reach 0.  Blocks until the steps
- * finish.  out_steps: steps run; out_ms: their device time; out_loss
- * (n_ids, nullable): each object's last loss, NaN if it did not train. */
+ * (<= 0: 64), while the device time of the steps so far plus the step time
+ * of the batch fits in budget_ms.  The step time of a batch composition is
+ * the measured one, else predicted from the measured time per ray; with
+ * nothing measured yet, one step runs to measure it.  When the whole batch
+ * no longer fits, one step trains the objects that owe the most steps, as
+ * many as fit.  An object leaves the batch when its owed steps reach 0.
+ * Blocks until the steps finish.  out_steps: batched steps run; out_ms:
+ * their device time; out_loss (n_ids, nullable): each object's last loss,
+ * NaN if it did not train. */
 ROMAP_API romap_status romap_train_budget(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, float budget_ms,
                                           int32_t max_chunk, int32_t* out_steps, float* out_ms, float* out_loss);
 

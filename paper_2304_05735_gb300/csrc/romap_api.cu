@@ -133,6 +133,7 @@ struct romap_ctx {
   bool graphs_enabled = true;
   // budgeted training: measured step time of each batch composition (ms, moving average)
   std::map<std::vector<int32_t>, double> step_ms_est;
+  double ms_per_ray = -1.0;  // device time of one step per ray of the batch (moving average), -1 until measured
   // phase timing
   bool profiling = false;
   struct Prof { int phase; cudaEvent_t a, b; int launches; };
@@ -1211,27 +1212,54 @@ romap_status romap_train_budget(romap_ctx* ctx, const int32_t* ids, int32_t n_id
   std::vector<float> loss;
   while (st == ROMAP_OK) {
     std::vector<int32_t> act;
-    int64_t min_pending = INT64_MAX;
     for (int32_t id : all)
-      if (ctx->objs[id].pending > 0) {
-        act.push_back(id);
-        min_pending = std::min(min_pending, ctx->objs[id].pending);
-      }
+      if (ctx->objs[id].pending > 0) act.push_back(id);
     if (act.empty()) break;
-    std::vector<int32_t> key(act);
-    for (int32_t id : act) key.push_back(ctx->objs_host[id].n_rays);
+    auto rays_of = [&](const std::vector<int32_t>& v) {
+      int64_t r = 0;
+      for (int32_t id : v) r += ctx->objs_host[id].n_rays;
+      return r;
+    };
+    auto key_of = [&](const std::vector<int32_t>& v) {
+      std::vector<int32_t> key(v);
+      for (int32_t id : v) key.push_back(ctx->objs_host[id].n_rays);
+      return key;
+    };
+    const double left = (double)budget_ms - elapsed;
+    std::vector<int32_t> key = key_of(act);
     auto it = ctx->step_ms_est.find(key);
-    // steps of this composition that fit in what is left of the budget; an unknown composition runs one step to
-    // learn its time
+    // the step time of this composition: measured, else predicted from the time per ray, else unknown
+    double est = it != ctx->step_ms_est.end() ? it->second
+                 : (ctx->ms_per_ray > 0.0 ? ctx->ms_per_ray * (double)rays_of(act) : -1.0);
     int64_t k = 1;
-    if (it != ctx->step_ms_est.end()) {
-      const double left = (double)budget_ms - elapsed;
-      k = it->second > 0.0 ? (int64_t)(left / it->second) : max_chunk;
-      if (k < 1) break;
-    } else if (elapsed > 0.0 && elapsed >= (double)budget_ms) {
-      break;
+    if (est < 0.0) {
+      if (elapsed > 0.0 && elapsed >= (double)budget_ms) break;  // nothing known: one step to measure
+    } else if (est <= left) {
+      int64_t min_pending = INT64_MAX;
+      for (int32_t id : act) min_pending = std::min(min_pending, ctx->objs[id].pending);
+      k = std::min<int64_t>(std::min<int64_t>(est > 0.0 ? (int64_t)(left / est) : max_chunk, max_chunk),
+                            min_pending);
+    } else {
+      // the whole batch does not fit: one step of the objects that owe the most steps, as many as fit
+      if (!(ctx->ms_per_ray > 0.0)) break;
+      std::vector<int32_t> order(act);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int32_t a, int32_t b) { return ctx->objs[a].pending > ctx->objs[b].pending; });
+      std::vector<int32_t> sub;
+      double acc = 0.0;
+      for (int32_t id : order) {
+        const double c = ctx->ms_per_ray * (double)ctx->objs_host[id].n_rays;
+        if (acc + c <= left) {
+          sub.push_back(id);
+          acc += c;
+        }
+      }
+      if (sub.empty()) break;
+      std::sort(sub.begin(), sub.end());
+      act = sub;
+      key = key_of(act);
+      it = ctx->step_ms_est.find(key);
     }
-    k = std::min<int64_t>(std::min<int64_t>(k, max_chunk), min_pending);
     loss.assign(act.size(), 0.f);
     CUDA_TRY(cudaEventRecord(e0, ctx->stream));
     st = romap_train_step(ctx, act.data(), (int32_t)act.size(), (int32_t)k, loss.data());
@@ -1241,9 +1269,11 @@ romap_status romap_train_budget(romap_ctx* ctx, const int32_t* ids, int32_t n_id
     CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
     elapsed += ms;
     const double per = ms / (double)k;
-    // a composition's first step includes its graph capture: keep the estimate from the later, replayed steps
+    // a composition's first step includes its graph capture: later, replayed steps refine the estimate
     if (it == ctx->step_ms_est.end()) ctx->step_ms_est[key] = per;
     else it->second = 0.5 * it->second + 0.5 * per;
+    const double per_ray = per / (double)std::max<int64_t>(1, rays_of(act));
+    ctx->ms_per_ray = ctx->ms_per_ray > 0.0 ? 0.8 * ctx->ms_per_ray + 0.2 * per_ray : per_ray;
     steps += (int32_t)k;
     for (int32_t id : act) ctx->objs[id].pending -= k;
     if (out_loss)

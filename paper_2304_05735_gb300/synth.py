@@ -290,3 +290,102 @@ def occupancy_bits(shape, half, dilate=2, p=0.0, seed=0, res=64):
 def random_params(n, seed, scale=1.0):
     """Uniform U(-scale, scale) parameters (for parity cases with non-trivial densities)."""
     return np.random.default_rng(seed).uniform(-scale, scale, size=n)
+
+
+# --------------------------------------------------------------------------
+# Streaming sequence: objects in a room seen along a camera path
+# --------------------------------------------------------------------------
+@dataclass
+class StreamObject:
+    shape: Shape
+    t: np.ndarray
+    yaw: float
+    half: np.ndarray
+    seed: int
+
+
+@dataclass
+class StreamScene:
+    objects: list
+    cam_pos: np.ndarray            # [n_frames, 3] camera centres (world)
+    cam_rot: np.ndarray            # [n_frames, 3, 3] camera-to-world rotations
+    W: int
+    H: int
+    f: float
+    rate_hz: float
+
+
+def streaming_scene(n_objects=96, n_frames=600, W=640, H=480, f=525.0, rate_hz=25.0, seed=1000, extent=12.0):
+    """Objects (random shapes as in multi_object_scene, unit boxes, random yaw) standing on the floor of a
+    2 extent x 2 extent room at least 1.5 apart, and a camera at eye height (1.6) that follows a figure-eight
+    around the room over n_frames frames (rate_hz) while looking towards the room's centre region."""
+    rng = np.random.default_rng(seed)
+    objs = []
+    pos = []
+    tries = 0
+    while len(objs) < n_objects:
+        tries += 1
+        if tries > 200 * n_objects:
+            raise ValueError("the room is too small for the objects at the minimum spacing")
+        p = np.array([rng.uniform(-extent, extent), rng.uniform(-extent, extent), 0.5])
+        if any(np.linalg.norm(p[:2] - q[:2]) < 1.5 for q in pos):
+            continue
+        k = len(objs)
+        orng = np.random.default_rng(seed + 1 + k)
+        objs.append(StreamObject(shape=random_shape(orng, k), t=p, yaw=float(orng.uniform(-np.pi, np.pi)),
+                                 half=np.array([0.5, 0.5, 0.5]), seed=seed + 1 + k))
+        pos.append(p)
+    s = np.arange(n_frames) / n_frames * 2.0 * np.pi
+    cam = np.stack([0.85 * extent * np.sin(s), 0.6 * extent * np.sin(2.0 * s), np.full(n_frames, 1.6)], axis=1)
+    look = np.stack([0.35 * extent * np.sin(s + 0.9), 0.35 * extent * np.cos(s + 0.4), np.full(n_frames, 0.5)],
+                    axis=1)
+    rot = np.stack([look_at(c, t) for c, t in zip(cam, look)])
+    return StreamScene(objects=objs, cam_pos=cam, cam_rot=rot, W=W, H=H, f=f, rate_hz=rate_hz)
+
+
+def detection_box(obj, cam_pos, R_cw, W, H, f):
+    """Pixel rectangle (u0, v0, u1, v1) of the object's projected 3D box clipped to the image, or None when a box
+    corner is behind the camera or the rectangle is empty."""
+    R = yaw_matrix(obj.yaw)
+    corners = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]) * obj.half
+    pc = ((corners @ R.T) + obj.t - cam_pos) @ R_cw
+    if np.any(pc[:, 2] <= 0.1):
+        return None
+    uv = pc[:, :2] / pc[:, 2:3] * f + np.array([W / 2.0, H / 2.0])
+    u0, v0 = np.floor(uv.min(0))
+    u1, v1 = np.ceil(uv.max(0))
+    u0, v0, u1, v1 = max(u0, 0), max(v0, 0), min(u1, W - 1), min(v1, H - 1)
+    if u1 < u0 or v1 < v0:
+        return None
+    return int(u0), int(v0), int(u1), int(v1)
+
+
+def frame_rays(obj, cam_pos, R_cw, box, f, W, H, rng, stride=2, depth_frac=0.02, occluder_prob=0.3):
+    """World-frame rays of the pixels of the detection box (every stride-th pixel), with the object's analytic
+    colour and mask class, random occluder discs and sparse first-hit depth, as in multi_object_scene."""
+    u0, v0, u1, v1 = box
+    us, vs = np.meshgrid(np.arange(u0, u1 + 1, stride), np.arange(v0, v1 + 1, stride))
+    us, vs = us.ravel().astype(np.float64), vs.ravel().astype(np.float64)
+    ow, dw = pixel_rays(R_cw, cam_pos, f, f, W / 2.0, H / 2.0, us, vs)
+    R = yaw_matrix(obj.yaw)
+    oo = (ow - obj.t) @ R
+    do = dw @ R
+    th = obj.shape.first_hit(oo, do)
+    hit = np.isfinite(th)
+    rgb = np.tile(rng.uniform(0, 1, size=3), (us.size, 1))
+    rgb[hit] = obj.shape.colour(oo[hit] + th[hit, None] * do[hit])
+    cls = np.where(hit, CLS_OBJECT, CLS_BACKGROUND).astype(np.uint8)
+    if occluder_prob > 0 and rng.uniform() < occluder_prob:
+        cu, cv = rng.uniform(u0, u1 + 1), rng.uniform(v0, v1 + 1)
+        rad = rng.uniform(0.1, 0.3) * max(u1 - u0 + 1, v1 - v0 + 1)
+        occ = (us - cu) ** 2 + (vs - cv) ** 2 < rad ** 2
+        cls[occ] = CLS_OCCLUDER
+        rgb[occ] = 0.3
+    depth = np.full(us.size, np.nan)
+    idx = np.nonzero(cls == CLS_OBJECT)[0]
+    if depth_frac > 0 and idx.size:
+        pick = idx[rng.uniform(size=idx.size) < depth_frac]
+        depth[pick] = th[pick]
+    return dict(origin=np.ascontiguousarray(ow, np.float32), dir=np.ascontiguousarray(dw, np.float32),
+                rgb=np.ascontiguousarray(rgb, np.float32), depth=np.ascontiguousarray(depth, np.float32),
+                cls=np.ascontiguousarray(cls, np.uint8))

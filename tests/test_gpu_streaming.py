@@ -102,6 +102,7 @@ def test_budgeted_training_consumes_owed_steps():
         assert steps.value == 0
         R.check(R.romap_train_budget(ctx.h, arr, 3, 10.5 * per, 4, C.byref(steps), C.byref(ms), None))
         print(f"\nstep {per:.3f} ms; budget {10.5 * per:.3f} ms -> {steps.value} steps in {ms.value:.3f} ms")
-        assert 5 <= steps.value <= 10 and ms.value <= 1.5 * 10.5 * per
+        # about 10 full steps, then single-object steps fill what is left
+        assert 5 <= steps.value <= 14 and ms.value <= 1.5 * 10.5 * per
     finally:
         ctx.close()
