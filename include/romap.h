@@ -266,6 +266,15 @@ ROMAP_API romap_status romap_set_pending(romap_ctx* ctx, int32_t id, int64_t pen
 ROMAP_API romap_status romap_train_budget(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, float budget_ms,
                                           int32_t max_chunk, int32_t* out_steps, float* out_ms, float* out_loss);
 
+/* The marching-cubes case table the mesh extraction uses, built by
+ * construction at load time: for each of the 256 inside/outside patterns of
+ * a cube's corners (corner c at (c & 1, (c >> 1) & 1, (c >> 2) & 1); bit c
+ * set = density above the iso-level), counts[case] triangles listed in
+ * triangles[case * 16 ..] as triples of edge numbers (edge 4 d + q along
+ * axis d; q = the other two axes' corner bits, lower axis first), -1 after
+ * the last; triangles face from inside to outside.  Host-only. */
+ROMAP_API romap_status romap_mc_case_table(int8_t* triangles, uint8_t* counts);
+
 /* ---- inference --------------------------------------------------------- */
 /* Renders n rays (world frame unless ROMAP_OBJECT_FRAME) with midpoint
  * samples over bg (3 floats, host).  Outputs per ray (nullable each):

@@ -41,6 +41,9 @@
  *  R-14 Adam (Kingma & Ba) with bias correction, step counter from 1.
  *  R-17 Occupancy update (not in the paper): density at the 64^3 cell
  *       centres, d = max(decay d, sigma), bit = d > threshold.
+ *  R-19 Mesh extraction (Table 3, 64^3 marching cubes): 64^3 cubes over the
+ *       object box, densities at the 65^3 lattice vertices, one vertex per
+ *       lattice edge crossing the iso-level, linear interpolation.
  *  R-18 Data-update rule (Eq. 5): the angle between the object-to-camera
  *       vectors of the last used and the current image; update when it
  *       exceeds the threshold, and always for the first image.
@@ -834,4 +837,65 @@ int oc_should_update(int have_last, const double t_m[3], const double t_n[3], co
                      double threshold_deg) {
   if (!have_last) return 1;
   return oc_view_angle_deg(t_m, t_n, t_o) > threshold_deg;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh extraction (Table 3: marching cubes, 64^3).  The oracle        */
+/* computes what any correct triangulation shares: the lattice         */
+/* densities and one vertex per lattice edge whose ends lie on         */
+/* opposite sides of the iso-level, placed by linear interpolation.    */
+/* ------------------------------------------------------------------ */
+/* Lattice vertex (i, j, k), 0..64 per axis, FP32 in a fixed order:
+ * x_a = -a + i * ((a - (-a)) / 64). */
+void oc_lattice_vertex(const float half[3], int i, int j, int k, float x[3]) {
+  const int idx[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    float lo = -half[a];
+    float w = (half[a] - lo) / 64.0f;
+    x[a] = lo + (float)idx[a] * w;
+  }
+}
+
+/* Densities at the 65^3 lattice vertices, index i + 65 j + 65^2 k. */
+void oc_density_lattice(const oc_config* c, const double* params, const float half[3], double* sigma) {
+  for (int k = 0; k <= 64; ++k)
+    for (int j = 0; j <= 64; ++j)
+      for (int i = 0; i <= 64; ++i) {
+        float p[3];
+        oc_lattice_vertex(half, i, j, k, p);
+        sigma[i + 65 * j + 65 * 65 * k] = oc_density(c, params, p, half);
+      }
+}
+
+/* Edge-crossing vertices: for every lattice edge from vertex v along axis d
+ * (v and its neighbour inside the lattice) with (sigma_v > iso) !=
+ * (sigma_n > iso), in the order (vertex index, axis), writes the edge code
+ * 3 v + d and the position p_v + t (p_n - p_v), t = (iso - sigma_v) /
+ * (sigma_n - sigma_v), in FP64 from the FP32 lattice vertices.  Returns the
+ * number of crossings (codes/pos may be NULL to count only). */
+int64_t oc_mesh_vertices(const double* sigma, const float half[3], double iso, int64_t* codes, double* pos) {
+  int64_t n = 0;
+  for (int k = 0; k <= 64; ++k)
+    for (int j = 0; j <= 64; ++j)
+      for (int i = 0; i <= 64; ++i) {
+        const int64_t v = i + 65 * j + 65 * 65 * k;
+        const int ijk[3] = {i, j, k};
+        for (int d = 0; d < 3; ++d) {
+          if (ijk[d] == 64) continue;
+          int nb[3] = {i, j, k};
+          nb[d] += 1;
+          const int64_t u = nb[0] + 65 * nb[1] + 65 * 65 * nb[2];
+          if ((sigma[v] > iso) == (sigma[u] > iso)) continue;
+          if (codes) codes[n] = 3 * v + d;
+          if (pos) {
+            float pv[3], pu[3];
+            oc_lattice_vertex(half, i, j, k, pv);
+            oc_lattice_vertex(half, nb[0], nb[1], nb[2], pu);
+            const double t = (iso - sigma[v]) / (sigma[u] - sigma[v]);
+            for (int a = 0; a < 3; ++a) pos[3 * n + a] = (double)pv[a] + t * ((double)pu[a] - (double)pv[a]);
+          }
+          ++n;
+        }
+      }
+  return n;
 }

@@ -78,6 +78,9 @@ def lib():
             "oc_density_grid": (None, [vp, vp, vp, vp]),
             "oc_occupancy_update": (None, [i64, vp, d, d, vp, vp]),
             "oc_view_angle_deg": (d, [vp, vp, vp]),
+            "oc_lattice_vertex": (None, [vp, C.c_int, C.c_int, C.c_int, vp]),
+            "oc_density_lattice": (None, [vp, vp, vp, vp]),
+            "oc_mesh_vertices": (i64, [vp, vp, d, vp, vp]),
             "oc_should_update": (C.c_int, [C.c_int, vp, vp, vp, d]),
         }
         for name, (res, args) in sig.items():
@@ -388,3 +391,27 @@ def should_update(t_m, t_n, t_o, threshold_deg):
     if t_m is None:
         return bool(lib().oc_should_update(0, None, _p(_f64(t_n)), _p(_f64(t_o)), float(threshold_deg)))
     return bool(lib().oc_should_update(1, _p(_f64(t_m)), _p(_f64(t_n)), _p(_f64(t_o)), float(threshold_deg)))
+
+
+def lattice_vertex(half, i, j, k):
+    """Marching-cubes lattice vertex (i, j, k), 0..64 per axis, of the box [-half, half] (FP32, fixed order)."""
+    x = np.zeros(3, np.float32)
+    lib().oc_lattice_vertex(_p(_f32(half)), int(i), int(j), int(k), _p(x))
+    return x
+
+
+def density_lattice(cfg, params, half):
+    """sigma at the 65^3 lattice vertices, index i + 65 j + 65^2 k."""
+    out = np.zeros(65 ** 3, np.float64)
+    lib().oc_density_lattice(_cp(cfg), _p(_f64(params)), _p(_f32(half)), _p(out))
+    return out
+
+
+def mesh_vertices(sigma, half, iso):
+    """Edge-crossing vertices of the lattice densities: (edge codes 3 v + axis, positions [n, 3])."""
+    sigma = _f64(sigma)
+    n = int(lib().oc_mesh_vertices(_p(sigma), _p(_f32(half)), float(iso), None, None))
+    codes = np.zeros(n, np.int64)
+    pos = np.zeros((n, 3), np.float64)
+    lib().oc_mesh_vertices(_p(sigma), _p(_f32(half)), float(iso), _p(codes), _p(pos))
+    return codes, pos

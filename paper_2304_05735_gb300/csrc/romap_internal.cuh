@@ -225,6 +225,9 @@ void launch_split_outputs(const float* ray_out, int64_t n, float* rgb, float* de
                           cudaStream_t stream);
 int tile_kernel_smem_bytes(int LF);
 // Mixed precision: fused forward + compositing + backward on tensor cores; P slots per ray (power of two <= 128).
+// Marching cubes: at most kMcMaxTri triangles per cube; the case table is built by construction (mc_table.cu).
+constexpr int kMcMaxTri = 5;
+int build_mc_table(int8_t table[256][3 * kMcMaxTri + 1], uint8_t counts[256]);
 void launch_occ_update(const GridParams& g, const ObjectDev* objs, int slot, float decay, float threshold, int reset,
                        float* dens, uint64_t* bits, cudaStream_t stream);
 void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream);

@@ -129,3 +129,32 @@ def test_view_angle_closed_forms():
         assert O.should_update(o + 2.5 * v, o + 0.7 * w, o, 25.0) == (deg > 25.0)
     assert O.should_update(None, o + [1, 0, 0], o, 25.0)
     assert O.view_angle_deg(o, o + [1, 0, 0], o) == 180.0  # degenerate: a camera at the object centre
+
+
+def test_lattice_and_crossing_vertices_closed_forms():
+    """Lattice vertices in closed form (the unit box is dyadic: exact); with an affine density field the crossing
+    vertices lie exactly on the iso-plane and there is one per lattice edge the plane cuts."""
+    half = np.full(3, 0.5, np.float32)
+    assert np.array_equal(O.lattice_vertex(half, 0, 32, 64), np.array([-0.5, 0.0, 0.5], np.float32))
+    h2 = np.array([0.3, 0.45, 0.7], np.float32)
+    for i in (0, 1, 17, 63, 64):
+        x = O.lattice_vertex(h2, i, 64 - i, i)
+        exact = -h2.astype(np.float64) + np.array([i, 64 - i, i]) * (2 * h2.astype(np.float64) / 64)
+        assert np.all(np.abs(x - exact) <= 2 * np.spacing(h2))
+    # sigma = 2 + x + 2 y - z at the lattice vertices, iso 2.1: the plane x + 2y - z = 0.1
+    g = np.array([O.lattice_vertex(half, i, j, k) for k in range(65) for j in range(65) for i in range(65)],
+                 np.float64)
+    sigma = 2.0 + g[:, 0] + 2.0 * g[:, 1] - g[:, 2]
+    codes, pos = O.mesh_vertices(sigma, half, 2.1)
+    assert np.allclose(pos[:, 0] + 2 * pos[:, 1] - pos[:, 2], 0.1, atol=1e-12)
+    # brute force over all lattice edges
+    want = []
+    for v in range(65 ** 3):
+        i, j, k = v % 65, (v // 65) % 65, v // 65 ** 2
+        for d, (di, dj, dk) in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+            if (i, j, k)[d] == 64:
+                continue
+            u = (i + di) + 65 * (j + dj) + 65 ** 2 * (k + dk)
+            if (sigma[v] > 2.1) != (sigma[u] > 2.1):
+                want.append(3 * v + d)
+    assert np.array_equal(codes, np.array(want, np.int64))
