@@ -266,6 +266,25 @@ ROMAP_API romap_status romap_set_pending(romap_ctx* ctx, int32_t id, int64_t pen
 ROMAP_API romap_status romap_train_budget(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, float budget_ms,
                                           int32_t max_chunk, int32_t* out_steps, float* out_ms, float* out_loss);
 
+/* ---- mesh extraction (Table 3: marching cubes, 64^3) -------------------- */
+/* Densities of the object's density net (FP32 master parameters) at the
+ * 65^3 lattice vertices of its box, x_a = -a + i (2a / 64) (FP32), index
+ * i + 65 j + 65^2 k, into out (host, or device with ROMAP_DEVICE_PTR). */
+ROMAP_API romap_status romap_density_lattice(romap_ctx* ctx, int32_t id, float* out, uint32_t flags);
+/* Marching cubes (Lorensen & Cline 1987) over the 64^3 cubes of the
+ * object's box at density iso-level `iso`: one vertex (object frame, 3
+ * floats) per lattice edge whose end densities lie on opposite sides of
+ * iso, by linear interpolation, numbered in lattice-vertex order (x fastest)
+ * then axis; per cube the triangles of its case (romap_mc_case_table) as
+ * vertex-index triples, in cube order, facing from the dense side to the
+ * empty side.  The surface is closed except where it meets the box.  The
+ * counts go to *out_n_vertices / *out_n_triangles (nullable); if they exceed
+ * max_vertices / max_triangles nothing is written and ROMAP_ERR_CAPACITY is
+ * returned, so a caller can size its buffers and call again.  Outputs are
+ * host memory, or device memory with ROMAP_DEVICE_PTR. */
+ROMAP_API romap_status romap_extract_mesh(romap_ctx* ctx, int32_t id, float iso, float* vertices,
+                                          int64_t max_vertices, int32_t* triangles, int64_t max_triangles,
+                                          int64_t* out_n_vertices, int64_t* out_n_triangles, uint32_t flags);
 /* The marching-cubes case table the mesh extraction uses, built by
  * construction at load time: for each of the 256 inside/outside patterns of
  * a cube's corners (corner c at (c & 1, (c >> 1) & 1, (c >> 2) & 1); bit c

@@ -3,7 +3,7 @@
 // per-cell moving maximum d = max(decay d, sigma), and the cells with d > threshold form the new bitgrid that culls
 // samples (a culled sample has sigma := 0 and keeps its delta).  One thread per cell; cell index x + 64 y + 4096 z,
 // so each warp covers 32 consecutive x and its ballot is one 32-bit half of a bitgrid word.
-#include "device_common.cuh"
+#include "density_eval.cuh"
 
 namespace romap {
 namespace {
@@ -13,15 +13,9 @@ constexpr int kCells = 64 * 64 * 64;
 template <int LFP>
 __global__ void __launch_bounds__(256) k_occ_update(GridParams g, const ObjectDev* objs, int slot, float decay,
                                                    float threshold, int reset, float* dens, uint32_t* bits) {
-  __shared__ float w1[kH * LFP];  // first layer [64][LF]
-  __shared__ float w2[kH];        // row 0 of the second layer (log-density)
+  __shared__ DensityWeights<LFP> sw;
   const ObjectDev& ob = objs[slot];
-  const float* P = ob.params;
-  for (int i = threadIdx.x; i < kH * LFP; i += blockDim.x) {  // columns past LF are zero
-    const int j = i / LFP, k = i % LFP;
-    w1[i] = k < g.LF ? P[g.mlp_off[0] + j * g.LF + k] : 0.f;
-  }
-  if (threadIdx.x < kH) w2[threadIdx.x] = P[g.mlp_off[1] + threadIdx.x];
+  load_density_weights<LFP>(sw, g, ob.params);
   __syncthreads();
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers exactly kCells
   const int idx[3] = {cell & 63, (cell >> 6) & 63, cell >> 12};
@@ -32,34 +26,7 @@ __global__ void __launch_bounds__(256) k_occ_update(GridParams g, const ObjectDe
     const float w = __fdiv_rn(__fsub_rn(ob.half[a], lo), 64.0f);
     x[a] = __fadd_rn(lo, __fmul_rn(__fadd_rn((float)idx[a], 0.5f), w));
   }
-  float e[LFP];
-#pragma unroll
-  for (int k = 0; k < LFP; ++k) e[k] = 0.f;
-  const float2* tab = reinterpret_cast<const float2*>(P);
-#pragma unroll
-  for (int l = 0; l < LFP / 2; ++l) {
-    if (l >= g.L) break;
-    Corners c;
-    level_corners(g, l, x, ob.half, ob.inv_ext, c);
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float2 v = tab[g.off[l] + c.idx[k]];
-      a0 = fmaf(c.w[k], v.x, a0);
-      a1 = fmaf(c.w[k], v.y, a1);
-    }
-    e[2 * l] = a0;
-    e[2 * l + 1] = a1;
-  }
-  float o0 = 0.f;
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float h = 0.f;
-#pragma unroll
-    for (int k = 0; k < LFP; ++k) h = fmaf(w1[j * LFP + k], e[k], h);
-    o0 = fmaf(w2[j], fmaxf(h, 0.f), o0);
-  }
-  const float sigma = expf(fminf(fmaxf(o0, -15.f), 15.f));
+  const float sigma = density_at<LFP>(sw, g, ob, x);
   const float d = reset ? sigma : fmaxf(decay * dens[cell], sigma);
   dens[cell] = d;
   const unsigned m = __ballot_sync(0xffffffffu, d > threshold);

@@ -96,7 +96,7 @@ struct romap_ctx {
   ObjectDev* objs_dev = nullptr;
   ObjectDev* fn_obj_dev = nullptr;   // object record of functional calls
   // step workspace
-  DevBuf ws_rays, ws_samples, ws_blocks, ws_batch, ws_dyn, ws_stage, ws_plan;
+  DevBuf ws_rays, ws_samples, ws_blocks, ws_batch, ws_dyn, ws_stage, ws_plan, ws_mesh, ws_mesh_out;
   int64_t cap_rays = 0, cap_samples = 0, cap_blocks = 0, cap_batch = 0;
   // tile plan of the mixed-precision path (capacities: rays, ray blocks, batch entries, tiles)
   int64_t cap_plan[4] = {0, 0, 0, 0};
@@ -889,6 +889,86 @@ romap_status romap_get_occupancy(romap_ctx* ctx, int32_t id, uint64_t* bits, flo
     CUDA_TRY(cudaMemcpyAsync(density, o.occ_density, sizeof(float) * 64 * 64 * 64, cudaMemcpyDeviceToHost,
                              ctx->stream));
   CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+// ---- mesh extraction (Table 3: marching cubes, 64^3) ----------------------------------------------------------------
+namespace {
+int8_t g_mc_tri[256][3 * kMcMaxTri + 1];
+uint8_t g_mc_cnt[256];
+std::once_flag g_mc_once;
+int g_mc_built = -1;
+
+romap_status mesh_workspace(romap_ctx* ctx, char** ws, uint32_t** totals) {
+  std::call_once(g_mc_once, [] { g_mc_built = build_mc_table(g_mc_tri, g_mc_cnt); });
+  if (g_mc_built < 0) return fail(ROMAP_ERR_BAD_STATE, "marching-cubes table construction failed");
+  const size_t bytes = mc_workspace_bytes();
+  if (ctx->ws_mesh.bytes < bytes) ROMAP_TRY(grow(ctx, ctx->ws_mesh, bytes));
+  *ws = (char*)ctx->ws_mesh.p;
+  *totals = (uint32_t*)((char*)ctx->ws_mesh.p + bytes - 8 * 256);
+  return ROMAP_OK;
+}
+}  // namespace
+
+romap_status romap_density_lattice(romap_ctx* ctx, int32_t id, float* out, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!out) return fail(ROMAP_ERR_INVALID_ARG, "out is required");
+  if (flags & ~ROMAP_DEVICE_PTR) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  char* ws;
+  uint32_t* totals;
+  ROMAP_TRY(mesh_workspace(ctx, &ws, &totals));
+  launch_lattice_density(ctx->g, ctx->objs_dev, id, (float*)ws, ctx->stream);
+  ctx->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(out, ws, sizeof(float) * mc_lattice_points(),
+                           (flags & ROMAP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  if (!(flags & ROMAP_DEVICE_PTR)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return ROMAP_OK;
+}
+
+romap_status romap_extract_mesh(romap_ctx* ctx, int32_t id, float iso, float* vertices, int64_t max_vertices,
+                                int32_t* triangles, int64_t max_triangles, int64_t* out_n_vertices,
+                                int64_t* out_n_triangles, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (!std::isfinite(iso)) return fail(ROMAP_ERR_INVALID_ARG, "iso must be finite");
+  if (max_vertices < 0 || max_triangles < 0) return fail(ROMAP_ERR_INVALID_ARG, "negative capacity");
+  if ((max_vertices > 0 && !vertices) || (max_triangles > 0 && !triangles))
+    return fail(ROMAP_ERR_INVALID_ARG, "NULL output with a non-zero capacity");
+  if (flags & ~ROMAP_DEVICE_PTR) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  char* ws;
+  uint32_t* totals;
+  ROMAP_TRY(mesh_workspace(ctx, &ws, &totals));
+  ctx->launches += launch_mc(ctx->g, ctx->objs_dev, id, iso, ws, 0, 0, nullptr, 0, nullptr, totals, &g_mc_tri[0][0],
+                             g_mc_cnt, ctx->stream);
+  CUDA_TRY(cudaGetLastError());
+  uint32_t nvt[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(nvt, totals, sizeof(nvt), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (out_n_vertices) *out_n_vertices = nvt[0];
+  if (out_n_triangles) *out_n_triangles = nvt[1];
+  if ((int64_t)nvt[0] > max_vertices || (int64_t)nvt[1] > max_triangles)
+    return fail(ROMAP_ERR_CAPACITY, "mesh has %u vertices and %u triangles", nvt[0], nvt[1]);
+  if (nvt[0] == 0) return ROMAP_OK;
+  const bool dev = flags & ROMAP_DEVICE_PTR;
+  float* v = vertices;
+  int32_t* t = triangles;
+  if (!dev) {
+    const size_t bytes = 12 * (size_t)nvt[0] + 12 * (size_t)nvt[1] + 256;
+    if (ctx->ws_mesh_out.bytes < bytes) ROMAP_TRY(grow(ctx, ctx->ws_mesh_out, bytes));
+    v = (float*)ctx->ws_mesh_out.p;
+    t = (int32_t*)((char*)ctx->ws_mesh_out.p + ((12 * (size_t)nvt[0] + 255) / 256) * 256);
+  }
+  ctx->launches += launch_mc(ctx->g, ctx->objs_dev, id, iso, ws, 1, nvt[0], v, nvt[1], t, totals, nullptr, nullptr,
+                             ctx->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (!dev) {
+    CUDA_TRY(cudaMemcpyAsync(vertices, v, 12 * (size_t)nvt[0], cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(triangles, t, 12 * (size_t)nvt[1], cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
   return ROMAP_OK;
 }
 

@@ -228,6 +228,12 @@ int tile_kernel_smem_bytes(int LF);
 // Marching cubes: at most kMcMaxTri triangles per cube; the case table is built by construction (mc_table.cu).
 constexpr int kMcMaxTri = 5;
 int build_mc_table(int8_t table[256][3 * kMcMaxTri + 1], uint8_t counts[256]);
+size_t mc_workspace_bytes();
+int mc_lattice_points();
+void launch_lattice_density(const GridParams& g, const ObjectDev* objs, int slot, float* dens, cudaStream_t stream);
+int launch_mc(const GridParams& g, const ObjectDev* objs, int slot, float iso, char* ws, int emit, int64_t cap_v,
+              float* verts, int64_t cap_t, int32_t* tris, uint32_t* totals_out, const int8_t* table,
+              const uint8_t* counts, cudaStream_t stream);
 void launch_occ_update(const GridParams& g, const ObjectDev* objs, int slot, float decay, float threshold, int reset,
                        float* dens, uint64_t* bits, cudaStream_t stream);
 void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream);

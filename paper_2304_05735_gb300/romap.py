@@ -91,6 +91,8 @@ SIGNATURES = {
     "romap_pending": (_i32, [_vp, _i32, _P(_i64)]),
     "romap_set_pending": (_i32, [_vp, _i32, _i64]),
     "romap_train_budget": (_i32, [_vp, _vp, _i32, C.c_float, _i32, _P(_i32), _P(C.c_float), _vp]),
+    "romap_density_lattice": (_i32, [_vp, _i32, _vp, _u32]),
+    "romap_extract_mesh": (_i32, [_vp, _i32, C.c_float, _vp, _i64, _vp, _i64, _P(_i64), _P(_i64), _u32]),
     "romap_mc_case_table": (_i32, [_vp, _vp]),
     "romap_update_occupancy": (_i32, [_vp, _i32, C.c_float, C.c_float, _u32]),
     "romap_get_occupancy": (_i32, [_vp, _i32, _vp, _vp]),
