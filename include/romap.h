@@ -103,6 +103,9 @@ typedef struct romap_config {
   int32_t precision;       /* ROMAP_PREC_* */
   int32_t max_objects;     /* capacity of live objects */
   int64_t max_rays_per_object; /* ray-pool capacity of one object */
+  int32_t accuracy_mode;   /* 1: the FP32 path accumulates the transmittance log-sum (the prefix of
+                              sigma * delta) and the compositing weights in FP64 (Eq. 6) */
+  int32_t reserved;        /* 0 */
   /* Optional device allocator (both or neither).  alloc returns NULL on
    * failure, which the library reports as ROMAP_ERR_OOM; a pointer that is
    * not 256-byte aligned is handed back to dealloc and reported as

@@ -53,7 +53,52 @@ __global__ void __launch_bounds__(256) k_composite(GridParams g, BatchDesc b, Ra
 
   // ---- forward: Eq. 6 -----------------------------------------------------
   float carry = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dh = 0.f, ssum = 0.f;
-  for (uint32_t base = 0; base < cnt; base += 32) {
+  if (g.accuracy) {  // the log-sum of transmittance, the weights and their sums in FP64
+    double carry_d = 0.0, C0d = 0.0, C1d = 0.0, C2d = 0.0, Dhd = 0.0;
+    for (uint32_t base = 0; base < cnt; base += 32) {
+      const uint32_t j = base + lane;
+      const bool in = j < cnt;
+      const float sg = in ? S.sigma[off + j] : 0.f;
+      const double sd = (double)sg * (double)(in ? S.dt[off + j] : 0.f);
+      double incl = sd;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+      }
+      double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+      if (lane == 0) excl = 0.0;
+      const double P = carry_d + excl;
+      const double w = exp(-P) * (-expm1(-sd));
+      if (in) {
+        C0d += w * (double)S.rgb[3 * (off + j)];
+        C1d += w * (double)S.rgb[3 * (off + j) + 1];
+        C2d += w * (double)S.rgb[3 * (off + j) + 2];
+        Dhd += w * (double)S.t[off + j];
+        ssum += sg;
+        if (MODE != 0) S.dsigma[off + j] = (float)P;
+      }
+      carry_d += __shfl_sync(0xffffffffu, incl, 31);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      C0d += __shfl_xor_sync(0xffffffffu, C0d, o);
+      C1d += __shfl_xor_sync(0xffffffffu, C1d, o);
+      C2d += __shfl_xor_sync(0xffffffffu, C2d, o);
+      Dhd += __shfl_xor_sync(0xffffffffu, Dhd, o);
+    }
+    ssum = warp_sum(ssum);
+    const double Tend_d = exp(-carry_d);
+    carry = (float)carry_d;
+    const float Ch0 = (float)(Tend_d * bg0 + C0d), Ch1 = (float)(Tend_d * bg1 + C1d);
+    const float Ch2 = (float)(Tend_d * bg2 + C2d);
+    C0 = Ch0; C1 = Ch1; C2 = Ch2; Dh = (float)Dhd;
+    if (lane == 0) {
+      float* o = R.out + 6 * r;
+      o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = (float)(-expm1(-carry_d)); o[5] = ssum;
+    }
+  }
+  for (uint32_t base = 0; base < cnt && !g.accuracy; base += 32) {
     const uint32_t j = base + lane;
     const bool in = j < cnt;
     const float sg = in ? S.sigma[off + j] : 0.f;
@@ -75,13 +120,18 @@ __global__ void __launch_bounds__(256) k_composite(GridParams g, BatchDesc b, Ra
     }
     carry += __shfl_sync(0xffffffffu, incl, 31);
   }
-  C0 = warp_sum(C0); C1 = warp_sum(C1); C2 = warp_sum(C2); Dh = warp_sum(Dh); ssum = warp_sum(ssum);
   const float Tend = expf(-carry);
-  const float A = -expm1f(-carry);
-  const float Ch0 = fmaf(Tend, bg0, C0), Ch1 = fmaf(Tend, bg1, C1), Ch2 = fmaf(Tend, bg2, C2);
-  if (lane == 0) {
-    float* o = R.out + 6 * r;
-    o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = A; o[5] = ssum;
+  float Ch0, Ch1, Ch2;
+  if (g.accuracy) {  // rendered above
+    Ch0 = C0; Ch1 = C1; Ch2 = C2;
+  } else {
+    C0 = warp_sum(C0); C1 = warp_sum(C1); C2 = warp_sum(C2); Dh = warp_sum(Dh); ssum = warp_sum(ssum);
+    const float A = -expm1f(-carry);
+    Ch0 = fmaf(Tend, bg0, C0); Ch1 = fmaf(Tend, bg1, C1); Ch2 = fmaf(Tend, bg2, C2);
+    if (lane == 0) {
+      float* o = R.out + 6 * r;
+      o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = A; o[5] = ssum;
+    }
   }
   if (MODE == 0) return;
 

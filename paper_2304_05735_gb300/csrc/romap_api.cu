@@ -421,6 +421,8 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
     return fail(ROMAP_ERR_INVALID_ARG, "invalid Adam hyperparameters");
   if (c->precision != ROMAP_PREC_FP32 && c->precision != ROMAP_PREC_MIXED_BF16)
     return fail(ROMAP_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+  if (c->accuracy_mode != 0 && c->accuracy_mode != 1) return fail(ROMAP_ERR_INVALID_ARG, "accuracy_mode is 0 or 1");
+  if (c->reserved != 0) return fail(ROMAP_ERR_INVALID_ARG, "reserved must be 0");
   if (c->max_objects < 1 || c->max_objects > 1024) return fail(ROMAP_ERR_INVALID_ARG, "max_objects must be in 1..1024");
   if (c->max_rays_per_object < 1 || c->max_rays_per_object > (int64_t)1 << 31)
     return fail(ROMAP_ERR_INVALID_ARG, "max_rays_per_object must be in 1..2^31");
@@ -468,6 +470,7 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   G.eps = c->eps;
   G.bg_random = c->bg_random ? 1 : 0;
   for (int k = 0; k < 3; ++k) G.bg_const[k] = c->bg_const[k];
+  G.accuracy = c->accuracy_mode ? 1 : 0;
   *g = G;
   return ROMAP_OK;
 }

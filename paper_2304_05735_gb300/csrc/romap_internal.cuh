@@ -51,6 +51,7 @@ struct GridParams {
   float lr, beta1, beta2, eps;
   int bg_random;
   float bg_const[3];
+  int accuracy;            // FP64 transmittance log-sum and weights in the FP32 compositing kernel
 };
 
 // One live object as the kernels see it (device-resident, indexed by slot).

@@ -426,3 +426,34 @@ def test_nonfinite_device_rays_reported_through_status_word(torch, precision):
         assert np.isfinite(ctx.train([oid])).all()
     finally:
         ctx.close()
+
+
+def test_accuracy_mode_tightens_long_ray_renders(torch):
+    """With the FP64 transmittance log-sum (accuracy_mode), 1024-sample renders of dense rays come closer to the FP64
+    oracle than the FP32 scan does; both stay within the forward tolerance."""
+    errs = {}
+    n, N = 256, 1024
+    rng = np.random.default_rng(77)
+    o, d = _rays_at_box(n, rng)
+    bg = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    half = np.array([0.5, 0.5, 0.5], np.float32)
+    for acc in (0, 1):
+        oc, rc = paired_config(L=4, T=2 ** 10, growth=2.0, n_samples=N)
+        rc.accuracy_mode = acc
+        p64 = O.init_params(oc, 12)
+        nh = O.hash_param_count(oc)
+        p64[:nh] = np.random.default_rng(5).uniform(-3, 3, nh)  # dense regions: long transmittance sums
+        p32 = p64.astype(np.float32)
+        ref = O.rays_loss_grad(oc, p32.astype(np.float64), half, 31, 9, o, d, bg=bg.astype(np.float64),
+                               upstream=np.zeros((n, 6)), inv_B=1.0, want_grad=False)["ray"]
+        ctx = Ctx(rc)
+        try:
+            to = lambda a: torch.tensor(a, device="cuda")
+            out, _, _ = ctx.fn_forward(to(p32), half, 31, 9, to(o), to(d), to(bg))
+            got = out.cpu().numpy().astype(np.float64)
+        finally:
+            ctx.close()
+        errs[acc] = np.abs(got[:, :5] - ref[:, :5]).max()
+        assert np.allclose(got[:, :5], ref[:, :5], rtol=FWD_RTOL, atol=FWD_ATOL)
+    print(f"\n1024-sample renders, max abs error vs FP64: FP32 scan {errs[0]:.2e}, FP64 log-sum {errs[1]:.2e}")
+    assert errs[1] <= errs[0]
