@@ -70,6 +70,10 @@ typedef int32_t romap_status;
 /* precision of the training step */
 #define ROMAP_PREC_FP32 0       /* FP32 tables, FP32 SIMT MLP */
 #define ROMAP_PREC_MIXED_BF16 1 /* FP16 table copy + FP32 masters, BF16 tensor-core MLP, FP32 accumulation */
+#define ROMAP_PREC_MIXED_FP8 2  /* as MIXED_BF16, with the forward GEMM of the hidden 64x64 layer (colour net,
+                                   second layer) in FP8 E4M3: each output row of the layer's weights scaled by
+                                   448 / its max |W|, each sample's input activations by 448 / their max, FP32
+                                   accumulation, dequantised before the ReLU; the backward stays BF16 */
 
 typedef struct romap_ctx romap_ctx;
 

@@ -63,7 +63,7 @@ struct TileBufs {
   int P, nrays; // slots per ray and rays of the tile
 };
 
-template <int LFP>
+template <int LFP, bool FP8>
 struct TcSmem {
   // weights (B operands of the forward), K-major BF16 [out][in]
   __align__(128) unsigned char w1[kH * LFP * 2];
@@ -72,10 +72,70 @@ struct TcSmem {
   __align__(128) unsigned char w4[kH * kH * 2];
   __align__(128) unsigned char w5[16 * kH * 2];
   TileBufs<LFP> tb[kTilesPerCta];
+  // FP8 E4M3 operands of the hidden 64x64 forward GEMM (ROMAP_PREC_MIXED_FP8): K-major W4 and each tile's H2 rows
+  __align__(128) unsigned char w4q[FP8 ? kH * kH : 16];
+  __align__(128) unsigned char h2q[kTilesPerCta][FP8 ? kT * kH : 16];
+  float w4_inv[kH];                    // 1 / (448 / max |W4 row n|) for each output n of the loaded object
   __align__(8) uint64_t mbar;
   uint32_t tmem_base;
   int fail;
 };
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ uint32_t fp8x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
+}
+
+// The FP8 copy of W4, each output row n scaled by 448 / max |W4[n][.]| (4 consecutive threads per row; needs
+// nthreads >= 4 kH and a barrier before the MMA reads it).
+template <class Smem>
+__device__ void load_w4_fp8(Smem& sm, const GridParams& g, const float* __restrict__ P, int t, int nthreads) {
+  const float* W = P + g.mlp_off[3];
+  for (int base = 0; base < 4 * kH; base += nthreads) {
+    const int i = base + t;  // row i / 4, columns 16 (i % 4) .. + 15
+    const int n = i >> 2, q = i & 3;
+    float v[16];
+    float m = 0.f;
+    if (n < kH) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        v[j] = W[n * kH + 16 * q + j];
+        m = fmaxf(m, fabsf(v[j]));
+      }
+    }
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    if (n < kH) {
+      const float sc = m > 0.f ? 448.f / m : 1.f;
+      uint4 w;
+      w.x = fp8x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc);
+      w.y = fp8x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc);
+      w.z = fp8x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc);
+      w.w = fp8x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc);
+      *reinterpret_cast<uint4*>(sm.w4q + kmaj8(n, 16 * q, kH)) = w;
+      if (q == 0) sm.w4_inv[n] = 1.f / sc;
+    }
+  }
+}
+
+// relu(row_scale * col_scale[j] * TMEM row) -> BF16 row (the dequantising epilogue of the FP8 GEMM)
+__device__ __forceinline__ void epi_relu64_scaled(uint32_t taddr, unsigned char* buf, int row, float row_scale,
+                                                  const float* col_scale) {
+  float v[64];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j] * row_scale * col_scale[j], 0.f);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c);
+}
 
 // relu(TMEM row) -> BF16 row of an activation buffer (64 columns); the four TMEM loads share one wait
 __device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, int row) {
@@ -104,11 +164,11 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
   }
 }
 
-template <int LFP>
+template <int LFP, bool FP8>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TcSmem<LFP>& sm = *reinterpret_cast<TcSmem<LFP>*>(smem_raw);
+  TcSmem<LFP, FP8>& sm = *reinterpret_cast<TcSmem<LFP, FP8>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int wg = t >> 7;          // tile of the pair
   const int s = t & (kT - 1);     // slot within the tile = TMEM lane
@@ -189,6 +249,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       bi = nx_bi;
       ob = nx_ob;
       load_weights<LFP>(sm, g, ob->params, kTcThreads);
+      if (FP8) load_w4_fp8(sm, g, ob->params, t, kTcThreads);
       acc_dw = 0;
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
@@ -250,16 +311,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (!(ok = wait_mma())) break;
     epi_relu64(tmp, tb.H2, s);
+    float h2_scale = 1.f;  // FP8: 448 / max of this sample's H2 row (1 when all zero)
+    if (FP8) {  // this sample's H2 row in E4M3; the row scale factors out of its GEMM outputs
+      float hv[64];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) load8(tb.H2, s, c, kH, hv + 8 * c);
+      float m = 0.f;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) m = fmaxf(m, hv[j]);
+      const float sc = m > 0.f ? 448.f / m : 1.f;
+      h2_scale = sc;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {  // 16 consecutive k of row s are one 16-byte core-matrix row
+        const float* h = hv + 16 * c;
+        uint4 q;
+        q.x = fp8x4(h[0] * sc, h[1] * sc, h[2] * sc, h[3] * sc);
+        q.y = fp8x4(h[4] * sc, h[5] * sc, h[6] * sc, h[7] * sc);
+        q.z = fp8x4(h[8] * sc, h[9] * sc, h[10] * sc, h[11] * sc);
+        q.w = fp8x4(h[12] * sc, h[13] * sc, h[14] * sc, h[15] * sc);
+        *reinterpret_cast<uint4*>(sm.h2q[wg] + kmaj8(s, 16 * c, kH)) = q;
+      }
+    }
     sync_then_issue();
     if (t == 0) {  // L4: H2 W4^T
-      for (int u = 0; u < kTilesPerCta; ++u)
+      for (int u = 0; u < kTilesPerCta; ++u) {
+        if (FP8) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+          for (int kk = 0; kk < 2; ++kk)
+            mma8(tmp_d(u), desc_k8(sm.h2q[u], kH, kk), desc_k8(sm.w4q, kH, kk), idesc8(64), kk > 0);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+        }
+      }
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    epi_relu64(tmp, tb.H3, s);
+    if (FP8) epi_relu64_scaled(tmp, tb.H3, s, 1.0f / h2_scale, sm.w4_inv);
+    else epi_relu64(tmp, tb.H3, s);
     sync_then_issue();
     if (t == 0) {  // L5: H3 W5^T (3 of 16 outputs)
       for (int u = 0; u < kTilesPerCta; ++u)
@@ -463,23 +553,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(kTmemCols));
 }
 
-template <int LFP>
+template <int LFP, bool FP8>
 void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                  int max_tiles, int n_ctas, cudaStream_t stream) {
   // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
   // CTA never waits on another
-  int bytes = (int)sizeof(TcSmem<LFP>);
+  int bytes = (int)sizeof(TcSmem<LFP, FP8>);
   if (bytes < 116 * 1024) bytes = 116 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_tc<LFP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_tile_tc<LFP, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr_set = true;
   }
   // the plan's pair count is read on the device; max_tiles only bounds the grid
   const int max_pairs = (max_tiles + kTilesPerCta - 1) / kTilesPerCta;
   int grid = n_ctas < max_pairs ? n_ctas : max_pairs;
   if (grid < 1) return;
-  k_tile_tc<LFP><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status);
+  k_tile_tc<LFP, FP8><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status);
 }
 
 // Places every ray of the batch in the tile plan: rays with live samples go to their class's position in
@@ -522,8 +612,13 @@ __global__ void __launch_bounds__(256) k_plan_rays(GridParams g, BatchDesc b, Ra
 
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int max_tiles, int n_ctas, cudaStream_t stream) {
-  if (g.LF <= 16) launch_tc_t<16>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
-  else launch_tc_t<32>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+  if (g.fp8) {
+    if (g.LF <= 16) launch_tc_t<16, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    else launch_tc_t<32, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+  } else {
+    if (g.LF <= 16) launch_tc_t<16, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    else launch_tc_t<32, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+  }
 }
 
 void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream) {

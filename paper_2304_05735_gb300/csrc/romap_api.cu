@@ -419,7 +419,7 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   if (!(c->lr > 0.f) || !(c->beta1 >= 0.f && c->beta1 < 1.f) || !(c->beta2 >= 0.f && c->beta2 < 1.f) ||
       !(c->eps >= 0.f))
     return fail(ROMAP_ERR_INVALID_ARG, "invalid Adam hyperparameters");
-  if (c->precision != ROMAP_PREC_FP32 && c->precision != ROMAP_PREC_MIXED_BF16)
+  if (c->precision != ROMAP_PREC_FP32 && c->precision != ROMAP_PREC_MIXED_BF16 && c->precision != ROMAP_PREC_MIXED_FP8)
     return fail(ROMAP_ERR_INVALID_ARG, "unknown precision %d", c->precision);
   if (c->accuracy_mode != 0 && c->accuracy_mode != 1) return fail(ROMAP_ERR_INVALID_ARG, "accuracy_mode is 0 or 1");
   if (c->reserved != 0) return fail(ROMAP_ERR_INVALID_ARG, "reserved must be 0");
@@ -471,6 +471,7 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   G.bg_random = c->bg_random ? 1 : 0;
   for (int k = 0; k < 3; ++k) G.bg_const[k] = c->bg_const[k];
   G.accuracy = c->accuracy_mode ? 1 : 0;
+  G.fp8 = c->precision == ROMAP_PREC_MIXED_FP8 ? 1 : 0;
   *g = G;
   return ROMAP_OK;
 }
@@ -560,6 +561,10 @@ romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& id
   CUDA_TRY(cudaEventCreate(&e1));
   int best = 0;
   for (int k = 0; k < kNumTileKernels; ++k) {
+    if (ctx->g.fp8 && k != 0) {  // only the lockstep kernel has the FP8 hidden layer
+      ctx->tile_kernel_ms[k] = 0.f;
+      continue;
+    }
     kTileKernels[k](ctx->g, b, ctx->dyn, ctx->R, ctx->status, max_tiles, tile_ctas(ctx), ctx->stream);  // warm
     CUDA_TRY(cudaEventRecord(e0, ctx->stream));
     for (int rep = 0; rep < 2; ++rep)
@@ -569,7 +574,7 @@ romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& id
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
     ctx->tile_kernel_ms[k] = ms / 2.f;
-    if (ctx->tile_kernel_ms[k] < ctx->tile_kernel_ms[best]) best = k;
+    if (ctx->tile_kernel_ms[k] < ctx->tile_kernel_ms[best] || ctx->tile_kernel_ms[best] <= 0.f) best = k;
     ctx->launches += 3;
   }
   cudaEventDestroy(e0);
@@ -589,7 +594,7 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
     rays[i] = ctx->objs_host[ids[i]].n_rays;
     if (rays[i] < 1) return fail(ROMAP_ERR_BAD_STATE, "object %d has no training rays", ids[i]);
   }
-  const bool mixed = ctx->cfg.precision == ROMAP_PREC_MIXED_BF16;
+  const bool mixed = ctx->cfg.precision != ROMAP_PREC_FP32;
   HostBatch hb;
   build_batch(slots, rays, &hb);
   int64_t ns = mixed ? 0 : (int64_t)hb.n_rays * ctx->g.n_samples + (int64_t)hb.n * kTile;
@@ -726,7 +731,7 @@ romap_status romap_init(const romap_config* cfg, void* cuda_stream, romap_ctx** 
   *out = nullptr;
   GridParams g;
   ROMAP_TRY(make_grid(cfg, &g));
-  if (cfg->precision == ROMAP_PREC_MIXED_BF16 && cfg->n_samples > kTile)
+  if (cfg->precision != ROMAP_PREC_FP32 && cfg->n_samples > kTile)
     return fail(ROMAP_ERR_UNSUPPORTED, "mixed precision needs n_samples <= %d", kTile);
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -810,7 +815,7 @@ romap_status romap_create_object(romap_ctx* ctx, const romap_object_desc* d, int
   if (s == ROMAP_OK) s = dev_alloc_t(ctx, np, &o.grad);
   if (s == ROMAP_OK) s = dev_alloc_t(ctx, np, &o.m);
   if (s == ROMAP_OK) s = dev_alloc_t(ctx, np, &o.v);
-  if (s == ROMAP_OK && ctx->cfg.precision == ROMAP_PREC_MIXED_BF16)
+  if (s == ROMAP_OK && ctx->cfg.precision != ROMAP_PREC_FP32)
     s = dev_alloc_t(ctx, (size_t)ctx->g.n_hash + 8, &o.table_h);
   if (s != ROMAP_OK) {
     o.alive = true;
@@ -1093,7 +1098,7 @@ romap_status romap_adam_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids) 
   ROMAP_TRY(upload_batch(ctx, hb, &b));
   {
     PhaseScope ps(ctx, 4, 2);
-    launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+    launch_adam(ctx->g, b, ctx->cfg.precision != ROMAP_PREC_FP32, ctx->stream);
   }
   ctx->launches += 2;
   CUDA_TRY(cudaGetLastError());
@@ -1110,7 +1115,7 @@ static romap_status enqueue_step(romap_ctx* ctx, const std::vector<int32_t>& v) 
   ROMAP_TRY(run_fwd_bwd(ctx, v, &b));
   {
     PhaseScope ps(ctx, 4, 2);
-    launch_adam(ctx->g, b, ctx->cfg.precision == ROMAP_PREC_MIXED_BF16, ctx->stream);
+    launch_adam(ctx->g, b, ctx->cfg.precision != ROMAP_PREC_FP32, ctx->stream);
   }
   ctx->launches += 2;
   CUDA_TRY(cudaGetLastError());
@@ -1197,7 +1202,7 @@ romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids,
       }
       ctx->stats.steps += (int64_t)v.size();
       ctx->stats.rays += rays;
-      ctx->launches += ctx->cfg.precision == ROMAP_PREC_MIXED_BF16 ? 6 : 8;
+      ctx->launches += ctx->cfg.precision != ROMAP_PREC_FP32 ? 6 : 8;
       continue;
     }
     ROMAP_TRY(enqueue_step(ctx, v));
@@ -1492,6 +1497,7 @@ romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_limit) {
 romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index) {
   ROMAP_TRY(check_ctx(ctx));
   if (index < -1 || index >= kNumTileKernels) return fail(ROMAP_ERR_INVALID_ARG, "tile kernel %d out of range", index);
+  if (ctx->g.fp8 && index > 0) return fail(ROMAP_ERR_UNSUPPORTED, "the FP8 precision runs on tile kernel 0 only");
   ctx->tile_kernel = index;
   drop_graph(ctx);
   return ROMAP_OK;

@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "device_common.cuh"
 #include "romap_internal.cuh"
@@ -41,6 +42,23 @@ __host__ __device__ constexpr uint32_t idesc(int N, int a_mn, int b_mn) {
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
   asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+// 8-bit operands (kind::f8f6f4, E4M3): core matrix = 8 rows x 16 elements; a K-major [rows][K] buffer holds element
+// (r, k) at byte (r/8)(K/16)128 + (k/16)128 + (r%8)16 + (k%16); one MMA covers K = 32 (two 16-element groups)
+__device__ __forceinline__ uint32_t kmaj8(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K >> 4) * 128 + (k >> 4) * 128 + (r & 7) * 16 + (k & 15));
+}
+__device__ __forceinline__ uint64_t desc_k8(const void* buf, int K, int kk) {
+  return make_desc(smem_u32(buf) + (uint32_t)kk * 256u, 128u, (uint32_t)(K / 16) * 128u);
+}
+// instruction descriptor, kind::f8f6f4: E4M3 A and B (format 0), FP32 D, K-major operands
+__host__ __device__ constexpr uint32_t idesc8(int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+}
+__device__ __forceinline__ void mma8(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
                :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {

@@ -30,15 +30,15 @@ def _cos(a, b):
     return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel,prec", [(0, MIXED), (1, MIXED), (0, R.ROMAP_PREC_MIXED_FP8)])
 @pytest.mark.parametrize("scene", ["plain", "masked"])
-def test_mixed_step_vs_oracle(torch, scene, kernel):
+def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
     if scene == "plain":
-        oc, rc = paired_config(precision=MIXED)
+        oc, rc = paired_config(precision=prec)
         sc = synth.config0_scene()
     else:
         oc, rc = paired_config(L=16, T=2 ** 16, growth=0.0, n_max=512, n_samples=64, rays_per_step=2048,
-                               bg_random=True, precision=MIXED)
+                               bg_random=True, precision=prec)
         sc = synth.multi_object_scene(1, seed0=5, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2, occluder_prob=1.0)[0]
     ctx = Ctx(rc)
     try:
@@ -53,7 +53,8 @@ def test_mixed_step_vs_oracle(torch, scene, kernel):
         nh = O.hash_param_count(oc)
         rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
         rel_h, rel_m = _rel(g[:nh], ref["grad"][:nh]), _rel(g[nh:], ref["grad"][nh:])
-        print(f"\n[{scene}, kernel {kernel}] mixed vs oracle: loss rel {rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
+        print(f"\n[{scene}, kernel {kernel}, {'fp8' if prec != MIXED else 'bf16'}] mixed vs oracle: loss rel "
+              f"{rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
               f"(cos {_cos(g[:nh], ref['grad'][:nh]):.6f}), mlp-grad rel L2 {rel_m:.2e}")
         assert rel_loss < 1e-3
         assert rel_h < 5e-2 and rel_m < 5e-2
@@ -139,7 +140,7 @@ def test_autotuner_picks_a_measured_candidate(torch):
         ctx.close()
 
 
-@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, MIXED])
+@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, MIXED, R.ROMAP_PREC_MIXED_FP8])
 def test_rendered_rgb_vs_oracle_after_training(torch, precision):
     """After 30 training steps, the next step's per-ray rendered colour (Eq. 6) and loss against the FP64 oracle
     evaluated on the same FP32 master parameters: the mixed path within 2e-3 absolute RGB and 1e-3 relative loss,
@@ -162,10 +163,15 @@ def test_rendered_rgb_vs_oracle_after_training(torch, precision):
                            do_adam=False, want_rays=True)
         err = np.abs(out[:, :3] - ref["rays"][:, :3]).max()
         rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
-        print(f"\n[{'mixed' if precision == MIXED else 'fp32'}] after 30 steps: max |RGB - oracle| {err:.2e}, "
+        name = {R.ROMAP_PREC_FP32: "fp32", MIXED: "bf16", R.ROMAP_PREC_MIXED_FP8: "fp8"}[precision]
+        print(f"\n[{name}] after 30 steps: max |RGB - oracle| {err:.2e}, "
               f"loss rel {rel_loss:.2e}, mean |RGB| {np.abs(ref['rays'][:, :3]).mean():.3f}")
         if precision == MIXED:
             assert err < 2e-3 and rel_loss < 1e-3
+        elif precision == R.ROMAP_PREC_MIXED_FP8:
+            # E4M3 keeps 3 mantissa bits: the hidden layer's outputs carry about 1% error, the rendered colour a few
+            # 1e-3 (measured 4.2e-3 with per-channel weight and per-sample activation scales)
+            assert err < 1e-2 and rel_loss < 1e-3
         else:
             assert np.allclose(out[:, :3], ref["rays"][:, :3], rtol=1e-5, atol=1e-5) and rel_loss < 1e-5
     finally:
