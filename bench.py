@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32", "mixed"), default="mixed")
+    ap.add_argument("--precision", choices=("fp32", "mixed", "fp8"), default="mixed")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="multi8")
     ap.add_argument("--loss-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
@@ -161,6 +161,7 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "fp32": ("kernels_tile.cu", "device_common.cuh", "romap_internal.cuh"),
     "mixed": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
+    "fp8": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
 }
 
 
@@ -235,7 +236,8 @@ def make_ctx(R, torch, precision):
     rc = R.make_config(n_levels=w["levels"], log2_table_size=w["log2_table"], base_resolution=w["base_resolution"],
                        growth=0.0, max_resolution=w["max_resolution"], n_samples=w["samples_per_ray"],
                        rays_per_step=4096, bg_random=True,
-                       precision=R.ROMAP_PREC_MIXED_BF16 if precision == "mixed" else R.ROMAP_PREC_FP32,
+                       precision={"mixed": R.ROMAP_PREC_MIXED_BF16, "fp8": R.ROMAP_PREC_MIXED_FP8}.get(
+                           precision, R.ROMAP_PREC_FP32),
                        max_objects=2 * w["objects"])
     h = C.c_void_p()
     R.check(R.romap_init(C.byref(rc), C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(h)), "romap_init")
@@ -309,7 +311,7 @@ def run_ours(args):
         # a second FP32 run with the same seeds measures the run-to-run spread of FP32 training itself (atomic
         # accumulation order), the floor under any mixed-vs-FP32 difference
         for prec in ("fp32", "mixed", "fp32_repeat"):
-            rc, h = make_ctx(R, torch, "fp32" if prec == "fp32_repeat" else prec)
+            rc, h = make_ctx(R, torch, "fp32" if prec == "fp32_repeat" else (main_prec if prec == "mixed" else prec))
             ids = add_objects(R, h, items)
             idarr = (C.c_int32 * n)(*ids)
             ls = np.zeros((args.loss_steps, n), np.float32)
@@ -343,7 +345,7 @@ def run_ours(args):
     live_per_step = st.live_samples / args.steps  # this rank
     launches = st.kernel_launches
     autotune = None
-    if main_prec == "mixed":
+    if main_prec != "fp32":
         chosen = C.c_int32()
         tms = (C.c_float * 4)()
         names = C.create_string_buffer(256)
@@ -370,7 +372,7 @@ def run_ours(args):
                         "share": phase_ms[i] / max(1e-9, sum(phase_ms))}
     bwd_ms = phase_ms[3] / args.steps
     fwd_ms = phase_ms[1] / args.steps
-    mixed = main_prec == "mixed"
+    mixed = main_prec != "fp32"
     peaks = {}
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
@@ -554,8 +556,9 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": w["scaling"], "vs_baseline": None,
-               "dtype": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)" if mixed
-               else "f32",
+               "dtype": {"mixed": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)",
+                         "fp8": "fp8 e4m3 hidden 64x64 GEMM, bf16 other GEMMs (FP16 table copy; FP32 accumulation, "
+                                "scan, loss, Adam)"}.get(main_prec, "f32"),
                "data": "synthetic (analytic shapes, seeded)",
                "config": {"workload": w["name"], **config_keys(w), "precision": main_prec, "path": "batched",
                           "objects_this_rank": n, "rays_per_step_this_rank": int(sum(it.rays for it in items)),
@@ -778,7 +781,8 @@ def run_stream(args):
            "warmup": 0, "ms_per_step": train_ms / max(1, int(steps.sum())), "higher_is_better": True,
            "scaling": w["scaling"], "vs_baseline": None,
            "dtype": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)"
-           if args.precision == "mixed" else "f32",
+           if args.precision == "mixed" else ("fp8 e4m3 hidden 64x64 GEMM, bf16 other GEMMs, FP16 tables, FP32 "
+                                                "accumulation, scan, loss, Adam" if args.precision == "fp8" else "f32"),
            "data": "synthetic (analytic shapes, seeded)",
            "config": {"workload": w["name"], **config_keys(w), "precision": args.precision,
                       "observations_accepted": n_obs, "rays_observed": int(rays_in)},
