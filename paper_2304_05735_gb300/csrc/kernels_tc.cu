@@ -44,7 +44,7 @@ constexpr int kTcThreads = 128 * kTilesPerCta;
 // overrun.
 template <int LFP>
 struct TileBufs {
-  __align__(128) unsigned char E[kT * LFP * 2];
+  __align__(128) unsigned char E[2][kT * LFP * 2];  // this pair's encoding and the next pair's, alternating
   __align__(128) unsigned char H1[kT * kH * 2];
   __align__(128) unsigned char CIN[kT * 32 * 2];
   __align__(128) unsigned char H2[kT * kH * 2];
@@ -61,7 +61,47 @@ struct TileBufs {
   int valid[kT];
   int ray[kT];  // global ray index of the slot (-1 outside the tile's rays)
   int P, nrays; // slots per ray and rays of the tile
+  // dL/dencoding of the slots, feature-major (thread s owns column s), in H2's space: H2 is dead from the end of the
+  // backward until the next pair's forward writes it
+  __device__ float* dEs(int k) { return reinterpret_cast<float*>(H2) + k * kT; }
 };
+static_assert(32 * kT * sizeof(float) <= kT * kH * 2, "dL/dencoding fits in H2");
+
+// Encoding levels [l0, l1) of one sample, interpolated in FP32 from the FP16 table, into row s of a K-major BF16
+// encoding buffer; two levels per round so that 16 gathers are in flight.
+template <int LFP>
+__device__ __forceinline__ void gather_rows(const GridParams& g, const ObjectDev* ob, const float p[3],
+                                            unsigned char* E, int s, int l0, int l1) {
+  const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
+#pragma unroll 1
+  for (int l = l0; l < l1; l += 2) {
+    const bool has1 = l + 1 < l1;
+    Corners c0, c1;
+    level_corners(g, l, p, ob->half, ob->inv_ext, c0);
+    if (has1) level_corners(g, l + 1, p, ob->half, ob->inv_ext, c1);
+    __half2 v0[8], v1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v0[k] = __ldg(tab + g.off[l] + c0.idx[k]);
+      v1[k] = has1 ? __ldg(tab + g.off[l + 1] + c1.idx[k]) : __half2{};
+    }
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 f0 = __half22float2(v0[k]), f1 = __half22float2(v1[k]);
+      a0 = fmaf(c0.w[k], f0.x, a0); a1 = fmaf(c0.w[k], f0.y, a1);
+      if (has1) { b0 = fmaf(c1.w[k], f1.x, b0); b1 = fmaf(c1.w[k], f1.y, b1); }
+    }
+    *reinterpret_cast<__nv_bfloat162*>(E + kmaj(s, 2 * l, LFP)) = __floats2bfloat162_rn(a0, a1);
+    if (has1) *reinterpret_cast<__nv_bfloat162*>(E + kmaj(s, 2 * l + 2, LFP)) = __floats2bfloat162_rn(b0, b1);
+  }
+}
+// zero row s of an encoding buffer over the levels [l0, l1)
+template <int LFP>
+__device__ __forceinline__ void zero_rows(unsigned char* E, int s, int l0, int l1) {
+#pragma unroll 1
+  for (int l = l0; l < l1; ++l) *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l, LFP)) = 0u;
+}
 
 template <int LFP, bool FP8>
 struct TcSmem {
@@ -80,6 +120,9 @@ struct TcSmem {
   uint32_t tmem_base;
   int fail;
 };
+
+static_assert(sizeof(TcSmem<32, false>) <= 227 * 1024 && sizeof(TcSmem<32, true>) <= 227 * 1024,
+              "shared memory of the fused kernel");
 
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -224,12 +267,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   int nx_bi = nx_ti.x;
   const ObjectDev* nx_ob = &b.objs[b.slot[nx_bi]];
   SlotSample nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
-  float ne[LFP];
-#pragma unroll
-  for (int k = 0; k < LFP; ++k) ne[k] = 0.f;
+  const int Lg = g.L < LMAX ? g.L : LMAX;
+  auto part = [&](int k) { return k * Lg / 5; };  // level ranges of the five backward windows
+  int cur = 0;  // encoding buffer of the current pair
+  // columns past 2 L stay zero in both buffers
+  for (int u = 0; u < 2; ++u) zero_rows<LFP>(tb.E[u], s, Lg, LMAX);
   if (nx.valid) {
     const float p[3] = {nx.x, nx.y, nx.z};
-    gather_levels<LFP, 0, LMAX>(g, nx_ob, p, ne);
+    gather_rows<LFP>(g, nx_ob, p, tb.E[0], s, 0, Lg);
+  } else {
+    zero_rows<LFP>(tb.E[0], s, 0, Lg);
   }
   for (int pair = pair_lo; pair < pair_hi && ok; ++pair) {
     // ---- 1-2. the prepared sample and encoding of this pair -> tile buffers ---------------------------------------
@@ -242,8 +289,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tb.px[0][s] = nx.x; tb.px[1][s] = nx.y; tb.px[2][s] = nx.z;
     tb.t[s] = nx.t;
     tb.dt[s] = nx.dt;
-#pragma unroll
-    for (int c = 0; c < LFP / 8; ++c) store8(tb.E, s, c, LFP, ne + 8 * c);
     if (nx_bi != bi) {
       if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
       bi = nx_bi;
@@ -266,7 +311,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
         for (int kk = 0; kk < LFP / 16; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].E, LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0), kk > 0);
+          mma(tmp_d(u), desc_k(sm.tb[u].E[cur], LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
@@ -408,16 +453,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
-    {  // while the MMAs run: part 0 of the next pair's sample and encoding
+    {  // while the MMAs run: the next pair's sample and part 0 of its encoding (into the other buffer)
       if (has_next) {
         nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
-#pragma unroll
-        for (int q = 0; q < LFP; ++q) ne[q] = 0.f;
-      }
-      if (has_next && nx.valid) {
-        constexpr int S0 = 0 * LMAX / 5, S1 = 1 * LMAX / 5;
         const float p[3] = {nx.x, nx.y, nx.z};
-        gather_levels<LFP, S0, S1>(g, nx_ob, p, ne);
+        if (nx.valid) gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(0), part(1));
+        else zero_rows<LFP>(tb.E[cur ^ 1], s, 0, Lg);
       }
     }
     if (!(ok = wait_mma())) break;
@@ -435,11 +476,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
-    {  // while the MMAs run: part 1 of the next pair's sample and encoding
+    {  // while the MMAs run: part 1 of the next pair's encoding
       if (has_next && nx.valid) {
-        constexpr int S1 = 1 * LMAX / 5, S2 = 2 * LMAX / 5;
         const float p[3] = {nx.x, nx.y, nx.z};
-        gather_levels<LFP, S1, S2>(g, nx_ob, p, ne);
+        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(1), part(2));
       }
     }
     if (!(ok = wait_mma())) break;
@@ -457,11 +497,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
-    {  // while the MMAs run: part 2 of the next pair's sample and encoding
+    {  // while the MMAs run: part 2 of the next pair's encoding
       if (has_next && nx.valid) {
-        constexpr int S2 = 2 * LMAX / 5, S3 = 3 * LMAX / 5;
         const float p[3] = {nx.x, nx.y, nx.z};
-        gather_levels<LFP, S2, S3>(g, nx_ob, p, ne);
+        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(2), part(3));
       }
     }
     if (!(ok = wait_mma())) break;
@@ -486,11 +525,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
-    {  // while the MMAs run: part 3 of the next pair's sample and encoding
+    {  // while the MMAs run: part 3 of the next pair's encoding
       if (has_next && nx.valid) {
-        constexpr int S3 = 3 * LMAX / 5, S4 = 4 * LMAX / 5;
         const float p[3] = {nx.x, nx.y, nx.z};
-        gather_levels<LFP, S3, S4>(g, nx_ob, p, ne);
+        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(3), part(4));
       }
     }
     if (!(ok = wait_mma())) break;
@@ -503,39 +541,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1), kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW1 + tm, desc_mn(sm.tb[u].E, LFP, kk), desc_mn(sm.tb[u].H1, kH, kk), idesc(64, 1, 1),
+          mma(kColDW1 + tm, desc_mn(sm.tb[u].E[cur], LFP, kk), desc_mn(sm.tb[u].H1, kH, kk), idesc(64, 1, 1),
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
     }
-    {  // while the MMAs run: part 4 of the next pair's sample and encoding
+    {  // while the MMAs run: part 4 of the next pair's encoding
       if (has_next && nx.valid) {
-        constexpr int S4 = 4 * LMAX / 5, S5 = LMAX;
         const float p[3] = {nx.x, nx.y, nx.z};
-        gather_levels<LFP, S4, S5>(g, nx_ob, p, ne);
+        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(4), part(5));
       }
     }
     if (!(ok = wait_mma())) break;
     acc_dw = 1;
     {  // ---- 6. scatter dL/dencoding into the FP32 table gradient ----
-      float de[LFP];
 #pragma unroll
-      for (int c = 0; c < LFP / 16; ++c) tmem_ld16(tmp + 16 * c, de + 16 * c);
-      tmem_wait_ld();
+      for (int c = 0; c < LFP / 16; ++c) {
+        float de[16];
+        tmem_ld16(tmp + 16 * c, de);
+        tmem_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) tb.dEs(16 * c + k)[s] = de[k];
+      }
       if (tb.valid[s]) {
         const float p[3] = {tb.px[0][s], tb.px[1][s], tb.px[2][s]};
         float2* gt = reinterpret_cast<float2*>(ob->grad);
-#pragma unroll
-        for (int l = 0; l < LFP / 2; ++l) {
-          const float d0 = de[2 * l], d1 = de[2 * l + 1];
-          if (l >= g.L || (d0 == 0.f && d1 == 0.f)) continue;
+#pragma unroll 1
+        for (int l = 0; l < Lg; ++l) {
+          const float d0 = tb.dEs(2 * l)[s], d1 = tb.dEs(2 * l + 1)[s];
+          if (d0 == 0.f && d1 == 0.f) continue;
           Corners c;
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
-#pragma unroll
           scatter_corners(gt + g.off[l], c.idx, c.w, d0, d1);
         }
       }
     }
+    cur ^= 1;  // the next pair's encoding is in the other buffer
     tc_before();
     __syncthreads();
     tc_after();
