@@ -37,6 +37,9 @@
  *  R-10 Compositing adjoint by explicit suffix sums.
  *  R-11 MLP: density (L*F)->H->16 ReLU; colour (15 + dir)->H->H->3, ReLU,
  *       sigmoid; no biases.
+ *  R-11' The paper's model (Sec. V: hash encoding and a single-layer MLP,
+ *       positions only): (L*F)->H->16 with sigma from output 0 and the
+ *       colour sigmoid(outputs 1..3); the colour-net layers are unused.
  *  R-13 sigma = exp(clamp(o_0, -15, 15)); zero gradient outside the clamp.
  *  R-14 Adam (Kingma & Ba) with bias correction, step counter from 1.
  *  R-17 Occupancy update (not in the paper): density at the 64^3 cell
@@ -84,6 +87,8 @@ typedef struct oc_config {
   double bg_const[3];     /* background when bg_random == 0 */
   double lambda1, lambda2;/* Eq. 11 */
   double lr, beta1, beta2, eps; /* Adam */
+  int32_t single_net;     /* 1: the paper's model (R-11'): colour logits = density-net outputs 1..3 */
+  int32_t pad_;
 } oc_config;
 
 /* ------------------------------------------------------------------ */
@@ -381,6 +386,15 @@ void oc_mlp_forward(const oc_config* c, const double* mlp, const double* enc, co
   if (o0 < -15.0) o0 = -15.0;
   if (o0 > 15.0) o0 = 15.0;
   a->sigma = exp(o0);
+  if (c->single_net) {
+    for (int j = 0; j < G + D; ++j) a->cin[j] = 0.0;
+    for (int i = 0; i < H; ++i) a->h2[i] = a->h3[i] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      a->logit[k] = a->out[1 + k];
+      a->rgb[k] = 1.0 / (1.0 + exp(-a->logit[k]));
+    }
+    return;
+  }
   for (int j = 0; j < G; ++j) a->cin[j] = a->out[1 + j];
   for (int j = 0; j < D; ++j) a->cin[G + j] = (double)dir[j];
   matvec(W2, H, G + D, a->cin, a->h2);
@@ -401,6 +415,10 @@ void oc_mlp_backward(const oc_config* c, const double* mlp, const oc_act* a, dou
   for (int l = 0; l < 5; ++l) { W[l] = mlp + oc_mlp_layer_offset(c, l); gW[l] = gmlp + oc_mlp_layer_offset(c, l); }
   double glogit[3], gh3[OC_MAX_H], gh2[OC_MAX_H], gcin[34], gout[32], gh1[OC_MAX_H];
   for (int k = 0; k < 3; ++k) glogit[k] = grgb[k] * a->rgb[k] * (1.0 - a->rgb[k]);
+  if (c->single_net) {  /* the colour logits are density-net outputs 1..3 */
+    for (int j = 0; j < G; ++j) gcin[j] = j < 3 ? glogit[j] : 0.0;
+    goto density_outputs;
+  }
   /* layer 4: logit = W4 h3 */
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < H; ++j) gW[4][k * H + j] += glogit[k] * a->h3[j];
@@ -427,6 +445,7 @@ void oc_mlp_backward(const oc_config* c, const double* mlp, const oc_act* a, dou
     gcin[j] = s;
   }
   /* density outputs: out0 -> sigma through exp(clamp); out1.. -> cin */
+density_outputs:;
   double o0 = a->out[0];
   gout[0] = (o0 >= -15.0 && o0 <= 15.0) ? gsigma * a->sigma : 0.0;
   for (int j = 0; j < G; ++j) gout[1 + j] = gcin[j];

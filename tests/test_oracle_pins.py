@@ -573,3 +573,32 @@ def test_training_decreases_loss_config0():
         p, m, v = r["params"], r["m"], r["v"]
         losses.append(r["loss"][0])
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_single_net_forward_and_backward():
+    """The paper's model (one hidden layer, positions only): sigma from output 0 and the colour sigmoid(outputs
+    1..3) of the density net, against numpy matrix products and torch autograd; the colour-net weights get no
+    gradient."""
+    torch = pytest.importorskip("torch")
+    cfg = O.make_config(L=8, T=2 ** 12, dir_dims=0, single_net=True)
+    rng = np.random.default_rng(3)
+    nm = O.param_count(cfg) - O.hash_param_count(cfg)
+    mlp = rng.normal(size=nm) * 0.3
+    W = _mlp_weights(cfg, mlp)
+    for _ in range(5):
+        enc = rng.normal(size=16)
+        f = O.mlp_forward(cfg, mlp, enc, np.zeros(3, np.float32))
+        out = W[1] @ np.maximum(W[0] @ enc, 0)
+        assert np.allclose(f["rgb"], 1 / (1 + np.exp(-out[1:4])), rtol=1e-13)
+        assert abs(f["sigma"] - math.exp(min(max(out[0], -15), 15))) < 1e-12 * f["sigma"]
+        gsig, grgb = rng.normal(), rng.normal(size=3)
+        gmlp, genc = O.mlp_backward(cfg, mlp, f, gsig, grgb)
+        tm = torch.tensor(mlp, dtype=torch.float64, requires_grad=True)
+        te = torch.tensor(enc, dtype=torch.float64, requires_grad=True)
+        Ws = _mlp_weights(cfg, tm)
+        o = Ws[1] @ torch.relu(Ws[0] @ te)
+        (gsig * torch.exp(torch.clamp(o[0], -15, 15)) + (torch.tensor(grgb) * torch.sigmoid(o[1:4])).sum()).backward()
+        assert np.allclose(gmlp, tm.grad.numpy(), rtol=1e-11, atol=1e-12)
+        assert np.allclose(genc, te.grad.numpy(), rtol=1e-11, atol=1e-12)
+        off2 = O.mlp_layer_offset(cfg, 2)
+        assert np.all(gmlp[off2:] == 0.0)
