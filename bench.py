@@ -231,11 +231,13 @@ def build_items(w, rank, world):
     return items
 
 
-def make_ctx(R, torch, precision):
+def make_ctx(R, torch, precision, single_net=False):
+    """A context for the current workload; single_net selects the one-hidden-layer, position-only model of
+    Sec. V instead of the density + colour nets."""
     w = WORKLOAD
     rc = R.make_config(n_levels=w["levels"], log2_table_size=w["log2_table"], base_resolution=w["base_resolution"],
                        growth=0.0, max_resolution=w["max_resolution"], n_samples=w["samples_per_ray"],
-                       rays_per_step=4096, bg_random=True,
+                       rays_per_step=4096, bg_random=True, single_net=single_net, dir_dims=0 if single_net else 3,
                        precision={"mixed": R.ROMAP_PREC_MIXED_BF16, "fp8": R.ROMAP_PREC_MIXED_FP8}.get(
                            precision, R.ROMAP_PREC_FP32),
                        max_objects=2 * w["objects"])
@@ -807,7 +809,8 @@ def run_stream(args):
 
 def run_table4(args):
     """ms per training iteration of one object (CUDA events over graph-replayed steps) for each table size, in both
-    precisions, next to the paper's Table 4 (RTX 4090, one-hidden-layer model)."""
+    precisions, for the two-net model and for the paper's single-network model, next to the paper's Table 4 (RTX
+    4090, single-network model)."""
     import numpy as np
     import torch
 
@@ -824,9 +827,9 @@ def run_table4(args):
     rows = []
     for lt in base["log2_tables"]:
         row = {"log2_table": lt, "paper_ms": base["paper_ms"][lt]}
-        for prec in ("mixed", "fp32"):
+        for prec, single in (("mixed", False), ("fp32", False), ("mixed", True), ("fp32", True)):
             WORKLOAD = dict(base, log2_table=lt)
-            rc, h = make_ctx(R, torch, prec)
+            rc, h = make_ctx(R, torch, prec, single_net=single)
             ids = add_objects(R, h, items)
             arr = (C.c_int32 * 1)(*ids)
             R.check(R.romap_train_step(h, arr, 1, max(args.warmup, 3), None))
@@ -835,8 +838,9 @@ def run_table4(args):
             ms = timed(torch, lambda: [R.check(R.romap_train_step(h, arr, 1, 1, None)) for _ in range(k)], 1, None)
             st = R.romap_stats()
             R.check(R.romap_get_stats(h, C.byref(st)))
-            row[f"{prec}_ms"] = ms / k
-            row[f"{prec}_samples_per_s"] = st.live_samples / (ms / 1e3)
+            key = ("single_" if single else "") + prec
+            row[f"{key}_ms"] = ms / k
+            row[f"{key}_samples_per_s"] = st.live_samples / (ms / 1e3)
             row["params"] = int(R.param_layout(rc).n_params)
             R.check(R.romap_destroy(h))
         rows.append(row)
@@ -848,8 +852,9 @@ def run_table4(args):
            "data": "synthetic (analytic shapes, seeded)",
            "config": {"workload": base["name"], **{k: v for k, v in config_keys(base).items() if k != "paper_ms"}},
            "sweep": rows,
-           "note": "value and ms_per_step: T = 2^16; the paper's times are for its one-hidden-layer model on an RTX "
-                   "4090 (context, not a target); this build trains the two-net model"}
+           "note": "value and ms_per_step: T = 2^16, two-net model; single_* columns: the paper's single-network "
+                   "model (one hidden layer, position only), the model its Table 4 times on an RTX 4090 (context, not "
+                   "a target)"}
     print(json.dumps(out), flush=True)
 
 

@@ -87,7 +87,7 @@ typedef struct romap_ctx romap_ctx;
  * MLP (Sec. V, "single-layer MLP", hidden 64): density net (L*F)->64->16
  * with ReLU, sigma = exp(clamp(out_0, -15, 15)); colour net
  * (15 geometry features + dir_dims)->64->64->3 with ReLU and sigmoid; no
- * biases.  Loss weights lambda1, lambda2 of Eq. 11. */
+ * biases (single_net = 0).  Loss weights lambda1, lambda2 of Eq. 11. */
 typedef struct romap_config {
   int32_t n_levels;        /* L, 1..16 */
   int32_t n_features;      /* F, must be 2 */
@@ -109,7 +109,10 @@ typedef struct romap_config {
   int64_t max_rays_per_object; /* ray-pool capacity of one object */
   int32_t accuracy_mode;   /* 1: the FP32 path accumulates the transmittance log-sum (the prefix of
                               sigma * delta) and the compositing weights in FP64 (Eq. 6) */
-  int32_t reserved;        /* 0 */
+  int32_t single_net;      /* 1: the single-network model of Sec. V (one hidden layer, position input
+                              only): the colour logits are density-net outputs 1..3 and the colour-net
+                              weights are neither read nor updated (their gradient stays 0).  Not
+                              combined with ROMAP_PREC_MIXED_FP8. */
   /* Optional device allocator (both or neither).  alloc returns NULL on
    * failure, which the library reports as ROMAP_ERR_OOM; a pointer that is
    * not 256-byte aligned is handed back to dealloc and reported as
@@ -385,7 +388,8 @@ ROMAP_API romap_status romap_reset_stats(romap_ctx* ctx);
  * (the expected outcome); the context stays usable. */
 ROMAP_API romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_limit);
 /* Forces candidate `index` (0 = lockstep tile pairs, 1 = warp-specialized),
- * or -1 to autotune again at the next mixed step. */
+ * or -1 to autotune again at the next mixed step.  ROMAP_ERR_UNSUPPORTED for
+ * index 1 under ROMAP_PREC_MIXED_FP8 or single_net (both run on kernel 0). */
 ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);
 ROMAP_API romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, int32_t n, char* names,
                                              size_t names_len);

@@ -207,7 +207,7 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
   }
 }
 
-template <int LFP, bool FP8>
+template <int LFP, bool FP8, bool SN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -268,7 +268,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const ObjectDev* nx_ob = &b.objs[b.slot[nx_bi]];
   SlotSample nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
   const int Lg = g.L < LMAX ? g.L : LMAX;
-  auto part = [&](int k) { return k * Lg / 5; };  // level ranges of the five backward windows
+  // level ranges of the backward windows that overlap the next pair's gather: five with the colour net, two (dH1,
+  // dE) without it
+  constexpr int kWin = SN ? 2 : 5;
+  auto part = [&](int k) { return k * Lg / kWin; };
   int cur = 0;  // encoding buffer of the current pair
   // columns past 2 L stay zero in both buffers
   for (int u = 0; u < 2; ++u) zero_rows<LFP>(tb.E[u], s, Lg, LMAX);
@@ -332,86 +335,93 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const float o0 = v[0];
       tb.o0[s] = o0;
       tb.sig[s] = expf(fminf(fmaxf(o0, -15.f), 15.f));
-      float cin[32];
+      if constexpr (SN) {  // the colour logits are density-net outputs 1..3
 #pragma unroll
-      for (int j = 0; j < 15; ++j) cin[j] = v[1 + j];
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-      if (g.dir_dims == 3 && tb.valid[s]) {
-        const int64_t r = tb.ray[s];
-        d0 = R.d[3 * r]; d1 = R.d[3 * r + 1]; d2 = R.d[3 * r + 2];
-      }
-      cin[15] = d0; cin[16] = d1; cin[17] = d2;
+        for (int k = 0; k < 3; ++k) tb.rgb[k][s] = 1.0f / (1.0f + expf(-v[1 + k]));
+      } else {
+        float cin[32];
 #pragma unroll
-      for (int j = 18; j < 32; ++j) cin[j] = 0.f;
+        for (int j = 0; j < 15; ++j) cin[j] = v[1 + j];
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        if (g.dir_dims == 3 && tb.valid[s]) {
+          const int64_t r = tb.ray[s];
+          d0 = R.d[3 * r]; d1 = R.d[3 * r + 1]; d2 = R.d[3 * r + 2];
+        }
+        cin[15] = d0; cin[16] = d1; cin[17] = d2;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) store8(tb.CIN, s, c, 32, cin + 8 * c);
-    }
-    sync_then_issue();
-    if (t == 0) {  // L3: CIN W3^T
-      for (int u = 0; u < kTilesPerCta; ++u)
+        for (int j = 18; j < 32; ++j) cin[j] = 0.f;
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0), kk > 0);
-      mma_commit(&sm.mbar);
-    }
-    if (!(ok = wait_mma())) break;
-    epi_relu64(tmp, tb.H2, s);
-    float h2_scale = 1.f;  // FP8: 448 / max of this sample's H2 row (1 when all zero)
-    if (FP8) {  // this sample's H2 row in E4M3; the row scale factors out of its GEMM outputs
-      float hv[64];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) load8(tb.H2, s, c, kH, hv + 8 * c);
-      float m = 0.f;
-#pragma unroll
-      for (int j = 0; j < 64; ++j) m = fmaxf(m, hv[j]);
-      const float sc = m > 0.f ? 448.f / m : 1.f;
-      h2_scale = sc;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {  // 16 consecutive k of row s are one 16-byte core-matrix row
-        const float* h = hv + 16 * c;
-        uint4 q;
-        q.x = fp8x4(h[0] * sc, h[1] * sc, h[2] * sc, h[3] * sc);
-        q.y = fp8x4(h[4] * sc, h[5] * sc, h[6] * sc, h[7] * sc);
-        q.z = fp8x4(h[8] * sc, h[9] * sc, h[10] * sc, h[11] * sc);
-        q.w = fp8x4(h[12] * sc, h[13] * sc, h[14] * sc, h[15] * sc);
-        *reinterpret_cast<uint4*>(sm.h2q[wg] + kmaj8(s, 16 * c, kH)) = q;
+        for (int c = 0; c < 4; ++c) store8(tb.CIN, s, c, 32, cin + 8 * c);
       }
     }
-    sync_then_issue();
-    if (t == 0) {  // L4: H2 W4^T
-      for (int u = 0; u < kTilesPerCta; ++u) {
-        if (FP8) {
+    if constexpr (!SN) {  // ---- colour net --------------------------------------------------------------------------
+      sync_then_issue();
+      if (t == 0) {  // L3: CIN W3^T
+        for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
-            mma8(tmp_d(u), desc_k8(sm.h2q[u], kH, kk), desc_k8(sm.w4q, kH, kk), idesc8(64), kk > 0);
-        } else {
+            mma(tmp_d(u), desc_k(sm.tb[u].CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0), kk > 0);
+        mma_commit(&sm.mbar);
+      }
+      if (!(ok = wait_mma())) break;
+      epi_relu64(tmp, tb.H2, s);
+      float h2_scale = 1.f;  // FP8: 448 / max of this sample's H2 row (1 when all zero)
+      if (FP8) {  // this sample's H2 row in E4M3; the row scale factors out of its GEMM outputs
+        float hv[64];
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+        for (int c = 0; c < 8; ++c) load8(tb.H2, s, c, kH, hv + 8 * c);
+        float m = 0.f;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) m = fmaxf(m, hv[j]);
+        const float sc = m > 0.f ? 448.f / m : 1.f;
+        h2_scale = sc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {  // 16 consecutive k of row s are one 16-byte core-matrix row
+          const float* h = hv + 16 * c;
+          uint4 q;
+          q.x = fp8x4(h[0] * sc, h[1] * sc, h[2] * sc, h[3] * sc);
+          q.y = fp8x4(h[4] * sc, h[5] * sc, h[6] * sc, h[7] * sc);
+          q.z = fp8x4(h[8] * sc, h[9] * sc, h[10] * sc, h[11] * sc);
+          q.w = fp8x4(h[12] * sc, h[13] * sc, h[14] * sc, h[15] * sc);
+          *reinterpret_cast<uint4*>(sm.h2q[wg] + kmaj8(s, 16 * c, kH)) = q;
         }
       }
-      mma_commit(&sm.mbar);
-    }
-    if (!(ok = wait_mma())) break;
-    if (FP8) epi_relu64_scaled(tmp, tb.H3, s, 1.0f / h2_scale, sm.w4_inv);
-    else epi_relu64(tmp, tb.H3, s);
-    sync_then_issue();
-    if (t == 0) {  // L5: H3 W5^T (3 of 16 outputs)
-      for (int u = 0; u < kTilesPerCta; ++u)
+      sync_then_issue();
+      if (t == 0) {  // L4: H2 W4^T
+        for (int u = 0; u < kTilesPerCta; ++u) {
+          if (FP8) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0), kk > 0);
-      mma_commit(&sm.mbar);
-    }
-    if (!(ok = wait_mma())) break;
-    {
-      float v[16];
-      tmem_ld16(tmp, v);
-      tmem_wait_ld();
-      tb.rgb[0][s] = 1.0f / (1.0f + expf(-v[0]));
-      tb.rgb[1][s] = 1.0f / (1.0f + expf(-v[1]));
-      tb.rgb[2][s] = 1.0f / (1.0f + expf(-v[2]));
-    }
+            for (int kk = 0; kk < 2; ++kk)
+              mma8(tmp_d(u), desc_k8(sm.h2q[u], kH, kk), desc_k8(sm.w4q, kH, kk), idesc8(64), kk > 0);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+          }
+        }
+        mma_commit(&sm.mbar);
+      }
+      if (!(ok = wait_mma())) break;
+      if (FP8) epi_relu64_scaled(tmp, tb.H3, s, 1.0f / h2_scale, sm.w4_inv);
+      else epi_relu64(tmp, tb.H3, s);
+      sync_then_issue();
+      if (t == 0) {  // L5: H3 W5^T (3 of 16 outputs)
+        for (int u = 0; u < kTilesPerCta; ++u)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0), kk > 0);
+        mma_commit(&sm.mbar);
+      }
+      if (!(ok = wait_mma())) break;
+      {
+        float v[16];
+        tmem_ld16(tmp, v);
+        tmem_wait_ld();
+        tb.rgb[0][s] = 1.0f / (1.0f + expf(-v[0]));
+        tb.rgb[1][s] = 1.0f / (1.0f + expf(-v[1]));
+        tb.rgb[2][s] = 1.0f / (1.0f + expf(-v[2]));
+      }
+    }  // colour net
     __syncthreads();
     // ---- 4. compositing, losses, adjoint: one warp per ray of the pair -----------------------------------------
     {
@@ -439,81 +449,88 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       const float o0 = tb.o0[s];
       dpre = (valid && o0 >= -15.f && o0 <= 15.f) ? tb.dsig[s] * tb.sig[s] : 0.f;
+      if constexpr (SN) {  // dOUT = [dsigma * sigma, dlogit 0..2, 0 ...]
+#pragma unroll
+        for (int k = 15; k > 0; --k) dl[k] = k <= 3 ? dl[k - 1] : 0.f;
+        dl[0] = dpre;
+      }
       store8(tb.DL, s, 0, 16, dl);
       store8(tb.DL, s, 1, 16, dl + 8);
     }
-    sync_then_issue();
-    if (t == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
-      for (int u = 0; u < kTilesPerCta; ++u) {
-        mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1), 0);
+    if constexpr (!SN) {  // ---- colour net backward ------------------------------------------------------------------
+      sync_then_issue();
+      if (t == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
+        for (int u = 0; u < kTilesPerCta; ++u) {
+          mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1), 0);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
-              (u > 0 || kk > 0) ? 1u : acc_dw);
+          for (int kk = 0; kk < 8; ++kk)
+            mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
+                (u > 0 || kk > 0) ? 1u : acc_dw);
+        }
+        mma_commit(&sm.mbar);
       }
-      mma_commit(&sm.mbar);
-    }
-    {  // while the MMAs run: the next pair's sample and part 0 of its encoding (into the other buffer)
-      if (has_next) {
-        nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
-        const float p[3] = {nx.x, nx.y, nx.z};
-        if (nx.valid) gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(0), part(1));
-        else zero_rows<LFP>(tb.E[cur ^ 1], s, 0, Lg);
+      {  // while the MMAs run: the next pair's sample and part 0 of its encoding (into the other buffer)
+        if (has_next) {
+          nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
+          const float p[3] = {nx.x, nx.y, nx.z};
+          if (nx.valid) gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(0), part(1));
+          else zero_rows<LFP>(tb.E[cur ^ 1], s, 0, Lg);
+        }
       }
-    }
-    if (!(ok = wait_mma())) break;
-    epi_mask64(tmp, tb.H3, s);
-    sync_then_issue();
-    if (t == 0) {  // dH2 = dH3 W4 ; dW4^T += H2^T dH3
-      for (int u = 0; u < kTilesPerCta; ++u) {
+      if (!(ok = wait_mma())) break;
+      epi_mask64(tmp, tb.H3, s);
+      sync_then_issue();
+      if (t == 0) {  // dH2 = dH3 W4 ; dW4^T += H2^T dH3
+        for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1), kk > 0);
+          for (int kk = 0; kk < 4; ++kk)
+            mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1), kk > 0);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW4 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1),
-              (u > 0 || kk > 0) ? 1u : acc_dw);
+          for (int kk = 0; kk < 8; ++kk)
+            mma(kColDW4 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1),
+                (u > 0 || kk > 0) ? 1u : acc_dw);
+        }
+        mma_commit(&sm.mbar);
       }
-      mma_commit(&sm.mbar);
-    }
-    {  // while the MMAs run: part 1 of the next pair's encoding
-      if (has_next && nx.valid) {
-        const float p[3] = {nx.x, nx.y, nx.z};
-        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(1), part(2));
+      {  // while the MMAs run: part 1 of the next pair's encoding
+        if (has_next && nx.valid) {
+          const float p[3] = {nx.x, nx.y, nx.z};
+          gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(1), part(2));
+        }
       }
-    }
-    if (!(ok = wait_mma())) break;
-    epi_mask64(tmp, tb.H2, s);
-    sync_then_issue();
-    if (t == 0) {  // dCIN = dH2 W3 (32 columns) ; dW3^T += CIN^T dH2
-      for (int u = 0; u < kTilesPerCta; ++u) {
+      if (!(ok = wait_mma())) break;
+      epi_mask64(tmp, tb.H2, s);
+      sync_then_issue();
+      if (t == 0) {  // dCIN = dH2 W3 (32 columns) ; dW3^T += CIN^T dH2
+        for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1), kk > 0);
+          for (int kk = 0; kk < 4; ++kk)
+            mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1), kk > 0);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW3 + tm, desc_mn(sm.tb[u].CIN, 32, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1),
-              (u > 0 || kk > 0) ? 1u : acc_dw);
+          for (int kk = 0; kk < 8; ++kk)
+            mma(kColDW3 + tm, desc_mn(sm.tb[u].CIN, 32, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1),
+                (u > 0 || kk > 0) ? 1u : acc_dw);
+        }
+        mma_commit(&sm.mbar);
       }
-      mma_commit(&sm.mbar);
-    }
-    {  // while the MMAs run: part 2 of the next pair's encoding
-      if (has_next && nx.valid) {
-        const float p[3] = {nx.x, nx.y, nx.z};
-        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(2), part(3));
+      {  // while the MMAs run: part 2 of the next pair's encoding
+        if (has_next && nx.valid) {
+          const float p[3] = {nx.x, nx.y, nx.z};
+          gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(2), part(3));
+        }
       }
-    }
-    if (!(ok = wait_mma())) break;
-    {  // dOUT = [dsigma * sigma, dCIN[0..14]] into DL
-      float v[16], d[16];
-      tmem_ld16(tmp, v);
-      tmem_wait_ld();
-      d[0] = dpre;
+      if (!(ok = wait_mma())) break;
+      {  // dOUT = [dsigma * sigma, dCIN[0..14]] into DL
+        float v[16], d[16];
+        tmem_ld16(tmp, v);
+        tmem_wait_ld();
+        d[0] = dpre;
 #pragma unroll
-      for (int j = 0; j < 15; ++j) d[1 + j] = v[j];
-      store8(tb.DL, s, 0, 16, d);
-      store8(tb.DL, s, 1, 16, d + 8);
-    }
+        for (int j = 0; j < 15; ++j) d[1 + j] = v[j];
+        store8(tb.DL, s, 0, 16, d);
+        store8(tb.DL, s, 1, 16, d + 8);
+      }
+    }  // colour net backward
     sync_then_issue();
     if (t == 0) {  // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
       for (int u = 0; u < kTilesPerCta; ++u) {
@@ -525,7 +542,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
-    {  // while the MMAs run: part 3 of the next pair's encoding
+    if constexpr (SN) {  // while the MMAs run: the next pair's sample and the first half of its encoding
+      if (has_next) {
+        nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
+        const float p[3] = {nx.x, nx.y, nx.z};
+        if (nx.valid) gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(0), part(1));
+        else zero_rows<LFP>(tb.E[cur ^ 1], s, 0, Lg);
+      }
+    } else {  // while the MMAs run: part 3 of the next pair's encoding
       if (has_next && nx.valid) {
         const float p[3] = {nx.x, nx.y, nx.z};
         gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(3), part(4));
@@ -546,10 +570,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       mma_commit(&sm.mbar);
     }
-    {  // while the MMAs run: part 4 of the next pair's encoding
+    {  // while the MMAs run: the last part of the next pair's encoding
       if (has_next && nx.valid) {
         const float p[3] = {nx.x, nx.y, nx.z};
-        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(4), part(5));
+        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(kWin - 1), part(kWin));
       }
     }
     if (!(ok = wait_mma())) break;
@@ -594,7 +618,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(kTmemCols));
 }
 
-template <int LFP, bool FP8>
+template <int LFP, bool FP8, bool SN>
 void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                  int max_tiles, int n_ctas, cudaStream_t stream) {
   // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
@@ -603,14 +627,14 @@ void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
   if (bytes < 116 * 1024) bytes = 116 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_tc<LFP, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_tile_tc<LFP, FP8, SN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr_set = true;
   }
   // the plan's pair count is read on the device; max_tiles only bounds the grid
   const int max_pairs = (max_tiles + kTilesPerCta - 1) / kTilesPerCta;
   int grid = n_ctas < max_pairs ? n_ctas : max_pairs;
   if (grid < 1) return;
-  k_tile_tc<LFP, FP8><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status);
+  k_tile_tc<LFP, FP8, SN><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status);
 }
 
 // Places every ray of the batch in the tile plan: rays with live samples go to their class's position in
@@ -653,12 +677,15 @@ __global__ void __launch_bounds__(256) k_plan_rays(GridParams g, BatchDesc b, Ra
 
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int max_tiles, int n_ctas, cudaStream_t stream) {
-  if (g.fp8) {
-    if (g.LF <= 16) launch_tc_t<16, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
-    else launch_tc_t<32, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+  if (g.fp8) {  // (the single-network model is never combined with FP8)
+    if (g.LF <= 16) launch_tc_t<16, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    else launch_tc_t<32, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+  } else if (g.single_net) {
+    if (g.LF <= 16) launch_tc_t<16, false, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    else launch_tc_t<32, false, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
   } else {
-    if (g.LF <= 16) launch_tc_t<16, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
-    else launch_tc_t<32, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    if (g.LF <= 16) launch_tc_t<16, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    else launch_tc_t<32, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
   }
 }
 

@@ -283,26 +283,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       store_tile<1>(sm.OC, acc, [](float v, int, int) { return v; });
     }
     __syncthreads();
-    {  // H2 = relu(CIN W3^T), CIN = OC rows 1..cin
-      float acc[8][4];
-      gemm_tile<4>(sm.OC + kAS, cin, sm.w3t, kH, acc);
-      store_tile<4>(sm.H2, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
+    if (!g.single_net) {
+      {  // H2 = relu(CIN W3^T), CIN = OC rows 1..cin
+        float acc[8][4];
+        gemm_tile<4>(sm.OC + kAS, cin, sm.w3t, kH, acc);
+        store_tile<4>(sm.H2, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
+      }
+      __syncthreads();
+      {  // H3 = relu(H2 W4^T)
+        float acc[8][4];
+        gemm_tile<4>(sm.H2, kH, sm.w4t, kH, acc);
+        store_tile<4>(sm.H3, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    {  // H3 = relu(H2 W4^T)
-      float acc[8][4];
-      gemm_tile<4>(sm.H2, kH, sm.w4t, kH, acc);
-      store_tile<4>(sm.H3, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
-    }
-    __syncthreads();
     if (t < kTile) {  // logits, sigmoid, density
       float l0 = 0.f, l1 = 0.f, l2 = 0.f;
+      if (g.single_net) {  // the colour logits are density-net outputs 1..3
+        l0 = sm.OC[kAS + t];
+        l1 = sm.OC[2 * kAS + t];
+        l2 = sm.OC[3 * kAS + t];
+      } else {
 #pragma unroll 8
-      for (int k = 0; k < kH; ++k) {
-        float h = sm.H3[k * kAS + t];
-        l0 = fmaf(sm.w5[k], h, l0);
-        l1 = fmaf(sm.w5[kH + k], h, l1);
-        l2 = fmaf(sm.w5[2 * kH + k], h, l2);
+        for (int k = 0; k < kH; ++k) {
+          float h = sm.H3[k * kAS + t];
+          l0 = fmaf(sm.w5[k], h, l0);
+          l1 = fmaf(sm.w5[kH + k], h, l1);
+          l2 = fmaf(sm.w5[2 * kH + k], h, l2);
+        }
       }
       float c0 = 1.0f / (1.0f + __expf(-l0));
       float c1 = 1.0f / (1.0f + __expf(-l1));
@@ -325,48 +333,64 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // ---- backward ----------------------------------------------------------
     __syncthreads();
-    if (t < kTile) {
-      const bool valid = sm.ray[t] != kNoRay;
-      float ds = valid ? S.dsigma[s0 + t] : 0.f;
-      float o0 = sm.OC[t];
-      float dpre = (o0 >= -15.0f && o0 <= 15.0f) ? ds * sm.sig[t] : 0.0f;
+    if (g.single_net) {  // dOUT = [dsigma * sigma, dlogit 0..2, 0 ...]
+      if (t < kTile) {
+        const bool valid = sm.ray[t] != kNoRay;
+        float ds = valid ? S.dsigma[s0 + t] : 0.f;
+        float o0 = sm.OC[t];
+        sm.OC[t] = (o0 >= -15.0f && o0 <= 15.0f) ? ds * sm.sig[t] : 0.0f;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        float c = sm.rgb[j][t];
-        float dc = valid ? S.drgb[3 * (s0 + t) + j] : 0.f;
-        sm.DL[j * kAS + t] = dc * c * (1.0f - c);
+        for (int j = 0; j < 3; ++j) {
+          float c = sm.rgb[j][t];
+          float dc = valid ? S.drgb[3 * (s0 + t) + j] : 0.f;
+          sm.OC[(1 + j) * kAS + t] = dc * c * (1.0f - c);
+        }
+        for (int j = 4; j < kDOut; ++j) sm.OC[j * kAS + t] = 0.0f;
       }
-      sm.DL[3 * kAS + t] = 0.0f;
-      sm.sig[t] = dpre;  // reuse: dL/d(out_0)
-    }
-    __syncthreads();
-    wgrad_tile<kC3Rows, kH, 1, 1>(sm.DL, sm.H3, g5);  // dW5 += DL^T H3
-    __syncthreads();
-    {  // dH3 = (DL W5) * [H3 > 0], in place
-      float acc[8][4];
-      gemm_tile<4>(sm.DL, kC3Rows, sm.w5, kH, acc);
-      const float* H3 = sm.H3;
-      store_tile<4>(sm.H3, acc, [H3](float v, int n, int m) { return H3[n * kAS + m] > 0.f ? v : 0.f; });
-    }
-    __syncthreads();
-    wgrad_tile<kH, kH, 4, 4>(sm.H3, sm.H2, g4);  // dW4 += dH3^T H2
-    __syncthreads();
-    {  // dH2 = (dH3 W4) * [H2 > 0], in place
-      float acc[8][4];
-      gemm_tile<4>(sm.H3, kH, sm.w4, kH, acc);
-      const float* H2 = sm.H2;
-      store_tile<4>(sm.H2, acc, [H2](float v, int n, int m) { return H2[n * kAS + m] > 0.f ? v : 0.f; });
-    }
-    __syncthreads();
-    wgrad_tile<kH, kCinPad, 1, 5>(sm.H2, sm.OC + kAS, g3);  // dW3 += dH2^T CIN
-    __syncthreads();
-    {  // dOUT[1..15] = (dH2 W3)[0..14]; dOUT[0] = dsigma * sigma (clamp mask)
-      float acc[8][1];
-      gemm_tile<1>(sm.H2, kH, sm.w3, kCinPad, acc);
-      store_tile<1>(sm.OC + kAS, acc, [](float v, int, int) { return v; });  // writes rows 1..16
-    }
-    __syncthreads();
-    if (t < kTile) sm.OC[t] = sm.sig[t];
+    } else {
+      if (t < kTile) {
+        const bool valid = sm.ray[t] != kNoRay;
+        float ds = valid ? S.dsigma[s0 + t] : 0.f;
+        float o0 = sm.OC[t];
+        float dpre = (o0 >= -15.0f && o0 <= 15.0f) ? ds * sm.sig[t] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          float c = sm.rgb[j][t];
+          float dc = valid ? S.drgb[3 * (s0 + t) + j] : 0.f;
+          sm.DL[j * kAS + t] = dc * c * (1.0f - c);
+        }
+        sm.DL[3 * kAS + t] = 0.0f;
+        sm.sig[t] = dpre;  // reuse: dL/d(out_0)
+      }
+      __syncthreads();
+      wgrad_tile<kC3Rows, kH, 1, 1>(sm.DL, sm.H3, g5);  // dW5 += DL^T H3
+      __syncthreads();
+      {  // dH3 = (DL W5) * [H3 > 0], in place
+        float acc[8][4];
+        gemm_tile<4>(sm.DL, kC3Rows, sm.w5, kH, acc);
+        const float* H3 = sm.H3;
+        store_tile<4>(sm.H3, acc, [H3](float v, int n, int m) { return H3[n * kAS + m] > 0.f ? v : 0.f; });
+      }
+      __syncthreads();
+      wgrad_tile<kH, kH, 4, 4>(sm.H3, sm.H2, g4);  // dW4 += dH3^T H2
+      __syncthreads();
+      {  // dH2 = (dH3 W4) * [H2 > 0], in place
+        float acc[8][4];
+        gemm_tile<4>(sm.H3, kH, sm.w4, kH, acc);
+        const float* H2 = sm.H2;
+        store_tile<4>(sm.H2, acc, [H2](float v, int n, int m) { return H2[n * kAS + m] > 0.f ? v : 0.f; });
+      }
+      __syncthreads();
+      wgrad_tile<kH, kCinPad, 1, 5>(sm.H2, sm.OC + kAS, g3);  // dW3 += dH2^T CIN
+      __syncthreads();
+      {  // dOUT[1..15] = (dH2 W3)[0..14]; dOUT[0] = dsigma * sigma (clamp mask)
+        float acc[8][1];
+        gemm_tile<1>(sm.H2, kH, sm.w3, kCinPad, acc);
+        store_tile<1>(sm.OC + kAS, acc, [](float v, int, int) { return v; });  // writes rows 1..16
+      }
+      __syncthreads();
+      if (t < kTile) sm.OC[t] = sm.sig[t];
+    }  // colour net
     __syncthreads();
     wgrad_tile<kDOut, kH, 1, 4>(sm.OC, sm.H1, g2);  // dW2 += dOUT^T H1
     __syncthreads();

@@ -422,7 +422,9 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   if (c->precision != ROMAP_PREC_FP32 && c->precision != ROMAP_PREC_MIXED_BF16 && c->precision != ROMAP_PREC_MIXED_FP8)
     return fail(ROMAP_ERR_INVALID_ARG, "unknown precision %d", c->precision);
   if (c->accuracy_mode != 0 && c->accuracy_mode != 1) return fail(ROMAP_ERR_INVALID_ARG, "accuracy_mode is 0 or 1");
-  if (c->reserved != 0) return fail(ROMAP_ERR_INVALID_ARG, "reserved must be 0");
+  if (c->single_net != 0 && c->single_net != 1) return fail(ROMAP_ERR_INVALID_ARG, "single_net is 0 or 1");
+  if (c->single_net && c->precision == ROMAP_PREC_MIXED_FP8)
+    return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model has no 64x64 hidden layer to run in FP8");
   if (c->max_objects < 1 || c->max_objects > 1024) return fail(ROMAP_ERR_INVALID_ARG, "max_objects must be in 1..1024");
   if (c->max_rays_per_object < 1 || c->max_rays_per_object > (int64_t)1 << 31)
     return fail(ROMAP_ERR_INVALID_ARG, "max_rays_per_object must be in 1..2^31");
@@ -472,6 +474,7 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   for (int k = 0; k < 3; ++k) G.bg_const[k] = c->bg_const[k];
   G.accuracy = c->accuracy_mode ? 1 : 0;
   G.fp8 = c->precision == ROMAP_PREC_MIXED_FP8 ? 1 : 0;
+  G.single_net = c->single_net ? 1 : 0;
   *g = G;
   return ROMAP_OK;
 }
@@ -561,7 +564,7 @@ romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& id
   CUDA_TRY(cudaEventCreate(&e1));
   int best = 0;
   for (int k = 0; k < kNumTileKernels; ++k) {
-    if (ctx->g.fp8 && k != 0) {  // only the lockstep kernel has the FP8 hidden layer
+    if ((ctx->g.fp8 || ctx->g.single_net) && k != 0) {  // only the lockstep kernel has these two variants
       ctx->tile_kernel_ms[k] = 0.f;
       continue;
     }
@@ -1498,6 +1501,8 @@ romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index) {
   ROMAP_TRY(check_ctx(ctx));
   if (index < -1 || index >= kNumTileKernels) return fail(ROMAP_ERR_INVALID_ARG, "tile kernel %d out of range", index);
   if (ctx->g.fp8 && index > 0) return fail(ROMAP_ERR_UNSUPPORTED, "the FP8 precision runs on tile kernel 0 only");
+  if (ctx->g.single_net && index > 0)
+    return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model runs on tile kernel 0 only");
   ctx->tile_kernel = index;
   drop_graph(ctx);
   return ROMAP_OK;

@@ -162,6 +162,7 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
   tmem_wait_ld();
   for (int j = 0; j < 16; ++j)
     if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[1] + j * kH + row, v[j]);
+  if (g.single_net) return;  // no colour net: its accumulators were never written
   for (int c = 0; c < kH; c += 16) {  // dW3^T: rows = colour inputs (cin), 64 columns
     tmem_ld16(lane_base + kColDW3 + c, v);
     tmem_wait_ld();

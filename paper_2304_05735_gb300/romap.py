@@ -44,7 +44,7 @@ class romap_config(C.Structure):
         ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
         ("bg_random", C.c_int32), ("bg_const", C.c_float * 3),
         ("precision", C.c_int32), ("max_objects", C.c_int32), ("max_rays_per_object", C.c_int64),
-        ("accuracy_mode", C.c_int32), ("reserved", C.c_int32),
+        ("accuracy_mode", C.c_int32), ("single_net", C.c_int32),
         ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN), ("alloc_user", C.c_void_p),
     ]
 
@@ -184,7 +184,8 @@ for _name in SIGNATURES:
 def make_config(n_levels=8, log2_table_size=12, base_resolution=16, growth=1.5, max_resolution=0, n_samples=32,
                 rays_per_step=256, dir_dims=3, lambda1=0.5, lambda2=0.01, lr=1e-2, beta1=0.9, beta2=0.99,
                 eps=1e-15, bg_random=False, bg_const=(1.0, 1.0, 1.0), precision=ROMAP_PREC_FP32, max_objects=64,
-                max_rays_per_object=1 << 24, alloc=None, dealloc=None, accuracy_mode=0):
+                max_rays_per_object=1 << 24, alloc=None, dealloc=None, accuracy_mode=0,
+                single_net=False):
     c = romap_config()
     c.n_levels, c.n_features, c.log2_table_size = n_levels, 2, log2_table_size
     c.base_resolution, c.growth, c.max_resolution = base_resolution, growth, max_resolution
@@ -195,7 +196,7 @@ def make_config(n_levels=8, log2_table_size=12, base_resolution=16, growth=1.5, 
     for k in range(3):
         c.bg_const[k] = bg_const[k]
     c.precision, c.max_objects, c.max_rays_per_object = precision, max_objects, max_rays_per_object
-    c.accuracy_mode, c.reserved = int(accuracy_mode), 0
+    c.accuracy_mode, c.single_net = int(accuracy_mode), 1 if single_net else 0
     if alloc is not None:
         c.alloc, c.dealloc = ALLOC_FN(alloc), DEALLOC_FN(dealloc)
     return c

@@ -50,6 +50,7 @@ def test_status_strings_and_null_arguments():
     ("n_samples", 0, R.ROMAP_ERR_INVALID_ARG), ("n_samples", 2000, R.ROMAP_ERR_INVALID_ARG),
     ("lr", 0.0, R.ROMAP_ERR_INVALID_ARG), ("beta1", 1.0, R.ROMAP_ERR_INVALID_ARG),
     ("precision", 7, R.ROMAP_ERR_INVALID_ARG), ("max_objects", 0, R.ROMAP_ERR_INVALID_ARG),
+    ("accuracy_mode", 2, R.ROMAP_ERR_INVALID_ARG), ("single_net", 2, R.ROMAP_ERR_INVALID_ARG),
 ])
 def test_config_validation_is_host_side(field, value, status):
     cfg = R.make_config()
@@ -58,6 +59,14 @@ def test_config_validation_is_host_side(field, value, status):
     assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == status
     out = C.c_void_p()
     assert R.romap_init(C.byref(cfg), None, C.byref(out)) == status
+
+
+def test_single_net_is_not_combined_with_fp8():
+    cfg = R.make_config(precision=R.ROMAP_PREC_MIXED_FP8, single_net=True)
+    lay = R.romap_layout()
+    assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == R.ROMAP_ERR_UNSUPPORTED
+    cfg = R.make_config(precision=R.ROMAP_PREC_MIXED_BF16, single_net=True)
+    assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == R.ROMAP_OK
 
 
 def test_allocator_hooks_must_come_in_pairs():

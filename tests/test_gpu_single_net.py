@@ -1,0 +1,186 @@
+"""The single-network model of Sec. V (one hidden layer of 64 units on the position encoding; the colour logits are
+density-net outputs 1..3, no colour net, no view direction) through the C ABI against the oracle's single-network
+model: FP32 renders and gradients element by element, the FP32 training step, the mixed-precision step and a
+rendered image after training within the mixed tolerances, and colour-net weights that are never updated."""
+import numpy as np
+import pytest
+
+from oracle import romap_oracle as O
+from paper_2304_05735_gb300 import romap as R
+from paper_2304_05735_gb300 import synth
+
+from _harness import FWD_ATOL, FWD_RTOL, Ctx, assert_grad_close, object_frame_pool, paired_config
+
+pytestmark = pytest.mark.gpu
+MIXED = R.ROMAP_PREC_MIXED_BF16
+
+
+@pytest.fixture
+def torch():
+    import torch
+    return torch
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _cos(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+
+
+def _colour_net(oc):
+    """Parameter slice of the colour-net weights (unused by the single-network model)."""
+    nh = O.hash_param_count(oc)
+    return slice(nh + O.mlp_layer_offset(oc, 2), O.param_count(oc))
+
+
+def _rays_at_box(n, rng, half=0.5, miss_frac=0.1):
+    o = np.zeros((n, 3)); d = np.zeros((n, 3))
+    for r in range(n):
+        az, el = rng.uniform(-np.pi, np.pi), rng.uniform(-0.6, 0.9)
+        cam = rng.uniform(1.5, 3.0) * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+        tgt = rng.uniform(-half, half, 3) * (3.0 if rng.uniform() < miss_frac else 0.9)
+        dd = tgt - cam
+        o[r], d[r] = cam, dd / np.linalg.norm(dd)
+    return o.astype(np.float32), d.astype(np.float32)
+
+
+@pytest.mark.parametrize("cfg_kw,N,n", [
+    (dict(L=8, T=2 ** 12, growth=1.5, dir_dims=0), 32, 256),             # plain-method configuration
+    (dict(L=4, T=2 ** 10, growth=2.0, dir_dims=3), 16, 64),              # direction given but unused
+    (dict(L=16, T=2 ** 16, growth=0.0, n_max=512, dir_dims=0), 64, 128),  # multi-object configuration
+])
+def test_fn_forward_backward_single_net(torch, cfg_kw, N, n):
+    oc, rc = paired_config(n_samples=N, single_net=True, **cfg_kw)
+    rng = np.random.default_rng(N + n + 1)
+    o, d = _rays_at_box(n, rng)
+    bg = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    half = np.array([0.5, 0.5, 0.5], np.float32)
+    p64 = O.init_params(oc, 13)
+    nh = O.hash_param_count(oc)
+    p64[:nh] = rng.uniform(-1, 1, nh)
+    p32 = p64.astype(np.float32)
+    up = rng.normal(size=(n, 6)).astype(np.float32)
+    ref = O.rays_loss_grad(oc, p32.astype(np.float64), half, 37, 5, o, d, bg=bg.astype(np.float64),
+                           upstream=up.astype(np.float64), inv_B=1.0, want_samples=True)
+    ctx = Ctx(rc)
+    try:
+        to = lambda a: torch.tensor(a, device="cuda")
+        params = to(p32)
+        out, _, ws = ctx.fn_forward(params, half, 37, 5, to(o), to(d), to(bg))
+        got = out.cpu().numpy()
+        assert np.allclose(got[:, :5], ref["ray"][:, :5], rtol=FWD_RTOL, atol=FWD_ATOL), \
+            np.abs(got[:, :5] - ref["ray"][:, :5]).max()
+        assert np.allclose(got[:, 5], ref["ray"][:, 5], rtol=FWD_RTOL, atol=FWD_ATOL * N)
+        g, ds = ctx.fn_backward(params, half, 37, 5, to(o), to(d), to(bg), ws, to(up))
+        g = g.cpu().numpy()
+        assert_grad_close(g[:nh], ref["grad"][:nh], what="hash gradient")
+        assert_grad_close(g[nh:], ref["grad"][nh:], what="MLP gradient")
+        assert_grad_close(ds.cpu().numpy().reshape(-1), ref["samples"][:, :, 7].reshape(-1), what="dL/dsigma")
+        cs = _colour_net(oc)
+        assert not ref["grad"][cs].any() and not g[cs].any()
+    finally:
+        ctx.close()
+
+
+def test_train_step_single_net_fp32(torch):
+    """One forward+backward+Adam step on the plain-method scene: loss, gradient and updated parameters against the
+    oracle; the colour-net weights keep their values; 30 steps bring the loss below 30% of the first."""
+    oc, rc = paired_config(single_net=True, dir_dims=0)
+    ctx = Ctx(rc)
+    try:
+        sc = synth.config0_scene()
+        oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=0)
+        ctx.add_rays(oid, sc.pool)
+        pool = object_frame_pool(sc)
+        p0 = O.init_params(oc, 0)
+        ref = O.train_step(oc, sc.half.astype(np.float32), 0, 1, pool, p0, np.zeros_like(p0), np.zeros_like(p0))
+        loss = ctx.fwd_bwd([oid])[0]
+        assert np.allclose(loss, ref["loss"], rtol=1e-5, atol=1e-7), (loss, ref["loss"])
+        g = ctx.grad(oid)
+        nh = O.hash_param_count(oc)
+        assert_grad_close(g[:nh], ref["grad"][:nh], what="hash gradient")
+        assert_grad_close(g[nh:], ref["grad"][nh:], what="MLP gradient")
+        ctx.adam([oid])
+        p1, _, _, _ = ctx.state(oid)
+        big = np.abs(ref["grad"]) > 1e-3 * np.abs(ref["grad"]).max()
+        assert np.allclose(p1[big], ref["params"][big], rtol=1e-6, atol=1e-6)
+        cs = _colour_net(oc)
+        assert np.array_equal(p1[cs], p0[cs].astype(np.float32))
+        losses = [ctx.train([oid])[0] for _ in range(30)]
+        assert losses[-1] < 0.3 * losses[0], losses
+        p30, _, _, _ = ctx.state(oid)
+        assert np.array_equal(p30[cs], p0[cs].astype(np.float32))
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("scene", ["plain", "masked"])
+def test_mixed_single_net_step_vs_oracle(torch, scene):
+    if scene == "plain":
+        oc, rc = paired_config(precision=MIXED, single_net=True, dir_dims=0)
+        sc = synth.config0_scene()
+    else:
+        oc, rc = paired_config(L=16, T=2 ** 16, growth=0.0, n_max=512, n_samples=64, rays_per_step=2048,
+                               bg_random=True, precision=MIXED, single_net=True, dir_dims=0)
+        sc = synth.multi_object_scene(1, seed0=5, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2, occluder_prob=1.0)[0]
+    ctx = Ctx(rc)
+    try:
+        assert R.romap_set_tile_kernel(ctx.h, 1) == R.ROMAP_ERR_UNSUPPORTED
+        oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed)
+        ctx.add_rays(oid, sc.pool)
+        pool = object_frame_pool(sc)
+        p0 = O.init_params(oc, sc.seed)
+        loss = ctx.fwd_bwd([oid])[0]
+        ref = O.train_step(oc, sc.half.astype(np.float32), sc.seed, 1, pool, p0, p0 * 0, p0 * 0, do_adam=False)
+        g = ctx.grad(oid)
+        nh = O.hash_param_count(oc)
+        rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
+        rel_h, rel_m = _rel(g[:nh], ref["grad"][:nh]), _rel(g[nh:], ref["grad"][nh:])
+        print(f"\n[{scene}, single net] mixed vs oracle: loss rel {rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
+              f"(cos {_cos(g[:nh], ref['grad'][:nh]):.6f}), mlp-grad rel L2 {rel_m:.2e}")
+        assert rel_loss < 1e-3
+        assert rel_h < 5e-2 and rel_m < 5e-2
+        assert _cos(g, ref["grad"]) > 0.998
+        assert not g[_colour_net(oc)].any()
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, MIXED])
+def test_single_net_rendered_rgb_vs_oracle_after_training(torch, precision):
+    """After 30 training steps (CUDA-graph replays on the mixed path), the next step's per-ray rendered colour and
+    loss against the FP64 oracle on the same FP32 master parameters: the mixed path within 2e-3 absolute RGB and
+    1e-3 relative loss, the FP32 path within its forward tolerance."""
+    oc, rc = paired_config(L=16, T=2 ** 16, growth=0.0, n_max=512, n_samples=64, rays_per_step=2048, bg_random=True,
+                           precision=precision, single_net=True, dir_dims=0)
+    sc = synth.multi_object_scene(1, seed0=6, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2)[0]
+    ctx = Ctx(rc)
+    try:
+        oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed)
+        ctx.add_rays(oid, sc.pool)
+        l30 = ctx.train([oid], n_steps=30)
+        p, m, v, step = ctx.state(oid)
+        loss = ctx.fwd_bwd([oid])[0]
+        n = R.C.c_int64()
+        out = np.zeros((2048, 6), np.float32)
+        R.check(R.romap_last_outputs(ctx.h, oid, out.ctypes.data, R.C.byref(n)))
+        assert n.value == 2048
+        ref = O.train_step(oc, sc.half.astype(np.float32), sc.seed, step + 1, object_frame_pool(sc), p, m, v,
+                           do_adam=False, want_rays=True)
+        err = np.abs(out[:, :3] - ref["rays"][:, :3]).max()
+        rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
+        print(f"\n[single net, {'fp32' if precision == R.ROMAP_PREC_FP32 else 'bf16'}] after 30 steps (loss "
+              f"{l30[0]:.4e}): max |RGB - oracle| {err:.2e}, loss rel {rel_loss:.2e}")
+        if precision == MIXED:
+            assert err < 2e-3 and rel_loss < 1e-3
+        else:
+            assert np.allclose(out[:, :3], ref["rays"][:, :3], rtol=1e-5, atol=1e-5) and rel_loss < 1e-5
+        p0 = O.init_params(oc, sc.seed)
+        cs = _colour_net(oc)
+        assert np.array_equal(p[cs], p0[cs].astype(np.float32))
+    finally:
+        ctx.close()
