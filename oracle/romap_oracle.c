@@ -88,7 +88,7 @@ typedef struct oc_config {
   double lambda1, lambda2;/* Eq. 11 */
   double lr, beta1, beta2, eps; /* Adam */
   int32_t single_net;     /* 1: the paper's model (R-11'): colour logits = density-net outputs 1..3 */
-  int32_t pad_;
+  int32_t hidden_layers;  /* single-network model: hidden layers of width H (1..3, Table 4); 0 reads as 1 */
 } oc_config;
 
 /* ------------------------------------------------------------------ */
@@ -156,15 +156,20 @@ uint64_t oc_hash_param_count(const oc_config* c) {
 }
 /* MLP layers (R-11), row-major [out][in]:
  *   0: density 1  H x (L*F)      1: density 2  (1+geo) x H
- *   2: colour 1   H x (geo+dir)  3: colour 2   H x H        4: colour 3  3 x H */
+ *   2: colour 1   H x (geo+dir)  3: colour 2   H x H        4: colour 3  3 x H
+ * and, for the single-network model with K > 1 hidden layers (Table 4), K - 1 more H x H layers 5, 6 between
+ * the first hidden layer and layer 1 (the colour-net layers 2..4 stay in the layout, unused). */
+int oc_extra_layers(const oc_config* c) {
+  return (c->single_net && c->hidden_layers > 1) ? c->hidden_layers - 1 : 0;
+}
 static void mlp_shape(const oc_config* c, int layer, int* out, int* in) {
   int H = c->hidden, LF = c->L * c->F;
   switch (layer) {
     case 0: *out = H; *in = LF; break;
     case 1: *out = 1 + c->geo; *in = H; break;
     case 2: *out = H; *in = c->geo + c->dir_dims; break;
-    case 3: *out = H; *in = H; break;
-    default: *out = 3; *in = H; break;
+    case 4: *out = 3; *in = H; break;
+    default: *out = H; *in = H; break;  /* 3, 5, 6 */
   }
 }
 uint64_t oc_mlp_layer_offset(const oc_config* c, int layer) {
@@ -172,7 +177,7 @@ uint64_t oc_mlp_layer_offset(const oc_config* c, int layer) {
   for (int i = 0; i < layer; ++i) { int o, n; mlp_shape(c, i, &o, &n); off += (uint64_t)o * n; }
   return off;
 }
-uint64_t oc_mlp_param_count(const oc_config* c) { return oc_mlp_layer_offset(c, 5); }
+uint64_t oc_mlp_param_count(const oc_config* c) { return oc_mlp_layer_offset(c, 5 + oc_extra_layers(c)); }
 uint64_t oc_param_count(const oc_config* c) { return oc_hash_param_count(c) + oc_mlp_param_count(c); }
 
 /* Index of grid vertex (cx, cy, cz) on level l (R-5). */
@@ -197,7 +202,7 @@ void oc_init_params(const oc_config* c, uint64_t seed, double* params) {
     float v = (2.0f * u - 1.0f) * 1e-4f;
     params[k] = (double)v;
   }
-  for (int layer = 0; layer < 5; ++layer) {
+  for (int layer = 0; layer < 5 + oc_extra_layers(c); ++layer) {
     int o, n;
     mlp_shape(c, layer, &o, &n);
     float limit = (float)sqrt(6.0 / (double)(o + n)); /* Glorot-uniform */
@@ -352,6 +357,7 @@ void oc_encode(const oc_config* c, const double* table, const float x[3], const 
 typedef struct oc_act {
   double enc[OC_MAX_LF];
   double h1[OC_MAX_H];        /* after ReLU */
+  double hx[2][OC_MAX_H];     /* single-network model: hidden layers 2 and 3, after ReLU */
   double out[1 + 31];         /* density net outputs (linear) */
   double cin[31 + 3];         /* colour net input */
   double h2[OC_MAX_H], h3[OC_MAX_H];
@@ -381,7 +387,13 @@ void oc_mlp_forward(const oc_config* c, const double* mlp, const double* enc, co
   for (int j = 0; j < LF; ++j) a->enc[j] = enc[j];
   matvec(W0, H, LF, a->enc, a->h1);
   for (int i = 0; i < H; ++i) a->h1[i] = relu(a->h1[i]);
-  matvec(W1, 1 + G, H, a->h1, a->out);
+  const double* last = a->h1;  /* the hidden layer that feeds layer 1 */
+  for (int j = 0; j < oc_extra_layers(c); ++j) {
+    matvec(mlp + oc_mlp_layer_offset(c, 5 + j), H, H, last, a->hx[j]);
+    for (int i = 0; i < H; ++i) a->hx[j][i] = relu(a->hx[j][i]);
+    last = a->hx[j];
+  }
+  matvec(W1, 1 + G, H, last, a->out);
   double o0 = a->out[0];
   if (o0 < -15.0) o0 = -15.0;
   if (o0 > 15.0) o0 = 15.0;
@@ -413,7 +425,8 @@ void oc_mlp_backward(const oc_config* c, const double* mlp, const oc_act* a, dou
   const double* W[5];
   double* gW[5];
   for (int l = 0; l < 5; ++l) { W[l] = mlp + oc_mlp_layer_offset(c, l); gW[l] = gmlp + oc_mlp_layer_offset(c, l); }
-  double glogit[3], gh3[OC_MAX_H], gh2[OC_MAX_H], gcin[34], gout[32], gh1[OC_MAX_H];
+  const int X = oc_extra_layers(c);
+  double glogit[3], gh3[OC_MAX_H], gh2[OC_MAX_H], gcin[34], gout[32], gh1[OC_MAX_H], gx[OC_MAX_H];
   for (int k = 0; k < 3; ++k) glogit[k] = grgb[k] * a->rgb[k] * (1.0 - a->rgb[k]);
   if (c->single_net) {  /* the colour logits are density-net outputs 1..3 */
     for (int j = 0; j < G; ++j) gcin[j] = j < 3 ? glogit[j] : 0.0;
@@ -449,13 +462,28 @@ density_outputs:;
   double o0 = a->out[0];
   gout[0] = (o0 >= -15.0 && o0 <= 15.0) ? gsigma * a->sigma : 0.0;
   for (int j = 0; j < G; ++j) gout[1 + j] = gcin[j];
-  /* layer 1: out = W1 h1 */
+  /* layer 1: out = W1 h, h the last hidden layer (h1 unless the single network has more) */
+  const double* last = X > 0 ? a->hx[X - 1] : a->h1;
   for (int i = 0; i < 1 + G; ++i)
-    for (int j = 0; j < H; ++j) gW[1][i * H + j] += gout[i] * a->h1[j];
+    for (int j = 0; j < H; ++j) gW[1][i * H + j] += gout[i] * last[j];
   for (int j = 0; j < H; ++j) {
     double s = 0.0;
     for (int i = 0; i < 1 + G; ++i) s += W[1][i * H + j] * gout[i];
-    gh1[j] = a->h1[j] > 0.0 ? s : 0.0;
+    gh1[j] = last[j] > 0.0 ? s : 0.0;
+  }
+  /* single-network hidden layers 5 + k, from the last: hx[k] = relu(M hprev), gh1 holding dL/d hx[k] */
+  for (int k = X - 1; k >= 0; --k) {
+    const double* M = mlp + oc_mlp_layer_offset(c, 5 + k);
+    double* gM = gmlp + oc_mlp_layer_offset(c, 5 + k);
+    const double* prev = k > 0 ? a->hx[k - 1] : a->h1;
+    for (int i = 0; i < H; ++i)
+      for (int j = 0; j < H; ++j) gM[i * H + j] += gh1[i] * prev[j];
+    for (int j = 0; j < H; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < H; ++i) s += M[i * H + j] * gh1[i];
+      gx[j] = prev[j] > 0.0 ? s : 0.0;
+    }
+    for (int j = 0; j < H; ++j) gh1[j] = gx[j];
   }
   /* layer 0: h1 = relu(W0 enc) */
   for (int i = 0; i < H; ++i)
@@ -781,10 +809,10 @@ void oc_cell_centre(const float half[3], int ix, int iy, int iz, float x[3]) {
 }
 
 /* sigma = exp(clamp(o_0, -15, 15)) of the density net (R-11, R-13) at one
- * object-frame point: encoding, first layer with ReLU, output 0 of the
- * second layer. */
+ * object-frame point: encoding, first layer with ReLU (then the single
+ * network's further hidden layers), output 0 of layer 1. */
 double oc_density(const oc_config* c, const double* params, const float x[3], const float half[3]) {
-  double enc[OC_MAX_LF], h[OC_MAX_H];
+  double enc[OC_MAX_LF], h[OC_MAX_H], hn[OC_MAX_H];
   int H = c->hidden, LF = c->L * c->F;
   const double* mlp = params + oc_hash_param_count(c);
   const double* W0 = mlp + oc_mlp_layer_offset(c, 0);
@@ -794,6 +822,10 @@ double oc_density(const oc_config* c, const double* params, const float x[3], co
     double s = 0.0;
     for (int j = 0; j < LF; ++j) s += W0[(size_t)i * LF + j] * enc[j];
     h[i] = relu(s);
+  }
+  for (int k = 0; k < oc_extra_layers(c); ++k) {
+    matvec(mlp + oc_mlp_layer_offset(c, 5 + k), H, H, h, hn);
+    for (int i = 0; i < H; ++i) h[i] = relu(hn[i]);
   }
   double o0 = 0.0;
   for (int i = 0; i < H; ++i) o0 += W1[i] * h[i];

@@ -28,7 +28,7 @@ class OracleConfig(C.Structure):
         ("bg_const", C.c_double * 3),
         ("lambda1", C.c_double), ("lambda2", C.c_double),
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
-        ("single_net", C.c_int32), ("pad_", C.c_int32),
+        ("single_net", C.c_int32), ("hidden_layers", C.c_int32),
     ]
 
 
@@ -118,7 +118,7 @@ def level_resolutions(L, n_min, growth=0.0, n_max=0.0):
 
 def make_config(L=8, F=2, T=2 ** 12, n_min=16, growth=1.5, n_max=0.0, n_samples=32, rays_per_step=256,
                 hidden=64, geo=15, dir_dims=3, bg_random=False, bg_const=(1.0, 1.0, 1.0), lambda1=0.5,
-                lambda2=0.01, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, single_net=False):
+                lambda2=0.01, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, single_net=False, hidden_layers=1):
     c = OracleConfig()
     c.L, c.F, c.T = L, F, T
     res = level_resolutions(L, n_min, growth, n_max)
@@ -132,6 +132,8 @@ def make_config(L=8, F=2, T=2 ** 12, n_min=16, growth=1.5, n_max=0.0, n_samples=
     c.lambda1, c.lambda2 = lambda1, lambda2
     c.lr, c.beta1, c.beta2, c.eps = lr, beta1, beta2, eps
     c.single_net = 1 if single_net else 0
+    assert 1 <= hidden_layers <= 3 and (single_net or hidden_layers == 1)
+    c.hidden_layers = int(hidden_layers)
     return c
 
 
@@ -242,7 +244,8 @@ def encode(cfg, table, x, half):
 
 
 class _Act(C.Structure):
-    _fields_ = [("enc", C.c_double * 64), ("h1", C.c_double * 128), ("out", C.c_double * 32),
+    _fields_ = [("enc", C.c_double * 64), ("h1", C.c_double * 128), ("hx", (C.c_double * 128) * 2),
+                ("out", C.c_double * 32),
                 ("cin", C.c_double * 34), ("h2", C.c_double * 128), ("h3", C.c_double * 128),
                 ("logit", C.c_double * 3), ("rgb", C.c_double * 3), ("sigma", C.c_double)]
 

@@ -327,6 +327,8 @@ def test_composite_adjoint_matches_finite_differences():
 def _mlp_weights(cfg, mlp):
     shapes = [(cfg.hidden, cfg.L * cfg.F), (1 + cfg.geo, cfg.hidden), (cfg.hidden, cfg.geo + cfg.dir_dims),
               (cfg.hidden, cfg.hidden), (3, cfg.hidden)]
+    if cfg.single_net:
+        shapes += [(cfg.hidden, cfg.hidden)] * (cfg.hidden_layers - 1)
     Ws, off = [], 0
     for (o, i) in shapes:
         Ws.append(mlp[off:off + o * i].reshape(o, i))
@@ -575,20 +577,25 @@ def test_training_decreases_loss_config0():
     assert losses[-1] < 0.5 * losses[0]
 
 
-def test_single_net_forward_and_backward():
-    """The paper's model (one hidden layer, positions only): sigma from output 0 and the colour sigmoid(outputs
-    1..3) of the density net, against numpy matrix products and torch autograd; the colour-net weights get no
-    gradient."""
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_single_net_forward_and_backward(K):
+    """The paper's model (K hidden layers of 64, positions only; Table 4 times K = 1, 2, 3): sigma from output 0
+    and the colour sigmoid(outputs 1..3) of the density net, against numpy matrix products and torch autograd; the
+    colour-net weights get no gradient."""
     torch = pytest.importorskip("torch")
-    cfg = O.make_config(L=8, T=2 ** 12, dir_dims=0, single_net=True)
-    rng = np.random.default_rng(3)
+    cfg = O.make_config(L=8, T=2 ** 12, dir_dims=0, single_net=True, hidden_layers=K)
+    rng = np.random.default_rng(3 + K)
     nm = O.param_count(cfg) - O.hash_param_count(cfg)
+    assert nm == 64 * 16 + 16 * 64 + 64 * 15 + 64 * 64 + 3 * 64 + (K - 1) * 64 * 64
     mlp = rng.normal(size=nm) * 0.3
     W = _mlp_weights(cfg, mlp)
     for _ in range(5):
         enc = rng.normal(size=16)
         f = O.mlp_forward(cfg, mlp, enc, np.zeros(3, np.float32))
-        out = W[1] @ np.maximum(W[0] @ enc, 0)
+        h = np.maximum(W[0] @ enc, 0)
+        for M in W[5:]:
+            h = np.maximum(M @ h, 0)
+        out = W[1] @ h
         assert np.allclose(f["rgb"], 1 / (1 + np.exp(-out[1:4])), rtol=1e-13)
         assert abs(f["sigma"] - math.exp(min(max(out[0], -15), 15))) < 1e-12 * f["sigma"]
         gsig, grgb = rng.normal(), rng.normal(size=3)
@@ -596,9 +603,49 @@ def test_single_net_forward_and_backward():
         tm = torch.tensor(mlp, dtype=torch.float64, requires_grad=True)
         te = torch.tensor(enc, dtype=torch.float64, requires_grad=True)
         Ws = _mlp_weights(cfg, tm)
-        o = Ws[1] @ torch.relu(Ws[0] @ te)
+        th = torch.relu(Ws[0] @ te)
+        for M in Ws[5:]:
+            th = torch.relu(M @ th)
+        o = Ws[1] @ th
         (gsig * torch.exp(torch.clamp(o[0], -15, 15)) + (torch.tensor(grgb) * torch.sigmoid(o[1:4])).sum()).backward()
         assert np.allclose(gmlp, tm.grad.numpy(), rtol=1e-11, atol=1e-12)
         assert np.allclose(genc, te.grad.numpy(), rtol=1e-11, atol=1e-12)
-        off2 = O.mlp_layer_offset(cfg, 2)
-        assert np.all(gmlp[off2:] == 0.0)
+        off2, off5 = O.mlp_layer_offset(cfg, 2), O.mlp_layer_offset(cfg, 5)
+        assert np.all(gmlp[off2:off5] == 0.0)
+        if K > 1:
+            assert np.any(gmlp[off5:] != 0.0)
+
+
+def test_single_net_identity_hidden_layers_reduce_to_one():
+    """Extra hidden layers equal to c I (c > 0) commute with ReLU: the K-layer network equals the one-layer network
+    whose output layer is scaled by c^(K-1) in the rendered colour, the density (also through the occupancy-grid
+    density) and the gradients of the encoding and the first layer; the output layer's gradient is c^(K-1) times
+    the scaled network's."""
+    cfg1 = O.make_config(L=8, T=2 ** 12, dir_dims=0, single_net=True, hidden_layers=1)
+    rng = np.random.default_rng(17)
+    p1 = O.init_params(cfg1, 2)
+    nh = O.hash_param_count(cfg1)
+    p1[:nh] = rng.uniform(-1, 1, nh)
+    half = np.array([0.5, 0.4, 0.45], np.float32)
+    for K, c in ((2, 1.0), (3, 0.7)):
+        cfgK = O.make_config(L=8, T=2 ** 12, dir_dims=0, single_net=True, hidden_layers=K)
+        pK = np.zeros(O.param_count(cfgK))
+        pK[:p1.size] = p1
+        offs = [nh + O.mlp_layer_offset(cfgK, 5 + k) for k in range(K - 1)]
+        for o in offs:
+            pK[o:o + 64 * 64] = (c * np.eye(64)).reshape(-1)
+        pS = p1.copy()   # one layer, output layer scaled by c^(K-1)
+        o1 = nh + O.mlp_layer_offset(cfg1, 1)
+        pS[o1:o1 + 16 * 64] *= c ** (K - 1)
+        enc = rng.normal(size=16)
+        fK = O.mlp_forward(cfgK, pK[nh:], enc, np.zeros(3, np.float32))
+        fS = O.mlp_forward(cfg1, pS[nh:], enc, np.zeros(3, np.float32))
+        assert np.allclose(fK["rgb"], fS["rgb"], rtol=1e-13) and fK["sigma"] == pytest.approx(fS["sigma"], rel=1e-13)
+        gK, eK = O.mlp_backward(cfgK, pK[nh:], fK, 0.3, np.array([0.1, -0.2, 0.4]))
+        gS, eS = O.mlp_backward(cfg1, pS[nh:], fS, 0.3, np.array([0.1, -0.2, 0.4]))
+        assert np.allclose(eK, eS, rtol=1e-12, atol=1e-15)
+        n0 = 64 * 16
+        assert np.allclose(gK[:n0], gS[:n0], rtol=1e-12, atol=1e-15)       # first layer
+        assert np.allclose(gK[n0:n0 + 1024], gS[n0:n0 + 1024] * c ** (K - 1), rtol=1e-12, atol=1e-15)  # output
+        x = rng.uniform(-0.4, 0.4, 3).astype(np.float32)
+        assert O.density(cfgK, pK, x, half) == pytest.approx(O.density(cfg1, pS, x, half), rel=1e-13)
