@@ -69,7 +69,7 @@ WORKLOADS = {
         log2_tables=(14, 16, 18, 20), base_resolution=16, max_resolution=2048, frames=30, width=320, height=240,
         focal=320.0, occupancy=None, seed0=1, scaling="weak",
         l2="per step 2 to 400 MB of parameters, moments and tables (L2 129 MB)",
-        paper_ms={14: 0.658, 16: 0.706, 18: 0.921, 20: 1.495}),
+        paper_ms={14: 0.658, 16: 0.706, 18: 0.921, 20: 1.495}, paper_layers_ms={2: 0.862, 3: 1.052}),
 }
 WORKLOAD = WORKLOADS["multi8"]
 # FP32 SIMT peak of the GB300: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2070 MHz maximum SM clock.
@@ -231,13 +231,14 @@ def build_items(w, rank, world):
     return items
 
 
-def make_ctx(R, torch, precision, single_net=False):
-    """A context for the current workload; single_net selects the one-hidden-layer, position-only model of
-    Sec. V instead of the density + colour nets."""
+def make_ctx(R, torch, precision, single_net=False, hidden_layers=1):
+    """A context for the current workload; single_net selects the position-only single-network model of Sec. V
+    (hidden_layers hidden layers of 64, Table 4) instead of the density + colour nets."""
     w = WORKLOAD
     rc = R.make_config(n_levels=w["levels"], log2_table_size=w["log2_table"], base_resolution=w["base_resolution"],
                        growth=0.0, max_resolution=w["max_resolution"], n_samples=w["samples_per_ray"],
                        rays_per_step=4096, bg_random=True, single_net=single_net, dir_dims=0 if single_net else 3,
+                       hidden_layers=hidden_layers,
                        precision={"mixed": R.ROMAP_PREC_MIXED_BF16, "fp8": R.ROMAP_PREC_MIXED_FP8}.get(
                            precision, R.ROMAP_PREC_FP32),
                        max_objects=2 * w["objects"])
@@ -825,11 +826,15 @@ def run_table4(args):
     base = dict(WORKLOAD)
     items = build_items(base, 0, 1)
     rows = []
-    for lt in base["log2_tables"]:
-        row = {"log2_table": lt, "paper_ms": base["paper_ms"][lt]}
-        for prec, single in (("mixed", False), ("fp32", False), ("mixed", True), ("fp32", True)):
+    cases = [(lt, 1, base["paper_ms"][lt], ((("mixed", False), ("fp32", False), ("mixed", True), ("fp32", True))))
+             for lt in base["log2_tables"]]
+    # Table 4's last two columns: the single network with 2 and 3 hidden layers at T = 2^16
+    cases += [(16, k, ms, (("mixed", True), ("fp32", True))) for k, ms in base["paper_layers_ms"].items()]
+    for lt, layers, paper_ms, arms in cases:
+        row = {"log2_table": lt, "hidden_layers": layers, "paper_ms": paper_ms}
+        for prec, single in arms:
             WORKLOAD = dict(base, log2_table=lt)
-            rc, h = make_ctx(R, torch, prec, single_net=single)
+            rc, h = make_ctx(R, torch, prec, single_net=single, hidden_layers=layers)
             ids = add_objects(R, h, items)
             arr = (C.c_int32 * 1)(*ids)
             R.check(R.romap_train_step(h, arr, 1, max(args.warmup, 3), None))
@@ -850,11 +855,12 @@ def run_table4(args):
            "scaling": "weak", "vs_baseline": None,
            "dtype": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)",
            "data": "synthetic (analytic shapes, seeded)",
-           "config": {"workload": base["name"], **{k: v for k, v in config_keys(base).items() if k != "paper_ms"}},
+           "config": {"workload": base["name"],
+                      **{k: v for k, v in config_keys(base).items() if k not in ("paper_ms", "paper_layers_ms")}},
            "sweep": rows,
            "note": "value and ms_per_step: T = 2^16, two-net model; single_* columns: the paper's single-network "
-                   "model (one hidden layer, position only), the model its Table 4 times on an RTX 4090 (context, not "
-                   "a target)"}
+                   "model (position only; hidden_layers of 64), the model its Table 4 times on an RTX 4090 (context, "
+                   "not a target)"}
     print(json.dumps(out), flush=True)
 
 

@@ -113,6 +113,10 @@ typedef struct romap_config {
                               only): the colour logits are density-net outputs 1..3 and the colour-net
                               weights are neither read nor updated (their gradient stays 0).  Not
                               combined with ROMAP_PREC_MIXED_FP8. */
+  int32_t hidden_layers;   /* hidden layers of width 64 of the single-network model (1..3, Table 4;
+                              0 reads as 1); must be 0 or 1 when single_net == 0.  Layers 2 and 3 are
+                              64x64 with ReLU, between the first hidden layer and the output layer. */
+  int32_t reserved;        /* 0 */
   /* Optional device allocator (both or neither).  alloc returns NULL on
    * failure, which the library reports as ROMAP_ERR_OOM; a pointer that is
    * not 256-byte aligned is handed back to dealloc and reported as
@@ -150,8 +154,10 @@ typedef struct romap_layout {
   int32_t dense[16];         /* 1 if level l is dense */
   int64_t level_offset[16];  /* first entry of level l: a multiple of 8; entries
                                 between (N_l+1)^3 and the next level are unused */
-  int64_t mlp_offset[5];     /* parameter offset of MLP layers: density 1, density 2, colour 1, colour 2, colour 3 */
-  int32_t mlp_rows[5], mlp_cols[5]; /* row-major [out][in] */
+  int64_t mlp_offset[7];     /* parameter offset of MLP layers: density 1, density 2 (output), colour 1, colour 2,
+                                colour 3, then the single-network model's hidden layers 2 and 3 */
+  int32_t mlp_rows[7], mlp_cols[7]; /* row-major [out][in] */
+  int32_t n_mlp_layers;      /* 5, or 5 + hidden_layers - 1 for the single-network model */
 } romap_layout;
 
 /* Checkpoint of one object: caller-owned arrays of n_params floats each

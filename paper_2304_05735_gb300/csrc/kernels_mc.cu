@@ -18,11 +18,11 @@ constexpr int kRow = 3 * kMcMaxTri + 1;
 __constant__ int8_t c_mc_tri[256 * kRow];
 __constant__ uint8_t c_mc_cnt[256];
 
-template <int LFP>
+template <int LFP, bool XL>
 __global__ void __launch_bounds__(256) k_lattice_density(GridParams g, const ObjectDev* objs, int slot, float* dens) {
-  __shared__ DensityWeights<LFP> sw;
+  __shared__ DensityWeights<LFP, XL> sw;
   const ObjectDev& ob = objs[slot];
-  load_density_weights<LFP>(sw, g, ob.params);
+  load_density_weights<LFP, XL>(sw, g, ob.params);
   __syncthreads();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= kLatN) return;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_lattice_density(GridParams g, const Obj
     const float w = __fdiv_rn(__fsub_rn(ob.half[a], lo), 64.0f);
     x[a] = __fadd_rn(lo, __fmul_rn((float)idx[a], w));
   }
-  dens[v] = density_at<LFP>(sw, g, ob, x);
+  dens[v] = density_at<LFP, XL>(sw, g, ob, x);
 }
 
 // bit d set: the lattice edge from v along axis d crosses the iso-level
@@ -206,8 +206,9 @@ int mc_lattice_points() { return kLatN; }
 
 void launch_lattice_density(const GridParams& g, const ObjectDev* objs, int slot, float* dens, cudaStream_t stream) {
   const int blocks = (kLatN + 255) / 256;
-  if (g.LF <= 16) k_lattice_density<16><<<blocks, 256, 0, stream>>>(g, objs, slot, dens);
-  else k_lattice_density<32><<<blocks, 256, 0, stream>>>(g, objs, slot, dens);
+  auto k = g.LF <= 16 ? (g.extra ? k_lattice_density<16, true> : k_lattice_density<16, false>)
+                      : (g.extra ? k_lattice_density<32, true> : k_lattice_density<32, false>);
+  k<<<blocks, 256, 0, stream>>>(g, objs, slot, dens);
 }
 
 // Counting pass (emit = 0): uploads the case table, evaluates the lattice densities into ws (laid out below) and

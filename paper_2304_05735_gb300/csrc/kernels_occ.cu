@@ -10,12 +10,12 @@ namespace {
 
 constexpr int kCells = 64 * 64 * 64;
 
-template <int LFP>
+template <int LFP, bool XL>
 __global__ void __launch_bounds__(256) k_occ_update(GridParams g, const ObjectDev* objs, int slot, float decay,
                                                    float threshold, int reset, float* dens, uint32_t* bits) {
-  __shared__ DensityWeights<LFP> sw;
+  __shared__ DensityWeights<LFP, XL> sw;
   const ObjectDev& ob = objs[slot];
-  load_density_weights<LFP>(sw, g, ob.params);
+  load_density_weights<LFP, XL>(sw, g, ob.params);
   __syncthreads();
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;  // grid covers exactly kCells
   const int idx[3] = {cell & 63, (cell >> 6) & 63, cell >> 12};
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_occ_update(GridParams g, const ObjectDe
     const float w = __fdiv_rn(__fsub_rn(ob.half[a], lo), 64.0f);
     x[a] = __fadd_rn(lo, __fmul_rn(__fadd_rn((float)idx[a], 0.5f), w));
   }
-  const float sigma = density_at<LFP>(sw, g, ob, x);
+  const float sigma = density_at<LFP, XL>(sw, g, ob, x);
   const float d = reset ? sigma : fmaxf(decay * dens[cell], sigma);
   dens[cell] = d;
   const unsigned m = __ballot_sync(0xffffffffu, d > threshold);
@@ -38,8 +38,9 @@ __global__ void __launch_bounds__(256) k_occ_update(GridParams g, const ObjectDe
 void launch_occ_update(const GridParams& g, const ObjectDev* objs, int slot, float decay, float threshold, int reset,
                        float* dens, uint64_t* bits, cudaStream_t stream) {
   uint32_t* b32 = reinterpret_cast<uint32_t*>(bits);  // word w = halves 2w (cells 64w..64w+31) and 2w+1
-  if (g.LF <= 16) k_occ_update<16><<<kCells / 256, 256, 0, stream>>>(g, objs, slot, decay, threshold, reset, dens, b32);
-  else k_occ_update<32><<<kCells / 256, 256, 0, stream>>>(g, objs, slot, decay, threshold, reset, dens, b32);
+  auto k = g.LF <= 16 ? (g.extra ? k_occ_update<16, true> : k_occ_update<16, false>)
+                      : (g.extra ? k_occ_update<32, true> : k_occ_update<32, false>);
+  k<<<kCells / 256, 256, 0, stream>>>(g, objs, slot, decay, threshold, reset, dens, b32);
 }
 
 }  // namespace romap

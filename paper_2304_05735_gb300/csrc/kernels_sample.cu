@@ -17,8 +17,9 @@ __device__ inline uint32_t philox_word(uint32_t c0, uint32_t c1, uint32_t c2, ui
 
 // ---------------------------------------------------------------------------
 // Parameter initialisation: hash entries U(-1e-4, 1e-4) (counter (k>>2, 0,
-// INIT_HASH, 0), word k&3); MLP layer l Glorot-uniform with limit
-// sqrt(6/(fan_in+fan_out)) (counter (k>>2, l, INIT_MLP, 0), word k&3).
+// INIT_HASH, 0), word k&3); MLP layer l (0..4, and 5..6 for the single-network
+// model's extra hidden layers) Glorot-uniform with limit sqrt(6/(fan_in+fan_out))
+// (counter (k>>2, l, INIT_MLP, 0), word k&3).
 // ---------------------------------------------------------------------------
 __global__ void k_init_params(GridParams g, float* params, uint32_t key0, uint32_t key1, float lim0, float lim1,
                               float lim2, float lim3, float lim4) {
@@ -32,12 +33,13 @@ __global__ void k_init_params(GridParams g, float* params, uint32_t key0, uint32
     if (i >= g.n_hash) {
       int layer = 0;
 #pragma unroll
-      for (int l = 1; l < 5; ++l)
-        if (i >= g.mlp_off[l]) layer = l;
+      for (int l = 1; l < 7; ++l)
+        if (i >= g.mlp_off[l]) layer = l;  // (layers 5, 6 exist only below n_params)
       k = i - g.mlp_off[layer];
       ctr1 = (uint32_t)layer;
       purpose = kPurposeInitMlp;
-      lim = layer == 0 ? lim0 : layer == 1 ? lim1 : layer == 2 ? lim2 : layer == 3 ? lim3 : lim4;
+      // layers 3, 5 and 6 are all 64 x 64
+      lim = layer == 0 ? lim0 : layer == 1 ? lim1 : layer == 2 ? lim2 : layer == 4 ? lim4 : lim3;
     }
     uint32_t x = philox_word((uint32_t)(k >> 2), ctr1, purpose, 0u, key0, key1, (int)(k & 3));
     float u = u01(x);

@@ -103,26 +103,39 @@ __device__ __forceinline__ void zero_rows(unsigned char* E, int s, int l0, int l
   for (int l = l0; l < l1; ++l) *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l, LFP)) = 0u;
 }
 
-template <int LFP, bool FP8>
+template <int LFP, bool FP8, bool SN>
 struct TcSmem {
-  // weights (B operands of the forward), K-major BF16 [out][in]
+  // weights (B operands of the forward), K-major BF16 [out][in]; w4 holds the colour net's 64x64 layer, or the
+  // single-network model's hidden layer 2, and w6() its hidden layer 3
   __align__(128) unsigned char w1[kH * LFP * 2];
   __align__(128) unsigned char w2[16 * kH * 2];
   __align__(128) unsigned char w3[kH * 32 * 2];
   __align__(128) unsigned char w4[kH * kH * 2];
   __align__(128) unsigned char w5[16 * kH * 2];
   TileBufs<LFP> tb[kTilesPerCta];
-  // FP8 E4M3 operands of the hidden 64x64 forward GEMM (ROMAP_PREC_MIXED_FP8): K-major W4 and each tile's H2 rows
+  // FP8 E4M3 operands of the hidden 64x64 forward GEMM (ROMAP_PREC_MIXED_FP8): K-major W4 here, each tile's H2
+  // rows in h2q(u)
   __align__(128) unsigned char w4q[FP8 ? kH * kH : 16];
-  __align__(128) unsigned char h2q[kTilesPerCta][FP8 ? kT * kH : 16];
   float w4_inv[kH];                    // 1 / (448 / max |W4 row n|) for each output n of the loaded object
   __align__(8) uint64_t mbar;
   uint32_t tmem_base;
   int fail;
+  // the single-network model has no colour-net input: tile 0's CIN buffer holds its hidden layer 3 (a separate
+  // buffer would take shared memory from the L1 cache that serves the encoding gathers)
+  __device__ unsigned char* w6() { return tb[0].CIN; }
+  // tile u's H2 rows in FP8 live in its H3 buffer, which is dead from the end of the backward until the epilogue of
+  // the GEMM that reads them writes H3.  Keeping the kernel's shared memory at or below 195 KB leaves the SM's L1
+  // cache, which serves the encoding gathers, at 60 KB instead of 28 KB.
+  __device__ unsigned char* h2q(int u) { return tb[u].H3; }
 };
+static_assert(kT * 32 * 2 == kH * kH * 2, "a 64x64 BF16 layer fits in a CIN buffer");
+static_assert(kT * kH <= kT * kH * 2, "a tile's FP8 H2 rows fit in its H3 buffer");
 
-static_assert(sizeof(TcSmem<32, false>) <= 227 * 1024 && sizeof(TcSmem<32, true>) <= 227 * 1024,
-              "shared memory of the fused kernel");
+// 195 KB plus the 1 KB the system reserves per CTA fit the 196 KB shared-memory carveout; one byte more and the
+// carveout becomes 228 KB, which leaves 28 KB of L1 (measured: the fused step 14% slower)
+static_assert(sizeof(TcSmem<32, false, false>) <= 195 * 1024 && sizeof(TcSmem<32, true, false>) <= 195 * 1024 &&
+                  sizeof(TcSmem<32, false, true>) <= 195 * 1024,
+              "shared memory of the fused kernel above the 196 KB carveout");
 
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -137,6 +150,15 @@ __device__ __forceinline__ uint32_t fp8x4(float a, float b, float c, float d) {
 
 // The FP8 copy of W4, each output row n scaled by 448 / max |W4[n][.]| (4 consecutive threads per row; needs
 // nthreads >= 4 kH and a barrier before the MMA reads it).
+// The single-network model's hidden layer 3 (64 x 64) as K-major BF16.
+template <class Smem>
+__device__ void load_w6(Smem& sm, const GridParams& g, const float* __restrict__ P, int t, int nthreads) {
+  for (int i = t; i < kH * kH; i += nthreads) {
+    int o = i / kH, k = i % kH;
+    *reinterpret_cast<__nv_bfloat16*>(sm.w6() + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[6] + i]);
+  }
+}
+
 template <class Smem>
 __device__ void load_w4_fp8(Smem& sm, const GridParams& g, const float* __restrict__ P, int t, int nthreads) {
   const float* W = P + g.mlp_off[3];
@@ -211,7 +233,7 @@ template <int LFP, bool FP8, bool SN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TcSmem<LFP, FP8>& sm = *reinterpret_cast<TcSmem<LFP, FP8>*>(smem_raw);
+  TcSmem<LFP, FP8, SN>& sm = *reinterpret_cast<TcSmem<LFP, FP8, SN>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int wg = t >> 7;          // tile of the pair
   const int s = t & (kT - 1);     // slot within the tile = TMEM lane
@@ -268,10 +290,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const ObjectDev* nx_ob = &b.objs[b.slot[nx_bi]];
   SlotSample nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
   const int Lg = g.L < LMAX ? g.L : LMAX;
-  // level ranges of the backward windows that overlap the next pair's gather: five with the colour net, two (dH1,
-  // dE) without it
-  constexpr int kWin = SN ? 2 : 5;
-  auto part = [&](int k) { return k * Lg / kWin; };
+  // hidden layers after the first (single-network model) and their activation buffers: hid(u, 0) = H1, 1 = H2,
+  // 2 = H3 of tile u; the last one feeds the density net's output layer
+  const int nl = SN ? g.extra : 0;
+  auto hid = [&](int u, int k) -> unsigned char* { return k == 0 ? sm.tb[u].H1 : k == 1 ? sm.tb[u].H2 : sm.tb[u].H3; };
+  // level ranges of the backward windows that overlap the next pair's gather: five with the colour net; without
+  // it one per hidden layer plus the output layer's
+  const int nwin = SN ? 2 + nl : 5;
+  auto part = [&](int k) { return k * Lg / nwin; };
   int cur = 0;  // encoding buffer of the current pair
   // columns past 2 L stay zero in both buffers
   for (int u = 0; u < 2; ++u) zero_rows<LFP>(tb.E[u], s, Lg, LMAX);
@@ -298,6 +324,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       ob = nx_ob;
       load_weights<LFP>(sm, g, ob->params, kTcThreads);
       if (FP8) load_w4_fp8(sm, g, ob->params, t, kTcThreads);
+      if (SN && g.extra >= 2) load_w6(sm, g, ob->params, t, kTcThreads);
       acc_dw = 0;
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
@@ -319,12 +346,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (!(ok = wait_mma())) break;
     epi_relu64(tmp, tb.H1, s);
+    if constexpr (SN) {  // single-network hidden layers 2 and 3: hid(k + 1) = relu(hid(k) M^T), M = w4, w6
+      for (int k = 0; k < nl; ++k) {
+        sync_then_issue();
+        if (t == 0) {
+          for (int u = 0; u < kTilesPerCta; ++u)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma(tmp_d(u), desc_k(hid(u, k), kH, kk), desc_k(k == 0 ? sm.w4 : sm.w6(), kH, kk), idesc(64, 0, 0),
+                  kk > 0);
+          mma_commit(&sm.mbar);
+        }
+        if (!(ok = wait_mma())) break;
+        epi_relu64(tmp, hid(wg, k + 1), s);
+      }
+      if (!ok) break;
+    }
     sync_then_issue();
-    if (t == 0) {  // L2: H1 W2^T (16 outputs)
+    if (t == 0) {  // L2: HL W2^T (16 outputs), HL = H1 unless the single network has more hidden layers
       for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0), kk > 0);
+          mma(tmp_d(u), desc_k(hid(u, nl), kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
@@ -383,7 +426,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           q.y = fp8x4(h[4] * sc, h[5] * sc, h[6] * sc, h[7] * sc);
           q.z = fp8x4(h[8] * sc, h[9] * sc, h[10] * sc, h[11] * sc);
           q.w = fp8x4(h[12] * sc, h[13] * sc, h[14] * sc, h[15] * sc);
-          *reinterpret_cast<uint4*>(sm.h2q[wg] + kmaj8(s, 16 * c, kH)) = q;
+          *reinterpret_cast<uint4*>(sm.h2q(wg) + kmaj8(s, 16 * c, kH)) = q;
         }
       }
       sync_then_issue();
@@ -392,7 +435,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (FP8) {
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk)
-              mma8(tmp_d(u), desc_k8(sm.h2q[u], kH, kk), desc_k8(sm.w4q, kH, kk), idesc8(64), kk > 0);
+              mma8(tmp_d(u), desc_k8(sm.h2q(u), kH, kk), desc_k8(sm.w4q, kH, kk), idesc8(64), kk > 0);
           } else {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
@@ -532,12 +575,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }  // colour net backward
     sync_then_issue();
-    if (t == 0) {  // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
+    if (t == 0) {  // dHL = dOUT W2 ; dW2^T += HL^T dOUT
       for (int u = 0; u < kTilesPerCta; ++u) {
         mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1), 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW2 + tm, desc_mn(sm.tb[u].H1, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
+          mma(kColDW2 + tm, desc_mn(hid(u, nl), kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
@@ -556,7 +599,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
     if (!(ok = wait_mma())) break;
-    epi_mask64(tmp, tb.H1, s);
+    epi_mask64(tmp, hid(wg, nl), s);
+    if constexpr (SN) {  // hidden layers 3, 2: dhid(k) = dhid(k + 1) M ; dM^T += hid(k)^T dhid(k + 1)
+      for (int k = nl - 1; k >= 0; --k) {
+        sync_then_issue();
+        if (t == 0) {
+          const unsigned char* w = k == 0 ? sm.w4 : sm.w6();
+          const uint32_t col = k == 0 ? kColDW4 : kColDW3;
+          for (int u = 0; u < kTilesPerCta; ++u) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma(tmp_d(u), desc_k(hid(u, k + 1), kH, kk), desc_mn(w, kH, kk), idesc(64, 0, 1), kk > 0);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+              mma(col + tm, desc_mn(hid(u, k), kH, kk), desc_mn(hid(u, k + 1), kH, kk), idesc(64, 1, 1),
+                  (u > 0 || kk > 0) ? 1u : acc_dw);
+          }
+          mma_commit(&sm.mbar);
+        }
+        {  // while the MMAs run: the next part of the next pair's encoding
+          if (has_next && nx.valid) {
+            const float p[3] = {nx.x, nx.y, nx.z};
+            gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(nl - k), part(nl - k + 1));
+          }
+        }
+        if (!(ok = wait_mma())) break;
+        epi_mask64(tmp, hid(wg, k), s);
+      }
+      if (!ok) break;
+    }
     sync_then_issue();
     if (t == 0) {  // dE = dH1 W1 (LFP columns) ; dW1^T += E^T dH1
       for (int u = 0; u < kTilesPerCta; ++u) {
@@ -573,7 +644,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     {  // while the MMAs run: the last part of the next pair's encoding
       if (has_next && nx.valid) {
         const float p[3] = {nx.x, nx.y, nx.z};
-        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(kWin - 1), part(kWin));
+        gather_rows<LFP>(g, nx_ob, p, tb.E[cur ^ 1], s, part(nwin - 1), part(nwin));
       }
     }
     if (!(ok = wait_mma())) break;
@@ -623,7 +694,7 @@ void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
                  int max_tiles, int n_ctas, cudaStream_t stream) {
   // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
   // CTA never waits on another
-  int bytes = (int)sizeof(TcSmem<LFP, FP8>);
+  int bytes = (int)sizeof(TcSmem<LFP, FP8, SN>);
   if (bytes < 116 * 1024) bytes = 116 * 1024;
   static bool attr_set = false;
   if (!attr_set) {

@@ -18,6 +18,8 @@
 
 namespace romap {
 
+constexpr int kW6S = kH + 4;  // row stride of w6: float4-aligned rows, conflict-free column reads
+
 template <int LFP>
 struct TileSmem {
   // weights: row-major [out][in] (backward input gradients) and transposed (forward)
@@ -30,6 +32,7 @@ struct TileSmem {
   float w4[kH * kH];
   float w4t[kH * kH];
   float w5[kC3Rows * kH];
+  float w6[kH * kW6S];    // single-network hidden layer 3, [out][in] only (its forward reads it transposed)
   // activations [feature][sample]
   float E[LFP * kAS];     // encoding, then dL/dencoding
   float H1[kH * kAS];     // density hidden, then its gradient
@@ -43,6 +46,8 @@ struct TileSmem {
   uint32_t ray[kTile];
   int cur_obj;
 };
+
+static_assert(sizeof(TileSmem<32>) <= 227 * 1024, "tile kernel shared memory above the per-CTA limit");
 
 int tile_kernel_smem_bytes(int LF) {
   return LF <= 16 ? (int)sizeof(TileSmem<16>) : (int)sizeof(TileSmem<32>);
@@ -77,6 +82,32 @@ __device__ inline void gemm_tile(const float* __restrict__ A, int K, const float
     } else {
       bv[0] = b[k * ldb];
     }
+    float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(xs[i], bv[j], acc[i][j]);
+  }
+}
+
+// The same product with B given transposed: B[k][n] = BT[n * ldbt + k].
+template <int TN>
+__device__ inline void gemm_tile_bt(const float* __restrict__ A, int K, const float* __restrict__ BT, int ldbt,
+                                    float (&acc)[8][TN]) {
+  const int t = threadIdx.x, mg = t & 15, ng = t >> 4;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+  const float* a = A + 4 * mg;
+  const float* b = BT + TN * ng * ldbt;
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    float4 x0 = *reinterpret_cast<const float4*>(a + k * kAS);
+    float4 x1 = *reinterpret_cast<const float4*>(a + k * kAS + 64);
+    float bv[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) bv[j] = b[j * ldbt + k];
     float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -173,10 +204,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t tile_hi = total_tiles * (blockIdx.x + 1) / gridDim.x;
   const int cin = g.cin;
 
-  // weight-gradient accumulators (per object, flushed on object change)
+  // weight-gradient accumulators (per object, flushed on object change); the single-network model keeps its
+  // hidden layers 2 and 3 in g4 and g6
   constexpr int TO1 = 2, TK1 = LFP / 8;   // dW1: 64 x LFP
-  float g1[TO1][TK1], g2[1][4], g3[1][5], g4[4][4], g5[1][1];
-  zero2(g1); zero2(g2); zero2(g3); zero2(g4); zero2(g5);
+  float g1[TO1][TK1], g2[1][4], g3[1][5], g4[4][4], g5[1][1], g6[4][4];
+  zero2(g1); zero2(g2); zero2(g3); zero2(g4); zero2(g5); zero2(g6);
+  auto flush = [&](float* gm) {
+    wgrad_flush<kH, LFP, TO1, TK1>(gm + g.mlp_off[0], kH, g.LF, g1);
+    wgrad_flush<kDOut, kH, 1, 4>(gm + g.mlp_off[1], kDOut, kH, g2);
+    if (!g.single_net) {
+      wgrad_flush<kH, kCinPad, 1, 5>(gm + g.mlp_off[2], kH, cin, g3);
+      wgrad_flush<kH, kH, 4, 4>(gm + g.mlp_off[3], kH, kH, g4);
+      wgrad_flush<kC3Rows, kH, 1, 1>(gm + g.mlp_off[4], 3, kH, g5);
+    } else {
+      if (g.extra >= 1) wgrad_flush<kH, kH, 4, 4>(gm + g.mlp_off[5], kH, kH, g4);
+      if (g.extra >= 2) wgrad_flush<kH, kH, 4, 4>(gm + g.mlp_off[6], kH, kH, g6);
+    }
+  };
 
   int bi = -1;
   const ObjectDev* ob = nullptr;
@@ -185,14 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int nbi = bi < 0 ? 0 : bi;
     while (nbi + 1 < b.n && tile >= dyn[nbi].tile_base + dyn[nbi].n_tiles) ++nbi;
     if (nbi != bi) {
-      if (MODE == 1 && bi >= 0) {
-        float* gm = ob->grad;
-        wgrad_flush<kH, LFP, TO1, TK1>(gm + g.mlp_off[0], kH, g.LF, g1);
-        wgrad_flush<kDOut, kH, 1, 4>(gm + g.mlp_off[1], kDOut, kH, g2);
-        wgrad_flush<kH, kCinPad, 1, 5>(gm + g.mlp_off[2], kH, cin, g3);
-        wgrad_flush<kH, kH, 4, 4>(gm + g.mlp_off[3], kH, kH, g4);
-        wgrad_flush<kC3Rows, kH, 1, 1>(gm + g.mlp_off[4], 3, kH, g5);
-      }
+      if (MODE == 1 && bi >= 0) flush(ob->grad);
       bi = nbi;
       ob = &b.objs[b.slot[bi]];
       __syncthreads();
@@ -215,13 +252,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         sm.w3[i] = v;
         sm.w3t[k * kH + o] = v;
       }
+      // the colour net's 64 x 64 layer, or the single-network model's hidden layer 2
+      const int64_t off4 = g.extra >= 1 ? g.mlp_off[5] : g.mlp_off[3];
       for (int i = t; i < kH * kH; i += kThreads) {
         int o = i / kH, k = i % kH;
-        float v = P[g.mlp_off[3] + i];
+        float v = P[off4 + i];
         sm.w4[i] = v;
         sm.w4t[k * kH + o] = v;
       }
       for (int i = t; i < kC3Rows * kH; i += kThreads) sm.w5[i] = i < 3 * kH ? P[g.mlp_off[4] + i] : 0.0f;
+      if (g.extra >= 2)
+        for (int i = t; i < kH * kH; i += kThreads) sm.w6[(i / kH) * kW6S + i % kH] = P[g.mlp_off[6] + i];
       __syncthreads();
     }
     const int64_t s0 = (int64_t)tile * kTile;
@@ -277,9 +318,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       store_tile<4>(sm.H1, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
     }
     __syncthreads();
-    {  // OC[0..15] = H1 W2^T
+    float* HL = sm.H1;  // the hidden layer that feeds the density net's output layer
+    if (g.extra >= 1) {  // single-network hidden layer 2: H2 = relu(H1 M1^T)
+      float acc[8][4];
+      gemm_tile<4>(sm.H1, kH, sm.w4t, kH, acc);
+      store_tile<4>(sm.H2, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
+      __syncthreads();
+      HL = sm.H2;
+      if (g.extra >= 2) {  // hidden layer 3: H3 = relu(H2 M2^T)
+        gemm_tile_bt<4>(sm.H2, kH, sm.w6, kW6S, acc);
+        store_tile<4>(sm.H3, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
+        __syncthreads();
+        HL = sm.H3;
+      }
+    }
+    {  // OC[0..15] = HL W2^T
       float acc[8][1];
-      gemm_tile<1>(sm.H1, kH, sm.w2t, kDOut, acc);
+      gemm_tile<1>(HL, kH, sm.w2t, kDOut, acc);
       store_tile<1>(sm.OC, acc, [](float v, int, int) { return v; });
     }
     __syncthreads();
@@ -392,15 +447,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (t < kTile) sm.OC[t] = sm.sig[t];
     }  // colour net
     __syncthreads();
-    wgrad_tile<kDOut, kH, 1, 4>(sm.OC, sm.H1, g2);  // dW2 += dOUT^T H1
+    wgrad_tile<kDOut, kH, 1, 4>(sm.OC, HL, g2);  // dW2 += dOUT^T HL
     __syncthreads();
-    {  // dH1 = (dOUT W2) * [H1 > 0], in place
+    {  // dHL = (dOUT W2) * [HL > 0], in place
       float acc[8][4];
       gemm_tile<4>(sm.OC, kDOut, sm.w2, kH, acc);
-      const float* H1 = sm.H1;
-      store_tile<4>(sm.H1, acc, [H1](float v, int n, int m) { return H1[n * kAS + m] > 0.f ? v : 0.f; });
+      const float* Hf = HL;
+      store_tile<4>(HL, acc, [Hf](float v, int n, int m) { return Hf[n * kAS + m] > 0.f ? v : 0.f; });
     }
     __syncthreads();
+    if (g.extra >= 2) {  // hidden layer 3: dM2 += dH3^T H2; dH2 = (dH3 M2) * [H2 > 0], in place
+      wgrad_tile<kH, kH, 4, 4>(sm.H3, sm.H2, g6);
+      __syncthreads();
+      float acc[8][4];
+      gemm_tile<4>(sm.H3, kH, sm.w6, kW6S, acc);
+      const float* H2 = sm.H2;
+      store_tile<4>(sm.H2, acc, [H2](float v, int n, int m) { return H2[n * kAS + m] > 0.f ? v : 0.f; });
+      __syncthreads();
+    }
+    if (g.extra >= 1) {  // hidden layer 2: dM1 += dH2^T H1; dH1 = (dH2 M1) * [H1 > 0], in place
+      wgrad_tile<kH, kH, 4, 4>(sm.H2, sm.H1, g4);
+      __syncthreads();
+      float acc[8][4];
+      gemm_tile<4>(sm.H2, kH, sm.w4, kH, acc);
+      const float* H1 = sm.H1;
+      store_tile<4>(sm.H1, acc, [H1](float v, int n, int m) { return H1[n * kAS + m] > 0.f ? v : 0.f; });
+      __syncthreads();
+    }
     wgrad_tile<kH, LFP, TO1, TK1>(sm.H1, sm.E, g1);  // dW1 += dH1^T E
     __syncthreads();
     {  // dE = dH1 W1, into E
@@ -426,14 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
   }
-  if (MODE == 1 && bi >= 0) {
-    float* gm = ob->grad;
-    wgrad_flush<kH, LFP, TO1, TK1>(gm + g.mlp_off[0], kH, g.LF, g1);
-    wgrad_flush<kDOut, kH, 1, 4>(gm + g.mlp_off[1], kDOut, kH, g2);
-    wgrad_flush<kH, kCinPad, 1, 5>(gm + g.mlp_off[2], kH, cin, g3);
-    wgrad_flush<kH, kH, 4, 4>(gm + g.mlp_off[3], kH, kH, g4);
-    wgrad_flush<kC3Rows, kH, 1, 1>(gm + g.mlp_off[4], 3, kH, g5);
-  }
+  if (MODE == 1 && bi >= 0) flush(ob->grad);
 }
 
 template <int LFP, int MODE>

@@ -423,6 +423,11 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
     return fail(ROMAP_ERR_INVALID_ARG, "unknown precision %d", c->precision);
   if (c->accuracy_mode != 0 && c->accuracy_mode != 1) return fail(ROMAP_ERR_INVALID_ARG, "accuracy_mode is 0 or 1");
   if (c->single_net != 0 && c->single_net != 1) return fail(ROMAP_ERR_INVALID_ARG, "single_net is 0 or 1");
+  if (c->hidden_layers < 0 || c->hidden_layers > 3)
+    return fail(ROMAP_ERR_INVALID_ARG, "hidden_layers must be in 0..3");
+  if (c->hidden_layers > 1 && !c->single_net)
+    return fail(ROMAP_ERR_UNSUPPORTED, "more than one hidden layer needs the single-network model");
+  if (c->reserved != 0) return fail(ROMAP_ERR_INVALID_ARG, "reserved must be 0");
   if (c->single_net && c->precision == ROMAP_PREC_MIXED_FP8)
     return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model has no 64x64 hidden layer to run in FP8");
   if (c->max_objects < 1 || c->max_objects > 1024) return fail(ROMAP_ERR_INVALID_ARG, "max_objects must be in 1..1024");
@@ -461,7 +466,10 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   G.mlp_off[2] = G.mlp_off[1] + (int64_t)kDOut * kH;
   G.mlp_off[3] = G.mlp_off[2] + (int64_t)kH * G.cin;
   G.mlp_off[4] = G.mlp_off[3] + (int64_t)kH * kH;
-  G.n_params = G.mlp_off[4] + 3 * kH;
+  G.extra = c->single_net && c->hidden_layers > 1 ? c->hidden_layers - 1 : 0;
+  G.mlp_off[5] = G.mlp_off[4] + 3 * kH;
+  G.mlp_off[6] = G.mlp_off[5] + (int64_t)kH * kH;
+  G.n_params = G.mlp_off[5] + (int64_t)G.extra * kH * kH;
   G.n_params_pad = (G.n_params + 3) / 4 * 4;
   G.n_samples = c->n_samples;
   G.lambda1 = c->lambda1;
@@ -720,8 +728,9 @@ romap_status romap_param_layout(const romap_config* cfg, romap_layout* out) {
     out->dense[l] = g.dense[l];
     out->level_offset[l] = g.off[l];
   }
-  int rows[5] = {kH, kDOut, kH, kH, 3}, cols[5] = {g.LF, kH, g.cin, kH, kH};
-  for (int i = 0; i < 5; ++i) {
+  int rows[7] = {kH, kDOut, kH, kH, 3, kH, kH}, cols[7] = {g.LF, kH, g.cin, kH, kH, kH, kH};
+  out->n_mlp_layers = 5 + g.extra;
+  for (int i = 0; i < out->n_mlp_layers; ++i) {
     out->mlp_offset[i] = g.mlp_off[i];
     out->mlp_rows[i] = rows[i];
     out->mlp_cols[i] = cols[i];

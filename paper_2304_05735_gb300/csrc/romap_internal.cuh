@@ -42,7 +42,7 @@ struct GridParams {
   uint32_t off[kMaxL];     // first entry of level l
   int dense[kMaxL];
   int64_t n_hash;          // hash parameters (entries * F)
-  int64_t mlp_off[5];      // absolute parameter offsets of the MLP layers
+  int64_t mlp_off[7];      // absolute parameter offsets of the MLP layers (5, 6: single-network hidden layers 2, 3)
   int64_t n_params;
   int64_t n_params_pad;    // n_params rounded up to a multiple of 4
   int dir_dims, cin;       // cin = 15 + dir_dims
@@ -54,6 +54,7 @@ struct GridParams {
   int accuracy;            // FP64 transmittance log-sum and weights in the FP32 compositing kernel
   int fp8;                 // mixed path: hidden 64x64 forward GEMM in FP8 E4M3
   int single_net;          // colour logits = density-net outputs 1..3; the colour net is skipped
+  int extra;               // single-network hidden layers after the first (0..2), 64x64 each
 };
 
 // One live object as the kernels see it (device-resident, indexed by slot).

@@ -131,9 +131,10 @@ __device__ void load_weights(Smem& sm, const GridParams& g, const float* __restr
     float v = k < g.cin ? P[g.mlp_off[2] + o * g.cin + k] : 0.f;
     *reinterpret_cast<__nv_bfloat16*>(sm.w3 + kmaj(o, k, 32)) = __float2bfloat16_rn(v);
   }
+  const int64_t off4 = g.extra >= 1 ? g.mlp_off[5] : g.mlp_off[3];  // single network: its hidden layer 2
   for (int i = t; i < kH * kH; i += nthreads) {
     int o = i / kH, k = i % kH;
-    *reinterpret_cast<__nv_bfloat16*>(sm.w4 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[3] + i]);
+    *reinterpret_cast<__nv_bfloat16*>(sm.w4 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[off4 + i]);
   }
   for (int i = t; i < 16 * kH; i += nthreads) {
     int o = i / kH, k = i % kH;
@@ -162,7 +163,19 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
   tmem_wait_ld();
   for (int j = 0; j < 16; ++j)
     if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[1] + j * kH + row, v[j]);
-  if (g.single_net) return;  // no colour net: its accumulators were never written
+  if (g.single_net) {  // no colour net; hidden layers 2 and 3 accumulate in the DW4 and DW3 columns
+    for (int x = 0; x < g.extra; ++x) {
+      const uint32_t col = x == 0 ? kColDW4 : kColDW3;
+      float* dst = grad + g.mlp_off[5 + x];
+      for (int c = 0; c < kH; c += 16) {  // dM^T: rows = inputs (64), 64 columns (outputs)
+        tmem_ld16(lane_base + col + c, v);
+        tmem_wait_ld();
+        for (int j = 0; j < 16; ++j)
+          if (v[j] != 0.f) atomicAdd(dst + (c + j) * kH + row, v[j]);
+      }
+    }
+    return;
+  }
   for (int c = 0; c < kH; c += 16) {  // dW3^T: rows = colour inputs (cin), 64 columns
     tmem_ld16(lane_base + kColDW3 + c, v);
     tmem_wait_ld();

@@ -45,6 +45,7 @@ class romap_config(C.Structure):
         ("bg_random", C.c_int32), ("bg_const", C.c_float * 3),
         ("precision", C.c_int32), ("max_objects", C.c_int32), ("max_rays_per_object", C.c_int64),
         ("accuracy_mode", C.c_int32), ("single_net", C.c_int32),
+        ("hidden_layers", C.c_int32), ("reserved", C.c_int32),
         ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN), ("alloc_user", C.c_void_p),
     ]
 
@@ -62,7 +63,8 @@ class romap_rays(C.Structure):
 class romap_layout(C.Structure):
     _fields_ = [("n_params", C.c_int64), ("n_hash_params", C.c_int64), ("n_levels", C.c_int32),
                 ("resolution", C.c_int32 * 16), ("dense", C.c_int32 * 16), ("level_offset", C.c_int64 * 16),
-                ("mlp_offset", C.c_int64 * 5), ("mlp_rows", C.c_int32 * 5), ("mlp_cols", C.c_int32 * 5)]
+                ("mlp_offset", C.c_int64 * 7), ("mlp_rows", C.c_int32 * 7), ("mlp_cols", C.c_int32 * 7),
+                ("n_mlp_layers", C.c_int32)]
 
 
 class romap_state(C.Structure):
@@ -185,7 +187,7 @@ def make_config(n_levels=8, log2_table_size=12, base_resolution=16, growth=1.5, 
                 rays_per_step=256, dir_dims=3, lambda1=0.5, lambda2=0.01, lr=1e-2, beta1=0.9, beta2=0.99,
                 eps=1e-15, bg_random=False, bg_const=(1.0, 1.0, 1.0), precision=ROMAP_PREC_FP32, max_objects=64,
                 max_rays_per_object=1 << 24, alloc=None, dealloc=None, accuracy_mode=0,
-                single_net=False):
+                single_net=False, hidden_layers=1):
     c = romap_config()
     c.n_levels, c.n_features, c.log2_table_size = n_levels, 2, log2_table_size
     c.base_resolution, c.growth, c.max_resolution = base_resolution, growth, max_resolution
@@ -197,6 +199,7 @@ def make_config(n_levels=8, log2_table_size=12, base_resolution=16, growth=1.5, 
         c.bg_const[k] = bg_const[k]
     c.precision, c.max_objects, c.max_rays_per_object = precision, max_objects, max_rays_per_object
     c.accuracy_mode, c.single_net = int(accuracy_mode), 1 if single_net else 0
+    c.hidden_layers, c.reserved = int(hidden_layers), 0
     if alloc is not None:
         c.alloc, c.dealloc = ALLOC_FN(alloc), DEALLOC_FN(dealloc)
     return c

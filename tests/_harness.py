@@ -13,14 +13,16 @@ GRAD_TOL = 1e-4
 
 def paired_config(L=8, T=2 ** 12, n_min=16, growth=1.5, n_max=0, n_samples=32, rays_per_step=256, dir_dims=3,
                   bg_random=False, lambda1=0.5, lambda2=0.01, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15,
-                  max_objects=64, precision=R.ROMAP_PREC_FP32, single_net=False):
+                  max_objects=64, precision=R.ROMAP_PREC_FP32, single_net=False, hidden_layers=1):
     oc = O.make_config(L=L, T=T, n_min=n_min, growth=growth, n_max=n_max, n_samples=n_samples,
                        rays_per_step=rays_per_step, dir_dims=dir_dims, bg_random=bg_random, lambda1=lambda1,
-                       lambda2=lambda2, lr=lr, beta1=beta1, beta2=beta2, eps=eps, single_net=single_net)
+                       lambda2=lambda2, lr=lr, beta1=beta1, beta2=beta2, eps=eps, single_net=single_net,
+                       hidden_layers=hidden_layers)
     rc = R.make_config(n_levels=L, log2_table_size=int(np.log2(T)), base_resolution=n_min, growth=growth,
                        max_resolution=n_max, n_samples=n_samples, rays_per_step=rays_per_step, dir_dims=dir_dims,
                        bg_random=bg_random, lambda1=lambda1, lambda2=lambda2, lr=lr, beta1=beta1, beta2=beta2,
-                       eps=eps, max_objects=max_objects, precision=precision, single_net=single_net)
+                       eps=eps, max_objects=max_objects, precision=precision, single_net=single_net,
+                       hidden_layers=hidden_layers)
     # the oracle takes the loss weights and Adam constants in FP64; feed it the FP32 values the GPU uses
     for name in ("lambda1", "lambda2", "lr", "beta1", "beta2", "eps"):
         setattr(oc, name, float(np.float32(getattr(oc, name))))

@@ -51,6 +51,8 @@ def test_status_strings_and_null_arguments():
     ("lr", 0.0, R.ROMAP_ERR_INVALID_ARG), ("beta1", 1.0, R.ROMAP_ERR_INVALID_ARG),
     ("precision", 7, R.ROMAP_ERR_INVALID_ARG), ("max_objects", 0, R.ROMAP_ERR_INVALID_ARG),
     ("accuracy_mode", 2, R.ROMAP_ERR_INVALID_ARG), ("single_net", 2, R.ROMAP_ERR_INVALID_ARG),
+    ("hidden_layers", 4, R.ROMAP_ERR_INVALID_ARG), ("hidden_layers", 2, R.ROMAP_ERR_UNSUPPORTED),
+    ("reserved", 1, R.ROMAP_ERR_INVALID_ARG),
 ])
 def test_config_validation_is_host_side(field, value, status):
     cfg = R.make_config()
@@ -83,6 +85,11 @@ def test_allocator_hooks_must_come_in_pairs():
     (dict(n_levels=4, log2_table_size=10, base_resolution=16, growth=2.0), dict(L=4, T=2 ** 10, growth=2.0)),
     (dict(n_levels=16, log2_table_size=19, base_resolution=16, growth=0.0, max_resolution=512, dir_dims=0),
      dict(L=16, T=2 ** 19, growth=0.0, n_max=512, dir_dims=0)),
+    (dict(n_levels=8, log2_table_size=12, growth=1.5, dir_dims=0, single_net=True, hidden_layers=2),
+     dict(L=8, T=2 ** 12, growth=1.5, dir_dims=0, single_net=True, hidden_layers=2)),
+    (dict(n_levels=16, log2_table_size=16, growth=0.0, max_resolution=2048, dir_dims=0, single_net=True,
+          hidden_layers=3),
+     dict(L=16, T=2 ** 16, growth=0.0, n_max=2048, dir_dims=0, single_net=True, hidden_layers=3)),
 ])
 def test_param_layout_matches_oracle(kw, okw):
     lay = R.param_layout(R.make_config(**kw))
@@ -93,8 +100,11 @@ def test_param_layout_matches_oracle(kw, okw):
         assert lay.resolution[l] == oc.res[l]
         assert lay.level_offset[l] == O.level_offset(oc, l)
         assert bool(lay.dense[l]) == O.level_is_dense(oc, l)
-    for i in range(5):
+    assert lay.n_mlp_layers == 5 + (okw.get("hidden_layers", 1) - 1)
+    for i in range(lay.n_mlp_layers):
         assert lay.mlp_offset[i] == O.hash_param_count(oc) + O.mlp_layer_offset(oc, i)
+        assert lay.mlp_offset[i] + lay.mlp_rows[i] * lay.mlp_cols[i] == \
+            (O.hash_param_count(oc) + O.mlp_layer_offset(oc, i + 1) if i + 1 < lay.n_mlp_layers else lay.n_params)
 
 
 def test_init_without_gpu_reports_cuda_error():

@@ -1,7 +1,8 @@
-"""The single-network model of Sec. V (one hidden layer of 64 units on the position encoding; the colour logits are
-density-net outputs 1..3, no colour net, no view direction) through the C ABI against the oracle's single-network
-model: FP32 renders and gradients element by element, the FP32 training step, the mixed-precision step and a
-rendered image after training within the mixed tolerances, and colour-net weights that are never updated."""
+"""The single-network model of Sec. V (K = 1 hidden layer of 64 units on the position encoding, and K = 2, 3 as in
+Table 4; the colour logits are density-net outputs 1..3, no colour net, no view direction) through the C ABI against
+the oracle's single-network model: initial parameters bit-exact, FP32 renders and gradients element by element, the
+FP32 training step, the mixed-precision step and a rendered image after training within the mixed tolerances, the
+lattice density of the mesh extraction, and colour-net weights that are never updated."""
 import numpy as np
 import pytest
 
@@ -34,7 +35,7 @@ def _cos(a, b):
 def _colour_net(oc):
     """Parameter slice of the colour-net weights (unused by the single-network model)."""
     nh = O.hash_param_count(oc)
-    return slice(nh + O.mlp_layer_offset(oc, 2), O.param_count(oc))
+    return slice(nh + O.mlp_layer_offset(oc, 2), nh + O.mlp_layer_offset(oc, 5))
 
 
 def _rays_at_box(n, rng, half=0.5, miss_frac=0.1):
@@ -48,10 +49,26 @@ def _rays_at_box(n, rng, half=0.5, miss_frac=0.1):
     return o.astype(np.float32), d.astype(np.float32)
 
 
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_init_params_bit_exact_single_net(torch, K):
+    oc, rc = paired_config(single_net=True, dir_dims=0, hidden_layers=K)
+    ctx = Ctx(rc)
+    try:
+        oid = ctx.create(seed=(5 << 32) + K)
+        p, _, _, _ = ctx.state(oid)
+        ref = O.init_params(oc, (5 << 32) + K)
+        assert p.size == ref.size and np.array_equal(p, ref.astype(np.float32))
+    finally:
+        ctx.close()
+
+
 @pytest.mark.parametrize("cfg_kw,N,n", [
     (dict(L=8, T=2 ** 12, growth=1.5, dir_dims=0), 32, 256),             # plain-method configuration
+    (dict(L=8, T=2 ** 12, growth=1.5, dir_dims=0, hidden_layers=2), 32, 256),
     (dict(L=4, T=2 ** 10, growth=2.0, dir_dims=3), 16, 64),              # direction given but unused
+    (dict(L=4, T=2 ** 10, growth=2.0, dir_dims=3, hidden_layers=3), 16, 64),
     (dict(L=16, T=2 ** 16, growth=0.0, n_max=512, dir_dims=0), 64, 128),  # multi-object configuration
+    (dict(L=16, T=2 ** 16, growth=0.0, n_max=512, dir_dims=0, hidden_layers=3), 64, 128),
 ])
 def test_fn_forward_backward_single_net(torch, cfg_kw, N, n):
     oc, rc = paired_config(n_samples=N, single_net=True, **cfg_kw)
@@ -86,10 +103,11 @@ def test_fn_forward_backward_single_net(torch, cfg_kw, N, n):
         ctx.close()
 
 
-def test_train_step_single_net_fp32(torch):
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_train_step_single_net_fp32(torch, K):
     """One forward+backward+Adam step on the plain-method scene: loss, gradient and updated parameters against the
     oracle; the colour-net weights keep their values; 30 steps bring the loss below 30% of the first."""
-    oc, rc = paired_config(single_net=True, dir_dims=0)
+    oc, rc = paired_config(single_net=True, dir_dims=0, hidden_layers=K)
     ctx = Ctx(rc)
     try:
         sc = synth.config0_scene()
@@ -118,14 +136,15 @@ def test_train_step_single_net_fp32(torch):
         ctx.close()
 
 
+@pytest.mark.parametrize("K", [1, 2, 3])
 @pytest.mark.parametrize("scene", ["plain", "masked"])
-def test_mixed_single_net_step_vs_oracle(torch, scene):
+def test_mixed_single_net_step_vs_oracle(torch, scene, K):
     if scene == "plain":
-        oc, rc = paired_config(precision=MIXED, single_net=True, dir_dims=0)
+        oc, rc = paired_config(precision=MIXED, single_net=True, dir_dims=0, hidden_layers=K)
         sc = synth.config0_scene()
     else:
         oc, rc = paired_config(L=16, T=2 ** 16, growth=0.0, n_max=512, n_samples=64, rays_per_step=2048,
-                               bg_random=True, precision=MIXED, single_net=True, dir_dims=0)
+                               bg_random=True, precision=MIXED, single_net=True, dir_dims=0, hidden_layers=K)
         sc = synth.multi_object_scene(1, seed0=5, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2, occluder_prob=1.0)[0]
     ctx = Ctx(rc)
     try:
@@ -140,23 +159,26 @@ def test_mixed_single_net_step_vs_oracle(torch, scene):
         nh = O.hash_param_count(oc)
         rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
         rel_h, rel_m = _rel(g[:nh], ref["grad"][:nh]), _rel(g[nh:], ref["grad"][nh:])
-        print(f"\n[{scene}, single net] mixed vs oracle: loss rel {rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
+        print(f"\n[{scene}, single net K={K}] mixed vs oracle: loss rel {rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
               f"(cos {_cos(g[:nh], ref['grad'][:nh]):.6f}), mlp-grad rel L2 {rel_m:.2e}")
         assert rel_loss < 1e-3
-        assert rel_h < 5e-2 and rel_m < 5e-2
-        assert _cos(g, ref["grad"]) > 0.998
+        # the first step's hash gradient sums many sample terms that nearly cancel (features start at 1e-4), so the
+        # BF16 roundings of each backward GEMM show up amplified, and each hidden layer adds two more roundings
+        # (measured 2.2e-2, 5.5e-2, 6.2e-2 for K = 1, 2, 3 on the plain scene; 1.0e-2 to 2.8e-2 on the masked one)
+        assert rel_h < (5e-2 if K == 1 else 1e-1) and rel_m < 5e-2
+        assert _cos(g, ref["grad"]) > 0.995
         assert not g[_colour_net(oc)].any()
     finally:
         ctx.close()
 
 
-@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, MIXED])
-def test_single_net_rendered_rgb_vs_oracle_after_training(torch, precision):
+@pytest.mark.parametrize("precision,K", [(R.ROMAP_PREC_FP32, 1), (MIXED, 1), (R.ROMAP_PREC_FP32, 3), (MIXED, 3)])
+def test_single_net_rendered_rgb_vs_oracle_after_training(torch, precision, K):
     """After 30 training steps (CUDA-graph replays on the mixed path), the next step's per-ray rendered colour and
     loss against the FP64 oracle on the same FP32 master parameters: the mixed path within 2e-3 absolute RGB and
     1e-3 relative loss, the FP32 path within its forward tolerance."""
     oc, rc = paired_config(L=16, T=2 ** 16, growth=0.0, n_max=512, n_samples=64, rays_per_step=2048, bg_random=True,
-                           precision=precision, single_net=True, dir_dims=0)
+                           precision=precision, single_net=True, dir_dims=0, hidden_layers=K)
     sc = synth.multi_object_scene(1, seed0=6, n_frames=3, W=80, H=60, f=80.0, depth_frac=0.2)[0]
     ctx = Ctx(rc)
     try:
@@ -173,7 +195,7 @@ def test_single_net_rendered_rgb_vs_oracle_after_training(torch, precision):
                            do_adam=False, want_rays=True)
         err = np.abs(out[:, :3] - ref["rays"][:, :3]).max()
         rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
-        print(f"\n[single net, {'fp32' if precision == R.ROMAP_PREC_FP32 else 'bf16'}] after 30 steps (loss "
+        print(f"\n[single net K={K}, {'fp32' if precision == R.ROMAP_PREC_FP32 else 'bf16'}] after 30 steps (loss "
               f"{l30[0]:.4e}): max |RGB - oracle| {err:.2e}, loss rel {rel_loss:.2e}")
         if precision == MIXED:
             assert err < 2e-3 and rel_loss < 1e-3
@@ -182,5 +204,30 @@ def test_single_net_rendered_rgb_vs_oracle_after_training(torch, precision):
         p0 = O.init_params(oc, sc.seed)
         cs = _colour_net(oc)
         assert np.array_equal(p[cs], p0[cs].astype(np.float32))
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_single_net_lattice_density_vs_oracle(torch, K):
+    """The density the occupancy update and the mesh extraction evaluate goes through the extra hidden layers: the
+    65^3 lattice densities within FP32 tolerance of the oracle's."""
+    oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, single_net=True, dir_dims=0, hidden_layers=K)
+    half = np.array([0.5, 0.4, 0.45], np.float32)
+    rng = np.random.default_rng(30 + K)
+    p = O.init_params(oc, 4)
+    nh = O.hash_param_count(oc)
+    p[:nh] = rng.uniform(-2, 2, nh)
+    p = p.astype(np.float32).astype(np.float64)
+    ctx = Ctx(rc)
+    try:
+        oid = ctx.create(half=tuple(half), seed=4)
+        ctx.set_state(oid, p)
+        d = np.zeros(65 ** 3, np.float32)
+        R.check(R.romap_density_lattice(ctx.h, oid, d.ctypes.data, 0))
+        ref = O.density_lattice(oc, p, half)
+        err = np.max(np.abs(d - ref) / ref)
+        print(f"\n[single net K={K}] lattice density max rel err {err:.2e}")
+        assert err < 5e-5
     finally:
         ctx.close()
