@@ -438,28 +438,27 @@ def run_ours(args):
     if not args.no_e2e:
         rng = np.random.default_rng(100 + rank)
         k_e2e = max(3, min(args.steps, 50))
+        # per step, every object's new rays in one page-locked structure of arrays (objects concatenated), handed
+        # to the library by one romap_add_rays_multi call (one keyframe's observations of all objects)
+        counts = (C.c_int64 * n)(*[it.rays for it in items])
         batches = []
         for _ in range(k_e2e + 2):
-            per = []
-            for it in items:
-                sc = it.scene
-                sel = rng.integers(0, sc.pool["cls"].size, it.rays)
-                arrs = {}
-                for k in ("origin", "dir", "rgb", "depth", "cls"):
-                    a = sc.pool[k][sel]
-                    t = torch.empty(a.shape, dtype=torch.uint8 if k == "cls" else torch.float32, pin_memory=True)
-                    t.numpy()[...] = a
-                    arrs[k] = t
-                per.append(arrs)
-            batches.append(per)
-        h2d = sum(t.numel() * t.element_size() for per in batches[:1] for arrs in per for t in arrs.values())
+            arrs = {}
+            sels = [rng.integers(0, it.scene.pool["cls"].size, it.rays) for it in items]
+            for k in ("origin", "dir", "rgb", "depth", "cls"):
+                a = np.concatenate([it.scene.pool[k][sel] for it, sel in zip(items, sels)])
+                t = torch.empty(a.shape, dtype=torch.uint8 if k == "cls" else torch.float32, pin_memory=True)
+                t.numpy()[...] = a
+                arrs[k] = t
+            batches.append(arrs)
+        h2d = sum(t.numel() * t.element_size() for t in batches[0].values())
         loss = np.zeros(n, np.float32)
 
-        def e2e_step(per):
-            for i, it, arrs in zip(ids, items, per):
-                rays = R.romap_rays(arrs["origin"].data_ptr(), arrs["dir"].data_ptr(), arrs["rgb"].data_ptr(),
-                                    arrs["depth"].data_ptr(), arrs["cls"].data_ptr())
-                R.check(R.romap_add_rays(h, i, C.byref(rays), it.rays, R.ROMAP_REPLACE), "romap_add_rays")
+        def e2e_step(arrs):
+            rays = R.romap_rays(arrs["origin"].data_ptr(), arrs["dir"].data_ptr(), arrs["rgb"].data_ptr(),
+                                arrs["depth"].data_ptr(), arrs["cls"].data_ptr())
+            R.check(R.romap_add_rays_multi(h, idarr, counts, n, C.byref(rays), R.ROMAP_REPLACE),
+                    "romap_add_rays_multi")
             R.check(R.romap_train_step(h, idarr, n, 1, loss.ctypes.data), "romap_train_step")
 
         for per in batches[:2]:
@@ -479,7 +478,8 @@ def run_ours(args):
         live_e = allsum(torch, dist, world, ste.live_samples)
         e2e = {"value": live_e / el, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(n * 48 + 4), "steps": k_e2e,
-               "path": f"romap_add_rays(REPLACE, pinned host) x {n} + romap_train_step(out_loss to host), wall clock"}
+               "path": f"romap_add_rays_multi(REPLACE, pinned host, {n} objects) + romap_train_step(out_loss to "
+                       f"host), wall clock"}
 
     # ---- mesh extraction of the trained objects (Table 3: marching cubes at 64^3) -----------------------------------
     mesh = None

@@ -219,6 +219,17 @@ ROMAP_API romap_status romap_get_occupancy(romap_ctx* ctx, int32_t id, uint64_t*
  * replaces the pool with ROMAP_REPLACE.  Rays are moved to the object frame
  * and their directions normalised on the device. */
 ROMAP_API romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* rays, int64_t n, uint32_t flags);
+/* romap_add_rays for several objects in one call: one keyframe's rays of
+ * every object it shows (Sec. V-A-1 feeds each object's model the rays of
+ * its detection box in every new keyframe).  rays holds the concatenation:
+ * counts[k] rays of object ids[k] follow the counts[k-1] rays of ids[k-1].
+ * n_ids distinct ids (else ROMAP_ERR_INVALID_ARG), counts[k] >= 0 (0 leaves
+ * the pool, or with ROMAP_REPLACE empties it).  Flags, host checks and
+ * ownership as romap_add_rays; host arrays are copied once and every
+ * object's rays are transformed by one launch.  Every argument and capacity
+ * is checked before any pool changes. */
+ROMAP_API romap_status romap_add_rays_multi(romap_ctx* ctx, const int32_t* ids, const int64_t* counts, int32_t n_ids,
+                                            const romap_rays* rays, uint32_t flags);
 ROMAP_API romap_status romap_pool_size(romap_ctx* ctx, int32_t id, int64_t* out_n);
 
 /* ---- training (Sec. V-A, V-B; Eq. 6-11; Adam) -------------------------- */
@@ -393,9 +404,14 @@ ROMAP_API romap_status romap_reset_stats(romap_ctx* ctx);
  * returns.  Returns ROMAP_ERR_TIMEOUT when the device reported the time-out
  * (the expected outcome); the context stays usable. */
 ROMAP_API romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_limit);
-/* Forces candidate `index` (0 = lockstep tile pairs, 1 = warp-specialized),
- * or -1 to autotune again at the next mixed step.  ROMAP_ERR_UNSUPPORTED for
- * index 1 under ROMAP_PREC_MIXED_FP8 or single_net (both run on kernel 0). */
+/* Forces candidate `index`, or -1 to autotune again at the next mixed
+ * step.  Candidates: 0 = lockstep tile pairs, 1 = warp-specialized, each
+ * giving every CTA a contiguous range of the tile plan; 2 and 3 = the same
+ * kernels with the plan interleaved over the CTAs (CTA c takes every
+ * grid-th pair or tile from c, so all CTAs work on the same few objects at
+ * a time).  ROMAP_ERR_UNSUPPORTED for the warp-specialized candidates (1, 3)
+ * under ROMAP_PREC_MIXED_FP8 or single_net (both run on the lockstep
+ * kernel). */
 ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);
 ROMAP_API romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, int32_t n, char* names,
                                              size_t names_len);

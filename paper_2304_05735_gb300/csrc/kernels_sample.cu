@@ -60,13 +60,13 @@ void launch_init_params(const GridParams& g, float* params, uint32_t key0, uint3
 // World -> object frame (Sec. IV-B pose: translation t, yaw about z):
 // x_o = R_z^T (x_w - t), d_o = R_z^T d_w / |R_z^T d_w|.
 // ---------------------------------------------------------------------------
-__global__ void k_transform_rays(const float* __restrict__ o_in, const float* __restrict__ d_in,
-                                 const float* __restrict__ rgb_in, const float* __restrict__ depth_in,
-                                 const uint8_t* __restrict__ cls_in, int64_t n, int object_frame, float tx, float ty,
-                                 float tz, float cz, float sz, float* o_out, float* d_out, float* rgb_out,
-                                 float* depth_out, uint8_t* cls_out) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+// Ray r of the inputs -> ray w of the outputs.
+__device__ __forceinline__ void transform_ray(const float* __restrict__ o_in, const float* __restrict__ d_in,
+                                              const float* __restrict__ rgb_in, const float* __restrict__ depth_in,
+                                              const uint8_t* __restrict__ cls_in, int64_t r, int object_frame,
+                                              float tx, float ty, float tz, float cz, float sz, float* o_out,
+                                              float* d_out, float* rgb_out, float* depth_out, uint8_t* cls_out,
+                                              int64_t w) {
   float ox = o_in[3 * r], oy = o_in[3 * r + 1], oz = o_in[3 * r + 2];
   float dx = d_in[3 * r], dy = d_in[3 * r + 1], dz = d_in[3 * r + 2];
   float rx = dx, ry = dy, rz = dz;
@@ -80,15 +80,45 @@ __global__ void k_transform_rays(const float* __restrict__ o_in, const float* __
     rz = dz;
   }
   float len = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)), __fmul_rn(rz, rz)));
-  o_out[3 * r] = ox; o_out[3 * r + 1] = oy; o_out[3 * r + 2] = oz;
-  d_out[3 * r] = __fdiv_rn(rx, len);
-  d_out[3 * r + 1] = __fdiv_rn(ry, len);
-  d_out[3 * r + 2] = __fdiv_rn(rz, len);
-  rgb_out[3 * r] = rgb_in ? rgb_in[3 * r] : 0.0f;
-  rgb_out[3 * r + 1] = rgb_in ? rgb_in[3 * r + 1] : 0.0f;
-  rgb_out[3 * r + 2] = rgb_in ? rgb_in[3 * r + 2] : 0.0f;
-  depth_out[r] = depth_in ? depth_in[r] : __int_as_float(0x7fc00000);
-  cls_out[r] = cls_in ? cls_in[r] : (uint8_t)kClsObject;
+  o_out[3 * w] = ox; o_out[3 * w + 1] = oy; o_out[3 * w + 2] = oz;
+  d_out[3 * w] = __fdiv_rn(rx, len);
+  d_out[3 * w + 1] = __fdiv_rn(ry, len);
+  d_out[3 * w + 2] = __fdiv_rn(rz, len);
+  rgb_out[3 * w] = rgb_in ? rgb_in[3 * r] : 0.0f;
+  rgb_out[3 * w + 1] = rgb_in ? rgb_in[3 * r + 1] : 0.0f;
+  rgb_out[3 * w + 2] = rgb_in ? rgb_in[3 * r + 2] : 0.0f;
+  depth_out[w] = depth_in ? depth_in[r] : __int_as_float(0x7fc00000);
+  cls_out[w] = cls_in ? cls_in[r] : (uint8_t)kClsObject;
+}
+
+__global__ void k_transform_rays(const float* __restrict__ o_in, const float* __restrict__ d_in,
+                                 const float* __restrict__ rgb_in, const float* __restrict__ depth_in,
+                                 const uint8_t* __restrict__ cls_in, int64_t n, int object_frame, float tx, float ty,
+                                 float tz, float cz, float sz, float* o_out, float* d_out, float* rgb_out,
+                                 float* depth_out, uint8_t* cls_out) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  transform_ray(o_in, d_in, rgb_in, depth_in, cls_in, r, object_frame, tx, ty, tz, cz, sz, o_out, d_out, rgb_out,
+                depth_out, cls_out, r);
+}
+
+// Several objects' rays, concatenated in the inputs: xo[k] (sorted by first, no empty ranges) says where object k's
+// range starts, its pose and where its rays go in its pool.
+__global__ void k_transform_rays_multi(const float* __restrict__ o_in, const float* __restrict__ d_in,
+                                       const float* __restrict__ rgb_in, const float* __restrict__ depth_in,
+                                       const uint8_t* __restrict__ cls_in, int64_t n, int object_frame,
+                                       const XformObj* __restrict__ xo, int n_obj) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int lo = 0, hi = n_obj - 1;  // the last k with xo[k].first <= r
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (xo[mid].first <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  const XformObj& x = xo[lo];
+  transform_ray(o_in, d_in, rgb_in, depth_in, cls_in, r, object_frame, x.t[0], x.t[1], x.t[2], x.cz, x.sz, x.o_out,
+                x.d_out, x.rgb_out, x.depth_out, x.cls_out, r - x.first);
 }
 
 void launch_transform_rays(const float* o_in, const float* d_in, const float* rgb_in, const float* depth_in,
@@ -99,6 +129,15 @@ void launch_transform_rays(const float* o_in, const float* d_in, const float* rg
   int64_t blocks = (n + 255) / 256;
   k_transform_rays<<<(unsigned)blocks, 256, 0, stream>>>(o_in, d_in, rgb_in, depth_in, cls_in, n, object_frame, tx,
                                                          ty, tz, cz, sz, o_out, d_out, rgb_out, depth_out, cls_out);
+}
+
+void launch_transform_rays_multi(const float* o_in, const float* d_in, const float* rgb_in, const float* depth_in,
+                                 const uint8_t* cls_in, int64_t n, int object_frame, const XformObj* xo, int n_obj,
+                                 cudaStream_t stream) {
+  if (n <= 0 || n_obj <= 0) return;
+  int64_t blocks = (n + 255) / 256;
+  k_transform_rays_multi<<<(unsigned)blocks, 256, 0, stream>>>(o_in, d_in, rgb_in, depth_in, cls_in, n, object_frame,
+                                                               xo, n_obj);
 }
 
 // Block-wide exclusive scan of 256 values.

@@ -231,16 +231,19 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 
 template <int LFP, bool FP8, bool SN>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status) {
+    k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int interleave) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem<LFP, FP8, SN>& sm = *reinterpret_cast<TcSmem<LFP, FP8, SN>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int wg = t >> 7;          // tile of the pair
   const int s = t & (kT - 1);     // slot within the tile = TMEM lane
   TileBufs<LFP>& tb = sm.tb[wg];
+  // pairs of this CTA: a contiguous range of the plan, or (interleave) every gridDim.x-th pair from blockIdx.x, so
+  // that all CTAs work on the same few objects at a time and those objects' tables and gradients stay in L2
   const int total_pairs = *b.plan_npairs;
-  const int pair_lo = (int)((int64_t)total_pairs * blockIdx.x / gridDim.x);
-  const int pair_hi = (int)((int64_t)total_pairs * (blockIdx.x + 1) / gridDim.x);
+  const int pair_lo = interleave ? (int)blockIdx.x : (int)((int64_t)total_pairs * blockIdx.x / gridDim.x);
+  const int pair_hi = interleave ? total_pairs : (int)((int64_t)total_pairs * (blockIdx.x + 1) / gridDim.x);
+  const int pair_step = interleave ? (int)gridDim.x : 1;
   if (pair_lo >= pair_hi) return;
 
   if (t == 0) {
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     zero_rows<LFP>(tb.E[0], s, 0, Lg);
   }
-  for (int pair = pair_lo; pair < pair_hi && ok; ++pair) {
+  for (int pair = pair_lo; pair < pair_hi && ok; pair += pair_step) {
     // ---- 1-2. the prepared sample and encoding of this pair -> tile buffers ---------------------------------------
     tb.valid[s] = nx.valid;
     tb.ray[s] = nx.ray;
@@ -329,9 +332,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
-    const bool has_next = pair + 1 < pair_hi;
+    const bool has_next = pair + pair_step < pair_hi;
     if (has_next) {
-      nx_ti = b.plan_tiles[(pair + 1) * kTilesPerCta + wg];
+      nx_ti = b.plan_tiles[(pair + pair_step) * kTilesPerCta + wg];
       nx_bi = nx_ti.x;
       nx_ob = &b.objs[b.slot[nx_bi]];
     }
@@ -691,7 +694,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 template <int LFP, bool FP8, bool SN>
 void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
-                 int max_tiles, int n_ctas, cudaStream_t stream) {
+                 int max_tiles, int n_ctas, int interleave, cudaStream_t stream) {
   // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
   // CTA never waits on another
   int bytes = (int)sizeof(TcSmem<LFP, FP8, SN>);
@@ -705,7 +708,7 @@ void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
   const int max_pairs = (max_tiles + kTilesPerCta - 1) / kTilesPerCta;
   int grid = n_ctas < max_pairs ? n_ctas : max_pairs;
   if (grid < 1) return;
-  k_tile_tc<LFP, FP8, SN><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status);
+  k_tile_tc<LFP, FP8, SN><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status, interleave);
 }
 
 // Places every ray of the batch in the tile plan: rays with live samples go to their class's position in
@@ -747,16 +750,16 @@ __global__ void __launch_bounds__(256) k_plan_rays(GridParams g, BatchDesc b, Ra
 
 
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
-                    int max_tiles, int n_ctas, cudaStream_t stream) {
+                    int max_tiles, int n_ctas, int interleave, cudaStream_t stream) {
   if (g.fp8) {  // (the single-network model is never combined with FP8)
-    if (g.LF <= 16) launch_tc_t<16, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
-    else launch_tc_t<32, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    if (g.LF <= 16) launch_tc_t<16, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_tc_t<32, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
   } else if (g.single_net) {
-    if (g.LF <= 16) launch_tc_t<16, false, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
-    else launch_tc_t<32, false, true>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    if (g.LF <= 16) launch_tc_t<16, false, true>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_tc_t<32, false, true>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
   } else {
-    if (g.LF <= 16) launch_tc_t<16, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
-    else launch_tc_t<32, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+    if (g.LF <= 16) launch_tc_t<16, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_tc_t<32, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
   }
 }
 

@@ -97,7 +97,7 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 // ---------------------------------------------------------------------------------------------------------------
 template <int LFP>
 __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, const RayBuf& R, int tile_lo,
-                            int n) {
+                            int tile_step, int n) {
   const int s = threadIdx.x - kCompute;
   constexpr int LMAX = LFP / 2;
   for (int k = 0; k < n + 2; ++k) {
@@ -110,7 +110,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
         break;
       }
       if (sl.valid[s]) {
-        const ObjectDev* ob = &b.objs[b.slot[b.plan_tiles[tile_lo + k - 2].x]];
+        const ObjectDev* ob = &b.objs[b.slot[b.plan_tiles[tile_lo + (k - 2) * tile_step].x]];
         const float p[3] = {sl.px[0][s], sl.px[1][s], sl.px[2][s]};
         float2* gt = reinterpret_cast<float2*>(ob->grad);
         float de[LFP];
@@ -131,7 +131,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
       }
     }
     if (k < n) {
-      const int4 ti = b.plan_tiles[tile_lo + k];
+      const int4 ti = b.plan_tiles[tile_lo + k * tile_step];
       const ObjectDev* ob = &b.objs[b.slot[ti.x]];
       const SlotSample q = plan_sample(g, b, R, ob, ti.x, ti, s);
       if (s == 0) {
@@ -164,7 +164,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
 // ---------------------------------------------------------------------------------------------------------------
 template <int LFP>
 __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf R,
-                             int32_t* status, int tile_lo, int n, uint32_t& phase, bool& pending) {
+                             int32_t* status, int tile_lo, int tile_step, int n, uint32_t& phase, bool& pending) {
   const int s = threadIdx.x, warp = s >> 5;
   const uint32_t tm = sm.tmem_base;
   const uint32_t tmp = tm + ((uint32_t)(32 * warp) << 16) + kColTmp;
@@ -387,14 +387,16 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
 
 template <int LFP>
 __global__ void __launch_bounds__(kWsThreads, 1)
-    k_tile_ws(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status) {
+    k_tile_ws(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int interleave) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   WsSmem<LFP>& sm = *reinterpret_cast<WsSmem<LFP>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int total_tiles = 2 * *b.plan_npairs;
-  const int tile_lo = (int)((int64_t)total_tiles * blockIdx.x / gridDim.x);
-  const int tile_hi = (int)((int64_t)total_tiles * (blockIdx.x + 1) / gridDim.x);
-  const int n = tile_hi - tile_lo;
+  // tiles of this CTA: a contiguous range of the plan, or (interleave) every gridDim.x-th tile from blockIdx.x
+  const int tile_lo = interleave ? (int)blockIdx.x : (int)((int64_t)total_tiles * blockIdx.x / gridDim.x);
+  const int tile_hi = interleave ? total_tiles : (int)((int64_t)total_tiles * (blockIdx.x + 1) / gridDim.x);
+  const int tile_step = interleave ? (int)gridDim.x : 1;
+  const int n = tile_hi > tile_lo ? (tile_hi - tile_lo + tile_step - 1) / tile_step : 0;
   if (n <= 0) return;
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mma_bar)));
@@ -416,8 +418,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   tc_after();
   uint32_t phase = 0;
   bool pending = false;
-  if (warp < 4) compute_role<LFP>(sm, g, b, dyn, R, status, tile_lo, n, phase, pending);
-  else memory_role<LFP>(sm, g, b, R, tile_lo, n);
+  if (warp < 4) compute_role<LFP>(sm, g, b, dyn, R, status, tile_lo, tile_step, n, phase, pending);
+  else memory_role<LFP>(sm, g, b, R, tile_lo, tile_step, n);
   if (t == 0 && sm.fail) {
     if (status) atomicOr(status, 2);
     if (pending) mbar_wait(&sm.mma_bar, phase ^ 1u);  // bounded: let MMAs in flight finish before freeing TMEM
@@ -431,7 +433,7 @@ static_assert(offsetof(WsSlot<16>, dE) % 16 == 0 && offsetof(WsSlot<32>, dE) % 1
 
 template <int LFP>
 void launch_ws_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int max_tiles,
-                 int n_ctas, cudaStream_t stream) {
+                 int n_ctas, int interleave, cudaStream_t stream) {
   int bytes = (int)sizeof(WsSmem<LFP>);
   if (bytes < 116 * 1024) bytes = 116 * 1024;  // one CTA per SM: the 512-column TMEM allocation never waits
   static bool attr_set = false;
@@ -442,15 +444,15 @@ void launch_ws_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
   // the plan's tile count is read on the device; max_tiles only bounds the grid
   int grid = n_ctas < max_tiles ? n_ctas : max_tiles;
   if (grid < 1) return;
-  k_tile_ws<LFP><<<grid, kWsThreads, bytes, stream>>>(g, b, dyn, r, status);
+  k_tile_ws<LFP><<<grid, kWsThreads, bytes, stream>>>(g, b, dyn, r, status, interleave);
 }
 
 }  // namespace
 
 void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
-                    int max_tiles, int n_ctas, cudaStream_t stream) {
-  if (g.LF <= 16) launch_ws_t<16>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
-  else launch_ws_t<32>(g, b, dyn, r, status, max_tiles, n_ctas, stream);
+                    int max_tiles, int n_ctas, int interleave, cudaStream_t stream) {
+  if (g.LF <= 16) launch_ws_t<16>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+  else launch_ws_t<32>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
 }
 
 }  // namespace romap

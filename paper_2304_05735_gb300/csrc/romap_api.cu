@@ -537,12 +537,23 @@ romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBu
 
 int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
 
-// Candidate fused tile kernels of the mixed path (same results, different schedules).
+// Candidate fused tile kernels of the mixed path (same results, different schedules): the two kernels, each with
+// contiguous per-CTA ranges of the tile plan or with the plan interleaved over the CTAs.  Even indices are the
+// lockstep kernel, the only one with the FP8 and single-network variants.
 typedef void (*TileKernelFn)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int,
                              cudaStream_t);
-const TileKernelFn kTileKernels[] = {launch_tile_tc, launch_tile_ws};
-const char* const kTileKernelNames[] = {"lockstep tile pairs", "warp-specialized"};
-constexpr int kNumTileKernels = 2;
+template <void (*F)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int, int, cudaStream_t),
+          int IL>
+void launch_tile_order(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
+                       int max_tiles, int n_ctas, cudaStream_t stream) {
+  F(g, b, dyn, r, status, max_tiles, n_ctas, IL, stream);
+}
+const TileKernelFn kTileKernels[] = {launch_tile_order<launch_tile_tc, 0>, launch_tile_order<launch_tile_ws, 0>,
+                                     launch_tile_order<launch_tile_tc, 1>, launch_tile_order<launch_tile_ws, 1>};
+const char* const kTileKernelNames[] = {"lockstep tile pairs", "warp-specialized", "lockstep tile pairs, interleaved",
+                                        "warp-specialized, interleaved"};
+constexpr int kNumTileKernels = 4;
+bool lockstep_kernel(int k) { return k % 2 == 0; }
 
 // Sampling stage of the mixed path: ray draw + slab + live counts and masks, the per-object scan (live-sample
 // counter, loss reset) with the tile plan, and the placement of every ray in the plan.  Samples are formed inside the
@@ -572,7 +583,7 @@ romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& id
   CUDA_TRY(cudaEventCreate(&e1));
   int best = 0;
   for (int k = 0; k < kNumTileKernels; ++k) {
-    if ((ctx->g.fp8 || ctx->g.single_net) && k != 0) {  // only the lockstep kernel has these two variants
+    if ((ctx->g.fp8 || ctx->g.single_net) && !lockstep_kernel(k)) {  // only the lockstep kernel has these variants
       ctx->tile_kernel_ms[k] = 0.f;
       continue;
     }
@@ -992,6 +1003,116 @@ romap_status romap_extract_mesh(romap_ctx* ctx, int32_t id, float iso, float* ve
   return ROMAP_OK;
 }
 
+namespace {
+
+bool finite_bits(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  return (b & 0x7f800000u) != 0x7f800000u;
+}
+
+// Host ray arrays (n rays): origin, direction and colour finite, depth not infinite (NaN = none), class 0..2,
+// direction of non-zero length.  The first pass is branch-free so that the compiler vectorises it; the loop that
+// names the first bad ray runs only when the first pass found one.
+romap_status check_host_rays(const romap_rays* r, int64_t n) {
+  uint32_t bad = 0;
+  for (int64_t i = 0; i < 3 * n; ++i)
+    bad |= (uint32_t)!finite_bits(r->origin[i]) | (uint32_t)!finite_bits(r->dir[i]) | (uint32_t)!finite_bits(r->rgb[i]);
+  if (r->depth)
+    for (int64_t i = 0; i < n; ++i) {
+      uint32_t b;
+      std::memcpy(&b, r->depth + i, 4);
+      bad |= (uint32_t)((b & 0x7fffffffu) == 0x7f800000u);
+    }
+  if (r->cls)
+    for (int64_t i = 0; i < n; ++i) bad |= (uint32_t)(r->cls[i] > 2);
+  for (int64_t i = 0; i < n; ++i) {
+    const float* d = r->dir + 3 * i;
+    bad |= (uint32_t)!(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > 0.f);
+  }
+  if (!bad) return ROMAP_OK;
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(r->origin[i]) || !std::isfinite(r->dir[i]) || !std::isfinite(r->rgb[i]))
+      return fail(ROMAP_ERR_NONFINITE, "non-finite origin, dir or rgb at ray %lld", (long long)(i / 3));
+  for (int64_t i = 0; i < n; ++i) {
+    if (r->depth && std::isinf(r->depth[i])) return fail(ROMAP_ERR_NONFINITE, "infinite depth at ray %lld", (long long)i);
+    if (r->cls && r->cls[i] > 2) return fail(ROMAP_ERR_INVALID_ARG, "class %d at ray %lld", r->cls[i], (long long)i);
+    float dd = r->dir[3 * i] * r->dir[3 * i] + r->dir[3 * i + 1] * r->dir[3 * i + 1] + r->dir[3 * i + 2] * r->dir[3 * i + 2];
+    if (!(dd > 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "zero direction at ray %lld", (long long)i);
+  }
+  return ROMAP_OK;
+}
+
+// Grows the object's pool so that it holds `need` rays, keeping its first `keep` rays.
+romap_status ensure_pool(romap_ctx* ctx, Object& o, int64_t keep, int64_t need) {
+  if (need <= o.pool_cap) return ROMAP_OK;
+  int64_t cap = need > 2 * o.pool_cap ? need : 2 * o.pool_cap;
+  if (cap > ctx->cfg.max_rays_per_object) cap = ctx->cfg.max_rays_per_object;
+  float *po, *pd, *prgb, *pdep;
+  uint8_t* pcls;
+  ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &po));
+  ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &pd));
+  ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &prgb));
+  ROMAP_TRY(dev_alloc_t(ctx, cap, &pdep));
+  ROMAP_TRY(dev_alloc_t(ctx, cap, &pcls));
+  if (keep > 0) {
+    CUDA_TRY(cudaMemcpyAsync(po, o.pool_o, 12 * keep, cudaMemcpyDeviceToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(pd, o.pool_d, 12 * keep, cudaMemcpyDeviceToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(prgb, o.pool_rgb, 12 * keep, cudaMemcpyDeviceToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(pdep, o.pool_depth, 4 * keep, cudaMemcpyDeviceToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(pcls, o.pool_cls, keep, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  dev_free(ctx, o.pool_o); dev_free(ctx, o.pool_d); dev_free(ctx, o.pool_rgb);
+  dev_free(ctx, o.pool_depth); dev_free(ctx, o.pool_cls);
+  o.pool_o = po; o.pool_d = pd; o.pool_rgb = prgb; o.pool_depth = pdep; o.pool_cls = pcls;
+  o.pool_cap = cap;
+  return ROMAP_OK;
+}
+
+// Input arrays of an append on the device: host arrays are copied into the staging buffer (followed by `extra`
+// bytes for the caller), device arrays are used in place (the staging buffer then holds only the extra bytes).
+struct StagedRays {
+  const float *o = nullptr, *d = nullptr, *rgb = nullptr, *depth = nullptr;
+  const uint8_t* cls = nullptr;
+  char* extra = nullptr;
+  bool pinned = false;  // host arrays in page-locked memory: copied asynchronously, so the call waits for them
+};
+romap_status stage_rays(romap_ctx* ctx, const romap_rays* r, int64_t n, bool dev, size_t extra, StagedRays* out) {
+  *out = StagedRays{};
+  out->o = r->origin; out->d = r->dir; out->rgb = r->rgb; out->depth = r->depth; out->cls = r->cls;
+  if (dev) {
+    if (extra) {
+      ROMAP_TRY(grow(ctx, ctx->ws_stage, extra));
+      out->extra = (char*)ctx->ws_stage.p;
+    }
+    return ROMAP_OK;
+  }
+  size_t b3 = align_up(12 * (size_t)n, 256), b1 = align_up(4 * (size_t)n, 256), bc = align_up((size_t)n, 256);
+  ROMAP_TRY(grow(ctx, ctx->ws_stage, 3 * b3 + b1 + bc + extra));
+  char* st = (char*)ctx->ws_stage.p;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, r->origin) == cudaSuccess && attr.type == cudaMemoryTypeHost) out->pinned = true;
+  cudaGetLastError();
+  CUDA_TRY(cudaMemcpyAsync(st, r->origin, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(cudaMemcpyAsync(st + b3, r->dir, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(cudaMemcpyAsync(st + 2 * b3, r->rgb, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
+  out->o = (const float*)st;
+  out->d = (const float*)(st + b3);
+  out->rgb = (const float*)(st + 2 * b3);
+  if (r->depth) {
+    CUDA_TRY(cudaMemcpyAsync(st + 3 * b3, r->depth, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+    out->depth = (const float*)(st + 3 * b3);
+  }
+  if (r->cls) {
+    CUDA_TRY(cudaMemcpyAsync(st + 3 * b3 + b1, r->cls, n, cudaMemcpyHostToDevice, ctx->stream));
+    out->cls = (const uint8_t*)(st + 3 * b3 + b1);
+  }
+  out->extra = st + 3 * b3 + b1 + bc;
+  return ROMAP_OK;
+}
+
+}  // namespace
+
 romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* r, int64_t n, uint32_t flags) {
   ROMAP_TRY(check_ctx(ctx));
   ROMAP_TRY(check_id(ctx, id));
@@ -1005,17 +1126,7 @@ romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* r, int
   if (need > ctx->cfg.max_rays_per_object)
     return fail(ROMAP_ERR_CAPACITY, "pool of object %d would hold %lld rays (max %lld)", id, (long long)need,
                 (long long)ctx->cfg.max_rays_per_object);
-  if (!dev) {  // host inputs: every value must be finite (depth may be NaN = none)
-    for (int64_t i = 0; i < 3 * n; ++i)
-      if (!std::isfinite(r->origin[i]) || !std::isfinite(r->dir[i]) || !std::isfinite(r->rgb[i]))
-        return fail(ROMAP_ERR_NONFINITE, "non-finite origin, dir or rgb at ray %lld", (long long)(i / 3));
-    for (int64_t i = 0; i < n; ++i) {
-      if (r->depth && std::isinf(r->depth[i])) return fail(ROMAP_ERR_NONFINITE, "infinite depth at ray %lld", (long long)i);
-      if (r->cls && r->cls[i] > 2) return fail(ROMAP_ERR_INVALID_ARG, "class %d at ray %lld", r->cls[i], (long long)i);
-      float dd = r->dir[3 * i] * r->dir[3 * i] + r->dir[3 * i + 1] * r->dir[3 * i + 1] + r->dir[3 * i + 2] * r->dir[3 * i + 2];
-      if (!(dd > 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "zero direction at ray %lld", (long long)i);
-    }
-  }
+  if (!dev) ROMAP_TRY(check_host_rays(r, n));
   if (n == 0) {
     if (flags & ROMAP_REPLACE) {
       o.pool_n = 0;
@@ -1023,62 +1134,78 @@ romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* r, int
     }
     return ROMAP_OK;
   }
-  if (need > o.pool_cap) {  // grow the pool
-    int64_t cap = need > 2 * o.pool_cap ? need : 2 * o.pool_cap;
-    if (cap > ctx->cfg.max_rays_per_object) cap = ctx->cfg.max_rays_per_object;
-    float *po, *pd, *prgb, *pdep;
-    uint8_t* pcls;
-    ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &po));
-    ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &pd));
-    ROMAP_TRY(dev_alloc_t(ctx, 3 * cap, &prgb));
-    ROMAP_TRY(dev_alloc_t(ctx, cap, &pdep));
-    ROMAP_TRY(dev_alloc_t(ctx, cap, &pcls));
-    if (start > 0) {
-      CUDA_TRY(cudaMemcpyAsync(po, o.pool_o, 12 * start, cudaMemcpyDeviceToDevice, ctx->stream));
-      CUDA_TRY(cudaMemcpyAsync(pd, o.pool_d, 12 * start, cudaMemcpyDeviceToDevice, ctx->stream));
-      CUDA_TRY(cudaMemcpyAsync(prgb, o.pool_rgb, 12 * start, cudaMemcpyDeviceToDevice, ctx->stream));
-      CUDA_TRY(cudaMemcpyAsync(pdep, o.pool_depth, 4 * start, cudaMemcpyDeviceToDevice, ctx->stream));
-      CUDA_TRY(cudaMemcpyAsync(pcls, o.pool_cls, start, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
-    dev_free(ctx, o.pool_o); dev_free(ctx, o.pool_d); dev_free(ctx, o.pool_rgb);
-    dev_free(ctx, o.pool_depth); dev_free(ctx, o.pool_cls);
-    o.pool_o = po; o.pool_d = pd; o.pool_rgb = prgb; o.pool_depth = pdep; o.pool_cls = pcls;
-    o.pool_cap = cap;
-  }
-  const float *so = r->origin, *sd = r->dir, *srgb = r->rgb, *sdep = r->depth;
-  const uint8_t* scls = r->cls;
-  bool pinned = false;
-  if (!dev) {  // stage host arrays on the device
-    size_t b3 = align_up(12 * (size_t)n, 256), b1 = align_up(4 * (size_t)n, 256), bc = align_up((size_t)n, 256);
-    ROMAP_TRY(grow(ctx, ctx->ws_stage, 3 * b3 + b1 + bc));
-    char* st = (char*)ctx->ws_stage.p;
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, r->origin) == cudaSuccess && attr.type == cudaMemoryTypeHost) pinned = true;
-    cudaGetLastError();
-    CUDA_TRY(cudaMemcpyAsync(st, r->origin, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
-    CUDA_TRY(cudaMemcpyAsync(st + b3, r->dir, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
-    CUDA_TRY(cudaMemcpyAsync(st + 2 * b3, r->rgb, 12 * n, cudaMemcpyHostToDevice, ctx->stream));
-    so = (const float*)st;
-    sd = (const float*)(st + b3);
-    srgb = (const float*)(st + 2 * b3);
-    if (r->depth) {
-      CUDA_TRY(cudaMemcpyAsync(st + 3 * b3, r->depth, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
-      sdep = (const float*)(st + 3 * b3);
-    }
-    if (r->cls) {
-      CUDA_TRY(cudaMemcpyAsync(st + 3 * b3 + b1, r->cls, n, cudaMemcpyHostToDevice, ctx->stream));
-      scls = (const uint8_t*)(st + 3 * b3 + b1);
-    }
-  }
+  ROMAP_TRY(ensure_pool(ctx, o, start, need));
+  StagedRays sr;
+  ROMAP_TRY(stage_rays(ctx, r, n, dev, 0, &sr));
   float cz = (float)std::cos(o.desc.yaw), sz = (float)std::sin(o.desc.yaw);
-  launch_transform_rays(so, sd, srgb, sdep, scls, n, (flags & ROMAP_OBJECT_FRAME) ? 1 : 0, o.desc.t[0], o.desc.t[1],
-                        o.desc.t[2], cz, sz, o.pool_o + 3 * start, o.pool_d + 3 * start, o.pool_rgb + 3 * start,
-                        o.pool_depth + start, o.pool_cls + start, ctx->stream);
+  launch_transform_rays(sr.o, sr.d, sr.rgb, sr.depth, sr.cls, n, (flags & ROMAP_OBJECT_FRAME) ? 1 : 0, o.desc.t[0],
+                        o.desc.t[1], o.desc.t[2], cz, sz, o.pool_o + 3 * start, o.pool_d + 3 * start,
+                        o.pool_rgb + 3 * start, o.pool_depth + start, o.pool_cls + start, ctx->stream);
   ctx->launches += 1;
   CUDA_TRY(cudaGetLastError());
-  if (pinned) CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // pinned host buffers are read asynchronously
+  if (sr.pinned) CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // pinned host buffers are read asynchronously
   o.pool_n = need;
   return sync_object(ctx, id);
+}
+
+romap_status romap_add_rays_multi(romap_ctx* ctx, const int32_t* ids, const int64_t* counts, int32_t n_ids,
+                                  const romap_rays* r, uint32_t flags) {
+  ROMAP_TRY(check_ctx(ctx));
+  std::vector<int32_t> v;
+  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+  if (!counts || !r) return fail(ROMAP_ERR_INVALID_ARG, "counts and rays must not be NULL");
+  if (flags & ~(ROMAP_DEVICE_PTR | ROMAP_OBJECT_FRAME | ROMAP_REPLACE)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  const bool dev = (flags & ROMAP_DEVICE_PTR) != 0, replace = (flags & ROMAP_REPLACE) != 0;
+  int64_t n = 0;
+  for (int k = 0; k < n_ids; ++k) {
+    if (counts[k] < 0) return fail(ROMAP_ERR_INVALID_ARG, "counts[%d] = %lld < 0", k, (long long)counts[k]);
+    const int64_t need = (replace ? 0 : ctx->objs[ids[k]].pool_n) + counts[k];
+    if (need > ctx->cfg.max_rays_per_object)
+      return fail(ROMAP_ERR_CAPACITY, "pool of object %d would hold %lld rays (max %lld)", ids[k], (long long)need,
+                  (long long)ctx->cfg.max_rays_per_object);
+    n += counts[k];
+  }
+  if (n > 0 && (!r->origin || !r->dir || !r->rgb)) return fail(ROMAP_ERR_INVALID_ARG, "origin, dir and rgb are required");
+  if (!dev) ROMAP_TRY(check_host_rays(r, n));
+  std::vector<XformObj> xo;
+  int64_t first = 0;
+  for (int k = 0; k < n_ids; ++k) {
+    Object& o = ctx->objs[ids[k]];
+    const int64_t start = replace ? 0 : o.pool_n;
+    if (counts[k] > 0) {
+      ROMAP_TRY(ensure_pool(ctx, o, start, start + counts[k]));
+      XformObj x;
+      x.first = first;
+      for (int a = 0; a < 3; ++a) x.t[a] = o.desc.t[a];
+      x.cz = (float)std::cos(o.desc.yaw);
+      x.sz = (float)std::sin(o.desc.yaw);
+      x.o_out = o.pool_o + 3 * start;
+      x.d_out = o.pool_d + 3 * start;
+      x.rgb_out = o.pool_rgb + 3 * start;
+      x.depth_out = o.pool_depth + start;
+      x.cls_out = o.pool_cls + start;
+      xo.push_back(x);
+    }
+    first += counts[k];
+  }
+  bool pinned = false;
+  if (!xo.empty()) {
+    StagedRays sr;
+    ROMAP_TRY(stage_rays(ctx, r, n, dev, sizeof(XformObj) * xo.size(), &sr));
+    CUDA_TRY(cudaMemcpyAsync(sr.extra, xo.data(), sizeof(XformObj) * xo.size(), cudaMemcpyHostToDevice, ctx->stream));
+    launch_transform_rays_multi(sr.o, sr.d, sr.rgb, sr.depth, sr.cls, n, (flags & ROMAP_OBJECT_FRAME) ? 1 : 0,
+                                reinterpret_cast<const XformObj*>(sr.extra), (int)xo.size(), ctx->stream);
+    ctx->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    pinned = sr.pinned;
+  }
+  if (pinned) CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // pinned host buffers are read asynchronously
+  for (int k = 0; k < n_ids; ++k) {
+    Object& o = ctx->objs[ids[k]];
+    o.pool_n = (replace ? 0 : o.pool_n) + counts[k];
+    ROMAP_TRY(sync_object(ctx, ids[k]));
+  }
+  return ROMAP_OK;
 }
 
 romap_status romap_pool_size(romap_ctx* ctx, int32_t id, int64_t* out_n) {
@@ -1509,9 +1636,10 @@ romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_limit) {
 romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index) {
   ROMAP_TRY(check_ctx(ctx));
   if (index < -1 || index >= kNumTileKernels) return fail(ROMAP_ERR_INVALID_ARG, "tile kernel %d out of range", index);
-  if (ctx->g.fp8 && index > 0) return fail(ROMAP_ERR_UNSUPPORTED, "the FP8 precision runs on tile kernel 0 only");
-  if (ctx->g.single_net && index > 0)
-    return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model runs on tile kernel 0 only");
+  if (ctx->g.fp8 && index >= 0 && !lockstep_kernel(index))
+    return fail(ROMAP_ERR_UNSUPPORTED, "the FP8 precision runs on the lockstep tile kernels (0, 2) only");
+  if (ctx->g.single_net && index >= 0 && !lockstep_kernel(index))
+    return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model runs on the lockstep tile kernels (0, 2) only");
   ctx->tile_kernel = index;
   drop_graph(ctx);
   return ROMAP_OK;

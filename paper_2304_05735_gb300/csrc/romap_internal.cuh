@@ -209,6 +209,19 @@ void launch_transform_rays(const float* o_in, const float* d_in, const float* rg
                            const uint8_t* cls_in, int64_t n, int object_frame, float tx, float ty, float tz, float cz,
                            float sz, float* o_out, float* d_out, float* rgb_out, float* depth_out, uint8_t* cls_out,
                            cudaStream_t stream);
+// One object's range of a multi-object ray append: its rays [first, first + count) of the concatenated inputs go to
+// its pool arrays (already offset to the append position), moved to the object frame with translation t and
+// yaw (cos cz, sin sz).
+struct XformObj {
+  int64_t first;
+  float t[3];
+  float cz, sz;
+  float *o_out, *d_out, *rgb_out, *depth_out;
+  uint8_t* cls_out;
+};
+void launch_transform_rays_multi(const float* o_in, const float* d_in, const float* rgb_in, const float* depth_in,
+                                 const uint8_t* cls_in, int64_t n, int object_frame, const XformObj* xo, int n_obj,
+                                 cudaStream_t stream);
 void launch_ray_setup(const GridParams& g, const BatchDesc& b, RayBuf r, uint32_t* block_sums, cudaStream_t stream);
 void launch_scan(const GridParams& g, const BatchDesc& b, uint32_t* block_sums, BatchDyn* dyn, int32_t* totals,
                  SampleBuf s, unsigned long long* live_counter, cudaStream_t stream);
@@ -241,13 +254,15 @@ int launch_mc(const GridParams& g, const ObjectDev* objs, int slot, float iso, c
 void launch_occ_update(const GridParams& g, const ObjectDev* objs, int slot, float decay, float threshold, int reset,
                        float* dens, uint64_t* bits, cudaStream_t stream);
 void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream);
+// interleave: CTA c takes every n_ctas-th tile pair (tile) from c instead of a contiguous range, so that all CTAs
+// work on the same few objects at a time (their tables and gradients then stay in L2).
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
-                    int total_tiles, int n_ctas, cudaStream_t stream);
+                    int total_tiles, int n_ctas, int interleave, cudaStream_t stream);
 void launch_to_half(const float* params, uint16_t* table_h, int64_t n_hash, cudaStream_t stream);
 // Warp-specialized variant of launch_tile_tc (same results): compute warps run the MMA chain of one tile while
 // memory warps gather the next tile and scatter the previous one.
 void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
-                    int total_tiles, int n_ctas, cudaStream_t stream);
+                    int total_tiles, int n_ctas, int interleave, cudaStream_t stream);
 // status word bits written by the kernels
 constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2;
 void launch_selftest_wait(int32_t* status, int limit, cudaStream_t stream);

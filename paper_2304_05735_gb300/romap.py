@@ -100,6 +100,7 @@ SIGNATURES = {
     "romap_update_occupancy": (_i32, [_vp, _i32, C.c_float, C.c_float, _u32]),
     "romap_get_occupancy": (_i32, [_vp, _i32, _vp, _vp]),
     "romap_add_rays": (_i32, [_vp, _i32, _P(romap_rays), _i64, _u32]),
+    "romap_add_rays_multi": (_i32, [_vp, _vp, _vp, _i32, _P(romap_rays), _u32]),
     "romap_pool_size": (_i32, [_vp, _i32, _P(_i64)]),
     "romap_train_step": (_i32, [_vp, _vp, _i32, _i32, _vp]),
     "romap_forward_backward": (_i32, [_vp, _vp, _i32, _vp]),

@@ -30,7 +30,8 @@ def _cos(a, b):
     return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("kernel,prec", [(0, MIXED), (1, MIXED), (0, R.ROMAP_PREC_MIXED_FP8)])
+@pytest.mark.parametrize("kernel,prec", [(0, MIXED), (1, MIXED), (2, MIXED), (3, MIXED), (0, R.ROMAP_PREC_MIXED_FP8),
+                                         (2, R.ROMAP_PREC_MIXED_FP8)])
 @pytest.mark.parametrize("scene", ["plain", "masked"])
 def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
     if scene == "plain":
@@ -63,7 +64,7 @@ def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
         ctx.close()
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_mixed_batched_equals_separate(torch, kernel):
     oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, n_samples=32, rays_per_step=700, bg_random=True,
                            precision=MIXED)
@@ -80,7 +81,7 @@ def test_mixed_batched_equals_separate(torch, kernel):
         gb = [ctx.grad(i) for i in ids]
         ctx2 = Ctx(rc)
         try:
-            R.check(R.romap_set_tile_kernel(ctx2.h, 1 - kernel))  # the other kernel, one object at a time
+            R.check(R.romap_set_tile_kernel(ctx2.h, (kernel + 1) % 4))  # another candidate, one object at a time
             for k, sc in enumerate(scenes):
                 oid = ctx2.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=333 + 100 * k)
                 ctx2.add_rays(oid, sc.pool)
@@ -134,8 +135,8 @@ def test_autotuner_picks_a_measured_candidate(torch):
         R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 4, names, 256))
         cands = names.value.decode().split(";")
         print(f"\nautotuner: {dict(zip(cands, list(ms)[:len(cands)]))} -> {cands[chosen.value]}")
-        assert len(cands) == 2 and 0 <= chosen.value < 2
-        assert all(ms[i] > 0 for i in range(2)) and ms[chosen.value] == min(ms[0], ms[1])
+        assert len(cands) == 4 and 0 <= chosen.value < 4
+        assert all(ms[i] > 0 for i in range(4)) and ms[chosen.value] == min(ms)
     finally:
         ctx.close()
 
