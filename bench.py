@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32", "mixed", "fp8"), default="mixed")
+    ap.add_argument("--precision", choices=("fp32", "mixed", "fp8", "fp16"), default="mixed")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="multi8")
     ap.add_argument("--loss-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
@@ -158,10 +158,16 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+DTYPES = {"mixed": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)",
+          "fp16": "fp16 (MLP GEMM operands, gradient operands scaled by the batch size; FP16 table copy; FP32 "
+                  "accumulation, scan, loss, Adam)",
+          "fp8": "fp8 e4m3 hidden 64x64 GEMM, bf16 other GEMMs (FP16 table copy; FP32 accumulation, scan, loss, "
+                 "Adam)"}
 KERNEL_SOURCES = {
     "fp32": ("kernels_tile.cu", "device_common.cuh", "romap_internal.cuh"),
     "mixed": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
     "fp8": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
+    "fp16": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
 }
 
 
@@ -239,7 +245,8 @@ def make_ctx(R, torch, precision, single_net=False, hidden_layers=1):
                        growth=0.0, max_resolution=w["max_resolution"], n_samples=w["samples_per_ray"],
                        rays_per_step=4096, bg_random=True, single_net=single_net, dir_dims=0 if single_net else 3,
                        hidden_layers=hidden_layers,
-                       precision={"mixed": R.ROMAP_PREC_MIXED_BF16, "fp8": R.ROMAP_PREC_MIXED_FP8}.get(
+                       precision={"mixed": R.ROMAP_PREC_MIXED_BF16, "fp8": R.ROMAP_PREC_MIXED_FP8,
+                                  "fp16": R.ROMAP_PREC_MIXED_FP16}.get(
                            precision, R.ROMAP_PREC_FP32),
                        max_objects=2 * w["objects"])
     h = C.c_void_p()
@@ -564,9 +571,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": w["scaling"], "vs_baseline": None,
-               "dtype": {"mixed": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)",
-                         "fp8": "fp8 e4m3 hidden 64x64 GEMM, bf16 other GEMMs (FP16 table copy; FP32 accumulation, "
-                                "scan, loss, Adam)"}.get(main_prec, "f32"),
+               "dtype": DTYPES.get(main_prec, "f32"),
                "data": "synthetic (analytic shapes, seeded)",
                "config": {"workload": w["name"], **config_keys(w), "precision": main_prec, "path": "batched",
                           "objects_this_rank": n, "rays_per_step_this_rank": int(sum(it.rays for it in items)),
@@ -788,9 +793,7 @@ def run_stream(args):
     out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": 1, "steps": int(steps.sum()),
            "warmup": 0, "ms_per_step": train_ms / max(1, int(steps.sum())), "higher_is_better": True,
            "scaling": w["scaling"], "vs_baseline": None,
-           "dtype": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation, scan, loss, Adam)"
-           if args.precision == "mixed" else ("fp8 e4m3 hidden 64x64 GEMM, bf16 other GEMMs, FP16 tables, FP32 "
-                                                "accumulation, scan, loss, Adam" if args.precision == "fp8" else "f32"),
+           "dtype": DTYPES.get(args.precision, "f32"),
            "data": "synthetic (analytic shapes, seeded)",
            "config": {"workload": w["name"], **config_keys(w), "precision": args.precision,
                       "observations_accepted": n_obs, "rays_observed": int(rays_in)},

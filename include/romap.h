@@ -74,6 +74,10 @@ typedef int32_t romap_status;
                                    second layer) in FP8 E4M3: each output row of the layer's weights scaled by
                                    448 / its max |W|, each sample's input activations by 448 / their max, FP32
                                    accumulation, dequantised before the ReLU; the backward stays BF16 */
+#define ROMAP_PREC_MIXED_FP16 3 /* as MIXED_BF16 with FP16 MLP operands (11-bit significand instead of 8, range
+                                   +-65504, saturated there); the backward's gradient operands are scaled by the
+                                   object's batch size B (the losses are means over B rays) before rounding and the
+                                   FP32 results unscaled */
 
 typedef struct romap_ctx romap_ctx;
 

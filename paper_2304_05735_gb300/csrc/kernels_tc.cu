@@ -92,8 +92,8 @@ __device__ __forceinline__ void gather_rows(const GridParams& g, const ObjectDev
       a0 = fmaf(c0.w[k], f0.x, a0); a1 = fmaf(c0.w[k], f0.y, a1);
       if (has1) { b0 = fmaf(c1.w[k], f1.x, b0); b1 = fmaf(c1.w[k], f1.y, b1); }
     }
-    *reinterpret_cast<__nv_bfloat162*>(E + kmaj(s, 2 * l, LFP)) = __floats2bfloat162_rn(a0, a1);
-    if (has1) *reinterpret_cast<__nv_bfloat162*>(E + kmaj(s, 2 * l + 2, LFP)) = __floats2bfloat162_rn(b0, b1);
+    *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l, LFP)) = pack2(a0, a1, g.f16 != 0);
+    if (has1) *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l + 2, LFP)) = pack2(b0, b1, g.f16 != 0);
   }
 }
 // zero row s of an encoding buffer over the levels [l0, l1)
@@ -155,7 +155,7 @@ template <class Smem>
 __device__ void load_w6(Smem& sm, const GridParams& g, const float* __restrict__ P, int t, int nthreads) {
   for (int i = t; i < kH * kH; i += nthreads) {
     int o = i / kH, k = i % kH;
-    *reinterpret_cast<__nv_bfloat16*>(sm.w6() + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[6] + i]);
+    *reinterpret_cast<uint16_t*>(sm.w6() + kmaj(o, k, kH)) = pack1(P[g.mlp_off[6] + i], g.f16 != 0);
   }
 }
 
@@ -191,7 +191,7 @@ __device__ void load_w4_fp8(Smem& sm, const GridParams& g, const float* __restri
 
 // relu(row_scale * col_scale[j] * TMEM row) -> BF16 row (the dequantising epilogue of the FP8 GEMM)
 __device__ __forceinline__ void epi_relu64_scaled(uint32_t taddr, unsigned char* buf, int row, float row_scale,
-                                                  const float* col_scale) {
+                                                  const float* col_scale, bool f16) {
   float v[64];
 #pragma unroll
   for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
@@ -199,11 +199,11 @@ __device__ __forceinline__ void epi_relu64_scaled(uint32_t taddr, unsigned char*
 #pragma unroll
   for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j] * row_scale * col_scale[j], 0.f);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c);
+  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c, f16);
 }
 
 // relu(TMEM row) -> BF16 row of an activation buffer (64 columns); the four TMEM loads share one wait
-__device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, int row) {
+__device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, int row, bool f16) {
   float v[64];
 #pragma unroll
   for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
@@ -211,10 +211,10 @@ __device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, i
 #pragma unroll
   for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j], 0.f);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c);
+  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c, f16);
 }
 // TMEM row masked by relu'(the forward activation stored in buf) -> written back into buf (64 columns)
-__device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, int row) {
+__device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, int row, bool f16) {
   float v[64];
 #pragma unroll
   for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
@@ -222,10 +222,10 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     float h[8];
-    load8(buf, row, c, kH, h);
+    load8(buf, row, c, kH, h, f16);
 #pragma unroll
     for (int j = 0; j < 8; ++j) h[j] = h[j] > 0.f ? v[8 * c + j] : 0.f;
-    store8(buf, row, c, kH, h);
+    store8(buf, row, c, kH, h, f16);
   }
 }
 
@@ -238,6 +238,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int wg = t >> 7;          // tile of the pair
   const int s = t & (kT - 1);     // slot within the tile = TMEM lane
   TileBufs<LFP>& tb = sm.tb[wg];
+  // MLP operands in FP16 instead of BF16: the backward's gradient operands are then scaled by the object's batch
+  // size B (the losses are means over B rays, so the scaled values are per-ray gradients, inside FP16's range) and
+  // the FP32 results unscaled
+  const bool f16 = g.f16 != 0;
+  auto unscale_of = [&](int bi_) { return f16 ? 1.0f / (float)(b.ray_base[bi_ + 1] - b.ray_base[bi_]) : 1.0f; };
   // pairs of this CTA: a contiguous range of the plan, or (interleave) every gridDim.x-th pair from blockIdx.x, so
   // that all CTAs work on the same few objects at a time and those objects' tables and gradients stay in L2
   const int total_pairs = *b.plan_npairs;
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tb.t[s] = nx.t;
     tb.dt[s] = nx.dt;
     if (nx_bi != bi) {
-      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
+      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
       bi = nx_bi;
       ob = nx_ob;
       load_weights<LFP>(sm, g, ob->params, kTcThreads);
@@ -332,6 +337,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
+    const float gscale = f16 ? (float)n_rays_obj : 1.0f, gunscale = f16 ? invB : 1.0f;
     const bool has_next = pair + pair_step < pair_hi;
     if (has_next) {
       nx_ti = b.plan_tiles[(pair + pair_step) * kTilesPerCta + wg];
@@ -344,11 +350,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
         for (int kk = 0; kk < LFP / 16; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].E[cur], LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0), kk > 0);
+          mma(tmp_d(u), desc_k(sm.tb[u].E[cur], LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0, f16), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
-    epi_relu64(tmp, tb.H1, s);
+    epi_relu64(tmp, tb.H1, s, f16);
     if constexpr (SN) {  // single-network hidden layers 2 and 3: hid(k + 1) = relu(hid(k) M^T), M = w4, w6
       for (int k = 0; k < nl; ++k) {
         sync_then_issue();
@@ -356,12 +362,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              mma(tmp_d(u), desc_k(hid(u, k), kH, kk), desc_k(k == 0 ? sm.w4 : sm.w6(), kH, kk), idesc(64, 0, 0),
+              mma(tmp_d(u), desc_k(hid(u, k), kH, kk), desc_k(k == 0 ? sm.w4 : sm.w6(), kH, kk), idesc(64, 0, 0, f16),
                   kk > 0);
           mma_commit(&sm.mbar);
         }
         if (!(ok = wait_mma())) break;
-        epi_relu64(tmp, hid(wg, k + 1), s);
+        epi_relu64(tmp, hid(wg, k + 1), s, f16);
       }
       if (!ok) break;
     }
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(hid(u, nl), kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0), kk > 0);
+          mma(tmp_d(u), desc_k(hid(u, nl), kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0, f16), kk > 0);
       mma_commit(&sm.mbar);
     }
     if (!(ok = wait_mma())) break;
@@ -397,7 +403,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int j = 18; j < 32; ++j) cin[j] = 0.f;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) store8(tb.CIN, s, c, 32, cin + 8 * c);
+        for (int c = 0; c < 4; ++c) store8(tb.CIN, s, c, 32, cin + 8 * c, f16);
       }
     }
     if constexpr (!SN) {  // ---- colour net --------------------------------------------------------------------------
@@ -406,16 +412,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
-            mma(tmp_d(u), desc_k(sm.tb[u].CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0), kk > 0);
+            mma(tmp_d(u), desc_k(sm.tb[u].CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0, f16), kk > 0);
         mma_commit(&sm.mbar);
       }
       if (!(ok = wait_mma())) break;
-      epi_relu64(tmp, tb.H2, s);
+      epi_relu64(tmp, tb.H2, s, f16);
       float h2_scale = 1.f;  // FP8: 448 / max of this sample's H2 row (1 when all zero)
       if (FP8) {  // this sample's H2 row in E4M3; the row scale factors out of its GEMM outputs
         float hv[64];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) load8(tb.H2, s, c, kH, hv + 8 * c);
+        for (int c = 0; c < 8; ++c) load8(tb.H2, s, c, kH, hv + 8 * c, f16);
         float m = 0.f;
 #pragma unroll
         for (int j = 0; j < 64; ++j) m = fmaxf(m, hv[j]);
@@ -442,20 +448,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           } else {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+              mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0, f16), kk > 0);
           }
         }
         mma_commit(&sm.mbar);
       }
       if (!(ok = wait_mma())) break;
-      if (FP8) epi_relu64_scaled(tmp, tb.H3, s, 1.0f / h2_scale, sm.w4_inv);
-      else epi_relu64(tmp, tb.H3, s);
+      if (FP8) epi_relu64_scaled(tmp, tb.H3, s, 1.0f / h2_scale, sm.w4_inv, f16);
+      else epi_relu64(tmp, tb.H3, s, f16);
       sync_then_issue();
       if (t == 0) {  // L5: H3 W5^T (3 of 16 outputs)
         for (int u = 0; u < kTilesPerCta; ++u)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0), kk > 0);
+            mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0, f16), kk > 0);
         mma_commit(&sm.mbar);
       }
       if (!(ok = wait_mma())) break;
@@ -495,22 +501,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       const float o0 = tb.o0[s];
       dpre = (valid && o0 >= -15.f && o0 <= 15.f) ? tb.dsig[s] * tb.sig[s] : 0.f;
+      if (f16) {  // FP16 operands: per-ray scale (undone on the FP32 results)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dl[k] *= gscale;
+        dpre *= gscale;
+      }
       if constexpr (SN) {  // dOUT = [dsigma * sigma, dlogit 0..2, 0 ...]
 #pragma unroll
         for (int k = 15; k > 0; --k) dl[k] = k <= 3 ? dl[k - 1] : 0.f;
         dl[0] = dpre;
       }
-      store8(tb.DL, s, 0, 16, dl);
-      store8(tb.DL, s, 1, 16, dl + 8);
+      store8(tb.DL, s, 0, 16, dl, f16);
+      store8(tb.DL, s, 1, 16, dl + 8, f16);
     }
     if constexpr (!SN) {  // ---- colour net backward ------------------------------------------------------------------
       sync_then_issue();
       if (t == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
         for (int u = 0; u < kTilesPerCta; ++u) {
-          mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1), 0);
+          mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
+            mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
                 (u > 0 || kk > 0) ? 1u : acc_dw);
         }
         mma_commit(&sm.mbar);
@@ -524,16 +535,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
       if (!(ok = wait_mma())) break;
-      epi_mask64(tmp, tb.H3, s);
+      epi_mask64(tmp, tb.H3, s, f16);
       sync_then_issue();
       if (t == 0) {  // dH2 = dH3 W4 ; dW4^T += H2^T dH3
         for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1), kk > 0);
+            mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW4 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1),
+            mma(kColDW4 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1, f16),
                 (u > 0 || kk > 0) ? 1u : acc_dw);
         }
         mma_commit(&sm.mbar);
@@ -545,16 +556,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
       if (!(ok = wait_mma())) break;
-      epi_mask64(tmp, tb.H2, s);
+      epi_mask64(tmp, tb.H2, s, f16);
       sync_then_issue();
       if (t == 0) {  // dCIN = dH2 W3 (32 columns) ; dW3^T += CIN^T dH2
         for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1), kk > 0);
+            mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1, f16), kk > 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW3 + tm, desc_mn(sm.tb[u].CIN, 32, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1),
+            mma(kColDW3 + tm, desc_mn(sm.tb[u].CIN, 32, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1, f16),
                 (u > 0 || kk > 0) ? 1u : acc_dw);
         }
         mma_commit(&sm.mbar);
@@ -573,17 +584,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         d[0] = dpre;
 #pragma unroll
         for (int j = 0; j < 15; ++j) d[1 + j] = v[j];
-        store8(tb.DL, s, 0, 16, d);
-        store8(tb.DL, s, 1, 16, d + 8);
+        store8(tb.DL, s, 0, 16, d, f16);
+        store8(tb.DL, s, 1, 16, d + 8, f16);
       }
     }  // colour net backward
     sync_then_issue();
     if (t == 0) {  // dHL = dOUT W2 ; dW2^T += HL^T dOUT
       for (int u = 0; u < kTilesPerCta; ++u) {
-        mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1), 0);
+        mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW2 + tm, desc_mn(hid(u, nl), kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1),
+          mma(kColDW2 + tm, desc_mn(hid(u, nl), kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
@@ -602,7 +613,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
     if (!(ok = wait_mma())) break;
-    epi_mask64(tmp, hid(wg, nl), s);
+    epi_mask64(tmp, hid(wg, nl), s, f16);
     if constexpr (SN) {  // hidden layers 3, 2: dhid(k) = dhid(k + 1) M ; dM^T += hid(k)^T dhid(k + 1)
       for (int k = nl - 1; k >= 0; --k) {
         sync_then_issue();
@@ -612,10 +623,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              mma(tmp_d(u), desc_k(hid(u, k + 1), kH, kk), desc_mn(w, kH, kk), idesc(64, 0, 1), kk > 0);
+              mma(tmp_d(u), desc_k(hid(u, k + 1), kH, kk), desc_mn(w, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-              mma(col + tm, desc_mn(hid(u, k), kH, kk), desc_mn(hid(u, k + 1), kH, kk), idesc(64, 1, 1),
+              mma(col + tm, desc_mn(hid(u, k), kH, kk), desc_mn(hid(u, k + 1), kH, kk), idesc(64, 1, 1, f16),
                   (u > 0 || kk > 0) ? 1u : acc_dw);
           }
           mma_commit(&sm.mbar);
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
         if (!(ok = wait_mma())) break;
-        epi_mask64(tmp, hid(wg, k), s);
+        epi_mask64(tmp, hid(wg, k), s, f16);
       }
       if (!ok) break;
     }
@@ -636,10 +647,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1), kk > 0);
+          mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1, f16), kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW1 + tm, desc_mn(sm.tb[u].E[cur], LFP, kk), desc_mn(sm.tb[u].H1, kH, kk), idesc(64, 1, 1),
+          mma(kColDW1 + tm, desc_mn(sm.tb[u].E[cur], LFP, kk), desc_mn(sm.tb[u].H1, kH, kk), idesc(64, 1, 1, f16),
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
@@ -659,7 +670,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tmem_ld16(tmp + 16 * c, de);
         tmem_wait_ld();
 #pragma unroll
-        for (int k = 0; k < 16; ++k) tb.dEs(16 * c + k)[s] = de[k];
+        for (int k = 0; k < 16; ++k) tb.dEs(16 * c + k)[s] = f16 ? de[k] * gunscale : de[k];
       }
       if (tb.valid[s]) {
         const float p[3] = {tb.px[0][s], tb.px[1][s], tb.px[2][s]};
@@ -680,7 +691,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_after();
   }
   if (ok && bi >= 0) {
-    flush_dw<LFP>(tm, g, ob->grad);
+    flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
   } else if (!ok) {
     if (t == 0) {
       if (status) atomicOr(status, 2);

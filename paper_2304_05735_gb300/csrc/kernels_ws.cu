@@ -67,7 +67,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, int row) {
+__device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, int row, bool f16) {
   float v[64];
 #pragma unroll
   for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
@@ -75,9 +75,9 @@ __device__ __forceinline__ void epi_relu64(uint32_t taddr, unsigned char* buf, i
 #pragma unroll
   for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j], 0.f);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c);
+  for (int c = 0; c < 8; ++c) store8(buf, row, c, kH, v + 8 * c, f16);
 }
-__device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, int row) {
+__device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, int row, bool f16) {
   float v[64];
 #pragma unroll
   for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
@@ -85,10 +85,10 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     float h[8];
-    load8(buf, row, c, kH, h);
+    load8(buf, row, c, kH, h, f16);
 #pragma unroll
     for (int j = 0; j < 8; ++j) h[j] = h[j] > 0.f ? v[8 * c + j] : 0.f;
-    store8(buf, row, c, kH, h);
+    store8(buf, row, c, kH, h, f16);
   }
 }
 
@@ -100,6 +100,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
                             int tile_step, int n) {
   const int s = threadIdx.x - kCompute;
   constexpr int LMAX = LFP / 2;
+  const bool f16 = g.f16 != 0;
   for (int k = 0; k < n + 2; ++k) {
     if (sm.fail) break;
     const int slot = k & 1;
@@ -125,7 +126,6 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
           if (l >= g.L || (d0 == 0.f && d1 == 0.f)) continue;
           Corners c;
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
-#pragma unroll
           scatter_corners(gt + g.off[l], c.idx, c.w, d0, d1);
         }
       }
@@ -152,7 +152,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
         gather_levels<LFP, 0, LMAX>(g, ob, p, e);
       }
 #pragma unroll
-      for (int c = 0; c < LFP / 8; ++c) store8(sl.E, s, c, LFP, e + 8 * c);
+      for (int c = 0; c < LFP / 8; ++c) store8(sl.E, s, c, LFP, e + 8 * c, f16);
       fence_async_smem();
       mbar_arrive(&sm.full_bar[slot]);
     }
@@ -167,6 +167,10 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
                              int32_t* status, int tile_lo, int tile_step, int n, uint32_t& phase, bool& pending) {
   const int s = threadIdx.x, warp = s >> 5;
   const uint32_t tm = sm.tmem_base;
+  // FP16 operands: gradient operands scaled by the object's batch size B, FP32 results unscaled (as the lockstep
+  // kernel)
+  const bool f16 = g.f16 != 0;
+  auto unscale_of = [&](int bi_) { return f16 ? 1.0f / (float)(b.ray_base[bi_ + 1] - b.ray_base[bi_]) : 1.0f; };
   const uint32_t tmp = tm + ((uint32_t)(32 * warp) << 16) + kColTmp;
   const uint32_t dtmp = tm + kColTmp;
   auto sync_then_issue = [&]() {
@@ -202,7 +206,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     if (sm.c_stop) break;
     const int nbi = sl.bi;
     if (nbi != bi) {
-      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
+      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
       bi = nbi;
       ob = &b.objs[b.slot[bi]];
       load_weights<LFP>(sm, g, ob->params, kCompute);
@@ -210,21 +214,22 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
+    const float gscale = f16 ? (float)n_rays_obj : 1.0f, gunscale = f16 ? invB : 1.0f;
     sync_then_issue();
     // ---- forward ----
     if (s == 0) {
       pending = true;
 #pragma unroll
       for (int kk = 0; kk < LFP / 16; ++kk)
-        mma(dtmp, desc_k(sl.E, LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0), kk > 0);
+        mma(dtmp, desc_k(sl.E, LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0, f16), kk > 0);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
-    epi_relu64(tmp, sl.H1, s);
+    epi_relu64(tmp, sl.H1, s, f16);
     sync_then_issue();
     if (s == 0) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H1, kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0), kk > 0);
+      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H1, kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0, f16), kk > 0);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
@@ -247,28 +252,28 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
 #pragma unroll
       for (int j = 18; j < 32; ++j) cin[j] = 0.f;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) store8(sl.CIN, s, c, 32, cin + 8 * c);
+      for (int c = 0; c < 4; ++c) store8(sl.CIN, s, c, 32, cin + 8 * c, f16);
     }
     sync_then_issue();
     if (s == 0) {
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) mma(dtmp, desc_k(sl.CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0), kk > 0);
+      for (int kk = 0; kk < 2; ++kk) mma(dtmp, desc_k(sl.CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0, f16), kk > 0);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
-    epi_relu64(tmp, sl.H2, s);
+    epi_relu64(tmp, sl.H2, s, f16);
     sync_then_issue();
     if (s == 0) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0), kk > 0);
+      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0, f16), kk > 0);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
-    epi_relu64(tmp, sl.H3, s);
+    epi_relu64(tmp, sl.H3, s, f16);
     sync_then_issue();
     if (s == 0) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0), kk > 0);
+      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0, f16), kk > 0);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
@@ -304,37 +309,42 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       }
       const float o0 = sl.o0[s];
       dpre = (valid && o0 >= -15.f && o0 <= 15.f) ? sl.dsig[s] * sl.sig[s] : 0.f;
-      store8(sl.DL, s, 0, 16, dl);
-      store8(sl.DL, s, 1, 16, dl + 8);
+      if (f16) {  // FP16 operands: per-ray scale (undone on the FP32 results)
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2) dl[k2] *= gscale;
+        dpre *= gscale;
+      }
+      store8(sl.DL, s, 0, 16, dl, f16);
+      store8(sl.DL, s, 1, 16, dl + 8, f16);
     }
     sync_then_issue();
     if (s == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
-      mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1), 0);
+      mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW5 + tm, desc_mn(sl.H3, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1), kk > 0 ? 1u : acc_dw);
+        mma(kColDW5 + tm, desc_mn(sl.H3, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
-    epi_mask64(tmp, sl.H3, s);
+    epi_mask64(tmp, sl.H3, s, f16);
     sync_then_issue();
     if (s == 0) {  // dH2 = dH3 W4 ; dW4^T += H2^T dH3
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1), kk > 0);
+      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW4 + tm, desc_mn(sl.H2, kH, kk), desc_mn(sl.H3, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+        mma(kColDW4 + tm, desc_mn(sl.H2, kH, kk), desc_mn(sl.H3, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
-    epi_mask64(tmp, sl.H2, s);
+    epi_mask64(tmp, sl.H2, s, f16);
     sync_then_issue();
     if (s == 0) {  // dCIN = dH2 W3 ; dW3^T += CIN^T dH2
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1), kk > 0);
+      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1, f16), kk > 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW3 + tm, desc_mn(sl.CIN, 32, kk), desc_mn(sl.H2, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+        mma(kColDW3 + tm, desc_mn(sl.CIN, 32, kk), desc_mn(sl.H2, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
@@ -345,26 +355,26 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       d[0] = dpre;
 #pragma unroll
       for (int j = 0; j < 15; ++j) d[1 + j] = v[j];
-      store8(sl.DL, s, 0, 16, d);
-      store8(sl.DL, s, 1, 16, d + 8);
+      store8(sl.DL, s, 0, 16, d, f16);
+      store8(sl.DL, s, 1, 16, d + 8, f16);
     }
     sync_then_issue();
     if (s == 0) {  // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
-      mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1), 0);
+      mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW2 + tm, desc_mn(sl.H1, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1), kk > 0 ? 1u : acc_dw);
+        mma(kColDW2 + tm, desc_mn(sl.H1, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
-    epi_mask64(tmp, sl.H1, s);
+    epi_mask64(tmp, sl.H1, s, f16);
     sync_then_issue();
     if (s == 0) {  // dE = dH1 W1 ; dW1^T += E^T dH1
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1), kk > 0);
+      for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1, f16), kk > 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW1 + tm, desc_mn(sl.E, LFP, kk), desc_mn(sl.H1, kH, kk), idesc(64, 1, 1), kk > 0 ? 1u : acc_dw);
+        mma(kColDW1 + tm, desc_mn(sl.E, LFP, kk), desc_mn(sl.H1, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
@@ -374,6 +384,10 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
 #pragma unroll
       for (int c = 0; c < LFP / 16; ++c) tmem_ld16(tmp + 16 * c, de + 16 * c);
       tmem_wait_ld();
+      if (f16) {
+#pragma unroll
+        for (int c = 0; c < LFP; ++c) de[c] *= gunscale;
+      }
 #pragma unroll
       for (int c = 0; c < LFP / 4; ++c)
         *reinterpret_cast<float4*>(&sl.dE[s][4 * c]) = make_float4(de[4 * c], de[4 * c + 1], de[4 * c + 2], de[4 * c + 3]);
@@ -382,7 +396,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
   }
   if (s == 0) sm.c_stop = sm.fail;
   bar_compute();
-  if (!sm.c_stop && bi >= 0) flush_dw<LFP>(tm, g, ob->grad);
+  if (!sm.c_stop && bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
 }
 
 template <int LFP>

@@ -419,7 +419,8 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   if (!(c->lr > 0.f) || !(c->beta1 >= 0.f && c->beta1 < 1.f) || !(c->beta2 >= 0.f && c->beta2 < 1.f) ||
       !(c->eps >= 0.f))
     return fail(ROMAP_ERR_INVALID_ARG, "invalid Adam hyperparameters");
-  if (c->precision != ROMAP_PREC_FP32 && c->precision != ROMAP_PREC_MIXED_BF16 && c->precision != ROMAP_PREC_MIXED_FP8)
+  if (c->precision != ROMAP_PREC_FP32 && c->precision != ROMAP_PREC_MIXED_BF16 && c->precision != ROMAP_PREC_MIXED_FP8 &&
+      c->precision != ROMAP_PREC_MIXED_FP16)
     return fail(ROMAP_ERR_INVALID_ARG, "unknown precision %d", c->precision);
   if (c->accuracy_mode != 0 && c->accuracy_mode != 1) return fail(ROMAP_ERR_INVALID_ARG, "accuracy_mode is 0 or 1");
   if (c->single_net != 0 && c->single_net != 1) return fail(ROMAP_ERR_INVALID_ARG, "single_net is 0 or 1");
@@ -482,6 +483,7 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   for (int k = 0; k < 3; ++k) G.bg_const[k] = c->bg_const[k];
   G.accuracy = c->accuracy_mode ? 1 : 0;
   G.fp8 = c->precision == ROMAP_PREC_MIXED_FP8 ? 1 : 0;
+  G.f16 = c->precision == ROMAP_PREC_MIXED_FP16 ? 1 : 0;
   G.single_net = c->single_net ? 1 : 0;
   *g = G;
   return ROMAP_OK;

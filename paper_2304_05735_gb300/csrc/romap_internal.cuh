@@ -53,6 +53,7 @@ struct GridParams {
   float bg_const[3];
   int accuracy;            // FP64 transmittance log-sum and weights in the FP32 compositing kernel
   int fp8;                 // mixed path: hidden 64x64 forward GEMM in FP8 E4M3
+  int f16;                 // mixed path: MLP operands in FP16 instead of BF16 (backward gradient operands scaled by B)
   int single_net;          // colour logits = density-net outputs 1..3; the colour net is skipped
   int extra;               // single-network hidden layers after the first (0..2), 64x64 each
 };

@@ -33,10 +33,10 @@ __device__ __forceinline__ uint64_t desc_k(const void* buf, int K, int kk) {
 __device__ __forceinline__ uint64_t desc_mn(const void* buf, int F, int kk) {
   return make_desc(smem_u32(buf) + (uint32_t)kk * 2u * (uint32_t)(F / 8) * 128u, (uint32_t)(F / 8) * 128u, 128u);
 }
-// instruction descriptor, kind::f16: BF16 A and B, FP32 D
-__host__ __device__ constexpr uint32_t idesc(int N, int a_mn, int b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+// instruction descriptor, kind::f16: A and B both BF16 (format 1) or both FP16 (format 0, f16), FP32 D
+__host__ __device__ constexpr uint32_t idesc(int N, int a_mn, int b_mn, bool f16) {
+  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) | ((uint32_t)a_mn << 15) |
+         ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
@@ -94,21 +94,40 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ uint32_t kmaj(int r, int k, int K) {
   return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
-// row r, 8 columns starting at 8c, packed as BF16
-__device__ __forceinline__ void store8(unsigned char* buf, int r, int c, int K, const float* v) {
-  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
-  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+// MLP operands are BF16, or FP16 (f16: 3 more mantissa bits, range +-65504: values are saturated there)
+__device__ __forceinline__ uint32_t pack2(float a, float b, bool f16) {
+  if (f16) {
+    __half2 h = __floats2half2_rn(fminf(fmaxf(a, -65504.f), 65504.f), fminf(fmaxf(b, -65504.f), 65504.f));
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack2(uint32_t x, bool f16) {
+  if (f16) return __half22float2(*reinterpret_cast<const __half2*>(&x));
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x));
+}
+__device__ __forceinline__ uint16_t pack1(float a, bool f16) {
+  if (f16) {
+    __half h = __float2half_rn(fminf(fmaxf(a, -65504.f), 65504.f));
+    return *reinterpret_cast<uint16_t*>(&h);
+  }
+  __nv_bfloat16 h = __float2bfloat16_rn(a);
+  return *reinterpret_cast<uint16_t*>(&h);
+}
+// row r, 8 columns starting at 8c, packed as BF16 / FP16
+__device__ __forceinline__ void store8(unsigned char* buf, int r, int c, int K, const float* v, bool f16) {
   uint4 q;
-  q.x = *reinterpret_cast<uint32_t*>(&p0); q.y = *reinterpret_cast<uint32_t*>(&p1);
-  q.z = *reinterpret_cast<uint32_t*>(&p2); q.w = *reinterpret_cast<uint32_t*>(&p3);
+  q.x = pack2(v[0], v[1], f16); q.y = pack2(v[2], v[3], f16);
+  q.z = pack2(v[4], v[5], f16); q.w = pack2(v[6], v[7], f16);
   *reinterpret_cast<uint4*>(buf + kmaj(r, 8 * c, K)) = q;
 }
-__device__ __forceinline__ void load8(const unsigned char* buf, int r, int c, int K, float* v) {
-  uint4 q = *reinterpret_cast<const uint4*>(buf + kmaj(r, 8 * c, K));
-  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+__device__ __forceinline__ void load8(const unsigned char* buf, int r, int c, int K, float* v, bool f16) {
+  const uint4 q = *reinterpret_cast<const uint4*>(buf + kmaj(r, 8 * c, K));
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float2 f = __bfloat1622float2(h[i]);
+    const float2 f = unpack2(w[i], f16);
     v[2 * i] = f.x;
     v[2 * i + 1] = f.y;
   }
@@ -117,35 +136,37 @@ __device__ __forceinline__ void load8(const unsigned char* buf, int r, int c, in
 template <int LFP, class Smem>
 __device__ void load_weights(Smem& sm, const GridParams& g, const float* __restrict__ P, int nthreads) {
   const int t = threadIdx.x % nthreads;
+  const bool f16 = g.f16 != 0;
   for (int i = t; i < kH * LFP; i += nthreads) {
     int o = i / LFP, k = i % LFP;
     float v = k < g.LF ? P[g.mlp_off[0] + o * g.LF + k] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(sm.w1 + kmaj(o, k, LFP)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<uint16_t*>(sm.w1 + kmaj(o, k, LFP)) = pack1(v, f16);
   }
   for (int i = t; i < 16 * kH; i += nthreads) {
     int o = i / kH, k = i % kH;
-    *reinterpret_cast<__nv_bfloat16*>(sm.w2 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[g.mlp_off[1] + i]);
+    *reinterpret_cast<uint16_t*>(sm.w2 + kmaj(o, k, kH)) = pack1(P[g.mlp_off[1] + i], f16);
   }
   for (int i = t; i < kH * 32; i += nthreads) {
     int o = i / 32, k = i % 32;
     float v = k < g.cin ? P[g.mlp_off[2] + o * g.cin + k] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(sm.w3 + kmaj(o, k, 32)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<uint16_t*>(sm.w3 + kmaj(o, k, 32)) = pack1(v, f16);
   }
   const int64_t off4 = g.extra >= 1 ? g.mlp_off[5] : g.mlp_off[3];  // single network: its hidden layer 2
   for (int i = t; i < kH * kH; i += nthreads) {
     int o = i / kH, k = i % kH;
-    *reinterpret_cast<__nv_bfloat16*>(sm.w4 + kmaj(o, k, kH)) = __float2bfloat16_rn(P[off4 + i]);
+    *reinterpret_cast<uint16_t*>(sm.w4 + kmaj(o, k, kH)) = pack1(P[off4 + i], f16);
   }
   for (int i = t; i < 16 * kH; i += nthreads) {
     int o = i / kH, k = i % kH;
     float v = o < 3 ? P[g.mlp_off[4] + o * kH + k] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(sm.w5 + kmaj(o, k, kH)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<uint16_t*>(sm.w5 + kmaj(o, k, kH)) = pack1(v, f16);
   }
 }
 
-// Adds the TMEM weight-gradient accumulators of one object to its FP32 gradient (rows = input features).
+// Adds the TMEM weight-gradient accumulators of one object, times scale (the inverse of the FP16 path's gradient
+// scale, else 1), to its FP32 gradient (rows = input features).
 template <int LFP>
-__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad) {
+__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad, float scale) {
   const int t = threadIdx.x, w = t >> 5;
   if (w >= 2) return;  // rows 0..63 live in the lanes read by warps 0 and 1
   const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);
@@ -157,12 +178,12 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
     tmem_wait_ld();
     if (row < g.LF)
       for (int j = 0; j < 16; ++j)
-        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[0] + (c + j) * g.LF + row, v[j]);
+        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[0] + (c + j) * g.LF + row, v[j] * scale);
   }
   tmem_ld16(lane_base + kColDW2, v);  // dW2^T: rows = hidden (64), 16 columns (density outputs)
   tmem_wait_ld();
   for (int j = 0; j < 16; ++j)
-    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[1] + j * kH + row, v[j]);
+    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[1] + j * kH + row, v[j] * scale);
   if (g.single_net) {  // no colour net; hidden layers 2 and 3 accumulate in the DW4 and DW3 columns
     for (int x = 0; x < g.extra; ++x) {
       const uint32_t col = x == 0 ? kColDW4 : kColDW3;
@@ -171,7 +192,7 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
         tmem_ld16(lane_base + col + c, v);
         tmem_wait_ld();
         for (int j = 0; j < 16; ++j)
-          if (v[j] != 0.f) atomicAdd(dst + (c + j) * kH + row, v[j]);
+          if (v[j] != 0.f) atomicAdd(dst + (c + j) * kH + row, v[j] * scale);
       }
     }
     return;
@@ -181,18 +202,18 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
     tmem_wait_ld();
     if (row < g.cin)
       for (int j = 0; j < 16; ++j)
-        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[2] + (c + j) * g.cin + row, v[j]);
+        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[2] + (c + j) * g.cin + row, v[j] * scale);
   }
   for (int c = 0; c < kH; c += 16) {  // dW4^T: rows = hidden (64), 64 columns
     tmem_ld16(lane_base + kColDW4 + c, v);
     tmem_wait_ld();
     for (int j = 0; j < 16; ++j)
-      if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[3] + (c + j) * kH + row, v[j]);
+      if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[3] + (c + j) * kH + row, v[j] * scale);
   }
   tmem_ld16(lane_base + kColDW5, v);  // dW5^T: rows = hidden (64), columns 0..2 real
   tmem_wait_ld();
   for (int j = 0; j < 3; ++j)
-    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[4] + j * kH + row, v[j]);
+    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[4] + j * kH + row, v[j] * scale);
 }
 
 __device__ __forceinline__ float warp_incl_prefix(float v, int lane) {

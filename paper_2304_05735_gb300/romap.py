@@ -29,7 +29,7 @@ ROMAP_REPLACE = 0x4
 ROMAP_JITTER = 0x8
 
 ROMAP_CLS_OBJECT, ROMAP_CLS_BACKGROUND, ROMAP_CLS_OCCLUDER = 0, 1, 2
-ROMAP_PREC_FP32, ROMAP_PREC_MIXED_BF16, ROMAP_PREC_MIXED_FP8 = 0, 1, 2
+ROMAP_PREC_FP32, ROMAP_PREC_MIXED_BF16, ROMAP_PREC_MIXED_FP8, ROMAP_PREC_MIXED_FP16 = 0, 1, 2, 3
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
 DEALLOC_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)

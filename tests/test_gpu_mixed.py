@@ -1,4 +1,4 @@
-"""Mixed-precision training step (FP16 table copy + FP32 masters, BF16 tcgen05 MLP, FP32 accumulation) against the
+"""Mixed-precision training step (FP16 table copy + FP32 masters, BF16 or FP16 tcgen05 MLP, FP32 accumulation) against the
 FP64 oracle and against the FP32 path.  Tolerances: loss within 1e-3 relative of the oracle; gradients compared by
 relative L2 error and cosine; the measured errors are printed."""
 import numpy as np
@@ -30,8 +30,11 @@ def _cos(a, b):
     return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
 
 
+F16 = R.ROMAP_PREC_MIXED_FP16
+
+
 @pytest.mark.parametrize("kernel,prec", [(0, MIXED), (1, MIXED), (2, MIXED), (3, MIXED), (0, R.ROMAP_PREC_MIXED_FP8),
-                                         (2, R.ROMAP_PREC_MIXED_FP8)])
+                                         (2, R.ROMAP_PREC_MIXED_FP8), (0, F16), (1, F16), (2, F16), (3, F16)])
 @pytest.mark.parametrize("scene", ["plain", "masked"])
 def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
     if scene == "plain":
@@ -54,7 +57,8 @@ def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
         nh = O.hash_param_count(oc)
         rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
         rel_h, rel_m = _rel(g[:nh], ref["grad"][:nh]), _rel(g[nh:], ref["grad"][nh:])
-        print(f"\n[{scene}, kernel {kernel}, {'fp8' if prec != MIXED else 'bf16'}] mixed vs oracle: loss rel "
+        pname = {MIXED: "bf16", F16: "fp16", R.ROMAP_PREC_MIXED_FP8: "fp8"}[prec]
+        print(f"\n[{scene}, kernel {kernel}, {pname}] mixed vs oracle: loss rel "
               f"{rel_loss:.2e}, hash-grad rel L2 {rel_h:.2e} "
               f"(cos {_cos(g[:nh], ref['grad'][:nh]):.6f}), mlp-grad rel L2 {rel_m:.2e}")
         assert rel_loss < 1e-3
@@ -64,10 +68,11 @@ def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
         ctx.close()
 
 
+@pytest.mark.parametrize("prec", [MIXED, F16])
 @pytest.mark.parametrize("kernel", [0, 1, 2, 3])
-def test_mixed_batched_equals_separate(torch, kernel):
+def test_mixed_batched_equals_separate(torch, kernel, prec):
     oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, n_samples=32, rays_per_step=700, bg_random=True,
-                           precision=MIXED)
+                           precision=prec)
     scenes = synth.multi_object_scene(3, seed0=21, n_frames=2, W=64, H=48, f=64.0)
     ctx = Ctx(rc)
     try:
@@ -141,7 +146,7 @@ def test_autotuner_picks_a_measured_candidate(torch):
         ctx.close()
 
 
-@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, MIXED, R.ROMAP_PREC_MIXED_FP8])
+@pytest.mark.parametrize("precision", [R.ROMAP_PREC_FP32, MIXED, R.ROMAP_PREC_MIXED_FP8, F16])
 def test_rendered_rgb_vs_oracle_after_training(torch, precision):
     """After 30 training steps, the next step's per-ray rendered colour (Eq. 6) and loss against the FP64 oracle
     evaluated on the same FP32 master parameters: the mixed path within 2e-3 absolute RGB and 1e-3 relative loss,
@@ -164,10 +169,10 @@ def test_rendered_rgb_vs_oracle_after_training(torch, precision):
                            do_adam=False, want_rays=True)
         err = np.abs(out[:, :3] - ref["rays"][:, :3]).max()
         rel_loss = abs(loss[0] - ref["loss"][0]) / abs(ref["loss"][0])
-        name = {R.ROMAP_PREC_FP32: "fp32", MIXED: "bf16", R.ROMAP_PREC_MIXED_FP8: "fp8"}[precision]
+        name = {R.ROMAP_PREC_FP32: "fp32", MIXED: "bf16", R.ROMAP_PREC_MIXED_FP8: "fp8", F16: "fp16"}[precision]
         print(f"\n[{name}] after 30 steps: max |RGB - oracle| {err:.2e}, "
               f"loss rel {rel_loss:.2e}, mean |RGB| {np.abs(ref['rays'][:, :3]).mean():.3f}")
-        if precision == MIXED:
+        if precision in (MIXED, F16):
             assert err < 2e-3 and rel_loss < 1e-3
         elif precision == R.ROMAP_PREC_MIXED_FP8:
             # E4M3 keeps 3 mantissa bits: the hidden layer's outputs carry about 1% error, the rendered colour a few
