@@ -165,9 +165,9 @@ DTYPES = {"mixed": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation,
                  "Adam)"}
 KERNEL_SOURCES = {
     "fp32": ("kernels_tile.cu", "device_common.cuh", "romap_internal.cuh"),
-    "mixed": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
-    "fp8": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
-    "fp16": ("kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
+    "mixed": ("tc_tile_kernel.cuh", "kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
+    "fp8": ("tc_tile_kernel.cuh", "kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
+    "fp16": ("tc_tile_kernel.cuh", "kernels_tc16.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
 }
 
 
@@ -181,13 +181,14 @@ def kernel_source_hash(precision):
 
 
 def profiled_traffic(kernel, precision):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel source is unchanged."""
+    """Per-launch DRAM bytes of `kernel` on this workload from the committed ncu summary, if the kernel source is
+    unchanged."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
-        e = d.get(f"{kernel}|{precision}")
+        e = d.get(f"{kernel}|{precision}|{next(k for k, v in WORKLOADS.items() if v is WORKLOAD)}")
         if e and e.get("source_hash") == kernel_source_hash(precision):
             return e.get("bytes_per_launch_full_workload")
     except (OSError, ValueError):
@@ -411,10 +412,14 @@ def run_ours(args):
         achieved = bytes_per_sample * live_per_step / (bwd_ms / 1e3) / 1e9
         tpeak = peaks.get("bf16_tflops_sustained") or 1700.0
         tach = flop_bwd / (bwd_ms / 1e3) / 1e12
-        kname = TC_KERNEL if not autotune or autotune["chosen"] != "warp-specialized" else WS_KERNEL
+        ws = bool(autotune and autotune["chosen"] and autotune["chosen"].startswith("warp-specialized"))
+        kname = WS_KERNEL if ws else TC_KERNEL.replace("BF16", {"fp16": "FP16", "fp8": "FP8/BF16"}.get(main_prec,
+                                                                                                        "BF16"))
+        if autotune and autotune["chosen"]:
+            kname += f"; autotuned: {autotune['chosen']}"
         roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm,
-                    "traffic": profiled_traffic(TC_TRAFFIC_KEY, main_prec) if kname == TC_KERNEL else None,
+                    "traffic": profiled_traffic(TC_TRAFFIC_KEY, main_prec) if not ws else None,
                     "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback",
                     "work_per_unit": f"{bytes_per_sample} B per live sample (FP16 gather {8 * lvl * 4} B + FP32 "
                                      f"scatter-add {8 * lvl * 8} B)",
@@ -565,7 +570,8 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(n_rays=4096, steps=1)
+        cpu = cpu_baseline_all_cores(n_rays=4096)
+        cpu["single_core"] = cpu_baseline(n_rays=4096, steps=1)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
@@ -591,16 +597,16 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # the CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def _oracle_setup(n_rays):
-    """One object of the workload (its first seed, up to 4 frames, its occupancy bitgrid if the workload culls)."""
+def _oracle_setup(n_rays, k=0):
+    """Object k of the workload (seed seed0 + k, up to 4 frames, its occupancy bitgrid if the workload culls)."""
     import numpy as np
 
     from oracle import romap_oracle as O
     from paper_2304_05735_gb300 import synth
 
     w = WORKLOAD
-    sc = synth.multi_object_scene(1, seed0=w["seed0"], n_frames=min(4, w["frames"]), W=w["width"], H=w["height"],
-                                  f=w["focal"])[0]
+    sc = synth.multi_object_scene(1, seed0=w["seed0"] + k, n_frames=min(4, w["frames"]), W=w["width"],
+                                  H=w["height"], f=w["focal"])[0]
     occ = None
     if w["occupancy"]:
         occ = synth.occupancy_bits(sc.shape, sc.half, dilate=w["occupancy"]["dilate"], p=w["occupancy"]["p"],
@@ -629,6 +635,54 @@ def cpu_baseline(n_rays=4096, steps=1):
     return {"value": live / el, "unit": "samples/s", "cores": 1, "kind": "oracle",
             "sample": f"{steps} step(s) of 1 object x {n_rays} rays x {WORKLOAD['samples_per_ray']} samples at the "
                       f"workload's model size (FP64 C oracle, single thread), {live} live samples in {el:.1f} s"}
+
+
+def _oracle_worker(workload, k, n_rays, barrier, queue):
+    """One process of the all-cores baseline: one oracle step of object k, timed after every worker is ready."""
+    global WORKLOAD
+    import numpy as np
+
+    WORKLOAD = WORKLOADS[workload]
+    O, oc, sc, pool, p, occ = _oracle_setup(n_rays, k)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    r = O.train_step(oc, sc.half.astype(np.float32), sc.seed, 1, pool, p, m, v, occ=occ, want_samples=True)
+    t1 = time.perf_counter()
+    queue.put((int(r["samples"][:, :, 5].sum()), t0, t1))
+
+
+def cpu_baseline_all_cores(n_rays=4096, workers=None):
+    """The oracle on every host core: one single-threaded process per core (started with spawn), each running one
+    step of a different object of the workload; live samples of all processes / wall time from the first start to
+    the last finish."""
+    import multiprocessing as mp
+
+    workers = workers or os.cpu_count() or 1
+    name = next(k for k, v in WORKLOADS.items() if v is WORKLOAD)
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(workers), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(name, k, n_rays, barrier, queue)) for k in range(workers)]
+    for pr in procs:
+        pr.start()
+    res, deadline = [], time.time() + 900
+    while len(res) < workers:  # a worker that dies ends the wait instead of leaving it blocked
+        try:
+            res.append(queue.get(timeout=5))
+        except Exception:
+            if time.time() > deadline or any(pr.exitcode not in (None, 0) for pr in procs):
+                for pr in procs:
+                    if pr.is_alive():
+                        pr.terminate()
+                raise RuntimeError("an oracle worker of the all-cores baseline failed")
+    for pr in procs:
+        pr.join()
+    live = sum(r[0] for r in res)
+    el = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": live / el, "unit": "samples/s", "cores": workers, "kind": "oracle",
+            "sample": f"{workers} processes x 1 step of 1 object x {n_rays} rays x {WORKLOAD['samples_per_ray']} "
+                      f"samples at the workload's model size (FP64 C oracle, one thread each, objects seed0 .. "
+                      f"seed0 + {workers - 1}), {live} live samples in {el:.1f} s"}
 
 
 def run_reference(args):

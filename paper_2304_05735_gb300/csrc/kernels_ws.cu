@@ -95,12 +95,12 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 // ---------------------------------------------------------------------------------------------------------------
 // memory warps: scatter the tile that left a slot, then gather the next tile into it
 // ---------------------------------------------------------------------------------------------------------------
-template <int LFP>
+template <int LFP, bool F16>
 __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, const RayBuf& R, int tile_lo,
                             int tile_step, int n) {
   const int s = threadIdx.x - kCompute;
   constexpr int LMAX = LFP / 2;
-  const bool f16 = g.f16 != 0;
+  constexpr bool f16 = F16;
   for (int k = 0; k < n + 2; ++k) {
     if (sm.fail) break;
     const int slot = k & 1;
@@ -162,14 +162,14 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
 // ---------------------------------------------------------------------------------------------------------------
 // compute warps: forward, compositing, backward of one tile at a time
 // ---------------------------------------------------------------------------------------------------------------
-template <int LFP>
+template <int LFP, bool F16>
 __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf R,
                              int32_t* status, int tile_lo, int tile_step, int n, uint32_t& phase, bool& pending) {
   const int s = threadIdx.x, warp = s >> 5;
   const uint32_t tm = sm.tmem_base;
   // FP16 operands: gradient operands scaled by the object's batch size B, FP32 results unscaled (as the lockstep
   // kernel)
-  const bool f16 = g.f16 != 0;
+  constexpr bool f16 = F16;
   auto unscale_of = [&](int bi_) { return f16 ? 1.0f / (float)(b.ray_base[bi_ + 1] - b.ray_base[bi_]) : 1.0f; };
   const uint32_t tmp = tm + ((uint32_t)(32 * warp) << 16) + kColTmp;
   const uint32_t dtmp = tm + kColTmp;
@@ -399,7 +399,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
   if (!sm.c_stop && bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
 }
 
-template <int LFP>
+template <int LFP, bool F16>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_tile_ws(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int interleave) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -432,8 +432,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   tc_after();
   uint32_t phase = 0;
   bool pending = false;
-  if (warp < 4) compute_role<LFP>(sm, g, b, dyn, R, status, tile_lo, tile_step, n, phase, pending);
-  else memory_role<LFP>(sm, g, b, R, tile_lo, tile_step, n);
+  if (warp < 4) compute_role<LFP, F16>(sm, g, b, dyn, R, status, tile_lo, tile_step, n, phase, pending);
+  else memory_role<LFP, F16>(sm, g, b, R, tile_lo, tile_step, n);
   if (t == 0 && sm.fail) {
     if (status) atomicOr(status, 2);
     if (pending) mbar_wait(&sm.mma_bar, phase ^ 1u);  // bounded: let MMAs in flight finish before freeing TMEM
@@ -445,28 +445,33 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 
 static_assert(offsetof(WsSlot<16>, dE) % 16 == 0 && offsetof(WsSlot<32>, dE) % 16 == 0, "float4 rows of dE");
 
-template <int LFP>
+template <int LFP, bool F16>
 void launch_ws_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status, int max_tiles,
                  int n_ctas, int interleave, cudaStream_t stream) {
   int bytes = (int)sizeof(WsSmem<LFP>);
   if (bytes < 116 * 1024) bytes = 116 * 1024;  // one CTA per SM: the 512-column TMEM allocation never waits
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_ws<LFP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_tile_ws<LFP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr_set = true;
   }
   // the plan's tile count is read on the device; max_tiles only bounds the grid
   int grid = n_ctas < max_tiles ? n_ctas : max_tiles;
   if (grid < 1) return;
-  k_tile_ws<LFP><<<grid, kWsThreads, bytes, stream>>>(g, b, dyn, r, status, interleave);
+  k_tile_ws<LFP, F16><<<grid, kWsThreads, bytes, stream>>>(g, b, dyn, r, status, interleave);
 }
 
 }  // namespace
 
 void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int max_tiles, int n_ctas, int interleave, cudaStream_t stream) {
-  if (g.LF <= 16) launch_ws_t<16>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
-  else launch_ws_t<32>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+  if (g.f16) {
+    if (g.LF <= 16) launch_ws_t<16, true>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_ws_t<32, true>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+  } else {
+    if (g.LF <= 16) launch_ws_t<16, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_ws_t<32, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+  }
 }
 
 }  // namespace romap

@@ -259,6 +259,9 @@ void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDy
 // work on the same few objects at a time (their tables and gradients then stay in L2).
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int total_tiles, int n_ctas, int interleave, cudaStream_t stream);
+// the FP16-operand instances of launch_tile_tc
+void launch_tile_tc_f16(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
+                        int total_tiles, int n_ctas, int interleave, cudaStream_t stream);
 void launch_to_half(const float* params, uint16_t* table_h, int64_t n_hash, cudaStream_t stream);
 // Warp-specialized variant of launch_tile_tc (same results): compute warps run the MMA chain of one tile while
 // memory warps gather the next tile and scatter the previous one.
