@@ -61,6 +61,9 @@ typedef int32_t romap_status;
 #define ROMAP_OBJECT_FRAME 0x2u /* rays are already in the object frame */
 #define ROMAP_REPLACE 0x4u      /* romap_add_rays: replace the pool instead of appending */
 #define ROMAP_JITTER 0x8u       /* functional forward: stratified jitter instead of midpoints */
+#define ROMAP_ASYNC_HOST 0x10u  /* romap_add_rays(_multi): page-locked host arrays are copied asynchronously on the
+                                   context's stream; the caller keeps them unchanged until the stream has passed
+                                   the call (without the flag the call waits for the copy) */
 
 /* ray classes from the instance mask (Sec. V-B) */
 #define ROMAP_CLS_OBJECT 0     /* R_o: photometric loss, Eq. 7 */
@@ -246,6 +249,22 @@ ROMAP_API romap_status romap_pool_size(romap_ctx* ctx, int32_t id, int64_t* out_
  * applies Adam.  out_loss (host, nullable) receives n_ids losses of the
  * last step.  Listed ids must be distinct. */
 ROMAP_API romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps, float* out_loss);
+/* romap_train_step without waiting for the device: the steps and, when
+ * out_loss is not NULL, a copy of the last step's n_ids losses into out_loss
+ * (page-locked host or device memory; other host memory makes the call wait
+ * for the copy) are enqueued on the context's stream and the call returns.
+ * Read out_loss after the stream has passed the call (an event recorded on
+ * the stream after it, or a stream synchronisation), so that the host can
+ * prepare the next step's rays while the device trains.  Device-side errors
+ * of these steps (a non-finite loss, which also shows in out_loss, or a
+ * bounded wait that gave up) are reported by romap_check_device_status or
+ * by the next call that reads losses synchronously. */
+ROMAP_API romap_status romap_train_step_async(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps,
+                                              float* out_loss);
+/* Waits for the context's stream and reports (then clears) the device
+ * status word: ROMAP_ERR_NONFINITE for a non-finite loss, ROMAP_ERR_TIMEOUT
+ * for a bounded device wait that gave up, else ROMAP_OK. */
+ROMAP_API romap_status romap_check_device_status(romap_ctx* ctx);
 /* The forward/backward half of a step without Adam: gradients are left in
  * the objects' gradient buffers (read them with romap_get_grad).
  * out_loss (host, nullable): 5 floats per object: L, then the rgb, rr,

@@ -299,6 +299,22 @@ __global__ void k_advance_step(GridParams g, BatchDesc b) {
   }
 }
 
+// Per-object loss of the batch's last step, L = (loss sum) / B with the same FP32 operations as the host read, into a
+// device array: the source of an asynchronous loss copy.
+__global__ void k_final_losses(const BatchDyn* __restrict__ dyn, const int32_t* __restrict__ ray_base, int n,
+                               float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float B = (float)(ray_base[i + 1] - ray_base[i]);
+  const float inv = B > 0.f ? 1.0f / B : 0.0f;
+  out[i] = dyn[i].loss[0] * inv;
+}
+
+void launch_final_losses(const BatchDyn* dyn, const BatchDesc& b, float* out, cudaStream_t stream) {
+  if (b.n <= 0) return;
+  k_final_losses<<<(b.n + 127) / 128, 128, 0, stream>>>(dyn, b.ray_base, b.n, out);
+}
+
 void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream) {
   if (b.n <= 0) return;
   int64_t n4 = g.n_params_pad / 4;

@@ -96,7 +96,7 @@ struct romap_ctx {
   ObjectDev* objs_dev = nullptr;
   ObjectDev* fn_obj_dev = nullptr;   // object record of functional calls
   // step workspace
-  DevBuf ws_rays, ws_samples, ws_blocks, ws_batch, ws_dyn, ws_stage, ws_plan, ws_mesh, ws_mesh_out;
+  DevBuf ws_rays, ws_samples, ws_blocks, ws_batch, ws_dyn, ws_stage, ws_plan, ws_mesh, ws_mesh_out, ws_loss;
   int64_t cap_rays = 0, cap_samples = 0, cap_blocks = 0, cap_batch = 0;
   // tile plan of the mixed-precision path (capacities: rays, ray blocks, batch entries, tiles)
   int64_t cap_plan[4] = {0, 0, 0, 0};
@@ -806,7 +806,8 @@ romap_status romap_destroy(romap_ctx* ctx) {
   dev_free(ctx, ctx->totals);
   dev_free(ctx, ctx->status);
   dev_free(ctx, ctx->live_counter);
-  for (DevBuf* b : {&ctx->ws_rays, &ctx->ws_samples, &ctx->ws_blocks, &ctx->ws_batch, &ctx->ws_dyn, &ctx->ws_stage})
+  for (DevBuf* b : {&ctx->ws_rays, &ctx->ws_samples, &ctx->ws_blocks, &ctx->ws_batch, &ctx->ws_dyn, &ctx->ws_stage,
+                    &ctx->ws_plan, &ctx->ws_mesh, &ctx->ws_mesh_out, &ctx->ws_loss})
     dev_free(ctx, b->p);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->dyn_host) cudaFreeHost(ctx->dyn_host);
@@ -1120,7 +1121,8 @@ romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* r, int
   ROMAP_TRY(check_id(ctx, id));
   if (!r || n < 0) return fail(ROMAP_ERR_INVALID_ARG, "rays must not be NULL and n >= 0");
   if (n > 0 && (!r->origin || !r->dir || !r->rgb)) return fail(ROMAP_ERR_INVALID_ARG, "origin, dir and rgb are required");
-  if (flags & ~(ROMAP_DEVICE_PTR | ROMAP_OBJECT_FRAME | ROMAP_REPLACE)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  if (flags & ~(ROMAP_DEVICE_PTR | ROMAP_OBJECT_FRAME | ROMAP_REPLACE | ROMAP_ASYNC_HOST))
+    return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
   Object& o = ctx->objs[id];
   bool dev = (flags & ROMAP_DEVICE_PTR) != 0;
   int64_t start = (flags & ROMAP_REPLACE) ? 0 : o.pool_n;
@@ -1145,7 +1147,8 @@ romap_status romap_add_rays(romap_ctx* ctx, int32_t id, const romap_rays* r, int
                         o.pool_rgb + 3 * start, o.pool_depth + start, o.pool_cls + start, ctx->stream);
   ctx->launches += 1;
   CUDA_TRY(cudaGetLastError());
-  if (sr.pinned) CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // pinned host buffers are read asynchronously
+  // page-locked host buffers are read asynchronously: wait for them unless the caller keeps them (ROMAP_ASYNC_HOST)
+  if (sr.pinned && !(flags & ROMAP_ASYNC_HOST)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   o.pool_n = need;
   return sync_object(ctx, id);
 }
@@ -1156,7 +1159,8 @@ romap_status romap_add_rays_multi(romap_ctx* ctx, const int32_t* ids, const int6
   std::vector<int32_t> v;
   ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
   if (!counts || !r) return fail(ROMAP_ERR_INVALID_ARG, "counts and rays must not be NULL");
-  if (flags & ~(ROMAP_DEVICE_PTR | ROMAP_OBJECT_FRAME | ROMAP_REPLACE)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  if (flags & ~(ROMAP_DEVICE_PTR | ROMAP_OBJECT_FRAME | ROMAP_REPLACE | ROMAP_ASYNC_HOST))
+    return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
   const bool dev = (flags & ROMAP_DEVICE_PTR) != 0, replace = (flags & ROMAP_REPLACE) != 0;
   int64_t n = 0;
   for (int k = 0; k < n_ids; ++k) {
@@ -1201,7 +1205,8 @@ romap_status romap_add_rays_multi(romap_ctx* ctx, const int32_t* ids, const int6
     CUDA_TRY(cudaGetLastError());
     pinned = sr.pinned;
   }
-  if (pinned) CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // pinned host buffers are read asynchronously
+  // page-locked host buffers are read asynchronously: wait for them unless the caller keeps them (ROMAP_ASYNC_HOST)
+  if (pinned && !(flags & ROMAP_ASYNC_HOST)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   for (int k = 0; k < n_ids; ++k) {
     Object& o = ctx->objs[ids[k]];
     o.pool_n = (replace ? 0 : o.pool_n) + counts[k];
@@ -1315,11 +1320,10 @@ static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, 
   return ROMAP_OK;
 }
 
-romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps, float* out_loss) {
-  ROMAP_TRY(check_ctx(ctx));
-  if (n_steps < 1) return fail(ROMAP_ERR_INVALID_ARG, "n_steps must be >= 1");
-  std::vector<int32_t> v;
-  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+namespace {
+
+// n_steps training steps of the validated batch v (CUDA-graph replay once captured), all enqueued on the stream
+romap_status run_train_steps(romap_ctx* ctx, const std::vector<int32_t>& v, int32_t n_steps) {
   // the graph key: the batch composition (object slots and their rays per step) and the precision
   std::vector<int32_t> key(v.begin(), v.end());
   for (int32_t id : v) key.push_back(ctx->objs_host[id].n_rays);
@@ -1350,12 +1354,57 @@ romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids,
     if (use_graph && (ctx->graph_key != key || !ctx->step_graph || ctx->graph_ws_generation != ctx->ws_generation))
       ROMAP_TRY(capture_step(ctx, v, key));
   }
+  return ROMAP_OK;
+}
+
+}  // namespace
+
+romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps, float* out_loss) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (n_steps < 1) return fail(ROMAP_ERR_INVALID_ARG, "n_steps must be >= 1");
+  std::vector<int32_t> v;
+  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+  ROMAP_TRY(run_train_steps(ctx, v, n_steps));
   if (out_loss) {
     std::vector<float> tmp(5 * (size_t)n_ids);
     ROMAP_TRY(read_losses(ctx, n_ids, tmp.data(), 5, v));
     for (int i = 0; i < n_ids; ++i) out_loss[i] = tmp[5 * i];
   }
   return ROMAP_OK;
+}
+
+romap_status romap_train_step_async(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, int32_t n_steps,
+                                    float* out_loss) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (n_steps < 1) return fail(ROMAP_ERR_INVALID_ARG, "n_steps must be >= 1");
+  std::vector<int32_t> v;
+  ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
+  ROMAP_TRY(run_train_steps(ctx, v, n_steps));
+  if (out_loss) {  // L = loss sum / B on the device, then one asynchronous copy into the caller's buffer
+    std::vector<int32_t> rays(v.size());
+    for (size_t i = 0; i < v.size(); ++i) rays[i] = ctx->objs_host[v[i]].n_rays;
+    HostBatch hb;
+    build_batch(v, rays, &hb);
+    BatchDesc b;
+    ROMAP_TRY(upload_batch(ctx, hb, &b));  // (the step left these arrays in place: no copy)
+    ROMAP_TRY(grow(ctx, ctx->ws_loss, sizeof(float) * v.size()));
+    launch_final_losses(ctx->dyn, b, (float*)ctx->ws_loss.p, ctx->stream);
+    ctx->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out_loss, ctx->ws_loss.p, sizeof(float) * v.size(), cudaMemcpyDefault, ctx->stream));
+  }
+  return ROMAP_OK;
+}
+
+romap_status romap_check_device_status(romap_ctx* ctx) {
+  ROMAP_TRY(check_ctx(ctx));
+  int32_t st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (st == 0) return ROMAP_OK;
+  CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
+  if (st & kStatusTimeout) return fail(ROMAP_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
+  return fail(ROMAP_ERR_NONFINITE, "non-finite loss (status %d)", st);
 }
 
 // ---- incremental training data and budgeted training (Sec. V-A-1, Eq. 5; Sec. VI) ---------------------------------

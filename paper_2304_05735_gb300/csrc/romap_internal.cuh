@@ -235,6 +235,7 @@ void launch_tile_mlp(int mode, const GridParams& g, const BatchDesc& b, const Ba
 void launch_composite(int mode, const GridParams& g, const BatchDesc& b, RayBuf r, SampleBuf s, BatchDyn* dyn,
                       int32_t* status, cudaStream_t stream);
 void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream);
+void launch_final_losses(const BatchDyn* dyn, const BatchDesc& b, float* out, cudaStream_t stream);
 void launch_scatter_slots(const GridParams& g, int64_t n_rays, const RayBuf r, const SampleBuf s, const float* src,
                           int src_stride, float* dst, int dst_stride, cudaStream_t stream);
 void launch_sample_slots(const GridParams& g, int64_t n_rays, const RayBuf r, const SampleBuf s, float* dst,

@@ -8,10 +8,10 @@
 // Per tile, in one CTA of 128 threads (thread s <-> sample slot s <-> TMEM lane s):
 //   1. sample positions of the slot (same FP32 operations as the sampling kernels: bit-identical),
 //   2. multiresolution hash encoding gathered from the FP16 copy of the table, interpolated in FP32,
-//      stored as BF16 (the A operand of the first layer),
-//   3. the five MLP layers (Sec. V; hidden 64) as tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM),
-//      each followed by an epilogue that reads its row from TMEM, applies the activation and writes the
-//      next BF16 operand row to shared memory,
+//      stored as BF16, or FP16 when F16 (the A operand of the first layer),
+//   3. the five MLP layers (Sec. V; hidden 64) as tcgen05.mma kind::f16 (BF16 x BF16 or FP16 x FP16 -> FP32
+//      in TMEM), each followed by an epilogue that reads its row from TMEM, applies the activation and writes
+//      the next operand row to shared memory,
 //   4. volume rendering (Eq. 6), the losses of Eq. 7-11 and the compositing adjoint, one warp per ray,
 //   5. the backward: per layer one GEMM for the input gradient (dX = dY W: A = dY K-major, B = W read
 //      MN-major from the forward copy) and one for the weight gradient (dW^T = X^T dY over the 128 samples:
@@ -19,7 +19,8 @@
 //      TMEM across all tiles of the same object and added to the FP32 gradient once per object change,
 //   6. the hash-gradient scatter (FP32 vector atomics into the FP32 gradient of the table).
 // The transmittance scan, the losses and every accumulation stay in FP32; Adam keeps FP32 masters and
-// refreshes the FP16 table copy.
+// refreshes the FP16 table copy.  With FP16 operands the backward's gradient operands are scaled by the object's
+// batch size B and the FP32 results unscaled (FP16's range; BF16 needs no scale).
 //
 // Shared-memory operands use the canonical no-swizzle core-matrix layout (8 rows x 16 bytes per core
 // matrix): for a K-major [R rows][K] buffer, element (r, k) sits at (r/8)*(K/8)*128 + (k/8)*128 +

@@ -27,6 +27,7 @@ ROMAP_DEVICE_PTR = 0x1
 ROMAP_OBJECT_FRAME = 0x2
 ROMAP_REPLACE = 0x4
 ROMAP_JITTER = 0x8
+ROMAP_ASYNC_HOST = 0x10
 
 ROMAP_CLS_OBJECT, ROMAP_CLS_BACKGROUND, ROMAP_CLS_OCCLUDER = 0, 1, 2
 ROMAP_PREC_FP32, ROMAP_PREC_MIXED_BF16, ROMAP_PREC_MIXED_FP8, ROMAP_PREC_MIXED_FP16 = 0, 1, 2, 3
@@ -101,6 +102,8 @@ SIGNATURES = {
     "romap_get_occupancy": (_i32, [_vp, _i32, _vp, _vp]),
     "romap_add_rays": (_i32, [_vp, _i32, _P(romap_rays), _i64, _u32]),
     "romap_add_rays_multi": (_i32, [_vp, _vp, _vp, _i32, _P(romap_rays), _u32]),
+    "romap_train_step_async": (_i32, [_vp, _vp, _i32, _i32, _vp]),
+    "romap_check_device_status": (_i32, [_vp]),
     "romap_pool_size": (_i32, [_vp, _i32, _P(_i64)]),
     "romap_train_step": (_i32, [_vp, _vp, _i32, _i32, _vp]),
     "romap_forward_backward": (_i32, [_vp, _vp, _i32, _vp]),
