@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 from paper_2304_05735_gb300.sharding import max_over_ranks, sum_over_ranks  # noqa: E402
 
 METRIC = "train samples/s (fwd+bwd+Adam), batched mixed vs plain fp32, at oracle-matched loss"
+WORKLOAD_KEY = "multi8"  # the chosen workload's key (set in main)
 WORKLOADS = {
     # the default: 8 objects of equal batch size (weak scaling under torchrun: every rank trains 8 objects)
     "multi8": dict(
@@ -94,6 +95,8 @@ def parse():
     ap.add_argument("--precision", choices=("fp32", "mixed", "fp8", "fp16"), default="mixed")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="multi8")
     ap.add_argument("--loss-steps", type=int, default=200)
+    ap.add_argument("--objects", type=int, default=None,
+                    help="train only the workload's first N objects (a smaller case of the same kind, e.g. for ncu)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -192,7 +195,7 @@ def profiled_traffic(kernel, precision):
         return None
     try:
         d = json.load(open(path))
-        e = d.get(f"{kernel}|{precision}|{next(k for k, v in WORKLOADS.items() if v is WORKLOAD)}")
+        e = d.get(f"{kernel}|{precision}|{workload_id()}")
         if e and e.get("source_hash") == kernel_source_hash(precision):
             return e.get("bytes_per_launch_full_workload")
     except (OSError, ValueError):
@@ -682,7 +685,7 @@ def cpu_baseline_all_cores(n_rays=4096, workers=None):
     import multiprocessing as mp
 
     workers = workers or os.cpu_count() or 1
-    name = next(k for k, v in WORKLOADS.items() if v is WORKLOAD)
+    name = WORKLOAD_KEY
     ctx = mp.get_context("spawn")
     barrier, queue = ctx.Barrier(workers), ctx.Queue()
     procs = [ctx.Process(target=_oracle_worker, args=(name, k, n_rays, barrier, queue)) for k in range(workers)]
@@ -949,10 +952,21 @@ def run_table4(args):
     print(json.dumps(out), flush=True)
 
 
+def workload_id():
+    """The workload's key, with the object count when --objects shrank it (keys of profiles/dram_traffic.json)."""
+    return WORKLOAD_KEY + (f":objects={WORKLOAD['objects']}" if WORKLOAD is not WORKLOADS[WORKLOAD_KEY] else "")
+
+
 def main():
-    global WORKLOAD
+    global WORKLOAD, WORKLOAD_KEY
     args = parse()
+    WORKLOAD_KEY = args.workload
     WORKLOAD = WORKLOADS[args.workload]
+    if args.objects is not None and args.workload in ("multi8", "uneven32"):
+        if not 1 <= args.objects <= WORKLOAD["objects"]:
+            raise SystemExit(f"--objects must be in 1..{WORKLOAD['objects']}")
+        WORKLOAD = dict(WORKLOAD, objects=args.objects,
+                        name=WORKLOAD["name"] + f" (only the first {args.objects} objects)")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stream96":
