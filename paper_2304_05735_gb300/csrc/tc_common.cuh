@@ -94,10 +94,12 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ uint32_t kmaj(int r, int k, int K) {
   return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
-// MLP operands are BF16, or FP16 (f16: 3 more mantissa bits, range +-65504: values are saturated there)
+// MLP operands are BF16, or FP16 (f16: 3 more mantissa bits, range +-65504: values are saturated there; a NaN
+// stays a NaN, so that a broken step still shows as a non-finite loss)
+__device__ __forceinline__ float sat_f16(float x) { return x > 65504.f ? 65504.f : (x < -65504.f ? -65504.f : x); }
 __device__ __forceinline__ uint32_t pack2(float a, float b, bool f16) {
   if (f16) {
-    __half2 h = __floats2half2_rn(fminf(fmaxf(a, -65504.f), 65504.f), fminf(fmaxf(b, -65504.f), 65504.f));
+    __half2 h = __floats2half2_rn(sat_f16(a), sat_f16(b));
     return *reinterpret_cast<uint32_t*>(&h);
   }
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -109,7 +111,7 @@ __device__ __forceinline__ float2 unpack2(uint32_t x, bool f16) {
 }
 __device__ __forceinline__ uint16_t pack1(float a, bool f16) {
   if (f16) {
-    __half h = __float2half_rn(fminf(fmaxf(a, -65504.f), 65504.f));
+    __half h = __float2half_rn(sat_f16(a));
     return *reinterpret_cast<uint16_t*>(&h);
   }
   __nv_bfloat16 h = __float2bfloat16_rn(a);
