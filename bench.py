@@ -282,6 +282,44 @@ def add_objects(R, h, items):
     return ids
 
 
+def curve_steps(k):
+    """Step indices of the reported loss curve: the first step, then every tenth of the run."""
+    return sorted({0, *range(max(1, k // 10) - 1, k, max(1, k // 10))})
+
+
+def psnr_rays(items, per_object=4096, seed=123):
+    """A fixed sample of each object's training rays (object and background classes) for the PSNR of a trained model."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for it in items:
+        p = it.scene.pool
+        keep = np.nonzero(p["cls"] <= 1)[0]
+        sel = np.sort(rng.choice(keep, min(per_object, keep.size), replace=False))
+        out.append({k: np.ascontiguousarray(p[k][sel]) for k in ("origin", "dir", "rgb", "cls")})
+    return out
+
+
+def trained_psnr(R, h, ids, evalset, bg=(0.5, 0.5, 0.5)):
+    """Training-view PSNR of each trained object: its rays rendered by romap_render (FP32 forward from the FP32
+    parameters, midpoint samples) over a grey background, against the target colour (object rays) or that
+    background (background rays)."""
+    import numpy as np
+
+    bgc = np.array(bg, np.float32)
+    vals = []
+    for oid, e in zip(ids, evalset):
+        m = e["cls"].size
+        col = np.zeros((m, 3), np.float32)
+        R.check(R.romap_render(h, oid, e["origin"].ctypes.data, e["dir"].ctypes.data, m, bgc.ctypes.data,
+                               col.ctypes.data, None, None, 0), "romap_render")
+        tgt = np.where(e["cls"][:, None] == 0, e["rgb"], bgc[None, :])
+        mse = float(((col.astype(np.float64) - tgt) ** 2).mean())
+        vals.append(-10.0 * np.log10(max(mse, 1e-12)))
+    return {"mean": float(np.mean(vals)), "median": float(np.median(vals)), "min": float(np.min(vals))}
+
+
 def timed(torch, fn, world, dist):
     """Runs fn() between barrier + synchronize brackets; returns (device ms on the current stream, max over ranks)."""
     if world > 1:
@@ -324,8 +362,9 @@ def run_ours(args):
     main_prec = args.precision
 
     # ---- loss comparison: same seeds, batched mixed vs batched FP32, per-step losses (untimed) -------------------
-    curves = {}
+    curves, psnr = {}, {}
     if not args.no_plain:
+        evalset = psnr_rays(items)
         # a second FP32 run with the same seeds measures the run-to-run spread of FP32 training itself (atomic
         # accumulation order), the floor under any mixed-vs-FP32 difference
         for prec in ("fp32", "mixed", "fp32_repeat"):
@@ -336,6 +375,7 @@ def run_ours(args):
             for k in range(args.loss_steps):
                 R.check(R.romap_train_step(h, idarr, n, 1, ls[k].ctypes.data))
             curves[prec] = ls.mean(axis=1)
+            psnr[prec] = trained_psnr(R, h, ids, evalset)
             R.check(R.romap_destroy(h))
 
     # ---- the timed batched step -------------------------------------------------------------------------------------
@@ -588,7 +628,11 @@ def run_ours(args):
                     "mixed": lm, "rel_diff": (lm - lf) / lf, "matched": bool(lm <= lf * (1 + 1e-3)),
                     "fp32_run_to_run_rel_diff": abs(lr_ - lf1) / lf, "first_step_rel_diff":
                     float(abs(curves["mixed"][0] - curves["fp32"][0]) / curves["fp32"][0]),
-                    "mixed_steps_to_fp32_final_loss": int(reach[0] + 1) if reach.size else None}
+                    "mixed_steps_to_fp32_final_loss": int(reach[0] + 1) if reach.size else None,
+                    "curve": {"steps": [k + 1 for k in curve_steps(args.loss_steps)],
+                              **{name: [float(curves[name][k]) for k in curve_steps(args.loss_steps)]
+                                 for name in ("fp32", "mixed", "fp32_repeat")}},
+                    "psnr_db_after_k_steps": psnr}
         if mixed and others.get("plain_fp32_per_object") and reach.size:
             t_mixed = (reach[0] + 1) * ms / args.steps
             t_plain = args.loss_steps * others["plain_fp32_per_object"]["ms_per_step"]

@@ -38,6 +38,7 @@ def _concat(parts):
 
 
 def _rays(arrs, ptr=lambda a: a.ctypes.data):
+    """Ray struct of raw pointers into arrs: the caller keeps arrs referenced until the library has read them."""
     return R.romap_rays(*(ptr(arrs[k]) for k in KEYS))
 
 
@@ -110,8 +111,9 @@ def test_multi_replace_and_object_frame(torch):
     try:
         for i, (_, ch) in zip(rid, objs):
             ref.add_rays(i, _concat(ch))
+        all_rays = _concat([_concat(ch) for _, ch in objs])  # referenced until the call has copied it
         R.check(R.romap_add_rays_multi(new.h, new.ids(nid), (C.c_int64 * 3)(*[120, 90, 110]), 3,
-                                       C.byref(_rays(_concat([_concat(ch) for _, ch in objs]))), 0))
+                                       C.byref(_rays(all_rays)), 0))
         # replace object 0's pool by its second chunk, empty object 2's (count 0), keep object 1 out of the call
         second = objs[0][1][1]
         ref.add_rays(rid[0], second, R.ROMAP_REPLACE)
