@@ -117,10 +117,9 @@ struct Corners {
   float w[8];
 };
 
-__device__ inline void level_corners(const GridParams& g, int l, const float p[3], const float half[3],
-                                     const float inv_ext[3], Corners& c) {
-  int i0[3];
-  float f[3];
+// Cell of level l holding p: its lower corner i0 and the fractions f within it.
+__device__ __forceinline__ void level_cell(const GridParams& g, int l, const float p[3], const float half[3],
+                                           const float inv_ext[3], int i0[3], float f[3]) {
   const int N = g.res[l];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -131,19 +130,33 @@ __device__ inline void level_corners(const GridParams& g, int l, const float p[3
     i0[a] = i;
     f[a] = __fsub_rn(pos, (float)i);
   }
-  const uint32_t n1 = (uint32_t)N + 1u;
-  const bool dense = g.dense[l];
+}
+// Table index of corner k (bits x, y, z) of the cell with lower corner i0 (T = 2^log2_table_size, so the modulo of
+// the spatial hash is a mask).
+__device__ __forceinline__ uint32_t corner_index(const GridParams& g, int l, const int i0[3], int k) {
+  const uint32_t n1 = (uint32_t)g.res[l] + 1u;
+  const uint32_t cx = (uint32_t)(i0[0] + (k & 1));
+  const uint32_t cy = (uint32_t)(i0[1] + ((k >> 1) & 1));
+  const uint32_t cz = (uint32_t)(i0[2] + ((k >> 2) & 1));
+  return g.dense[l] ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) & (g.T - 1u));
+}
+// Trilinear weight of corner k for the fractions f.
+__device__ __forceinline__ float corner_weight(const float f[3], int k) {
+  const float wx = (k & 1) ? f[0] : 1.0f - f[0];
+  const float wy = ((k >> 1) & 1) ? f[1] : 1.0f - f[1];
+  const float wz = ((k >> 2) & 1) ? f[2] : 1.0f - f[2];
+  return wx * wy * wz;
+}
+
+__device__ inline void level_corners(const GridParams& g, int l, const float p[3], const float half[3],
+                                     const float inv_ext[3], Corners& c) {
+  int i0[3];
+  float f[3];
+  level_cell(g, l, p, half, inv_ext, i0, f);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    uint32_t cx = (uint32_t)(i0[0] + (k & 1));
-    uint32_t cy = (uint32_t)(i0[1] + ((k >> 1) & 1));
-    uint32_t cz = (uint32_t)(i0[2] + ((k >> 2) & 1));
-    // T = 2^log2_table_size, so the modulo is a mask
-    c.idx[k] = dense ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) & (g.T - 1u));
-    float wx = (k & 1) ? f[0] : 1.0f - f[0];
-    float wy = ((k >> 1) & 1) ? f[1] : 1.0f - f[1];
-    float wz = ((k >> 2) & 1) ? f[2] : 1.0f - f[2];
-    c.w[k] = wx * wy * wz;
+    c.idx[k] = corner_index(g, l, i0, k);
+    c.w[k] = corner_weight(f, k);
   }
 }
 

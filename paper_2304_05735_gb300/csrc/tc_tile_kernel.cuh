@@ -74,32 +74,60 @@ struct TileBufs {
 static_assert(32 * kT * sizeof(float) <= kT * kH * 2, "dL/dencoding fits in H2");
 
 // Encoding levels [l0, l1) of one sample, interpolated in FP32 from the FP16 table, into row s of a K-major BF16
-// encoding buffer; two levels per round so that 16 gathers are in flight.
+// encoding buffer; three levels per round so that 24 gathers are in flight (a gather window of 3 levels is one round).
 template <int LFP, bool F16>
 __device__ __forceinline__ void gather_rows(const GridParams& g, const ObjectDev* ob, const float p[3],
                                             unsigned char* E, int s, int l0, int l1) {
   const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
 #pragma unroll 1
-  for (int l = l0; l < l1; l += 2) {
-    const bool has1 = l + 1 < l1;
-    Corners c0, c1;
-    level_corners(g, l, p, ob->half, ob->inv_ext, c0);
-    if (has1) level_corners(g, l + 1, p, ob->half, ob->inv_ext, c1);
-    __half2 v0[8], v1[8];
+  for (int l = l0; l < l1; l += 3) {
+    // the loads of three levels go out first; only the cells' fractions are kept while they are in flight and the
+    // trilinear weights are formed from them afterwards (fewer live registers than 24 weights)
+    const bool has1 = l + 1 < l1, has2 = l + 2 < l1;
+    int i0[3];
+    float f0[3], f1[3], f2[3];
+    __half2 v0[8], v1[8], v2[8];
+    level_cell(g, l, p, ob->half, ob->inv_ext, i0, f0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      v0[k] = __ldg(tab + g.off[l] + c0.idx[k]);
-      v1[k] = has1 ? __ldg(tab + g.off[l + 1] + c1.idx[k]) : __half2{};
+    for (int k = 0; k < 8; ++k) v0[k] = __ldg(tab + g.off[l] + corner_index(g, l, i0, k));
+    if (has1) {
+      level_cell(g, l + 1, p, ob->half, ob->inv_ext, i0, f1);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v1[k] = __ldg(tab + g.off[l + 1] + corner_index(g, l + 1, i0, k));
     }
-    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+    if (has2) {
+      level_cell(g, l + 2, p, ob->half, ob->inv_ext, i0, f2);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v2[k] = __ldg(tab + g.off[l + 2] + corner_index(g, l + 2, i0, k));
+    }
+    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const float2 f0 = __half22float2(v0[k]), f1 = __half22float2(v1[k]);
-      a0 = fmaf(c0.w[k], f0.x, a0); a1 = fmaf(c0.w[k], f0.y, a1);
-      if (has1) { b0 = fmaf(c1.w[k], f1.x, b0); b1 = fmaf(c1.w[k], f1.y, b1); }
+      const float w = corner_weight(f0, k);
+      const float2 h = __half22float2(v0[k]);
+      a0 = fmaf(w, h.x, a0); a1 = fmaf(w, h.y, a1);
     }
     *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l, LFP)) = pack2(a0, a1, F16);
-    if (has1) *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l + 2, LFP)) = pack2(b0, b1, F16);
+    if (has1) {
+      float b0 = 0.f, b1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float w = corner_weight(f1, k);
+        const float2 h = __half22float2(v1[k]);
+        b0 = fmaf(w, h.x, b0); b1 = fmaf(w, h.y, b1);
+      }
+      *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l + 2, LFP)) = pack2(b0, b1, F16);
+    }
+    if (has2) {
+      float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float w = corner_weight(f2, k);
+        const float2 h = __half22float2(v2[k]);
+        d0 = fmaf(w, h.x, d0); d1 = fmaf(w, h.y, d1);
+      }
+      *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l + 4, LFP)) = pack2(d0, d1, F16);
+    }
   }
 }
 // zero row s of an encoding buffer over the levels [l0, l1)
