@@ -493,6 +493,90 @@ def test_zero_density_loss_invariant():
     assert np.all(r["grad"][O.hash_param_count(cfg):] == 0)
 
 
+def _constant_field_params(cfg, log_sigma):
+    """Parameters whose model is a constant field: every hash entry 0.5, so every encoding feature is 0.5
+    (trilinear weights sum to 1); density hidden unit 0 = relu(feature 0) = 0.5 and output 0 = 2 log_sigma * 0.5,
+    so sigma = exp(log_sigma) everywhere; every other output, hence every colour-net input, hidden unit and logit,
+    is 0, so the colour is sigmoid(0) = 1/2 in each channel, for every direction."""
+    p = np.zeros(O.param_count(cfg))
+    nh = O.hash_param_count(cfg)
+    p[:nh] = 0.5
+    LF = cfg.L * cfg.F
+    p[nh + O.mlp_layer_offset(cfg, 0) + 0 * LF + 0] = 1.0      # W1[0][0] (layer 0 is H x LF, row-major)
+    p[nh + O.mlp_layer_offset(cfg, 1) + 0 * cfg.hidden + 0] = 2.0 * log_sigma  # W2[0][0] (layer 1 is 16 x H)
+    return p
+
+
+def _live_by_grid(x, occ, half):
+    """Occupancy of sample positions from the bitgrid's definition: cell c = min(floor(u * 64), 63) per axis with
+    u = clamp((x + a) / (2 a), 0, 1) in FP32, bit c_x + 64 c_y + 4096 c_z."""
+    x = np.asarray(x, np.float32)
+    h = np.asarray(half, np.float32)
+    u = np.clip((x - (-h)) * (np.float32(1.0) / (h - (-h))), 0, 1).astype(np.float32)
+    c = np.minimum((u * np.float32(64.0)).astype(np.int64), 63)
+    bit = c[..., 0] + 64 * c[..., 1] + 4096 * c[..., 2]
+    words = np.asarray(occ, np.uint64)
+    return ((words[bit >> 6] >> (bit & 63).astype(np.uint64)) & np.uint64(1)).astype(bool)
+
+
+@pytest.mark.parametrize("culled", [False, True])
+def test_density_loss_closed_form_constant_field(culled):
+    """Eq. 7-11 at constant density sigma > 0 and constant colour c = 1/2, on a mix of object, background,
+    occluder and depth rays.  Per ray with live-sample spacings delta_i: A = 1 - exp(-sigma sum_live delta_i),
+    C_hat = c A + b (1 - A), D_hat = sum_live (T_i - T_{i+1}) t_i with T_i = exp(-sigma sum_{live j < i} delta_j);
+    L = (1/B)[sum_{R_o} ||C_hat - C||^2 + sum_{R_b} ||C_hat - b||^2 + lambda1 sum_{R_d} |D_hat - D|
+    + lambda2 sum_{R_b} sigma n_live].  With culled=True the bitgrid empties the half-box x < 0, so part of most rays
+    is culled (O-8: no density term and no opacity there).  The density term counts live samples of R_b rays only."""
+    sigma0, lam1, lam2, n = 3.0, 0.5, 0.04, 60
+    cfg = O.make_config(L=4, T=2 ** 10, growth=2.0, n_samples=16, rays_per_step=n, bg_random=True,
+                        lambda1=lam1, lambda2=lam2)
+    rng = np.random.default_rng(31)
+    pool = _mixed_pool(n, rng)
+    pool["cls"][:6] = [0, 1, 2, 0, 1, 1]           # every class present whatever the draw
+    half = np.full(3, 0.5, np.float32)
+    occ = None
+    if culled:
+        cells = np.zeros(64 ** 3, bool)
+        cells.reshape(64, 64, 64)[:, :, 32:] = True   # index [z][y][x]: keep cells with x >= 32 (x >= 0)
+        occ = np.packbits(cells.reshape(-1, 64)[:, ::-1], axis=1).view(">u8").reshape(-1).astype(np.uint64)
+    p = _constant_field_params(cfg, math.log(sigma0))
+    z = np.zeros_like(p)
+    r = O.train_step(cfg, half, 9, 1, pool, p, z, z, occ=occ, do_adam=False, want_samples=True)
+    S = r["samples"]                                   # per sample: t, delta, x, y, z, live, sigma, dL/dsigma
+    t, delta, x = S[..., 0], S[..., 1], S[..., 2:5]
+    hit = np.array([O.ray_aabb(pool["o"][i], pool["d"][i], half)[0] for i in range(n)])
+    live = hit[:, None] & (np.ones_like(t, bool) if occ is None else _live_by_grid(x, occ, half))
+    bg = r["bg"]
+    comps = np.zeros(4)
+    n_culled = 0
+    for i in range(n):
+        dl = np.where(live[i], delta[i], 0.0)
+        cum = np.concatenate([[0.0], np.cumsum(dl)])
+        T = np.exp(-sigma0 * cum)
+        A = 1.0 - T[-1]
+        C_hat = 0.5 * A + bg[i] * (1.0 - A)
+        D_hat = float(np.sum((T[:-1] - T[1:]) * t[i]))
+        cls = pool["cls"][i]
+        n_culled += int(hit[i]) * int(np.count_nonzero(~live[i]))
+        if cls == 2:
+            continue
+        tgt = pool["rgb"][i].astype(np.float64) if cls == 0 else bg[i]
+        comps[0 if cls == 0 else 1] += np.sum((C_hat - tgt) ** 2)
+        if np.isfinite(pool["depth"][i]):
+            comps[2] += abs(D_hat - float(pool["depth"][i]))
+        if cls == 1:
+            comps[3] += sigma0 * np.count_nonzero(live[i])
+    L = (comps[0] + comps[1] + lam1 * comps[2] + lam2 * comps[3]) / n
+    assert comps[3] > 0 and np.all(np.isfinite(comps))
+    if culled:
+        assert n_culled > 100                       # the grid really culls part of the rays
+    assert abs(r["loss"][0] - L) < 1e-12, (r["loss"][0], L)
+    assert np.allclose(r["loss"][1:], comps / n, rtol=0, atol=1e-12), (r["loss"][1:], comps / n)
+    # the live flags and densities of the step agree with the bitgrid and the constant field
+    assert np.array_equal(S[..., 5].astype(bool), live)
+    assert np.allclose(S[..., 6][live], sigma0, rtol=1e-14) and np.all(S[..., 6][~live] == 0)
+
+
 def _fd_check(cfg, params, pool, seed, step, occ, idx, h=1e-4, tol=1e-6):
     """Central differences of the step loss.  A parameter whose h=1e-4 difference disagrees is re-checked at
     h=1e-6: a ReLU or |.| kink within +-1e-4 of the point is the only legitimate cause of disagreement."""
