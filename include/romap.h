@@ -386,13 +386,19 @@ ROMAP_API romap_status romap_fn_backward(romap_ctx* ctx, const float* params, co
  * device memory and offers no allocator; a real-time loop that must not call
  * cudaMalloc/cudaFree because they can synchronise the device).  The paper
  * has no counterpart; this is a deployment convenience.
- *  - Scratch lives in one static 32 MiB device array inside the library,
- *    held by every GPU that loads it until process exit.  Calls whose
- *    scratch would not fit (about n * (105 + 60 * n_samples) bytes) return
+ *  - Scratch lives in one static 32 MiB device array inside the library.
+ *    A device reserves it when the library's device code is first loaded
+ *    there (with lazy module loading, possibly at this call) and holds it
+ *    until process exit.  n must be in 1..2^24, and calls whose scratch
+ *    would not fit (about n * (105 + 60 * n_samples) bytes) return
  *    ROMAP_ERR_CAPACITY with the largest n that fits.
  *  - The first call on each device resolves the array's device address
  *    (cudaGetSymbolAddress) with that device current; make it before any
- *    stream capture.
+ *    stream capture.  cuda_stream must belong to the current device, else
+ *    ROMAP_ERR_INVALID_ARG.
+ *  - The object record and batch arrays are written into the array by a
+ *    kernel that receives them by value: nothing is read from host memory
+ *    after the call returns.
  *  - All calls on a device share the array: calls that overlap on the GPU
  *    race and must be serialised by the caller.
  * cfg as for romap_init (validated, nothing allocated); cuda_stream is a

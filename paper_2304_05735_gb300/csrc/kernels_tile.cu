@@ -505,12 +505,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int LFP, int MODE>
 static void launch_tile_t(const GridParams& g, const BatchDesc& b, const BatchDyn* dyn, const int32_t* totals,
                           RayBuf r, SampleBuf s, int n_ctas, cudaStream_t stream) {
-  static bool attr_set = false;
+  static std::atomic<uint64_t> attr_done{0};
   int bytes = (int)sizeof(TileSmem<LFP>);
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_mlp<LFP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    attr_set = true;
-  }
+  set_smem_attr(k_tile_mlp<LFP, MODE>, bytes, attr_done);
   k_tile_mlp<LFP, MODE><<<n_ctas, kThreads, bytes, stream>>>(g, b, dyn, totals, r, s);
 }
 

@@ -450,11 +450,8 @@ void launch_ws_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
                  int n_ctas, int interleave, cudaStream_t stream) {
   int bytes = (int)sizeof(WsSmem<LFP>);
   if (bytes < 116 * 1024) bytes = 116 * 1024;  // one CTA per SM: the 512-column TMEM allocation never waits
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_ws<LFP, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  set_smem_attr(k_tile_ws<LFP, F16>, bytes, attr_done);
   // the plan's tile count is read on the device; max_tiles only bounds the grid
   int grid = n_ctas < max_tiles ? n_ctas : max_tiles;
   if (grid < 1) return;

@@ -1970,13 +1970,17 @@ romap_status romap_render(romap_ctx* ctx, int32_t id, const float* origin, const
 // stall the frame).  romap_fn_forward needs a caller workspace, which such a
 // caller cannot provide.  This variant keeps its scratch (ray records,
 // compacted samples, scan totals, the object record) in one file-scope device
-// array of kNoAllocScratchBytes, loaded with the library: every GPU that
-// loads libromap holds those bytes until the process exits.
+// array of kNoAllocScratchBytes: a device reserves those bytes when the
+// library's device code is first loaded there (under lazy module loading that
+// may be the first call) and holds them until the process exits.
 //
 // Set-up: the first call on each device, with that device current, looks up
 // the array's device address with cudaGetSymbolAddress (host code cannot use
 // the array's name as a device address) and caches it; make that first call
-// before any stream capture.  All calls on a device share the one array and
+// before any stream capture.  The caller's stream must belong to the current
+// device (the cached address is that device's).  The object record and the
+// batch arrays reach the array through a set-up kernel's by-value parameters,
+// never through a copy from host memory.  All calls on a device share the one array and
 // it keeps the last call's contents: every scratch word the kernels read is
 // written earlier in the same call, so nothing needs clearing, but calls that
 // overlap on the GPU (two streams, two threads) race on the array and must be
@@ -1988,6 +1992,21 @@ constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Writes the one-object record and the one-entry batch arrays (slot 0; rays 0..n; blocks 0..nb; no tiles; every
+// block in entry 0) into the static scratch.  Everything arrives by value in the launch parameters, so nothing is
+// copied from host memory that may be gone when the kernel runs.
+__global__ void k_noalloc_setup(ObjectDev d, ObjectDev* od, int32_t* batch, int32_t n, int32_t nb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *od = d;
+    batch[0] = 0;                     // slot[1]
+    batch[1] = 0; batch[2] = n;       // ray_base[2]
+    batch[3] = 0; batch[4] = nb;      // block_base[2]
+    batch[5] = 0; batch[6] = 0;       // tile_base[2]
+  }
+  if (i < nb) batch[7 + i] = 0;       // block_obj[nb]
+}
 
 romap_status noalloc_scratch(int dev, char** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ROMAP_ERR_UNSUPPORTED, "device %d out of range", dev);
@@ -2011,7 +2030,7 @@ extern "C" romap_status romap_fn_forward_noalloc(const romap_config* cfg, void* 
   GridParams g;
   ROMAP_TRY(make_grid(cfg, &g));
   if (!params || !half_size || !origin || !dir || !bg || !out_ray) return fail(ROMAP_ERR_INVALID_ARG, "NULL argument");
-  if (n < 1) return fail(ROMAP_ERR_INVALID_ARG, "n must be >= 1");
+  if (n < 1 || n > (int64_t)1 << 24) return fail(ROMAP_ERR_INVALID_ARG, "n must be in 1..2^24");
   if (flags & ~(ROMAP_JITTER)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
   for (int a = 0; a < 3; ++a)
     if (!(half_size[a] > 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "half_size must be positive");
@@ -2030,16 +2049,19 @@ extern "C" romap_status romap_fn_forward_noalloc(const romap_config* cfg, void* 
   }
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  int stream_dev = dev;
+  CUDA_TRY(cudaStreamGetDevice(stream, &stream_dev));
+  if (stream_dev != dev)
+    return fail(ROMAP_ERR_INVALID_ARG, "the stream belongs to device %d but device %d is current", stream_dev, dev);
   char* base = nullptr;
   ROMAP_TRY(noalloc_scratch(dev, &base));
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  cudaStream_t stream = (cudaStream_t)cuda_stream;
   ObjectDev* od = (ObjectDev*)base;
   FnView v = fn_view(base + rec, L);
-  HostBatch hb;
+  HostBatch hb;  // host description only (counts and offsets); its arrays are written on the device below
   build_batch(std::vector<int32_t>{0}, std::vector<int32_t>{(int32_t)n}, &hb);
-  CUDA_TRY(cudaMemcpyAsync(v.batch, hb.arr.data(), sizeof(int32_t) * hb.arr.size(), cudaMemcpyHostToDevice, stream));
   ObjectDev d{};
   d.params = const_cast<float*>(params);
   d.occ = occupancy;
@@ -2051,7 +2073,8 @@ extern "C" romap_status romap_fn_forward_noalloc(const romap_config* cfg, void* 
   d.key1 = (uint32_t)(seed >> 32);
   d.n_rays = (int32_t)n;
   d.step = step;  // the forward reads the step as the RNG counter only
-  CUDA_TRY(cudaMemcpyAsync(od, &d, sizeof(d), cudaMemcpyHostToDevice, stream));
+  k_noalloc_setup<<<(unsigned)((hb.n_blocks + 255) / 256), 256, 0, stream>>>(d, od, v.batch, (int32_t)n,
+                                                                               hb.n_blocks);
   BatchDesc b = desc_from(hb, v.batch, od);
   b.explicit_rays = 1;
   b.explicit_step = step;

@@ -13,6 +13,7 @@
 //    keeps no sample records: it packs whole rays into tiles by their number
 //    of live samples (the tile plan below) and forms the samples in-kernel.
 #pragma once
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -268,6 +269,19 @@ void launch_to_half(const float* params, uint16_t* table_h, int64_t n_hash, cuda
 // memory warps gather the next tile and scatter the previous one.
 void launch_tile_ws(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int total_tiles, int n_ctas, int interleave, cudaStream_t stream);
+// Dynamic shared-memory opt-in of a kernel above 48 KB.  The attribute belongs to a device context, so it is set
+// once per device (one bit of `done` per device index below 64; devices beyond that set it on every launch).  A
+// failed call stays in the runtime's last error, which the caller's launch check reports.
+template <class K>
+inline void set_smem_attr(K* kernel, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && bit)
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
+
 // status word bits written by the kernels
 constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2;
 void launch_selftest_wait(int32_t* status, int limit, cudaStream_t stream);

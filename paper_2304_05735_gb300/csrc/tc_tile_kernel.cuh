@@ -744,11 +744,8 @@ void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf 
   // CTA never waits on another
   int bytes = (int)sizeof(TcSmem<LFP, FP8, SN>);
   if (bytes < 116 * 1024) bytes = 116 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_tc<LFP, FP8, SN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  set_smem_attr(k_tile_tc<LFP, FP8, SN, F16>, bytes, attr_done);
   // the plan's pair count is read on the device; max_tiles only bounds the grid
   const int max_pairs = (max_tiles + kTilesPerCta - 1) / kTilesPerCta;
   int grid = n_ctas < max_pairs ? n_ctas : max_pairs;

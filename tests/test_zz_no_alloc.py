@@ -44,17 +44,24 @@ def test_noalloc_forward_matches_workspace_forward_twice():
         params = torch.tensor(p.astype(np.float32), device="cuda")
         half = (0.5, 0.45, 0.4)
         stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-        for call, (n, seed, step) in enumerate([(700, 1, 3), (300, 2, 4)]):
+        # two calls on the caller's stream, then one on the legacy default stream (cuda_stream = NULL); the last
+        # call is smaller than the first, so a stale scratch word from the first call would show
+        for call, (n, seed, step, strm) in enumerate([(700, 1, 3, stream), (300, 2, 4, stream), (520, 3, 5, None)]):
             o, d, bg = (torch.tensor(a, device="cuda") for a in _rays(n, seed))
             ref, _, _ = ctx.fn_forward(params, half, 17, step, o, d, bg, jitter=True)
+            torch.cuda.synchronize()
             out = torch.full((n, 6), float("nan"), device="cuda")
-            R.check(R.romap_fn_forward_noalloc(C.byref(rc), stream, params.data_ptr(), (C.c_float * 3)(*half), 17,
+            torch.cuda.synchronize()
+            R.check(R.romap_fn_forward_noalloc(C.byref(rc), strm, params.data_ptr(), (C.c_float * 3)(*half), 17,
                                                step, None, o.data_ptr(), d.data_ptr(), bg.data_ptr(), n,
                                                R.ROMAP_JITTER, out.data_ptr()), "romap_fn_forward_noalloc")
             torch.cuda.synchronize()
             got, want = out.cpu().numpy(), ref.cpu().numpy()
             assert np.all(np.isfinite(got)), call
+            # the same kernels on the same inputs: the rays agree bit for bit (the forward has no atomics), which
+            # also catches a carving or offset slip in the static scratch that a tolerance could hide
             assert np.allclose(got, want, rtol=FWD_RTOL, atol=FWD_ATOL), (call, np.abs(got - want).max())
+            assert np.array_equal(got, want), (call, np.abs(got - want).max())
             assert (got[:, 4] > 0).sum() > n // 2
     finally:
         ctx.close()
@@ -69,3 +76,6 @@ def test_noalloc_forward_rejects_sizes_beyond_its_scratch():
                                     x.data_ptr(), x.data_ptr(), x.data_ptr(), 1 << 20, 0, x.data_ptr())
     assert st == R.ROMAP_ERR_CAPACITY
     assert "static scratch" in R.last_error() and "at most" in R.last_error()
+    st = R.romap_fn_forward_noalloc(C.byref(rc), None, x.data_ptr(), (C.c_float * 3)(0.5, 0.5, 0.5), 0, 0, None,
+                                    x.data_ptr(), x.data_ptr(), x.data_ptr(), (1 << 24) + 1, 0, x.data_ptr())
+    assert st == R.ROMAP_ERR_INVALID_ARG and "2^24" in R.last_error()
