@@ -4,12 +4,16 @@
 One step = one forward + loss + backward + Adam pass of every object of the
 workload (ray draw, box sampling, hash encoding, MLP, compositing, Eq. 7-11
 losses, adjoints, hash-gradient scatter, Adam), run through the C ABI of
-libromap.  The default workload is the multi-object configuration: 8
-objects, 4096 rays per object per step, 64 samples per ray, hash grid L=16,
-F=2, T=2^16, resolutions 16..512, each object seen in 30 frames of 320x240.
+libromap.  The default workload is the uneven batched configuration: 32
+objects whose rays per step are log-uniform in 256..16384, 128 candidate
+samples per ray culled by a 64^3 occupancy bitgrid, hash grid L=16, F=2,
+T=2^19, resolutions 16..512, each object seen in 3 frames of 640x480; the
+batched mixed-precision step is timed against the plain per-object FP32
+path, and the two are compared at the same final loss over several seeds
+(the FP32 side in its bit-reproducible deterministic mode).
 
-Prints one JSON line (rank 0).  Under torchrun every rank trains its own 8
-objects on its own GPU (weak scaling, no collective on the data path).
+Prints one JSON line (rank 0).  Under torchrun the 32 objects are placed on
+the ranks by LPT bin-packing (no collective on the data path).
 --impl reference times the CPU oracle (plain FP64 C) on a bounded sample of
 the same workload.
 """
@@ -93,8 +97,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "mixed", "fp8", "fp16"), default="mixed")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="multi8")
-    ap.add_argument("--loss-steps", type=int, default=200)
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="uneven32")
+    ap.add_argument("--loss-steps", type=int, default=500)
+    ap.add_argument("--loss-seeds", type=int, default=3,
+                    help="training runs per precision for the loss comparison (object seeds shifted per run)")
     ap.add_argument("--objects", type=int, default=None,
                     help="train only the workload's first N objects (a smaller case of the same kind, e.g. for ncu)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -245,9 +251,10 @@ def build_items(w, rank, world):
     return items
 
 
-def make_ctx(R, torch, precision, single_net=False, hidden_layers=1):
+def make_ctx(R, torch, precision, single_net=False, hidden_layers=1, deterministic=False, per_object=False):
     """A context for the current workload; single_net selects the position-only single-network model of Sec. V
-    (hidden_layers hidden layers of 64, Table 4) instead of the density + colour nets."""
+    (hidden_layers hidden layers of 64, Table 4) instead of the density + colour nets; deterministic the
+    bit-reproducible FP32 mode; per_object one launch sequence per object (the plain per-object path)."""
     w = WORKLOAD
     rc = R.make_config(n_levels=w["levels"], log2_table_size=w["log2_table"], base_resolution=w["base_resolution"],
                        growth=0.0, max_resolution=w["max_resolution"], n_samples=w["samples_per_ray"],
@@ -256,20 +263,23 @@ def make_ctx(R, torch, precision, single_net=False, hidden_layers=1):
                        precision={"mixed": R.ROMAP_PREC_MIXED_BF16, "fp8": R.ROMAP_PREC_MIXED_FP8,
                                   "fp16": R.ROMAP_PREC_MIXED_FP16}.get(
                            precision, R.ROMAP_PREC_FP32),
-                       max_objects=2 * w["objects"])
+                       max_objects=2 * w["objects"], deterministic=deterministic, per_object=per_object)
     h = C.c_void_p()
     R.check(R.romap_init(C.byref(rc), C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(h)), "romap_init")
     return rc, h
 
 
-def add_objects(R, h, items):
+def add_objects(R, h, items, seed_offset=0):
+    """Creates the workload's objects; seed_offset shifts every object's random stream (initial parameters, ray
+    draws, jitter, background colours) for repeated training runs on the same scenes."""
     import numpy as np
 
     ids = []
     for it in items:
         sc = it.scene
         oid = C.c_int32()
-        d = R.object_desc(t=tuple(sc.t), yaw=sc.yaw, half_size=tuple(sc.half), seed=sc.seed, rays_per_step=it.rays)
+        d = R.object_desc(t=tuple(sc.t), yaw=sc.yaw, half_size=tuple(sc.half), seed=sc.seed + seed_offset,
+                          rays_per_step=it.rays)
         R.check(R.romap_create_object(h, C.byref(d), C.byref(oid)), "romap_create_object")
         if it.occ is not None:
             bits = np.ascontiguousarray(it.occ)
@@ -361,22 +371,32 @@ def run_ours(args):
     n = len(items)
     main_prec = args.precision
 
-    # ---- loss comparison: same seeds, batched mixed vs batched FP32, per-step losses (untimed) -------------------
-    curves, psnr = {}, {}
+    # ---- loss comparison (untimed): batched mixed vs plain FP32 at the same final loss ----------------------------
+    # args.loss_seeds runs per precision, run k with every object's seed shifted by 1000 k (initial parameters, ray
+    # draws, jitter, background colours); the FP32 side runs in the deterministic mode (fixed-point accumulation), so
+    # a run is reproducible bit for bit and the spread between runs is the spread between seeds alone.  The final
+    # loss of a run is its mean per-step loss over the last K/4 steps, averaged over the objects.
+    runs = {"fp32": [], "mixed": []}
+    psnr = {}
+    fp32_repeat_identical = None
     if not args.no_plain:
         evalset = psnr_rays(items)
-        # a second FP32 run with the same seeds measures the run-to-run spread of FP32 training itself (atomic
-        # accumulation order), the floor under any mixed-vs-FP32 difference
-        for prec in ("fp32", "mixed", "fp32_repeat"):
-            rc, h = make_ctx(R, torch, "fp32" if prec == "fp32_repeat" else (main_prec if prec == "mixed" else prec))
-            ids = add_objects(R, h, items)
-            idarr = (C.c_int32 * n)(*ids)
-            ls = np.zeros((args.loss_steps, n), np.float32)
-            for k in range(args.loss_steps):
-                R.check(R.romap_train_step(h, idarr, n, 1, ls[k].ctypes.data))
-            curves[prec] = ls.mean(axis=1)
-            psnr[prec] = trained_psnr(R, h, ids, evalset)
-            R.check(R.romap_destroy(h))
+        for k in range(args.loss_seeds):
+            for prec in ("fp32", "mixed") + (("fp32_repeat",) if k == 0 else ()):
+                det = prec != "mixed"
+                rc, h = make_ctx(R, torch, main_prec if prec == "mixed" else "fp32", deterministic=det)
+                ids = add_objects(R, h, items, seed_offset=1000 * k)
+                idarr = (C.c_int32 * n)(*ids)
+                ls = np.zeros((args.loss_steps, n), np.float32)
+                for j in range(args.loss_steps):
+                    R.check(R.romap_train_step(h, idarr, n, 1, ls[j].ctypes.data))
+                if prec == "fp32_repeat":
+                    fp32_repeat_identical = bool(np.array_equal(ls.mean(axis=1), runs["fp32"][0]))
+                else:
+                    runs[prec].append(ls.mean(axis=1))
+                    if k == 0:
+                        psnr[prec] = trained_psnr(R, h, ids, evalset)
+                R.check(R.romap_destroy(h))
 
     # ---- the timed batched step -------------------------------------------------------------------------------------
     rc, h = make_ctx(R, torch, main_prec)
@@ -447,8 +467,12 @@ def run_ours(args):
     adam_bytes = (32.0 + (2.0 if mixed else 0.0)) * n_params * n
     hbm = peaks.get("hbm_gbs") or 6800.0
     if phase_ms[4] > 0:
+        # dense-equivalent rate: Adam skips 256-parameter chunks that never received a gradient (their update is
+        # exactly zero) and reads only their gradient, so this counts bytes a dense Adam would move
         phases["adam"]["achieved_gbs"] = adam_bytes / (phase_ms[4] / args.steps / 1e3) / 1e9
         phases["adam"]["frac_of_hbm"] = phases["adam"]["achieved_gbs"] / hbm
+        phases["adam"]["note"] = ("dense-equivalent: 34 B per parameter of every object; never-touched chunks are "
+                                  "skipped after a 4 B gradient read")
     dominant = max(range(R.ROMAP_N_PHASES), key=lambda i: phase_ms[i])
     if dominant == 3 and mixed:
         # the fused kernel's algorithmic traffic: per live sample the FP16 gather of 8 corners x L levels x F
@@ -464,13 +488,27 @@ def run_ours(args):
                                                                                                         "BF16"))
         if autotune and autotune["chosen"]:
             kname += f"; autotuned: {autotune['chosen']}"
-        roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm,
+        # the roof that binds: the SMs' scattered-request rate into L2, measured live (romap_measure_request_rates:
+        # one 4-byte load and one 8-byte reduction per step, every lane its own random address in L2-resident
+        # buffers); per live sample the kernel needs 8 L gathers and 8 L scatter-adds, i.e. 8 L such pairs
+        rates = (C.c_double * 3)()
+        R.check(R.romap_measure_request_rates(C.c_void_p(torch.cuda.current_stream().cuda_stream), rates),
+                "romap_measure_request_rates")
+        pair_bytes = 2 * 2 + 2 * 4  # FP16 feature pair + FP32 gradient pair
+        l2_peak = rates[2] * pair_bytes / 1e9
+        roofline = {"bound": "l2", "kernel": kname, "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+                    "frac": achieved / l2_peak,
                     "traffic": profiled_traffic(TC_TRAFFIC_KEY, main_prec) if not ws else None,
-                    "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback",
+                    "peak_source": "measured live by romap_measure_request_rates: "
+                                   f"{rates[2]:.4g} scattered load + red.global.add.v2.f32 pairs/s x {pair_bytes} B "
+                                   f"(loads alone {rates[0]:.4g}/s, reductions alone {rates[1]:.4g}/s)",
                     "work_per_unit": f"{bytes_per_sample} B per live sample (FP16 gather {8 * lvl * 4} B + FP32 "
-                                     f"scatter-add {8 * lvl * 8} B)",
+                                     f"scatter-add {8 * lvl * 8} B) = {8 * lvl} load/reduction pairs",
                     "units_per_launch": live_per_step, "ms_per_launch": bwd_ms,
+                    "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                            "note": "the same logical bytes against the HBM copy bandwidth; the tables stay in L2, "
+                                    "see traffic for the DRAM bytes actually moved",
+                            "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if peaks else "fallback"},
                     "tensor": {"achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
                                "work_per_unit": f"{2 * (MAC_FWD + MAC_DX + MAC_DW)} FLOP per live sample (BF16 MMA)",
                                "peak_source": "measured bf16 dense, sustained (MEASURED_PEAKS.json)"}}
@@ -586,53 +624,68 @@ def run_ours(args):
                 "paper_ms_per_object": 2.84}
     R.check(R.romap_destroy(h))
 
-    # ---- the comparison paths: batched FP32 and the plain per-object FP32 path ---------------------------------------
+    # ---- the comparison paths: batched FP32 and the plain per-object FP32 path -------------------------------------
+    # the plain path trains each object with its own launch sequence (per_object: one CUDA graph per object, all
+    # kept in the context's graph cache and replayed), and again with eager launches (no graphs)
     others = {}
     if not args.no_plain:
         k_cmp = max(5, min(args.steps, 100))
-        rc2, h2 = make_ctx(R, torch, "fp32")
-        ids2 = add_objects(R, h2, items)
-        arr2 = (C.c_int32 * n)(*ids2)
-        R.check(R.romap_train_step(h2, arr2, n, 3, None))
-        for label, per_object in (("batched_fp32", False), ("plain_fp32_per_object", True)):
+        for label, per_object, graphs, det in (("batched_fp32", False, True, False),
+                                               ("plain_fp32_per_object", True, True, False),
+                                               ("plain_fp32_per_object_eager", True, False, False),
+                                               ("plain_fp32_per_object_deterministic", True, True, True)):
+            rc2, h2 = make_ctx(R, torch, "fp32", per_object=per_object, deterministic=det)
+            R.check(R.romap_set_graphs(h2, 1 if graphs else 0))
+            ids2 = add_objects(R, h2, items)
+            arr2 = (C.c_int32 * n)(*ids2)
+            R.check(R.romap_train_step(h2, arr2, n, 3, None))
             R.check(R.romap_reset_stats(h2))
 
             def run_cmp():
-                for _ in range(k_cmp):
-                    if per_object:
-                        for i in ids2:
-                            R.check(R.romap_train_step(h2, (C.c_int32 * 1)(i), 1, 1, None))
-                    else:
-                        R.check(R.romap_train_step(h2, arr2, n, 1, None))
+                R.check(R.romap_train_step(h2, arr2, n, k_cmp, None))
 
             ms_c = timed(torch, run_cmp, world, dist)
             stc = R.romap_stats()
             R.check(R.romap_get_stats(h2, C.byref(stc)))
             live_c = allsum(torch, dist, world, stc.live_samples)
-            others[label] = {"value": live_c / (ms_c / 1e3), "ms_per_step": ms_c / k_cmp, "steps": k_cmp}
-        R.check(R.romap_destroy(h2))
+            others[label] = {"value": live_c / (ms_c / 1e3), "ms_per_step": ms_c / k_cmp, "steps": k_cmp,
+                             "graph_captures": int(stc.graph_captures), "graph_replays": int(stc.graph_replays),
+                             "path": ("one launch sequence per object" if per_object else "one batched launch sequence")
+                                     + (", CUDA graphs replayed" if graphs else ", eager launches")
+                                     + (", deterministic fixed-point accumulation" if det else "")}
+            R.check(R.romap_destroy(h2))
 
     loss_cmp = None
-    if curves:
-        # final loss = mean per-step loss over the last quarter of the K steps.  The two FP32 runs differ only in
-        # the order of their atomic additions; their mean is the FP32 final loss and their difference the FP32
-        # run-to-run spread.  The runs are "matched" when the mixed path's final loss is at most 1e-3 above the
-        # FP32 one (a lower mixed loss is at least the same quality).
+    if runs["fp32"]:
+        # "at oracle-matched loss", two-sided: the mean final loss of the mixed runs within 1e-3 (relative) of the mean
+        # final loss of the deterministic FP32 runs over the same seeds; the paired per-seed differences and their
+        # standard error say whether a gap is larger than the seed-to-seed spread
         tail = max(1, args.loss_steps // 4)
-        lf1, lm = float(curves["fp32"][-tail:].mean()), float(curves["mixed"][-tail:].mean())
-        lr_ = float(curves["fp32_repeat"][-tail:].mean())
-        lf = 0.5 * (lf1 + lr_)
-        target = lf
-        reach = np.nonzero(curves["mixed"] <= target)[0]
-        loss_cmp = {"steps": args.loss_steps, "mean_loss_last_steps": tail, "fp32": lf, "fp32_runs": [lf1, lr_],
-                    "mixed": lm, "rel_diff": (lm - lf) / lf, "matched": bool(lm <= lf * (1 + 1e-3)),
-                    "fp32_run_to_run_rel_diff": abs(lr_ - lf1) / lf, "first_step_rel_diff":
-                    float(abs(curves["mixed"][0] - curves["fp32"][0]) / curves["fp32"][0]),
-                    "mixed_steps_to_fp32_final_loss": int(reach[0] + 1) if reach.size else None,
-                    "curve": {"steps": [k + 1 for k in curve_steps(args.loss_steps)],
-                              **{name: [float(curves[name][k]) for k in curve_steps(args.loss_steps)]
-                                 for name in ("fp32", "mixed", "fp32_repeat")}},
-                    "psnr_db_after_k_steps": psnr}
+        fin = {p: np.array([float(c[-tail:].mean()) for c in runs[p]]) for p in runs}
+        mf, mm = float(fin["fp32"].mean()), float(fin["mixed"].mean())
+        paired = (fin["mixed"] - fin["fp32"]) / fin["fp32"]
+        se = float(paired.std(ddof=1) / np.sqrt(paired.size)) if paired.size > 1 else None
+        cf, cm = np.mean(runs["fp32"], axis=0), np.mean(runs["mixed"], axis=0)
+        reach = np.nonzero(cm <= mf)[0]
+        loss_cmp = {
+            "steps": args.loss_steps, "seeds": args.loss_seeds, "mean_loss_last_steps": tail,
+            "criterion": "two-sided: |mean mixed - mean FP32| <= 1e-3 x mean FP32, final loss = mean per-step loss of "
+                         "the last K/4 steps; FP32 in the deterministic (bit-reproducible) mode; seeds shift every "
+                         "object's random stream",
+            "fp32": {"mean": mf, "std": float(fin["fp32"].std(ddof=1)) if paired.size > 1 else 0.0,
+                     "runs": fin["fp32"].tolist()},
+            "mixed": {"mean": mm, "std": float(fin["mixed"].std(ddof=1)) if paired.size > 1 else 0.0,
+                      "runs": fin["mixed"].tolist()},
+            "rel_diff": (mm - mf) / mf, "matched": bool(abs(mm - mf) <= 1e-3 * mf),
+            "paired_rel_diff": paired.tolist(), "paired_rel_diff_se": se,
+            "within_two_se": bool(se is not None and abs(float(paired.mean())) <= 2.0 * se),
+            "fp32_repeat_bit_identical": fp32_repeat_identical,
+            "first_step_rel_diff": float(abs(cm[0] - cf[0]) / cf[0]),
+            "mixed_steps_to_fp32_final_loss": int(reach[0] + 1) if reach.size else None,
+            "curve": {"steps": [k + 1 for k in curve_steps(args.loss_steps)],
+                      "fp32": [float(cf[k]) for k in curve_steps(args.loss_steps)],
+                      "mixed": [float(cm[k]) for k in curve_steps(args.loss_steps)]},
+            "psnr_db_after_k_steps": psnr}
         if mixed and others.get("plain_fp32_per_object") and reach.size:
             t_mixed = (reach[0] + 1) * ms / args.steps
             t_plain = args.loss_steps * others["plain_fp32_per_object"]["ms_per_step"]

@@ -64,6 +64,11 @@ typedef int32_t romap_status;
 #define ROMAP_ASYNC_HOST 0x10u  /* romap_add_rays(_multi): page-locked host arrays are copied asynchronously on the
                                    context's stream; the caller keeps them unchanged until the stream has passed
                                    the call (without the flag the call waits for the copy) */
+#define ROMAP_STORE_ACT 0x20u   /* functional forward/backward: the forward stores every sample's MLP activations
+                                   (encoding, hidden layers, density-net outputs: about 4 (L F + 208) bytes per
+                                   sample slot) in the workspace and the backward reads them back; without the flag
+                                   (recompute) the backward re-gathers the encoding and recomputes the forward.  Both
+                                   calls of a pair pass the same flags. */
 
 /* ray classes from the instance mask (Sec. V-B) */
 #define ROMAP_CLS_OBJECT 0     /* R_o: photometric loss, Eq. 7 */
@@ -123,6 +128,19 @@ typedef struct romap_config {
   int32_t hidden_layers;   /* hidden layers of width 64 of the single-network model (1..3, Table 4;
                               0 reads as 1); must be 0 or 1 when single_net == 0.  Layers 2 and 3 are
                               64x64 with ReLU, between the first hidden layer and the output layer. */
+  int32_t deterministic;   /* 1: bit-reproducible training (ROMAP_PREC_FP32 only, else ROMAP_ERR_UNSUPPORTED):
+                              every gradient contribution of the backward (hash scatter and MLP weight
+                              gradients) and every per-ray loss term is rounded once to a 64-bit fixed-point
+                              integer (2^-46 for gradients, 2^-32 for loss sums) and added with an integer
+                              atomic, so sums do not depend on the order the GPU adds them in: two runs with the
+                              same inputs give the same bits, and a batch of objects gives each object the bits
+                              of its own separate step.  A contribution above 1024 in magnitude (2^20 for a
+                              ray's loss) is not added and the step reports ROMAP_ERR_CAPACITY; per-entry sums
+                              must stay within +-2^17.  Applies to training steps (romap_fn_backward keeps
+                              floating-point atomics). */
+  int32_t per_object;      /* 1: romap_train_step(_async) runs one launch sequence (one CUDA graph) per listed
+                              object and step instead of one batched sequence for all of them (the plain
+                              per-object path); 0: batched */
   int32_t reserved;        /* 0 */
   /* Optional device allocator (both or neither).  alloc returns NULL on
    * failure, which the library reports as ROMAP_ERR_OOM; a pointer that is
@@ -184,6 +202,8 @@ typedef struct romap_stats {
   int64_t rays;           /* rays drawn */
   int64_t live_samples;   /* samples that went through forward, backward and Adam */
   int64_t kernel_launches;/* kernels enqueued by the library */
+  int64_t graph_captures; /* training-step CUDA graphs captured (one per new batch composition) */
+  int64_t graph_replays;  /* training steps run by replaying a cached graph */
 } romap_stats;
 
 /* ---- lifetime ---------------------------------------------------------- */
@@ -240,7 +260,12 @@ ROMAP_API romap_status romap_add_rays_multi(romap_ctx* ctx, const int32_t* ids, 
 ROMAP_API romap_status romap_pool_size(romap_ctx* ctx, int32_t id, int64_t* out_n);
 
 /* ---- training (Sec. V-A, V-B; Eq. 6-11; Adam) -------------------------- */
-/* Runs n_steps training steps of every listed object.  Each step of an
+/* Runs n_steps training steps of every listed object (one batched launch
+ * sequence per step; with per_object, one per object and step).  The first
+ * step of a batch composition (the listed objects and their rays per step)
+ * runs eagerly and is captured as a CUDA graph; later steps of that
+ * composition replay it.  The context keeps the graphs of up to 128
+ * compositions and evicts the least recently used one beyond that.  Each step of an
  * object draws B = min(rays_per_step, pool size) rays (uniformly with
  * replacement, or the whole pool in order when B equals the pool size),
  * samples N stratified points in the box per ray, encodes and evaluates
@@ -363,9 +388,10 @@ ROMAP_API romap_status romap_set_state(romap_ctx* ctx, int32_t id, const romap_s
  * The RNG of ray r uses key seed and counter (step, r, purpose, .).
  * Outputs per ray: out_ray [6n] = (C_hat rgb, D_hat, opacity A = 1 -
  * T_{N+1}, sum_i sigma_i over live samples).  workspace holds the samples
- * between forward and backward; its size comes from
- * romap_fn_workspace_size.  Flags: ROMAP_JITTER. */
-ROMAP_API romap_status romap_fn_workspace_size(romap_ctx* ctx, int64_t n, size_t* bytes);
+ * (and with ROMAP_STORE_ACT the activations) between forward and backward;
+ * its size comes from romap_fn_workspace_size with the same n and flags.
+ * Flags: ROMAP_JITTER, ROMAP_STORE_ACT.  n in 1..2^24. */
+ROMAP_API romap_status romap_fn_workspace_size(romap_ctx* ctx, int64_t n, uint32_t flags, size_t* bytes);
 ROMAP_API romap_status romap_fn_forward(romap_ctx* ctx, const float* params, const float half_size[3], uint64_t seed,
                               uint32_t step, const uint64_t* occupancy, const float* origin, const float* dir,
                               const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
@@ -374,7 +400,9 @@ ROMAP_API romap_status romap_fn_forward(romap_ctx* ctx, const float* params, con
  * dL/dparams into grad_params (n_params floats, device, 16-byte aligned,
  * else ROMAP_ERR_INVALID_ARG).  out_dsigma
  * (nullable, [n*N]) receives dL/dsigma per sample slot (0 for missed or
- * culled slots).  flags: ROMAP_JITTER as in the forward. */
+ * culled slots).  flags: as in the forward (ROMAP_JITTER, ROMAP_STORE_ACT).
+ * The gradient uses floating-point atomics even in the deterministic
+ * mode. */
 ROMAP_API romap_status romap_fn_backward(romap_ctx* ctx, const float* params, const float half_size[3], uint64_t seed,
                                uint32_t step, const uint64_t* occupancy, const float* origin, const float* dir,
                                const float* bg, int64_t n, uint32_t flags, void* workspace, size_t ws_bytes,
@@ -445,7 +473,33 @@ ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);
 ROMAP_API romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, int32_t n, char* names,
                                              size_t names_len);
 ROMAP_API romap_status romap_set_profiling(romap_ctx* ctx, int32_t on);
+/* Adam (Kingma & Ba) skips parameter chunks (256 parameters) whose
+ * gradient has been zero at every step so far: their moments are then 0 and
+ * their update is exactly 0, so the skip changes no bit of the parameters,
+ * moments or FP16 table copy; it saves the traffic of untouched table
+ * regions (empty space of a culled object).  on = 0 updates every chunk
+ * (dense Adam, for comparison); on = 1 (the default) skips.  A state load
+ * (romap_set_state) marks the chunks whose loaded moments are non-zero.
+ * Drops the captured step graphs. */
+ROMAP_API romap_status romap_set_adam_skip(romap_ctx* ctx, int32_t on);
+/* on = 0: training steps launch their kernels eagerly, every step (no CUDA
+ * graph capture or replay; drops the cached graphs); on = 1 (the default):
+ * the first step of a composition is captured and later ones replayed. */
+ROMAP_API romap_status romap_set_graphs(romap_ctx* ctx, int32_t on);
 ROMAP_API romap_status romap_phase_times(romap_ctx* ctx, double* ms, int64_t* launches);
+
+/* Measurement utility (no counterpart in the paper): the request rates that
+ * bound the fused training kernel's hash gather and scatter, measured on
+ * the current device.  Every lane issues its own pseudo-random request into
+ * an L2-resident buffer (32 MiB of 4-byte words; 64 MiB of float pairs),
+ * 8 in flight per thread, 2048 threads per SM.  out[0] = 4-byte loads per
+ * second, out[1] = red.global.add.v2.f32 reductions per second, out[2] =
+ * load + reduction pairs per second (the fused kernel issues one 4-byte
+ * gather and one 8-byte reduction per corner and level).  Best of three
+ * timed launches on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream); allocates about 96 MiB with cudaMalloc for the duration of the
+ * call and synchronises the stream. */
+ROMAP_API romap_status romap_measure_request_rates(void* cuda_stream, double* out);
 
 #ifdef __cplusplus
 }

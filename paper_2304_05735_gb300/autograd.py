@@ -2,16 +2,21 @@
 
 ``render(params, origin, dir, bg, ...)`` returns per ray (C_hat rgb, D_hat, opacity, sum of sigma) computed by
 romap_fn_forward (sampling, hash encoding, MLP, volume rendering of Sec. V-B, Eq. 6); its backward is
-romap_fn_backward (compositing adjoint, MLP input and weight gradients, hash-gradient scatter), which recomputes the
-per-sample MLP activations instead of storing them.  Only ``params`` (the object's hash table and MLP weights, FP32,
-laid out as romap_param_layout describes) receives a gradient.  PyTorch provides device memory and streams; every
-computation runs in libromap's kernels.
+romap_fn_backward (compositing adjoint, MLP input and weight gradients, hash-gradient scatter).  For short rays the
+forward stores every sample's MLP activations and the backward reads them back (ROMAP_STORE_ACT); when rays get long
+(more than ``STORE_MAX_SAMPLES`` samples per ray) the backward recomputes them instead, so memory does not grow with
+the activations.  Only ``params`` (the object's hash table and MLP weights, FP32, laid out as romap_param_layout
+describes) receives a gradient.  PyTorch provides device memory and streams; every computation runs in libromap's
+kernels.
 """
 import ctypes as C
 
 import torch
 
 from . import romap as R
+
+# rays with at most this many samples keep their activations between forward and backward; longer ones recompute
+STORE_MAX_SAMPLES = 256
 
 
 class Context:
@@ -38,14 +43,14 @@ class Context:
 
 class RenderFunction(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, params, origin, direction, bg, rctx, half, seed, step, jitter, occupancy):
+    def forward(ctx, params, origin, direction, bg, rctx, half, seed, step, jitter, occupancy, store_act):
         n = origin.shape[0]
+        flags = (R.ROMAP_JITTER if jitter else 0) | (R.ROMAP_STORE_ACT if store_act else 0)
         ws_bytes = C.c_size_t()
-        R.check(R.romap_fn_workspace_size(rctx.h, n, C.byref(ws_bytes)), "romap_fn_workspace_size")
+        R.check(R.romap_fn_workspace_size(rctx.h, n, flags, C.byref(ws_bytes)), "romap_fn_workspace_size")
         ws = torch.empty(ws_bytes.value, dtype=torch.uint8, device=params.device)
         out = torch.empty(n, 6, dtype=torch.float32, device=params.device)
         halfa = (C.c_float * 3)(*half)
-        flags = R.ROMAP_JITTER if jitter else 0
         R.check(R.romap_fn_forward(rctx.h, params.data_ptr(), halfa, seed, step, R.ptr(occupancy), origin.data_ptr(),
                                    direction.data_ptr(), bg.data_ptr(), n, flags, ws.data_ptr(), ws.numel(),
                                    out.data_ptr(), None), "romap_fn_forward")
@@ -63,13 +68,17 @@ class RenderFunction(torch.autograd.Function):
                                     origin.data_ptr(), direction.data_ptr(), bg.data_ptr(), origin.shape[0],
                                     ctx.flags, ws.data_ptr(), ws.numel(), g.data_ptr(), grad.data_ptr(), None),
                 "romap_fn_backward")
-        return grad, None, None, None, None, None, None, None, None, None
+        return grad, None, None, None, None, None, None, None, None, None, None
 
 
-def render(params, origin, direction, bg, rctx, half=(0.5, 0.5, 0.5), seed=0, step=0, jitter=True, occupancy=None):
-    """Differentiable render of object-frame rays (unit directions).  Returns [n, 6]."""
+def render(params, origin, direction, bg, rctx, half=(0.5, 0.5, 0.5), seed=0, step=0, jitter=True, occupancy=None,
+           recompute=None):
+    """Differentiable render of object-frame rays (unit directions).  Returns [n, 6].  recompute: None picks by ray
+    length (stored activations up to STORE_MAX_SAMPLES samples per ray), True / False force it."""
     for t in (params, origin, direction, bg):
         if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
             raise ValueError("params, origin, direction and bg must be contiguous float32 CUDA tensors")
+    if recompute is None:
+        recompute = rctx.cfg.n_samples > STORE_MAX_SAMPLES
     return RenderFunction.apply(params, origin, direction, bg, rctx, tuple(half), int(seed), int(step), bool(jitter),
-                                occupancy)
+                                occupancy, not recompute)

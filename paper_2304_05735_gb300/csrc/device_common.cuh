@@ -98,6 +98,29 @@ __device__ __forceinline__ void scatter_corners(float2* gt, const uint32_t idx[8
   }
 }
 
+// Deterministic mode: one contribution added to a 64-bit fixed-point accumulator (kFixBits fractional bits), rounded
+// once to nearest.  Zero is skipped; a NaN or a contribution beyond kFixMaxContribution is not added and sets
+// kStatusFixRange (NaN also kStatusNonfinite) so that the step reports it.
+__device__ __forceinline__ void red_add_fix(unsigned long long* addr, float v, int32_t* status, int bits = kFixBits,
+                                            float max_abs = kFixMaxContribution) {
+  if (v == 0.0f) return;
+  if (!(fabsf(v) <= max_abs)) {
+    if (status) atomicOr(status, (v != v) ? (kStatusFixRange | kStatusNonfinite) : kStatusFixRange);
+    return;
+  }
+  const long long q = __double2ll_rn(ldexp((double)v, bits));
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(addr), "l"((unsigned long long)q) : "memory");
+}
+// Fixed-point scatter of one level (gt points at the level's first entry, F = 2 accumulators per entry).
+__device__ __forceinline__ void scatter_corners_fix(unsigned long long* gt, const uint32_t idx[8], const float w[8],
+                                                    float d0, float d1, int32_t* status) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    red_add_fix(gt + 2 * (size_t)idx[k], w[k] * d0, status);
+    red_add_fix(gt + 2 * (size_t)idx[k] + 1, w[k] * d1, status);
+  }
+}
+
 // Position of candidate i of a ray (same operations as for_candidates).
 __device__ inline float candidate_t(float tn, float step_len, int i, uint32_t k0, uint32_t k1, uint32_t step,
                                     uint32_t slot, int jitter) {

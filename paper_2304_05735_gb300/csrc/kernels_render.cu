@@ -14,6 +14,7 @@
 // background rays to learn).
 #include <cuda_fp16.h>
 
+#include "device_common.cuh"
 #include "romap_internal.cuh"
 
 namespace romap {
@@ -166,12 +167,21 @@ __global__ void __launch_bounds__(256) k_composite(GridParams g, BatchDesc b, Ra
       }
     }
     if (lane == 0) {
-      float* L = dyn[bi].loss;
-      atomicAdd(L + 0, loss);
-      if (l_rgb != 0.f) atomicAdd(L + 1, l_rgb);
-      if (l_rr != 0.f) atomicAdd(L + 2, l_rr);
-      if (l_dep != 0.f) atomicAdd(L + 3, l_dep);
-      if (l_den != 0.f) atomicAdd(L + 4, l_den);
+      if (g.det) {  // fixed-point sums (converted after the backward): the same bits in any order
+        unsigned long long* Q = dyn[bi].loss_fix;
+        red_add_fix(Q + 0, loss, status, kFixLossBits, kFixLossMaxContribution);
+        red_add_fix(Q + 1, l_rgb, status, kFixLossBits, kFixLossMaxContribution);
+        red_add_fix(Q + 2, l_rr, status, kFixLossBits, kFixLossMaxContribution);
+        red_add_fix(Q + 3, l_dep, status, kFixLossBits, kFixLossMaxContribution);
+        red_add_fix(Q + 4, l_den, status, kFixLossBits, kFixLossMaxContribution);
+      } else {
+        float* L = dyn[bi].loss;
+        atomicAdd(L + 0, loss);
+        if (l_rgb != 0.f) atomicAdd(L + 1, l_rgb);
+        if (l_rr != 0.f) atomicAdd(L + 2, l_rr);
+        if (l_dep != 0.f) atomicAdd(L + 3, l_dep);
+        if (l_den != 0.f) atomicAdd(L + 4, l_den);
+      }
       if (!isfinite(loss) && status) atomicOr(status, 1);
     }
   } else {
@@ -246,6 +256,16 @@ __device__ __forceinline__ void adam4(float4& p, float4& m, float4& v, const flo
   }
 }
 
+// Exact skip of never-touched parameters.  Every chunk of kAdamChunk parameters (64 float4 groups, two per lane of one
+// warp) has a touched flag, 0 while every gradient the chunk has received was 0.  Such a chunk has m = v = g = 0, for
+// which the Adam step is exactly nothing: m' = b1 0 + (1 - b1) 0 = 0, v' = 0, p' = p - lr 0 / (0 + eps) = p, the
+// gradient is already 0 and the FP16 copy already equals p.  So the warp reads only the chunk's gradient and moves
+// on; the first non-zero (or NaN) gradient flags the chunk, which is updated at every step from then on, as in dense
+// Adam.  The results are bit-identical to updating every parameter.
+__device__ __forceinline__ bool nonzero4(const float4& a) {
+  return a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f;
+}
+
 __global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int write_half) {
   const ObjectDev& ob = b.objs[b.slot[blockIdx.y]];
   const float c1 = ob.bc1, c2 = ob.bc2;  // bias corrections of this step, set with the step counter
@@ -256,39 +276,108 @@ __global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int wri
   float4* M = reinterpret_cast<float4*>(ob.m);
   float4* V = reinterpret_cast<float4*>(ob.v);
   __half2* H = reinterpret_cast<__half2*>(ob.table_h);
+  uint8_t* touched = g.adam_dense ? nullptr : ob.touched;
   const bool half = write_half && ob.table_h;
   const int64_t n4 = g.n_params_pad / 4;
   const int64_t nh4 = g.n_hash / 4;  // n_hash is even; the FP16 copy covers whole float4s below n_hash
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int kChunk4 = kAdamChunk / 4;
+  const int64_t n_chunks = (n4 + kChunk4 - 1) / kChunk4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  // two float4 groups per thread in flight; the moments are streamed (only this kernel touches them)
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + stride < n4; i += 2 * stride) {
-    const int64_t j = i + stride;
-    float4 g0 = G[i], g1 = G[j];
-    float4 m0 = __ldcs(M + i), m1 = __ldcs(M + j);
-    float4 v0 = __ldcs(V + i), v1 = __ldcs(V + j);
-    float4 p0 = P[i], p1 = P[j];
-    adam4(p0, m0, v0, g0, b1, b2, ob1, ob2, lr, eps, c1, c2);
-    adam4(p1, m1, v1, g1, b1, b2, ob1, ob2, lr, eps, c1, c2);
-    P[i] = p0; P[j] = p1;
-    __stcs(M + i, m0); __stcs(M + j, m1);
-    __stcs(V + i, v0); __stcs(V + j, v1);
-    G[i] = zero; G[j] = zero;
-    if (half) {
-      if (i < nh4) { H[2 * i] = __floats2half2_rn(p0.x, p0.y); H[2 * i + 1] = __floats2half2_rn(p0.z, p0.w); }
-      if (j < nh4) { H[2 * j] = __floats2half2_rn(p1.x, p1.y); H[2 * j + 1] = __floats2half2_rn(p1.z, p1.w); }
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
+    const int64_t i = c * kChunk4 + lane, j = i + 32;
+    const bool vi = i < n4, vj = j < n4;
+    float4 g0, g1, m0 = zero, m1 = zero, v0 = zero, v1 = zero, p0 = zero, p1 = zero;
+    const bool was = touched == nullptr || touched[c] != 0;  // one byte, the same for the whole warp
+    if (was) {  // issue every load of the chunk at once
+      g0 = vi ? G[i] : zero; g1 = vj ? G[j] : zero;
+      if (vi) { m0 = __ldcs(M + i); v0 = __ldcs(V + i); p0 = P[i]; }
+      if (vj) { m1 = __ldcs(M + j); v1 = __ldcs(V + j); p1 = P[j]; }
+    } else {
+      g0 = vi ? G[i] : zero; g1 = vj ? G[j] : zero;
+      if (!__any_sync(0xffffffffu, nonzero4(g0) || nonzero4(g1))) continue;  // m = v = g = 0: nothing changes
+      if (lane == 0) touched[c] = 1;
+      if (vi) { m0 = __ldcs(M + i); v0 = __ldcs(V + i); p0 = P[i]; }
+      if (vj) { m1 = __ldcs(M + j); v1 = __ldcs(V + j); p1 = P[j]; }
+    }
+    if (vi) {
+      adam4(p0, m0, v0, g0, b1, b2, ob1, ob2, lr, eps, c1, c2);
+      P[i] = p0;
+      __stcs(M + i, m0);
+      __stcs(V + i, v0);
+      G[i] = zero;
+      if (half && i < nh4) { H[2 * i] = __floats2half2_rn(p0.x, p0.y); H[2 * i + 1] = __floats2half2_rn(p0.z, p0.w); }
+    }
+    if (vj) {
+      adam4(p1, m1, v1, g1, b1, b2, ob1, ob2, lr, eps, c1, c2);
+      P[j] = p1;
+      __stcs(M + j, m1);
+      __stcs(V + j, v1);
+      G[j] = zero;
+      if (half && j < nh4) { H[2 * j] = __floats2half2_rn(p1.x, p1.y); H[2 * j + 1] = __floats2half2_rn(p1.z, p1.w); }
     }
   }
-  for (; i < n4; i += stride) {
-    float4 g0 = G[i], m0 = __ldcs(M + i), v0 = __ldcs(V + i), p0 = P[i];
-    adam4(p0, m0, v0, g0, b1, b2, ob1, ob2, lr, eps, c1, c2);
-    P[i] = p0;
-    __stcs(M + i, m0);
-    __stcs(V + i, v0);
-    G[i] = zero;
-    if (half && i < nh4) { H[2 * i] = __floats2half2_rn(p0.x, p0.y); H[2 * i + 1] = __floats2half2_rn(p0.z, p0.w); }
+}
+
+// Deterministic mode: fixed-point gradient -> FP32 gradient (added; zero accumulators are skipped) and accumulator
+// reset; block (0, entry) also converts the entry's fixed-point loss sums.
+__global__ void __launch_bounds__(256) k_fix_finish(GridParams g, BatchDesc b, BatchDyn* dyn) {
+  const ObjectDev& ob = b.objs[b.slot[blockIdx.y]];
+  if (blockIdx.x == 0 && threadIdx.x < 5) {
+    const int k = threadIdx.x;
+    dyn[blockIdx.y].loss[k] = (float)ldexp((double)(long long)dyn[blockIdx.y].loss_fix[k], -kFixLossBits);
   }
+  longlong2* Q = reinterpret_cast<longlong2*>(ob.gfix);
+  float2* G = reinterpret_cast<float2*>(ob.grad);
+  if (!Q) return;
+  const int64_t n2 = g.n_params_pad / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const longlong2 q = Q[i];
+    if (q.x == 0 && q.y == 0) continue;
+    float2 gg = G[i];
+    gg.x += (float)ldexp((double)q.x, -kFixBits);
+    gg.y += (float)ldexp((double)q.y, -kFixBits);
+    G[i] = gg;
+    Q[i] = make_longlong2(0, 0);
+  }
+}
+
+void launch_fix_finish(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, cudaStream_t stream) {
+  if (b.n <= 0) return;
+  int64_t n2 = g.n_params_pad / 2;
+  int chunks = (int)((n2 + 255) / 256);
+  int max_chunks = 4096 / (b.n < 1 ? 1 : b.n) + 1;
+  if (max_chunks < 16) max_chunks = 16;
+  if (chunks > max_chunks) chunks = max_chunks;
+  k_fix_finish<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, dyn);
+}
+
+__global__ void k_touched_from_moments(int64_t n4, const float4* __restrict__ M, const float4* __restrict__ V,
+                                       uint8_t* __restrict__ touched) {
+  constexpr int kChunk4 = kAdamChunk / 4;
+  const int64_t n_chunks = (n4 + kChunk4 - 1) / kChunk4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
+    bool nz = false;
+    for (int64_t i = c * kChunk4 + lane; i < (c + 1) * kChunk4 && i < n4; i += 32)
+      nz = nz || nonzero4(M[i]) || nonzero4(V[i]);
+    nz = __any_sync(0xffffffffu, nz);
+    if (lane == 0) touched[c] = nz ? 1 : 0;
+  }
+}
+
+void launch_touched_from_moments(const GridParams& g, const float* m, const float* v, uint8_t* touched,
+                                 cudaStream_t stream) {
+  const int64_t n4 = g.n_params_pad / 4;
+  const int64_t n_chunks = (n4 + kAdamChunk / 4 - 1) / (kAdamChunk / 4);
+  int blocks = (int)((n_chunks + 7) / 8);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_touched_from_moments<<<blocks, 256, 0, stream>>>(n4, reinterpret_cast<const float4*>(m),
+                                                     reinterpret_cast<const float4*>(v), touched);
 }
 
 __global__ void k_advance_step(GridParams g, BatchDesc b) {
@@ -318,8 +407,8 @@ void launch_final_losses(const BatchDyn* dyn, const BatchDesc& b, float* out, cu
 void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream) {
   if (b.n <= 0) return;
   int64_t n4 = g.n_params_pad / 4;
-  int chunks = (int)((n4 + 255) / 256);
-  int max_chunks = 4096 / (b.n < 1 ? 1 : b.n) + 1;  // about 4k blocks of 256 threads, two float4 groups each
+  int chunks = (int)((n4 + 511) / 512);  // blocks of 8 warps, one 64-float4 chunk per warp and round
+  int max_chunks = 4096 / (b.n < 1 ? 1 : b.n) + 1;  // about 4k blocks of 256 threads, two float4 groups per lane
   if (max_chunks < 16) max_chunks = 16;
   if (chunks > max_chunks) chunks = max_chunks;
   k_adam<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, write_half);

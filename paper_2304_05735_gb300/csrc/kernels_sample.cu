@@ -418,8 +418,12 @@ __global__ void __launch_bounds__(1024) k_scan(BatchDesc b, uint32_t* block_sums
     dd.sample_base = (int64_t)tile_base * kTile;
     dd.n_samples = (int32_t)s_count[i];
     dd.pad_ = 0;
-    for (int k = 0; k < 5; ++k) dd.loss[k] = 0.0f;
+    for (int k = 0; k < 5; ++k) {
+      dd.loss[k] = 0.0f;
+      dd.loss_fix[k] = 0ull;
+    }
     dd.pad2_[0] = dd.pad2_[1] = dd.pad2_[2] = 0.0f;
+    dd.pad3_ = 0;
     dyn[i] = dd;
   }
   if (threadIdx.x < (unsigned)b.n) s_tiles[threadIdx.x] = tile_base;  // now the first tile of entry i

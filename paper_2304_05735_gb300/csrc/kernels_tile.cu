@@ -180,6 +180,42 @@ __device__ inline void wgrad_flush(float* __restrict__ dst, int rows, int cols, 
     }
 }
 
+// Deterministic mode: the same flush into the fixed-point accumulator (called after every tile, so each flushed sum
+// covers one tile, whose samples and their order do not depend on the launch: the sums are reproducible).
+template <int NO, int NK, int TO, int TK>
+__device__ inline void wgrad_flush_fix(unsigned long long* __restrict__ dst, int rows, int cols, float (&g)[TO][TK],
+                                       int32_t* status) {
+  const int t = threadIdx.x, og = t / (NK / TK), kg = t % (NK / TK);
+#pragma unroll
+  for (int i = 0; i < TO; ++i)
+#pragma unroll
+    for (int j = 0; j < TK; ++j) {
+      int o = og + (NO / TO) * i, k = kg + (NK / TK) * j;
+      if (o < rows && k < cols) red_add_fix(dst + o * cols + k, g[i][j], status);
+      g[i][j] = 0.0f;
+    }
+}
+
+// Stored activations of one tile (ACT): rows [encoding (LFP) | H1 (64) | density-net outputs 0..15 | H2 (64) |
+// H3 (64)] x 128 samples, copied as float4 between shared memory and the workspace (to_global: smem -> act).
+__host__ __device__ constexpr int act_rows(int lfp) { return lfp + kH + kDOut + kH + kH; }
+
+template <int LFP, bool TO_GLOBAL>
+__device__ inline void act_copy(TileSmem<LFP>& sm, float* __restrict__ act) {
+  constexpr int kRows = act_rows(LFP), kQ = kTile / 4;
+  for (int i = threadIdx.x; i < kRows * kQ; i += kThreads) {
+    const int r = i / kQ, q = i % kQ;
+    float* row = r < LFP ? sm.E + r * kAS
+                 : r < LFP + kH ? sm.H1 + (r - LFP) * kAS
+                 : r < LFP + kH + kDOut ? sm.OC + (r - LFP - kH) * kAS
+                 : r < LFP + 2 * kH + kDOut ? sm.H2 + (r - LFP - kH - kDOut) * kAS
+                 : sm.H3 + (r - LFP - 2 * kH - kDOut) * kAS;
+    float4* gp = reinterpret_cast<float4*>(act + (size_t)r * kTile) + q;
+    float4* sp = reinterpret_cast<float4*>(row) + q;
+    if (TO_GLOBAL) *gp = *sp; else *sp = *gp;
+  }
+}
+
 template <int TO, int TK>
 __device__ inline void zero2(float (&g)[TO][TK]) {
 #pragma unroll
@@ -191,8 +227,13 @@ __device__ inline void zero2(float (&g)[TO][TK]) {
 // ---------------------------------------------------------------------------
 // The kernel.  MODE 0: forward only (writes sigma and rgb per sample).
 // MODE 1: recompute forward, then backward from dL/dsigma and dL/drgb.
+// DET (MODE 1 only): gradients go to the object's fixed-point accumulator,
+// the weight gradients flushed after every tile.
+// ACT (stored activations): MODE 0 also writes the tile's activations (the
+// encoding, every hidden layer and the density-net outputs) to S.act; MODE 1
+// reads them back instead of gathering and recomputing the forward.
 // ---------------------------------------------------------------------------
-template <int LFP, int MODE>
+template <int LFP, int MODE, bool DET = false, bool ACT = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tile_mlp(GridParams g, BatchDesc b, const BatchDyn* __restrict__ dyn, const int32_t* __restrict__ totals,
                RayBuf R, SampleBuf S) {
@@ -209,6 +250,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int TO1 = 2, TK1 = LFP / 8;   // dW1: 64 x LFP
   float g1[TO1][TK1], g2[1][4], g3[1][5], g4[4][4], g5[1][1], g6[4][4];
   zero2(g1); zero2(g2); zero2(g3); zero2(g4); zero2(g5); zero2(g6);
+  auto flush_fix = [&](unsigned long long* gm) {
+    wgrad_flush_fix<kH, LFP, TO1, TK1>(gm + g.mlp_off[0], kH, g.LF, g1, b.status);
+    wgrad_flush_fix<kDOut, kH, 1, 4>(gm + g.mlp_off[1], kDOut, kH, g2, b.status);
+    if (!g.single_net) {
+      wgrad_flush_fix<kH, kCinPad, 1, 5>(gm + g.mlp_off[2], kH, cin, g3, b.status);
+      wgrad_flush_fix<kH, kH, 4, 4>(gm + g.mlp_off[3], kH, kH, g4, b.status);
+      wgrad_flush_fix<kC3Rows, kH, 1, 1>(gm + g.mlp_off[4], 3, kH, g5, b.status);
+    } else {
+      if (g.extra >= 1) wgrad_flush_fix<kH, kH, 4, 4>(gm + g.mlp_off[5], kH, kH, g4, b.status);
+      if (g.extra >= 2) wgrad_flush_fix<kH, kH, 4, 4>(gm + g.mlp_off[6], kH, kH, g6, b.status);
+    }
+  };
   auto flush = [&](float* gm) {
     wgrad_flush<kH, LFP, TO1, TK1>(gm + g.mlp_off[0], kH, g.LF, g1);
     wgrad_flush<kDOut, kH, 1, 4>(gm + g.mlp_off[1], kDOut, kH, g2);
@@ -229,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int nbi = bi < 0 ? 0 : bi;
     while (nbi + 1 < b.n && tile >= dyn[nbi].tile_base + dyn[nbi].n_tiles) ++nbi;
     if (nbi != bi) {
-      if (MODE == 1 && bi >= 0) flush(ob->grad);
+      if (MODE == 1 && !DET && bi >= 0) flush(ob->grad);
       bi = nbi;
       ob = &b.objs[b.slot[bi]];
       __syncthreads();
@@ -283,6 +336,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
 
+    float* HL = sm.H1;  // the hidden layer that feeds the density net's output layer
+    if (g.extra >= 1) HL = g.extra >= 2 ? sm.H3 : sm.H2;
+    float* const act = ACT ? S.act + (size_t)tile * act_rows(LFP) * kTile : nullptr;
+    if (MODE == 1 && ACT) {  // stored activations of this tile instead of the gather and the forward GEMMs
+      act_copy<LFP, false>(sm, act);
+      __syncthreads();
+    } else {
     // ---- hash encoding (gather): thread -> (sample, half of the levels) --
     {
       const int s = t & (kTile - 1), h = t >> 7;
@@ -318,18 +378,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       store_tile<4>(sm.H1, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
     }
     __syncthreads();
-    float* HL = sm.H1;  // the hidden layer that feeds the density net's output layer
     if (g.extra >= 1) {  // single-network hidden layer 2: H2 = relu(H1 M1^T)
       float acc[8][4];
       gemm_tile<4>(sm.H1, kH, sm.w4t, kH, acc);
       store_tile<4>(sm.H2, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
       __syncthreads();
-      HL = sm.H2;
       if (g.extra >= 2) {  // hidden layer 3: H3 = relu(H2 M2^T)
         gemm_tile_bt<4>(sm.H2, kH, sm.w6, kW6S, acc);
         store_tile<4>(sm.H3, acc, [](float v, int, int) { return fmaxf(v, 0.0f); });
         __syncthreads();
-        HL = sm.H3;
       }
     }
     {  // OC[0..15] = HL W2^T
@@ -352,6 +409,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
     }
+    }  // gather and forward
+    if (MODE == 0 && ACT) act_copy<LFP, true>(sm, act);  // (reads rows the logits below do not write)
     if (t < kTile) {  // logits, sigmoid, density
       float l0 = 0.f, l1 = 0.f, l2 = 0.f;
       if (g.single_net) {  // the colour logits are density-net outputs 1..3
@@ -492,34 +551,52 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (d0 == 0.f && d1 == 0.f) continue;
           Corners c;
           level_corners(g, l, p, ob->half, ob->inv_ext, c);
-          float2* gt = reinterpret_cast<float2*>(ob->grad) + g.off[l];
-          scatter_corners(gt, c.idx, c.w, d0, d1);
+          if (DET) {
+            scatter_corners_fix(ob->gfix + 2 * (size_t)g.off[l], c.idx, c.w, d0, d1, b.status);
+          } else {
+            float2* gt = reinterpret_cast<float2*>(ob->grad) + g.off[l];
+            scatter_corners(gt, c.idx, c.w, d0, d1);
+          }
         }
       }
     }
+    if (DET) flush_fix(ob->gfix);  // this tile's weight gradients
     __syncthreads();
   }
-  if (MODE == 1 && bi >= 0) flush(ob->grad);
+  if (MODE == 1 && !DET && bi >= 0) flush(ob->grad);
 }
 
-template <int LFP, int MODE>
+template <int LFP, int MODE, bool DET, bool ACT>
 static void launch_tile_t(const GridParams& g, const BatchDesc& b, const BatchDyn* dyn, const int32_t* totals,
                           RayBuf r, SampleBuf s, int n_ctas, cudaStream_t stream) {
   static std::atomic<uint64_t> attr_done{0};
   int bytes = (int)sizeof(TileSmem<LFP>);
-  set_smem_attr(k_tile_mlp<LFP, MODE>, bytes, attr_done);
-  k_tile_mlp<LFP, MODE><<<n_ctas, kThreads, bytes, stream>>>(g, b, dyn, totals, r, s);
+  set_smem_attr(k_tile_mlp<LFP, MODE, DET, ACT>, bytes, attr_done);
+  k_tile_mlp<LFP, MODE, DET, ACT><<<n_ctas, kThreads, bytes, stream>>>(g, b, dyn, totals, r, s);
+}
+
+template <int LFP>
+static void launch_tile_l(int mode, const GridParams& g, const BatchDesc& b, const BatchDyn* dyn,
+                          const int32_t* totals, RayBuf r, SampleBuf s, int n_ctas, cudaStream_t stream) {
+  const bool act = s.act != nullptr;  // stored activations (the deterministic mode keeps recomputing)
+  if (mode == 0) {
+    if (act) launch_tile_t<LFP, 0, false, true>(g, b, dyn, totals, r, s, n_ctas, stream);
+    else launch_tile_t<LFP, 0, false, false>(g, b, dyn, totals, r, s, n_ctas, stream);
+  } else if (g.det) {
+    launch_tile_t<LFP, 1, true, false>(g, b, dyn, totals, r, s, n_ctas, stream);
+  } else if (act) {
+    launch_tile_t<LFP, 1, false, true>(g, b, dyn, totals, r, s, n_ctas, stream);
+  } else {
+    launch_tile_t<LFP, 1, false, false>(g, b, dyn, totals, r, s, n_ctas, stream);
+  }
 }
 
 void launch_tile_mlp(int mode, const GridParams& g, const BatchDesc& b, const BatchDyn* dyn, const int32_t* totals,
                      RayBuf r, SampleBuf s, int n_ctas, cudaStream_t stream) {
-  if (g.LF <= 16) {
-    if (mode == 0) launch_tile_t<16, 0>(g, b, dyn, totals, r, s, n_ctas, stream);
-    else launch_tile_t<16, 1>(g, b, dyn, totals, r, s, n_ctas, stream);
-  } else {
-    if (mode == 0) launch_tile_t<32, 0>(g, b, dyn, totals, r, s, n_ctas, stream);
-    else launch_tile_t<32, 1>(g, b, dyn, totals, r, s, n_ctas, stream);
-  }
+  if (g.LF <= 16) launch_tile_l<16>(mode, g, b, dyn, totals, r, s, n_ctas, stream);
+  else launch_tile_l<32>(mode, g, b, dyn, totals, r, s, n_ctas, stream);
 }
+
+int act_rows_for(int LF) { return act_rows(LF <= 16 ? 16 : 32); }
 
 }  // namespace romap

@@ -69,6 +69,8 @@ struct Object {
   int64_t pool_n = 0, pool_cap = 0;
   uint64_t* occ = nullptr;
   float* occ_density = nullptr;  // per-cell moving maximum of the learned density (romap_update_occupancy)
+  unsigned long long* gfix = nullptr;  // deterministic mode: fixed-point gradient accumulator
+  uint8_t* touched = nullptr;          // Adam's per-chunk touched flags
   // incremental training data (Eq. 5): camera centre of the last image used, training iterations still owed
   bool have_view = false;
   double last_view[3] = {0, 0, 0};
@@ -115,21 +117,36 @@ struct romap_ctx {
   int32_t* status = nullptr;
   unsigned long long* live_counter = nullptr;
   int32_t* batch_arrays = nullptr;
-  std::vector<int32_t> batch_key;  // host copy of the uploaded batch arrays
+  std::vector<int32_t> batch_key;  // host copy of the batch arrays uploaded to ws_batch
   int batch_n = 0;                 // entries of the uploaded batch
+  std::vector<int32_t> last_batch; // batch arrays of the last step that ran (eager or replayed)
+  int last_batch_n = 0;
+  const int32_t* batch_override = nullptr;  // while capturing: the graph's own copy of its batch arrays
   BatchDyn* dyn_host = nullptr;    // pinned
+  BatchDyn* dyn_gather = nullptr;  // per_object: each listed object's BatchDyn after its last step [max_objects]
+  BatchDyn* dyn_gather_host = nullptr;  // pinned [max_objects]
   romap_stats stats{};
   int64_t launches = 0;
   // autotuned choice of the mixed-precision tile kernel: -1 until tuned, then an index of kTileKernels
   int tile_kernel = -1;
   float tile_kernel_ms[4] = {0, 0, 0, 0};
-  // CUDA graph of one training step of the last batch composition (captured on cap_stream, replayed on stream)
+  // CUDA graphs of one training step, one per batch composition (captured on cap_stream, replayed on stream), least
+  // recently used first out beyond kMaxStepGraphs
+  struct StepGraph {
+    std::vector<int32_t> key;
+    cudaGraphExec_t exec = nullptr;
+    int32_t* batch_dev = nullptr;      // the graph's own device copy of its batch arrays
+    std::vector<int32_t> batch;        // host copy of them
+    int batch_n = 0;
+    int launches = 0;                  // kernels one replay runs
+    uint64_t last_use = 0;
+    uint64_t ws_generation = 0;        // workspace generation it was captured against
+  };
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t step_graph = nullptr;
-  std::vector<int32_t> graph_key;
-  std::vector<int32_t> graph_batch;  // batch arrays the graph's kernels read from ws_batch
+  std::vector<StepGraph> graphs;
+  uint64_t graph_clock = 0;
+  int64_t graph_captures = 0, graph_replays = 0;
   uint64_t ws_generation = 0;   // bumped whenever a workspace buffer moves
-  uint64_t graph_ws_generation = 0;
   bool graphs_enabled = true;
   // budgeted training: measured step time of each batch composition (ms, moving average)
   std::map<std::vector<int32_t>, double> step_ms_est;
@@ -271,6 +288,7 @@ size_t carve_samples(char* base, int64_t ns, SampleBuf* S) {
   S->rgb = (float*)take(sizeof(float) * 3 * ns);
   S->dsigma = (float*)take(sizeof(float) * ns);
   S->drgb = (float*)take(sizeof(float) * 3 * ns);
+  S->act = nullptr;  // stored activations are carved separately (functional API with ROMAP_STORE_ACT)
   return o;
 }
 
@@ -348,6 +366,10 @@ BatchDesc desc_from(const HostBatch& hb, const int32_t* dev, ObjectDev* objs) {
 }
 
 romap_status upload_batch(romap_ctx* ctx, const HostBatch& hb, BatchDesc* out) {
+  if (ctx->batch_override) {  // capturing a step graph: its kernels read the graph's own copy of these arrays
+    *out = desc_from(hb, ctx->batch_override, ctx->objs_dev);
+    return ROMAP_OK;
+  }
   size_t bytes = sizeof(int32_t) * hb.arr.size();
   if (ctx->batch_key != hb.arr) {
     ROMAP_TRY(grow(ctx, ctx->ws_batch, bytes));
@@ -385,6 +407,8 @@ romap_status sync_object(romap_ctx* ctx, int slot) {
   d.whole_pool = o.rays_per_step >= o.pool_n ? 1 : 0;
   set_object_step(d, (uint32_t)(o.steps_done + 1), ctx->cfg.beta1, ctx->cfg.beta2);
   d.pad_ = 0;
+  d.gfix = o.gfix;
+  d.touched = o.touched;
   CUDA_TRY(cudaMemcpyAsync(ctx->objs_dev + slot, &d, sizeof(ObjectDev), cudaMemcpyHostToDevice, ctx->stream));
   return ROMAP_OK;
 }
@@ -429,6 +453,10 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   if (c->hidden_layers > 1 && !c->single_net)
     return fail(ROMAP_ERR_UNSUPPORTED, "more than one hidden layer needs the single-network model");
   if (c->reserved != 0) return fail(ROMAP_ERR_INVALID_ARG, "reserved must be 0");
+  if (c->deterministic != 0 && c->deterministic != 1) return fail(ROMAP_ERR_INVALID_ARG, "deterministic is 0 or 1");
+  if (c->per_object != 0 && c->per_object != 1) return fail(ROMAP_ERR_INVALID_ARG, "per_object is 0 or 1");
+  if (c->deterministic && c->precision != ROMAP_PREC_FP32)
+    return fail(ROMAP_ERR_UNSUPPORTED, "the deterministic mode is built for ROMAP_PREC_FP32 only");
   if (c->single_net && c->precision == ROMAP_PREC_MIXED_FP8)
     return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model has no 64x64 hidden layer to run in FP8");
   if (c->max_objects < 1 || c->max_objects > 1024) return fail(ROMAP_ERR_INVALID_ARG, "max_objects must be in 1..1024");
@@ -485,6 +513,7 @@ romap_status make_grid(const romap_config* c, GridParams* g) {
   G.fp8 = c->precision == ROMAP_PREC_MIXED_FP8 ? 1 : 0;
   G.f16 = c->precision == ROMAP_PREC_MIXED_FP16 ? 1 : 0;
   G.single_net = c->single_net ? 1 : 0;
+  G.det = c->deterministic ? 1 : 0;
   *g = G;
   return ROMAP_OK;
 }
@@ -502,6 +531,8 @@ void free_object(romap_ctx* ctx, Object& o) {
   dev_free(ctx, o.pool_cls);
   dev_free(ctx, o.occ);
   dev_free(ctx, o.occ_density);
+  dev_free(ctx, o.gfix);
+  dev_free(ctx, o.touched);
   o = Object{};
 }
 
@@ -611,6 +642,21 @@ romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& id
   return ROMAP_OK;
 }
 
+// tile plan bound: per entry at most one partly filled tile per class plus the even padding
+int64_t plan_max_tiles(const HostBatch& hb) { return (int64_t)hb.n_rays + (int64_t)(kPlanClasses + 1) * hb.n; }
+
+// Grows the step workspace (and the tile plan of the mixed path) to hold one step of a batch with these rays per
+// entry.
+romap_status ensure_step_workspace(romap_ctx* ctx, const std::vector<int32_t>& rays) {
+  HostBatch hb;
+  build_batch(std::vector<int32_t>(rays.size(), 0), rays, &hb);
+  const bool mixed = ctx->cfg.precision != ROMAP_PREC_FP32;
+  int64_t ns = mixed ? 0 : (int64_t)hb.n_rays * ctx->g.n_samples + (int64_t)hb.n * kTile;
+  ROMAP_TRY(ensure_workspace(ctx, hb.n_rays, ns, hb.n_blocks, hb.n));
+  if (mixed) ROMAP_TRY(ensure_plan(ctx, hb.n_rays, hb.n_blocks, hb.n, plan_max_tiles(hb)));
+  return ROMAP_OK;
+}
+
 // forward + loss + backward of a batch (no Adam)
 romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchDesc* out_b) {
   std::vector<int32_t> slots(ids.begin(), ids.end()), rays(ids.size());
@@ -621,13 +667,13 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
   const bool mixed = ctx->cfg.precision != ROMAP_PREC_FP32;
   HostBatch hb;
   build_batch(slots, rays, &hb);
-  int64_t ns = mixed ? 0 : (int64_t)hb.n_rays * ctx->g.n_samples + (int64_t)hb.n * kTile;
-  ROMAP_TRY(ensure_workspace(ctx, hb.n_rays, ns, hb.n_blocks, hb.n));
-  // tile plan bound: per entry at most one partly filled tile per class plus the even padding
-  const int64_t max_tiles = (int64_t)hb.n_rays + (int64_t)(kPlanClasses + 1) * hb.n;
-  if (mixed) ROMAP_TRY(ensure_plan(ctx, hb.n_rays, hb.n_blocks, hb.n, max_tiles));
+  ROMAP_TRY(ensure_step_workspace(ctx, rays));
+  const int64_t max_tiles = plan_max_tiles(hb);
   BatchDesc b;
   ROMAP_TRY(upload_batch(ctx, hb, &b));
+  b.status = ctx->status;
+  ctx->last_batch = hb.arr;
+  ctx->last_batch_n = hb.n;
   if (mixed) {
     b.plan = 1;
     b.plan_bcls = ctx->plan.bcls;
@@ -653,10 +699,11 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
       launch_composite(1, ctx->g, b, ctx->R, ctx->S, ctx->dyn, ctx->status, ctx->stream);
     }
     {
-      PhaseScope ps(ctx, 3, 1);
+      PhaseScope ps(ctx, 3, ctx->g.det ? 2 : 1);
       launch_tile_mlp(1, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
+      if (ctx->g.det) launch_fix_finish(ctx->g, b, ctx->dyn, ctx->stream);
     }
-    ctx->launches += 3;
+    ctx->launches += ctx->g.det ? 4 : 3;
   }
   CUDA_TRY(cudaGetLastError());
   ctx->stats.steps += hb.n;
@@ -679,8 +726,21 @@ romap_status validate_ids(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, std
   return ROMAP_OK;
 }
 
-romap_status read_losses(romap_ctx* ctx, int n, float* out_loss, int per_obj, const std::vector<int32_t>& ids) {
-  CUDA_TRY(cudaMemcpyAsync(ctx->dyn_host, ctx->dyn, sizeof(BatchDyn) * n, cudaMemcpyDeviceToHost, ctx->stream));
+// The error a non-zero device status word stands for.
+romap_status status_error(int32_t st) {
+  if (st & kStatusTimeout) return fail(ROMAP_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
+  if (st & kStatusNonfinite) return fail(ROMAP_ERR_NONFINITE, "non-finite loss or gradient (status %d)", st);
+  if (st & kStatusFixRange)
+    return fail(ROMAP_ERR_CAPACITY,
+                "a gradient or loss contribution exceeded the deterministic mode's fixed-point range (status %d)", st);
+  return fail(ROMAP_ERR_NONFINITE, "non-finite loss (status %d)", st);
+}
+
+romap_status read_losses(romap_ctx* ctx, int n, float* out_loss, int per_obj, const std::vector<int32_t>& ids,
+                         bool gathered = false) {
+  BatchDyn* host = gathered ? ctx->dyn_gather_host : ctx->dyn_host;
+  CUDA_TRY(cudaMemcpyAsync(host, gathered ? ctx->dyn_gather : ctx->dyn, sizeof(BatchDyn) * n, cudaMemcpyDeviceToHost,
+                           ctx->stream));
   int32_t st = 0;
   CUDA_TRY(cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -689,14 +749,14 @@ romap_status read_losses(romap_ctx* ctx, int n, float* out_loss, int per_obj, co
     float B = (float)ctx->objs_host[ids[i]].n_rays;
     float inv = B > 0 ? 1.0f / B : 0.0f;
     for (int k = 0; k < per_obj; ++k) {
-      float v = ctx->dyn_host[i].loss[k] * inv;
+      float v = host[i].loss[k] * inv;
       out_loss[per_obj * i + k] = v;
       if (!std::isfinite(v)) bad = true;
     }
   }
   if (bad) {
     CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
-    if (st & kStatusTimeout) return fail(ROMAP_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
+    if (st) return status_error(st);
     return fail(ROMAP_ERR_NONFINITE, "non-finite loss");
   }
   return ROMAP_OK;
@@ -776,6 +836,9 @@ romap_status romap_init(const romap_config* cfg, void* cuda_stream, romap_ctx** 
   if (s == ROMAP_OK) s = dev_alloc_t(ctx, 4, &ctx->totals);
   if (s == ROMAP_OK) s = dev_alloc_t(ctx, 1, &ctx->status);
   if (s == ROMAP_OK) s = dev_alloc_t(ctx, 1, &ctx->live_counter);
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, cfg->max_objects, &ctx->dyn_gather);
+  if (s == ROMAP_OK && cudaMallocHost((void**)&ctx->dyn_gather_host, sizeof(BatchDyn) * cfg->max_objects) != cudaSuccess)
+    s = fail(ROMAP_ERR_OOM, "page-locked allocation of the loss buffer failed");
   if (s == ROMAP_OK) {
     cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->live_counter, 0, sizeof(unsigned long long), ctx->stream);
@@ -806,11 +869,13 @@ romap_status romap_destroy(romap_ctx* ctx) {
   dev_free(ctx, ctx->totals);
   dev_free(ctx, ctx->status);
   dev_free(ctx, ctx->live_counter);
+  dev_free(ctx, ctx->dyn_gather);
   for (DevBuf* b : {&ctx->ws_rays, &ctx->ws_samples, &ctx->ws_blocks, &ctx->ws_batch, &ctx->ws_dyn, &ctx->ws_stage,
                     &ctx->ws_plan, &ctx->ws_mesh, &ctx->ws_mesh_out, &ctx->ws_loss})
     dev_free(ctx, b->p);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->dyn_host) cudaFreeHost(ctx->dyn_host);
+  if (ctx->dyn_gather_host) cudaFreeHost(ctx->dyn_gather_host);
   for (auto& p : ctx->prof) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -843,6 +908,9 @@ romap_status romap_create_object(romap_ctx* ctx, const romap_object_desc* d, int
   if (s == ROMAP_OK) s = dev_alloc_t(ctx, np, &o.v);
   if (s == ROMAP_OK && ctx->cfg.precision != ROMAP_PREC_FP32)
     s = dev_alloc_t(ctx, (size_t)ctx->g.n_hash + 8, &o.table_h);
+  const size_t n_chunks = (np + kAdamChunk - 1) / kAdamChunk;
+  if (s == ROMAP_OK) s = dev_alloc_t(ctx, n_chunks, &o.touched);
+  if (s == ROMAP_OK && ctx->g.det) s = dev_alloc_t(ctx, np, &o.gfix);
   if (s != ROMAP_OK) {
     o.alive = true;
     free_object(ctx, o);
@@ -851,6 +919,8 @@ romap_status romap_create_object(romap_ctx* ctx, const romap_object_desc* d, int
   cudaMemsetAsync(o.grad, 0, np * sizeof(float), ctx->stream);
   cudaMemsetAsync(o.m, 0, np * sizeof(float), ctx->stream);
   cudaMemsetAsync(o.v, 0, np * sizeof(float), ctx->stream);
+  cudaMemsetAsync(o.touched, 0, n_chunks, ctx->stream);
+  if (o.gfix) cudaMemsetAsync(o.gfix, 0, np * sizeof(unsigned long long), ctx->stream);
   launch_init_params(ctx->g, o.params, (uint32_t)d->seed, (uint32_t)(d->seed >> 32), ctx->stream);
   ctx->launches += 1;
   if (o.table_h) {
@@ -1272,16 +1342,57 @@ static romap_status enqueue_step(romap_ctx* ctx, const std::vector<int32_t>& v) 
   return ROMAP_OK;
 }
 
-static void drop_graph(romap_ctx* ctx) {
-  if (ctx->step_graph) cudaGraphExecDestroy(ctx->step_graph);
-  ctx->step_graph = nullptr;
-  ctx->graph_key.clear();
+constexpr int kMaxStepGraphs = 128;
+
+static void free_graph(romap_ctx* ctx, romap_ctx::StepGraph& sg) {
+  if (sg.exec) cudaGraphExecDestroy(sg.exec);
+  dev_free(ctx, sg.batch_dev);
+  sg = romap_ctx::StepGraph{};
 }
 
-// Captures one step of batch v into ctx->step_graph (nothing executes during capture).
+// Drops every cached step graph.
+static void drop_graph(romap_ctx* ctx) {
+  for (auto& sg : ctx->graphs) free_graph(ctx, sg);
+  ctx->graphs.clear();
+}
+
+// The cached graph of composition `key`, or null.  Graphs captured before a workspace buffer moved are dropped
+// (their kernels hold the old addresses).
+static romap_ctx::StepGraph* find_graph(romap_ctx* ctx, const std::vector<int32_t>& key) {
+  for (size_t i = 0; i < ctx->graphs.size();) {
+    if (ctx->graphs[i].ws_generation != ctx->ws_generation) {
+      free_graph(ctx, ctx->graphs[i]);
+      ctx->graphs.erase(ctx->graphs.begin() + (ptrdiff_t)i);
+    } else {
+      ++i;
+    }
+  }
+  for (auto& sg : ctx->graphs)
+    if (sg.key == key) return &sg;
+  return nullptr;
+}
+
+// Captures one step of batch v (nothing executes during capture) into a new cache entry, evicting the least recently
+// used entry when the cache is full.  The graph reads its batch arrays from its own device copy, so graphs of
+// different compositions replay in any order without re-uploading anything.
 static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, const std::vector<int32_t>& key) {
-  drop_graph(ctx);
   if (!ctx->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  if ((int)ctx->graphs.size() >= kMaxStepGraphs) {
+    size_t lru = 0;
+    for (size_t i = 1; i < ctx->graphs.size(); ++i)
+      if (ctx->graphs[i].last_use < ctx->graphs[lru].last_use) lru = i;
+    free_graph(ctx, ctx->graphs[lru]);
+    ctx->graphs.erase(ctx->graphs.begin() + (ptrdiff_t)lru);
+  }
+  romap_ctx::StepGraph sg;
+  sg.key = key;
+  sg.batch = ctx->last_batch;  // the eager step that just ran had this composition
+  sg.batch_n = ctx->last_batch_n;
+  ROMAP_TRY(dev_alloc_t(ctx, sg.batch.size(), &sg.batch_dev));
+  CUDA_TRY(cudaMemcpyAsync(sg.batch_dev, sg.batch.data(), sizeof(int32_t) * sg.batch.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+  // the copy above is pageable: wait for it so that the host vector may change while the graph lives
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   // the capture records launches only; host-side counters are restored afterwards and advanced per replay
   std::vector<int64_t> done(v.size());
   for (size_t i = 0; i < v.size(); ++i) done[i] = ctx->objs[v[i]].steps_done;
@@ -1289,6 +1400,7 @@ static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, 
   int64_t saved_launches = ctx->launches;
   cudaStream_t user = ctx->stream;
   ctx->stream = ctx->cap_stream;
+  ctx->batch_override = sg.batch_dev;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
   romap_status st = ROMAP_OK;
@@ -1296,27 +1408,30 @@ static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, 
     st = enqueue_step(ctx, v);
     e = cudaStreamEndCapture(ctx->cap_stream, &graph);
   }
+  ctx->batch_override = nullptr;
   ctx->stream = user;
   for (size_t i = 0; i < v.size(); ++i) {
     ctx->objs[v[i]].steps_done = done[i];
     set_object_step(ctx->objs_host[v[i]], (uint32_t)(done[i] + 1), ctx->cfg.beta1, ctx->cfg.beta2);
   }
+  sg.launches = (int)(ctx->launches - saved_launches);
   ctx->stats = saved;
   ctx->launches = saved_launches;
   if (e == cudaSuccess && st == ROMAP_OK && graph) {
-    e = cudaGraphInstantiate(&ctx->step_graph, graph, 0);
-    if (e != cudaSuccess) ctx->step_graph = nullptr;
+    e = cudaGraphInstantiate(&sg.exec, graph, 0);
+    if (e != cudaSuccess) sg.exec = nullptr;
   }
   if (graph) cudaGraphDestroy(graph);
-  if (e != cudaSuccess || st != ROMAP_OK || !ctx->step_graph) {
+  if (e != cudaSuccess || st != ROMAP_OK || !sg.exec) {
     cudaGetLastError();
-    ctx->step_graph = nullptr;
+    free_graph(ctx, sg);
     ctx->graphs_enabled = false;  // fall back to eager launches for the rest of the context
     return ROMAP_OK;
   }
-  ctx->graph_key = key;
-  ctx->graph_batch = ctx->batch_key;
-  ctx->graph_ws_generation = ctx->ws_generation;
+  sg.last_use = ++ctx->graph_clock;
+  sg.ws_generation = ctx->ws_generation;
+  ctx->graph_captures += 1;
+  ctx->graphs.push_back(std::move(sg));
   return ROMAP_OK;
 }
 
@@ -1324,20 +1439,30 @@ namespace {
 
 // n_steps training steps of the validated batch v (CUDA-graph replay once captured), all enqueued on the stream
 romap_status run_train_steps(romap_ctx* ctx, const std::vector<int32_t>& v, int32_t n_steps) {
+  // size the workspace for this batch and for the largest single live object up front, so that alternating
+  // single-object compositions (the per-object path) do not move it and invalidate each other's graphs
+  {
+    std::vector<int32_t> rays;
+    for (int32_t id : v) rays.push_back(ctx->objs_host[id].n_rays);
+    ROMAP_TRY(ensure_step_workspace(ctx, rays));
+    int32_t largest = 0;
+    for (size_t i = 0; i < ctx->objs.size(); ++i)
+      if (ctx->objs[i].alive) largest = std::max(largest, ctx->objs_host[i].n_rays);
+    if (largest > 0) ROMAP_TRY(ensure_step_workspace(ctx, std::vector<int32_t>{largest}));
+  }
   // the graph key: the batch composition (object slots and their rays per step) and the precision
   std::vector<int32_t> key(v.begin(), v.end());
   for (int32_t id : v) key.push_back(ctx->objs_host[id].n_rays);
   key.push_back(ctx->cfg.precision);
   for (int s = 0; s < n_steps; ++s) {
     const bool use_graph = ctx->graphs_enabled && !ctx->profiling;
-    if (use_graph && ctx->step_graph && ctx->graph_key == key && ctx->graph_ws_generation == ctx->ws_generation) {
-      if (ctx->batch_key != ctx->graph_batch) {  // another call reused the batch buffer: restore the graph's arrays
-        CUDA_TRY(cudaMemcpyAsync(ctx->ws_batch.p, ctx->graph_batch.data(), sizeof(int32_t) * ctx->graph_batch.size(),
-                                 cudaMemcpyHostToDevice, ctx->stream));
-        ctx->batch_key = ctx->graph_batch;
-        ctx->batch_n = (int)v.size();
-      }
-      CUDA_TRY(cudaGraphLaunch(ctx->step_graph, ctx->stream));
+    romap_ctx::StepGraph* sg = use_graph ? find_graph(ctx, key) : nullptr;
+    if (sg) {
+      CUDA_TRY(cudaGraphLaunch(sg->exec, ctx->stream));
+      sg->last_use = ++ctx->graph_clock;
+      ctx->graph_replays += 1;
+      ctx->last_batch = sg->batch;
+      ctx->last_batch_n = sg->batch_n;
       // what enqueue_step does on the host for each step
       int64_t rays = 0;
       for (int32_t id : v) {
@@ -1347,12 +1472,24 @@ romap_status run_train_steps(romap_ctx* ctx, const std::vector<int32_t>& v, int3
       }
       ctx->stats.steps += (int64_t)v.size();
       ctx->stats.rays += rays;
-      ctx->launches += ctx->cfg.precision != ROMAP_PREC_FP32 ? 6 : 8;
+      ctx->launches += sg->launches;
       continue;
     }
     ROMAP_TRY(enqueue_step(ctx, v));
-    if (use_graph && (ctx->graph_key != key || !ctx->step_graph || ctx->graph_ws_generation != ctx->ws_generation))
-      ROMAP_TRY(capture_step(ctx, v, key));
+    if (use_graph) ROMAP_TRY(capture_step(ctx, v, key));
+  }
+  return ROMAP_OK;
+}
+
+// Steps of the listed objects: one batched launch sequence per step, or with per_object one sequence per object
+// (each object's steps back to back).  per_object: losses (5 floats per object) of each object's last step are
+// copied to dyn_host[k] on the stream as the object finishes, since every single-object step reuses dyn[0].
+romap_status run_listed_steps(romap_ctx* ctx, const std::vector<int32_t>& v, int32_t n_steps, bool gather_losses) {
+  if (!ctx->cfg.per_object) return run_train_steps(ctx, v, n_steps);
+  for (size_t k = 0; k < v.size(); ++k) {
+    ROMAP_TRY(run_train_steps(ctx, std::vector<int32_t>{v[k]}, n_steps));
+    if (gather_losses)
+      CUDA_TRY(cudaMemcpyAsync(ctx->dyn_gather + k, ctx->dyn, sizeof(BatchDyn), cudaMemcpyDeviceToDevice, ctx->stream));
   }
   return ROMAP_OK;
 }
@@ -1364,10 +1501,10 @@ romap_status romap_train_step(romap_ctx* ctx, const int32_t* ids, int32_t n_ids,
   if (n_steps < 1) return fail(ROMAP_ERR_INVALID_ARG, "n_steps must be >= 1");
   std::vector<int32_t> v;
   ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
-  ROMAP_TRY(run_train_steps(ctx, v, n_steps));
+  ROMAP_TRY(run_listed_steps(ctx, v, n_steps, out_loss != nullptr));
   if (out_loss) {
     std::vector<float> tmp(5 * (size_t)n_ids);
-    ROMAP_TRY(read_losses(ctx, n_ids, tmp.data(), 5, v));
+    ROMAP_TRY(read_losses(ctx, n_ids, tmp.data(), 5, v, ctx->cfg.per_object != 0));
     for (int i = 0; i < n_ids; ++i) out_loss[i] = tmp[5 * i];
   }
   return ROMAP_OK;
@@ -1379,7 +1516,7 @@ romap_status romap_train_step_async(romap_ctx* ctx, const int32_t* ids, int32_t 
   if (n_steps < 1) return fail(ROMAP_ERR_INVALID_ARG, "n_steps must be >= 1");
   std::vector<int32_t> v;
   ROMAP_TRY(validate_ids(ctx, ids, n_ids, &v));
-  ROMAP_TRY(run_train_steps(ctx, v, n_steps));
+  ROMAP_TRY(run_listed_steps(ctx, v, n_steps, out_loss != nullptr));
   if (out_loss) {  // L = loss sum / B on the device, then one asynchronous copy into the caller's buffer
     std::vector<int32_t> rays(v.size());
     for (size_t i = 0; i < v.size(); ++i) rays[i] = ctx->objs_host[v[i]].n_rays;
@@ -1388,7 +1525,7 @@ romap_status romap_train_step_async(romap_ctx* ctx, const int32_t* ids, int32_t 
     BatchDesc b;
     ROMAP_TRY(upload_batch(ctx, hb, &b));  // (the step left these arrays in place: no copy)
     ROMAP_TRY(grow(ctx, ctx->ws_loss, sizeof(float) * v.size()));
-    launch_final_losses(ctx->dyn, b, (float*)ctx->ws_loss.p, ctx->stream);
+    launch_final_losses(ctx->cfg.per_object ? ctx->dyn_gather : ctx->dyn, b, (float*)ctx->ws_loss.p, ctx->stream);
     ctx->launches += 1;
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(out_loss, ctx->ws_loss.p, sizeof(float) * v.size(), cudaMemcpyDefault, ctx->stream));
@@ -1403,8 +1540,7 @@ romap_status romap_check_device_status(romap_ctx* ctx) {
   CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (st == 0) return ROMAP_OK;
   CUDA_TRY(cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
-  if (st & kStatusTimeout) return fail(ROMAP_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
-  return fail(ROMAP_ERR_NONFINITE, "non-finite loss (status %d)", st);
+  return status_error(st);
 }
 
 // ---- incremental training data and budgeted training (Sec. V-A-1, Eq. 5; Sec. VI) ---------------------------------
@@ -1580,9 +1716,9 @@ romap_status romap_get_grad(romap_ctx* ctx, int32_t id, float* out, uint32_t fla
 romap_status romap_last_batch(romap_ctx* ctx, int32_t id, int64_t* pool_idx, float* bg, int64_t* out_n) {
   ROMAP_TRY(check_ctx(ctx));
   ROMAP_TRY(check_id(ctx, id));
-  const std::vector<int32_t>& k = ctx->batch_key;
+  const std::vector<int32_t>& k = ctx->last_batch;
   if (k.empty()) return fail(ROMAP_ERR_BAD_STATE, "no step has run");
-  const int n = ctx->batch_n;
+  const int n = ctx->last_batch_n;
   int pos = -1;
   for (int i = 0; i < n; ++i)
     if (k[i] == id) pos = i;
@@ -1601,9 +1737,9 @@ romap_status romap_last_batch(romap_ctx* ctx, int32_t id, int64_t* pool_idx, flo
 romap_status romap_last_outputs(romap_ctx* ctx, int32_t id, float* out, int64_t* out_n) {
   ROMAP_TRY(check_ctx(ctx));
   ROMAP_TRY(check_id(ctx, id));
-  const std::vector<int32_t>& k = ctx->batch_key;
+  const std::vector<int32_t>& k = ctx->last_batch;
   if (k.empty()) return fail(ROMAP_ERR_BAD_STATE, "no step has run");
-  const int n = ctx->batch_n;
+  const int n = ctx->last_batch_n;
   int pos = -1;
   for (int i = 0; i < n; ++i)
     if (k[i] == id) pos = i;
@@ -1650,7 +1786,10 @@ romap_status romap_set_state(romap_ctx* ctx, int32_t id, const romap_state* in) 
   CUDA_TRY(cudaMemcpyAsync(o.m, in->adam_m, bytes, k, ctx->stream));
   CUDA_TRY(cudaMemcpyAsync(o.v, in->adam_v, bytes, k, ctx->stream));
   CUDA_TRY(cudaMemsetAsync(o.grad, 0, sizeof(float) * ctx->g.n_params_pad, ctx->stream));
+  if (o.gfix) CUDA_TRY(cudaMemsetAsync(o.gfix, 0, sizeof(unsigned long long) * ctx->g.n_params_pad, ctx->stream));
   if (o.table_h) launch_to_half(o.params, o.table_h, ctx->g.n_hash, ctx->stream);
+  launch_touched_from_moments(ctx->g, o.m, o.v, o.touched, ctx->stream);  // the loaded moments decide
+  CUDA_TRY(cudaGetLastError());
   o.steps_done = in->step;
   ROMAP_TRY(sync_object(ctx, id));
   if (!(in->flags & ROMAP_DEVICE_PTR)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -1666,6 +1805,8 @@ romap_status romap_get_stats(romap_ctx* ctx, romap_stats* out) {
   *out = ctx->stats;
   out->live_samples = (int64_t)live;
   out->kernel_launches = ctx->launches;
+  out->graph_captures = ctx->graph_captures;
+  out->graph_replays = ctx->graph_replays;
   return ROMAP_OK;
 }
 
@@ -1709,6 +1850,22 @@ romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, i
   return ROMAP_OK;
 }
 
+romap_status romap_set_adam_skip(romap_ctx* ctx, int32_t on) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (on != 0 && on != 1) return fail(ROMAP_ERR_INVALID_ARG, "on must be 0 or 1");
+  ctx->g.adam_dense = on ? 0 : 1;
+  drop_graph(ctx);  // the captured steps carry the old setting
+  return ROMAP_OK;
+}
+
+romap_status romap_set_graphs(romap_ctx* ctx, int32_t on) {
+  ROMAP_TRY(check_ctx(ctx));
+  if (on != 0 && on != 1) return fail(ROMAP_ERR_INVALID_ARG, "on must be 0 or 1");
+  ctx->graphs_enabled = on != 0;
+  drop_graph(ctx);
+  return ROMAP_OK;
+}
+
 romap_status romap_set_profiling(romap_ctx* ctx, int32_t on) {
   ROMAP_TRY(check_ctx(ctx));
   ctx->profiling = on != 0;
@@ -1738,6 +1895,8 @@ romap_status romap_reset_stats(romap_ctx* ctx) {
   ROMAP_TRY(check_ctx(ctx));
   ctx->stats = romap_stats{};
   ctx->launches = 0;
+  ctx->graph_captures = 0;
+  ctx->graph_replays = 0;
   cudaStreamSynchronize(ctx->stream);
   for (auto& p : ctx->prof) {
     cudaEventDestroy(p.a);
@@ -1757,11 +1916,12 @@ romap_status romap_reset_stats(romap_ctx* ctx) {
 // rays, workspace carved from a caller buffer or the context.
 // ---------------------------------------------------------------------------
 struct FnLayout {
-  size_t rays, samples, blocks, batch, dyn, totals, total;
+  size_t rays, samples, blocks, batch, dyn, totals, act, total;
   int64_t nr, ns, nb;
 };
 
-static FnLayout fn_layout(const GridParams& g, int64_t n) {
+// store_act: room for the stored activations of every tile (ROMAP_STORE_ACT)
+static FnLayout fn_layout(const GridParams& g, int64_t n, bool store_act = false) {
   FnLayout L{};
   L.nr = n;
   L.ns = n * g.n_samples + kTile;
@@ -1774,7 +1934,9 @@ static FnLayout fn_layout(const GridParams& g, int64_t n) {
   L.batch = align_up(sizeof(int32_t) * (4 + L.nb + 8), 256);
   L.dyn = align_up(sizeof(BatchDyn), 256);
   L.totals = 256;
-  L.total = L.rays + L.samples + L.blocks + L.batch + L.dyn + L.totals + 256;
+  const int64_t tiles = (L.ns + kTile - 1) / kTile;  // one object: its samples start at tile 0
+  L.act = store_act ? align_up(sizeof(float) * (size_t)tiles * act_rows_for(g.LF) * kTile, 256) : 0;
+  L.total = L.rays + L.samples + L.blocks + L.batch + L.dyn + L.totals + L.act + 256;
   return L;
 }
 
@@ -1796,7 +1958,8 @@ static FnView fn_view(char* base, const FnLayout& L) {
   v.blocks = (uint32_t*)(base + o); o += L.blocks;
   v.batch = (int32_t*)(base + o); o += L.batch;
   v.dyn = (BatchDyn*)(base + o); o += L.dyn;
-  v.totals = (int32_t*)(base + o);
+  v.totals = (int32_t*)(base + o); o += L.totals;
+  v.S.act = L.act ? (float*)(base + o) : nullptr;
   return v;
 }
 
@@ -1806,10 +1969,10 @@ static romap_status fn_setup(romap_ctx* ctx, const float* params, float* grad, c
                              BatchDesc* out_b, bool upload) {
   if (!params || !half || !origin || !dir || !bg || !ws) return fail(ROMAP_ERR_INVALID_ARG, "NULL argument");
   if (n < 1 || n > (int64_t)1 << 24) return fail(ROMAP_ERR_INVALID_ARG, "n must be in 1..2^24");
-  if (flags & ~(ROMAP_JITTER)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  if (flags & ~(ROMAP_JITTER | ROMAP_STORE_ACT)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
   for (int a = 0; a < 3; ++a)
     if (!(half[a] > 0.f)) return fail(ROMAP_ERR_INVALID_ARG, "half_size must be positive");
-  FnLayout L = fn_layout(ctx->g, n);
+  FnLayout L = fn_layout(ctx->g, n, (flags & ROMAP_STORE_ACT) != 0);
   if (ws_bytes < L.total) return fail(ROMAP_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes, L.total);
   FnView v = fn_view(ws, L);
   HostBatch hb;
@@ -1843,10 +2006,11 @@ static romap_status fn_setup(romap_ctx* ctx, const float* params, float* grad, c
   return ROMAP_OK;
 }
 
-romap_status romap_fn_workspace_size(romap_ctx* ctx, int64_t n, size_t* bytes) {
+romap_status romap_fn_workspace_size(romap_ctx* ctx, int64_t n, uint32_t flags, size_t* bytes) {
   if (!ctx || !bytes) return fail(ROMAP_ERR_INVALID_ARG, "NULL argument");
-  if (n < 1) return fail(ROMAP_ERR_INVALID_ARG, "n must be >= 1");
-  *bytes = fn_layout(ctx->g, n).total;
+  if (n < 1 || n > (int64_t)1 << 24) return fail(ROMAP_ERR_INVALID_ARG, "n must be in 1..2^24");
+  if (flags & ~(ROMAP_JITTER | ROMAP_STORE_ACT)) return fail(ROMAP_ERR_INVALID_ARG, "bad flags");
+  *bytes = fn_layout(ctx->g, n, (flags & ROMAP_STORE_ACT) != 0).total;
   return ROMAP_OK;
 }
 
@@ -1887,8 +2051,10 @@ romap_status romap_fn_backward(romap_ctx* ctx, const float* params, const float 
   ROMAP_TRY(fn_setup(ctx, params, grad_params, half_size, seed, step, occupancy, origin, dir, bg, n, flags,
                      (char*)workspace, ws_bytes, &v, &b, false));
   v.R.gout = grad_ray;
-  launch_composite(2, ctx->g, b, v.R, v.S, v.dyn, nullptr, ctx->stream);
-  launch_tile_mlp(1, ctx->g, b, v.dyn, v.totals, v.R, v.S, tile_ctas(ctx), ctx->stream);
+  GridParams g = ctx->g;
+  g.det = 0;  // the caller's gradient buffer is FP32: floating-point atomics
+  launch_composite(2, g, b, v.R, v.S, v.dyn, nullptr, ctx->stream);
+  launch_tile_mlp(1, g, b, v.dyn, v.totals, v.R, v.S, tile_ctas(ctx), ctx->stream);
   ctx->launches += 2;
   if (out_dsigma) {
     CUDA_TRY(cudaMemsetAsync(out_dsigma, 0, sizeof(float) * n * ctx->g.n_samples, ctx->stream));

@@ -57,7 +57,20 @@ struct GridParams {
   int f16;                 // mixed path: MLP operands in FP16 instead of BF16 (backward gradient operands scaled by B)
   int single_net;          // colour logits = density-net outputs 1..3; the colour net is skipped
   int extra;               // single-network hidden layers after the first (0..2), 64x64 each
+  int det;                 // FP32 path: gradients and losses accumulated in 64-bit fixed point (bit-reproducible)
+  int adam_dense;          // 1: Adam updates every chunk (no skip of never-touched chunks; same results)
 };
+
+// Deterministic accumulation (the `deterministic` configuration): every gradient contribution is rounded once to a
+// 64-bit fixed-point integer with kFixBits fractional bits and added with an integer atomic.  Integer addition is
+// associative, so a sum has the same bits whatever order its atomics land in.  Range per accumulator +-2^(63 -
+// kFixBits); a single contribution beyond +-kFixMaxContribution (or NaN) is not added and sets a status bit.
+constexpr int kFixBits = 46;
+constexpr float kFixMaxContribution = 1024.0f;
+constexpr int kFixLossBits = 32;   // per-object loss sums (B L and its four components): range +-2^31
+constexpr float kFixLossMaxContribution = 1048576.0f;  // per ray
+// Adam skips chunks of kAdamChunk parameters that were never touched (see k_adam).
+constexpr int kAdamChunk = 256;
 
 // One live object as the kernels see it (device-resident, indexed by slot).
 struct ObjectDev {
@@ -81,6 +94,9 @@ struct ObjectDev {
   uint32_t step;           // Adam step about to run (1-based); advanced after the Adam kernel
   float bc1, bc2;          // Adam bias corrections of that step: 1 / (1 - beta1^step), 1 / (1 - beta2^step)
   int32_t pad_;
+  unsigned long long* gfix; // deterministic mode: fixed-point gradient accumulator [n_params_pad], else null
+  uint8_t* touched;        // per chunk of kAdamChunk parameters: 1 once any gradient entry was non-zero (or null:
+                           // every chunk counts as touched)
 };
 
 // Adam bias corrections of step t (Kingma & Ba, Algorithm 1), evaluated in FP64 and rounded once to FP32.
@@ -102,6 +118,8 @@ struct BatchDyn {
   int32_t pad_;
   float loss[5];           // B*L, then rgb, rr, depth, density sums (unscaled)
   float pad2_[3];
+  unsigned long long loss_fix[5];  // deterministic mode: the same sums in fixed point (kFixLossBits)
+  int64_t pad3_;
 };
 
 // Tile plan of the mixed-precision path.  A ray with c > 0 live samples belongs to class k (1..kPlanClasses-1), the
@@ -145,6 +163,7 @@ struct BatchDesc {
   int32_t* plan_perm;        // [n_rays] ray indices in tile order (rays with live samples only)
   int4* plan_tiles;          // [max tiles] {batch entry, slots per ray P, rays in the tile, first perm index}
   int32_t* plan_npairs;      // [1] number of tile pairs
+  int32_t* status;           // device status word (deterministic accumulation range), or null
 };
 
 // Per-step ray records (structure of arrays, capacity R).
@@ -177,6 +196,7 @@ struct SampleBuf {
   float* rgb;      // [3S]
   float* dsigma;   // [S] dL/dsigma including the direct density term
   float* drgb;     // [3S]
+  float* act;      // stored activations [tiles][act_rows][128] (functional API, ROMAP_STORE_ACT), or null
 };
 
 // ---------------------------------------------------------------------------
@@ -236,6 +256,12 @@ void launch_tile_mlp(int mode, const GridParams& g, const BatchDesc& b, const Ba
 void launch_composite(int mode, const GridParams& g, const BatchDesc& b, RayBuf r, SampleBuf s, BatchDyn* dyn,
                       int32_t* status, cudaStream_t stream);
 void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream);
+// Deterministic mode, after the backward: adds each object's fixed-point gradient into its FP32 gradient (entries
+// with a zero accumulator are left alone), zeroes the accumulator, and converts the fixed-point loss sums.
+void launch_fix_finish(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, cudaStream_t stream);
+// Sets each chunk's Adam touched flag from its moments (1 where any m or v entry is non-zero): after a state load.
+void launch_touched_from_moments(const GridParams& g, const float* m, const float* v, uint8_t* touched,
+                                 cudaStream_t stream);
 void launch_final_losses(const BatchDyn* dyn, const BatchDesc& b, float* out, cudaStream_t stream);
 void launch_scatter_slots(const GridParams& g, int64_t n_rays, const RayBuf r, const SampleBuf s, const float* src,
                           int src_stride, float* dst, int dst_stride, cudaStream_t stream);
@@ -244,6 +270,9 @@ void launch_sample_slots(const GridParams& g, int64_t n_rays, const RayBuf r, co
 void launch_split_outputs(const float* ray_out, int64_t n, float* rgb, float* depth, float* opacity,
                           cudaStream_t stream);
 int tile_kernel_smem_bytes(int LF);
+// Rows of one tile's stored activations (ROMAP_STORE_ACT): encoding (L F padded to 16 or 32), the density hidden
+// layer, the 16 density-net outputs and the two colour hidden layers (or the single-network hidden layers 2, 3).
+int act_rows_for(int LF);
 // Mixed precision: fused forward + compositing + backward on tensor cores; P slots per ray (power of two <= 128).
 // Marching cubes: at most kMcMaxTri triangles per cube; the case table is built by construction (mc_table.cu).
 constexpr int kMcMaxTri = 5;
@@ -283,7 +312,7 @@ inline void set_smem_attr(K* kernel, int bytes, std::atomic<uint64_t>& done) {
 }
 
 // status word bits written by the kernels
-constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2;
+constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2, kStatusFixRange = 4;
 void launch_selftest_wait(int32_t* status, int limit, cudaStream_t stream);
 
 }  // namespace romap

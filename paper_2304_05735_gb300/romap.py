@@ -28,6 +28,7 @@ ROMAP_OBJECT_FRAME = 0x2
 ROMAP_REPLACE = 0x4
 ROMAP_JITTER = 0x8
 ROMAP_ASYNC_HOST = 0x10
+ROMAP_STORE_ACT = 0x20
 
 ROMAP_CLS_OBJECT, ROMAP_CLS_BACKGROUND, ROMAP_CLS_OCCLUDER = 0, 1, 2
 ROMAP_PREC_FP32, ROMAP_PREC_MIXED_BF16, ROMAP_PREC_MIXED_FP8, ROMAP_PREC_MIXED_FP16 = 0, 1, 2, 3
@@ -46,7 +47,8 @@ class romap_config(C.Structure):
         ("bg_random", C.c_int32), ("bg_const", C.c_float * 3),
         ("precision", C.c_int32), ("max_objects", C.c_int32), ("max_rays_per_object", C.c_int64),
         ("accuracy_mode", C.c_int32), ("single_net", C.c_int32),
-        ("hidden_layers", C.c_int32), ("reserved", C.c_int32),
+        ("hidden_layers", C.c_int32), ("deterministic", C.c_int32), ("per_object", C.c_int32),
+        ("reserved", C.c_int32),
         ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN), ("alloc_user", C.c_void_p),
     ]
 
@@ -75,7 +77,7 @@ class romap_state(C.Structure):
 
 class romap_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rays", C.c_int64), ("live_samples", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("graph_captures", C.c_int64), ("graph_replays", C.c_int64)]
 
 
 _vp, _i32, _i64, _u32, _u64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_size_t
@@ -114,7 +116,7 @@ SIGNATURES = {
     "romap_render": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _u32]),
     "romap_get_state": (_i32, [_vp, _i32, _P(romap_state)]),
     "romap_set_state": (_i32, [_vp, _i32, _P(romap_state)]),
-    "romap_fn_workspace_size": (_i32, [_vp, _i64, _P(_sz)]),
+    "romap_fn_workspace_size": (_i32, [_vp, _i64, _u32, _P(_sz)]),
     "romap_fn_forward": (_i32, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _i64, _u32, _vp, _sz, _vp, _vp]),
     "romap_fn_backward": (_i32, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _i64, _u32, _vp, _sz, _vp, _vp,
                                  _vp]),
@@ -126,7 +128,10 @@ SIGNATURES = {
     "romap_set_tile_kernel": (_i32, [_vp, _i32]),
     "romap_autotune_report": (_i32, [_vp, _P(_i32), _vp, _i32, C.c_char_p, _sz]),
     "romap_set_profiling": (_i32, [_vp, _i32]),
+    "romap_set_adam_skip": (_i32, [_vp, _i32]),
+    "romap_set_graphs": (_i32, [_vp, _i32]),
     "romap_phase_times": (_i32, [_vp, _vp, _vp]),
+    "romap_measure_request_rates": (_i32, [_vp, _vp]),
 }
 ROMAP_N_PHASES = 5
 PHASES = ("sampling", "mlp_forward", "composite_loss_adjoint", "mlp_backward_scatter", "adam")
@@ -191,7 +196,7 @@ def make_config(n_levels=8, log2_table_size=12, base_resolution=16, growth=1.5, 
                 rays_per_step=256, dir_dims=3, lambda1=0.5, lambda2=0.01, lr=1e-2, beta1=0.9, beta2=0.99,
                 eps=1e-15, bg_random=False, bg_const=(1.0, 1.0, 1.0), precision=ROMAP_PREC_FP32, max_objects=64,
                 max_rays_per_object=1 << 24, alloc=None, dealloc=None, accuracy_mode=0,
-                single_net=False, hidden_layers=1):
+                single_net=False, hidden_layers=1, deterministic=False, per_object=False):
     c = romap_config()
     c.n_levels, c.n_features, c.log2_table_size = n_levels, 2, log2_table_size
     c.base_resolution, c.growth, c.max_resolution = base_resolution, growth, max_resolution
@@ -204,6 +209,7 @@ def make_config(n_levels=8, log2_table_size=12, base_resolution=16, growth=1.5, 
     c.precision, c.max_objects, c.max_rays_per_object = precision, max_objects, max_rays_per_object
     c.accuracy_mode, c.single_net = int(accuracy_mode), 1 if single_net else 0
     c.hidden_layers, c.reserved = int(hidden_layers), 0
+    c.deterministic, c.per_object = int(bool(deterministic)), int(bool(per_object))
     if alloc is not None:
         c.alloc, c.dealloc = ALLOC_FN(alloc), DEALLOC_FN(dealloc)
     return c

@@ -107,29 +107,33 @@ class Ctx:
         return idx, bg
 
     # functional API on torch device tensors
-    def fn_forward(self, params, half, seed, step, o, d, bg, jitter=True, occ=None, want_samples=False):
+    def fn_forward(self, params, half, seed, step, o, d, bg, jitter=True, occ=None, want_samples=False,
+                   store_act=False):
         torch = self.torch
         n = o.shape[0]
         ws_bytes = C.c_size_t()
-        R.check(R.romap_fn_workspace_size(self.h, n, C.byref(ws_bytes)), "romap_fn_workspace_size")
+        flags = (R.ROMAP_JITTER if jitter else 0) | (R.ROMAP_STORE_ACT if store_act else 0)
+        R.check(R.romap_fn_workspace_size(self.h, n, flags, C.byref(ws_bytes)), "romap_fn_workspace_size")
         ws = torch.empty(ws_bytes.value + 256, dtype=torch.uint8, device="cuda")
         out = torch.empty(n, 6, dtype=torch.float32, device="cuda")
         samples = torch.empty(n, self.rc.n_samples, 6, device="cuda") if want_samples else None
         halfa = (C.c_float * 3)(*half)
         R.check(R.romap_fn_forward(self.h, params.data_ptr(), halfa, seed, step, R.ptr(occ), o.data_ptr(),
-                                   d.data_ptr(), bg.data_ptr(), n, R.ROMAP_JITTER if jitter else 0, ws.data_ptr(),
+                                   d.data_ptr(), bg.data_ptr(), n, flags, ws.data_ptr(),
                                    ws.numel(), out.data_ptr(), R.ptr(samples)), "romap_fn_forward")
         return out, samples, ws
 
-    def fn_backward(self, params, half, seed, step, o, d, bg, ws, grad_ray, jitter=True, occ=None):
+    def fn_backward(self, params, half, seed, step, o, d, bg, ws, grad_ray, jitter=True, occ=None, store_act=False):
         torch = self.torch
         n = o.shape[0]
         g = torch.zeros(self.n_params, dtype=torch.float32, device="cuda")
         ds = torch.empty(n, self.rc.n_samples, device="cuda")
         halfa = (C.c_float * 3)(*half)
         R.check(R.romap_fn_backward(self.h, params.data_ptr(), halfa, seed, step, R.ptr(occ), o.data_ptr(),
-                                    d.data_ptr(), bg.data_ptr(), n, R.ROMAP_JITTER if jitter else 0, ws.data_ptr(),
-                                    ws.numel(), grad_ray.data_ptr(), g.data_ptr(), ds.data_ptr()), "romap_fn_backward")
+                                    d.data_ptr(), bg.data_ptr(), n,
+                                    (R.ROMAP_JITTER if jitter else 0) | (R.ROMAP_STORE_ACT if store_act else 0),
+                                    ws.data_ptr(), ws.numel(), grad_ray.data_ptr(), g.data_ptr(), ds.data_ptr()),
+                "romap_fn_backward")
         return g, ds
 
 

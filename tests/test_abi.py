@@ -52,7 +52,8 @@ def test_status_strings_and_null_arguments():
     ("precision", 7, R.ROMAP_ERR_INVALID_ARG), ("max_objects", 0, R.ROMAP_ERR_INVALID_ARG),
     ("accuracy_mode", 2, R.ROMAP_ERR_INVALID_ARG), ("single_net", 2, R.ROMAP_ERR_INVALID_ARG),
     ("hidden_layers", 4, R.ROMAP_ERR_INVALID_ARG), ("hidden_layers", 2, R.ROMAP_ERR_UNSUPPORTED),
-    ("reserved", 1, R.ROMAP_ERR_INVALID_ARG),
+    ("reserved", 1, R.ROMAP_ERR_INVALID_ARG), ("deterministic", 2, R.ROMAP_ERR_INVALID_ARG),
+    ("per_object", -1, R.ROMAP_ERR_INVALID_ARG),
 ])
 def test_config_validation_is_host_side(field, value, status):
     cfg = R.make_config()
@@ -68,6 +69,15 @@ def test_single_net_is_not_combined_with_fp8():
     lay = R.romap_layout()
     assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == R.ROMAP_ERR_UNSUPPORTED
     cfg = R.make_config(precision=R.ROMAP_PREC_MIXED_BF16, single_net=True)
+    assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == R.ROMAP_OK
+
+
+def test_deterministic_mode_is_fp32_only():
+    lay = R.romap_layout()
+    for prec in (R.ROMAP_PREC_MIXED_BF16, R.ROMAP_PREC_MIXED_FP16, R.ROMAP_PREC_MIXED_FP8):
+        cfg = R.make_config(precision=prec, deterministic=True)
+        assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == R.ROMAP_ERR_UNSUPPORTED
+    cfg = R.make_config(deterministic=True, per_object=True)
     assert R.romap_param_layout(C.byref(cfg), C.byref(lay)) == R.ROMAP_OK
 
 
