@@ -425,9 +425,9 @@ def run_ours(args):
     autotune = None
     if main_prec != "fp32":
         chosen = C.c_int32()
-        tms = (C.c_float * 4)()
-        names = C.create_string_buffer(256)
-        R.check(R.romap_autotune_report(h, C.byref(chosen), tms, 4, names, 256))
+        tms = (C.c_float * 8)()
+        names = C.create_string_buffer(1024)
+        R.check(R.romap_autotune_report(h, C.byref(chosen), tms, 8, names, 1024))
         cands = names.value.decode().split(";")
         autotune = {"chosen": cands[chosen.value] if chosen.value >= 0 else None,
                     "ms_per_launch": {c: float(tms[i]) for i, c in enumerate(cands)}}

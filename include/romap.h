@@ -466,9 +466,10 @@ ROMAP_API romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_
  * giving every CTA a contiguous range of the tile plan; 2 and 3 = the same
  * kernels with the plan interleaved over the CTAs (CTA c takes every
  * grid-th pair or tile from c, so all CTAs work on the same few objects at
- * a time).  ROMAP_ERR_UNSUPPORTED for the warp-specialized candidates (1, 3)
- * under ROMAP_PREC_MIXED_FP8 or single_net (both run on the lockstep
- * kernel). */
+ * a time); 4, 5 and 6, 7 = interleaved in chunks of 2 and 4 consecutive
+ * pairs or tiles (longer runs of one object per CTA).  Odd indices are the
+ * warp-specialized kernel: ROMAP_ERR_UNSUPPORTED for them under
+ * ROMAP_PREC_MIXED_FP8 or single_net (both run on the lockstep kernel). */
 ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);
 ROMAP_API romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, int32_t n, char* names,
                                              size_t names_len);

@@ -186,8 +186,8 @@ __device__ inline RayCtx ray_of_thread(const BatchDesc& b) {
 // background is u01 of Philox(step, s, BG, 0) words 0..2 when random.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, RayBuf R, uint32_t* block_sums) {
-  __shared__ uint32_t s_cls[kPlanClasses];
-  if (b.plan && threadIdx.x < kPlanClasses) s_cls[threadIdx.x] = 0u;
+  __shared__ uint32_t s_cnt[kPlanCounts];
+  if (b.plan && threadIdx.x < kPlanCounts) s_cnt[threadIdx.x] = 0u;
   RayCtx c = ray_of_thread(b);
   const ObjectDev& ob = b.objs[b.slot[c.bi]];
   uint32_t count = 0;
@@ -265,11 +265,16 @@ __global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, Ra
     R.obj[c.r] = c.bi;
     if (b.plan) *reinterpret_cast<uint4*>(R.mask + 4 * c.r) = make_uint4(m0, m1, m2, m3);
   }
-  if (b.plan) {  // rays of each plan class in this block
+  if (b.plan) {  // rays of each live count in this block, added to the entry's histogram; the block's offset within
+                 // each count is the histogram value it found (the order of the blocks within a count is arbitrary)
     __syncthreads();
-    if (c.valid) atomicAdd(&s_cls[plan_class(count)], 1u);
+    if (c.valid) atomicAdd(&s_cnt[count], 1u);
     __syncthreads();
-    if (threadIdx.x < kPlanClasses) b.plan_bcls[blockIdx.x * kPlanClasses + threadIdx.x] = s_cls[threadIdx.x];
+    if (threadIdx.x < kPlanCounts) {
+      const uint32_t v = s_cnt[threadIdx.x];
+      b.plan_bcnt[blockIdx.x * kPlanCounts + threadIdx.x] =
+          v ? atomicAdd(&b.plan_hist[(size_t)c.bi * kPlanCounts + threadIdx.x], v) : 0u;
+    }
   }
   uint32_t total;
   uint32_t excl = block_excl_scan256(count, &total);
@@ -289,46 +294,138 @@ void launch_ray_setup(const GridParams& g, const BatchDesc& b, RayBuf r, uint32_
 // ---------------------------------------------------------------------------
 constexpr int kMaxBatch = 1024;
 
-// Tile plan (mixed-precision path), run by the single block of k_scan: per batch entry (one warp each), the class
-// counts of its ray blocks become block offsets within the entry's class, the classes get consecutive ranges of
-// plan_perm (class 1 first) and consecutive tiles; entries get consecutive, even tile ranges; then every tile record
-// {entry, P, rays, first perm index} is written and the pair count stored.  s_tiles and s_wsum are scratch.
+// Largest c <= lim whose bit is set in the 160-bit mask m (bit c of word c / 32), or -1.
+__device__ __forceinline__ int highest_set_at_most(const uint32_t m[5], int lim) {
+  if (lim < 0) return -1;
+  int q = lim >> 5;
+  const int bit = lim & 31;
+  uint32_t x = m[q] & (bit == 31 ? 0xffffffffu : ((2u << bit) - 1u));
+  while (x == 0u && q > 0) x = m[--q];
+  return x ? 32 * q + 31 - __clz(x) : -1;
+}
+
+// Tile plan (mixed-precision path), run by the single block of k_scan.  Per batch entry (one warp each): the block
+// offsets of every live count within the entry (in place in plan_bcnt) and the count histogram; then the patterns
+// (greedy over the histogram, see kPlanMaxCount) with their segments.  The warp computes every pattern in lockstep
+// (all lanes read the same shared values); lane 0 writes the records.  Then the entries' even tile counts are
+// scanned into first tiles and every tile record is written.  s_tiles and s_wsum are scratch.
+// Tile patterns of one batch entry (one warp per block, one block per entry): the entry's count histogram (then
+// reset for the next step), the greedy patterns (see kPlanMaxCount) and their segments.  The warp computes every
+// pattern in lockstep (all lanes read the same shared values); lane 0 writes the records.  The entry's even tile count
+// goes to plan_ent for the scan that follows.
+__global__ void __launch_bounds__(32) k_plan_patterns(BatchDesc b) {
+  __shared__ int hh[kPlanCounts];    // rays of each count not placed yet
+  __shared__ int cons[kPlanCounts];  // rays of each count placed so far (the next segment's first rank)
+  __shared__ uint8_t ic[kPlanMaxCount], ia[kPlanMaxCount];  // the pattern being built: counts, copies
+  __shared__ uint8_t ns[kPlanCounts];  // segments of each count
+  const int lane = threadIdx.x, i = blockIdx.x;
+  for (int c = lane; c < kPlanCounts; c += 32) {
+    uint32_t* h = b.plan_hist + (size_t)i * kPlanCounts + c;
+    hh[c] = (int)*h;
+    *h = 0u;
+    cons[c] = 0;
+    ns[c] = 0;
+  }
+  __syncwarp();
+  int4* pat = b.plan_pat + (size_t)i * kPlanMaxPat * 2;
+  int4* seg = b.plan_seg + (size_t)i * kPlanCounts * kPlanSegsPerCount * 2;
+  int npat = 0, T = 0, PB = 0;
+  bool fallback = false;
+  for (;;) {
+    uint32_t m[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int c = 32 * q + lane;
+      m[q] = __ballot_sync(0xffffffffu, c >= 1 && c < kPlanCounts && hh[c] > 0);
+    }
+    if (!(m[0] | m[1] | m[2] | m[3] | m[4])) break;
+    if (npat >= kPlanMaxPat - kPlanCounts - 1) {
+      fallback = true;
+      break;
+    }
+    // one pattern: the largest remaining count opens the tile, then the largest counts that still fit
+    int rem = kTile, lim = kPlanMaxCount, ni = 0, nrays = 0;
+    for (;;) {
+      const int c = highest_set_at_most(m, rem < lim ? rem : lim);
+      if (c <= 0) break;
+      const int a = hh[c] < rem / c ? hh[c] : rem / c;
+      if (lane == 0) {
+        ic[ni] = (uint8_t)c;
+        ia[ni] = (uint8_t)a;
+      }
+      ++ni;
+      nrays += a;
+      rem -= a * c;
+      lim = c - 1;
+    }
+    __syncwarp();
+    int rep = 0x7fffffff;
+    bool seg_full = false;
+    for (int q = 0; q < ni; ++q) {
+      const int c = ic[q], a = ia[q];
+      rep = min(rep, hh[c] / a);
+      seg_full = seg_full || ns[c] >= kPlanSegsPerCount - 1;  // keep one segment per count for the fallback
+    }
+    if (seg_full) {
+      fallback = true;
+      break;
+    }
+    if (lane == 0) {
+      pat[2 * npat] = make_int4(T, rep, nrays, PB);
+      pat[2 * npat + 1] = make_int4(rep * nrays, kTile - rem, 0, 0);
+      int slot_off = 0, perm_off = 0;
+      for (int q = 0; q < ni; ++q) {
+        const int c = ic[q], a = ia[q];
+        int4* sg = seg + ((size_t)c * kPlanSegsPerCount + ns[c]) * 2;
+        sg[0] = make_int4(cons[c], T, a, rep);
+        sg[1] = make_int4(slot_off, perm_off, nrays, PB);
+        ns[c] += 1;
+        cons[c] += rep * a;
+        hh[c] -= rep * a;
+        slot_off += a * c;
+        perm_off += a;
+      }
+    }
+    __syncwarp();
+    T += rep;
+    PB += rep * nrays;
+    ++npat;
+  }
+  if (fallback) {  // every count left in tiles of its own: floor(128 / c) rays of count c per tile
+    for (int c = kPlanMaxCount; c >= 1; --c) {
+      const int rays = hh[c];
+      if (rays <= 0) continue;
+      const int a = kTile / c, tiles = (rays + a - 1) / a;
+      if (lane == 0) {
+        pat[2 * npat] = make_int4(T, tiles, a, PB);
+        pat[2 * npat + 1] = make_int4(rays, a * c, c, 0);
+        int4* sg = seg + ((size_t)c * kPlanSegsPerCount + ns[c]) * 2;
+        sg[0] = make_int4(cons[c], T, a, tiles);
+        sg[1] = make_int4(0, 0, a, PB);
+        ns[c] += 1;
+        cons[c] += rays;
+        hh[c] = 0;
+      }
+      __syncwarp();
+      T += tiles;
+      PB += rays;
+      ++npat;
+    }
+  }
+  __syncwarp();
+  for (int c = lane; c < kPlanCounts; c += 32) b.plan_nseg[(size_t)i * kPlanCounts + c] = ns[c];
+  if (lane == 0) {
+    b.plan_npat[i] = npat;
+    b.plan_ent[i] = (T + 1) & ~1;  // even: a pair never mixes entries (the scan turns it into the first tile)
+  }
+}
+
+// Tile plan (mixed-precision path), run by the single block of k_scan after k_plan_patterns: the entries' even tile
+// counts are scanned into first tiles and every tile record is written.  s_tiles and s_wsum are scratch.
 __device__ void plan_tiles_of_batch(const BatchDesc& b, uint32_t* s_tiles, uint32_t* s_wsum) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
-  for (int i = w; i < b.n; i += 32) {
-    const int bb = b.block_base[i], nb = b.block_base[i + 1] - bb;
-    int32_t* po = b.plan_obj + i * 3 * kPlanClasses;
-    int perm_base = 0, tile_base = 0;
-    for (int k = 0; k < kPlanClasses; ++k) {
-      uint32_t carry = 0;
-      for (int c = 0; c < nb; c += 32) {
-        uint32_t* p = b.plan_bcls + (size_t)(bb + c + lane) * kPlanClasses + k;
-        const uint32_t v = (c + lane < nb) ? *p : 0u;
-        uint32_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += n;
-        }
-        if (c + lane < nb) *p = carry + incl - v;
-        carry += __shfl_sync(0xffffffffu, incl, 31);
-      }
-      const int rays_k = (int)carry;
-      const int per = plan_rays_per_tile(k);
-      const int tiles_k = k == 0 ? 0 : (rays_k + per - 1) / per;
-      if (lane == 0) {
-        po[k] = k == 0 ? 0 : perm_base;
-        po[kPlanClasses + k] = tile_base;
-        po[2 * kPlanClasses + k] = rays_k;
-      }
-      if (k > 0) {
-        perm_base += rays_k;
-        tile_base += tiles_k;
-      }
-    }
-    if (lane == 0) s_tiles[i] = (uint32_t)((tile_base + 1) & ~1);  // even: a pair never mixes entries
-  }
+  if (threadIdx.x < (unsigned)b.n) s_tiles[threadIdx.x] = (uint32_t)b.plan_ent[threadIdx.x];
   __syncthreads();
   // exclusive scan of the entries' tile counts
   const uint32_t v = threadIdx.x < (unsigned)b.n ? s_tiles[threadIdx.x] : 0u;
@@ -346,23 +443,33 @@ __device__ void plan_tiles_of_batch(const BatchDesc& b, uint32_t* s_tiles, uint3
     all += s_wsum[k];
   }
   __syncthreads();
-  if (threadIdx.x < (unsigned)b.n) s_tiles[threadIdx.x] = base + incl - v;  // first tile of entry i
+  if (threadIdx.x < (unsigned)b.n) {
+    s_tiles[threadIdx.x] = base + incl - v;  // first tile of entry i
+    b.plan_ent[threadIdx.x] = (int32_t)(base + incl - v);
+  }
   if (threadIdx.x == 0) b.plan_npairs[0] = (int32_t)(all / 2);
   __syncthreads();
   for (int i = w; i < b.n; i += 32) {
-    const int32_t* po = b.plan_obj + i * 3 * kPlanClasses;
+    const int4* pat = b.plan_pat + (size_t)i * kPlanMaxPat * 2;
+    const int npat = b.plan_npat[i];
     const int t0 = (int)s_tiles[i];
     const int nt = (int)((i + 1 < b.n ? s_tiles[i + 1] : all) - s_tiles[i]);
     for (int t = lane; t < nt; t += 32) {
-      // the class whose tiles cover t: the highest one that starts at or before t (a class that starts at t with no
-      // tiles is never followed by one that starts at t too, except past the last class: the padding tile)
-      int k = kPlanClasses - 1;
-      while (k > 1 && po[kPlanClasses + k] > t) --k;
-      int4 rec = make_int4(i, kTile, 0, b.ray_base[i]);  // padding tile: no rays
-      const int per = plan_rays_per_tile(k);
-      const int q = t - po[kPlanClasses + k];
-      const int left = po[2 * kPlanClasses + k] - q * per;
-      if (q >= 0 && left > 0) rec = make_int4(i, plan_slots(k), left < per ? left : per, b.ray_base[i] + po[k] + q * per);
+      int lo = 0, hi = npat - 1, p = -1;  // the last pattern whose first tile is at or before t
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pat[2 * mid].x <= t) { p = mid; lo = mid + 1; } else { hi = mid - 1; }
+      }
+      int4 rec = make_int4(i, t0 + t, 0, b.ray_base[i]);  // padding tile: no rays, no used slots
+      if (p >= 0) {
+        const int4 P0 = pat[2 * p], P1 = pat[2 * p + 1];
+        const int q = t - P0.x;
+        if (q < P0.y) {
+          const int nr = min(P0.z, P1.x - q * P0.z);
+          const int used = P1.z > 0 ? nr * P1.z : P1.y;
+          rec = make_int4(i, t0 + t, nr | (used << 8), b.ray_base[i] + P0.w + q * P0.z);
+        }
+      }
       b.plan_tiles[t0 + t] = rec;
     }
   }
@@ -445,6 +552,11 @@ __global__ void __launch_bounds__(1024) k_scan(BatchDesc b, uint32_t* block_sums
     if (live_counter) atomicAdd(live_counter, (unsigned long long)tot);
   }
   if (b.plan) plan_tiles_of_batch(b, s_tiles, s_wsum);
+}
+
+void launch_plan_patterns(const BatchDesc& b, cudaStream_t stream) {
+  if (b.n <= 0) return;
+  k_plan_patterns<<<b.n, 32, 0, stream>>>(b);
 }
 
 void launch_scan(const GridParams&, const BatchDesc& b, uint32_t* block_sums, BatchDyn* dyn, int32_t* totals,

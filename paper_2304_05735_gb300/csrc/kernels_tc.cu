@@ -7,33 +7,44 @@ namespace romap {
 namespace {
 using namespace tc;
 
-// Places every ray of the batch in the tile plan: rays with live samples go to their class's position in
-// plan_perm (stable: class base of the entry + offset of the ray block within the entry + rank in the block); rays
-// without live samples add their loss here (C_hat = background, D_hat = 0) and write their outputs.
+// Places every ray of the batch in the tile plan.  A ray with c > 0 live samples has rank j among its entry's rays of
+// count c (offset of its ray block for count c + rank within the block, in ray order); the segments of count c
+// (in rank order) give its pattern, tile and copy; the ray goes to its position in plan_perm with its first slot in
+// plan_rstart, and its slots' {ray, sample index} go to plan_slot.  Rays without live samples add their loss here
+// (C_hat = background, D_hat = 0) and write their outputs.
 __global__ void __launch_bounds__(256) k_plan_rays(GridParams g, BatchDesc b, RayBuf R, BatchDyn* dyn) {
-  __shared__ uint32_t s_wcnt[8][kPlanClasses];
+  __shared__ uint32_t s_wcnt[8][kPlanCounts];  // rays of each count per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int bi = b.block_obj[blockIdx.x];
   const int rl = (blockIdx.x - b.block_base[bi]) * 256 + threadIdx.x;
   const int n_obj = b.ray_base[bi + 1] - b.ray_base[bi];
   const bool valid = rl < n_obj;
   const int64_t r = b.ray_base[bi] + rl;
-  const int cls = valid ? plan_class(R.count[r]) : -1;
-  uint32_t rank = 0;
-#pragma unroll
-  for (int k = 0; k < kPlanClasses; ++k) {
-    const uint32_t m = __ballot_sync(0xffffffffu, cls == k);
-    if (cls == k) rank = __popc(m & ((1u << lane) - 1u));
-    if (lane == 0) s_wcnt[warp][k] = __popc(m);
-  }
+  const int c = valid ? (int)R.count[r] : -1;
+  for (int k = threadIdx.x; k < 8 * kPlanCounts; k += blockDim.x) (&s_wcnt[0][0])[k] = 0u;
   __syncthreads();
-  if (cls > 0) {
+  const uint32_t same = __match_any_sync(0xffffffffu, c);
+  const uint32_t rank = __popc(same & ((1u << lane) - 1u));
+  if (c > 0 && rank == 0) s_wcnt[warp][c] = __popc(same);
+  __syncthreads();
+  if (c > 0) {
     uint32_t before = 0;
-    for (int w = 0; w < warp; ++w) before += s_wcnt[w][cls];
-    const int pos = b.plan_obj[bi * 3 * kPlanClasses + cls] + (int)b.plan_bcls[blockIdx.x * kPlanClasses + cls] +
-                    (int)(before + rank);
-    b.plan_perm[b.ray_base[bi] + pos] = (int32_t)r;
-  } else if (cls == 0) {
+    for (int w = 0; w < warp; ++w) before += s_wcnt[w][c];
+    const int j = (int)(b.plan_bcnt[blockIdx.x * kPlanCounts + c] + before + rank);
+    const int nseg = b.plan_nseg[(size_t)bi * kPlanCounts + c];
+    const int4* sg = b.plan_seg + ((size_t)bi * kPlanCounts + c) * kPlanSegsPerCount * 2;
+    int k = 0;
+    while (k + 1 < nseg && j >= sg[2 * k].x + sg[2 * k].z * sg[2 * k].w) ++k;
+    const int4 s0 = sg[2 * k], s1 = sg[2 * k + 1];
+    const int q = j - s0.x, tt = q / s0.z, cp = q - tt * s0.z;
+    const int64_t tile = (int64_t)b.plan_ent[bi] + s0.y + tt;
+    const int pos = b.ray_base[bi] + s1.w + tt * s1.z + s1.y + cp;
+    const int start = s1.x + cp * c;
+    b.plan_perm[pos] = (int32_t)r;
+    b.plan_rstart[pos] = start;
+    int2* slot = b.plan_slot + tile * kTile + start;
+    for (int i = 0; i < c; ++i) slot[i] = make_int2((int)r, i);
+  } else if (c == 0) {
     const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
     float* o = R.out + 6 * r;
     o[0] = bg0; o[1] = bg1; o[2] = bg2; o[3] = 0.f; o[4] = 0.f; o[5] = 0.f;

@@ -43,7 +43,7 @@ struct WsSlot {
   int valid[kT];
   int ray[kT];            // global ray index of the slot (-1 outside the tile's rays)
   __align__(16) float dE[kT][LFP + 4];  // dL/dencoding staged for the scatter (padded rows: float4 access)
-  int P, nrays, bi;       // slots per ray, rays and batch entry of the tile
+  int pfirst, nrays, bi;  // first plan_perm index, rays and batch entry of the tile
 };
 
 template <int LFP>
@@ -96,8 +96,8 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
 // memory warps: scatter the tile that left a slot, then gather the next tile into it
 // ---------------------------------------------------------------------------------------------------------------
 template <int LFP, bool F16>
-__device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, const RayBuf& R, int tile_lo,
-                            int tile_step, int n) {
+__device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, const RayBuf& R,
+                            const WorkOrder& wo, int n) {
   const int s = threadIdx.x - kCompute;
   constexpr int LMAX = LFP / 2;
   constexpr bool f16 = F16;
@@ -111,7 +111,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
         break;
       }
       if (sl.valid[s]) {
-        const ObjectDev* ob = &b.objs[b.slot[b.plan_tiles[tile_lo + (k - 2) * tile_step].x]];
+        const ObjectDev* ob = &b.objs[b.slot[b.plan_tiles[wo.item(k - 2)].x]];
         const float p[3] = {sl.px[0][s], sl.px[1][s], sl.px[2][s]};
         float2* gt = reinterpret_cast<float2*>(ob->grad);
         float de[LFP];
@@ -131,12 +131,12 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
       }
     }
     if (k < n) {
-      const int4 ti = b.plan_tiles[tile_lo + k * tile_step];
+      const int4 ti = b.plan_tiles[wo.item(k)];
       const ObjectDev* ob = &b.objs[b.slot[ti.x]];
       const SlotSample q = plan_sample(g, b, R, ob, ti.x, ti, s);
       if (s == 0) {
-        sl.P = ti.y;
-        sl.nrays = ti.z;
+        sl.pfirst = ti.w;
+        sl.nrays = ti.z & 255;
         sl.bi = ti.x;
       }
       sl.ray[s] = q.ray;
@@ -164,7 +164,7 @@ __device__ void memory_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDes
 // ---------------------------------------------------------------------------------------------------------------
 template <int LFP, bool F16>
 __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf R,
-                             int32_t* status, int tile_lo, int tile_step, int n, uint32_t& phase, bool& pending) {
+                             int32_t* status, int n, uint32_t& phase, bool& pending) {
   const int s = threadIdx.x, warp = s >> 5;
   const uint32_t tm = sm.tmem_base;
   // FP16 operands: gradient operands scaled by the object's batch size B, FP32 results unscaled (as the lockstep
@@ -288,9 +288,12 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     bar_compute();
     // ---- compositing, losses, adjoint: one warp per ray ----
     {
-      const int P = sl.P, nr = sl.nrays;
-      for (int j = warp; j < nr; j += kCompute / 32)
-        composite_ray(sl, g, b, R, dyn, bi, (int64_t)sl.ray[j * P], j * P, P, invB, status);
+      const int nr = sl.nrays;
+      for (int j = warp; j < nr; j += kCompute / 32) {
+        const int pi = sl.pfirst + j;
+        const int64_t r = b.plan_perm[pi];
+        composite_ray(sl, g, b, R, dyn, bi, r, b.plan_rstart[pi], (int)R.count[r], invB, status);
+      }
     }
     bar_compute();
     // ---- backward ----
@@ -406,11 +409,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   WsSmem<LFP>& sm = *reinterpret_cast<WsSmem<LFP>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int total_tiles = 2 * *b.plan_npairs;
-  // tiles of this CTA: a contiguous range of the plan, or (interleave) every gridDim.x-th tile from blockIdx.x
-  const int tile_lo = interleave ? (int)blockIdx.x : (int)((int64_t)total_tiles * blockIdx.x / gridDim.x);
-  const int tile_hi = interleave ? total_tiles : (int)((int64_t)total_tiles * (blockIdx.x + 1) / gridDim.x);
-  const int tile_step = interleave ? (int)gridDim.x : 1;
-  const int n = tile_hi > tile_lo ? (tile_hi - tile_lo + tile_step - 1) / tile_step : 0;
+  // tiles of this CTA: a contiguous range of the plan, or chunks of `interleave` tiles dealt round-robin (WorkOrder)
+  const WorkOrder wo(total_tiles, (int)gridDim.x, (int)blockIdx.x, interleave);
+  const int n = wo.count();
   if (n <= 0) return;
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mma_bar)));
@@ -432,8 +433,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   tc_after();
   uint32_t phase = 0;
   bool pending = false;
-  if (warp < 4) compute_role<LFP, F16>(sm, g, b, dyn, R, status, tile_lo, tile_step, n, phase, pending);
-  else memory_role<LFP, F16>(sm, g, b, R, tile_lo, tile_step, n);
+  if (warp < 4) compute_role<LFP, F16>(sm, g, b, dyn, R, status, n, phase, pending);
+  else memory_role<LFP, F16>(sm, g, b, R, wo, n);
   if (t == 0 && sm.fail) {
     if (status) atomicOr(status, 2);
     if (pending) mbar_wait(&sm.mma_bar, phase ^ 1u);  // bounded: let MMAs in flight finish before freeing TMEM

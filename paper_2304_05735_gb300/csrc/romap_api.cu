@@ -103,9 +103,16 @@ struct romap_ctx {
   // tile plan of the mixed-precision path (capacities: rays, ray blocks, batch entries, tiles)
   int64_t cap_plan[4] = {0, 0, 0, 0};
   struct PlanView {
-    uint32_t* bcls = nullptr;
-    int32_t* obj = nullptr;
+    uint32_t* hist = nullptr;
+    uint32_t* bcnt = nullptr;
+    int4* pat = nullptr;
+    int32_t* npat = nullptr;
+    int4* seg = nullptr;
+    int32_t* nseg = nullptr;
+    int32_t* ent = nullptr;
     int32_t* perm = nullptr;
+    int32_t* rstart = nullptr;
+    int2* slot = nullptr;
     int4* tiles = nullptr;
     int32_t* npairs = nullptr;
   } plan;
@@ -129,7 +136,7 @@ struct romap_ctx {
   int64_t launches = 0;
   // autotuned choice of the mixed-precision tile kernel: -1 until tuned, then an index of kTileKernels
   int tile_kernel = -1;
-  float tile_kernel_ms[4] = {0, 0, 0, 0};
+  float tile_kernel_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   // CUDA graphs of one training step, one per batch composition (captured on cap_stream, replayed on stream), least
   // recently used first out beyond kMaxStepGraphs
   struct StepGraph {
@@ -246,9 +253,16 @@ size_t carve_plan(char* base, const int64_t cap[4], romap_ctx::PlanView* P) {
     o = align_up(o + bytes, 256);
     return p;
   };
-  P->bcls = (uint32_t*)take(sizeof(uint32_t) * kPlanClasses * cap[1]);
-  P->obj = (int32_t*)take(sizeof(int32_t) * 3 * kPlanClasses * cap[2]);
+  P->hist = (uint32_t*)take(sizeof(uint32_t) * kPlanCounts * cap[2]);
+  P->bcnt = (uint32_t*)take(sizeof(uint32_t) * kPlanCounts * cap[1]);
+  P->pat = (int4*)take(sizeof(int4) * 2 * kPlanMaxPat * cap[2]);
+  P->npat = (int32_t*)take(sizeof(int32_t) * cap[2]);
+  P->seg = (int4*)take(sizeof(int4) * 2 * kPlanSegsPerCount * kPlanCounts * cap[2]);
+  P->nseg = (int32_t*)take(sizeof(int32_t) * kPlanCounts * cap[2]);
+  P->ent = (int32_t*)take(sizeof(int32_t) * cap[2]);
   P->perm = (int32_t*)take(sizeof(int32_t) * cap[0]);
+  P->rstart = (int32_t*)take(sizeof(int32_t) * cap[0]);
+  P->slot = (int2*)take(sizeof(int2) * kTile * cap[3]);
   P->tiles = (int4*)take(sizeof(int4) * cap[3]);
   P->npairs = (int32_t*)take(sizeof(int32_t));
   return o;
@@ -268,6 +282,8 @@ romap_status ensure_plan(romap_ctx* ctx, int64_t nr, int64_t nblocks, int64_t nb
   ROMAP_TRY(grow(ctx, ctx->ws_plan, carve_plan(nullptr, cap, &pv)));
   carve_plan((char*)ctx->ws_plan.p, cap, &ctx->plan);
   for (int k = 0; k < 4; ++k) ctx->cap_plan[k] = cap[k];
+  // the count histograms start at zero; each step's pattern kernel resets the entries it read
+  CUDA_TRY(cudaMemsetAsync(ctx->plan.hist, 0, sizeof(uint32_t) * kPlanCounts * cap[2], ctx->stream));
   ctx->ws_generation += 1;
   return ROMAP_OK;
 }
@@ -571,8 +587,9 @@ romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBu
 int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
 
 // Candidate fused tile kernels of the mixed path (same results, different schedules): the two kernels, each with
-// contiguous per-CTA ranges of the tile plan or with the plan interleaved over the CTAs.  Even indices are the
-// lockstep kernel, the only one with the FP8 and single-network variants.
+// contiguous per-CTA ranges of the tile plan or with the plan dealt round-robin over the CTAs in chunks of 1, 2 or 4
+// work items (tile pairs of the lockstep kernel, tiles of the warp-specialized one).  Even indices are the lockstep
+// kernel, the only one with the FP8 and single-network variants.
 typedef void (*TileKernelFn)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int,
                              cudaStream_t);
 template <void (*F)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int, int, cudaStream_t),
@@ -582,10 +599,14 @@ void launch_tile_order(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, R
   F(g, b, dyn, r, status, max_tiles, n_ctas, IL, stream);
 }
 const TileKernelFn kTileKernels[] = {launch_tile_order<launch_tile_tc, 0>, launch_tile_order<launch_tile_ws, 0>,
-                                     launch_tile_order<launch_tile_tc, 1>, launch_tile_order<launch_tile_ws, 1>};
+                                     launch_tile_order<launch_tile_tc, 1>, launch_tile_order<launch_tile_ws, 1>,
+                                     launch_tile_order<launch_tile_tc, 2>, launch_tile_order<launch_tile_ws, 2>,
+                                     launch_tile_order<launch_tile_tc, 4>, launch_tile_order<launch_tile_ws, 4>};
 const char* const kTileKernelNames[] = {"lockstep tile pairs", "warp-specialized", "lockstep tile pairs, interleaved",
-                                        "warp-specialized, interleaved"};
-constexpr int kNumTileKernels = 4;
+                                        "warp-specialized, interleaved", "lockstep tile pairs, interleaved by 2",
+                                        "warp-specialized, interleaved by 2", "lockstep tile pairs, interleaved by 4",
+                                        "warp-specialized, interleaved by 4"};
+constexpr int kNumTileKernels = 8;
 bool lockstep_kernel(int k) { return k % 2 == 0; }
 
 // Sampling stage of the mixed path: ray draw + slab + live counts and masks, the per-object scan (live-sample
@@ -593,11 +614,12 @@ bool lockstep_kernel(int k) { return k % 2 == 0; }
 // fused kernel from the masks, so no sample records are written.
 romap_status run_sampling_mixed(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBuf S, uint32_t* block_sums,
                                 BatchDyn* dyn, int32_t* totals) {
-  PhaseScope ps(ctx, 0, 3);
+  PhaseScope ps(ctx, 0, 4);
   launch_ray_setup(ctx->g, b, R, block_sums, ctx->stream);
+  launch_plan_patterns(b, ctx->stream);
   launch_scan(ctx->g, b, block_sums, dyn, totals, S, ctx->live_counter, ctx->stream);
   launch_plan_rays(ctx->g, b, R, dyn, ctx->stream);
-  ctx->launches += 3;
+  ctx->launches += 4;
   CUDA_TRY(cudaGetLastError());
   return ROMAP_OK;
 }
@@ -643,7 +665,8 @@ romap_status autotune_tile_kernel(romap_ctx* ctx, const std::vector<int32_t>& id
 }
 
 // tile plan bound: per entry at most one partly filled tile per class plus the even padding
-int64_t plan_max_tiles(const HostBatch& hb) { return (int64_t)hb.n_rays + (int64_t)(kPlanClasses + 1) * hb.n; }
+// (every tile of the plan holds at least one ray, and each entry adds at most one padding tile)
+int64_t plan_max_tiles(const HostBatch& hb) { return (int64_t)hb.n_rays + 2 * (int64_t)hb.n; }
 
 // Grows the step workspace (and the tile plan of the mixed path) to hold one step of a batch with these rays per
 // entry.
@@ -676,9 +699,16 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
   ctx->last_batch_n = hb.n;
   if (mixed) {
     b.plan = 1;
-    b.plan_bcls = ctx->plan.bcls;
-    b.plan_obj = ctx->plan.obj;
+    b.plan_hist = ctx->plan.hist;
+    b.plan_bcnt = ctx->plan.bcnt;
+    b.plan_pat = ctx->plan.pat;
+    b.plan_npat = ctx->plan.npat;
+    b.plan_seg = ctx->plan.seg;
+    b.plan_nseg = ctx->plan.nseg;
+    b.plan_ent = ctx->plan.ent;
     b.plan_perm = ctx->plan.perm;
+    b.plan_rstart = ctx->plan.rstart;
+    b.plan_slot = ctx->plan.slot;
     b.plan_tiles = ctx->plan.tiles;
     b.plan_npairs = ctx->plan.npairs;
     SampleBuf none{};

@@ -122,22 +122,25 @@ struct BatchDyn {
   int64_t pad3_;
 };
 
-// Tile plan of the mixed-precision path.  A ray with c > 0 live samples belongs to class k (1..kPlanClasses-1), the
-// largest one whose slot count P_k = 128 / kPlanRays[k] (floor) is >= c; a tile holds up to kPlanRays[k] rays of one
-// class and one object, P_k slots each, and the ray's live samples fill the first c slots of its range.  Class 0
-// holds the rays without live samples, which only add their loss (Eq. 7-11 with C_hat = background).  Every object's
-// tile count is rounded up to even so that a pair of tiles never mixes objects.
-constexpr int kPlanClasses = 10;
-__host__ __device__ constexpr int plan_rays_per_tile(int k) {
-  return k <= 0 ? 0 : (k <= 8 ? k : 16);
-}
-__host__ __device__ constexpr int plan_slots(int k) { return k <= 0 ? 0 : kTile / plan_rays_per_tile(k); }
-__host__ __device__ inline int plan_class(uint32_t live) {
-  if (live == 0) return 0;
-  int k = kPlanClasses - 1;
-  while (k > 1 && (uint32_t)plan_slots(k) < live) --k;
-  return k;
-}
+// Tile plan of the mixed-precision path: whole rays packed into tiles of kTile sample slots, each ray's live samples
+// in consecutive slots, the rays of a tile one after another from slot 0.  Rays are grouped by their exact live count
+// c (1..kPlanMaxCount); per object, tile *patterns* are formed greedily from the count histogram (first fit
+// decreasing over the histogram: the largest remaining count opens a tile, then the largest counts that still fit
+// fill it, as many copies of each as fit) and every pattern is repeated as often as its counts allow.  Each pattern
+// repetition exhausts the rarest of its counts relative to its multiplicity, so the histogram empties in a bounded
+// number of patterns; past kPlanMaxPat - kPlanMaxCount - 1 patterns or kPlanSegsPerCount segments of one count, the
+// remaining rays of each count go into single-count tiles of floor(128 / c) rays.  Rays with c = 0 take no slot.
+constexpr int kPlanMaxCount = 128;           // N <= 128 candidates per ray in the mixed path
+constexpr int kPlanCounts = kPlanMaxCount + 1;
+constexpr int kPlanMaxPat = 512;             // patterns per object
+constexpr int kPlanSegsPerCount = 32;        // patterns one count may appear in
+// Per pattern (two int4): {first tile (object-relative), tiles, rays per full tile, first perm index
+// (object-relative)} and {rays, used slots of a full tile, the count of a single-count pattern (else 0), 0}; the last
+// tile of a single-count pattern may hold fewer rays.
+// Per segment (count c in pattern p, two int4): {first rank among the object's rays of count c, first tile, copies
+// per tile a, tiles} and {slot of the first copy in a tile, its position in the tile's ray list, rays per full
+// tile, first perm index of the pattern}.
+// Tile record (int4): {batch entry, tile index, rays | used slots << 8, first perm index}.
 
 // Batch description (device): object slots and the ray/block prefix sums.
 struct BatchDesc {
@@ -158,10 +161,17 @@ struct BatchDesc {
   ObjectDev* objs;           // device array indexed by slot
   // tile plan (mixed-precision path only; plan == 0 elsewhere)
   int32_t plan;
-  uint32_t* plan_bcls;       // [n_blocks * kPlanClasses] rays of each class per ray block, then offsets in the entry
-  int32_t* plan_obj;         // [n * 3 * kPlanClasses] per entry and class: first perm index, first tile, rays
+  uint32_t* plan_hist;       // [n * kPlanCounts] rays of each live count per entry (zero between steps)
+  uint32_t* plan_bcnt;       // [n_blocks * kPlanCounts] each ray block's offset within each live count of its entry
+  int4* plan_pat;            // [n * kPlanMaxPat * 2] patterns of each entry (two int4 each)
+  int32_t* plan_npat;        // [n] patterns of each entry
+  int4* plan_seg;            // [n * kPlanCounts * kPlanSegsPerCount * 2] segments of each entry and count
+  int32_t* plan_nseg;        // [n * kPlanCounts] segments of each entry and count
+  int32_t* plan_ent;         // [n] first tile of each entry
   int32_t* plan_perm;        // [n_rays] ray indices in tile order (rays with live samples only)
-  int4* plan_tiles;          // [max tiles] {batch entry, slots per ray P, rays in the tile, first perm index}
+  int32_t* plan_rstart;      // [n_rays] first slot (in its tile) of the ray at each perm position
+  int2* plan_slot;           // [max tiles * kTile] {ray, live-sample index} of each used slot
+  int4* plan_tiles;          // [max tiles] tile records
   int32_t* plan_npairs;      // [1] number of tile pairs
   int32_t* status;           // device status word (deterministic accumulation range), or null
 };
@@ -286,6 +296,8 @@ int launch_mc(const GridParams& g, const ObjectDev* objs, int slot, float iso, c
 void launch_occ_update(const GridParams& g, const ObjectDev* objs, int slot, float decay, float threshold, int reset,
                        float* dens, uint64_t* bits, cudaStream_t stream);
 void launch_plan_rays(const GridParams& g, const BatchDesc& b, RayBuf r, BatchDyn* dyn, cudaStream_t stream);
+// Tile patterns of every batch entry (after the ray setup, before the scan writes the tile records).
+void launch_plan_patterns(const BatchDesc& b, cudaStream_t stream);
 // interleave: CTA c takes every n_ctas-th tile pair (tile) from c instead of a contiguous range, so that all CTAs
 // work on the same few objects at a time (their tables and gradients then stay in L2).
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,

@@ -388,6 +388,26 @@ __device__ __forceinline__ void gather_levels(const GridParams& g, const ObjectD
 }
 
 // The sample of one slot: candidate i of ray rl of the object (same FP32 operations as the sampling kernels).
+// Work items (tile pairs, or tiles) of CTA c of a grid: a contiguous range of the plan (chunk = 0), or chunks of
+// `chunk` consecutive items dealt round-robin over the CTAs (CTA c takes items [c chunk, c chunk + chunk), then
+// [(c + grid) chunk, ...)), so that all CTAs work on the same few objects at a time and those objects' tables and
+// gradients stay in L2; larger chunks give each CTA longer runs of one object (fewer weight reloads and
+// weight-gradient flushes).
+struct WorkOrder {
+  int total, grid, c, chunk, lo, hi;
+  __device__ WorkOrder(int total_, int grid_, int c_, int chunk_) : total(total_), grid(grid_), c(c_), chunk(chunk_) {
+    lo = chunk ? 0 : (int)((int64_t)total * c / grid);
+    hi = chunk ? 0 : (int)((int64_t)total * (c + 1) / grid);
+  }
+  __device__ int count() const {
+    if (!chunk) return hi - lo;
+    const int round = grid * chunk, full = total / round, rem = total - full * round;
+    const int extra = rem - c * chunk;
+    return full * chunk + (extra < 0 ? 0 : (extra > chunk ? chunk : extra));
+  }
+  __device__ int item(int it) const { return chunk ? (it / chunk) * grid * chunk + c * chunk + it % chunk : lo + it; }
+};
+
 struct SlotSample {
   float x, y, z, t, dt;
   int valid;
@@ -409,17 +429,17 @@ __device__ __forceinline__ int nth_set_bit(uint32_t x, int j) {
   return pos;
 }
 
-// The sample of slot s of a planned tile (see kPlanClasses): ray jr = s / P of the tile, its (s % P)-th live
-// candidate i, found in the ray's live-candidate mask; same FP32 operations as the sampling kernels.
+// The sample of slot s of a planned tile (see kPlanMaxCount): the slot table gives its ray and the index j of its
+// live sample; the j-th live candidate i is found in the ray's live-candidate mask; same FP32 operations as the
+// sampling kernels.  Slots past the tile's used ones hold no sample.
 __device__ __forceinline__ SlotSample plan_sample(const GridParams& g, const BatchDesc& b, const RayBuf& R,
                                                   const ObjectDev* ob, int bi, int4 tile, int s) {
   SlotSample q{0.f, 0.f, 0.f, 0.f, 0.f, 0, -1};
-  const int P = tile.y;
-  const int jr = s / P;
-  if (jr >= tile.z) return q;
-  const int r = b.plan_perm[tile.w + jr];
+  if (s >= (tile.z >> 8)) return q;
+  const int2 e = b.plan_slot[(int64_t)tile.y * kTile + s];
+  const int r = e.x;
   q.ray = r;
-  int j = s - jr * P;
+  int j = e.y;
   if ((uint32_t)j >= R.count[r]) return q;
   int i = 0;
 #pragma unroll 1

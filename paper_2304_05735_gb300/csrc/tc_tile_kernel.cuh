@@ -66,7 +66,7 @@ struct TileBufs {
   float drgb[3][kT];
   int valid[kT];
   int ray[kT];  // global ray index of the slot (-1 outside the tile's rays)
-  int P, nrays; // slots per ray and rays of the tile
+  int pfirst, nrays;  // first plan_perm index and number of the tile's rays
   // dL/dencoding of the slots, feature-major (thread s owns column s), in H2's space: H2 is dead from the end of the
   // backward until the next pair's forward writes it
   __device__ float* dEs(int k) { return reinterpret_cast<float*>(H2) + k * kT; }
@@ -277,13 +277,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // the FP32 results unscaled
   constexpr bool f16 = F16;
   auto unscale_of = [&](int bi_) { return f16 ? 1.0f / (float)(b.ray_base[bi_ + 1] - b.ray_base[bi_]) : 1.0f; };
-  // pairs of this CTA: a contiguous range of the plan, or (interleave) every gridDim.x-th pair from blockIdx.x, so
-  // that all CTAs work on the same few objects at a time and those objects' tables and gradients stay in L2
-  const int total_pairs = *b.plan_npairs;
-  const int pair_lo = interleave ? (int)blockIdx.x : (int)((int64_t)total_pairs * blockIdx.x / gridDim.x);
-  const int pair_hi = interleave ? total_pairs : (int)((int64_t)total_pairs * (blockIdx.x + 1) / gridDim.x);
-  const int pair_step = interleave ? (int)gridDim.x : 1;
-  if (pair_lo >= pair_hi) return;
+  // pairs of this CTA: a contiguous range of the plan, or chunks of `interleave` pairs dealt round-robin (WorkOrder)
+  const WorkOrder wo(*b.plan_npairs, (int)gridDim.x, (int)blockIdx.x, interleave);
+  const int n_items = wo.count();
+  if (n_items <= 0) return;
 
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar)));
@@ -327,7 +324,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr int LMAX = LFP / 2;
   // the sample and encoding of the next pair are computed ahead, mostly while the backward GEMMs of the current
   // pair run, and kept in registers until the current pair no longer reads the tile buffers
-  int4 nx_ti = b.plan_tiles[pair_lo * kTilesPerCta + wg];  // both tiles of a pair belong to the same object
+  int4 nx_ti = b.plan_tiles[wo.item(0) * kTilesPerCta + wg];  // both tiles of a pair belong to the same object
   int nx_bi = nx_ti.x;
   const ObjectDev* nx_ob = &b.objs[b.slot[nx_bi]];
   SlotSample nx = plan_sample(g, b, R, nx_ob, nx_bi, nx_ti, s);
@@ -349,13 +346,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     zero_rows<LFP>(tb.E[0], s, 0, Lg);
   }
-  for (int pair = pair_lo; pair < pair_hi && ok; pair += pair_step) {
+  for (int it = 0; it < n_items && ok; ++it) {
     // ---- 1-2. the prepared sample and encoding of this pair -> tile buffers ---------------------------------------
     tb.valid[s] = nx.valid;
     tb.ray[s] = nx.ray;
     if (s == 0) {
-      tb.P = nx_ti.y;
-      tb.nrays = nx_ti.z;
+      tb.pfirst = nx_ti.w;
+      tb.nrays = nx_ti.z & 255;
     }
     tb.px[0][s] = nx.x; tb.px[1][s] = nx.y; tb.px[2][s] = nx.z;
     tb.t[s] = nx.t;
@@ -372,9 +369,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
     const float invB = 1.0f / (float)n_rays_obj;
     const float gscale = f16 ? (float)n_rays_obj : 1.0f, gunscale = f16 ? invB : 1.0f;
-    const bool has_next = pair + pair_step < pair_hi;
+    const bool has_next = it + 1 < n_items;
     if (has_next) {
-      nx_ti = b.plan_tiles[(pair + pair_step) * kTilesPerCta + wg];
+      nx_ti = b.plan_tiles[wo.item(it + 1) * kTilesPerCta + wg];
       nx_bi = nx_ti.x;
       nx_ob = &b.objs[b.slot[nx_bi]];
     }
@@ -514,8 +511,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int nr0 = sm.tb[0].nrays, nr_all = nr0 + sm.tb[1].nrays;
       for (int j = warp; j < nr_all; j += kTcThreads / 32) {
         const int u = j < nr0 ? 0 : 1, jr = j < nr0 ? j : j - nr0;
-        const int Pu = sm.tb[u].P;
-        composite_ray(sm.tb[u], g, b, R, dyn, bi, (int64_t)sm.tb[u].ray[jr * Pu], jr * Pu, Pu, invB, status);
+        const int pi = sm.tb[u].pfirst + jr;
+        const int64_t r = b.plan_perm[pi];
+        composite_ray(sm.tb[u], g, b, R, dyn, bi, r, b.plan_rstart[pi], (int)R.count[r], invB, status);
       }
     }
     __syncthreads();

@@ -69,7 +69,7 @@ def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
 
 
 @pytest.mark.parametrize("prec", [MIXED, F16])
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
+@pytest.mark.parametrize("kernel", list(range(8)))
 def test_mixed_batched_equals_separate(torch, kernel, prec):
     oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, n_samples=32, rays_per_step=700, bg_random=True,
                            precision=prec)
@@ -86,7 +86,7 @@ def test_mixed_batched_equals_separate(torch, kernel, prec):
         gb = [ctx.grad(i) for i in ids]
         ctx2 = Ctx(rc)
         try:
-            R.check(R.romap_set_tile_kernel(ctx2.h, (kernel + 1) % 4))  # another candidate, one object at a time
+            R.check(R.romap_set_tile_kernel(ctx2.h, (kernel + 1) % 8))  # another candidate, one object at a time
             for k, sc in enumerate(scenes):
                 oid = ctx2.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=333 + 100 * k)
                 ctx2.add_rays(oid, sc.pool)
@@ -132,16 +132,16 @@ def test_autotuner_picks_a_measured_candidate(torch):
         oid = ctx.create(seed=0)
         ctx.add_rays(oid, sc.pool)
         chosen = R.C.c_int32()
-        ms = (R.C.c_float * 4)()
-        names = R.C.create_string_buffer(256)
-        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 4, names, 256))
+        ms = (R.C.c_float * 8)()
+        names = R.C.create_string_buffer(1024)
+        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 8, names, 1024))
         assert chosen.value == -1
         ctx.train([oid], n_steps=2)
-        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 4, names, 256))
+        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 8, names, 1024))
         cands = names.value.decode().split(";")
         print(f"\nautotuner: {dict(zip(cands, list(ms)[:len(cands)]))} -> {cands[chosen.value]}")
-        assert len(cands) == 4 and 0 <= chosen.value < 4
-        assert all(ms[i] > 0 for i in range(4)) and ms[chosen.value] == min(ms)
+        assert len(cands) == 8 and 0 <= chosen.value < 8
+        assert all(ms[i] > 0 for i in range(8)) and ms[chosen.value] == min(ms)
     finally:
         ctx.close()
 
