@@ -55,6 +55,7 @@ typedef int32_t romap_status;
 #define ROMAP_ERR_TIMEOUT (-7)     /* a bounded device wait gave up */
 #define ROMAP_ERR_BAD_STATE (-8)   /* call not valid in the object's state */
 #define ROMAP_ERR_UNSUPPORTED (-9) /* configuration not built */
+#define ROMAP_ERR_BOUNDS (-10)     /* libromap_checked.so: a device index failed its bounds check */
 
 /* flags */
 #define ROMAP_DEVICE_PTR 0x1u   /* pointers are device pointers */
@@ -487,6 +488,23 @@ ROMAP_API romap_status romap_set_adam_skip(romap_ctx* ctx, int32_t on);
  * graph capture or replay; drops the cached graphs); on = 1 (the default):
  * the first step of a composition is captured and later ones replayed. */
 ROMAP_API romap_status romap_set_graphs(romap_ctx* ctx, int32_t on);
+
+/* ---- bounds-checked build ------------------------------------------------
+ * libromap_checked.so is this library compiled with ROMAP_CHECKED: every
+ * device index into a ray pool, a hash table level, the ray and sample
+ * records and the tile plan is checked against its logical size; a failed
+ * check records the violation in the context's status word and the kernel
+ * uses a safe in-range index (or skips the write) instead, never a trap.
+ * Calls that report device status (loss reads, romap_check_device_status)
+ * then return ROMAP_ERR_BOUNDS.  The unchecked library compiles the checks
+ * away.  romap_checked_build tells which one is loaded (*out = 1 checked). */
+ROMAP_API romap_status romap_checked_build(int32_t* out);
+/* Test hook for the bounds checks: sets the object's pool size as the
+ * kernels see it to n (0..its pool size), leaving its rays per step and its
+ * pool as they are, so that the next step's ray draw indexes past the
+ * logical pool while staying inside the allocated one.  Drops the captured
+ * step graphs. */
+ROMAP_API romap_status romap_debug_set_pool_size(romap_ctx* ctx, int32_t id, int64_t n);
 ROMAP_API romap_status romap_phase_times(romap_ctx* ctx, double* ms, int64_t* launches);
 
 /* Measurement utility (no counterpart in the paper): the request rates that

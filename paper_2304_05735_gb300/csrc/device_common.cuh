@@ -161,7 +161,10 @@ __device__ __forceinline__ uint32_t corner_index(const GridParams& g, int l, con
   const uint32_t cx = (uint32_t)(i0[0] + (k & 1));
   const uint32_t cy = (uint32_t)(i0[1] + ((k >> 1) & 1));
   const uint32_t cz = (uint32_t)(i0[2] + ((k >> 2) & 1));
-  return g.dense[l] ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) & (g.T - 1u));
+  const uint32_t idx =
+      g.dense[l] ? (cx + cy * n1 + cz * n1 * n1) : (((cx * 1u) ^ (cy * 2654435761u) ^ (cz * 805459861u)) & (g.T - 1u));
+  if (!ROMAP_IN_BOUNDS(idx < (g.dense[l] ? n1 * n1 * n1 : g.T), g.status)) return 0u;
+  return idx;
 }
 // Trilinear weight of corner k for the fractions f.
 __device__ __forceinline__ float corner_weight(const float f[3], int k) {

@@ -40,6 +40,10 @@ __global__ void __launch_bounds__(256) k_plan_rays(GridParams g, BatchDesc b, Ra
     const int64_t tile = (int64_t)b.plan_ent[bi] + s0.y + tt;
     const int pos = b.ray_base[bi] + s1.w + tt * s1.z + s1.y + cp;
     const int start = s1.x + cp * c;
+    if (!ROMAP_IN_BOUNDS(pos >= b.ray_base[bi] && pos < b.ray_base[bi + 1] && start >= 0 && start + c <= kTile &&
+                             tile >= 0 && tile < b.plan_cap_tiles,
+                         g.status))
+      return;
     b.plan_perm[pos] = (int32_t)r;
     b.plan_rstart[pos] = start;
     int2* slot = b.plan_slot + tile * kTile + start;

@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- per-sample inputs ----------------------------------------------
     if (t < kTile) {
       uint32_t r = S.ray[s0 + t];
+      if (r != kNoRay && !ROMAP_IN_BOUNDS(r < (uint32_t)b.n_rays, g.status)) r = kNoRay;
       sm.ray[t] = r;
       float x = 0.f, y = 0.f, z = 0.f;
       if (r != kNoRay) {

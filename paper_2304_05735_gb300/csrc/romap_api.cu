@@ -711,6 +711,7 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
     b.plan_slot = ctx->plan.slot;
     b.plan_tiles = ctx->plan.tiles;
     b.plan_npairs = ctx->plan.npairs;
+    b.plan_cap_tiles = (int32_t)ctx->cap_plan[3];
     SampleBuf none{};
     if (ctx->tile_kernel < 0) ROMAP_TRY(autotune_tile_kernel(ctx, v_ids_for_tuning(ids), b, (int)max_tiles));
     ROMAP_TRY(run_sampling_mixed(ctx, b, ctx->R, none, ctx->block_sums, ctx->dyn, ctx->totals));
@@ -760,6 +761,8 @@ romap_status validate_ids(romap_ctx* ctx, const int32_t* ids, int32_t n_ids, std
 romap_status status_error(int32_t st) {
   if (st & kStatusTimeout) return fail(ROMAP_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
   if (st & kStatusNonfinite) return fail(ROMAP_ERR_NONFINITE, "non-finite loss or gradient (status %d)", st);
+  if (st & kStatusBounds)
+    return fail(ROMAP_ERR_BOUNDS, "a device index failed its bounds check (status %d)", st);
   if (st & kStatusFixRange)
     return fail(ROMAP_ERR_CAPACITY,
                 "a gradient or loss contribution exceeded the deterministic mode's fixed-point range (status %d)", st);
@@ -808,6 +811,7 @@ const char* romap_status_string(romap_status s) {
     case ROMAP_ERR_TIMEOUT: return "device wait timed out";
     case ROMAP_ERR_BAD_STATE: return "bad state";
     case ROMAP_ERR_UNSUPPORTED: return "unsupported configuration";
+    case ROMAP_ERR_BOUNDS: return "device index out of bounds";
     default: return "unknown status";
   }
 }
@@ -876,6 +880,7 @@ romap_status romap_init(const romap_config* cfg, void* cuda_stream, romap_ctx** 
     if (e != cudaSuccess) s = fail(ROMAP_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
   if (s == ROMAP_OK) s = ensure_workspace(ctx, 1024, 1024 * 8, 8, 8);
+  ctx->g.status = ctx->status;  // bounds checks of the checked build report here
   if (s != ROMAP_OK) {
     romap_destroy(ctx);
     return s;
@@ -1885,6 +1890,29 @@ romap_status romap_set_adam_skip(romap_ctx* ctx, int32_t on) {
   if (on != 0 && on != 1) return fail(ROMAP_ERR_INVALID_ARG, "on must be 0 or 1");
   ctx->g.adam_dense = on ? 0 : 1;
   drop_graph(ctx);  // the captured steps carry the old setting
+  return ROMAP_OK;
+}
+
+romap_status romap_debug_set_pool_size(romap_ctx* ctx, int32_t id, int64_t n) {
+  ROMAP_TRY(check_ctx(ctx));
+  ROMAP_TRY(check_id(ctx, id));
+  if (n < 0 || n > ctx->objs[id].pool_n)
+    return fail(ROMAP_ERR_INVALID_ARG, "n must be in 0..%lld (the pool size)", (long long)ctx->objs[id].pool_n);
+  ObjectDev& d = ctx->objs_host[id];
+  d.pool_n = n;  // the device record only: the rays per step and the host pool keep their sizes
+  CUDA_TRY(cudaMemcpyAsync(ctx->objs_dev + id, &d, sizeof(ObjectDev), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  drop_graph(ctx);
+  return ROMAP_OK;
+}
+
+romap_status romap_checked_build(int32_t* out) {
+  if (!out) return fail(ROMAP_ERR_INVALID_ARG, "out is NULL");
+#ifdef ROMAP_CHECKED
+  *out = 1;
+#else
+  *out = 0;
+#endif
   return ROMAP_OK;
 }
 

@@ -59,6 +59,7 @@ struct GridParams {
   int extra;               // single-network hidden layers after the first (0..2), 64x64 each
   int det;                 // FP32 path: gradients and losses accumulated in 64-bit fixed point (bit-reproducible)
   int adam_dense;          // 1: Adam updates every chunk (no skip of never-touched chunks; same results)
+  int32_t* status;         // device status word of the context (bounds checks of the ROMAP_CHECKED build), or null
 };
 
 // Deterministic accumulation (the `deterministic` configuration): every gradient contribution is rounded once to a
@@ -174,6 +175,7 @@ struct BatchDesc {
   int4* plan_tiles;          // [max tiles] tile records
   int32_t* plan_npairs;      // [1] number of tile pairs
   int32_t* status;           // device status word (deterministic accumulation range), or null
+  int32_t plan_cap_tiles;    // capacity of plan_tiles (bounds checks)
 };
 
 // Per-step ray records (structure of arrays, capacity R).
@@ -324,7 +326,20 @@ inline void set_smem_attr(K* kernel, int bytes, std::atomic<uint64_t>& done) {
 }
 
 // status word bits written by the kernels
-constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2, kStatusFixRange = 4;
+constexpr int32_t kStatusNonfinite = 1, kStatusTimeout = 2, kStatusFixRange = 4, kStatusBounds = 8;
+
+// ROMAP_CHECKED build (compiled with -DROMAP_CHECKED into libromap_checked.so): device indices into pools, tables,
+// ray and sample records and the tile plan are checked against their logical sizes; a failed check sets
+// kStatusBounds in the status word and the access goes to a safe in-range index (or is skipped), never a trap.
+#ifdef ROMAP_CHECKED
+__device__ __forceinline__ bool bounds_ok(bool ok, int32_t* status) {
+  if (!ok && status) atomicOr(status, kStatusBounds);
+  return ok;
+}
+#define ROMAP_IN_BOUNDS(cond, status) ::romap::bounds_ok((cond), (status))
+#else
+#define ROMAP_IN_BOUNDS(cond, status) true
+#endif
 void launch_selftest_wait(int32_t* status, int limit, cudaStream_t stream);
 
 }  // namespace romap

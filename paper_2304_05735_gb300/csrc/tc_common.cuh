@@ -438,6 +438,7 @@ __device__ __forceinline__ SlotSample plan_sample(const GridParams& g, const Bat
   if (s >= (tile.z >> 8)) return q;
   const int2 e = b.plan_slot[(int64_t)tile.y * kTile + s];
   const int r = e.x;
+  if (!ROMAP_IN_BOUNDS(r >= b.ray_base[bi] && r < b.ray_base[bi + 1] && e.y >= 0, g.status)) return q;
   q.ray = r;
   int j = e.y;
   if ((uint32_t)j >= R.count[r]) return q;

@@ -11,6 +11,8 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libromap.so")
+# ROMAP_LIB=checked loads the bounds-checked build (libromap_checked.so, see romap_checked_build in romap.h)
+LIB_PATH_CHECKED = os.path.join(HERE, "libromap_checked.so")
 
 ROMAP_OK = 0
 ROMAP_ERR_INVALID_ARG = -1
@@ -22,6 +24,7 @@ ROMAP_ERR_NONFINITE = -6
 ROMAP_ERR_TIMEOUT = -7
 ROMAP_ERR_BAD_STATE = -8
 ROMAP_ERR_UNSUPPORTED = -9
+ROMAP_ERR_BOUNDS = -10
 
 ROMAP_DEVICE_PTR = 0x1
 ROMAP_OBJECT_FRAME = 0x2
@@ -130,6 +133,8 @@ SIGNATURES = {
     "romap_set_profiling": (_i32, [_vp, _i32]),
     "romap_set_adam_skip": (_i32, [_vp, _i32]),
     "romap_set_graphs": (_i32, [_vp, _i32]),
+    "romap_checked_build": (_i32, [_P(_i32)]),
+    "romap_debug_set_pool_size": (_i32, [_vp, _i32, _i64]),
     "romap_phase_times": (_i32, [_vp, _vp, _vp]),
     "romap_measure_request_rates": (_i32, [_vp, _vp]),
 }
@@ -146,13 +151,16 @@ class RomapError(RuntimeError):
 
 
 def lib():
-    """Loads libromap.so (building it first if it is absent and nvcc is available)."""
+    """Loads libromap.so, or libromap_checked.so when ROMAP_LIB=checked (building it first if it is absent and nvcc
+    is available)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
+        checked = os.environ.get("ROMAP_LIB", "") == "checked"
+        path = LIB_PATH_CHECKED if checked else LIB_PATH
+        if not os.path.exists(path):
             from . import build as _build
-            _build.build()
-        L = C.CDLL(LIB_PATH)
+            _build.build(checked=checked)
+        L = C.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)
             fn.restype = res
