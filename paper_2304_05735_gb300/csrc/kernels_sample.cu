@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, Ra
         uint32_t x = philox(step, (uint32_t)c.rl, kPurposeRay, 0u, ob.key0, ob.key1).x;
         p = (int64_t)(((uint64_t)x * (uint64_t)ob.pool_n) >> 32);
       }
+      if (!ROMAP_IN_BOUNDS(p >= 0 && p < ob.pool_n, g.status)) p = 0;
       for (int a = 0; a < 3; ++a) {
         o[a] = ob.pool_o[3 * p + a];
         d[a] = ob.pool_d[3 * p + a];
@@ -310,21 +311,32 @@ __device__ __forceinline__ int highest_set_at_most(const uint32_t m[5], int lim)
 // (all lanes read the same shared values); lane 0 writes the records.  Then the entries' even tile counts are
 // scanned into first tiles and every tile record is written.  s_tiles and s_wsum are scratch.
 // Tile patterns of one batch entry (one warp per block, one block per entry): the entry's count histogram (then
-// reset for the next step), the greedy patterns (see kPlanMaxCount) and their segments.  The warp computes every
-// pattern in lockstep (all lanes read the same shared values); lane 0 writes the records.  The entry's even tile count
-// goes to plan_ent for the scan that follows.
+// reset for the next step), the greedy patterns (see kPlanMaxCount) and their segments.  Lane l keeps the state of
+// counts c = 32 k + l (k = 0..4) in registers: rays not placed yet, rays placed so far (the next segment's first
+// rank) and its segment count.  Every lane builds the same pattern (uniform values, shuffles from the owner lanes);
+// then each owner lane writes the segment of its count and lane 0 the pattern record.
+__device__ __forceinline__ int pick5(const int v[5], int k) {
+  return k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : k == 3 ? v[3] : v[4];
+}
+
 __global__ void __launch_bounds__(32) k_plan_patterns(BatchDesc b) {
-  __shared__ int hh[kPlanCounts];    // rays of each count not placed yet
-  __shared__ int cons[kPlanCounts];  // rays of each count placed so far (the next segment's first rank)
-  __shared__ uint8_t ic[kPlanMaxCount], ia[kPlanMaxCount];  // the pattern being built: counts, copies
-  __shared__ uint8_t ns[kPlanCounts];  // segments of each count
+  __shared__ int8_t item_of[160];                   // item of the pattern being built holding count c, or -1
+  __shared__ uint8_t ia[kPlanMaxCount];             // copies of each item
+  __shared__ uint8_t io_slot[kPlanMaxCount], io_perm[kPlanMaxCount];  // slot / ray offset of its first copy
   const int lane = threadIdx.x, i = blockIdx.x;
-  for (int c = lane; c < kPlanCounts; c += 32) {
-    uint32_t* h = b.plan_hist + (size_t)i * kPlanCounts + c;
-    hh[c] = (int)*h;
-    *h = 0u;
-    cons[c] = 0;
-    ns[c] = 0;
+  int h[5], cons[5], ns[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int c = 32 * k + lane;
+    h[k] = 0;
+    if (c < kPlanCounts) {
+      uint32_t* hp = b.plan_hist + (size_t)i * kPlanCounts + c;
+      h[k] = c >= 1 ? (int)*hp : 0;
+      *hp = 0u;
+    }
+    cons[k] = 0;
+    ns[k] = 0;
+    item_of[c] = -1;
   }
   __syncwarp();
   int4* pat = b.plan_pat + (size_t)i * kPlanMaxPat * 2;
@@ -334,57 +346,62 @@ __global__ void __launch_bounds__(32) k_plan_patterns(BatchDesc b) {
   for (;;) {
     uint32_t m[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const int c = 32 * q + lane;
-      m[q] = __ballot_sync(0xffffffffu, c >= 1 && c < kPlanCounts && hh[c] > 0);
-    }
+    for (int k = 0; k < 5; ++k) m[k] = __ballot_sync(0xffffffffu, h[k] > 0);
     if (!(m[0] | m[1] | m[2] | m[3] | m[4])) break;
     if (npat >= kPlanMaxPat - kPlanCounts - 1) {
       fallback = true;
       break;
     }
     // one pattern: the largest remaining count opens the tile, then the largest counts that still fit
-    int rem = kTile, lim = kPlanMaxCount, ni = 0, nrays = 0;
+    int rem = kTile, lim = kPlanMaxCount, ni = 0, nrays = 0, rep = 0x7fffffff;
+    bool seg_full = false;
     for (;;) {
       const int c = highest_set_at_most(m, rem < lim ? rem : lim);
       if (c <= 0) break;
-      const int a = hh[c] < rem / c ? hh[c] : rem / c;
+      const int k = c >> 5, src = c & 31;
+      const int hv = __shfl_sync(0xffffffffu, pick5(h, k), src);
+      const int nsv = __shfl_sync(0xffffffffu, pick5(ns, k), src);
+      const int a = hv < rem / c ? hv : rem / c;
       if (lane == 0) {
-        ic[ni] = (uint8_t)c;
+        item_of[c] = (int8_t)ni;
         ia[ni] = (uint8_t)a;
+        io_slot[ni] = (uint8_t)(kTile - rem);
+        io_perm[ni] = (uint8_t)nrays;
       }
+      rep = min(rep, hv / a);
+      seg_full = seg_full || nsv >= kPlanSegsPerCount - 1;  // keep one segment per count for the fallback
       ++ni;
       nrays += a;
       rem -= a * c;
       lim = c - 1;
     }
     __syncwarp();
-    int rep = 0x7fffffff;
-    bool seg_full = false;
-    for (int q = 0; q < ni; ++q) {
-      const int c = ic[q], a = ia[q];
-      rep = min(rep, hh[c] / a);
-      seg_full = seg_full || ns[c] >= kPlanSegsPerCount - 1;  // keep one segment per count for the fallback
-    }
     if (seg_full) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) item_of[32 * k + lane] = -1;
+      __syncwarp();
       fallback = true;
       break;
+    }
+    // segments: each count's owner lane; the pattern record: lane 0
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int c = 32 * k + lane;
+      const int q = item_of[c];
+      if (q >= 0) {
+        const int a = ia[q];
+        int4* sg = seg + ((size_t)c * kPlanSegsPerCount + ns[k]) * 2;
+        sg[0] = make_int4(cons[k], T, a, rep);
+        sg[1] = make_int4(io_slot[q], io_perm[q], nrays, PB);
+        ns[k] += 1;
+        cons[k] += rep * a;
+        h[k] -= rep * a;
+        item_of[c] = -1;
+      }
     }
     if (lane == 0) {
       pat[2 * npat] = make_int4(T, rep, nrays, PB);
       pat[2 * npat + 1] = make_int4(rep * nrays, kTile - rem, 0, 0);
-      int slot_off = 0, perm_off = 0;
-      for (int q = 0; q < ni; ++q) {
-        const int c = ic[q], a = ia[q];
-        int4* sg = seg + ((size_t)c * kPlanSegsPerCount + ns[c]) * 2;
-        sg[0] = make_int4(cons[c], T, a, rep);
-        sg[1] = make_int4(slot_off, perm_off, nrays, PB);
-        ns[c] += 1;
-        cons[c] += rep * a;
-        hh[c] -= rep * a;
-        slot_off += a * c;
-        perm_off += a;
-      }
     }
     __syncwarp();
     T += rep;
@@ -393,27 +410,36 @@ __global__ void __launch_bounds__(32) k_plan_patterns(BatchDesc b) {
   }
   if (fallback) {  // every count left in tiles of its own: floor(128 / c) rays of count c per tile
     for (int c = kPlanMaxCount; c >= 1; --c) {
-      const int rays = hh[c];
+      const int k = c >> 5, src = c & 31;
+      const int rays = __shfl_sync(0xffffffffu, pick5(h, k), src);
       if (rays <= 0) continue;
       const int a = kTile / c, tiles = (rays + a - 1) / a;
+      if (lane == src) {
+        int4* sg = seg + ((size_t)c * kPlanSegsPerCount + pick5(ns, k)) * 2;
+        sg[0] = make_int4(pick5(cons, k), T, a, tiles);
+        sg[1] = make_int4(0, 0, a, PB);
+#pragma unroll
+        for (int kk = 0; kk < 5; ++kk)
+          if (kk == k) {
+            ns[kk] += 1;
+            cons[kk] += rays;
+            h[kk] = 0;
+          }
+      }
       if (lane == 0) {
         pat[2 * npat] = make_int4(T, tiles, a, PB);
         pat[2 * npat + 1] = make_int4(rays, a * c, c, 0);
-        int4* sg = seg + ((size_t)c * kPlanSegsPerCount + ns[c]) * 2;
-        sg[0] = make_int4(cons[c], T, a, tiles);
-        sg[1] = make_int4(0, 0, a, PB);
-        ns[c] += 1;
-        cons[c] += rays;
-        hh[c] = 0;
       }
-      __syncwarp();
       T += tiles;
       PB += rays;
       ++npat;
     }
   }
-  __syncwarp();
-  for (int c = lane; c < kPlanCounts; c += 32) b.plan_nseg[(size_t)i * kPlanCounts + c] = ns[c];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int c = 32 * k + lane;
+    if (c < kPlanCounts) b.plan_nseg[(size_t)i * kPlanCounts + c] = ns[k];
+  }
   if (lane == 0) {
     b.plan_npat[i] = npat;
     b.plan_ent[i] = (T + 1) & ~1;  // even: a pair never mixes entries (the scan turns it into the first tile)
