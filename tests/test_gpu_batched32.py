@@ -68,18 +68,19 @@ def test_uneven_batch_with_occupancy_mixed():
                 assert np.linalg.norm(gs - g_small[k]) <= 1e-5 * np.linalg.norm(g_small[k])
         finally:
             ctx2.close()
-        # the smallest object against the FP64 oracle (mixed precision: loss within 1e-3 relative)
-        k = order[0]
-        oc.rays_per_step = int(rays[k])
-        pool = object_frame_pool(scenes[k])
-        p0 = O.init_params(oc, scenes[k].seed)
-        ref = O.train_step(oc, scenes[k].half.astype(np.float32), scenes[k].seed, 1, pool, p0, p0 * 0, p0 * 0,
-                           occ=occ[k], do_adam=False)
-        rel = abs(lb[k][0] - ref["loss"][0]) / abs(ref["loss"][0])
-        g = g_small[k].astype(np.float64)
-        cos = g @ ref["grad"] / (np.linalg.norm(g) * np.linalg.norm(ref["grad"]))
-        print(f"object {k} ({pools[k]} rays): loss rel {rel:.2e}, gradient cosine {cos:.6f}")
-        assert rel < 1e-3 and cos > 0.995
+        # the four smallest objects against the FP64 oracle (mixed precision: loss within 1e-3 relative, gradient
+        # direction within BF16 rounding)
+        for k in order[:4]:
+            oc.rays_per_step = int(rays[k])
+            pool = object_frame_pool(scenes[k])
+            p0 = O.init_params(oc, scenes[k].seed)
+            ref = O.train_step(oc, scenes[k].half.astype(np.float32), scenes[k].seed, 1, pool, p0, p0 * 0, p0 * 0,
+                               occ=occ[k], do_adam=False)
+            rel = abs(lb[k][0] - ref["loss"][0]) / abs(ref["loss"][0])
+            g = (g_small[k] if k in g_small else ctx.grad(ids[k])).astype(np.float64)
+            cos = g @ ref["grad"] / (np.linalg.norm(g) * np.linalg.norm(ref["grad"]))
+            print(f"object {k} ({pools[k]} rays): loss rel {rel:.2e}, gradient cosine {cos:.6f}")
+            assert rel < 1e-3 and cos > 0.995
     finally:
         ctx.close()
 
