@@ -80,7 +80,7 @@ def test_uneven_batch_with_occupancy_mixed():
             g = (g_small[k] if k in g_small else ctx.grad(ids[k])).astype(np.float64)
             cos = g @ ref["grad"] / (np.linalg.norm(g) * np.linalg.norm(ref["grad"]))
             print(f"object {k} ({pools[k]} rays): loss rel {rel:.2e}, gradient cosine {cos:.6f}")
-            assert rel < 1e-3 and cos > 0.995
+            assert rel < 1e-3 and cos > 0.999
     finally:
         ctx.close()
 
