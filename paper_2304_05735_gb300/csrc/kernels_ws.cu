@@ -24,8 +24,8 @@ constexpr int kCompute = 128;
 
 template <int LFP>
 struct WsSlot {
-  // activation buffers: contiguous and in this order (the MN-major views of the weight-gradient GEMMs read up to
-  // 2 KB past a buffer into the next one of the slot; DL is read without overrun)
+  // activation buffers: contiguous and in this order (the MN-major A operands of the weight-gradient GEMMs, dY^T with
+  // M padded to 128, read up to 2 KB past their buffer into the next one of the slot; past DL: the float arrays)
   __align__(128) unsigned char E[kT * LFP * 2];
   __align__(128) unsigned char H1[kT * kH * 2];
   __align__(128) unsigned char CIN[kT * 32 * 2];
@@ -206,7 +206,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     if (sm.c_stop) break;
     const int nbi = sl.bi;
     if (nbi != bi) {
-      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
+      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kCompute);
       bi = nbi;
       ob = &b.objs[b.slot[bi]];
       load_weights<LFP>(sm, g, ob->params, kCompute);
@@ -321,33 +321,33 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       store8(sl.DL, s, 1, 16, dl + 8, f16);
     }
     sync_then_issue();
-    if (s == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
+    if (s == 0) {  // dH3 = DL W5 ; dW5 += DL^T H3
       mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW5 + tm, desc_mn(sl.H3, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1, f16), kk > 0 ? 1u : acc_dw);
+        mma(kColDW5 + tm, desc_mn(sl.DL, 16, kk), desc_mn(sl.H3, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
     epi_mask64(tmp, sl.H3, s, f16);
     sync_then_issue();
-    if (s == 0) {  // dH2 = dH3 W4 ; dW4^T += H2^T dH3
+    if (s == 0) {  // dH2 = dH3 W4 ; dW4 += dH3^T H2
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW4 + tm, desc_mn(sl.H2, kH, kk), desc_mn(sl.H3, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
+        mma(kColDW4 + tm, desc_mn(sl.H3, kH, kk), desc_mn(sl.H2, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
     epi_mask64(tmp, sl.H2, s, f16);
     sync_then_issue();
-    if (s == 0) {  // dCIN = dH2 W3 ; dW3^T += CIN^T dH2
+    if (s == 0) {  // dCIN = dH2 W3 ; dW3 += dH2^T CIN
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1, f16), kk > 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW3 + tm, desc_mn(sl.CIN, 32, kk), desc_mn(sl.H2, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
+        mma(kColDW3 + tm, desc_mn(sl.H2, kH, kk), desc_mn(sl.CIN, 32, kk), idesc(32, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
@@ -362,22 +362,22 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       store8(sl.DL, s, 1, 16, d + 8, f16);
     }
     sync_then_issue();
-    if (s == 0) {  // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
+    if (s == 0) {  // dH1 = dOUT W2 ; dW2 += dOUT^T H1
       mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW2 + tm, desc_mn(sl.H1, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1, f16), kk > 0 ? 1u : acc_dw);
+        mma(kColDW2 + tm, desc_mn(sl.DL, 16, kk), desc_mn(sl.H1, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
     epi_mask64(tmp, sl.H1, s, f16);
     sync_then_issue();
-    if (s == 0) {  // dE = dH1 W1 ; dW1^T += E^T dH1
+    if (s == 0) {  // dE = dH1 W1 ; dW1 += dH1^T E
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) mma(dtmp, desc_k(sl.H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1, f16), kk > 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW1 + tm, desc_mn(sl.E, LFP, kk), desc_mn(sl.H1, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
+        mma(kColDW1 + tm, desc_mn(sl.H1, kH, kk), desc_mn(sl.E, LFP, kk), idesc(LFP, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
@@ -399,7 +399,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
   }
   if (s == 0) sm.c_stop = sm.fail;
   bar_compute();
-  if (!sm.c_stop && bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
+  if (!sm.c_stop && bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kCompute);
 }
 
 template <int LFP, bool F16>

@@ -15,8 +15,12 @@ namespace tc {
 
 constexpr int kT = 128;           // samples per tile (MMA M)
 constexpr int kTmemCols = 512;
-// TMEM columns: weight-gradient accumulators (shared by the tiles of a pair), then one 64-column temporary per tile
-constexpr uint32_t kColDW1 = 0, kColDW2 = 64, kColDW3 = 80, kColDW4 = 144, kColDW5 = 208, kColTmp = 256;
+// TMEM columns: weight-gradient accumulators (shared by the tiles of a pair), then one 64-column temporary per tile.
+// A weight gradient dW [out][in] accumulates with its output rows o in TMEM lanes (M = out, padded to 128) and its
+// inputs in columns: dW1 LFP columns, dW3 32 (the colour input; 64 for the single network's hidden layer 3), dW2, dW4
+// and dW5 64 each.  A lane then holds a contiguous row of the FP32 gradient, which the flush adds with 16-byte vector
+// reductions.
+constexpr uint32_t kColDW1 = 0, kColDW3 = 32, kColDW2 = 96, kColDW4 = 160, kColDW5 = 224, kColTmp = 288;
 constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -135,87 +139,115 @@ __device__ __forceinline__ void load8(const unsigned char* buf, int r, int c, in
   }
 }
 
+// The five forward weight matrices of an object as K-major BF16 (FP16) operands, in one index space of padded shapes:
+// [w1: kH x LFP][w2: 16 x kH][w3: kH x 32][w4: kH x kH][w5: 16 x kH] (padding reads as 0).  A thread's loads of a batch
+// are all issued before its first shared-memory store, so that a batch costs one round trip to L2: under the load of
+// the other CTAs' hash gathers and scatters a round trip takes a few thousand cycles, and staging the weights one
+// load at a time made every object change of a CTA cost tens of microseconds.
+template <int LFP>
+struct WeightIndex {
+  static constexpr int n1 = kH * LFP, n2 = n1 + 16 * kH, n3 = n2 + kH * 32, n4 = n3 + kH * kH, total = n4 + 16 * kH;
+};
+template <int LFP>
+__device__ __forceinline__ float weight_fetch(const GridParams& g, const float* __restrict__ P, int64_t off4, int i) {
+  using W = WeightIndex<LFP>;
+  if (i < W::n1) {
+    const int o = i / LFP, k = i % LFP;
+    return k < g.LF ? __ldg(P + g.mlp_off[0] + o * g.LF + k) : 0.f;
+  }
+  if (i < W::n2) return __ldg(P + g.mlp_off[1] + (i - W::n1));
+  if (i < W::n3) {
+    const int j = i - W::n2, o = j / 32, k = j % 32;
+    return k < g.cin ? __ldg(P + g.mlp_off[2] + o * g.cin + k) : 0.f;
+  }
+  if (i < W::n4) return __ldg(P + off4 + (i - W::n3));
+  const int j = i - W::n4;
+  return j < 3 * kH ? __ldg(P + g.mlp_off[4] + j) : 0.f;
+}
+template <int LFP, class Smem>
+__device__ __forceinline__ unsigned char* weight_dest(Smem& sm, int i) {
+  using W = WeightIndex<LFP>;
+  if (i < W::n1) return sm.w1 + kmaj(i / LFP, i % LFP, LFP);
+  if (i < W::n2) { const int j = i - W::n1; return sm.w2 + kmaj(j / kH, j % kH, kH); }
+  if (i < W::n3) { const int j = i - W::n2; return sm.w3 + kmaj(j / 32, j % 32, 32); }
+  if (i < W::n4) { const int j = i - W::n3; return sm.w4 + kmaj(j / kH, j % kH, kH); }
+  const int j = i - W::n4;
+  return sm.w5 + kmaj(j / kH, j % kH, kH);
+}
 template <int LFP, class Smem>
 __device__ void load_weights(Smem& sm, const GridParams& g, const float* __restrict__ P, int nthreads) {
+  constexpr int kBatch = 20;
   const int t = threadIdx.x % nthreads;
   const bool f16 = g.f16 != 0;
-  for (int i = t; i < kH * LFP; i += nthreads) {
-    int o = i / LFP, k = i % LFP;
-    float v = k < g.LF ? P[g.mlp_off[0] + o * g.LF + k] : 0.f;
-    *reinterpret_cast<uint16_t*>(sm.w1 + kmaj(o, k, LFP)) = pack1(v, f16);
-  }
-  for (int i = t; i < 16 * kH; i += nthreads) {
-    int o = i / kH, k = i % kH;
-    *reinterpret_cast<uint16_t*>(sm.w2 + kmaj(o, k, kH)) = pack1(P[g.mlp_off[1] + i], f16);
-  }
-  for (int i = t; i < kH * 32; i += nthreads) {
-    int o = i / 32, k = i % 32;
-    float v = k < g.cin ? P[g.mlp_off[2] + o * g.cin + k] : 0.f;
-    *reinterpret_cast<uint16_t*>(sm.w3 + kmaj(o, k, 32)) = pack1(v, f16);
-  }
   const int64_t off4 = g.extra >= 1 ? g.mlp_off[5] : g.mlp_off[3];  // single network: its hidden layer 2
-  for (int i = t; i < kH * kH; i += nthreads) {
-    int o = i / kH, k = i % kH;
-    *reinterpret_cast<uint16_t*>(sm.w4 + kmaj(o, k, kH)) = pack1(P[off4 + i], f16);
-  }
-  for (int i = t; i < 16 * kH; i += nthreads) {
-    int o = i / kH, k = i % kH;
-    float v = o < 3 ? P[g.mlp_off[4] + o * kH + k] : 0.f;
-    *reinterpret_cast<uint16_t*>(sm.w5 + kmaj(o, k, kH)) = pack1(v, f16);
+  for (int base = t; base < WeightIndex<LFP>::total; base += kBatch * nthreads) {
+    float v[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const int i = base + j * nthreads;
+      v[j] = i < WeightIndex<LFP>::total ? weight_fetch<LFP>(g, P, off4, i) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const int i = base + j * nthreads;
+      if (i < WeightIndex<LFP>::total) *reinterpret_cast<uint16_t*>(weight_dest<LFP>(sm, i)) = pack1(v[j], f16);
+    }
   }
 }
 
-// Adds the TMEM weight-gradient accumulators of one object, times scale (the inverse of the FP16 path's gradient
-// scale, else 1), to its FP32 gradient (rows = input features).
-template <int LFP>
-__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad, float scale) {
-  const int t = threadIdx.x, w = t >> 5;
-  if (w >= 2) return;  // rows 0..63 live in the lanes read by warps 0 and 1
-  const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);
-  const int row = t;
-  float v[16];
-  // dW1^T: rows = encoding features (LF), 64 columns (hidden units)
-  for (int c = 0; c < kH; c += 16) {
-    tmem_ld16(lane_base + kColDW1 + c, v);
+__device__ __forceinline__ void red_add4f(float* addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+// Adds TMEM columns [c0, c0 + ncols) of this thread's lane (row o of a weight gradient when valid), times scale, to
+// row[0 .. in): columns in 16-column blocks, the blocks dealt to the nh flushing warps of the same lanes (half h).
+// tcgen05.ld is warp-collective, so every lane loads and only the valid rows add.
+__device__ __forceinline__ void flush_rows(uint32_t lane_taddr, uint32_t c0, int ncols, bool valid, float* row, int in,
+                                           float scale, int h, int nh) {
+  for (int blk = h; blk * 16 < ncols; blk += nh) {
+    float v[16];
+    tmem_ld16(lane_taddr + c0 + 16u * (uint32_t)blk, v);
     tmem_wait_ld();
-    if (row < g.LF)
-      for (int j = 0; j < 16; ++j)
-        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[0] + (c + j) * g.LF + row, v[j] * scale);
-  }
-  tmem_ld16(lane_base + kColDW2, v);  // dW2^T: rows = hidden (64), 16 columns (density outputs)
-  tmem_wait_ld();
-  for (int j = 0; j < 16; ++j)
-    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[1] + j * kH + row, v[j] * scale);
-  if (g.single_net) {  // no colour net; hidden layers 2 and 3 accumulate in the DW4 and DW3 columns
-    for (int x = 0; x < g.extra; ++x) {
-      const uint32_t col = x == 0 ? kColDW4 : kColDW3;
-      float* dst = grad + g.mlp_off[5 + x];
-      for (int c = 0; c < kH; c += 16) {  // dM^T: rows = inputs (64), 64 columns (outputs)
-        tmem_ld16(lane_base + col + c, v);
-        tmem_wait_ld();
-        for (int j = 0; j < 16; ++j)
-          if (v[j] != 0.f) atomicAdd(dst + (c + j) * kH + row, v[j] * scale);
+    if (!valid) continue;
+#pragma unroll
+    for (int j = 0; j < 16; j += 4) {
+      const int k = 16 * blk + j;
+      if (k >= in) break;
+      float* a = row + k;
+      if (k + 3 < in && (reinterpret_cast<uintptr_t>(a) & 15u) == 0) {
+        if (v[j] != 0.f || v[j + 1] != 0.f || v[j + 2] != 0.f || v[j + 3] != 0.f)
+          red_add4f(a, v[j] * scale, v[j + 1] * scale, v[j + 2] * scale, v[j + 3] * scale);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (k + jj < in && v[j + jj] != 0.f) atomicAdd(a + jj, v[j + jj] * scale);
       }
     }
+  }
+}
+// Adds the TMEM weight-gradient accumulators of one object, times scale (the inverse of the FP16 path's gradient
+// scale, else 1), to its FP32 gradient.  Rows 0..63 live in TMEM lanes 0..63, which warps w with w % 4 < 2 can read;
+// with nthreads >= 256 warps 0, 1, 4 and 5 share the work (warps 4 and 5 take every other 16-column block).
+template <int LFP>
+__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad, float scale, int nthreads) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if ((w & 3) >= 2 || w >= nthreads / 32) return;
+  const int q = w & 1;                     // lanes 32 q .. 32 q + 31
+  const int nh = nthreads >= 256 ? 2 : 1;  // flushing warps per lane group
+  const int h = (w >> 2) & (nh - 1);
+  const uint32_t lt = tm + ((uint32_t)(32 * q) << 16);
+  const int o = 32 * q + lane;  // output row of this lane
+  // density output layer [16][64] (the hidden layer feeding it: H1, or the single network's last hidden layer)
+  if (q == 0) flush_rows(lt, kColDW2, kH, o < 16, grad + g.mlp_off[1] + o * kH, kH, scale, h, nh);
+  // first layer [64][LF]
+  flush_rows(lt, kColDW1, LFP, true, grad + g.mlp_off[0] + o * g.LF, g.LF, scale, h, nh);
+  if (g.single_net) {  // hidden layers 2 and 3 [64][64] in the DW4 and DW3 columns
+    for (int x = 0; x < g.extra; ++x)
+      flush_rows(lt, x == 0 ? kColDW4 : kColDW3, kH, true, grad + g.mlp_off[5 + x] + o * kH, kH, scale, h, nh);
     return;
   }
-  for (int c = 0; c < kH; c += 16) {  // dW3^T: rows = colour inputs (cin), 64 columns
-    tmem_ld16(lane_base + kColDW3 + c, v);
-    tmem_wait_ld();
-    if (row < g.cin)
-      for (int j = 0; j < 16; ++j)
-        if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[2] + (c + j) * g.cin + row, v[j] * scale);
-  }
-  for (int c = 0; c < kH; c += 16) {  // dW4^T: rows = hidden (64), 64 columns
-    tmem_ld16(lane_base + kColDW4 + c, v);
-    tmem_wait_ld();
-    for (int j = 0; j < 16; ++j)
-      if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[3] + (c + j) * kH + row, v[j] * scale);
-  }
-  tmem_ld16(lane_base + kColDW5, v);  // dW5^T: rows = hidden (64), columns 0..2 real
-  tmem_wait_ld();
-  for (int j = 0; j < 3; ++j)
-    if (v[j] != 0.f) atomicAdd(grad + g.mlp_off[4] + j * kH + row, v[j] * scale);
+  flush_rows(lt, kColDW3, 32, true, grad + g.mlp_off[2] + o * g.cin, g.cin, scale, h, nh);  // colour input [64][cin]
+  flush_rows(lt, kColDW4, kH, true, grad + g.mlp_off[3] + o * kH, kH, scale, h, nh);         // [64][64]
+  if (q == 0) flush_rows(lt, kColDW5, kH, o < 3, grad + g.mlp_off[4] + o * kH, kH, scale, h, nh);  // [3][64]
 }
 
 __device__ __forceinline__ float warp_incl_prefix(float v, int lane) {

@@ -14,9 +14,10 @@
 //      the next operand row to shared memory,
 //   4. volume rendering (Eq. 6), the losses of Eq. 7-11 and the compositing adjoint, one warp per ray,
 //   5. the backward: per layer one GEMM for the input gradient (dX = dY W: A = dY K-major, B = W read
-//      MN-major from the forward copy) and one for the weight gradient (dW^T = X^T dY over the 128 samples:
-//      both operands read MN-major from the activation buffers, M padded to 128), the latter accumulated in
-//      TMEM across all tiles of the same object and added to the FP32 gradient once per object change,
+//      MN-major from the forward copy) and one for the weight gradient (dW = dY^T X over the 128 samples:
+//      both operands read MN-major from the activation buffers, M = the layer's outputs padded to 128), the latter
+//      accumulated in TMEM across all tiles of the same object and added to the FP32 gradient once per object
+//      change,
 //   6. the hash-gradient scatter (FP32 vector atomics into the FP32 gradient of the table).
 // The transmittance scan, the losses and every accumulation stay in FP32; Adam keeps FP32 masters and
 // refreshes the FP16 table copy.  With FP16 operands the backward's gradient operands are scaled by the object's
@@ -44,10 +45,10 @@ using namespace tc;
 constexpr int kTilesPerCta = 2;   // tiles processed in lockstep: warpgroup g works on tile g of the pair
 constexpr int kTcThreads = 128 * kTilesPerCta;
 
-// Buffers of one tile.  The activation buffers are contiguous and in this order: the MN-major views of the
-// weight-gradient GEMMs read up to 2 KB past a buffer (the rows >= its feature count of the padded M = 128), which
-// lands in the next buffer of the same tile and only feeds TMEM rows that are never read; DL is read without
-// overrun.
+// Buffers of one tile.  The activation buffers are contiguous and in this order: the MN-major A operands of the
+// weight-gradient GEMMs (dY^T, M padded to 128) read up to 2 KB past their buffer (the rows >= its feature count),
+// which lands in the next buffer of the same tile (past DL: the tile's float arrays) and only feeds TMEM rows that
+// are never read.
 template <int LFP>
 struct TileBufs {
   __align__(128) unsigned char E[2][kT * LFP * 2];  // this pair's encoding and the next pair's, alternating
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tb.t[s] = nx.t;
     tb.dt[s] = nx.dt;
     if (nx_bi != bi) {
-      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
+      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kTcThreads);
       bi = nx_bi;
       ob = nx_ob;
       load_weights<LFP>(sm, g, ob->params, kTcThreads);
@@ -548,12 +549,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if constexpr (!SN) {  // ---- colour net backward ------------------------------------------------------------------
       sync_then_issue();
-      if (t == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
+      if (t == 0) {  // dH3 = DL W5 ; dW5 += DL^T H3
         for (int u = 0; u < kTilesPerCta; ++u) {
           mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
+            mma(kColDW5 + tm, desc_mn(sm.tb[u].DL, 16, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1, f16),
                 (u > 0 || kk > 0) ? 1u : acc_dw);
         }
         mma_commit(&sm.mbar);
@@ -569,14 +570,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!(ok = wait_mma())) break;
       epi_mask64(tmp, tb.H3, s, f16);
       sync_then_issue();
-      if (t == 0) {  // dH2 = dH3 W4 ; dW4^T += H2^T dH3
+      if (t == 0) {  // dH2 = dH3 W4 ; dW4 += dH3^T H2
         for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW4 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1, f16),
+            mma(kColDW4 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1, f16),
                 (u > 0 || kk > 0) ? 1u : acc_dw);
         }
         mma_commit(&sm.mbar);
@@ -590,14 +591,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!(ok = wait_mma())) break;
       epi_mask64(tmp, tb.H2, s, f16);
       sync_then_issue();
-      if (t == 0) {  // dCIN = dH2 W3 (32 columns) ; dW3^T += CIN^T dH2
+      if (t == 0) {  // dCIN = dH2 W3 (32 columns) ; dW3 += dH2^T CIN
         for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1, f16), kk > 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW3 + tm, desc_mn(sm.tb[u].CIN, 32, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1, f16),
+            mma(kColDW3 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].CIN, 32, kk), idesc(32, 1, 1, f16),
                 (u > 0 || kk > 0) ? 1u : acc_dw);
         }
         mma_commit(&sm.mbar);
@@ -621,12 +622,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }  // colour net backward
     sync_then_issue();
-    if (t == 0) {  // dHL = dOUT W2 ; dW2^T += HL^T dOUT
+    if (t == 0) {  // dHL = dOUT W2 ; dW2 += dOUT^T HL
       for (int u = 0; u < kTilesPerCta; ++u) {
         mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW2 + tm, desc_mn(hid(u, nl), kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
+          mma(kColDW2 + tm, desc_mn(sm.tb[u].DL, 16, kk), desc_mn(hid(u, nl), kH, kk), idesc(64, 1, 1, f16),
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
@@ -646,7 +647,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (!(ok = wait_mma())) break;
     epi_mask64(tmp, hid(wg, nl), s, f16);
-    if constexpr (SN) {  // hidden layers 3, 2: dhid(k) = dhid(k + 1) M ; dM^T += hid(k)^T dhid(k + 1)
+    if constexpr (SN) {  // hidden layers 3, 2: dhid(k) = dhid(k + 1) M ; dM += dhid(k + 1)^T hid(k)
       for (int k = nl - 1; k >= 0; --k) {
         sync_then_issue();
         if (t == 0) {
@@ -658,7 +659,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               mma(tmp_d(u), desc_k(hid(u, k + 1), kH, kk), desc_mn(w, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-              mma(col + tm, desc_mn(hid(u, k), kH, kk), desc_mn(hid(u, k + 1), kH, kk), idesc(64, 1, 1, f16),
+              mma(col + tm, desc_mn(hid(u, k + 1), kH, kk), desc_mn(hid(u, k), kH, kk), idesc(64, 1, 1, f16),
                   (u > 0 || kk > 0) ? 1u : acc_dw);
           }
           mma_commit(&sm.mbar);
@@ -675,14 +676,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!ok) break;
     }
     sync_then_issue();
-    if (t == 0) {  // dE = dH1 W1 (LFP columns) ; dW1^T += E^T dH1
+    if (t == 0) {  // dE = dH1 W1 (LFP columns) ; dW1 += dH1^T E
       for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
           mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1, f16), kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW1 + tm, desc_mn(sm.tb[u].E[cur], LFP, kk), desc_mn(sm.tb[u].H1, kH, kk), idesc(64, 1, 1, f16),
+          mma(kColDW1 + tm, desc_mn(sm.tb[u].H1, kH, kk), desc_mn(sm.tb[u].E[cur], LFP, kk), idesc(LFP, 1, 1, f16),
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_after();
   }
   if (ok && bi >= 0) {
-    flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi));
+    flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kTcThreads);
   } else if (!ok) {
     if (t == 0) {
       if (status) atomicOr(status, 2);
