@@ -78,24 +78,33 @@ __device__ __forceinline__ void red_add2(float2* addr, float a, float b) {
 __device__ __forceinline__ void red_add4(float2* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
-// Scatter of one level: the 8 corner gradients (w_k d0, w_k d1) added into the FP32 gradient of the level (gt points
-// at the level's first entry, 16-byte aligned since levels start at multiples of 8 entries).  Corners k and k+1
-// differ by one step in x; when their entries form an aligned pair {2m, 2m+1} (x even on a hashed level, an even
-// index on a dense one) one 16-byte vector add covers both, which saves one L1->L2 request.
-__device__ __forceinline__ void scatter_corners(float2* gt, const uint32_t idx[8], const float w[8], float d0,
-                                                float d1) {
+// Scatter of one level: the 8 corner gradients a[2k], a[2k+1] (features 0, 1 of corner k) added into the FP32
+// gradient of the level (gt points at the level's first entry, 16-byte aligned since levels start at multiples of 8
+// entries).  Corners k and k+1 differ by one step in x; when their entries form an aligned pair {2m, 2m+1} (x even on
+// a hashed level, an even index on a dense one) one 16-byte vector add covers both, which saves one L1->L2 request.
+__device__ __forceinline__ void scatter_sums(float2* gt, const uint32_t idx[8], const float a[16]) {
 #pragma unroll
   for (int k = 0; k < 8; k += 2) {
     const uint32_t i0 = idx[k], i1 = idx[k + 1];
-    const float a0 = w[k] * d0, a1 = w[k] * d1, b0 = w[k + 1] * d0, b1 = w[k + 1] * d1;
     if ((i0 ^ i1) == 1u) {
-      if (i0 < i1) red_add4(gt + i0, a0, a1, b0, b1);
-      else red_add4(gt + i1, b0, b1, a0, a1);
+      if (i0 < i1) red_add4(gt + i0, a[2 * k], a[2 * k + 1], a[2 * k + 2], a[2 * k + 3]);
+      else red_add4(gt + i1, a[2 * k + 2], a[2 * k + 3], a[2 * k], a[2 * k + 1]);
     } else {
-      red_add2(gt + i0, a0, a1);
-      red_add2(gt + i1, b0, b1);
+      red_add2(gt + i0, a[2 * k], a[2 * k + 1]);
+      red_add2(gt + i1, a[2 * k + 2], a[2 * k + 3]);
     }
   }
+}
+// The same for one sample: corner k receives (w_k d0, w_k d1).
+__device__ __forceinline__ void scatter_corners(float2* gt, const uint32_t idx[8], const float w[8], float d0,
+                                                float d1) {
+  float a[16];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[2 * k] = w[k] * d0;
+    a[2 * k + 1] = w[k] * d1;
+  }
+  scatter_sums(gt, idx, a);
 }
 
 // Deterministic mode: one contribution added to a 64-bit fixed-point accumulator (kFixBits fractional bits), rounded

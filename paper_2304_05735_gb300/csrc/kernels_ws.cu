@@ -209,7 +209,7 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kCompute);
       bi = nbi;
       ob = &b.objs[b.slot[bi]];
-      load_weights<LFP>(sm, g, ob->params, kCompute);
+      load_weights<LFP, 20>(sm, g, ob->params, s, kCompute);
       acc_dw = 0;
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];

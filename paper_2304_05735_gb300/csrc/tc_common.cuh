@@ -21,6 +21,9 @@ constexpr int kTmemCols = 512;
 // and dW5 64 each.  A lane then holds a contiguous row of the FP32 gradient, which the flush adds with 16-byte vector
 // reductions.
 constexpr uint32_t kColDW1 = 0, kColDW3 = 32, kColDW2 = 96, kColDW4 = 160, kColDW5 = 224, kColTmp = 288;
+// The fused kernel's dL/dencoding of each tile (up to 32 columns), read by the scatter.
+constexpr uint32_t kColDE = 416;
+static_assert(kColDE + 64 <= 512, "TMEM columns of the fused kernel");
 constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,6 +94,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
                : "r"(taddr));
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// 2 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float& a, float& b) {
+  uint32_t r0, r1;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
+  a = __uint_as_float(r0);
+  b = __uint_as_float(r1);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -174,24 +184,35 @@ __device__ __forceinline__ unsigned char* weight_dest(Smem& sm, int i) {
   const int j = i - W::n4;
   return sm.w5 + kmaj(j / kH, j % kH, kH);
 }
-template <int LFP, class Smem>
-__device__ void load_weights(Smem& sm, const GridParams& g, const float* __restrict__ P, int nthreads) {
-  constexpr int kBatch = 20;
-  const int t = threadIdx.x % nthreads;
-  const bool f16 = g.f16 != 0;
+// Weights i = t + j nthreads, j < kBatch, of the index space above: fetched into v, then stored (the split lets a
+// caller overlap the fetch's round trip with other work).
+template <int LFP, int kBatch>
+__device__ __forceinline__ void weights_fetch(const GridParams& g, const float* __restrict__ P, int t, int nthreads,
+                                              float (&v)[kBatch]) {
   const int64_t off4 = g.extra >= 1 ? g.mlp_off[5] : g.mlp_off[3];  // single network: its hidden layer 2
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    const int i = t + j * nthreads;
+    v[j] = i < WeightIndex<LFP>::total ? weight_fetch<LFP>(g, P, off4, i) : 0.f;
+  }
+}
+template <int LFP, int kBatch, class Smem>
+__device__ __forceinline__ void weights_store(Smem& sm, const GridParams& g, int t, int nthreads,
+                                              const float (&v)[kBatch]) {
+  const bool f16 = g.f16 != 0;
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    const int i = t + j * nthreads;
+    if (i < WeightIndex<LFP>::total) *reinterpret_cast<uint16_t*>(weight_dest<LFP>(sm, i)) = pack1(v[j], f16);
+  }
+}
+// All weights by thread t of nthreads, kBatch loads in flight per thread.
+template <int LFP, int kBatch, class Smem>
+__device__ void load_weights(Smem& sm, const GridParams& g, const float* __restrict__ P, int t, int nthreads) {
   for (int base = t; base < WeightIndex<LFP>::total; base += kBatch * nthreads) {
     float v[kBatch];
-#pragma unroll
-    for (int j = 0; j < kBatch; ++j) {
-      const int i = base + j * nthreads;
-      v[j] = i < WeightIndex<LFP>::total ? weight_fetch<LFP>(g, P, off4, i) : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < kBatch; ++j) {
-      const int i = base + j * nthreads;
-      if (i < WeightIndex<LFP>::total) *reinterpret_cast<uint16_t*>(weight_dest<LFP>(sm, i)) = pack1(v[j], f16);
-    }
+    weights_fetch<LFP, kBatch>(g, P, base, nthreads, v);
+    weights_store<LFP, kBatch>(sm, g, base, nthreads, v);
   }
 }
 
@@ -395,12 +416,14 @@ __device__ void composite_ray(Bufs& sm, const GridParams& g, const BatchDesc& b,
 template <int LFP, int L0, int L1>
 __device__ __forceinline__ void gather_levels(const GridParams& g, const ObjectDev* ob, const float p[3], float* e) {
   const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
+  const float hf[3] = {ob->half[0], ob->half[1], ob->half[2]};
+  const float ie[3] = {ob->inv_ext[0], ob->inv_ext[1], ob->inv_ext[2]};
 #pragma unroll
   for (int l = L0; l < L1; l += 2) {
     const bool has0 = l < g.L, has1 = (l + 1 < L1) && (l + 1 < g.L);
     Corners c0, c1;
-    if (has0) level_corners(g, l, p, ob->half, ob->inv_ext, c0);
-    if (has1) level_corners(g, l + 1, p, ob->half, ob->inv_ext, c1);
+    if (has0) level_corners(g, l, p, hf, ie, c0);
+    if (has1) level_corners(g, l + 1, p, hf, ie, c1);
     __half2 v0[8], v1[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {

@@ -68,11 +68,7 @@ struct TileBufs {
   int valid[kT];
   int ray[kT];  // global ray index of the slot (-1 outside the tile's rays)
   int pfirst, nrays;  // first plan_perm index and number of the tile's rays
-  // dL/dencoding of the slots, feature-major (thread s owns column s), in H2's space: H2 is dead from the end of the
-  // backward until the next pair's forward writes it
-  __device__ float* dEs(int k) { return reinterpret_cast<float*>(H2) + k * kT; }
 };
-static_assert(32 * kT * sizeof(float) <= kT * kH * 2, "dL/dencoding fits in H2");
 
 // Encoding levels [l0, l1) of one sample, interpolated in FP32 from the FP16 table, into row s of a K-major BF16
 // encoding buffer; three levels per round so that 24 gathers are in flight (a gather window of 3 levels is one round).
@@ -80,6 +76,10 @@ template <int LFP, bool F16>
 __device__ __forceinline__ void gather_rows(const GridParams& g, const ObjectDev* ob, const float p[3],
                                             unsigned char* E, int s, int l0, int l1) {
   const __half2* tab = reinterpret_cast<const __half2*>(ob->table_h);
+  // the box in registers: the encoding stores below may alias global memory as far as the compiler knows, which would
+  // make every round reload it
+  const float hf[3] = {ob->half[0], ob->half[1], ob->half[2]};
+  const float ie[3] = {ob->inv_ext[0], ob->inv_ext[1], ob->inv_ext[2]};
 #pragma unroll 1
   for (int l = l0; l < l1; l += 3) {
     // the loads of three levels go out first; only the cells' fractions are kept while they are in flight and the
@@ -88,16 +88,16 @@ __device__ __forceinline__ void gather_rows(const GridParams& g, const ObjectDev
     int i0[3];
     float f0[3], f1[3], f2[3];
     __half2 v0[8], v1[8], v2[8];
-    level_cell(g, l, p, ob->half, ob->inv_ext, i0, f0);
+    level_cell(g, l, p, hf, ie, i0, f0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) v0[k] = __ldg(tab + g.off[l] + corner_index(g, l, i0, k));
     if (has1) {
-      level_cell(g, l + 1, p, ob->half, ob->inv_ext, i0, f1);
+      level_cell(g, l + 1, p, hf, ie, i0, f1);
 #pragma unroll
       for (int k = 0; k < 8; ++k) v1[k] = __ldg(tab + g.off[l + 1] + corner_index(g, l + 1, i0, k));
     }
     if (has2) {
-      level_cell(g, l + 2, p, ob->half, ob->inv_ext, i0, f2);
+      level_cell(g, l + 2, p, hf, ie, i0, f2);
 #pragma unroll
       for (int k = 0; k < 8; ++k) v2[k] = __ldg(tab + g.off[l + 2] + corner_index(g, l + 2, i0, k));
     }
@@ -136,6 +136,71 @@ template <int LFP>
 __device__ __forceinline__ void zero_rows(unsigned char* E, int s, int l0, int l1) {
 #pragma unroll 1
   for (int l = l0; l < l1; ++l) *reinterpret_cast<uint32_t*>(E + kmaj(s, 2 * l, LFP)) = 0u;
+}
+
+// Hash-gradient scatter of levels [0, L) of a tile's slots, one warp = 32 consecutive slots: slot s at p (valid),
+// its dL/dencoding (times unscale) read from TMEM columns de .. de + 2L - 1 of its lane.  Consecutive live samples
+// of a ray lie close together, so on the coarse levels runs of adjacent lanes fall in the same grid cell and update
+// the same eight corners.  The L1 spends about a cycle on every active lane of a reduction, same address or not, so
+// where enough lanes continue a run the runs are summed first (segmented suffix sums by shuffles, as many rounds as
+// the longest run needs) and only their first lanes issue the reductions; elsewhere every lane issues its own.  The
+// loop reads no memory: after the reductions' memory clobbers, a read of the object's box would be reissued every
+// level and wait behind the reductions already queued.
+__device__ __forceinline__ void scatter_levels(const GridParams& g, const ObjectDev* ob, int s, int L, const float p[3],
+                                               bool valid, uint32_t de, float unscale) {
+  constexpr uint32_t kAll = 0xffffffffu;
+  constexpr int kMinMerged = 4;  // lanes that must continue a run before a level is summed by shuffles
+  const int lane = s & 31;
+  const float hf[3] = {ob->half[0], ob->half[1], ob->half[2]};
+  const float ie[3] = {ob->inv_ext[0], ob->inv_ext[1], ob->inv_ext[2]};
+  float2* gt = reinterpret_cast<float2*>(ob->grad);
+#pragma unroll 1
+  for (int l = 0; l < L; ++l) {
+    float d0, d1;
+    tmem_ld2(de + 2u * (uint32_t)l, d0, d1);
+    tmem_wait_ld();
+    d0 = valid ? d0 * unscale : 0.f;
+    d1 = valid ? d1 * unscale : 0.f;
+    const bool act = d0 != 0.f || d1 != 0.f;
+    if (!__any_sync(kAll, act)) continue;
+    int i0[3];
+    float f[3];
+    level_cell(g, l, p, hf, ie, i0, f);
+    // run key: the cell (21 bits per axis); a lane without a contribution gets a key no other lane has
+    const unsigned long long key = act ? ((unsigned long long)(uint32_t)i0[0] |
+                                          ((unsigned long long)(uint32_t)i0[1] << 21) |
+                                          ((unsigned long long)(uint32_t)i0[2] << 42))
+                                       : ~0ull - (unsigned long long)lane;
+    const unsigned long long prev = __shfl_up_sync(kAll, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const uint32_t heads = __ballot_sync(kAll, head);
+    float a[16];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float w = corner_weight(f, k);
+      a[2 * k] = w * d0;
+      a[2 * k + 1] = w * d1;
+    }
+    const bool merge = __popc(~heads) >= kMinMerged;
+    if (merge) {
+      const uint32_t above = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);  // run heads after this lane
+      const int span = (above ? __ffs(above) - 2 : 31) - lane;                 // lanes after this one in its run
+      const int max_span = (int)__reduce_max_sync(kAll, (uint32_t)span);
+      for (int off = 1; off <= max_span; off <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float o = __shfl_down_sync(kAll, a[k], off);
+          if (off <= span) a[k] += o;
+        }
+      }
+    }
+    if (act && (head || !merge)) {
+      uint32_t idx[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) idx[k] = corner_index(g, l, i0, k);
+      scatter_sums(gt + g.off[l], idx, a);
+    }
+  }
 }
 
 template <int LFP, bool FP8, bool SN>
@@ -339,6 +404,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nwin = SN ? 2 + nl : 5;
   auto part = [&](int k) { return k * Lg / nwin; };
   int cur = 0;  // encoding buffer of the current pair
+  const uint32_t lt = tm + ((uint32_t)(32 * (warp & 3)) << 16);  // this thread's TMEM lane
   // columns past 2 L stay zero in both buffers
   for (int u = 0; u < 2; ++u) zero_rows<LFP>(tb.E[u], s, Lg, LMAX);
   if (nx.valid) {
@@ -359,10 +425,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tb.t[s] = nx.t;
     tb.dt[s] = nx.dt;
     if (nx_bi != bi) {
+      // the new object's weights are fetched first, so that their round trip overlaps the flush of the previous
+      // object's weight gradients (warps 0, 1, 4 and 5)
+      constexpr int kWB = (WeightIndex<LFP>::total + kTcThreads - 1) / kTcThreads;
+      float wv[kWB];
+      weights_fetch<LFP, kWB>(g, nx_ob->params, t, kTcThreads, wv);
       if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kTcThreads);
       bi = nx_bi;
       ob = nx_ob;
-      load_weights<LFP>(sm, g, ob->params, kTcThreads);
+      weights_store<LFP, kWB>(sm, g, t, kTcThreads, wv);
       if (FP8) load_w4_fp8(sm, g, ob->params, t, kTcThreads);
       if (SN && g.extra >= 2) load_w6(sm, g, ob->params, t, kTcThreads);
       acc_dw = 0;
@@ -680,7 +751,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1, f16), kk > 0);
+          mma(tm + kColDE + 32u * (uint32_t)u, desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk),
+              idesc(LFP, 0, 1, f16), kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
           mma(kColDW1 + tm, desc_mn(sm.tb[u].H1, kH, kk), desc_mn(sm.tb[u].E[cur], LFP, kk), idesc(LFP, 1, 1, f16),
@@ -697,26 +769,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (!(ok = wait_mma())) break;
     acc_dw = 1;
     {  // ---- 6. scatter dL/dencoding into the FP32 table gradient ----
-#pragma unroll
-      for (int c = 0; c < LFP / 16; ++c) {
-        float de[16];
-        tmem_ld16(tmp + 16 * c, de);
-        tmem_wait_ld();
-#pragma unroll
-        for (int k = 0; k < 16; ++k) tb.dEs(16 * c + k)[s] = f16 ? de[k] * gunscale : de[k];
-      }
-      if (tb.valid[s]) {
-        const float p[3] = {tb.px[0][s], tb.px[1][s], tb.px[2][s]};
-        float2* gt = reinterpret_cast<float2*>(ob->grad);
-#pragma unroll 1
-        for (int l = 0; l < Lg; ++l) {
-          const float d0 = tb.dEs(2 * l)[s], d1 = tb.dEs(2 * l + 1)[s];
-          if (d0 == 0.f && d1 == 0.f) continue;
-          Corners c;
-          level_corners(g, l, p, ob->half, ob->inv_ext, c);
-          scatter_corners(gt + g.off[l], c.idx, c.w, d0, d1);
-        }
-      }
+      const float p[3] = {tb.px[0][s], tb.px[1][s], tb.px[2][s]};
+      scatter_levels(g, ob, s, Lg, p, tb.valid[s] != 0, lt + kColDE + 32u * (uint32_t)wg, gunscale);
     }
     cur ^= 1;  // the next pair's encoding is in the other buffer
     tc_before();
