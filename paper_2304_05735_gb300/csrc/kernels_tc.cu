@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_plan_rays(GridParams g, BatchDesc b, Ra
     const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
     float* o = R.out + 6 * r;
     o[0] = bg0; o[1] = bg1; o[2] = bg2; o[3] = 0.f; o[4] = 0.f; o[5] = 0.f;
-    const RayLoss q = ray_loss(g, R, r, bg0, bg1, bg2, 0.f, 0.f, bg0, bg1, bg2, 1.0f / (float)n_obj);
+    const RayLoss q = ray_loss(g, ray_target(R, r), bg0, bg1, bg2, 0.f, 0.f, 1.0f / (float)n_obj);
     add_ray_loss(dyn, bi, q, nullptr);
   }
 }

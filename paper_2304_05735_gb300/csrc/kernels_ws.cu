@@ -288,12 +288,8 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
     bar_compute();
     // ---- compositing, losses, adjoint: one warp per ray ----
     {
-      const int nr = sl.nrays;
-      for (int j = warp; j < nr; j += kCompute / 32) {
-        const int pi = sl.pfirst + j;
-        const int64_t r = b.plan_perm[pi];
-        composite_ray(sl, g, b, R, dyn, bi, r, b.plan_rstart[pi], (int)R.count[r], invB, status);
-      }
+      auto tile_of = [&](int) -> WsSlot<LFP>& { return sl; };
+      composite_rays(tile_of, sl.nrays, sl.nrays, warp, kCompute / 32, g, b, R, dyn, bi, invB, status);
     }
     bar_compute();
     // ---- backward ----

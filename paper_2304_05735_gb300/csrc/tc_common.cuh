@@ -293,27 +293,41 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Per-ray inputs of the losses of Eq. 7-11: background colour (the random colour of Eq. 8), target colour, sparse
+// depth (NaN without one) and class.
+struct RayTarget {
+  float bg0, bg1, bg2, t0, t1, t2, dep;
+  int cls;
+};
+__device__ __forceinline__ RayTarget ray_target(const RayBuf& R, int64_t r) {
+  RayTarget q;
+  q.bg0 = R.bg[3 * r]; q.bg1 = R.bg[3 * r + 1]; q.bg2 = R.bg[3 * r + 2];
+  q.t0 = R.rgb[3 * r]; q.t1 = R.rgb[3 * r + 1]; q.t2 = R.rgb[3 * r + 2];
+  q.dep = R.depth[r];
+  q.cls = R.cls[r];
+  return q;
+}
+
 // Losses of Eq. 7-11 of one ray from its rendered colour and depth (every term divided by the batch size B through
 // invB in the gradients; the sums are accumulated unscaled).
 struct RayLoss {
   float loss, l_rgb, l_rr, l_dep, l_den;
   float gC0, gC1, gC2, gD, gdir;
 };
-__device__ __forceinline__ RayLoss ray_loss(const GridParams& g, const RayBuf& R, int64_t r, float Ch0, float Ch1,
-                                            float Ch2, float Dh, float ssum, float bg0, float bg1, float bg2,
-                                            float invB) {
+__device__ __forceinline__ RayLoss ray_loss(const GridParams& g, const RayTarget& tg, float Ch0, float Ch1, float Ch2,
+                                            float Dh, float ssum, float invB) {
   RayLoss q{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int cls = R.cls[r];
+  const int cls = tg.cls;
   if (cls != kClsOccluder) {
-    const float t0 = cls == kClsObject ? R.rgb[3 * r] : bg0;
-    const float t1 = cls == kClsObject ? R.rgb[3 * r + 1] : bg1;
-    const float t2 = cls == kClsObject ? R.rgb[3 * r + 2] : bg2;
+    const float t0 = cls == kClsObject ? tg.t0 : tg.bg0;
+    const float t1 = cls == kClsObject ? tg.t1 : tg.bg1;
+    const float t2 = cls == kClsObject ? tg.t2 : tg.bg2;
     const float e0 = Ch0 - t0, e1 = Ch1 - t1, e2 = Ch2 - t2;
     const float sq = e0 * e0 + e1 * e1 + e2 * e2;
     q.loss += sq;
     if (cls == kClsObject) q.l_rgb = sq; else q.l_rr = sq;
     q.gC0 = 2.f * e0 * invB; q.gC1 = 2.f * e1 * invB; q.gC2 = 2.f * e2 * invB;
-    const float dep = R.depth[r];
+    const float dep = tg.dep;
     if (isfinite(dep)) {
       const float e = Dh - dep;
       q.loss += g.lambda1 * fabsf(e);
@@ -340,10 +354,10 @@ __device__ __forceinline__ void add_ray_loss(BatchDyn* dyn, int bi, const RayLos
 
 // Eq. 6 + Eq. 7-11 + adjoint for one ray whose samples occupy slots [base, base + P) of the tile.
 template <class Bufs>
-__device__ void composite_ray(Bufs& sm, const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
-                              int bi, int64_t r, int base, int P, float invB, int32_t* status) {
+__device__ void composite_ray(Bufs& sm, const GridParams& g, RayBuf R, BatchDyn* dyn, int bi, int64_t r, int base,
+                              int P, const RayTarget& tg, float invB, int32_t* status) {
   const int lane = threadIdx.x & 31;
-  const float bg0 = R.bg[3 * r], bg1 = R.bg[3 * r + 1], bg2 = R.bg[3 * r + 2];
+  const float bg0 = tg.bg0, bg1 = tg.bg1, bg2 = tg.bg2;
   float carry = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dh = 0.f, ssum = 0.f;
   for (int c = 0; c < P; c += 32) {
     const int j = c + lane;
@@ -374,7 +388,7 @@ __device__ void composite_ray(Bufs& sm, const GridParams& g, const BatchDesc& b,
     o[0] = Ch0; o[1] = Ch1; o[2] = Ch2; o[3] = Dh; o[4] = -expm1f(-carry); o[5] = ssum;
   }
   // losses of Eq. 7-11 (every term divided by the batch size B)
-  const RayLoss q = ray_loss(g, R, r, Ch0, Ch1, Ch2, Dh, ssum, bg0, bg1, bg2, invB);
+  const RayLoss q = ray_loss(g, tg, Ch0, Ch1, Ch2, Dh, ssum, invB);
   if (lane == 0) add_ray_loss(dyn, bi, q, status);
   const float gC0 = q.gC0, gC1 = q.gC1, gC2 = q.gC2, gD = q.gD, gdir = q.gdir;
   // adjoint, chunks in reverse order
@@ -408,6 +422,42 @@ __device__ void composite_ray(Bufs& sm, const GridParams& g, const BatchDesc& b,
     SC1 += __shfl_sync(0xffffffffu, s1, 0);
     SC2 += __shfl_sync(0xffffffffu, s2, 0);
     SD += __shfl_sync(0xffffffffu, s3, 0);
+  }
+}
+
+// Compositing, losses and adjoint of the rays of up to two tiles (rays j < nr0 in tile_of(0), the others in
+// tile_of(1)), ray j by warp j mod nwarps.  Lane k of a warp first fetches the plan entry and targets of the warp's
+// k-th ray, so that all of a warp's fetches are in flight together instead of three dependent round trips per ray.
+template <class TileOf>
+__device__ __forceinline__ void composite_rays(TileOf tile_of, int nr0, int nr_all, int warp, int nwarps,
+                                               const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
+                                               int bi, float invB, int32_t* status) {
+  constexpr uint32_t kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  for (int k0 = 0; warp + nwarps * k0 < nr_all; k0 += 32) {
+    const int j = warp + nwarps * (k0 + lane);
+    int u = 0, r = 0, base = 0, P = 0;
+    RayTarget tg{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kClsOccluder};
+    if (j < nr_all) {
+      u = j < nr0 ? 0 : 1;
+      const int pi = tile_of(u).pfirst + (j < nr0 ? j : j - nr0);
+      r = b.plan_perm[pi];
+      base = b.plan_rstart[pi];
+      P = (int)R.count[r];
+      tg = ray_target(R, r);
+    }
+    const int rem = (nr_all - 1 - warp) / nwarps + 1 - k0;  // this warp's rays from k0 on
+    const int n = rem < 32 ? rem : 32;
+    for (int k = 0; k < n; ++k) {
+      const int uk = __shfl_sync(kAll, u, k), rk = __shfl_sync(kAll, r, k);
+      const int bk = __shfl_sync(kAll, base, k), pk = __shfl_sync(kAll, P, k);
+      RayTarget tk;
+      tk.bg0 = __shfl_sync(kAll, tg.bg0, k); tk.bg1 = __shfl_sync(kAll, tg.bg1, k);
+      tk.bg2 = __shfl_sync(kAll, tg.bg2, k); tk.t0 = __shfl_sync(kAll, tg.t0, k);
+      tk.t1 = __shfl_sync(kAll, tg.t1, k); tk.t2 = __shfl_sync(kAll, tg.t2, k);
+      tk.dep = __shfl_sync(kAll, tg.dep, k); tk.cls = __shfl_sync(kAll, tg.cls, k);
+      composite_ray(tile_of(uk), g, R, dyn, bi, rk, bk, pk, tk, invB, status);
+    }
   }
 }
 

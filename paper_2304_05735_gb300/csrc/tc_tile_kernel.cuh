@@ -581,12 +581,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- 4. compositing, losses, adjoint: one warp per ray of the pair -----------------------------------------
     {
       const int nr0 = sm.tb[0].nrays, nr_all = nr0 + sm.tb[1].nrays;
-      for (int j = warp; j < nr_all; j += kTcThreads / 32) {
-        const int u = j < nr0 ? 0 : 1, jr = j < nr0 ? j : j - nr0;
-        const int pi = sm.tb[u].pfirst + jr;
-        const int64_t r = b.plan_perm[pi];
-        composite_ray(sm.tb[u], g, b, R, dyn, bi, r, b.plan_rstart[pi], (int)R.count[r], invB, status);
-      }
+      auto tile_of = [&](int u) -> TileBufs<LFP>& { return sm.tb[u]; };
+      composite_rays(tile_of, nr0, nr_all, warp, kTcThreads / 32, g, b, R, dyn, bi, invB, status);
     }
     __syncthreads();
     // ---- 5. backward -----------------------------------------------------------------------------------------------
