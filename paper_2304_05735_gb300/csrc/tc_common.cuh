@@ -220,11 +220,14 @@ __device__ __forceinline__ void red_add4f(float* addr, float a, float b, float c
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 // Adds TMEM columns [c0, c0 + ncols) of this thread's lane (row o of a weight gradient when valid), times scale, to
-// row[0 .. in): columns in 16-column blocks, the blocks dealt to the nh flushing warps of the same lanes (half h).
-// tcgen05.ld is warp-collective, so every lane loads and only the valid rows add.
+// row[0 .. in): columns in 16-column blocks, the blocks dealt to the nh flushing warps of the same lanes (half h),
+// starting at block rot (mod the block count).  tcgen05.ld is warp-collective, so every lane loads and only the valid
+// rows add.
 __device__ __forceinline__ void flush_rows(uint32_t lane_taddr, uint32_t c0, int ncols, bool valid, float* row, int in,
-                                           float scale, int h, int nh) {
-  for (int blk = h; blk * 16 < ncols; blk += nh) {
+                                           float scale, int h, int nh, int rot) {
+  const int nblk = ncols / 16;
+  for (int i = h; i < nblk; i += nh) {
+    const int blk = (i + rot) % nblk;
     float v[16];
     tmem_ld16(lane_taddr + c0 + 16u * (uint32_t)blk, v);
     tmem_wait_ld();
@@ -247,7 +250,9 @@ __device__ __forceinline__ void flush_rows(uint32_t lane_taddr, uint32_t c0, int
 }
 // Adds the TMEM weight-gradient accumulators of one object, times scale (the inverse of the FP16 path's gradient
 // scale, else 1), to its FP32 gradient.  Rows 0..63 live in TMEM lanes 0..63, which warps w with w % 4 < 2 can read;
-// with nthreads >= 256 warps 0, 1, 4 and 5 share the work (warps 4 and 5 take every other 16-column block).
+// with nthreads >= 256 warps 0, 1, 4 and 5 share the work (warps 4 and 5 take every other 16-column block).  Every CTA
+// that finishes an object flushes the same few kilobytes at about the same time, so each CTA starts at a different
+// matrix and column block: the reductions of different CTAs then mostly meet different L2 lines.
 template <int LFP>
 __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad, float scale, int nthreads) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -257,18 +262,25 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
   const int h = (w >> 2) & (nh - 1);
   const uint32_t lt = tm + ((uint32_t)(32 * q) << 16);
   const int o = 32 * q + lane;  // output row of this lane
-  // density output layer [16][64] (the hidden layer feeding it: H1, or the single network's last hidden layer)
-  if (q == 0) flush_rows(lt, kColDW2, kH, o < 16, grad + g.mlp_off[1] + o * kH, kH, scale, h, nh);
-  // first layer [64][LF]
-  flush_rows(lt, kColDW1, LFP, true, grad + g.mlp_off[0] + o * g.LF, g.LF, scale, h, nh);
-  if (g.single_net) {  // hidden layers 2 and 3 [64][64] in the DW4 and DW3 columns
-    for (int x = 0; x < g.extra; ++x)
-      flush_rows(lt, x == 0 ? kColDW4 : kColDW3, kH, true, grad + g.mlp_off[5 + x] + o * kH, kH, scale, h, nh);
-    return;
+  const int rot = (int)blockIdx.x;
+  const int nmat = g.single_net ? 2 + g.extra : 5;
+  for (int i = 0; i < nmat; ++i) {
+    const int m = (i + rot) % nmat;
+    if (m == 0) {  // first layer [64][LF]
+      flush_rows(lt, kColDW1, LFP, true, grad + g.mlp_off[0] + o * g.LF, g.LF, scale, h, nh, rot);
+    } else if (m == 1) {  // density output layer [16][64] (fed by H1, or the single network's last hidden layer)
+      if (q == 0) flush_rows(lt, kColDW2, kH, o < 16, grad + g.mlp_off[1] + o * kH, kH, scale, h, nh, rot);
+    } else if (g.single_net) {  // hidden layers 2 and 3 [64][64] in the DW4 and DW3 columns
+      const int x = m - 2;
+      flush_rows(lt, x == 0 ? kColDW4 : kColDW3, kH, true, grad + g.mlp_off[5 + x] + o * kH, kH, scale, h, nh, rot);
+    } else if (m == 2) {  // colour input [64][cin]
+      flush_rows(lt, kColDW3, 32, true, grad + g.mlp_off[2] + o * g.cin, g.cin, scale, h, nh, rot);
+    } else if (m == 3) {  // [64][64]
+      flush_rows(lt, kColDW4, kH, true, grad + g.mlp_off[3] + o * kH, kH, scale, h, nh, rot);
+    } else if (q == 0) {  // colour output [3][64]
+      flush_rows(lt, kColDW5, kH, o < 3, grad + g.mlp_off[4] + o * kH, kH, scale, h, nh, rot);
+    }
   }
-  flush_rows(lt, kColDW3, 32, true, grad + g.mlp_off[2] + o * g.cin, g.cin, scale, h, nh);  // colour input [64][cin]
-  flush_rows(lt, kColDW4, kH, true, grad + g.mlp_off[3] + o * kH, kH, scale, h, nh);         // [64][64]
-  if (q == 0) flush_rows(lt, kColDW5, kH, o < 3, grad + g.mlp_off[4] + o * kH, kH, scale, h, nh);  // [3][64]
 }
 
 __device__ __forceinline__ float warp_incl_prefix(float v, int lane) {
@@ -354,8 +366,8 @@ __device__ __forceinline__ void add_ray_loss(BatchDyn* dyn, int bi, const RayLos
 
 // Eq. 6 + Eq. 7-11 + adjoint for one ray whose samples occupy slots [base, base + P) of the tile.
 template <class Bufs>
-__device__ void composite_ray(Bufs& sm, const GridParams& g, RayBuf R, BatchDyn* dyn, int bi, int64_t r, int base,
-                              int P, const RayTarget& tg, float invB, int32_t* status) {
+__device__ RayLoss composite_ray(Bufs& sm, const GridParams& g, RayBuf R, int64_t r, int base, int P,
+                                 const RayTarget& tg, float invB) {
   const int lane = threadIdx.x & 31;
   const float bg0 = tg.bg0, bg1 = tg.bg1, bg2 = tg.bg2;
   float carry = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dh = 0.f, ssum = 0.f;
@@ -389,7 +401,6 @@ __device__ void composite_ray(Bufs& sm, const GridParams& g, RayBuf R, BatchDyn*
   }
   // losses of Eq. 7-11 (every term divided by the batch size B)
   const RayLoss q = ray_loss(g, tg, Ch0, Ch1, Ch2, Dh, ssum, invB);
-  if (lane == 0) add_ray_loss(dyn, bi, q, status);
   const float gC0 = q.gC0, gC1 = q.gC1, gC2 = q.gC2, gD = q.gD, gdir = q.gdir;
   // adjoint, chunks in reverse order
   float SC0 = 0.f, SC1 = 0.f, SC2 = 0.f, SD = 0.f;
@@ -423,17 +434,20 @@ __device__ void composite_ray(Bufs& sm, const GridParams& g, RayBuf R, BatchDyn*
     SC2 += __shfl_sync(0xffffffffu, s2, 0);
     SD += __shfl_sync(0xffffffffu, s3, 0);
   }
+  return q;
 }
 
 // Compositing, losses and adjoint of the rays of up to two tiles (rays j < nr0 in tile_of(0), the others in
 // tile_of(1)), ray j by warp j mod nwarps.  Lane k of a warp first fetches the plan entry and targets of the warp's
-// k-th ray, so that all of a warp's fetches are in flight together instead of three dependent round trips per ray.
+// k-th ray, so that all of a warp's fetches are in flight together instead of three dependent round trips per ray;
+// the warp's loss terms go to the object's sums in one set of atomics.
 template <class TileOf>
 __device__ __forceinline__ void composite_rays(TileOf tile_of, int nr0, int nr_all, int warp, int nwarps,
                                                const GridParams& g, const BatchDesc& b, RayBuf R, BatchDyn* dyn,
                                                int bi, float invB, int32_t* status) {
   constexpr uint32_t kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  RayLoss sum{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // this warp's loss terms, added once at the end
   for (int k0 = 0; warp + nwarps * k0 < nr_all; k0 += 32) {
     const int j = warp + nwarps * (k0 + lane);
     int u = 0, r = 0, base = 0, P = 0;
@@ -456,9 +470,11 @@ __device__ __forceinline__ void composite_rays(TileOf tile_of, int nr0, int nr_a
       tk.bg2 = __shfl_sync(kAll, tg.bg2, k); tk.t0 = __shfl_sync(kAll, tg.t0, k);
       tk.t1 = __shfl_sync(kAll, tg.t1, k); tk.t2 = __shfl_sync(kAll, tg.t2, k);
       tk.dep = __shfl_sync(kAll, tg.dep, k); tk.cls = __shfl_sync(kAll, tg.cls, k);
-      composite_ray(tile_of(uk), g, R, dyn, bi, rk, bk, pk, tk, invB, status);
+      const RayLoss q = composite_ray(tile_of(uk), g, R, rk, bk, pk, tk, invB);
+      sum.loss += q.loss; sum.l_rgb += q.l_rgb; sum.l_rr += q.l_rr; sum.l_dep += q.l_dep; sum.l_den += q.l_den;
     }
   }
+  if (lane == 0 && warp < nr_all) add_ray_loss(dyn, bi, sum, status);
 }
 
 // Hash encoding of levels [L0, L1) of one sample from the FP16 table, two levels per round so that 16 gathers are
