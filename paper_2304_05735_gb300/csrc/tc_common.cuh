@@ -561,30 +561,35 @@ __device__ __forceinline__ SlotSample plan_sample(const GridParams& g, const Bat
   const int r = e.x;
   if (!ROMAP_IN_BOUNDS(r >= b.ray_base[bi] && r < b.ray_base[bi + 1] && e.y >= 0, g.status)) return q;
   q.ray = r;
+  // everything the sample needs from the ray, loaded at once (one round trip after the slot's)
+  const uint4 m4 = *reinterpret_cast<const uint4*>(R.mask + 4 * (int64_t)r);
+  const uint32_t cnt = R.count[r];
+  const float tn = R.tn[r], tf = R.tf[r];
+  const float o0 = R.o[3 * r], o1 = R.o[3 * r + 1], o2 = R.o[3 * r + 2];
+  const float d0 = R.d[3 * r], d1 = R.d[3 * r + 1], d2 = R.d[3 * r + 2];
   int j = e.y;
-  if ((uint32_t)j >= R.count[r]) return q;
-  int i = 0;
-#pragma unroll 1
-  for (int wd = 0; wd < 4; ++wd) {
-    const uint32_t m = R.mask[4 * (int64_t)r + wd];
-    const int c = __popc(m);
-    if (j < c) {
-      i = 32 * wd + nth_set_bit(m, j);
-      break;
+  if ((uint32_t)j >= cnt) return q;
+  // candidate index of the j-th live candidate: its mask word, then its bit
+  uint32_t m = m4.x;
+  int wd = 0;
+  if (j >= __popc(m)) {
+    j -= __popc(m); m = m4.y; wd = 1;
+    if (j >= __popc(m)) {
+      j -= __popc(m); m = m4.z; wd = 2;
+      if (j >= __popc(m)) { j -= __popc(m); m = m4.w; wd = 3; }
     }
-    j -= c;
   }
+  const int i = 32 * wd + nth_set_bit(m, j);
   const int N = g.n_samples;
   const int rl = r - b.ray_base[bi];
-  const float tn = R.tn[r], tf = R.tf[r];
   const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
   const uint32_t step = ob->step;
   q.t = candidate_t(tn, step_len, i, ob->key0, ob->key1, step, (uint32_t)rl, 1);
   const float tnext = (i + 1 < N) ? candidate_t(tn, step_len, i + 1, ob->key0, ob->key1, step, (uint32_t)rl, 1) : tf;
   q.dt = __fsub_rn(tnext, q.t);
-  q.x = __fadd_rn(R.o[3 * r], __fmul_rn(q.t, R.d[3 * r]));
-  q.y = __fadd_rn(R.o[3 * r + 1], __fmul_rn(q.t, R.d[3 * r + 1]));
-  q.z = __fadd_rn(R.o[3 * r + 2], __fmul_rn(q.t, R.d[3 * r + 2]));
+  q.x = __fadd_rn(o0, __fmul_rn(q.t, d0));
+  q.y = __fadd_rn(o1, __fmul_rn(q.t, d1));
+  q.z = __fadd_rn(o2, __fmul_rn(q.t, d2));
   q.valid = 1;
   return q;
 }
