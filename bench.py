@@ -177,7 +177,8 @@ DTYPES = {"mixed": "bf16 (MLP GEMM operands; FP16 table copy; FP32 accumulation,
                  "Adam)"}
 KERNEL_SOURCES = {
     "fp32": ("kernels_tile.cu", "device_common.cuh", "romap_internal.cuh"),
-    "mixed": ("tc_tile_kernel.cuh", "kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
+    "mixed": ("tc_tile_kernel.cuh", "kernels_tc.cu", "kernels_tc1.cu", "tc_common.cuh", "device_common.cuh",
+              "romap_internal.cuh"),
     "fp8": ("tc_tile_kernel.cuh", "kernels_tc.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
     "fp16": ("tc_tile_kernel.cuh", "kernels_tc16.cu", "tc_common.cuh", "device_common.cuh", "romap_internal.cuh"),
 }
@@ -428,9 +429,9 @@ def run_ours(args):
     autotune = None
     if main_prec != "fp32":
         chosen = C.c_int32()
-        tms = (C.c_float * 8)()
-        names = C.create_string_buffer(1024)
-        R.check(R.romap_autotune_report(h, C.byref(chosen), tms, 8, names, 1024))
+        tms = (C.c_float * 12)()
+        names = C.create_string_buffer(2048)
+        R.check(R.romap_autotune_report(h, C.byref(chosen), tms, 12, names, 2048))
         cands = names.value.decode().split(";")
         autotune = {"chosen": cands[chosen.value] if chosen.value >= 0 else None,
                     "ms_per_launch": {c: float(tms[i]) for i, c in enumerate(cands)}}

@@ -468,9 +468,11 @@ ROMAP_API romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_
  * kernels with the plan interleaved over the CTAs (CTA c takes every
  * grid-th pair or tile from c, so all CTAs work on the same few objects at
  * a time); 4, 5 and 6, 7 = interleaved in chunks of 2 and 4 consecutive
- * pairs or tiles (longer runs of one object per CTA).  Odd indices are the
- * warp-specialized kernel: ROMAP_ERR_UNSUPPORTED for them under
- * ROMAP_PREC_MIXED_FP8 or single_net (both run on the lockstep kernel). */
+ * pairs or tiles (longer runs of one object per CTA); 8, 9, 10, 11 = the
+ * lockstep kernel on single tiles of 128 slots, two CTAs per SM, with the
+ * contiguous, interleaved, by-2 and by-4 orders.  Only 0, 2, 4 and 6 run
+ * ROMAP_PREC_MIXED_FP8 or the single_net model: ROMAP_ERR_UNSUPPORTED for
+ * the others there. */
 ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);
 ROMAP_API romap_status romap_autotune_report(romap_ctx* ctx, int32_t* chosen, float* ms, int32_t n, char* names,
                                              size_t names_len);

@@ -65,14 +65,14 @@ void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayB
   if (g.f16) {  // FP16 operands: instances in kernels_tc16.cu (never combined with FP8)
     launch_tile_tc_f16(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
   } else if (g.fp8) {  // (the single-network model is never combined with FP8)
-    if (g.LF <= 16) launch_tc_t<16, true, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
-    else launch_tc_t<32, true, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    if (g.LF <= 16) launch_tc_t<16, true, false, false, 2>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_tc_t<32, true, false, false, 2>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
   } else if (g.single_net) {
-    if (g.LF <= 16) launch_tc_t<16, false, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
-    else launch_tc_t<32, false, true, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    if (g.LF <= 16) launch_tc_t<16, false, true, false, 2>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_tc_t<32, false, true, false, 2>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
   } else {
-    if (g.LF <= 16) launch_tc_t<16, false, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
-    else launch_tc_t<32, false, false, false>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    if (g.LF <= 16) launch_tc_t<16, false, false, false, 2>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
+    else launch_tc_t<32, false, false, false, 2>(g, b, dyn, r, status, max_tiles, n_ctas, interleave, stream);
   }
 }
 

@@ -317,11 +317,11 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       store8(sl.DL, s, 1, 16, dl + 8, f16);
     }
     sync_then_issue();
-    if (s == 0) {  // dH3 = DL W5 ; dW5 += DL^T H3
+    if (s == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
       mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW5 + tm, desc_mn(sl.DL, 16, kk), desc_mn(sl.H3, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
+        mma(kColDW5 + tm, desc_mn(sl.H3, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;
@@ -358,11 +358,11 @@ __device__ void compute_role(WsSmem<LFP>& sm, const GridParams& g, const BatchDe
       store8(sl.DL, s, 1, 16, d + 8, f16);
     }
     sync_then_issue();
-    if (s == 0) {  // dH1 = dOUT W2 ; dW2 += dOUT^T H1
+    if (s == 0) {  // dH1 = dOUT W2 ; dW2^T += H1^T dOUT
       mma(dtmp, desc_k(sl.DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma(kColDW2 + tm, desc_mn(sl.DL, 16, kk), desc_mn(sl.H1, kH, kk), idesc(64, 1, 1, f16), kk > 0 ? 1u : acc_dw);
+        mma(kColDW2 + tm, desc_mn(sl.H1, kH, kk), desc_mn(sl.DL, 16, kk), idesc(16, 1, 1, f16), kk > 0 ? 1u : acc_dw);
       mma_commit(&sm.mma_bar);
     }
     if (!wait_mma()) break;

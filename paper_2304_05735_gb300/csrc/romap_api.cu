@@ -136,7 +136,7 @@ struct romap_ctx {
   int64_t launches = 0;
   // autotuned choice of the mixed-precision tile kernel: -1 until tuned, then an index of kTileKernels
   int tile_kernel = -1;
-  float tile_kernel_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float tile_kernel_ms[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // CUDA graphs of one training step, one per batch composition (captured on cap_stream, replayed on stream), least
   // recently used first out beyond kMaxStepGraphs
   struct StepGraph {
@@ -586,10 +586,11 @@ romap_status run_sampling(romap_ctx* ctx, const BatchDesc& b, RayBuf R, SampleBu
 
 int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
 
-// Candidate fused tile kernels of the mixed path (same results, different schedules): the two kernels, each with
-// contiguous per-CTA ranges of the tile plan or with the plan dealt round-robin over the CTAs in chunks of 1, 2 or 4
-// work items (tile pairs of the lockstep kernel, tiles of the warp-specialized one).  Even indices are the lockstep
-// kernel, the only one with the FP8 and single-network variants.
+// Candidate fused tile kernels of the mixed path (same results, different schedules): the lockstep kernel on tile
+// pairs (one CTA per SM) and the warp-specialized kernel (0..7, even and odd indices), then the lockstep kernel on
+// single tiles with two CTAs per SM (8..11), each with contiguous per-CTA ranges of the tile plan or with the plan
+// dealt round-robin over the CTAs in chunks of 1, 2 or 4 work items (tile pairs, or tiles).  Only the tile-pair
+// lockstep kernel has the FP8 and single-network variants.
 typedef void (*TileKernelFn)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int,
                              cudaStream_t);
 template <void (*F)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int, int, cudaStream_t),
@@ -601,13 +602,20 @@ void launch_tile_order(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, R
 const TileKernelFn kTileKernels[] = {launch_tile_order<launch_tile_tc, 0>, launch_tile_order<launch_tile_ws, 0>,
                                      launch_tile_order<launch_tile_tc, 1>, launch_tile_order<launch_tile_ws, 1>,
                                      launch_tile_order<launch_tile_tc, 2>, launch_tile_order<launch_tile_ws, 2>,
-                                     launch_tile_order<launch_tile_tc, 4>, launch_tile_order<launch_tile_ws, 4>};
+                                     launch_tile_order<launch_tile_tc, 4>, launch_tile_order<launch_tile_ws, 4>,
+                                     launch_tile_order<launch_tile_tc1, 0>, launch_tile_order<launch_tile_tc1, 1>,
+                                     launch_tile_order<launch_tile_tc1, 2>, launch_tile_order<launch_tile_tc1, 4>};
 const char* const kTileKernelNames[] = {"lockstep tile pairs", "warp-specialized", "lockstep tile pairs, interleaved",
                                         "warp-specialized, interleaved", "lockstep tile pairs, interleaved by 2",
                                         "warp-specialized, interleaved by 2", "lockstep tile pairs, interleaved by 4",
-                                        "warp-specialized, interleaved by 4"};
-constexpr int kNumTileKernels = 8;
-bool lockstep_kernel(int k) { return k % 2 == 0; }
+                                        "warp-specialized, interleaved by 4", "lockstep single tiles, 2 CTAs per SM",
+                                        "lockstep single tiles, 2 CTAs per SM, interleaved",
+                                        "lockstep single tiles, 2 CTAs per SM, interleaved by 2",
+                                        "lockstep single tiles, 2 CTAs per SM, interleaved by 4"};
+constexpr int kNumTileKernels = 12;
+static_assert(sizeof(kTileKernels) / sizeof(kTileKernels[0]) == kNumTileKernels, "candidate table");
+// the candidates with the FP8 and single-network variants (the tile-pair lockstep kernel)
+bool lockstep_kernel(int k) { return k < 8 && k % 2 == 0; }
 
 // Sampling stage of the mixed path: ray draw + slab + live counts and masks, the per-object scan (live-sample
 // counter, loss reset) with the tile plan, and the placement of every ray in the plan.  Samples are formed inside the
@@ -1864,9 +1872,9 @@ romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index) {
   ROMAP_TRY(check_ctx(ctx));
   if (index < -1 || index >= kNumTileKernels) return fail(ROMAP_ERR_INVALID_ARG, "tile kernel %d out of range", index);
   if (ctx->g.fp8 && index >= 0 && !lockstep_kernel(index))
-    return fail(ROMAP_ERR_UNSUPPORTED, "the FP8 precision runs on the lockstep tile kernels (0, 2) only");
+    return fail(ROMAP_ERR_UNSUPPORTED, "the FP8 precision runs on the tile-pair lockstep kernels (0, 2, 4, 6) only");
   if (ctx->g.single_net && index >= 0 && !lockstep_kernel(index))
-    return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model runs on the lockstep tile kernels (0, 2) only");
+    return fail(ROMAP_ERR_UNSUPPORTED, "the single-network model runs on the tile-pair lockstep kernels (0, 2, 4, 6) only");
   ctx->tile_kernel = index;
   drop_graph(ctx);
   return ROMAP_OK;

@@ -304,6 +304,9 @@ void launch_plan_patterns(const BatchDesc& b, cudaStream_t stream);
 // work on the same few objects at a time (their tables and gradients then stay in L2).
 void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                     int total_tiles, int n_ctas, int interleave, cudaStream_t stream);
+// launch_tile_tc with one tile per CTA and two CTAs per SM (BF16 or FP16 operands, two-network model only)
+void launch_tile_tc1(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
+                     int max_tiles, int n_ctas, int interleave, cudaStream_t stream);
 // the FP16-operand instances of launch_tile_tc
 void launch_tile_tc_f16(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                         int total_tiles, int n_ctas, int interleave, cudaStream_t stream);
@@ -323,6 +326,15 @@ inline void set_smem_attr(K* kernel, int bytes, std::atomic<uint64_t>& done) {
   if (bit && (done.load(std::memory_order_acquire) & bit)) return;
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && bit)
     done.fetch_or(bit, std::memory_order_acq_rel);
+}
+
+template <class K>
+inline void set_func_attr(K* kernel, cudaFuncAttribute attr, int value, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  if (cudaFuncSetAttribute(kernel, attr, value) == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
 // status word bits written by the kernels

@@ -15,15 +15,14 @@ namespace tc {
 
 constexpr int kT = 128;           // samples per tile (MMA M)
 constexpr int kTmemCols = 512;
-// TMEM columns: weight-gradient accumulators (shared by the tiles of a pair), then one 64-column temporary per tile.
-// A weight gradient dW [out][in] accumulates with its output rows o in TMEM lanes (M = out, padded to 128) and its
-// inputs in columns: dW1 LFP columns, dW3 32 (the colour input; 64 for the single network's hidden layer 3), dW2, dW4
-// and dW5 64 each.  A lane then holds a contiguous row of the FP32 gradient, which the flush adds with 16-byte vector
-// reductions.
-constexpr uint32_t kColDW1 = 0, kColDW3 = 32, kColDW2 = 96, kColDW4 = 160, kColDW5 = 224, kColTmp = 288;
-// The fused kernel's dL/dencoding of each tile (up to 32 columns), read by the scatter.
-constexpr uint32_t kColDE = 416;
-static_assert(kColDE + 64 <= 512, "TMEM columns of the fused kernel");
+// TMEM columns: weight-gradient accumulators (shared by the tiles of a CTA), then one 64-column temporary per tile.
+// dW1, dW3 and dW4 accumulate with their output rows in TMEM lanes (M = out, padded to 128) and their inputs in
+// columns (dW1: LFP columns, dW3: 32, or 64 for the single network's hidden layer 3, dW4: 64), so that a lane holds a
+// contiguous row of the FP32 gradient, flushed with 16-byte reductions; dW2 and dW5 (16 and 3 outputs of 64 inputs)
+// accumulate transposed, inputs in lanes and 16 output columns each, flushed with reductions that are contiguous
+// across lanes.  192 columns of accumulators plus 64 per tile: 256 for a one-tile CTA (two CTAs per SM), 320 of 512
+// for a tile pair.
+constexpr uint32_t kColDW1 = 0, kColDW3 = 32, kColDW2 = 96, kColDW4 = 112, kColDW5 = 176, kColTmp = 192;
 constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -248,11 +247,24 @@ __device__ __forceinline__ void flush_rows(uint32_t lane_taddr, uint32_t c0, int
     }
   }
 }
+// Adds TMEM columns c0 .. c0 + nout - 1 of this thread's lane (input k of a transposed weight gradient), times
+// scale, to col[o * 64] for output o (col = the gradient of output 0 at input k): a warp's lanes add 32 consecutive
+// floats per output.  The 16 columns are loaded once; flushing warp h of nh takes every nh-th output.
+__device__ __forceinline__ void flush_cols(uint32_t lane_taddr, uint32_t c0, int nout, float* col, float scale, int h,
+                                           int nh) {
+  float v[16];
+  tmem_ld16(lane_taddr + c0, v);
+  tmem_wait_ld();
+#pragma unroll
+  for (int o = 0; o < 16; ++o)
+    if (o < nout && o % nh == h && v[o] != 0.f) atomicAdd(col + o * kH, v[o] * scale);
+}
 // Adds the TMEM weight-gradient accumulators of one object, times scale (the inverse of the FP16 path's gradient
-// scale, else 1), to its FP32 gradient.  Rows 0..63 live in TMEM lanes 0..63, which warps w with w % 4 < 2 can read;
-// with nthreads >= 256 warps 0, 1, 4 and 5 share the work (warps 4 and 5 take every other 16-column block).  Every CTA
-// that finishes an object flushes the same few kilobytes at about the same time, so each CTA starts at a different
-// matrix and column block: the reductions of different CTAs then mostly meet different L2 lines.
+// scale, else 1), to its FP32 gradient.  Lanes 0..63 hold the rows (dW1, dW3, dW4) or the inputs (dW2, dW5), which
+// warps w with w % 4 < 2 can read; with nthreads >= 256 warps 0, 1, 4 and 5 share the work (warps 4 and 5 take every
+// other 16-column block or output).  Every CTA that finishes an object flushes the same few kilobytes at about the
+// same time, so each CTA starts at a different matrix and column block: the reductions of different CTAs then mostly
+// meet different L2 lines.
 template <int LFP>
 __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad, float scale, int nthreads) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -261,15 +273,15 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
   const int nh = nthreads >= 256 ? 2 : 1;  // flushing warps per lane group
   const int h = (w >> 2) & (nh - 1);
   const uint32_t lt = tm + ((uint32_t)(32 * q) << 16);
-  const int o = 32 * q + lane;  // output row of this lane
+  const int o = 32 * q + lane;  // this lane's output row, or input for the transposed ones
   const int rot = (int)blockIdx.x;
   const int nmat = g.single_net ? 2 + g.extra : 5;
   for (int i = 0; i < nmat; ++i) {
     const int m = (i + rot) % nmat;
     if (m == 0) {  // first layer [64][LF]
       flush_rows(lt, kColDW1, LFP, true, grad + g.mlp_off[0] + o * g.LF, g.LF, scale, h, nh, rot);
-    } else if (m == 1) {  // density output layer [16][64] (fed by H1, or the single network's last hidden layer)
-      if (q == 0) flush_rows(lt, kColDW2, kH, o < 16, grad + g.mlp_off[1] + o * kH, kH, scale, h, nh, rot);
+    } else if (m == 1) {  // density output layer [16][64], transposed (fed by H1 or the last hidden layer)
+      flush_cols(lt, kColDW2, 16, grad + g.mlp_off[1] + o, scale, h, nh);
     } else if (g.single_net) {  // hidden layers 2 and 3 [64][64] in the DW4 and DW3 columns
       const int x = m - 2;
       flush_rows(lt, x == 0 ? kColDW4 : kColDW3, kH, true, grad + g.mlp_off[5 + x] + o * kH, kH, scale, h, nh, rot);
@@ -277,8 +289,8 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
       flush_rows(lt, kColDW3, 32, true, grad + g.mlp_off[2] + o * g.cin, g.cin, scale, h, nh, rot);
     } else if (m == 3) {  // [64][64]
       flush_rows(lt, kColDW4, kH, true, grad + g.mlp_off[3] + o * kH, kH, scale, h, nh, rot);
-    } else if (q == 0) {  // colour output [3][64]
-      flush_rows(lt, kColDW5, kH, o < 3, grad + g.mlp_off[4] + o * kH, kH, scale, h, nh, rot);
+    } else {  // colour output [3][64], transposed
+      flush_cols(lt, kColDW5, 3, grad + g.mlp_off[4] + o, scale, h, nh);
     }
   }
 }

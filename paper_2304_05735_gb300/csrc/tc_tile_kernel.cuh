@@ -42,8 +42,9 @@ namespace {
 using namespace tc;
 
 
-constexpr int kTilesPerCta = 2;   // tiles processed in lockstep: warpgroup g works on tile g of the pair
-constexpr int kTcThreads = 128 * kTilesPerCta;
+// A CTA processes TPC tiles in lockstep, warpgroup g on tile g: TPC = 2 (a tile pair, one CTA of 256 threads per SM,
+// 512 TMEM columns) or TPC = 1 (one tile, two CTAs of 128 threads per SM, 256 TMEM columns each; the two CTAs of an
+// SM pass no barrier together, so one's memory-bound phases can overlap the other's GEMMs and epilogues).
 
 // Buffers of one tile.  The activation buffers are contiguous and in this order: the MN-major A operands of the
 // weight-gradient GEMMs (dY^T, M padded to 128) read up to 2 KB past their buffer (the rows >= its feature count),
@@ -203,7 +204,7 @@ __device__ __forceinline__ void scatter_levels(const GridParams& g, const Object
   }
 }
 
-template <int LFP, bool FP8, bool SN>
+template <int LFP, bool FP8, bool SN, int TPC>
 struct TcSmem {
   // weights (B operands of the forward), K-major BF16 [out][in]; w4 holds the colour net's 64x64 layer, or the
   // single-network model's hidden layer 2, and w6() its hidden layer 3
@@ -212,7 +213,7 @@ struct TcSmem {
   __align__(128) unsigned char w3[kH * 32 * 2];
   __align__(128) unsigned char w4[kH * kH * 2];
   __align__(128) unsigned char w5[16 * kH * 2];
-  TileBufs<LFP> tb[kTilesPerCta];
+  TileBufs<LFP> tb[TPC];
   // FP8 E4M3 operands of the hidden 64x64 forward GEMM (ROMAP_PREC_MIXED_FP8): K-major W4 here, each tile's H2
   // rows in h2q(u)
   __align__(128) unsigned char w4q[FP8 ? kH * kH : 16];
@@ -233,9 +234,11 @@ static_assert(kT * kH <= kT * kH * 2, "a tile's FP8 H2 rows fit in its H3 buffer
 
 // 195 KB plus the 1 KB the system reserves per CTA fit the 196 KB shared-memory carveout; one byte more and the
 // carveout becomes 228 KB, which leaves 28 KB of L1 (measured: the fused step 14% slower)
-static_assert(sizeof(TcSmem<32, false, false>) <= 195 * 1024 && sizeof(TcSmem<32, true, false>) <= 195 * 1024 &&
-                  sizeof(TcSmem<32, false, true>) <= 195 * 1024,
+static_assert(sizeof(TcSmem<32, false, false, 2>) <= 195 * 1024 && sizeof(TcSmem<32, true, false, 2>) <= 195 * 1024 &&
+                  sizeof(TcSmem<32, false, true, 2>) <= 195 * 1024,
               "shared memory of the fused kernel above the 196 KB carveout");
+// two one-tile CTAs (plus 1 KB each reserved by the system) in the 228 KB carveout
+static_assert(2 * (sizeof(TcSmem<32, false, false, 1>) + 1024) <= 228 * 1024, "two one-tile CTAs per SM");
 
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -329,11 +332,13 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
   }
 }
 
-template <int LFP, bool FP8, bool SN, bool F16>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <int LFP, bool FP8, bool SN, bool F16, int TPC>
+__global__ void __launch_bounds__(128 * TPC, 3 - TPC)
     k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int interleave) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TcSmem<LFP, FP8, SN>& sm = *reinterpret_cast<TcSmem<LFP, FP8, SN>*>(smem_raw);
+  constexpr int kTilesPerCta = TPC, kTcThreads = 128 * TPC;
+  constexpr uint32_t kCols = TPC == 2 ? 512u : 256u;  // TMEM columns: kColTmp + 64 per tile, a power of 2
+  TcSmem<LFP, FP8, SN, TPC>& sm = *reinterpret_cast<TcSmem<LFP, FP8, SN, TPC>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   const int wg = t >> 7;          // tile of the pair
   const int s = t & (kT - 1);     // slot within the tile = TMEM lane
@@ -344,7 +349,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr bool f16 = F16;
   auto unscale_of = [&](int bi_) { return f16 ? 1.0f / (float)(b.ray_base[bi_ + 1] - b.ray_base[bi_]) : 1.0f; };
   // pairs of this CTA: a contiguous range of the plan, or chunks of `interleave` pairs dealt round-robin (WorkOrder)
-  const WorkOrder wo(*b.plan_npairs, (int)gridDim.x, (int)blockIdx.x, interleave);
+  // work items: tile pairs, or single tiles (both tiles of a pair hold the same object; the second may be empty)
+  const WorkOrder wo((TPC == 2 ? 1 : 2) * *b.plan_npairs, (int)gridDim.x, (int)blockIdx.x, interleave);
   const int n_items = wo.count();
   if (n_items <= 0) return;
 
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&sm.tmem_base)),
-                 "r"(kTmemCols));
+                 "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_before();
@@ -404,7 +410,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nwin = SN ? 2 + nl : 5;
   auto part = [&](int k) { return k * Lg / nwin; };
   int cur = 0;  // encoding buffer of the current pair
-  const uint32_t lt = tm + ((uint32_t)(32 * (warp & 3)) << 16);  // this thread's TMEM lane
   // columns past 2 L stay zero in both buffers
   for (int u = 0; u < 2; ++u) zero_rows<LFP>(tb.E[u], s, Lg, LMAX);
   if (nx.valid) {
@@ -580,7 +585,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     // ---- 4. compositing, losses, adjoint: one warp per ray of the pair -----------------------------------------
     {
-      const int nr0 = sm.tb[0].nrays, nr_all = nr0 + sm.tb[1].nrays;
+      const int nr0 = sm.tb[0].nrays;
+      int nr_all = nr0;
+      if constexpr (TPC == 2) nr_all += sm.tb[1].nrays;
       auto tile_of = [&](int u) -> TileBufs<LFP>& { return sm.tb[u]; };
       composite_rays(tile_of, nr0, nr_all, warp, kTcThreads / 32, g, b, R, dyn, bi, invB, status);
     }
@@ -616,12 +623,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if constexpr (!SN) {  // ---- colour net backward ------------------------------------------------------------------
       sync_then_issue();
-      if (t == 0) {  // dH3 = DL W5 ; dW5 += DL^T H3
+      if (t == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
         for (int u = 0; u < kTilesPerCta; ++u) {
           mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW5 + tm, desc_mn(sm.tb[u].DL, 16, kk), desc_mn(sm.tb[u].H3, kH, kk), idesc(64, 1, 1, f16),
+            mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
                 (u > 0 || kk > 0) ? 1u : acc_dw);
         }
         mma_commit(&sm.mbar);
@@ -689,12 +696,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }  // colour net backward
     sync_then_issue();
-    if (t == 0) {  // dHL = dOUT W2 ; dW2 += dOUT^T HL
+    if (t == 0) {  // dHL = dOUT W2 ; dW2^T += HL^T dOUT
       for (int u = 0; u < kTilesPerCta; ++u) {
         mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW2 + tm, desc_mn(sm.tb[u].DL, 16, kk), desc_mn(hid(u, nl), kH, kk), idesc(64, 1, 1, f16),
+          mma(kColDW2 + tm, desc_mn(hid(u, nl), kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
               (u > 0 || kk > 0) ? 1u : acc_dw);
       }
       mma_commit(&sm.mbar);
@@ -747,8 +754,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int u = 0; u < kTilesPerCta; ++u) {
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma(tm + kColDE + 32u * (uint32_t)u, desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk),
-              idesc(LFP, 0, 1, f16), kk > 0);
+          mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1, f16), kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
           mma(kColDW1 + tm, desc_mn(sm.tb[u].H1, kH, kk), desc_mn(sm.tb[u].E[cur], LFP, kk), idesc(LFP, 1, 1, f16),
@@ -766,7 +772,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     acc_dw = 1;
     {  // ---- 6. scatter dL/dencoding into the FP32 table gradient ----
       const float p[3] = {tb.px[0][s], tb.px[1][s], tb.px[2][s]};
-      scatter_levels(g, ob, s, Lg, p, tb.valid[s] != 0, lt + kColDE + 32u * (uint32_t)wg, gunscale);
+      scatter_levels(g, ob, s, Lg, p, tb.valid[s] != 0, tmp, gunscale);
     }
     cur ^= 1;  // the next pair's encoding is in the other buffer
     tc_before();
@@ -783,23 +789,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   tc_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(kTmemCols));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(kCols));
 }
 
-template <int LFP, bool FP8, bool SN, bool F16>
+template <int LFP, bool FP8, bool SN, bool F16, int TPC>
 void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                  int max_tiles, int n_ctas, int interleave, cudaStream_t stream) {
-  // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
-  // CTA never waits on another
-  int bytes = (int)sizeof(TcSmem<LFP, FP8, SN>);
-  if (bytes < 116 * 1024) bytes = 116 * 1024;
+  auto kernel = k_tile_tc<LFP, FP8, SN, F16, TPC>;
+  int bytes = (int)sizeof(TcSmem<LFP, FP8, SN, TPC>);
   static std::atomic<uint64_t> attr_done{0};
-  set_smem_attr(k_tile_tc<LFP, FP8, SN, F16>, bytes, attr_done);
+  if (TPC == 2) {
+    // at least 116 KB of shared memory per CTA keeps one CTA per SM, so that the 512-column TMEM allocation of one
+    // CTA never waits on another
+    if (bytes < 116 * 1024) bytes = 116 * 1024;
+    set_smem_attr(kernel, bytes, attr_done);
+  } else {
+    // two CTAs per SM (256 TMEM columns each): the largest shared-memory carveout
+    static std::atomic<uint64_t> carve_done{0};
+    set_smem_attr(kernel, bytes, attr_done);
+    set_func_attr(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared,
+                  carve_done);
+  }
   // the plan's pair count is read on the device; max_tiles only bounds the grid
-  const int max_pairs = (max_tiles + kTilesPerCta - 1) / kTilesPerCta;
-  int grid = n_ctas < max_pairs ? n_ctas : max_pairs;
+  const int max_units = TPC == 2 ? (max_tiles + 1) / 2 : max_tiles;
+  const int ctas = TPC == 2 ? n_ctas : 2 * n_ctas;
+  const int grid = ctas < max_units ? ctas : max_units;
   if (grid < 1) return;
-  k_tile_tc<LFP, FP8, SN, F16><<<grid, kTcThreads, bytes, stream>>>(g, b, dyn, r, status, interleave);
+  kernel<<<grid, 128 * TPC, bytes, stream>>>(g, b, dyn, r, status, interleave);
 }
 
 }  // namespace

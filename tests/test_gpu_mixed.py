@@ -31,10 +31,12 @@ def _cos(a, b):
 
 
 F16 = R.ROMAP_PREC_MIXED_FP16
+N_KERNELS = 12  # fused-kernel candidates (romap_set_tile_kernel)
 
 
-@pytest.mark.parametrize("kernel,prec", [(0, MIXED), (1, MIXED), (2, MIXED), (3, MIXED), (0, R.ROMAP_PREC_MIXED_FP8),
-                                         (2, R.ROMAP_PREC_MIXED_FP8), (0, F16), (1, F16), (2, F16), (3, F16)])
+@pytest.mark.parametrize("kernel,prec", [(0, MIXED), (1, MIXED), (2, MIXED), (3, MIXED), (8, MIXED), (9, MIXED),
+                                         (0, R.ROMAP_PREC_MIXED_FP8), (2, R.ROMAP_PREC_MIXED_FP8), (0, F16), (1, F16),
+                                         (2, F16), (3, F16), (9, F16)])
 @pytest.mark.parametrize("scene", ["plain", "masked"])
 def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
     if scene == "plain":
@@ -69,7 +71,7 @@ def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
 
 
 @pytest.mark.parametrize("prec", [MIXED, F16])
-@pytest.mark.parametrize("kernel", list(range(8)))
+@pytest.mark.parametrize("kernel", list(range(N_KERNELS)))
 def test_mixed_batched_equals_separate(torch, kernel, prec):
     oc, rc = paired_config(L=8, T=2 ** 12, growth=1.5, n_samples=32, rays_per_step=700, bg_random=True,
                            precision=prec)
@@ -86,7 +88,7 @@ def test_mixed_batched_equals_separate(torch, kernel, prec):
         gb = [ctx.grad(i) for i in ids]
         ctx2 = Ctx(rc)
         try:
-            R.check(R.romap_set_tile_kernel(ctx2.h, (kernel + 1) % 8))  # another candidate, one object at a time
+            R.check(R.romap_set_tile_kernel(ctx2.h, (kernel + 1) % N_KERNELS))  # another candidate, one object at a time
             for k, sc in enumerate(scenes):
                 oid = ctx2.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed, rays_per_step=333 + 100 * k)
                 ctx2.add_rays(oid, sc.pool)
@@ -132,16 +134,16 @@ def test_autotuner_picks_a_measured_candidate(torch):
         oid = ctx.create(seed=0)
         ctx.add_rays(oid, sc.pool)
         chosen = R.C.c_int32()
-        ms = (R.C.c_float * 8)()
-        names = R.C.create_string_buffer(1024)
-        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 8, names, 1024))
+        ms = (R.C.c_float * N_KERNELS)()
+        names = R.C.create_string_buffer(2048)
+        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, N_KERNELS, names, 2048))
         assert chosen.value == -1
         ctx.train([oid], n_steps=2)
-        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, 8, names, 1024))
+        R.check(R.romap_autotune_report(ctx.h, R.C.byref(chosen), ms, N_KERNELS, names, 2048))
         cands = names.value.decode().split(";")
         print(f"\nautotuner: {dict(zip(cands, list(ms)[:len(cands)]))} -> {cands[chosen.value]}")
-        assert len(cands) == 8 and 0 <= chosen.value < 8
-        assert all(ms[i] > 0 for i in range(8)) and ms[chosen.value] == min(ms)
+        assert len(cands) == N_KERNELS and 0 <= chosen.value < N_KERNELS
+        assert all(ms[i] > 0 for i in range(N_KERNELS)) and ms[chosen.value] == min(ms)
     finally:
         ctx.close()
 
