@@ -429,9 +429,9 @@ def run_ours(args):
     autotune = None
     if main_prec != "fp32":
         chosen = C.c_int32()
-        tms = (C.c_float * 12)()
+        tms = (C.c_float * 16)()
         names = C.create_string_buffer(2048)
-        R.check(R.romap_autotune_report(h, C.byref(chosen), tms, 12, names, 2048))
+        R.check(R.romap_autotune_report(h, C.byref(chosen), tms, 16, names, 2048))
         cands = names.value.decode().split(";")
         autotune = {"chosen": cands[chosen.value] if chosen.value >= 0 else None,
                     "ms_per_launch": {c: float(tms[i]) for i, c in enumerate(cands)}}

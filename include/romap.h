@@ -470,7 +470,9 @@ ROMAP_API romap_status romap_selftest_wait_timeout(romap_ctx* ctx, int32_t poll_
  * a time); 4, 5 and 6, 7 = interleaved in chunks of 2 and 4 consecutive
  * pairs or tiles (longer runs of one object per CTA); 8, 9, 10, 11 = the
  * lockstep kernel on single tiles of 128 slots, two CTAs per SM, with the
- * contiguous, interleaved, by-2 and by-4 orders.  Only 0, 2, 4 and 6 run
+ * contiguous, interleaved, by-2 and by-4 orders; 12, 13, 14, 15 = tile
+ * pairs whose two warpgroups run decoupled (own MMA issue and barriers,
+ * meeting only at object changes), same orders.  Only 0, 2, 4 and 6 run
  * ROMAP_PREC_MIXED_FP8 or the single_net model: ROMAP_ERR_UNSUPPORTED for
  * the others there. */
 ROMAP_API romap_status romap_set_tile_kernel(romap_ctx* ctx, int32_t index);

@@ -136,7 +136,7 @@ struct romap_ctx {
   int64_t launches = 0;
   // autotuned choice of the mixed-precision tile kernel: -1 until tuned, then an index of kTileKernels
   int tile_kernel = -1;
-  float tile_kernel_ms[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  float tile_kernel_ms[16] = {};
   // CUDA graphs of one training step, one per batch composition (captured on cap_stream, replayed on stream), least
   // recently used first out beyond kMaxStepGraphs
   struct StepGraph {
@@ -588,9 +588,10 @@ int tile_ctas(romap_ctx* ctx) { return ctx->n_sms > 0 ? ctx->n_sms : 1; }
 
 // Candidate fused tile kernels of the mixed path (same results, different schedules): the lockstep kernel on tile
 // pairs (one CTA per SM) and the warp-specialized kernel (0..7, even and odd indices), then the lockstep kernel on
-// single tiles with two CTAs per SM (8..11), each with contiguous per-CTA ranges of the tile plan or with the plan
-// dealt round-robin over the CTAs in chunks of 1, 2 or 4 work items (tile pairs, or tiles).  Only the tile-pair
-// lockstep kernel has the FP8 and single-network variants.
+// single tiles with two CTAs per SM (8..11) and the tile-pair kernel with its two warpgroups decoupled (12..15), each
+// with contiguous per-CTA ranges of the tile plan or with the plan dealt round-robin over the CTAs in chunks of 1, 2
+// or 4 work items (tile pairs, or tiles).  Only the tile-pair lockstep kernel has the FP8 and single-network
+// variants.
 typedef void (*TileKernelFn)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int,
                              cudaStream_t);
 template <void (*F)(const GridParams&, const BatchDesc&, BatchDyn*, RayBuf, int32_t*, int, int, int, cudaStream_t),
@@ -604,15 +605,19 @@ const TileKernelFn kTileKernels[] = {launch_tile_order<launch_tile_tc, 0>, launc
                                      launch_tile_order<launch_tile_tc, 2>, launch_tile_order<launch_tile_ws, 2>,
                                      launch_tile_order<launch_tile_tc, 4>, launch_tile_order<launch_tile_ws, 4>,
                                      launch_tile_order<launch_tile_tc1, 0>, launch_tile_order<launch_tile_tc1, 1>,
-                                     launch_tile_order<launch_tile_tc1, 2>, launch_tile_order<launch_tile_tc1, 4>};
+                                     launch_tile_order<launch_tile_tc1, 2>, launch_tile_order<launch_tile_tc1, 4>,
+                                     launch_tile_order<launch_tile_tcd, 0>, launch_tile_order<launch_tile_tcd, 1>,
+                                     launch_tile_order<launch_tile_tcd, 2>, launch_tile_order<launch_tile_tcd, 4>};
 const char* const kTileKernelNames[] = {"lockstep tile pairs", "warp-specialized", "lockstep tile pairs, interleaved",
                                         "warp-specialized, interleaved", "lockstep tile pairs, interleaved by 2",
                                         "warp-specialized, interleaved by 2", "lockstep tile pairs, interleaved by 4",
                                         "warp-specialized, interleaved by 4", "lockstep single tiles, 2 CTAs per SM",
                                         "lockstep single tiles, 2 CTAs per SM, interleaved",
                                         "lockstep single tiles, 2 CTAs per SM, interleaved by 2",
-                                        "lockstep single tiles, 2 CTAs per SM, interleaved by 4"};
-constexpr int kNumTileKernels = 12;
+                                        "lockstep single tiles, 2 CTAs per SM, interleaved by 4",
+                                        "decoupled tile pairs", "decoupled tile pairs, interleaved",
+                                        "decoupled tile pairs, interleaved by 2", "decoupled tile pairs, interleaved by 4"};
+constexpr int kNumTileKernels = 16;
 static_assert(sizeof(kTileKernels) / sizeof(kTileKernels[0]) == kNumTileKernels, "candidate table");
 // the candidates with the FP8 and single-network variants (the tile-pair lockstep kernel)
 bool lockstep_kernel(int k) { return k < 8 && k % 2 == 0; }

@@ -307,6 +307,9 @@ void launch_tile_tc(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayB
 // launch_tile_tc with one tile per CTA and two CTAs per SM (BF16 or FP16 operands, two-network model only)
 void launch_tile_tc1(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                      int max_tiles, int n_ctas, int interleave, cudaStream_t stream);
+// launch_tile_tc with the two warpgroups of a tile pair decoupled (BF16 or FP16 operands, two-network model only)
+void launch_tile_tcd(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
+                     int max_tiles, int n_ctas, int interleave, cudaStream_t stream);
 // the FP16-operand instances of launch_tile_tc
 void launch_tile_tc_f16(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                         int total_tiles, int n_ctas, int interleave, cudaStream_t stream);

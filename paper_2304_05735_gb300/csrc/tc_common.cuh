@@ -264,16 +264,12 @@ __device__ __forceinline__ void flush_cols(uint32_t lane_taddr, uint32_t c0, int
 // warps w with w % 4 < 2 can read; with nthreads >= 256 warps 0, 1, 4 and 5 share the work (warps 4 and 5 take every
 // other 16-column block or output).  Every CTA that finishes an object flushes the same few kilobytes at about the
 // same time, so each CTA starts at a different matrix and column block: the reductions of different CTAs then mostly
-// meet different L2 lines.
+// meet different L2 lines.  flush_dw_lanes: the matrices' rows (or inputs) 32 q .. 32 q + 31 of one lane group (lt:
+// the group's TMEM lane address), flushing warp h of nh.
 template <int LFP>
-__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad, float scale, int nthreads) {
-  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  if ((w & 3) >= 2 || w >= nthreads / 32) return;
-  const int q = w & 1;                     // lanes 32 q .. 32 q + 31
-  const int nh = nthreads >= 256 ? 2 : 1;  // flushing warps per lane group
-  const int h = (w >> 2) & (nh - 1);
-  const uint32_t lt = tm + ((uint32_t)(32 * q) << 16);
-  const int o = 32 * q + lane;  // this lane's output row, or input for the transposed ones
+__device__ void flush_dw_lanes(uint32_t lt, int q, int h, int nh, const GridParams& g, float* __restrict__ grad,
+                               float scale) {
+  const int o = 32 * q + (threadIdx.x & 31);  // this lane's output row, or input for the transposed ones
   const int rot = (int)blockIdx.x;
   const int nmat = g.single_net ? 2 + g.extra : 5;
   for (int i = 0; i < nmat; ++i) {
@@ -293,6 +289,21 @@ __device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ g
       flush_cols(lt, kColDW5, 3, grad + g.mlp_off[4] + o, scale, h, nh);
     }
   }
+}
+template <int LFP>
+__device__ void flush_dw(uint32_t tm, const GridParams& g, float* __restrict__ grad, float scale, int nthreads) {
+  const int w = threadIdx.x >> 5;
+  if ((w & 3) >= 2 || w >= nthreads / 32) return;
+  const int q = w & 1;                     // lanes 32 q .. 32 q + 31
+  const int nh = nthreads >= 256 ? 2 : 1;  // flushing warps per lane group
+  flush_dw_lanes<LFP>(tm + ((uint32_t)(32 * q) << 16), q, (w >> 2) & (nh - 1), nh, g, grad, scale);
+}
+// The accumulators at TMEM column base dwb of one warpgroup, flushed by that warpgroup's warps 0 and 1.
+template <int LFP>
+__device__ void flush_dw_group(uint32_t dwb, const GridParams& g, float* __restrict__ grad, float scale) {
+  const int q = (threadIdx.x >> 5) & 3;
+  if (q >= 2) return;
+  flush_dw_lanes<LFP>(dwb + ((uint32_t)(32 * q) << 16), q, 0, 1, g, grad, scale);
 }
 
 __device__ __forceinline__ float warp_incl_prefix(float v, int lane) {

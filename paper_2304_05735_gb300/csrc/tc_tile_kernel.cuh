@@ -218,9 +218,11 @@ struct TcSmem {
   // rows in h2q(u)
   __align__(128) unsigned char w4q[FP8 ? kH * kH : 16];
   float w4_inv[kH];                    // 1 / (448 / max |W4 row n|) for each output n of the loaded object
-  __align__(8) uint64_t mbar;
+  __align__(8) uint64_t mbar[2];  // MMA completion: [0] for the CTA, or [g] for warpgroup g when decoupled
   uint32_t tmem_base;
   int fail;
+  int stop[2];  // each group's copy of fail, written by its MMA-issuing thread before a group barrier only
+  int rv;       // decoupled warpgroups: rendezvous arrivals
   // the single-network model has no colour-net input: tile 0's CIN buffer holds its hidden layer 3 (a separate
   // buffer would take shared memory from the L1 cache that serves the encoding gathers)
   __device__ unsigned char* w6() { return tb[0].CIN; }
@@ -332,10 +334,16 @@ __device__ __forceinline__ void epi_mask64(uint32_t taddr, unsigned char* buf, i
   }
 }
 
-template <int LFP, bool FP8, bool SN, bool F16, int TPC>
+// DEC (decoupled, with TPC = 2): the two warpgroups of the CTA run their tiles of each pair independently, each with
+// its own MMA-issuing thread, mbarrier, named barrier and 256 TMEM columns (its own weight-gradient accumulators and
+// temporary); they share the weights in shared memory and meet only at object changes (a bounded rendezvous), so
+// that one tile's memory-bound phases (gathers, scatter) can run while the other tile's GEMMs, epilogues and
+// compositing do.
+template <int LFP, bool FP8, bool SN, bool F16, int TPC, bool DEC>
 __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
     k_tile_tc(GridParams g, BatchDesc b, BatchDyn* dyn, RayBuf R, int32_t* status, int interleave) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  static_assert(!DEC || TPC == 2, "decoupled warpgroups need a tile pair");
   constexpr int kTilesPerCta = TPC, kTcThreads = 128 * TPC;
   constexpr uint32_t kCols = TPC == 2 ? 512u : 256u;  // TMEM columns: kColTmp + 64 per tile, a power of 2
   TcSmem<LFP, FP8, SN, TPC>& sm = *reinterpret_cast<TcSmem<LFP, FP8, SN, TPC>*>(smem_raw);
@@ -355,9 +363,12 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
   if (n_items <= 0) return;
 
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sm.fail = 0;
+    sm.stop[0] = sm.stop[1] = 0;
+    sm.rv = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&sm.tmem_base)),
@@ -368,27 +379,63 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
   __syncthreads();
   tc_after();
   const uint32_t tm = sm.tmem_base;
-  const uint32_t tmp = tm + ((uint32_t)(32 * (warp & 3)) << 16) + kColTmp + 64u * (uint32_t)wg;  // this thread's row
+  // TMEM column of tile u's temporary, and the weight-gradient accumulators the tiles of this thread's warpgroup use:
+  // shared by the pair (columns 0..191), or decoupled: warpgroup g's own block of 256 columns
+  auto tcol = [](int u) { return DEC ? 256u * (uint32_t)u + kColTmp : kColTmp + 64u * (uint32_t)u; };
+  const uint32_t dwb = tm + (DEC ? 256u * (uint32_t)wg : 0u);
+  const uint32_t tmp = tm + ((uint32_t)(32 * (warp & 3)) << 16) + tcol(wg);  // this thread's row
   uint32_t phase = 0;
   bool ok = true;
+  // the MMA-issuing thread and the tiles it issues for: thread 0 for both tiles, or the first thread of each
+  // decoupled warpgroup for its own tile
+  const bool issuer = DEC ? (t & 127) == 0 : t == 0;
+  const int u_lo = DEC ? wg : 0, u_hi = DEC ? wg + 1 : kTilesPerCta;
+  uint64_t* const mbar = &sm.mbar[DEC ? wg : 0];
+  auto group_sync = [&]() {  // the CTA, or this decoupled warpgroup (named barrier 1 + g)
+    if constexpr (DEC) asm volatile("bar.sync %0, 128;" :: "r"(1 + wg) : "memory");
+    else __syncthreads();
+  };
 
   auto sync_then_issue = [&]() {  // every thread's shared writes and TMEM reads become visible to the MMAs
     fence_async_smem();
     tc_before();
-    __syncthreads();
+    group_sync();
     tc_after();
   };
-  auto wait_mma = [&]() -> bool {  // one thread polls the mbarrier; the others wait at the CTA barrier
-    if (t == 0) {
-      if (!mbar_wait(&sm.mbar, phase)) sm.fail = 1;
+  // every stop decision of a group reads its stop copy after a group barrier, so that all of its threads take the
+  // same branch (fail itself may be set by the other decoupled group at any time)
+  const int grp = DEC ? wg : 0;
+  auto wait_mma = [&]() -> bool {  // one thread polls the mbarrier; the others wait at the barrier
+    if (issuer) {
+      if (!mbar_wait(mbar, phase)) sm.fail = 1;
+      sm.stop[grp] = *(volatile int*)&sm.fail;
     }
     phase ^= 1u;
-    __syncthreads();
+    group_sync();
     tc_after();
-    return sm.fail == 0;
+    return sm.stop[grp] == 0;
   };
-  // thread 0 issues for both tiles; tile u's temporary starts at column kColTmp + 64 u
-  auto tmp_d = [&](int u) { return tm + kColTmp + 64u * (uint32_t)u; };
+  auto tmp_d = [&](int u) { return tm + tcol(u); };
+  // decoupled warpgroups meet at object changes: each one's first thread arrives on the shared counter and waits
+  // (bounded) for the other's arrival; a time-out or the other's failure sets the failure flag
+  int rv_round = 0;
+  auto rendezvous = [&]() -> bool {
+    fence_async_smem();  // this thread's shared-memory writes (the weights) visible to the other group's MMAs
+    group_sync();
+    if ((t & 127) == 0) {
+      __threadfence_block();
+      const int target = 2 * (++rv_round);
+      atomicAdd(&sm.rv, 1);
+      int it = 0;
+      while (*(volatile int*)&sm.rv < target && *(volatile int*)&sm.fail == 0 && ++it < kWaitLimit) {
+      }
+      if (it >= kWaitLimit) sm.fail = 1;
+      sm.stop[grp] = *(volatile int*)&sm.fail;
+      __threadfence_block();
+    }
+    group_sync();
+    return sm.stop[grp] == 0;
+  };
 
   int bi = -1;
   const ObjectDev* ob = nullptr;
@@ -435,12 +482,27 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
       constexpr int kWB = (WeightIndex<LFP>::total + kTcThreads - 1) / kTcThreads;
       float wv[kWB];
       weights_fetch<LFP, kWB>(g, nx_ob->params, t, kTcThreads, wv);
-      if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kTcThreads);
+      if constexpr (DEC) {
+        // both warpgroups are done with the previous object's weights; each flushes its own accumulators
+        if (!rendezvous()) {
+          ok = false;
+          break;
+        }
+        if (bi >= 0) flush_dw_group<LFP>(dwb, g, ob->grad, unscale_of(bi));
+      } else {
+        if (bi >= 0) flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kTcThreads);
+      }
       bi = nx_bi;
       ob = nx_ob;
       weights_store<LFP, kWB>(sm, g, t, kTcThreads, wv);
       if (FP8) load_w4_fp8(sm, g, ob->params, t, kTcThreads);
       if (SN && g.extra >= 2) load_w6(sm, g, ob->params, t, kTcThreads);
+      if constexpr (DEC) {  // the new weights are in place for both warpgroups
+        if (!rendezvous()) {
+          ok = false;
+          break;
+        }
+      }
       acc_dw = 0;
     }
     const int n_rays_obj = b.ray_base[bi + 1] - b.ray_base[bi];
@@ -454,25 +516,25 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
     }
     sync_then_issue();
     // ---- 3. forward ----------------------------------------------------------------------------------------------
-    if (t == 0) {  // L1: E W1^T
-      for (int u = 0; u < kTilesPerCta; ++u)
+    if (issuer) {  // L1: E W1^T
+      for (int u = u_lo; u < u_hi; ++u)
 #pragma unroll
         for (int kk = 0; kk < LFP / 16; ++kk)
           mma(tmp_d(u), desc_k(sm.tb[u].E[cur], LFP, kk), desc_k(sm.w1, LFP, kk), idesc(64, 0, 0, f16), kk > 0);
-      mma_commit(&sm.mbar);
+      mma_commit(mbar);
     }
     if (!(ok = wait_mma())) break;
     epi_relu64(tmp, tb.H1, s, f16);
     if constexpr (SN) {  // single-network hidden layers 2 and 3: hid(k + 1) = relu(hid(k) M^T), M = w4, w6
       for (int k = 0; k < nl; ++k) {
         sync_then_issue();
-        if (t == 0) {
-          for (int u = 0; u < kTilesPerCta; ++u)
+        if (issuer) {
+          for (int u = u_lo; u < u_hi; ++u)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
               mma(tmp_d(u), desc_k(hid(u, k), kH, kk), desc_k(k == 0 ? sm.w4 : sm.w6(), kH, kk), idesc(64, 0, 0, f16),
                   kk > 0);
-          mma_commit(&sm.mbar);
+          mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
         epi_relu64(tmp, hid(wg, k + 1), s, f16);
@@ -480,12 +542,12 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
       if (!ok) break;
     }
     sync_then_issue();
-    if (t == 0) {  // L2: HL W2^T (16 outputs), HL = H1 unless the single network has more hidden layers
-      for (int u = 0; u < kTilesPerCta; ++u)
+    if (issuer) {  // L2: HL W2^T (16 outputs), HL = H1 unless the single network has more hidden layers
+      for (int u = u_lo; u < u_hi; ++u)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
           mma(tmp_d(u), desc_k(hid(u, nl), kH, kk), desc_k(sm.w2, kH, kk), idesc(16, 0, 0, f16), kk > 0);
-      mma_commit(&sm.mbar);
+      mma_commit(mbar);
     }
     if (!(ok = wait_mma())) break;
     {
@@ -516,12 +578,12 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
     }
     if constexpr (!SN) {  // ---- colour net --------------------------------------------------------------------------
       sync_then_issue();
-      if (t == 0) {  // L3: CIN W3^T
-        for (int u = 0; u < kTilesPerCta; ++u)
+      if (issuer) {  // L3: CIN W3^T
+        for (int u = u_lo; u < u_hi; ++u)
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
             mma(tmp_d(u), desc_k(sm.tb[u].CIN, 32, kk), desc_k(sm.w3, 32, kk), idesc(64, 0, 0, f16), kk > 0);
-        mma_commit(&sm.mbar);
+        mma_commit(mbar);
       }
       if (!(ok = wait_mma())) break;
       epi_relu64(tmp, tb.H2, s, f16);
@@ -547,8 +609,8 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
         }
       }
       sync_then_issue();
-      if (t == 0) {  // L4: H2 W4^T
-        for (int u = 0; u < kTilesPerCta; ++u) {
+      if (issuer) {  // L4: H2 W4^T
+        for (int u = u_lo; u < u_hi; ++u) {
           if (FP8) {
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk)
@@ -559,18 +621,18 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
               mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_k(sm.w4, kH, kk), idesc(64, 0, 0, f16), kk > 0);
           }
         }
-        mma_commit(&sm.mbar);
+        mma_commit(mbar);
       }
       if (!(ok = wait_mma())) break;
       if (FP8) epi_relu64_scaled(tmp, tb.H3, s, 1.0f / h2_scale, sm.w4_inv, f16);
       else epi_relu64(tmp, tb.H3, s, f16);
       sync_then_issue();
-      if (t == 0) {  // L5: H3 W5^T (3 of 16 outputs)
-        for (int u = 0; u < kTilesPerCta; ++u)
+      if (issuer) {  // L5: H3 W5^T (3 of 16 outputs)
+        for (int u = u_lo; u < u_hi; ++u)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_k(sm.w5, kH, kk), idesc(16, 0, 0, f16), kk > 0);
-        mma_commit(&sm.mbar);
+        mma_commit(mbar);
       }
       if (!(ok = wait_mma())) break;
       {
@@ -582,16 +644,21 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
         tb.rgb[2][s] = 1.0f / (1.0f + expf(-v[2]));
       }
     }  // colour net
-    __syncthreads();
+    group_sync();
     // ---- 4. compositing, losses, adjoint: one warp per ray of the pair -----------------------------------------
     {
-      const int nr0 = sm.tb[0].nrays;
-      int nr_all = nr0;
-      if constexpr (TPC == 2) nr_all += sm.tb[1].nrays;
-      auto tile_of = [&](int u) -> TileBufs<LFP>& { return sm.tb[u]; };
-      composite_rays(tile_of, nr0, nr_all, warp, kTcThreads / 32, g, b, R, dyn, bi, invB, status);
+      if constexpr (DEC) {  // this warpgroup's tile, its four warps
+        auto tile_of = [&](int) -> TileBufs<LFP>& { return tb; };
+        composite_rays(tile_of, tb.nrays, tb.nrays, warp & 3, 4, g, b, R, dyn, bi, invB, status);
+      } else {
+        const int nr0 = sm.tb[0].nrays;
+        int nr_all = nr0;
+        if constexpr (TPC == 2) nr_all += sm.tb[1].nrays;
+        auto tile_of = [&](int u) -> TileBufs<LFP>& { return sm.tb[u]; };
+        composite_rays(tile_of, nr0, nr_all, warp, kTcThreads / 32, g, b, R, dyn, bi, invB, status);
+      }
     }
-    __syncthreads();
+    group_sync();
     // ---- 5. backward -----------------------------------------------------------------------------------------------
     float dpre;
     {
@@ -623,15 +690,15 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
     }
     if constexpr (!SN) {  // ---- colour net backward ------------------------------------------------------------------
       sync_then_issue();
-      if (t == 0) {  // dH3 = DL W5 ; dW5^T += H3^T DL
-        for (int u = 0; u < kTilesPerCta; ++u) {
+      if (issuer) {  // dH3 = DL W5 ; dW5^T += H3^T DL
+        for (int u = u_lo; u < u_hi; ++u) {
           mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w5, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW5 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
-                (u > 0 || kk > 0) ? 1u : acc_dw);
+            mma(kColDW5 + dwb, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
+                (u > u_lo || kk > 0) ? 1u : acc_dw);
         }
-        mma_commit(&sm.mbar);
+        mma_commit(mbar);
       }
       {  // while the MMAs run: the next pair's sample and part 0 of its encoding (into the other buffer)
         if (has_next) {
@@ -644,17 +711,17 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
       if (!(ok = wait_mma())) break;
       epi_mask64(tmp, tb.H3, s, f16);
       sync_then_issue();
-      if (t == 0) {  // dH2 = dH3 W4 ; dW4 += dH3^T H2
-        for (int u = 0; u < kTilesPerCta; ++u) {
+      if (issuer) {  // dH2 = dH3 W4 ; dW4 += dH3^T H2
+        for (int u = u_lo; u < u_hi; ++u) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma(tmp_d(u), desc_k(sm.tb[u].H3, kH, kk), desc_mn(sm.w4, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW4 + tm, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1, f16),
-                (u > 0 || kk > 0) ? 1u : acc_dw);
+            mma(kColDW4 + dwb, desc_mn(sm.tb[u].H3, kH, kk), desc_mn(sm.tb[u].H2, kH, kk), idesc(64, 1, 1, f16),
+                (u > u_lo || kk > 0) ? 1u : acc_dw);
         }
-        mma_commit(&sm.mbar);
+        mma_commit(mbar);
       }
       {  // while the MMAs run: part 1 of the next pair's encoding
         if (has_next && nx.valid) {
@@ -665,17 +732,17 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
       if (!(ok = wait_mma())) break;
       epi_mask64(tmp, tb.H2, s, f16);
       sync_then_issue();
-      if (t == 0) {  // dCIN = dH2 W3 (32 columns) ; dW3 += dH2^T CIN
-        for (int u = 0; u < kTilesPerCta; ++u) {
+      if (issuer) {  // dCIN = dH2 W3 (32 columns) ; dW3 += dH2^T CIN
+        for (int u = u_lo; u < u_hi; ++u) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma(tmp_d(u), desc_k(sm.tb[u].H2, kH, kk), desc_mn(sm.w3, 32, kk), idesc(32, 0, 1, f16), kk > 0);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            mma(kColDW3 + tm, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].CIN, 32, kk), idesc(32, 1, 1, f16),
-                (u > 0 || kk > 0) ? 1u : acc_dw);
+            mma(kColDW3 + dwb, desc_mn(sm.tb[u].H2, kH, kk), desc_mn(sm.tb[u].CIN, 32, kk), idesc(32, 1, 1, f16),
+                (u > u_lo || kk > 0) ? 1u : acc_dw);
         }
-        mma_commit(&sm.mbar);
+        mma_commit(mbar);
       }
       {  // while the MMAs run: part 2 of the next pair's encoding
         if (has_next && nx.valid) {
@@ -696,15 +763,15 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
       }
     }  // colour net backward
     sync_then_issue();
-    if (t == 0) {  // dHL = dOUT W2 ; dW2^T += HL^T dOUT
-      for (int u = 0; u < kTilesPerCta; ++u) {
+    if (issuer) {  // dHL = dOUT W2 ; dW2^T += HL^T dOUT
+      for (int u = u_lo; u < u_hi; ++u) {
         mma(tmp_d(u), desc_k(sm.tb[u].DL, 16, 0), desc_mn(sm.w2, kH, 0), idesc(64, 0, 1, f16), 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW2 + tm, desc_mn(hid(u, nl), kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
-              (u > 0 || kk > 0) ? 1u : acc_dw);
+          mma(kColDW2 + dwb, desc_mn(hid(u, nl), kH, kk), desc_mn(sm.tb[u].DL, 16, kk), idesc(16, 1, 1, f16),
+              (u > u_lo || kk > 0) ? 1u : acc_dw);
       }
-      mma_commit(&sm.mbar);
+      mma_commit(mbar);
     }
     if constexpr (SN) {  // while the MMAs run: the next pair's sample and the first half of its encoding
       if (has_next) {
@@ -724,19 +791,19 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
     if constexpr (SN) {  // hidden layers 3, 2: dhid(k) = dhid(k + 1) M ; dM += dhid(k + 1)^T hid(k)
       for (int k = nl - 1; k >= 0; --k) {
         sync_then_issue();
-        if (t == 0) {
+        if (issuer) {
           const unsigned char* w = k == 0 ? sm.w4 : sm.w6();
           const uint32_t col = k == 0 ? kColDW4 : kColDW3;
-          for (int u = 0; u < kTilesPerCta; ++u) {
+          for (int u = u_lo; u < u_hi; ++u) {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
               mma(tmp_d(u), desc_k(hid(u, k + 1), kH, kk), desc_mn(w, kH, kk), idesc(64, 0, 1, f16), kk > 0);
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-              mma(col + tm, desc_mn(hid(u, k + 1), kH, kk), desc_mn(hid(u, k), kH, kk), idesc(64, 1, 1, f16),
-                  (u > 0 || kk > 0) ? 1u : acc_dw);
+              mma(col + dwb, desc_mn(hid(u, k + 1), kH, kk), desc_mn(hid(u, k), kH, kk), idesc(64, 1, 1, f16),
+                  (u > u_lo || kk > 0) ? 1u : acc_dw);
           }
-          mma_commit(&sm.mbar);
+          mma_commit(mbar);
         }
         {  // while the MMAs run: the next part of the next pair's encoding
           if (has_next && nx.valid) {
@@ -750,17 +817,17 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
       if (!ok) break;
     }
     sync_then_issue();
-    if (t == 0) {  // dE = dH1 W1 (LFP columns) ; dW1 += dH1^T E
-      for (int u = 0; u < kTilesPerCta; ++u) {
+    if (issuer) {  // dE = dH1 W1 (LFP columns) ; dW1 += dH1^T E
+      for (int u = u_lo; u < u_hi; ++u) {
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
           mma(tmp_d(u), desc_k(sm.tb[u].H1, kH, kk), desc_mn(sm.w1, LFP, kk), idesc(LFP, 0, 1, f16), kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma(kColDW1 + tm, desc_mn(sm.tb[u].H1, kH, kk), desc_mn(sm.tb[u].E[cur], LFP, kk), idesc(LFP, 1, 1, f16),
-              (u > 0 || kk > 0) ? 1u : acc_dw);
+          mma(kColDW1 + dwb, desc_mn(sm.tb[u].H1, kH, kk), desc_mn(sm.tb[u].E[cur], LFP, kk), idesc(LFP, 1, 1, f16),
+              (u > u_lo || kk > 0) ? 1u : acc_dw);
       }
-      mma_commit(&sm.mbar);
+      mma_commit(mbar);
     }
     {  // while the MMAs run: the last part of the next pair's encoding
       if (has_next && nx.valid) {
@@ -776,15 +843,16 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
     }
     cur ^= 1;  // the next pair's encoding is in the other buffer
     tc_before();
-    __syncthreads();
+    group_sync();
     tc_after();
   }
   if (ok && bi >= 0) {
-    flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kTcThreads);
+    if constexpr (DEC) flush_dw_group<LFP>(dwb, g, ob->grad, unscale_of(bi));
+    else flush_dw<LFP>(tm, g, ob->grad, unscale_of(bi), kTcThreads);
   } else if (!ok) {
-    if (t == 0) {
+    if (issuer) {
       if (status) atomicOr(status, 2);
-      mbar_wait(&sm.mbar, phase ^ 1u);  // bounded: let the MMAs still in flight finish before the columns are freed
+      mbar_wait(mbar, phase ^ 1u);  // bounded: let the MMAs still in flight finish before the columns are freed
     }
   }
   tc_before();
@@ -792,10 +860,10 @@ __global__ void __launch_bounds__(128 * TPC, 3 - TPC)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(kCols));
 }
 
-template <int LFP, bool FP8, bool SN, bool F16, int TPC>
+template <int LFP, bool FP8, bool SN, bool F16, int TPC, bool DEC = false>
 void launch_tc_t(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, RayBuf r, int32_t* status,
                  int max_tiles, int n_ctas, int interleave, cudaStream_t stream) {
-  auto kernel = k_tile_tc<LFP, FP8, SN, F16, TPC>;
+  auto kernel = k_tile_tc<LFP, FP8, SN, F16, TPC, DEC>;
   int bytes = (int)sizeof(TcSmem<LFP, FP8, SN, TPC>);
   static std::atomic<uint64_t> attr_done{0};
   if (TPC == 2) {

@@ -110,7 +110,7 @@ def test_fp32_step_with_occupancy_matches_oracle():
         ctx.close()
 
 
-@pytest.mark.parametrize("kernel", list(range(12)))
+@pytest.mark.parametrize("kernel", list(range(16)))
 def test_uneven_batch_every_object_mixed_vs_fp32(kernel):
     """Every object of the 32-object batch, not only the smallest: its first-step mixed gradient against the FP32
     path's (same inputs, same parameters), for each fused-kernel schedule and tile order.  Objects spread over many

@@ -31,12 +31,13 @@ def _cos(a, b):
 
 
 F16 = R.ROMAP_PREC_MIXED_FP16
-N_KERNELS = 12  # fused-kernel candidates (romap_set_tile_kernel)
+N_KERNELS = 16  # fused-kernel candidates (romap_set_tile_kernel)
 
 
 @pytest.mark.parametrize("kernel,prec", [(0, MIXED), (1, MIXED), (2, MIXED), (3, MIXED), (8, MIXED), (9, MIXED),
+                                         (12, MIXED), (13, MIXED),
                                          (0, R.ROMAP_PREC_MIXED_FP8), (2, R.ROMAP_PREC_MIXED_FP8), (0, F16), (1, F16),
-                                         (2, F16), (3, F16), (9, F16)])
+                                         (2, F16), (3, F16), (9, F16), (13, F16)])
 @pytest.mark.parametrize("scene", ["plain", "masked"])
 def test_mixed_step_vs_oracle(torch, scene, kernel, prec):
     if scene == "plain":

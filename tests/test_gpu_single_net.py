@@ -151,6 +151,7 @@ def test_mixed_single_net_step_vs_oracle(torch, scene, K):
         assert R.romap_set_tile_kernel(ctx.h, 1) == R.ROMAP_ERR_UNSUPPORTED
         assert R.romap_set_tile_kernel(ctx.h, 3) == R.ROMAP_ERR_UNSUPPORTED
         assert R.romap_set_tile_kernel(ctx.h, 8) == R.ROMAP_ERR_UNSUPPORTED
+        assert R.romap_set_tile_kernel(ctx.h, 12) == R.ROMAP_ERR_UNSUPPORTED
         oid = ctx.create(t=tuple(sc.t), yaw=sc.yaw, seed=sc.seed)
         ctx.add_rays(oid, sc.pool)
         pool = object_frame_pool(sc)
