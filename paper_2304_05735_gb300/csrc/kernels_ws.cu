@@ -24,8 +24,8 @@ constexpr int kCompute = 128;
 
 template <int LFP>
 struct WsSlot {
-  // activation buffers: contiguous and in this order (the MN-major A operands of the weight-gradient GEMMs, dY^T with
-  // M padded to 128, read up to 2 KB past their buffer into the next one of the slot; past DL: the float arrays)
+  // activation buffers: contiguous and in this order (the MN-major A operands of the weight-gradient GEMMs, 64
+  // features with M padded to 128, read up to 1 KB past their buffer into the next one of the slot)
   __align__(128) unsigned char E[kT * LFP * 2];
   __align__(128) unsigned char H1[kT * kH * 2];
   __align__(128) unsigned char CIN[kT * 32 * 2];

@@ -14,10 +14,10 @@
 //      the next operand row to shared memory,
 //   4. volume rendering (Eq. 6), the losses of Eq. 7-11 and the compositing adjoint, one warp per ray,
 //   5. the backward: per layer one GEMM for the input gradient (dX = dY W: A = dY K-major, B = W read
-//      MN-major from the forward copy) and one for the weight gradient (dW = dY^T X over the 128 samples:
-//      both operands read MN-major from the activation buffers, M = the layer's outputs padded to 128), the latter
-//      accumulated in TMEM across all tiles of the same object and added to the FP32 gradient once per object
-//      change,
+//      MN-major from the forward copy) and one for the weight gradient (dW = dY^T X over the 128 samples, or its
+//      transpose for the 16-output layers: both operands read MN-major from the activation buffers, M padded to
+//      128), the latter accumulated in TMEM across all tiles of the same object and added to the FP32 gradient once
+//      per object change,
 //   6. the hash-gradient scatter (FP32 vector atomics into the FP32 gradient of the table).
 // The transmittance scan, the losses and every accumulation stay in FP32; Adam keeps FP32 masters and
 // refreshes the FP16 table copy.  With FP16 operands the backward's gradient operands are scaled by the object's
@@ -47,9 +47,9 @@ using namespace tc;
 // SM pass no barrier together, so one's memory-bound phases can overlap the other's GEMMs and epilogues).
 
 // Buffers of one tile.  The activation buffers are contiguous and in this order: the MN-major A operands of the
-// weight-gradient GEMMs (dY^T, M padded to 128) read up to 2 KB past their buffer (the rows >= its feature count),
-// which lands in the next buffer of the same tile (past DL: the tile's float arrays) and only feeds TMEM rows that
-// are never read.
+// weight-gradient GEMMs (64 features, M padded to 128: dH^T for dW1, dW3, dW4; H3^T and HL^T for the transposed dW5
+// and dW2) read up to 1 KB past their buffer (the rows >= its feature count), which lands in the next buffer of the
+// same tile and only feeds TMEM rows that are never read; DL and E are read as B operands, without overrun.
 template <int LFP>
 struct TileBufs {
   __align__(128) unsigned char E[2][kT * LFP * 2];  // this pair's encoding and the next pair's, alternating
