@@ -296,6 +296,20 @@ def add_objects(R, h, items, seed_offset=0):
     return ids
 
 
+def per_object_cmp(obj_final):
+    """Per object and seed, the relative difference of the mixed run's final loss from the FP32 run's: median,
+    quartiles and the fraction within 1e-3."""
+    import numpy as np
+
+    if not obj_final["fp32"] or not obj_final["mixed"]:
+        return None
+    f = np.concatenate(obj_final["fp32"]).astype(np.float64)
+    m = np.concatenate(obj_final["mixed"]).astype(np.float64)
+    d = (m - f) / f
+    return {"pairs": int(d.size), "median": float(np.median(d)), "q25": float(np.quantile(d, 0.25)),
+            "q75": float(np.quantile(d, 0.75)), "within_1e-3": float(np.mean(np.abs(d) <= 1e-3))}
+
+
 def curve_steps(k):
     """Step indices of the reported loss curve: the first step, then every tenth of the run."""
     return sorted({0, *range(max(1, k // 10) - 1, k, max(1, k // 10))})
@@ -381,6 +395,7 @@ def run_ours(args):
     # a run is reproducible bit for bit and the spread between runs is the spread between seeds alone.  The final
     # loss of a run is its mean per-step loss over the last K/4 steps, averaged over the objects.
     runs = {"fp32": [], "mixed": []}
+    obj_final = {"fp32": [], "mixed": []}  # per run: each object's mean loss over the last K/4 steps
     psnr = {}
     fp32_repeat_identical = None
     if not args.no_plain:
@@ -398,6 +413,7 @@ def run_ours(args):
                     fp32_repeat_identical = bool(np.array_equal(ls.mean(axis=1), runs["fp32"][0]))
                 else:
                     runs[prec].append(ls.mean(axis=1))
+                    obj_final[prec].append(ls[-max(1, args.loss_steps // 4):].mean(axis=0))
                     if k == 0:
                         psnr[prec] = trained_psnr(R, h, ids, evalset)
                 R.check(R.romap_destroy(h))
@@ -685,6 +701,8 @@ def run_ours(args):
             "paired_rel_diff": paired.tolist(), "paired_rel_diff_se": se,
             # robust to the occasional seed whose mixed or FP32 run reaches a sharp loss drop many steps earlier
             "paired_rel_diff_median": float(np.median(paired)),
+            # the same per object (every object of every seed): how a typical object's final loss compares
+            "per_object": per_object_cmp(obj_final),
             "within_two_se": bool(se is not None and abs(float(paired.mean())) <= 2.0 * se),
             "fp32_repeat_bit_identical": fp32_repeat_identical,
             "first_step_rel_diff": float(abs(cm[0] - cf[0]) / cf[0]),
