@@ -398,11 +398,15 @@ def run_ours(args):
     obj_final = {"fp32": [], "mixed": []}  # per run: each object's mean loss over the last K/4 steps
     psnr = {}
     fp32_repeat_identical = None
+    # control: seed 0 once more in FP32 with ordinary (order-dependent) atomic accumulation, against the
+    # deterministic FP32 run of the same seed: how far training alone moves the final losses when only the rounding
+    # order of the sums changes
+    fp32_nondet = None
     if not args.no_plain:
         evalset = psnr_rays(items)
         for k in range(args.loss_seeds):
-            for prec in ("fp32", "mixed") + (("fp32_repeat",) if k == 0 else ()):
-                det = prec != "mixed"
+            for prec in ("fp32", "mixed") + (("fp32_repeat", "fp32_nondet") if k == 0 else ()):
+                det = prec not in ("mixed", "fp32_nondet")
                 rc, h = make_ctx(R, torch, main_prec if prec == "mixed" else "fp32", deterministic=det)
                 ids = add_objects(R, h, items, seed_offset=1000 * k)
                 idarr = (C.c_int32 * n)(*ids)
@@ -411,6 +415,9 @@ def run_ours(args):
                     R.check(R.romap_train_step(h, idarr, n, 1, ls[j].ctypes.data))
                 if prec == "fp32_repeat":
                     fp32_repeat_identical = bool(np.array_equal(ls.mean(axis=1), runs["fp32"][0]))
+                elif prec == "fp32_nondet":
+                    tail_nd = max(1, args.loss_steps // 4)
+                    fp32_nondet = {"run": ls.mean(axis=1), "obj": ls[-tail_nd:].mean(axis=0)}
                 else:
                     runs[prec].append(ls.mean(axis=1))
                     obj_final[prec].append(ls[-max(1, args.loss_steps // 4):].mean(axis=0))
@@ -703,6 +710,12 @@ def run_ours(args):
             "paired_rel_diff_median": float(np.median(paired)),
             # the same per object (every object of every seed): how a typical object's final loss compares
             "per_object": per_object_cmp(obj_final),
+            "control_fp32_order": None if fp32_nondet is None else {
+                "what": "seed 0: FP32 with order-dependent atomic sums vs the deterministic FP32 run (no precision "
+                        "change, only the rounding order of the sums)",
+                "rel_diff": float((fp32_nondet["run"][-tail:].mean() - runs["fp32"][0][-tail:].mean())
+                                  / runs["fp32"][0][-tail:].mean()),
+                "per_object": per_object_cmp({"fp32": [obj_final["fp32"][0]], "mixed": [fp32_nondet["obj"]]})},
             "within_two_se": bool(se is not None and abs(float(paired.mean())) <= 2.0 * se),
             "fp32_repeat_bit_identical": fp32_repeat_identical,
             "first_step_rel_diff": float(abs(cm[0] - cf[0]) / cf[0]),
