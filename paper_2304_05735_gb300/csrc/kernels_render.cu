@@ -266,9 +266,11 @@ __device__ __forceinline__ bool nonzero4(const float4& a) {
   return a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f;
 }
 
-__global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int write_half) {
+__global__ void __launch_bounds__(256) k_adam(GridParams g, BatchDesc b, int write_half, int prev) {
   const ObjectDev& ob = b.objs[b.slot[blockIdx.y]];
-  const float c1 = ob.bc1, c2 = ob.bc2;  // bias corrections of this step, set with the step counter
+  // bias corrections of this step, set with the step counter; prev: the update of the step before, run after the
+  // counter has already advanced (it overlaps the next step's sampling)
+  const float c1 = prev ? ob.bc1_prev : ob.bc1, c2 = prev ? ob.bc2_prev : ob.bc2;
   const float b1 = g.beta1, b2 = g.beta2, lr = g.lr, eps = g.eps;
   const float ob1 = 1.0f - b1, ob2 = 1.0f - b2;
   float4* P = reinterpret_cast<float4*>(ob.params);
@@ -404,15 +406,24 @@ void launch_final_losses(const BatchDyn* dyn, const BatchDesc& b, float* out, cu
   k_final_losses<<<(b.n + 127) / 128, 128, 0, stream>>>(dyn, b.ray_base, b.n, out);
 }
 
-void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream) {
+void launch_adam_update(const GridParams& g, const BatchDesc& b, int write_half, int prev, cudaStream_t stream) {
   if (b.n <= 0) return;
   int64_t n4 = g.n_params_pad / 4;
   int chunks = (int)((n4 + 511) / 512);  // blocks of 8 warps, one 64-float4 chunk per warp and round
   int max_chunks = 4096 / (b.n < 1 ? 1 : b.n) + 1;  // about 4k blocks of 256 threads, two float4 groups per lane
   if (max_chunks < 16) max_chunks = 16;
   if (chunks > max_chunks) chunks = max_chunks;
-  k_adam<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, write_half);
+  k_adam<<<dim3(chunks, b.n), 256, 0, stream>>>(g, b, write_half, prev);
+}
+
+void launch_advance_step(const GridParams& g, const BatchDesc& b, cudaStream_t stream) {
+  if (b.n <= 0) return;
   k_advance_step<<<(b.n + 127) / 128, 128, 0, stream>>>(g, b);
+}
+
+void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream) {
+  launch_adam_update(g, b, write_half, 0, stream);
+  launch_advance_step(g, b, stream);
 }
 
 __global__ void k_split_outputs(const float* __restrict__ ray_out, int64_t n, float* rgb, float* depth,

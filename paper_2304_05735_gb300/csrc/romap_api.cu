@@ -150,6 +150,10 @@ struct romap_ctx {
     uint64_t ws_generation = 0;        // workspace generation it was captured against
   };
   cudaStream_t cap_stream = nullptr;
+  // a second stream on which a step's Adam update of the step before overlaps the step's sampling (n_steps > 1 in
+  // one call): side_stream for eager launches, cap_side while a graph is captured, side the one in use
+  cudaStream_t side_stream = nullptr, cap_side = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<StepGraph> graphs;
   uint64_t graph_clock = 0;
   int64_t graph_captures = 0, graph_replays = 0;
@@ -694,7 +698,36 @@ romap_status ensure_step_workspace(romap_ctx* ctx, const std::vector<int32_t>& r
 }
 
 // forward + loss + backward of a batch (no Adam)
-romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchDesc* out_b) {
+// The side stream (lowest priority, so that the sampling kernels it overlaps are scheduled first) and the fork/join
+// events, created on first use.
+romap_status ensure_side(romap_ctx* ctx) {
+  if (ctx->side_stream) return ROMAP_OK;
+  int least = 0, greatest = 0;
+  CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side_stream, cudaStreamNonBlocking, least));
+  CUDA_TRY(cudaStreamCreateWithPriority(&ctx->cap_side, cudaStreamNonBlocking, least));
+  CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  ctx->side = ctx->side_stream;
+  return ROMAP_OK;
+}
+
+// Enqueues the Adam update of the batch's previous step on the side stream after everything on the stream so far.
+romap_status fork_prev_adam(romap_ctx* ctx, const BatchDesc& b) {
+  ROMAP_TRY(ensure_side(ctx));
+  CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  launch_adam_update(ctx->g, b, ctx->cfg.precision != ROMAP_PREC_FP32, 1, ctx->side);
+  CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->side));
+  ctx->launches += 1;
+  return ROMAP_OK;
+}
+
+// overlap_prev_adam: the Adam update of the step before (launch_adam_update with prev) runs on the side stream,
+// forked after the batch is uploaded and joined before the first kernel that reads the parameters, so that it
+// overlaps this step's sampling (which reads none).
+romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchDesc* out_b,
+                         bool overlap_prev_adam = false) {
   std::vector<int32_t> slots(ids.begin(), ids.end()), rays(ids.size());
   for (size_t i = 0; i < ids.size(); ++i) {
     rays[i] = ctx->objs_host[ids[i]].n_rays;
@@ -727,13 +760,17 @@ romap_status run_fwd_bwd(romap_ctx* ctx, const std::vector<int32_t>& ids, BatchD
     b.plan_cap_tiles = (int32_t)ctx->cap_plan[3];
     SampleBuf none{};
     if (ctx->tile_kernel < 0) ROMAP_TRY(autotune_tile_kernel(ctx, v_ids_for_tuning(ids), b, (int)max_tiles));
+    if (overlap_prev_adam) ROMAP_TRY(fork_prev_adam(ctx, b));
     ROMAP_TRY(run_sampling_mixed(ctx, b, ctx->R, none, ctx->block_sums, ctx->dyn, ctx->totals));
+    if (overlap_prev_adam) CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     PhaseScope ps(ctx, 3, 1);
     kTileKernels[ctx->tile_kernel](ctx->g, b, ctx->dyn, ctx->R, ctx->status, (int)max_tiles, tile_ctas(ctx),
                                    ctx->stream);
     ctx->launches += 1;
   } else {
+    if (overlap_prev_adam) ROMAP_TRY(fork_prev_adam(ctx, b));
     ROMAP_TRY(run_sampling(ctx, b, ctx->R, ctx->S, ctx->block_sums, ctx->dyn, ctx->totals, true));
+    if (overlap_prev_adam) CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     {
       PhaseScope ps(ctx, 1, 1);
       launch_tile_mlp(0, ctx->g, b, ctx->dyn, ctx->totals, ctx->R, ctx->S, tile_ctas(ctx), ctx->stream);
@@ -910,6 +947,10 @@ romap_status romap_destroy(romap_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->cap_side) cudaStreamDestroy(ctx->cap_side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (auto& o : ctx->objs)
     if (o.alive) free_object(ctx, o);
   dev_free(ctx, ctx->objs_dev);
@@ -1390,6 +1431,36 @@ static romap_status enqueue_step(romap_ctx* ctx, const std::vector<int32_t>& v) 
   return ROMAP_OK;
 }
 
+// Pieces of a pipelined run of n_steps > 1 steps of one batch in one call: kind 1, the first step without its Adam
+// update; kind 2, a step whose sampling overlaps the previous step's Adam update; kind 3, the last step's update.
+// Kind 0 is a whole step (enqueue_step).  The parameters after kinds 1, 2 x (n - 1), 3 are those after n whole
+// steps, bit for bit: the sampling reads no parameter, and the update of a step uses that step's bias corrections.
+static romap_status enqueue_kind(romap_ctx* ctx, const std::vector<int32_t>& v, int kind) {
+  if (kind == 0) return enqueue_step(ctx, v);
+  if (kind == 3) {
+    std::vector<int32_t> rays(v.size());
+    for (size_t i = 0; i < v.size(); ++i) rays[i] = ctx->objs_host[v[i]].n_rays;
+    HostBatch hb;
+    build_batch(v, rays, &hb);
+    BatchDesc b;
+    ROMAP_TRY(upload_batch(ctx, hb, &b));
+    launch_adam_update(ctx->g, b, ctx->cfg.precision != ROMAP_PREC_FP32, 1, ctx->stream);
+    ctx->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    return ROMAP_OK;
+  }
+  BatchDesc b;
+  ROMAP_TRY(run_fwd_bwd(ctx, v, &b, kind == 2));
+  launch_advance_step(ctx->g, b, ctx->stream);
+  ctx->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  for (int32_t id : v) {
+    ctx->objs[id].steps_done += 1;
+    set_object_step(ctx->objs_host[id], (uint32_t)(ctx->objs[id].steps_done + 1), ctx->cfg.beta1, ctx->cfg.beta2);
+  }
+  return ROMAP_OK;
+}
+
 constexpr int kMaxStepGraphs = 128;
 
 static void free_graph(romap_ctx* ctx, romap_ctx::StepGraph& sg) {
@@ -1423,8 +1494,13 @@ static romap_ctx::StepGraph* find_graph(romap_ctx* ctx, const std::vector<int32_
 // Captures one step of batch v (nothing executes during capture) into a new cache entry, evicting the least recently
 // used entry when the cache is full.  The graph reads its batch arrays from its own device copy, so graphs of
 // different compositions replay in any order without re-uploading anything.
-static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, const std::vector<int32_t>& key) {
-  if (!ctx->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, const std::vector<int32_t>& key,
+                                 int kind = 0) {
+  if (!ctx->cap_stream) {  // the highest priority: a captured step's sampling goes ahead of the overlapping update
+    int least = 0, greatest = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CUDA_TRY(cudaStreamCreateWithPriority(&ctx->cap_stream, cudaStreamNonBlocking, greatest));
+  }
   if ((int)ctx->graphs.size() >= kMaxStepGraphs) {
     size_t lru = 0;
     for (size_t i = 1; i < ctx->graphs.size(); ++i)
@@ -1448,16 +1524,21 @@ static romap_status capture_step(romap_ctx* ctx, const std::vector<int32_t>& v, 
   int64_t saved_launches = ctx->launches;
   cudaStream_t user = ctx->stream;
   ctx->stream = ctx->cap_stream;
+  if (kind == 2) {  // the fork joins the capture through the events
+    ROMAP_TRY(ensure_side(ctx));
+    ctx->side = ctx->cap_side;
+  }
   ctx->batch_override = sg.batch_dev;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
   romap_status st = ROMAP_OK;
   if (e == cudaSuccess) {
-    st = enqueue_step(ctx, v);
+    st = enqueue_kind(ctx, v, kind);
     e = cudaStreamEndCapture(ctx->cap_stream, &graph);
   }
   ctx->batch_override = nullptr;
   ctx->stream = user;
+  if (ctx->side_stream) ctx->side = ctx->side_stream;
   for (size_t i = 0; i < v.size(); ++i) {
     ctx->objs[v[i]].steps_done = done[i];
     set_object_step(ctx->objs_host[v[i]], (uint32_t)(done[i] + 1), ctx->cfg.beta1, ctx->cfg.beta2);
@@ -1498,17 +1579,23 @@ romap_status run_train_steps(romap_ctx* ctx, const std::vector<int32_t>& v, int3
       if (ctx->objs[i].alive) largest = std::max(largest, ctx->objs_host[i].n_rays);
     if (largest > 0) ROMAP_TRY(ensure_step_workspace(ctx, std::vector<int32_t>{largest}));
   }
-  // the graph key: the batch composition (object slots and their rays per step) and the precision
+  // the graph key: the batch composition (object slots and their rays per step), the precision and the kind of piece
   std::vector<int32_t> key(v.begin(), v.end());
   for (int32_t id : v) key.push_back(ctx->objs_host[id].n_rays);
   key.push_back(ctx->cfg.precision);
-  for (int s = 0; s < n_steps; ++s) {
+  // n_steps > 1: each step's sampling overlaps the previous step's Adam update (kinds 1, 2 ..., 3; enqueue_kind)
+  const bool pipelined = n_steps > 1 && !ctx->profiling;
+  auto run_piece = [&](int kind) -> romap_status {
+    std::vector<int32_t> k = key;
+    k.push_back(kind);
     const bool use_graph = ctx->graphs_enabled && !ctx->profiling;
-    romap_ctx::StepGraph* sg = use_graph ? find_graph(ctx, key) : nullptr;
+    romap_ctx::StepGraph* sg = use_graph ? find_graph(ctx, k) : nullptr;
     if (sg) {
       CUDA_TRY(cudaGraphLaunch(sg->exec, ctx->stream));
       sg->last_use = ++ctx->graph_clock;
       ctx->graph_replays += 1;
+      ctx->launches += sg->launches;
+      if (kind == 3) return ROMAP_OK;
       ctx->last_batch = sg->batch;
       ctx->last_batch_n = sg->batch_n;
       // what enqueue_step does on the host for each step
@@ -1520,12 +1607,14 @@ romap_status run_train_steps(romap_ctx* ctx, const std::vector<int32_t>& v, int3
       }
       ctx->stats.steps += (int64_t)v.size();
       ctx->stats.rays += rays;
-      ctx->launches += sg->launches;
-      continue;
+      return ROMAP_OK;
     }
-    ROMAP_TRY(enqueue_step(ctx, v));
-    if (use_graph) ROMAP_TRY(capture_step(ctx, v, key));
-  }
+    ROMAP_TRY(enqueue_kind(ctx, v, kind));
+    if (use_graph) ROMAP_TRY(capture_step(ctx, v, k, kind));
+    return ROMAP_OK;
+  };
+  for (int s = 0; s < n_steps; ++s) ROMAP_TRY(run_piece(pipelined ? (s == 0 ? 1 : 2) : 0));
+  if (pipelined) ROMAP_TRY(run_piece(3));
   return ROMAP_OK;
 }
 

@@ -94,6 +94,7 @@ struct ObjectDev {
   int32_t whole_pool;      // 1 if the whole pool is used in order
   uint32_t step;           // Adam step about to run (1-based); advanced after the Adam kernel
   float bc1, bc2;          // Adam bias corrections of that step: 1 / (1 - beta1^step), 1 / (1 - beta2^step)
+  float bc1_prev, bc2_prev; // those of the step before (the update that runs after the counter has advanced)
   int32_t pad_;
   unsigned long long* gfix; // deterministic mode: fixed-point gradient accumulator [n_params_pad], else null
   uint8_t* touched;        // per chunk of kAdamChunk parameters: 1 once any gradient entry was non-zero (or null:
@@ -108,6 +109,11 @@ __host__ __device__ inline void adam_bias_corrections(float beta1, float beta2, 
 __host__ __device__ inline void set_object_step(ObjectDev& d, uint32_t t, float beta1, float beta2) {
   d.step = t;
   adam_bias_corrections(beta1, beta2, t, &d.bc1, &d.bc2);
+  if (t >= 2) {
+    adam_bias_corrections(beta1, beta2, t - 1u, &d.bc1_prev, &d.bc2_prev);
+  } else {
+    d.bc1_prev = d.bc2_prev = 1.0f;
+  }
 }
 
 // Per-batch-object values written on the device during a step.
@@ -268,6 +274,10 @@ void launch_tile_mlp(int mode, const GridParams& g, const BatchDesc& b, const Ba
 void launch_composite(int mode, const GridParams& g, const BatchDesc& b, RayBuf r, SampleBuf s, BatchDyn* dyn,
                       int32_t* status, cudaStream_t stream);
 void launch_adam(const GridParams& g, const BatchDesc& b, int write_half, cudaStream_t stream);
+// the two halves of launch_adam: the update (prev: of the step before the object's current step counter) and the
+// step-counter advance
+void launch_adam_update(const GridParams& g, const BatchDesc& b, int write_half, int prev, cudaStream_t stream);
+void launch_advance_step(const GridParams& g, const BatchDesc& b, cudaStream_t stream);
 // Deterministic mode, after the backward: adds each object's fixed-point gradient into its FP32 gradient (entries
 // with a zero accumulator are left alone), zeroes the accumulator, and converts the fixed-point loss sums.
 void launch_fix_finish(const GridParams& g, const BatchDesc& b, BatchDyn* dyn, cudaStream_t stream);

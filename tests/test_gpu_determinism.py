@@ -107,3 +107,62 @@ def test_deterministic_gradient_matches_oracle_and_atomic_path():
     assert np.allclose(losses[0], losses[1], rtol=1e-5, atol=1e-8)
     assert_grad_close(grads[0], grads[1], tol=1e-5, what="deterministic vs atomic FP32")
     assert np.array_equal(grads[0] != 0, grads[1] != 0)  # the same entries receive gradient
+
+
+@pytest.mark.parametrize("per_object", [False, True])
+def test_pipelined_steps_equal_single_steps(per_object):
+    """n_steps > 1 in one call runs each step's sampling beside the previous step's Adam update (a second stream,
+    captured as a fork in the step graphs).  In the deterministic mode the result is bit for bit that of the same
+    number of one-step calls: parameters, moments, the step counter and the last step's losses, and so is a second
+    pipelined call (graph replays) continuing from there."""
+    import torch  # noqa: F401
+
+    _, rc = _config()
+    rc.per_object = 1 if per_object else 0
+    scenes, occ = _scenes()
+    out = []
+    for pipelined in (False, True):
+        ctx = Ctx(rc)
+        try:
+            ids = _load(ctx, scenes, occ)
+            if pipelined:
+                la = ctx.train(ids, n_steps=5)
+                lb = ctx.train(ids, n_steps=5)
+            else:
+                la = [ctx.train(ids) for _ in range(5)][-1]
+                lb = [ctx.train(ids) for _ in range(5)][-1]
+            out.append((la, lb, [ctx.state(i) for i in ids]))
+        finally:
+            ctx.close()
+    (la0, lb0, s0), (la1, lb1, s1) = out
+    assert np.array_equal(la0, la1) and np.array_equal(lb0, lb1)
+    for (p0, m0, v0, t0), (p1, m1, v1, t1) in zip(s0, s1):
+        assert t0 == t1 == 10
+        assert np.array_equal(p0, p1) and np.array_equal(m0, m1) and np.array_equal(v0, v1)
+
+
+def test_pipelined_mixed_steps_train_like_single_steps():
+    """The mixed-precision path pipelined the same way: its atomics make single runs differ in the last bits, so the
+    parameters after a pipelined call and after one-step calls agree to the rounding of those sums."""
+    import torch  # noqa: F401
+
+    _, rc = _config(precision=R.ROMAP_PREC_MIXED_BF16)
+    rc.deterministic = 0
+    scenes, occ = _scenes()
+    out = []
+    for pipelined in (False, True):
+        ctx = Ctx(rc)
+        try:
+            ids = _load(ctx, scenes, occ)
+            if pipelined:
+                losses = ctx.train(ids, n_steps=4)
+            else:
+                losses = [ctx.train(ids) for _ in range(4)][-1]
+            out.append((losses, [ctx.state(i) for i in ids]))
+        finally:
+            ctx.close()
+    (l0, s0), (l1, s1) = out
+    assert np.allclose(l0, l1, rtol=1e-3)
+    for (p0, _, _, t0), (p1, _, _, t1) in zip(s0, s1):
+        assert t0 == t1 == 4
+        assert np.abs(p0 - p1).max() <= 1e-3 * np.abs(p0).max()
