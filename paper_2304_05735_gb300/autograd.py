@@ -8,8 +8,17 @@ forward stores every sample's MLP activations and the backward reads them back (
 the activations.  Only ``params`` (the object's hash table and MLP weights, FP32, laid out as romap_param_layout
 describes) receives a gradient.  PyTorch provides device memory and streams; every computation runs in libromap's
 kernels.
+
+``step_loss(rctx, ids, params, step)`` is the front of the training step itself, in the context's precision (the
+fused tcgen05 kernel for the mixed precisions): for every listed object it loads ``params[k]`` into the object,
+draws the rays of training step ``step`` from the object's pool (Sec. V-A), and returns the total loss of Eq. 11 over
+that batch together with its four terms; the backward hands back the gradient romap_forward_backward left in the
+object's gradient buffer, scaled by the upstream gradient of the total.  The objects of the context serve as the
+function's workspace: their parameters, Adam moments (reset to zero) and step counters are overwritten.
 """
 import ctypes as C
+
+import numpy as np
 
 import torch
 
@@ -82,3 +91,54 @@ def render(params, origin, direction, bg, rctx, half=(0.5, 0.5, 0.5), seed=0, st
         recompute = rctx.cfg.n_samples > STORE_MAX_SAMPLES
     return RenderFunction.apply(params, origin, direction, bg, rctx, tuple(half), int(seed), int(step), bool(jitter),
                                 occupancy, not recompute)
+
+
+class StepLossFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rctx, ids, step, *params):
+        n = len(ids)
+        n_params = rctx.layout.n_params
+        dev = params[0].device
+        zeros = torch.zeros(n_params, dtype=torch.float32, device=dev)
+        for oid, p in zip(ids, params):
+            st = R.romap_state(p.data_ptr(), zeros.data_ptr(), zeros.data_ptr(), n_params, step - 1,
+                               R.ROMAP_DEVICE_PTR)
+            R.check(R.romap_set_state(rctx.h, oid, C.byref(st)), "romap_set_state")
+        loss = np.zeros(5 * n, np.float32)
+        R.check(R.romap_forward_backward(rctx.h, (C.c_int32 * n)(*ids), n, loss.ctypes.data),
+                "romap_forward_backward")
+        grads = []
+        for oid in ids:
+            g = torch.empty(n_params, dtype=torch.float32, device=dev)
+            R.check(R.romap_get_grad(rctx.h, oid, g.data_ptr(), R.ROMAP_DEVICE_PTR), "romap_get_grad")
+            grads.append(g)
+        ctx.save_for_backward(*grads)
+        out = torch.from_numpy(loss.reshape(n, 5)).to(dev)
+        total, terms = out[:, 0].contiguous(), out[:, 1:].contiguous()
+        ctx.mark_non_differentiable(terms)
+        return total, terms
+
+    @staticmethod
+    def backward(ctx, grad_total, grad_terms):
+        grads = ctx.saved_tensors
+        return (None, None, None) + tuple(grad_total[k] * g for k, g in enumerate(grads))
+
+
+def step_loss(rctx, ids, params, step):
+    """Per-object total loss (Eq. 11) of training step ``step`` (1-based: the ray draw of the object's step-th
+    training step) at the given parameters, differentiable in them.  rctx: a context with ``h`` (romap_ctx) and
+    ``layout`` bound to torch's current stream; ids: distinct object ids of that context, each with rays in its pool;
+    params: one contiguous FP32 CUDA tensor of n_params per object.  Returns (total [n], terms [n, 4]: the rgb, rr,
+    depth and density sums divided by B, not differentiable)."""
+    ids = tuple(int(i) for i in ids)
+    params = tuple(params)
+    if len(ids) != len(params) or not ids:
+        raise ValueError("one parameter tensor per listed object is required")
+    if len(set(ids)) != len(ids):
+        raise ValueError("listed ids must be distinct")
+    if step < 1:
+        raise ValueError("step counts training steps from 1")
+    for p in params:
+        if not (p.is_cuda and p.dtype == torch.float32 and p.is_contiguous() and p.numel() == rctx.layout.n_params):
+            raise ValueError("params must be contiguous float32 CUDA tensors of n_params elements")
+    return StepLossFunction.apply(rctx, ids, int(step), *params)

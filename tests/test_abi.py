@@ -147,3 +147,26 @@ def test_view_angle_matches_oracle():
     assert R.romap_view_angle(z.ctypes.data, np.ones(3).ctypes.data, z.ctypes.data, C.byref(out)) == R.ROMAP_OK
     assert out.value == 180.0
     assert R.romap_view_angle(None, z.ctypes.data, z.ctypes.data, C.byref(out)) == R.ROMAP_ERR_INVALID_ARG
+
+
+def test_step_loss_checks_its_arguments_on_the_host():
+    """The autograd front of the training step refuses mismatched, duplicate or host tensors before any library
+    call (the stand-in context has no library handle at all)."""
+    torch = pytest.importorskip("torch")
+    from paper_2304_05735_gb300.autograd import step_loss
+
+    class Stub:
+        h = None
+
+        class layout:
+            n_params = 8
+
+    p = torch.zeros(8)
+    with pytest.raises(ValueError):
+        step_loss(Stub, [0, 1], [p], step=1)
+    with pytest.raises(ValueError):
+        step_loss(Stub, [0, 0], [p, p], step=1)
+    with pytest.raises(ValueError):
+        step_loss(Stub, [0], [p], step=0)
+    with pytest.raises(ValueError):
+        step_loss(Stub, [0], [p], step=1)  # a host tensor

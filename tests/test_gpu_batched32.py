@@ -134,7 +134,9 @@ def test_uneven_batch_every_object_mixed_vs_fp32(kernel):
     cos = [float(a[:nh].astype(np.float64) @ b[:nh] / (np.linalg.norm(a[:nh]) * np.linalg.norm(b[:nh])))
            for a, b in zip(gm, gf)]
     mlp = [float(np.linalg.norm(a[nh:] - b[nh:]) / np.linalg.norm(b[nh:])) for a, b in zip(gm, gf)]
-    print(f"\nkernel {kernel}: hash-gradient cosine min {min(cos):.6f}, MLP-gradient rel max {max(mlp):.2e}, "
-          f"loss rel max {np.max(np.abs(lm - lf) / lf):.2e}")
+    print(f"\nkernel {kernel}: hash-gradient cosine min {min(cos):.6f}, MLP-gradient rel max {max(mlp):.2e} "
+          f"(median {np.median(mlp):.2e}), loss rel max {np.max(np.abs(lm - lf) / lf):.2e}")
     assert np.all(np.abs(lm - lf) <= 1e-3 * lf)
-    assert min(cos) > 0.999 and max(mlp) < 0.1
+    # the worst object's MLP-gradient error (4.95e-2) is the same under every schedule and tile order: the BF16
+    # rounding of that object's operands, not the order of its sums
+    assert min(cos) > 0.999 and max(mlp) < 0.06
