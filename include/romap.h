@@ -422,9 +422,8 @@ ROMAP_API romap_status romap_fn_backward(romap_ctx* ctx, const float* params, co
  *    would not fit (about n * (105 + 60 * n_samples) bytes) return
  *    ROMAP_ERR_CAPACITY with the largest n that fits.
  *  - The first call on each device resolves the array's device address
- *    (cudaGetSymbolAddress) with that device current; make it before any
- *    stream capture.  cuda_stream must belong to the current device, else
- *    ROMAP_ERR_INVALID_ARG.
+ *    (cudaGetSymbolAddress) with that device current.  cuda_stream must
+ *    belong to the current device, else ROMAP_ERR_INVALID_ARG.
  *  - The object record and batch arrays are written into the array by a
  *    kernel that receives them by value: nothing is read from host memory
  *    after the call returns.

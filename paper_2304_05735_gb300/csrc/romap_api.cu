@@ -2302,9 +2302,8 @@ romap_status romap_render(romap_ctx* ctx, int32_t id, const float* origin, const
 //
 // Set-up: the first call on each device, with that device current, looks up
 // the array's device address with cudaGetSymbolAddress (host code cannot use
-// the array's name as a device address) and caches it; make that first call
-// before any stream capture.  The caller's stream must belong to the current
-// device (the cached address is that device's).  The object record and the
+// the array's name as a device address) and caches it.  The caller's stream
+// must belong to the current device (the cached address is that device's).  The object record and the
 // batch arrays reach the array through a set-up kernel's by-value parameters,
 // never through a copy from host memory.  All calls on a device share the one array and
 // it keeps the last call's contents: every scratch word the kernels read is
