@@ -44,29 +44,41 @@ __device__ inline bool occupied(const uint64_t* occ, float x, float y, float z, 
 
 // Stratified candidates t_i = t_near + (i + u_i) dt_N, delta_i = t_{i+1} - t_i
 // (last: t_far - t_{N-1}), x_i = o + t_i d; f(i, t, delta, x, y, z, live).
+// u_i is word i mod 4 of the Philox draw (step, slot, jitter, i / 4), or 1/2 without jitter.  The candidates are
+// walked in blocks of 16 whose four draws are independent of one another, so that their rounds overlap instead of
+// running back to back; the next block's first draw comes with them (delta of the block's last candidate).
 template <class Fn>
 __device__ inline void for_candidates(const float o[3], const float d[3], float tn, float tf, int N, uint32_t k0,
                                       uint32_t k1, uint32_t step, uint32_t slot, int jitter, const uint64_t* occ,
                                       const float half[3], const float inv_ext[3], Fn f) {
-  float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
-  U4 rnd = {0, 0, 0, 0};
-  auto t_of = [&](int i) -> float {
-    float u = 0.5f;
-    if (jitter) {
-      if ((i & 3) == 0) rnd = philox(step, slot, kPurposeJitter, (uint32_t)i >> 2, k0, k1);
-      u = u01(u4_word(rnd, i & 3));
-    }
-    return __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, u), step_len));
+  const float step_len = __fdiv_rn(__fsub_rn(tf, tn), (float)N);
+  auto t_at = [&](int i, float u) { return __fadd_rn(tn, __fmul_rn(__fadd_rn((float)i, u), step_len)); };
+  auto draw = [&](int q) -> U4 {
+    if (!jitter || 4 * q >= N) return U4{0u, 0u, 0u, 0u};  // not needed
+    return philox(step, slot, kPurposeJitter, (uint32_t)q, k0, k1);
   };
-  float t_cur = t_of(0);
-  for (int i = 0; i < N; ++i) {
-    float t_next = (i + 1 < N) ? t_of(i + 1) : tf;
-    float dt = __fsub_rn(t_next, t_cur);
-    float x = __fadd_rn(o[0], __fmul_rn(t_cur, d[0]));
-    float y = __fadd_rn(o[1], __fmul_rn(t_cur, d[1]));
-    float z = __fadd_rn(o[2], __fmul_rn(t_cur, d[2]));
-    f(i, t_cur, dt, x, y, z, occupied(occ, x, y, z, half, inv_ext));
-    t_cur = t_next;
+  auto u_of = [&](const U4& r, int w) { return jitter ? u01(u4_word(r, w)) : 0.5f; };
+  U4 r0 = draw(0);
+  float t_cur = t_at(0, u_of(r0, 0));
+  for (int b0 = 0; b0 < N; b0 += 16) {
+    const int q = b0 >> 2;
+    const U4 r1 = draw(q + 1), r2 = draw(q + 2), r3 = draw(q + 3), rn = draw(q + 4);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int i = b0 + j;
+      if (i >= N) break;
+      const int jn = j + 1;
+      const float u_next = jn < 4 ? u_of(r0, jn & 3) : jn < 8 ? u_of(r1, jn & 3) : jn < 12 ? u_of(r2, jn & 3)
+                           : jn < 16 ? u_of(r3, jn & 3) : u_of(rn, 0);
+      const float t_next = i + 1 < N ? t_at(i + 1, u_next) : tf;
+      float dt = __fsub_rn(t_next, t_cur);
+      float x = __fadd_rn(o[0], __fmul_rn(t_cur, d[0]));
+      float y = __fadd_rn(o[1], __fmul_rn(t_cur, d[1]));
+      float z = __fadd_rn(o[2], __fmul_rn(t_cur, d[2]));
+      f(i, t_cur, dt, x, y, z, occupied(occ, x, y, z, half, inv_ext));
+      t_cur = t_next;
+    }
+    r0 = rn;
   }
 }
 

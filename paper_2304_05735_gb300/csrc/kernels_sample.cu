@@ -185,7 +185,7 @@ __device__ inline RayCtx ray_of_thread(const BatchDesc& b) {
 // pool is used, else mulhi32(Philox(step, s, RAY, 0).x, pool size); its
 // background is u01 of Philox(step, s, BG, 0) words 0..2 when random.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ray_setup(GridParams g, BatchDesc b, RayBuf R, uint32_t* block_sums) {
+__global__ void __launch_bounds__(256, 3) k_ray_setup(GridParams g, BatchDesc b, RayBuf R, uint32_t* block_sums) {
   __shared__ uint32_t s_cnt[kPlanCounts];
   if (b.plan && threadIdx.x < kPlanCounts) s_cnt[threadIdx.x] = 0u;
   RayCtx c = ray_of_thread(b);
